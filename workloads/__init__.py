@@ -1,0 +1,111 @@
+"""Seeded synthetic inputs for the H^2-ULV solver.
+
+This module only draws random numbers. It contains none of the solver's
+arithmetic, so the oracle (``oracle/``) and the GPU path
+(``paper_2502_02395_gb300``) can both use it without sharing any part of the
+method.
+
+The point sets are stand-ins for the geometries the paper measures on:
+  * points on a unit-sphere surface, for the paper's Laplace sphere test
+    (Section 6.2; the paper spaces the points evenly, we draw them uniformly
+    at random on the surface);
+  * points uniform in the unit cube, the volume case behind the Yukawa and
+    Laplace-kernel workloads (Section 6.4 uses hemoglobin surface meshes, which
+    are not available here; a random volume set is the harder case for
+    compression).
+All generators use NumPy's PCG64 ``default_rng(seed)`` and return float64.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+__all__ = [
+    "cube_points",
+    "sphere_points",
+    "uniform_rhs",
+    "Workload",
+    "WORKLOADS",
+    "workload",
+]
+
+
+def cube_points(n: int, seed: int) -> np.ndarray:
+    """``n`` points uniform in the unit cube [0,1]^3, shape (n, 3), float64."""
+    rng = np.random.default_rng(seed)
+    return rng.random((n, 3))
+
+
+def sphere_points(n: int, seed: int) -> np.ndarray:
+    """``n`` points uniform on the unit sphere surface (normalised Gaussians)."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((n, 3))
+    return g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
+def uniform_rhs(n: int, seed: int, nrhs: int = 1) -> np.ndarray:
+    """Right-hand side entries uniform in [-1, 1]; shape (n,) or (n, nrhs)."""
+    rng = np.random.default_rng(seed)
+    b = rng.uniform(-1.0, 1.0, size=(n, nrhs))
+    return b[:, 0].copy() if nrhs == 1 else b
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """A named problem: geometry, kernel and solver parameters.
+
+    ``kernel`` is one of ``laplace_eps`` (1/(r+eps), diagonal 1/eps),
+    ``yukawa_eps`` (exp(-r)/(r+eps), diagonal 1/eps + diag_shift),
+    ``gaussian``, ``laplace_paper`` (Eq. 35), ``yukawa_paper`` (Eq. 36) and
+    ``poly2_test`` ((1 + x.y)^2 + diag_shift on the diagonal; every
+    off-diagonal block has rank <= 10).
+    """
+
+    name: str
+    n: int
+    geometry: str  # "cube" | "sphere"
+    point_seed: int
+    rhs_seed: int
+    kernel: str
+    leaf: int
+    eta: float
+    tol: float
+    max_rank: int = 0  # 0: the default cap (half the box dimension)
+    eps: float = 1e-3
+    ell: float = 1.0
+    diag_shift: float = 0.0
+    far_samples: int = 1024
+    near_samples: int = 64
+
+    def points(self) -> np.ndarray:
+        if self.geometry == "cube":
+            return cube_points(self.n, self.point_seed)
+        if self.geometry == "sphere":
+            return sphere_points(self.n, self.point_seed)
+        raise ValueError(self.geometry)
+
+    def rhs(self, nrhs: int = 1) -> np.ndarray:
+        return uniform_rhs(self.n, self.rhs_seed, nrhs)
+
+
+# The solver configurations the library is measured and tested on.
+WORKLOADS = {
+    # 2048 points in the unit cube, 1/(r+1e-3), leaf 64, eta 1, tol 1e-10.
+    "cube2048_laplace": Workload("cube2048_laplace", 2048, "cube", 1, 2,
+                                 "laplace_eps", 64, 1.0, 1e-10),
+    # Its compressing twin (tol 1e-4), where elimination really drops terms.
+    "cube2048_laplace_tol4": Workload("cube2048_laplace_tol4", 2048, "cube", 1, 2,
+                                      "laplace_eps", 64, 1.0, 1e-4),
+    # 65536 points on the unit sphere, 1/(r+1e-3), leaf 256, tol 1e-8, FP64.
+    "sphere65536_laplace": Workload("sphere65536_laplace", 65536, "sphere", 3, 4,
+                                    "laplace_eps", 256, 1.0, 1e-8),
+    # 262144 points in the unit cube, Yukawa exp(-r)/(r+1e-3) + 1 on the
+    # diagonal, leaf 256, eta 1, tol 1e-10 with the default rank cap.
+    "cube262144_yukawa": Workload("cube262144_yukawa", 262144, "cube", 5, 6,
+                                  "yukawa_eps", 256, 1.0, 1e-10, diag_shift=1.0),
+}
+
+
+def workload(name: str) -> Workload:
+    return WORKLOADS[name]
