@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Factor + refined-solve benchmark of the GB300 H^2-ULV solver.
+
+Metric: seconds for h2_factor + h2_solve to reach a relative residual
+||b - A_H2 x|| / ||b|| <= 1e-10 at N = 2^18 (points uniform in the unit cube,
+Yukawa kernel exp(-r)/(r+1e-3) with diagonal + 1, leaf 256, eta 1), mixed
+precision (FP16 contractions + FP64 refinement) against the plain FP64
+factorization on the same instance, one GB300.
+
+One step = one full factorization (all levels) + one refined solve, with the
+H^2 instance (h2_build, not timed) resident in HBM.  Inputs (13 GB of FP64
+leaf blocks, ~30 GB of factors) are far larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank solves its own replica of the problem
+("replicas only": the method has no data-path exchange on one system).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "factor+solve s at N=2^18 to 1e-10 residual: mixed-prec vs FP64 H²-ULV, 1 GB300"
+UNIT = "s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube262144_yukawa")
+    ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16", "fp64"])
+    ap.add_argument("--target", type=float, default=1e-10)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-n", type=int, default=8192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks ---
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- oracle arm ---
+def oracle_sample(wl, n_sample: int, target: float):
+    """Time the FP64 oracle (factor + refinement) on a sample of the workload:
+    the same geometry, kernel, leaf, eta and tolerance at n_sample points.
+    Returns (seconds for the sample, seconds scaled to the full N, threads)."""
+    import dataclasses
+
+    from oracle import ulv
+    from oracle.construct import construct
+    from oracle.kernels import Kernel
+    import workloads as W
+    ws = dataclasses.replace(wl, n=n_sample)
+    P = ws.points()
+    b = ws.rhs()
+    H = construct(P, Kernel(wl.kernel, eps=wl.eps, ell=wl.ell, diag_shift=wl.diag_shift), wl.leaf, wl.eta, wl.tol,
+                  wl.max_rank, wl.far_samples, wl.near_samples)
+    t0 = time.perf_counter()
+    F = ulv.factor(H)
+    x, hist = ulv.refine(F, H, b, target, 60)
+    dt = time.perf_counter() - t0
+    return dt, dt * (wl.n / n_sample), hist
+
+
+def threads_used() -> int:
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        if os.environ.get(v, "").isdigit():
+            return int(os.environ[v])
+    return os.cpu_count() or 1
+
+
+def run_reference(args, wl):
+    """--impl reference: the FP64 CPU oracle, timed per step on a bounded
+    sample of the workload and scaled to the full N (the method is O(N))."""
+    steps = []
+    hist = None
+    for k in range(args.warmup + args.steps):
+        dt, scaled, hist = oracle_sample(wl, args.cpu_sample_n, args.target)
+        if k >= args.warmup:
+            steps.append(scaled)
+    value = float(np.mean(steps))
+    sample = (f"oracle factor + refinement to {args.target:g} at N={args.cpu_sample_n} (same kernel, leaf, eta, "
+              f"tol, cube geometry), time scaled by N/{args.cpu_sample_n} = {wl.n / args.cpu_sample_n:g}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "N": wl.n, "kernel": wl.kernel, "leaf": wl.leaf, "eta": wl.eta,
+                       "tol": wl.tol, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "refinement_history": hist}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm ---
+PHASES = ("a1_qr", "a2_proj", "a3_lu", "a45_schur", "a2c_coupling", "a6_merge", "a7_root")
+
+
+def roofline_for(phase, stats, t_phase, peaks, prec, tc):
+    """Roofline of one factorization phase (algorithmic flops / CUDA-event time)."""
+    fl = stats["flops"]
+    key = {"a1_qr": "a1_qr", "a2_proj": "a2_proj", "a3_lu": "a3_lu", "a45_schur": "a45_schur",
+           "a2c_coupling": "a2c_coupling"}.get(phase)
+    if key is None or t_phase <= 0:
+        return None
+    achieved = fl[key] / t_phase / 1e12
+    if phase in ("a2_proj", "a45_schur", "a2c_coupling") and tc:
+        bound, peak, src = "tensor", peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops"), "measured"
+    else:
+        # SIMT arithmetic: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
+        bound = "alu"
+        fp32 = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak = fp32 if prec != "fp64" and phase != "a3_lu" else fp32 / 64.0
+        src = "derived"
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "phase": phase, "peak_source": src}
+
+
+def main():
+    args = parse()
+    import workloads as W
+    wl = W.workload(args.workload)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        from paper_2502_02395_gb300 import build as bld
+        bld.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2502_02395_gb300 import H2Solver, h2_solve
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+
+    P = wl.points()
+    b = wl.rhs()
+    t0 = time.perf_counter()
+    S = H2Solver.build(P, kernel=wl.kernel, leaf=wl.leaf, eta=wl.eta, tol=wl.tol, max_rank=wl.max_rank,
+                       far_samples=wl.far_samples, near_samples=wl.near_samples, eps=wl.eps, ell=wl.ell,
+                       diag_shift=wl.diag_shift)
+    build_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    S.set_stream(stream)
+    b_dev = torch.from_numpy(b).cuda()
+    x_dev = torch.zeros_like(b_dev)
+    torch.cuda.synchronize()
+
+    def step(prec):
+        S.factor(prec)
+        st, rel, its = h2_solve(S.ctx, b_dev, x_dev, args.target, 200, check=False)
+        return st, rel, its
+
+    for _ in range(args.warmup):
+        step(args.prec)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches0 = S.stats()["kernel_launches"]
+    sampler = ClockSampler(local)
+    sampler.start()
+    ph = {p: 0.0 for p in PHASES}
+    ph["factor"] = 0.0
+    ph["solve"] = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rels, its_all = [], []
+    for _ in range(args.steps):
+        st, rel, its = step(args.prec)
+        s = S.stats()
+        for p in PHASES:
+            ph[p] += s["times"][p]
+        ph["factor"] += s["times"]["factor"]
+        ph["solve"] += s["times"]["solve"]
+        rels.append(rel)
+        its_all.append(its)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_ms = e0.elapsed_time(e1) / args.steps
+    launches = S.stats()["kernel_launches"] - launches0
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    stats = S.stats()
+    for k in ph:
+        ph[k] /= args.steps
+    x_host = x_dev.cpu().numpy()
+
+    # end to end through the C ABI with host buffers (H2D of b, D2H of x inside)
+    xh = np.zeros_like(b)
+    from paper_2502_02395_gb300 import h2_factor
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h2_factor(S.ctx, args.prec)
+        h2_solve(S.ctx, b, xh, args.target, 200, check=False)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+
+    # the plain FP64 H^2-ULV on the same instance (the metric's comparison)
+    fp64 = None
+    if args.fp64_steps > 0 and args.prec != "fp64":
+        step("fp64")
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        r64 = []
+        for _ in range(args.fp64_steps):
+            r64.append(step("fp64"))
+        f1.record(stream)
+        torch.cuda.synchronize()
+        s64 = S.stats()
+        fp64 = {"s_per_step": f0.elapsed_time(f1) / args.fp64_steps / 1e3, "relres": r64[-1][1],
+                "iters": r64[-1][2], "factor_s": s64["times"]["factor"], "solve_s": s64["times"]["solve"],
+                "phases": {p: s64["times"][p] for p in PHASES}}
+
+    # dominant phase and its roofline
+    tc = stats.get("tensor_cores", False)
+    top = max(PHASES, key=lambda p: ph[p])
+    roof = roofline_for(top, stats, ph[top], peaks, args.prec, tc)
+    roof_proj = roofline_for("a2_proj", stats, ph["a2_proj"], peaks, args.prec, tc)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, scaled, hist = oracle_sample(wl, args.cpu_sample_n, args.target)
+        cpu = {"value": scaled, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
+               "sample": f"oracle factor + refinement at N={args.cpu_sample_n} of the same workload took {dt:.2f} s; "
+                         f"scaled by N/{args.cpu_sample_n} (the method is O(N))"}
+
+    value = t_ms / 1e3
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp16": "f16/f32/f64", "bf16": "bf16/f32/f64", "fp64": "f64"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": wl.name, "N": wl.n, "geometry": wl.geometry, "kernel": wl.kernel, "leaf": wl.leaf,
+                   "eta": wl.eta, "tol": wl.tol, "prec": args.prec, "target_relres": args.target,
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "no flush: inputs (13 GB leaf blocks, factors) exceed L2"},
+        "relres": float(np.max(rels)), "iters": int(np.max(its_all)),
+        "phases_s": ph, "build_s": build_s, "fp64": fp64,
+        "speedup_vs_fp64": (fp64["s_per_step"] / value) if fp64 else None,
+        "roofline": roof, "roofline_a2_proj": roof_proj,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(b.nbytes), "d2h_bytes_per_step": int(b.nbytes)},
+        "gpu_launches": int(launches), "clocks": clocks,
+        "levels": stats["levels"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+"""ctypes binding of the C ABI declared in include/h2ulv.h.
+
+The module-level functions carry the C names (h2_build, h2_import,
+h2_factor, h2_solve, h2_ulv_apply, h2_matvec, h2_set_stream, h2_stats,
+h2_export, h2_last_error, h2_destroy) and only marshal arguments: every step
+of the computation runs in the library.  ``H2Solver`` wraps a context.
+
+Vectors may be NumPy float64 arrays (host) or CUDA torch float64 tensors
+(device); the library tells the two apart.  The library must have been built
+(``paper_2502_02395_gb300.build.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libh2ulv.so")
+
+KERNELS = {"laplace_eps": 0, "yukawa_eps": 1, "gaussian": 2, "laplace_paper": 3,
+           "yukawa_paper": 4, "poly2_test": 5}
+PRECS = {"fp64": 0, "fp16": 1, "bf16": 2}
+STATUS = {0: "H2_OK", -1: "H2_ERR_INVALID_ARG", -2: "H2_ERR_OOM", -3: "H2_ERR_SINGULAR",
+          -4: "H2_ERR_NOT_CONVERGED", -5: "H2_ERR_CUDA", -6: "H2_ERR_TIMEOUT", -7: "H2_ERR_STATE"}
+
+# every symbol include/h2ulv.h declares
+EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_ulv_apply", "h2_matvec",
+            "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
+
+
+class H2Error(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("eps", ctypes.c_double), ("ell", ctypes.c_double),
+                ("diag_shift", ctypes.c_double), ("leaf_size", ctypes.c_int32), ("eta", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_rank", ctypes.c_int32), ("far_samples", ctypes.c_int32),
+                ("near_samples", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("L", ctypes.c_int32), ("points", _P), ("perm", _P),
+                ("leaf_offsets", _P), ("D", _P), ("K", _P), ("n_near", _P), ("near", _P),
+                ("n_far", _P), ("far", _P), ("X", _P), ("SK", _P)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2502_02395_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "h2_build": (i32, [pp, vp, vp, i64]),
+            "h2_plan": (i32, [vp, vp, i64, ctypes.c_char_p, ctypes.c_size_t]),
+            "h2_import": (i32, [pp, vp, vp]),
+            "h2_factor": (i32, [vp, i32]),
+            "h2_solve": (i32, [vp, vp, vp, dbl, i32, vp, vp]),
+            "h2_ulv_apply": (i32, [vp, vp, vp]),
+            "h2_matvec": (i32, [vp, vp, vp]),
+            "h2_set_stream": (i32, [vp, vp]),
+            "h2_stats": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+            "h2_export": (i32, [vp, ctypes.c_char_p, i32, vp, ctypes.c_size_t, vp, vp]),
+            "h2_last_error": (ctypes.c_char_p, [vp]),
+            "h2_destroy": (None, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """Address of a NumPy array or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(st: int, ctx=None):
+    if st != 0:
+        msg = lib().h2_last_error(ctx)
+        raise H2Error(st, msg.decode() if msg else "")
+
+
+def make_params(kernel="laplace_eps", leaf=256, eta=1.0, tol=1e-10, max_rank=0, far_samples=1024,
+                near_samples=64, eps=1e-3, ell=1.0, diag_shift=0.0) -> Params:
+    return Params(KERNELS[kernel] if isinstance(kernel, str) else int(kernel), eps, ell, diag_shift, leaf,
+                  eta, tol, max_rank, far_samples, near_samples)
+
+
+# ------------------------------------------------------------ C names ---
+def h2_build(params: Params, points: np.ndarray):
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    out = ctypes.c_void_p()
+    st = lib().h2_build(ctypes.byref(out), ctypes.byref(params), _ptr(pts), len(pts))
+    _check(st, None)
+    return out
+
+
+def h2_plan(params: Params, points: np.ndarray) -> dict:
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    buf = ctypes.create_string_buffer(1 << 20)
+    st = lib().h2_plan(ctypes.byref(params), _ptr(pts), len(pts), buf, len(buf))
+    _check(st, None)
+    return json.loads(buf.value.decode())
+
+
+def h2_import(params: Params, flat: dict):
+    """flat: the dict of arrays oracle.instance.flatten produces."""
+    L = int(flat["L"])
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    def ptrs(lst, dt):
+        vals = [arr(a, dt) if a is not None else 0 for a in lst]
+        a = (ctypes.c_void_p * len(vals))(*vals)
+        keep.append(a)
+        return ctypes.cast(a, ctypes.c_void_p)
+
+    inst = Instance()
+    inst.N = int(flat["N"])
+    inst.L = L
+    inst.points = arr(flat["points"], np.float64)
+    inst.perm = arr(flat["perm"], np.int64)
+    inst.leaf_offsets = arr(flat["leaf_offsets"], np.int64)
+    inst.D = arr(flat["D"], np.int32)
+    inst.K = arr(flat["K"], np.int32)
+    inst.n_near = arr([len(a) for a in flat["near"]], np.int64)
+    inst.near = ptrs([np.asarray(a).reshape(-1, 2) for a in flat["near"]], np.int32)
+    inst.n_far = arr([len(a) for a in flat["far"]], np.int64)
+    inst.far = ptrs([np.asarray(a).reshape(-1, 2) if len(a) else np.zeros((0, 2)) for a in flat["far"]],
+                    np.int32)
+    inst.X = ptrs([None] + [flat["X"][l] for l in range(1, L + 1)], np.float64)
+    inst.SK = ptrs([None] + [flat["SK"][l] for l in range(1, L + 1)], np.int64)
+    out = ctypes.c_void_p()
+    st = lib().h2_import(ctypes.byref(out), ctypes.byref(params), ctypes.byref(inst))
+    _check(st, None)
+    return out
+
+
+def h2_factor(ctx, prec: str | int = "fp64"):
+    _check(lib().h2_factor(ctx, PRECS[prec] if isinstance(prec, str) else prec), ctx)
+
+
+def h2_solve(ctx, b, x, target=1e-10, max_iters=50, check=True):
+    rel = ctypes.c_double()
+    its = ctypes.c_int32()
+    st = lib().h2_solve(ctx, _ptr(b), _ptr(x), target, max_iters, ctypes.byref(rel), ctypes.byref(its))
+    if check:
+        _check(st, ctx)
+    return st, rel.value, its.value
+
+
+def h2_ulv_apply(ctx, b, x):
+    _check(lib().h2_ulv_apply(ctx, _ptr(b), _ptr(x)), ctx)
+
+
+def h2_matvec(ctx, x, y):
+    _check(lib().h2_matvec(ctx, _ptr(x), _ptr(y)), ctx)
+
+
+def h2_set_stream(ctx, stream):
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().h2_set_stream(ctx, ctypes.c_void_p(int(handle) if handle else 0)), ctx)
+
+
+def h2_stats(ctx) -> dict:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().h2_stats(ctx, buf, len(buf)), ctx)
+    return json.loads(buf.value.decode())
+
+
+def h2_export(ctx, name: str, level: int = 0) -> np.ndarray:
+    cnt = ctypes.c_size_t()
+    es = ctypes.c_int32()
+    _check(lib().h2_export(ctx, name.encode(), level, None, 0, ctypes.byref(cnt), ctypes.byref(es)), ctx)
+    dt = {("perm", 8): np.int64, ("piv", 4): np.int32, ("root_piv", 4): np.int32}.get(
+        (name, es.value), np.float64 if es.value == 8 else np.float32)
+    out = np.empty(cnt.value, dtype=dt)
+    _check(lib().h2_export(ctx, name.encode(), level, _ptr(out), out.nbytes, ctypes.byref(cnt),
+                           ctypes.byref(es)), ctx)
+    return out
+
+
+def h2_last_error(ctx=None) -> str:
+    m = lib().h2_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def h2_destroy(ctx):
+    lib().h2_destroy(ctx)
+
+
+# ------------------------------------------------------------ wrapper ---
+class H2Solver:
+    """A factorizable H^2 instance on the current CUDA device."""
+
+    def __init__(self, ctx, n: int):
+        self.ctx = ctx
+        self.n = n
+
+    @classmethod
+    def build(cls, points, **kw):
+        return cls(h2_build(make_params(**kw), points), len(points))
+
+    @classmethod
+    def from_instance(cls, flat: dict, **kw):
+        return cls(h2_import(make_params(**kw), flat), int(flat["N"]))
+
+    def factor(self, prec="fp64"):
+        h2_factor(self.ctx, prec)
+
+    def solve(self, b, target=1e-10, max_iters=50, x=None):
+        if x is None:
+            x = np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)
+        st, rel, its = h2_solve(self.ctx, b, x, target, max_iters)
+        return x, rel, its
+
+    def ulv_apply(self, b):
+        x = np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)
+        h2_ulv_apply(self.ctx, b, x)
+        return x
+
+    def matvec(self, x):
+        y = np.zeros_like(x) if isinstance(x, np.ndarray) else x.new_zeros(x.shape)
+        h2_matvec(self.ctx, x, y)
+        return y
+
+    def set_stream(self, stream):
+        h2_set_stream(self.ctx, stream)
+
+    def stats(self) -> dict:
+        return h2_stats(self.ctx)
+
+    def export(self, name, level=0):
+        return h2_export(self.ctx, name, level)
+
+    def close(self):
+        if self.ctx:
+            h2_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

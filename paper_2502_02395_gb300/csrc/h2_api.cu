@@ -1,0 +1,761 @@
+// C ABI of the H^2-ULV library: context setup, factorization driver,
+// substitution / refinement driver, matvec, export and statistics.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <sstream>
+
+#include "h2_internal.h"
+#include "kernels.h"
+
+using namespace h2;
+
+std::atomic<long long> h2::g_launches{0};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+#define CKC(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      c->err = std::string(#call) + ": " + cudaGetErrorString(e_);                       \
+      return e_ == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA;                \
+    }                                                                                   \
+  } while (0)
+
+#define CKS(call)                      \
+  do {                                 \
+    h2_status s_ = (call);             \
+    if (s_ != H2_OK) return s_;        \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+h2_status check_params(const h2_params* p, std::string& err) {
+  if (!p) { err = "params is NULL"; return H2_ERR_INVALID_ARG; }
+  if (p->kernel < 0 || p->kernel > H2_K_POLY2_TEST) { err = "unknown kernel"; return H2_ERR_INVALID_ARG; }
+  if (p->leaf_size < 1) { err = "leaf_size < 1"; return H2_ERR_INVALID_ARG; }
+  if (!(p->eta >= 0.0)) { err = "eta < 0"; return H2_ERR_INVALID_ARG; }
+  if (!(p->tol > 0.0)) { err = "tol <= 0"; return H2_ERR_INVALID_ARG; }
+  if (p->max_rank < 0) { err = "max_rank < 0"; return H2_ERR_INVALID_ARG; }
+  if ((p->kernel == H2_K_LAPLACE_EPS || p->kernel == H2_K_YUKAWA_EPS) && !(p->eps > 0.0)) {
+    err = "eps <= 0";
+    return H2_ERR_INVALID_ARG;
+  }
+  if (p->kernel == H2_K_GAUSSIAN && !(p->ell > 0.0)) { err = "ell <= 0"; return H2_ERR_INVALID_ARG; }
+  return H2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device setup from the host structure
+// ---------------------------------------------------------------------------
+template <typename V>
+h2_status upload(h2_ctx* c, V** dst, const std::vector<V>& src) {
+  CKC(dalloc(c, dst, src.size()));
+  if (!src.empty()) CKC(cudaMemcpy(*dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return H2_OK;
+}
+
+h2_status setup_device(h2_ctx* c) {
+  HostH2& H = c->host;
+  c->L = H.L;
+  c->N = H.N;
+  const int L = H.L;
+  CKC(cudaGetDevice(&c->dev));
+  c->lv.assign(L + 1, DevLevel());
+  for (int l = 0; l <= L; ++l) {
+    DevLevel& d = c->lv[l];
+    const HostLevel& h = H.lv[l];
+    d.nb = 1 << l;
+    d.D = h.D;
+    d.K = l ? h.K : 0;
+    d.R = d.D - d.K;
+    d.NP = (int64_t)h.near.size() / 2;
+    d.FP = (int64_t)h.far.size() / 2;
+    d.h_near_ptr.assign(d.nb + 1, 0);
+    d.h_far_ptr.assign(d.nb + 1, 0);
+    d.h_diag_pair.assign(d.nb, -1);
+    for (int64_t q = 0; q < d.NP; ++q) {
+      int i = h.near[2 * q], j = h.near[2 * q + 1];
+      d.h_near_i.push_back(i);
+      d.h_near_j.push_back(j);
+      d.h_near_ptr[i + 1]++;
+      if (i == j) d.h_diag_pair[i] = (int32_t)q;
+    }
+    for (int64_t q = 0; q < d.FP; ++q) {
+      d.h_far_i.push_back(h.far[2 * q]);
+      d.h_far_j.push_back(h.far[2 * q + 1]);
+      d.h_far_ptr[h.far[2 * q] + 1]++;
+    }
+    for (int i = 0; i < d.nb; ++i) {
+      d.h_near_ptr[i + 1] += d.h_near_ptr[i];
+      d.h_far_ptr[i + 1] += d.h_far_ptr[i];
+      if (d.h_diag_pair[i] < 0) {
+        c->err = "level " + std::to_string(l) + " box " + std::to_string(i) + " lacks its diagonal near pair";
+        return H2_ERR_INVALID_ARG;
+      }
+    }
+    CKS(upload(c, &d.near_i, d.h_near_i));
+    CKS(upload(c, &d.near_j, d.h_near_j));
+    CKS(upload(c, &d.near_ptr, d.h_near_ptr));
+    CKS(upload(c, &d.diag_pair, d.h_diag_pair));
+    CKS(upload(c, &d.far_i, d.h_far_i));
+    CKS(upload(c, &d.far_j, d.h_far_j));
+    CKS(upload(c, &d.far_ptr, d.h_far_ptr));
+    if (l >= 1) {
+      CKS(upload(c, &d.X, h.X));
+      CKS(upload(c, &d.SK, h.SK));
+    }
+  }
+  // parent near-pair index of every near and far pair (merge destinations)
+  for (int l = 1; l <= L; ++l) {
+    DevLevel& d = c->lv[l];
+    const DevLevel& pd = c->lv[l - 1];
+    std::map<std::pair<int, int>, int32_t> pidx;
+    for (int64_t q = 0; q < pd.NP; ++q) pidx[{pd.h_near_i[q], pd.h_near_j[q]}] = (int32_t)q;
+    auto find = [&](int i, int j, int32_t& out) -> bool {
+      auto it = pidx.find({i >> 1, j >> 1});
+      if (it == pidx.end()) return false;
+      out = it->second;
+      return true;
+    };
+    d.h_near_dst.resize(d.NP);
+    d.h_far_dst.resize(d.FP);
+    for (int64_t q = 0; q < d.NP; ++q)
+      if (!find(d.h_near_i[q], d.h_near_j[q], d.h_near_dst[q])) {
+        c->err = "near pair without a near parent pair at level " + std::to_string(l);
+        return H2_ERR_INVALID_ARG;
+      }
+    for (int64_t q = 0; q < d.FP; ++q)
+      if (!find(d.h_far_i[q], d.h_far_j[q], d.h_far_dst[q])) {
+        c->err = "far pair without a near parent pair at level " + std::to_string(l);
+        return H2_ERR_INVALID_ARG;
+      }
+    CKS(upload(c, &d.near_dst, d.h_near_dst));
+    CKS(upload(c, &d.far_dst, d.h_far_dst));
+  }
+  // points, leaf slots, leaf blocks, couplings
+  CKS(upload(c, &c->pts, H.points));
+  const DevLevel& lf = c->lv[L];
+  std::vector<int64_t> slot((size_t)lf.nb * lf.D, -1);
+  for (int i = 0; i < lf.nb; ++i)
+    for (int64_t t = H.leaf_offsets[i]; t < H.leaf_offsets[i + 1]; ++t)
+      slot[(size_t)i * lf.D + (t - H.leaf_offsets[i])] = H.perm[t];
+  CKS(upload(c, &c->slot_pt, slot));
+  CKC(dalloc(c, &c->A64, (size_t)lf.NP * lf.D * lf.D));
+  launch_eval_blocks(c->kfn, c->pts, lf.NP, lf.near_i, lf.near_j, c->slot_pt, lf.D, lf.D, lf.D, c->A64, 0);
+  CKC(cudaGetLastError());
+  for (int l = 1; l <= L; ++l) {
+    DevLevel& d = c->lv[l];
+    CKC(dalloc(c, &d.S, (size_t)std::max<int64_t>(d.FP, 1) * d.K * d.K));
+    launch_eval_blocks(c->kfn, c->pts, d.FP, d.far_i, d.far_j, d.SK, d.K, d.K, d.K, d.S, 0);
+    CKC(cudaGetLastError());
+  }
+  // vectors and scratch
+  const int64_t nslot = (int64_t)lf.nb * lf.D;
+  for (double** p : {&c->b64, &c->x64, &c->r64, &c->y64, &c->t64}) CKC(dalloc(c, p, nslot));
+  CKC(dalloc(c, &c->io_a, c->N));
+  CKC(dalloc(c, &c->io_b, c->N));
+  c->hat_off.assign(L + 2, 0);
+  for (int l = 1; l <= L; ++l) c->hat_off[l + 1] = c->hat_off[l] + (int64_t)c->lv[l].nb * c->lv[l].K;
+  CKC(dalloc(c, &c->xhat, c->hat_off[L + 1]));
+  CKC(dalloc(c, &c->yhat, c->hat_off[L + 1]));
+  CKC(dalloc(c, &c->red, 1024));  // three norm slots of 257 doubles: 0, 300, 600
+  CKC(dalloc(c, &c->status, 4));
+  CKC(cudaMemset(c->status, 0, 4 * sizeof(int32_t)));
+  CKC(cudaDeviceSynchronize());
+  return H2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// factorization
+// ---------------------------------------------------------------------------
+struct Ev {
+  cudaEvent_t e[2];
+};
+
+template <typename T>
+h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
+  if (!F.lv.empty()) return H2_OK;
+  const int L = c->L;
+  F.lv.assign(L + 1, FacLevel<T>());
+  size_t wk = 0;
+  for (int l = 0; l <= L; ++l) {
+    const DevLevel& d = c->lv[l];
+    FacLevel<T>& f = F.lv[l];
+    const size_t nb = d.nb, D = d.D, K = d.K, R = d.R;
+    wk = std::max(wk, (size_t)d.NP * D * D);
+    wk = std::max(wk, (size_t)d.FP * K * K);
+    bool leaf64 = (l == L) && std::is_same<T, double>::value;
+    if (!leaf64) CKC(dalloc(c, &f.Ain, (size_t)d.NP * D * D));
+    if (l == 0) continue;
+    CKC(dalloc(c, &f.U, nb * D * D));
+    CKC(dalloc(c, &f.Tm, nb * K * K));
+    CKC(dalloc(c, &f.Xo, nb * D * K));
+    CKC(dalloc(c, &f.Ahat, (size_t)d.NP * D * D));
+    CKC(dalloc(c, &f.Shat, (size_t)std::max<int64_t>(d.FP, 1) * K * K));
+    CKC(dalloc(c, &f.Z, nb * R * K));
+    CKC(dalloc(c, &f.lu, nb * R * R));
+    CKC(dalloc(c, &f.Ainv, nb * R * R));
+    CKC(dalloc(c, &f.piv, nb * R));
+    if (std::is_same<T, double>::value) f.Sc = reinterpret_cast<T*>(d.S);
+    else CKC(dalloc(c, &f.Sc, (size_t)std::max<int64_t>(d.FP, 1) * K * K));
+    for (T** p : {&f.vin, &f.c, &f.xs}) CKC(dalloc(c, p, nb * D));
+    for (T** p : {&f.u, &f.v, &f.om}) CKC(dalloc(c, p, nb * std::max<size_t>(R, 1)));
+  }
+  const int D0 = c->lv[0].D;
+  CKC(dalloc(c, &F.Wk, wk));
+  CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
+  CKC(dalloc(c, &F.root_inv, (size_t)D0 * D0));
+  CKC(dalloc(c, &F.root_piv, D0));
+  CKC(dalloc(c, &F.root_vec, D0));
+  CKC(dalloc(c, &F.root_x, D0));
+  return H2_OK;
+}
+
+template <typename T>
+void gemm(int prec, int M, int N, int K, const T* A, int64_t sA, const int32_t* ia, int lda, bool tA, const T* B,
+          int64_t sB, const int32_t* ib, int ldb, bool tB, T* C, int64_t sC, const int32_t* ic, int ldc, T alpha,
+          T beta, int64_t batch, cudaStream_t st) {
+  (void)prec;
+  gemm_simt<T, T>(M, N, K, A, sA, ia, lda, tA, B, sB, ib, ldb, tB, C, sC, ic, ldc, alpha, beta, batch, st);
+}
+
+template <typename T>
+h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
+  CKS(alloc_factor(c, F));
+  const int L = c->L;
+  cudaStream_t st = c->stream;
+  CKC(cudaMemsetAsync(c->status, 0, 4 * sizeof(int32_t), st));
+  std::vector<cudaEvent_t> ev;
+  auto mark = [&]() {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    ev.push_back(e);
+  };
+  // phase boundaries per level: [start, a1, a2, a3, a45, a2c, a6]
+  mark();
+  const T* Aleaf = nullptr;
+  if (std::is_same<T, double>::value) {
+    Aleaf = reinterpret_cast<const T*>(c->A64);
+  } else {
+    launch_convert<double, T>(c->A64, F.lv[L].Ain, (int64_t)c->lv[L].NP * c->lv[L].D * c->lv[L].D, st);
+    Aleaf = F.lv[L].Ain;
+  }
+  mark();
+  for (int l = L; l >= 1; --l) {
+    const DevLevel& d = c->lv[l];
+    FacLevel<T>& f = F.lv[l];
+    const int D = d.D, K = d.K, R = d.R;
+    const int64_t DD = (int64_t)D * D;
+    // a1: complement bases
+    const int Kc = (l < L) ? c->lv[l + 1].K : 0;
+    launch_orth_input<T>(d.nb, D, K, Kc, d.X, (l < L) ? F.lv[l + 1].Tm : nullptr, f.Xo, st);
+    launch_qr_complement<T>(d.nb, D, K, f.Xo, f.U, f.Tm, st);
+    mark();
+    // a2: Ahat_ij = U_i^T A_ij U_j
+    const T* Ain = (l == L) ? Aleaf : f.Ain;
+    gemm<T>(prec, D, D, D, Ain, DD, nullptr, D, false, f.U, DD, d.near_j, D, true, F.Wk, DD, nullptr, D, T(1), T(0),
+            d.NP, st);
+    gemm<T>(prec, D, D, D, f.U, DD, d.near_i, D, false, F.Wk, DD, nullptr, D, false, f.Ahat, DD, nullptr, D, T(1),
+            T(0), d.NP, st);
+    mark();
+    // a3: FP64 LU of Ahat_ii^RR and its inverse
+    launch_lu_inverse<T>(d.nb, D, R, f.Ahat, d.diag_pair, f.lu, f.piv, f.Ainv, c->status, l, st);
+    mark();
+    // a4 + a5: Z = Ainv Ahat_ii^RS; Ahat_ii^SS -= Ahat_ii^SR Z
+    if (R > 0 && K > 0) {
+      gemm<T>(prec, R, K, R, f.Ainv, (int64_t)R * R, nullptr, R, false, f.Ahat + R, DD, d.diag_pair, D, false, f.Z,
+              (int64_t)R * K, nullptr, K, T(1), T(0), d.nb, st);
+      gemm<T>(prec, K, K, R, f.Ahat + (int64_t)R * D, DD, d.diag_pair, D, false, f.Z, (int64_t)R * K, nullptr, K,
+              false, f.Ahat + (int64_t)R * D + R, DD, d.diag_pair, D, T(-1), T(1), d.nb, st);
+    }
+    mark();
+    // a2': couplings Shat_ij = T_i S_ij T_j^T
+    if (d.FP > 0 && K > 0) {
+      const int64_t KK = (int64_t)K * K;
+      if (!std::is_same<T, double>::value) launch_convert<double, T>(d.S, f.Sc, d.FP * KK, st);
+      gemm<T>(prec, K, K, K, f.Sc, KK, nullptr, K, false, f.Tm, KK, d.far_j, K, true, F.Wk, KK, nullptr, K, T(1),
+              T(0), d.FP, st);
+      gemm<T>(prec, K, K, K, f.Tm, KK, d.far_i, K, false, F.Wk, KK, nullptr, K, false, f.Shat, KK, nullptr, K, T(1),
+              T(0), d.FP, st);
+    }
+    mark();
+    // a6: merge into the parent level's near blocks
+    launch_merge<T>(D, K, d.NP, f.Ahat, d.near_i, d.near_j, d.near_dst, d.FP, f.Shat, d.far_i, d.far_j, d.far_dst,
+                    F.lv[l - 1].Ain, st);
+    mark();
+  }
+  // a7: root
+  const int D0 = c->lv[0].D;
+  const T* Aroot = (L == 0) ? Aleaf : F.lv[0].Ain;
+  launch_lu_inverse<T>(1, D0, D0, Aroot, nullptr, F.root_lu, F.root_piv, F.root_inv, c->status, 0, st);
+  mark();
+  CKC(cudaGetLastError());
+  CKC(cudaStreamSynchronize(st));
+  // phase times
+  PhaseTimes& t = c->times;
+  t = PhaseTimes();
+  auto el = [&](int a, int b) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev[a], ev[b]);
+    return (double)ms * 1e-3;
+  };
+  t.a2_proj += el(0, 1);  // leaf conversion counted with the projection
+  int k = 1;
+  for (int l = L; l >= 1; --l) {
+    t.a1_qr += el(k, k + 1);
+    t.a2_proj += el(k + 1, k + 2);
+    t.a3_lu += el(k + 2, k + 3);
+    t.a5_schur += el(k + 3, k + 4);
+    t.a2c_coupling += el(k + 4, k + 5);
+    t.a6_merge += el(k + 5, k + 6);
+    k += 6;
+  }
+  t.a7_root = el(k, k + 1);
+  t.total_factor = el(0, k + 1);
+  for (auto e : ev) cudaEventDestroy(e);
+  int32_t stw[4];
+  CKC(cudaMemcpy(stw, c->status, sizeof(stw), cudaMemcpyDeviceToHost));
+  if (stw[0] != 0) {
+    c->err = "zero pivot in the LU of level " + std::to_string(stw[0] - 1) + " box " + std::to_string(stw[1]);
+    return H2_ERR_SINGULAR;
+  }
+  F.ready = true;
+  return H2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// substitution: x_tree (+)= ULV^-1 r_tree   (FP64 padded tree vectors)
+// ---------------------------------------------------------------------------
+template <typename T>
+void ulv_apply_impl(h2_ctx* c, Factor<T>& F, const double* r, double* x) {
+  const int L = c->L;
+  cudaStream_t st = c->stream;
+  const int64_t nslot = (int64_t)c->lv[L].nb * c->lv[L].D;
+  launch_norm2(r, nslot, c->red, st);
+  T* leaf_in = (L >= 1) ? F.lv[L].vin : F.root_vec;
+  launch_scale_to<T>(r, c->red, leaf_in, nslot, st);
+  for (int l = L; l >= 1; --l) {
+    const DevLevel& d = c->lv[l];
+    FacLevel<T>& f = F.lv[l];
+    T* pv = (l > 1) ? F.lv[l - 1].vin : F.root_vec;
+    launch_fwd1<T>(d, f, f.Ainv, st);
+    launch_fwd2<T>(d, f, f.Ainv, st);
+    launch_fwd3<T>(d, f, pv, st);
+  }
+  launch_gemv_rows<T>(c->lv[0].D, F.root_inv, F.root_vec, F.root_x, st);
+  for (int l = 1; l <= L; ++l) {
+    const DevLevel& d = c->lv[l];
+    FacLevel<T>& f = F.lv[l];
+    const T* px = (l > 1) ? F.lv[l - 1].xs : F.root_x;
+    launch_bwd1<T>(d, f, f.Ainv, px, st);
+    launch_bwd2<T>(d, f, f.Ainv, px, st);
+  }
+  const T* out = (L >= 1) ? F.lv[L].xs : F.root_x;
+  launch_axpy_from<T>(out, c->red, x, nslot, st);
+}
+
+void matvec_impl(h2_ctx* c, const double* x, double* y) {
+  const int L = c->L;
+  cudaStream_t st = c->stream;
+  if (L == 0) {
+    launch_matvec_leaf(c->lv[0], c->A64, x, nullptr, y, st);
+    return;
+  }
+  launch_matvec_up_leaf(c->lv[L], x, c->xhat + c->hat_off[L], st);
+  for (int l = L - 1; l >= 1; --l) launch_matvec_up(c->lv[l], c->xhat + c->hat_off[l + 1], c->xhat + c->hat_off[l], st);
+  for (int l = 1; l <= L; ++l) launch_matvec_far(c->lv[l], c->xhat + c->hat_off[l], c->yhat + c->hat_off[l], st);
+  for (int l = 1; l < L; ++l) launch_matvec_down(c->lv[l], c->yhat + c->hat_off[l], c->yhat + c->hat_off[l + 1], st);
+  launch_matvec_leaf(c->lv[L], c->A64, x, c->yhat + c->hat_off[L], y, st);
+}
+
+bool factor_ready(const h2_ctx* c) {
+  return (c->prec == H2_PREC_FP64 && c->f64.ready) || (c->prec > 0 && c->f32.ready);
+}
+
+void ulv_apply_any(h2_ctx* c, const double* r, double* x) {
+  if (c->prec == H2_PREC_FP64) ulv_apply_impl<double>(c, c->f64, r, x);
+  else ulv_apply_impl<float>(c, c->f32, r, x);
+}
+
+// copy an N-vector in (orig order, host or device) to the padded tree vector
+h2_status vec_in(h2_ctx* c, const double* src, double* tree) {
+  const double* dsrc = src;
+  if (!is_device_ptr(src)) {
+    CKC(cudaMemcpyAsync(c->io_a, src, c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    dsrc = c->io_a;
+  }
+  const DevLevel& lf = c->lv[c->L];
+  launch_gather(c->slot_pt, dsrc, tree, (int64_t)lf.nb * lf.D, c->stream);
+  return H2_OK;
+}
+
+h2_status vec_out(h2_ctx* c, const double* tree, double* dst) {
+  const DevLevel& lf = c->lv[c->L];
+  bool dev = is_device_ptr(dst);
+  double* ddst = dev ? dst : c->io_b;
+  launch_scatter(c->slot_pt, tree, ddst, (int64_t)lf.nb * lf.D, c->stream);
+  if (!dev) {
+    CKC(cudaMemcpyAsync(dst, ddst, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CKC(cudaStreamSynchronize(c->stream));
+  }
+  return H2_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+h2_status h2_build(h2_ctx** out, const h2_params* p, const double* points, int64_t N) {
+  g_last_error.clear();
+  if (!out) { g_last_error = "out is NULL"; return H2_ERR_INVALID_ARG; }
+  *out = nullptr;
+  h2_status s = check_params(p, g_last_error);
+  if (s != H2_OK) return s;
+  if (N < 1 || !points) { g_last_error = "N < 1 or points NULL"; return H2_ERR_INVALID_ARG; }
+  for (int64_t t = 0; t < 3 * N; ++t)
+    if (!std::isfinite(points[t])) { g_last_error = "non-finite coordinate"; return H2_ERR_INVALID_ARG; }
+  h2_ctx* c = new h2_ctx();
+  c->params = *p;
+  c->kfn = KernelFn{p->kernel, p->eps, p->ell, p->diag_shift};
+  std::string e = build_host(*p, points, N, c->host);
+  if (!e.empty()) {
+    g_last_error = e;
+    delete c;
+    return H2_ERR_SINGULAR;
+  }
+  s = setup_device(c);
+  if (s != H2_OK) {
+    g_last_error = c->err;
+    h2_destroy(c);
+    return s;
+  }
+  *out = c;
+  return H2_OK;
+}
+
+h2_status h2_plan(const h2_params* p, const double* points, int64_t N, char* json, size_t cap) {
+  g_last_error.clear();
+  h2_status s = check_params(p, g_last_error);
+  if (s != H2_OK) return s;
+  if (N < 1 || !points || !json) { g_last_error = "N < 1 or NULL pointer"; return H2_ERR_INVALID_ARG; }
+  for (int64_t t = 0; t < 3 * N; ++t)
+    if (!std::isfinite(points[t])) { g_last_error = "non-finite coordinate"; return H2_ERR_INVALID_ARG; }
+  HostH2 H;
+  std::string e = build_host(*p, points, N, H);
+  if (!e.empty()) { g_last_error = e; return H2_ERR_SINGULAR; }
+  std::ostringstream o;
+  double bytes_build = 0, bytes_factor64 = 0;
+  o << "{\"N\":" << N << ",\"L\":" << H.L << ",\"levels\":[";
+  for (int l = 0; l <= H.L; ++l) {
+    const HostLevel& h = H.lv[l];
+    double D = h.D, K = l ? h.K : 0, R = D - K, NP = h.near.size() / 2, FP = h.far.size() / 2, nb = h.nb;
+    if (l) o << ",";
+    o << "{\"l\":" << l << ",\"nb\":" << h.nb << ",\"D\":" << h.D << ",\"K\":" << (l ? h.K : 0)
+      << ",\"NP\":" << (int64_t)NP << ",\"FP\":" << (int64_t)FP;
+    if (l == H.L && !H.ranks_leaf.empty())
+      o << ",\"rank_max\":" << *std::max_element(H.ranks_leaf.begin(), H.ranks_leaf.end())
+        << ",\"rank_min\":" << *std::min_element(H.ranks_leaf.begin(), H.ranks_leaf.end());
+    o << "}";
+    bytes_build += 8.0 * (nb * D * K + FP * K * K) + (l == H.L ? 8.0 * NP * D * D : 0.0);
+    bytes_factor64 += 8.0 * (2 * NP * D * D + nb * (D * D + D * K + 2 * R * R + R * K) + FP * K * K);
+  }
+  o << "],\"device_bytes_build\":" << bytes_build << ",\"device_bytes_factor_fp64\":" << bytes_factor64 << "}";
+  std::string str = o.str();
+  if (str.size() + 1 > cap) { g_last_error = "cap too small"; return H2_ERR_INVALID_ARG; }
+  std::memcpy(json, str.c_str(), str.size() + 1);
+  return H2_OK;
+}
+
+h2_status h2_import(h2_ctx** out, const h2_params* p, const h2_instance* in) {
+  g_last_error.clear();
+  if (!out || !in) { g_last_error = "NULL argument"; return H2_ERR_INVALID_ARG; }
+  *out = nullptr;
+  h2_status s = check_params(p, g_last_error);
+  if (s != H2_OK) return s;
+  if (in->N < 1 || in->L < 0 || in->L > 30 || !in->points || !in->perm || !in->leaf_offsets || !in->D || !in->K) {
+    g_last_error = "inconsistent instance";
+    return H2_ERR_INVALID_ARG;
+  }
+  h2_ctx* c = new h2_ctx();
+  c->params = *p;
+  c->kfn = KernelFn{p->kernel, p->eps, p->ell, p->diag_shift};
+  HostH2& H = c->host;
+  H.N = in->N;
+  H.L = in->L;
+  H.points.assign(in->points, in->points + 3 * in->N);
+  H.perm.assign(in->perm, in->perm + in->N);
+  H.leaf_offsets.assign(in->leaf_offsets, in->leaf_offsets + (1 << in->L) + 1);
+  H.lv.assign(in->L + 1, HostLevel());
+  std::string err;
+  for (int l = 0; l <= in->L; ++l) {
+    HostLevel& h = H.lv[l];
+    h.nb = 1 << l;
+    h.D = in->D[l];
+    h.K = l ? in->K[l] : 0;
+    if (h.D < 0 || h.K < 0 || h.K > h.D || (l < in->L && h.D != 2 * in->K[l + 1])) err = "bad D/K";
+    h.near.assign(in->near[l], in->near[l] + 2 * in->n_near[l]);
+    if (in->n_far[l] > 0) h.far.assign(in->far[l], in->far[l] + 2 * in->n_far[l]);
+    for (int32_t v : h.near)
+      if (v < 0 || v >= h.nb) err = "near pair index out of range";
+    for (int32_t v : h.far)
+      if (v < 0 || v >= h.nb) err = "far pair index out of range";
+    if (l >= 1) {
+      h.X.assign(in->X[l], in->X[l] + (size_t)h.nb * h.D * h.K);
+      h.SK.assign(in->SK[l], in->SK[l] + (size_t)h.nb * h.K);
+      for (int64_t v : h.SK)
+        if (v < 0 || v >= in->N) err = "skeleton index out of range";
+    }
+  }
+  for (int i = 0; i < (1 << in->L); ++i)
+    if (H.leaf_offsets[i + 1] - H.leaf_offsets[i] > H.lv[in->L].D || H.leaf_offsets[i + 1] < H.leaf_offsets[i])
+      err = "leaf larger than D_L";
+  if (H.leaf_offsets[0] != 0 || H.leaf_offsets[1 << in->L] != in->N) err = "bad leaf offsets";
+  for (int64_t t = 0; t < in->N; ++t)
+    if (H.perm[t] < 0 || H.perm[t] >= in->N) err = "perm out of range";
+  if (!err.empty()) {
+    g_last_error = err;
+    delete c;
+    return H2_ERR_INVALID_ARG;
+  }
+  s = setup_device(c);
+  if (s != H2_OK) {
+    g_last_error = c->err;
+    h2_destroy(c);
+    return s;
+  }
+  *out = c;
+  return H2_OK;
+}
+
+h2_status h2_factor(h2_ctx* c, int32_t prec) {
+  if (!c) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  if (prec < H2_PREC_FP64 || prec > H2_PREC_BF16) {
+    c->err = "unknown precision";
+    return H2_ERR_INVALID_ARG;
+  }
+  c->prec = -1;
+  h2_status s = (prec == H2_PREC_FP64) ? factor_impl<double>(c, c->f64, prec) : factor_impl<float>(c, c->f32, prec);
+  if (s == H2_OK) c->prec = prec;
+  return s;
+}
+
+h2_status h2_ulv_apply(h2_ctx* c, const double* b, double* x) {
+  if (!c || !b || !x) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!factor_ready(c)) { c->err = "no factorization"; return H2_ERR_STATE; }
+  const DevLevel& lf = c->lv[c->L];
+  const int64_t nslot = (int64_t)lf.nb * lf.D;
+  CKS(vec_in(c, b, c->r64));
+  CKC(cudaMemsetAsync(c->x64, 0, nslot * sizeof(double), c->stream));
+  ulv_apply_any(c, c->r64, c->x64);
+  CKC(cudaGetLastError());
+  CKS(vec_out(c, c->x64, x));
+  CKC(cudaStreamSynchronize(c->stream));
+  return H2_OK;
+}
+
+h2_status h2_matvec(h2_ctx* c, const double* x, double* y) {
+  if (!c || !x || !y) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  CKS(vec_in(c, x, c->x64));
+  matvec_impl(c, c->x64, c->y64);
+  CKC(cudaGetLastError());
+  CKS(vec_out(c, c->y64, y));
+  CKC(cudaStreamSynchronize(c->stream));
+  return H2_OK;
+}
+
+h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t max_iters, double* relres_out,
+                   int32_t* iters_out) {
+  if (!c || !b || !x || max_iters < 0) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!factor_ready(c)) { c->err = "no factorization"; return H2_ERR_STATE; }
+  cudaStream_t st = c->stream;
+  const DevLevel& lf = c->lv[c->L];
+  const int64_t nslot = (int64_t)lf.nb * lf.D;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  CKS(vec_in(c, b, c->b64));
+  launch_norm2(c->b64, nslot, c->red + 300, st);  // ||b||^2 apart from the substitution scratch
+  double bn2 = 0;
+  CKC(cudaMemcpyAsync(&bn2, c->red + 300, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKC(cudaMemsetAsync(c->x64, 0, nslot * sizeof(double), st));
+  CKC(cudaMemcpyAsync(c->r64, c->b64, nslot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CKC(cudaStreamSynchronize(st));
+  const double bnorm = std::sqrt(bn2);
+  double rel = bnorm > 0 ? 1.0 : 0.0;
+  int it = 0;
+  while (it < max_iters && (target <= 0 || rel > target) && bnorm > 0) {
+    ulv_apply_any(c, c->r64, c->x64);
+    matvec_impl(c, c->x64, c->y64);
+    launch_residual(c->b64, c->y64, c->r64, nslot, st);
+    launch_norm2(c->r64, nslot, c->red + 600, st);
+    double rn2 = 0;
+    CKC(cudaMemcpyAsync(&rn2, c->red + 600, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    rel = std::sqrt(rn2) / bnorm;
+    ++it;
+    if (!std::isfinite(rel)) break;
+  }
+  CKC(cudaGetLastError());
+  CKS(vec_out(c, c->x64, x));
+  cudaEventRecord(e1, st);
+  CKC(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->times.solve_total = ms * 1e-3;
+  c->times.iters = it;
+  c->times.relres = rel;
+  if (relres_out) *relres_out = rel;
+  if (iters_out) *iters_out = it;
+  if (target > 0 && !(rel <= target)) {
+    c->err = "refinement stopped at relative residual " + std::to_string(rel);
+    return H2_ERR_NOT_CONVERGED;
+  }
+  return H2_OK;
+}
+
+h2_status h2_set_stream(h2_ctx* c, void* stream) {
+  if (!c) return H2_ERR_INVALID_ARG;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  return H2_OK;
+}
+
+h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
+  if (!c || !json) return H2_ERR_INVALID_ARG;
+  std::ostringstream o;
+  o.precision(9);
+  const PhaseTimes& t = c->times;
+  double fl_proj = 0, fl_lu = 0, fl_schur = 0, fl_coup = 0, fl_qr = 0;
+  o << "{\"N\":" << c->N << ",\"L\":" << c->L << ",\"prec\":" << c->prec << ",\"levels\":[";
+  for (int l = 0; l <= c->L; ++l) {
+    const DevLevel& d = c->lv[l];
+    double D = d.D, K = d.K, R = d.R;
+    if (l) o << ",";
+    o << "{\"l\":" << l << ",\"nb\":" << d.nb << ",\"D\":" << d.D << ",\"K\":" << d.K << ",\"NP\":" << d.NP
+      << ",\"FP\":" << d.FP << "}";
+    if (l == 0) {
+      fl_lu += 2.0 * D * D * D;
+      continue;
+    }
+    fl_proj += d.NP * 4.0 * D * D * D;
+    fl_lu += d.nb * 2.0 * R * R * R;
+    fl_schur += d.nb * (2.0 * R * R * K + 2.0 * K * K * R);
+    fl_coup += d.FP * 4.0 * K * K * K;
+    fl_qr += d.nb * (4.0 * D * K * K + 4.0 * D * D * K);
+  }
+  o << "],\"flops\":{\"a1_qr\":" << fl_qr << ",\"a2_proj\":" << fl_proj << ",\"a3_lu\":" << fl_lu
+    << ",\"a45_schur\":" << fl_schur << ",\"a2c_coupling\":" << fl_coup << "}";
+  o << ",\"times\":{\"a1_qr\":" << t.a1_qr << ",\"a2_proj\":" << t.a2_proj << ",\"a3_lu\":" << t.a3_lu
+    << ",\"a45_schur\":" << t.a5_schur << ",\"a2c_coupling\":" << t.a2c_coupling << ",\"a6_merge\":" << t.a6_merge
+    << ",\"a7_root\":" << t.a7_root << ",\"factor\":" << t.total_factor << ",\"solve\":" << t.solve_total
+    << "},\"iters\":" << t.iters << ",\"relres\":" << t.relres
+    << ",\"kernel_launches\":" << g_launches.load() << "}";
+  std::string s = o.str();
+  if (s.size() + 1 > cap) return H2_ERR_INVALID_ARG;
+  std::memcpy(json, s.c_str(), s.size() + 1);
+  return H2_OK;
+}
+
+h2_status h2_export(const h2_ctx* c, const char* name, int32_t level, void* dst, size_t cap_bytes, size_t* count,
+                    int32_t* elem_size) {
+  if (!c || !name || !count || !elem_size) return H2_ERR_INVALID_ARG;
+  const std::string n(name);
+  if (n == "perm") {
+    *count = c->host.perm.size();
+    *elem_size = 8;
+    if (dst) {
+      if (cap_bytes < *count * 8) return H2_ERR_INVALID_ARG;
+      std::memcpy(dst, c->host.perm.data(), *count * 8);
+    }
+    return H2_OK;
+  }
+  if (level < 0 || level > c->L) return H2_ERR_INVALID_ARG;
+  const DevLevel& d = c->lv[level];
+  const void* src = nullptr;
+  size_t cnt = 0;
+  int es = 8;
+  const bool f64 = c->prec == H2_PREC_FP64;
+  const bool ready = factor_ready(c);
+  auto pick = [&](const void* p64, const void* p32, size_t k, bool need_factor) -> h2_status {
+    if (need_factor && !ready) return H2_ERR_STATE;
+    src = f64 ? p64 : p32;
+    es = f64 ? 8 : 4;
+    cnt = k;
+    return H2_OK;
+  };
+  h2_status s = H2_OK;
+  const size_t nb = d.nb, D = d.D, K = d.K, R = d.R;
+  if (n == "X") {
+    if (level == 0) return H2_ERR_INVALID_ARG;
+    src = d.X; cnt = nb * D * K; es = 8;
+  } else if (n == "A") {
+    if (level == c->L) { src = c->A64; cnt = (size_t)d.NP * D * D; es = 8; }
+    else s = pick(c->f64.lv.empty() ? nullptr : c->f64.lv[level].Ain,
+                  c->f32.lv.empty() ? nullptr : c->f32.lv[level].Ain, (size_t)d.NP * D * D, true);
+  } else if (level >= 1 && (n == "U" || n == "T" || n == "Ahat" || n == "Ainv" || n == "Shat")) {
+    const FacLevel<double>* a = c->f64.lv.empty() ? nullptr : &c->f64.lv[level];
+    const FacLevel<float>* b = c->f32.lv.empty() ? nullptr : &c->f32.lv[level];
+    if (!ready || (f64 && !a) || (!f64 && !b)) return H2_ERR_STATE;
+    if (n == "U") s = pick(a ? a->U : nullptr, b ? b->U : nullptr, nb * D * D, true);
+    if (n == "T") s = pick(a ? a->Tm : nullptr, b ? b->Tm : nullptr, nb * K * K, true);
+    if (n == "Ahat") s = pick(a ? a->Ahat : nullptr, b ? b->Ahat : nullptr, (size_t)d.NP * D * D, true);
+    if (n == "Ainv") s = pick(a ? a->Ainv : nullptr, b ? b->Ainv : nullptr, nb * R * R, true);
+    if (n == "Shat") s = pick(a ? a->Shat : nullptr, b ? b->Shat : nullptr, (size_t)d.FP * K * K, true);
+  } else if (level >= 1 && (n == "lu" || n == "piv")) {
+    if (!ready) return H2_ERR_STATE;
+    const bool p64 = f64;
+    src = (n == "lu") ? (const void*)(p64 ? c->f64.lv[level].lu : c->f32.lv[level].lu)
+                      : (const void*)(p64 ? c->f64.lv[level].piv : c->f32.lv[level].piv);
+    es = (n == "lu") ? 8 : 4;
+    cnt = (n == "lu") ? nb * R * R : nb * R;
+  } else if (n == "root" || n == "root_piv" || n == "root_inv") {
+    if (!ready) return H2_ERR_STATE;
+    const size_t D0 = c->lv[0].D;
+    if (n == "root") { src = f64 ? (const void*)c->f64.root_lu : (const void*)c->f32.root_lu; es = 8; cnt = D0 * D0; }
+    if (n == "root_piv") { src = f64 ? (const void*)c->f64.root_piv : (const void*)c->f32.root_piv; es = 4; cnt = D0; }
+    if (n == "root_inv") s = pick(c->f64.root_inv, c->f32.root_inv, D0 * D0, true);
+  } else {
+    return H2_ERR_INVALID_ARG;
+  }
+  if (s != H2_OK) return s;
+  *count = cnt;
+  *elem_size = es;
+  if (dst) {
+    if (!src) return H2_ERR_STATE;
+    if (cap_bytes < cnt * es) return H2_ERR_INVALID_ARG;
+    if (cudaMemcpy(dst, src, cnt * es, cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ERR_CUDA;
+  }
+  return H2_OK;
+}
+
+const char* h2_last_error(const h2_ctx* c) { return c ? c->err.c_str() : g_last_error.c_str(); }
+
+void h2_destroy(h2_ctx* c) {
+  if (!c) return;
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+// Internal declarations of the H^2-ULV library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/h2ulv.h"
+
+#if defined(__CUDACC__)
+#define H2_HD __host__ __device__ __forceinline__
+#else
+#define H2_HD inline
+#endif
+
+namespace h2 {
+
+// ---------------------------------------------------------------------------
+// Kernel function G(x, y) (the formulas listed in h2ulv.h).  Shared by the
+// host-side construction and the device-side block evaluation.
+// ---------------------------------------------------------------------------
+struct KernelFn {
+  int kind;
+  double eps, ell, diag_shift;
+
+  H2_HD double off(const double* a, const double* b) const {
+    if (kind == H2_K_POLY2_TEST) {
+      double d = 1.0 + a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+      return d * d;
+    }
+    double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    double r = sqrt(r2);
+    switch (kind) {
+      case H2_K_LAPLACE_EPS: return 1.0 / (r + eps);
+      case H2_K_YUKAWA_EPS: return exp(-r) / (r + eps);
+      case H2_K_GAUSSIAN: return exp(-r2 / (ell * ell));
+      case H2_K_LAPLACE_PAPER: return 1.0 / r;
+      default: return exp(-r) / r;  // H2_K_YUKAWA_PAPER
+    }
+  }
+  H2_HD double diag(const double* a) const {
+    switch (kind) {
+      case H2_K_LAPLACE_EPS:
+      case H2_K_YUKAWA_EPS: return 1.0 / eps + diag_shift;
+      case H2_K_GAUSSIAN: return 1.0 + diag_shift;
+      case H2_K_LAPLACE_PAPER:
+      case H2_K_YUKAWA_PAPER: return 1e3 + diag_shift;
+      default: {
+        double q = 1.0 + a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+        return q * q + diag_shift * q;
+      }
+    }
+  }
+  // Entry for point indices ia, ib (-1 = padding: 1 on the diagonal, else 0).
+  H2_HD double entry(const double* pts, int64_t ia, int64_t ib, bool same_slot) const {
+    if (ia < 0 || ib < 0) return (ia < 0 && ib < 0 && same_slot) ? 1.0 : 0.0;
+    if (ia == ib) return diag(pts + 3 * ia);
+    return off(pts + 3 * ia, pts + 3 * ib);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Host-side H^2 structure (tree, lists, ID bases) produced by the
+// construction or by h2_import.
+// ---------------------------------------------------------------------------
+struct HostLevel {
+  int nb = 0, D = 0, K = 0;
+  std::vector<int32_t> near;  // 2 * NP, sorted (i, j)
+  std::vector<int32_t> far;   // 2 * FP, sorted (i, j)
+  std::vector<double> X;      // nb * D * K
+  std::vector<int64_t> SK;    // nb * K
+};
+
+struct HostH2 {
+  int64_t N = 0;
+  int L = 0;
+  std::vector<double> points;        // N * 3
+  std::vector<int64_t> perm;         // N
+  std::vector<int64_t> leaf_offsets; // 2^L + 1
+  std::vector<HostLevel> lv;         // L + 1
+  std::vector<int> ranks_leaf;       // tol-rank per leaf box (diagnostic)
+};
+
+// Host construction (host_build.cpp).  Returns an empty string on success.
+std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& out);
+
+// ---------------------------------------------------------------------------
+// Device-side state.
+// ---------------------------------------------------------------------------
+struct DevLevel {
+  int nb = 0, D = 0, K = 0, R = 0;
+  int64_t NP = 0, FP = 0;
+  // pair lists (device)
+  int32_t *near_i = nullptr, *near_j = nullptr;  // NP
+  int64_t* near_ptr = nullptr;                   // nb + 1 (CSR over i)
+  int32_t* diag_pair = nullptr;                  // nb
+  int32_t *far_i = nullptr, *far_j = nullptr;    // FP
+  int64_t* far_ptr = nullptr;                    // nb + 1
+  int32_t *near_dst = nullptr, *far_dst = nullptr;  // parent near-pair index of each pair
+  // host copies
+  std::vector<int32_t> h_near_i, h_near_j, h_far_i, h_far_j, h_diag_pair, h_near_dst, h_far_dst;
+  std::vector<int64_t> h_near_ptr, h_far_ptr;
+  // construction data (FP64)
+  double* X = nullptr;    // nb * D * K
+  int64_t* SK = nullptr;  // nb * K
+  double* S = nullptr;    // FP * K * K couplings G(SK_i, SK_j)
+};
+
+// Factorization storage of one level in storage type T (double or float).
+template <typename T>
+struct FacLevel {
+  T* U = nullptr;      // nb * D * D   [U^R U^S], column-major
+  T* Tm = nullptr;     // nb * K * K   row-major, upper triangular
+  T* Xo = nullptr;     // nb * D * K   orthogonalisation workspace (column-major)
+  T* Ain = nullptr;    // NP * D * D   input near blocks of this level (row-major)
+  T* Ahat = nullptr;   // NP * D * D   projected blocks (row-major)
+  T* Shat = nullptr;   // FP * K * K   couplings in orthogonal coordinates
+  T* Sc = nullptr;     // FP * K * K   couplings G(SK_i, SK_j) in T
+  T* Z = nullptr;      // nb * R * K   (Ahat_ii^RR)^-1 Ahat_ii^RS
+  double* lu = nullptr;    // nb * R * R  LU of Ahat_ii^RR, column-major, FP64
+  T* Ainv = nullptr;       // nb * R * R  (Ahat_ii^RR)^-1, row-major
+  int32_t* piv = nullptr;  // nb * R (LAPACK-style row interchanges)
+  // substitution vectors
+  T *vin = nullptr, *c = nullptr, *u = nullptr, *v = nullptr, *om = nullptr, *xs = nullptr;
+};
+
+template <typename T>
+struct Factor {
+  bool ready = false;
+  std::vector<FacLevel<T>> lv;
+  double* root_lu = nullptr;  // D0 * D0 column-major
+  T* root_inv = nullptr;      // D0 * D0 row-major
+  int32_t* root_piv = nullptr;
+  T* root_vec = nullptr;      // D0
+  T* root_x = nullptr;        // D0
+  T* Wk = nullptr;            // workspace: max NP * D * D
+};
+
+struct PhaseTimes {
+  double a1_qr = 0, a2_proj = 0, a3_lu = 0, a5_schur = 0, a2c_coupling = 0, a6_merge = 0,
+         a7_root = 0, total_factor = 0;
+  double solve_total = 0, subst = 0, matvec = 0;
+  int iters = 0;
+  double relres = 0;
+};
+
+}  // namespace h2
+
+struct h2_ctx {
+  h2_params params{};
+  h2::KernelFn kfn{};
+  h2::HostH2 host;
+  std::vector<h2::DevLevel> lv;
+  int L = 0;
+  int64_t N = 0;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  // device geometry and vectors
+  double* pts = nullptr;         // N * 3
+  int64_t* slot_pt = nullptr;    // nbL * DL: original index of each padded leaf slot, -1 pad
+  double* A64 = nullptr;         // NP_L * DL * DL leaf near blocks (FP64, for the matvec)
+  double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *y64 = nullptr, *t64 = nullptr;  // padded tree vectors
+  double *io_a = nullptr, *io_b = nullptr;  // original-order staging vectors (N)
+  double* xhat = nullptr;  // matvec upward/downward scratch (sum over levels nb*K)
+  double* yhat = nullptr;
+  std::vector<int64_t> hat_off;  // per-level offsets into xhat / yhat
+  double* red = nullptr;         // reduction scratch
+  int32_t* status = nullptr;     // device error word(s)
+  int prec = -1;                 // precision of the current factorization
+  h2::Factor<double> f64;
+  h2::Factor<float> f32;
+  h2::PhaseTimes times;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace h2 {
+
+// device allocation helper: records the pointer in ctx->allocs
+template <typename T>
+inline cudaError_t dalloc(h2_ctx* c, T** p, size_t n) {
+  if (n == 0) n = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e == cudaSuccess) {
+    c->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+  }
+  return e;
+}
+
+}  // namespace h2

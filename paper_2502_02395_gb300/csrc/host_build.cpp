@@ -1,0 +1,369 @@
+// Host-side part of h2_build: cluster tree, near/far lists and the
+// interpolative decompositions of Algorithm 1 (construction with the
+// pre-factorization basis, Section 3.4-3.5).  Dense kernel blocks are not
+// formed here; the GPU evaluates them from the points (h2_api.cu).
+//
+// Per box i of level l the composite matrix
+//     M_i = [ G(B_i, S_F) | G(B_i, S_C^j) G(S_C^j, S_C^j)^-1  (close j != i) ]
+// is row-compressed.  M_i^T is streamed in row chunks through a structured
+// Householder update of an n x n triangular factor (the R of a tall QR,
+// which carries the same column norms and column-pivoting decisions as M_i^T
+// itself); a column-pivoted QR of that triangle then gives the skeleton
+// pivots and X_i = P [I; (R11^-1 R12)^T].  Boxes of a level are independent
+// and run in parallel (OpenMP).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "h2_internal.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace h2 {
+namespace {
+
+int depth_of(int64_t n, int leaf) {
+  int L = 0;
+  while ((int64_t)leaf << L < n) ++L;
+  return L;
+}
+
+// Median split along the longest bounding-box axis; ties by original index.
+void build_tree(const double* P, int64_t N, int L, std::vector<int64_t>& perm,
+                std::vector<int64_t>& leaf_off) {
+  perm.resize(N);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::vector<int64_t> off = {0, N};
+  for (int l = 0; l < L; ++l) {
+    int nb = 1 << l;
+    std::vector<int64_t> nxt(2 * nb + 1);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < nb; ++i) {
+      int64_t a = off[i], b = off[i + 1];
+      double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int64_t t = a; t < b; ++t)
+        for (int d = 0; d < 3; ++d) {
+          double v = P[3 * perm[t] + d];
+          lo[d] = std::min(lo[d], v);
+          hi[d] = std::max(hi[d], v);
+        }
+      int ax = 0;
+      for (int d = 1; d < 3; ++d)
+        if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
+      std::sort(perm.begin() + a, perm.begin() + b, [&](int64_t u, int64_t v) {
+        double pu = P[3 * u + ax], pv = P[3 * v + ax];
+        return pu < pv || (pu == pv && u < v);
+      });
+      nxt[2 * i] = a;
+      nxt[2 * i + 1] = a + (b - a) / 2;
+    }
+    nxt[2 * nb] = N;
+    off.swap(nxt);
+  }
+  leaf_off = off;
+}
+
+struct Geo {
+  std::vector<double> c, R;  // centres (3 per box), half-diagonals
+};
+
+Geo geometry(const double* P, const std::vector<int64_t>& perm, const std::vector<int64_t>& off) {
+  int nb = (int)off.size() - 1;
+  Geo g;
+  g.c.assign(3 * nb, 0.0);
+  g.R.assign(nb, 0.0);
+  for (int i = 0; i < nb; ++i) {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t t = off[i]; t < off[i + 1]; ++t)
+      for (int d = 0; d < 3; ++d) {
+        double v = P[3 * perm[t] + d];
+        lo[d] = std::min(lo[d], v);
+        hi[d] = std::max(hi[d], v);
+      }
+    double s = 0;
+    for (int d = 0; d < 3; ++d) {
+      g.c[3 * i + d] = 0.5 * (lo[d] + hi[d]);
+      s += (hi[d] - lo[d]) * (hi[d] - lo[d]);
+    }
+    g.R[i] = 0.5 * std::sqrt(s);
+  }
+  return g;
+}
+
+// ---- small dense kernels (host) ------------------------------------------
+
+// Stacked QR update: [R; C] = Q [R'; 0], R n x n row-major upper triangular,
+// C c x n column-major (column j at C + j*c).  C is destroyed.
+void tsqr_update(double* R, int n, double* C, int c) {
+  for (int k = 0; k < n; ++k) {
+    double* ck = C + (size_t)k * c;
+    double alpha = R[(size_t)k * n + k];
+    double xn2 = 0.0;
+#pragma omp simd reduction(+ : xn2)
+    for (int r = 0; r < c; ++r) xn2 += ck[r] * ck[r];
+    if (xn2 == 0.0) continue;
+    double beta = -std::copysign(std::sqrt(alpha * alpha + xn2), alpha);
+    double tau = (beta - alpha) / beta;
+    double scal = 1.0 / (alpha - beta);
+#pragma omp simd
+    for (int r = 0; r < c; ++r) ck[r] *= scal;
+    R[(size_t)k * n + k] = beta;
+    for (int j = k + 1; j < n; ++j) {
+      double* cj = C + (size_t)j * c;
+      double w = 0.0;
+#pragma omp simd reduction(+ : w)
+      for (int r = 0; r < c; ++r) w += ck[r] * cj[r];
+      w = tau * (w + R[(size_t)k * n + j]);
+      R[(size_t)k * n + j] -= w;
+#pragma omp simd
+      for (int r = 0; r < c; ++r) cj[r] -= w * ck[r];
+    }
+  }
+}
+
+// Column-pivoted Householder QR of the n x n row-major matrix R (in place;
+// the result is upper triangular, row-major).  piv[t] = original column.
+void pivoted_qr(double* R, int n, std::vector<int>& piv) {
+  std::vector<double> A((size_t)n * n);  // column-major working copy
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[(size_t)j * n + i] = R[(size_t)i * n + j];
+  piv.resize(n);
+  std::iota(piv.begin(), piv.end(), 0);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = -1.0;
+    for (int j = k; j < n; ++j) {
+      const double* aj = &A[(size_t)j * n];
+      double s = 0.0;
+      for (int r = k; r < n; ++r) s += aj[r] * aj[r];
+      if (s > best) {
+        best = s;
+        p = j;
+      }
+    }
+    if (p != k) {
+      std::swap_ranges(A.begin() + (size_t)k * n, A.begin() + (size_t)(k + 1) * n,
+                       A.begin() + (size_t)p * n);
+      std::swap(piv[k], piv[p]);
+    }
+    double* ak = &A[(size_t)k * n];
+    double alpha = ak[k], xn2 = 0.0;
+    for (int r = k + 1; r < n; ++r) xn2 += ak[r] * ak[r];
+    if (xn2 == 0.0) continue;
+    double beta = -std::copysign(std::sqrt(alpha * alpha + xn2), alpha);
+    double tau = (beta - alpha) / beta, scal = 1.0 / (alpha - beta);
+    for (int r = k + 1; r < n; ++r) ak[r] *= scal;
+    ak[k] = beta;
+    for (int j = k + 1; j < n; ++j) {
+      double* aj = &A[(size_t)j * n];
+      double w = aj[k];
+      for (int r = k + 1; r < n; ++r) w += ak[r] * aj[r];
+      w *= tau;
+      aj[k] -= w;
+      for (int r = k + 1; r < n; ++r) aj[r] -= w * ak[r];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) R[(size_t)i * n + j] = (j >= i) ? A[(size_t)j * n + i] : 0.0;
+}
+
+// Solve Acc Y = B in place (Acc s x s row-major, destroyed; B s x m
+// column-major).  Partial pivoting.  Returns false on a zero pivot.
+bool lu_solve_cols(double* Acc, int s, double* B, int m) {
+  std::vector<int> ip(s);
+  for (int k = 0; k < s; ++k) {
+    int p = k;
+    for (int r = k + 1; r < s; ++r)
+      if (std::fabs(Acc[(size_t)r * s + k]) > std::fabs(Acc[(size_t)p * s + k])) p = r;
+    ip[k] = p;
+    if (Acc[(size_t)p * s + k] == 0.0) return false;
+    if (p != k)
+      for (int j = 0; j < s; ++j) std::swap(Acc[(size_t)k * s + j], Acc[(size_t)p * s + j]);
+    double d = Acc[(size_t)k * s + k];
+    for (int r = k + 1; r < s; ++r) {
+      double f = Acc[(size_t)r * s + k] /= d;
+      for (int j = k + 1; j < s; ++j) Acc[(size_t)r * s + j] -= f * Acc[(size_t)k * s + j];
+    }
+  }
+  for (int c = 0; c < m; ++c) {
+    double* b = B + (size_t)c * s;
+    for (int k = 0; k < s; ++k)
+      if (ip[k] != k) std::swap(b[k], b[ip[k]]);
+    for (int k = 0; k < s; ++k)
+      for (int r = k + 1; r < s; ++r) b[r] -= Acc[(size_t)r * s + k] * b[k];
+    for (int k = s - 1; k >= 0; --k) {
+      b[k] /= Acc[(size_t)k * s + k];
+      for (int r = 0; r < k; ++r) b[r] -= Acc[(size_t)r * s + k] * b[k];
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& H) {
+  KernelFn G{p.kernel, p.eps, p.ell, p.diag_shift};
+  H.N = N;
+  H.points.assign(pts, pts + 3 * N);
+  const double* P = H.points.data();
+  int L = depth_of(N, p.leaf_size);
+  H.L = L;
+  build_tree(P, N, L, H.perm, H.leaf_offsets);
+  H.lv.assign(L + 1, HostLevel());
+
+  // box offsets per level (tree positions)
+  std::vector<std::vector<int64_t>> off(L + 1);
+  for (int l = 0; l <= L; ++l) {
+    int nb = 1 << l;
+    off[l].resize(nb + 1);
+    for (int i = 0; i <= nb; ++i) off[l][i] = H.leaf_offsets[(size_t)i << (L - l)];
+  }
+  // near / far lists
+  H.lv[0].nb = 1;
+  H.lv[0].near = {0, 0};
+  for (int l = 1; l <= L; ++l) {
+    Geo g = geometry(P, H.perm, off[l]);
+    std::vector<std::pair<int, int>> nl, fl;
+    const auto& pn = H.lv[l - 1].near;
+    for (size_t q = 0; q < pn.size() / 2; ++q) {
+      int pp = pn[2 * q], qq = pn[2 * q + 1];
+      for (int a = 2 * pp; a <= 2 * pp + 1; ++a)
+        for (int b = 2 * qq; b <= 2 * qq + 1; ++b) {
+          double dx = g.c[3 * a] - g.c[3 * b], dy = g.c[3 * a + 1] - g.c[3 * b + 1],
+                 dz = g.c[3 * a + 2] - g.c[3 * b + 2];
+          double dist = std::sqrt(dx * dx + dy * dy + dz * dz);
+          bool adm = (a != b) && dist > p.eta * (g.R[a] + g.R[b]);
+          (adm ? fl : nl).push_back({a, b});
+        }
+    }
+    std::sort(nl.begin(), nl.end());
+    std::sort(fl.begin(), fl.end());
+    HostLevel& hl = H.lv[l];
+    hl.nb = 1 << l;
+    for (auto& e : nl) { hl.near.push_back(e.first); hl.near.push_back(e.second); }
+    for (auto& e : fl) { hl.far.push_back(e.first); hl.far.push_back(e.second); }
+  }
+
+  // leaf dimension and the level points (original indices)
+  std::vector<std::vector<std::vector<int64_t>>> bp(L + 1);
+  bp[L].resize((size_t)1 << L);
+  int Dl = 0;
+  for (int i = 0; i < (1 << L); ++i) {
+    bp[L][i].assign(H.perm.begin() + off[L][i], H.perm.begin() + off[L][i + 1]);
+    Dl = std::max<int>(Dl, (int)bp[L][i].size());
+  }
+  H.lv[L].D = Dl;
+
+  const int CH = 256;  // chunk rows of the streamed QR
+  for (int l = L; l >= 1; --l) {
+    HostLevel& hl = H.lv[l];
+    int nb = hl.nb, D = hl.D;
+    std::vector<std::vector<int>> nbrs(nb);
+    for (size_t q = 0; q < hl.near.size() / 2; ++q) nbrs[hl.near[2 * q]].push_back(hl.near[2 * q + 1]);
+    std::vector<std::vector<double>> Rb(nb);
+    std::vector<std::vector<int>> pivs(nb);
+    std::vector<int> ranks(nb, 0);
+    int bad = -1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < nb; ++i) {
+      const std::vector<int64_t>& Pi = bp[l][i];
+      int n = (int)Pi.size();
+      std::vector<double> R((size_t)n * n, 0.0), C((size_t)CH * n);
+      // far field: tree positions outside the near boxes, stride-sampled
+      int64_t nearcnt = 0;
+      for (int j : nbrs[i]) nearcnt += off[l][j + 1] - off[l][j];
+      int64_t F = N - nearcnt;
+      int64_t s = (p.far_samples <= 0 || p.far_samples >= F) ? F : p.far_samples;
+      for (int64_t t0 = 0; t0 < s; t0 += CH) {
+        int c = (int)std::min<int64_t>(CH, s - t0);
+        for (int r = 0; r < c; ++r) {
+          int64_t q = ((t0 + r) * F) / s;
+          for (int j : nbrs[i]) {  // sorted intervals
+            if (q < off[l][j]) break;
+            q += off[l][j + 1] - off[l][j];
+          }
+          int64_t pt = H.perm[q];
+          for (int cc = 0; cc < n; ++cc) C[(size_t)cc * c + r] = G.entry(P, pt, Pi[cc], false);
+        }
+        tsqr_update(R.data(), n, C.data(), c);
+      }
+      // close field: G(S_C, S_C)^-1 G(S_C, B_i) for each close j != i
+      for (int j : nbrs[i]) {
+        if (j == i) continue;
+        const std::vector<int64_t>& Pj = bp[l][j];
+        int nj = (int)Pj.size();
+        int sc = (p.near_samples <= 0 || p.near_samples >= nj) ? nj : p.near_samples;
+        std::vector<int64_t> SC(sc);
+        for (int t = 0; t < sc; ++t) SC[t] = Pj[((int64_t)t * nj) / sc];
+        std::vector<double> Acc((size_t)sc * sc), B((size_t)sc * n);
+        for (int a = 0; a < sc; ++a)
+          for (int b = 0; b < sc; ++b) Acc[(size_t)a * sc + b] = G.entry(P, SC[a], SC[b], a == b);
+        for (int cc = 0; cc < n; ++cc)
+          for (int a = 0; a < sc; ++a) B[(size_t)cc * sc + a] = G.entry(P, SC[a], Pi[cc], false);
+        if (!lu_solve_cols(Acc.data(), sc, B.data(), n)) {
+#pragma omp critical
+          bad = i;
+          continue;
+        }
+        tsqr_update(R.data(), n, B.data(), sc);
+      }
+      std::vector<int> piv;
+      pivoted_qr(R.data(), n, piv);
+      double r0 = n ? std::fabs(R[0]) : 0.0;
+      int k = 0;
+      if (r0 > 0)
+        for (int t = 0; t < n; ++t) k += std::fabs(R[(size_t)t * n + t]) > p.tol * r0;
+      ranks[i] = k;
+      Rb[i].swap(R);
+      pivs[i].swap(piv);
+    }
+    if (bad >= 0)
+      return "singular close-field sample block at level " + std::to_string(l) + " box " + std::to_string(bad);
+    int kmax = *std::max_element(ranks.begin(), ranks.end());
+    int cap = p.max_rank > 0 ? p.max_rank : D / 2;
+    int nmin = D;
+    for (int i = 0; i < nb; ++i) nmin = std::min<int>(nmin, (int)bp[l][i].size());
+    int K = std::max(1, std::min(std::min(kmax, cap), nmin));
+    if (nmin == 0) K = 0;
+    hl.K = K;
+    if (l == L) H.ranks_leaf = ranks;
+    hl.X.assign((size_t)nb * D * K, 0.0);
+    hl.SK.assign((size_t)nb * K, 0);
+    bp[l - 1].resize(nb / 2);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < nb; ++i) {
+      const std::vector<double>& R = Rb[i];
+      const std::vector<int>& piv = pivs[i];
+      int n = (int)bp[l][i].size();
+      int m = n - K;
+      // T = R11^-1 R12 (K x m); rows with a zero pivot are set to 0
+      std::vector<double> T((size_t)K * m, 0.0);
+      double r0 = n ? std::fabs(R[0]) : 0.0;
+      for (int t = K - 1; t >= 0; --t) {
+        double d = R[(size_t)t * n + t];
+        if (!(std::fabs(d) > 1e-15 * r0) || d == 0.0) continue;
+        for (int b = 0; b < m; ++b) {
+          double s = R[(size_t)t * n + K + b];
+          for (int u = t + 1; u < K; ++u) s -= R[(size_t)t * n + u] * T[(size_t)u * m + b];
+          T[(size_t)t * m + b] = s / d;
+        }
+      }
+      double* X = &hl.X[(size_t)i * D * K];
+      for (int a = 0; a < K; ++a) X[(size_t)piv[a] * K + a] = 1.0;
+      for (int b = 0; b < m; ++b)
+        for (int a = 0; a < K; ++a) X[(size_t)piv[K + b] * K + a] = T[(size_t)a * m + b];
+      for (int a = 0; a < K; ++a) hl.SK[(size_t)i * K + a] = bp[l][i][piv[a]];
+    }
+    for (int q = 0; q < nb / 2; ++q) {
+      bp[l - 1][q].assign(hl.SK.begin() + (size_t)(2 * q) * K, hl.SK.begin() + (size_t)(2 * q + 2) * K);
+    }
+    H.lv[l - 1].D = 2 * K;
+  }
+  if (L == 0) H.lv[0].D = (int)N;
+  return "";
+}
+
+}  // namespace h2

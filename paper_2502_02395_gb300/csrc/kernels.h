@@ -1,0 +1,76 @@
+// Launchers of the device kernels (internal).
+#pragma once
+
+#include <atomic>
+
+#include "h2_internal.h"
+
+namespace h2 {
+
+// Number of kernels this library has launched (reported by h2_stats).
+extern std::atomic<long long> g_launches;
+
+// kernels_factor.cu
+void launch_eval_blocks(const KernelFn& G, const double* pts, int64_t npairs, const int32_t* pi,
+                        const int32_t* pj, const int64_t* idx, int idx_stride, int rows, int cols,
+                        double* out, cudaStream_t st);
+template <typename S, typename T>
+void launch_convert(const S* in, T* out, int64_t n, cudaStream_t st);
+template <typename T, typename TB>
+void gemm_simt(int M, int N, int K, const T* A, int64_t sA, const int32_t* ia, int lda, bool tA, const TB* B,
+               int64_t sB, const int32_t* ib, int ldb, bool tB, T* C, int64_t sC, const int32_t* ic, int ldc,
+               T alpha, T beta, int64_t batch, cudaStream_t st);
+template <typename T>
+void launch_orth_input(int nb, int D, int K, int Kc, const double* X, const T* Tc, T* Xo, cudaStream_t st);
+template <typename T>
+void launch_qr_complement(int nb, int D, int K, T* Xo, T* U, T* Tm, cudaStream_t st);
+template <typename T>
+void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, int32_t* piv,
+                       T* Ainv, int32_t* status, int level, cudaStream_t st);
+template <typename T>
+void launch_merge(int D, int K, int64_t NP, const T* Ahat, const int32_t* ni, const int32_t* nj,
+                  const int32_t* ndst, int64_t FP, const T* Shat, const int32_t* fi, const int32_t* fj,
+                  const int32_t* fdst, T* Apar, cudaStream_t st);
+
+// kernels_tc.cu: tensor-core (tcgen05) batched GEMM, FP16/BF16 inputs, FP32
+// accumulation and output.  Operands as in gemm_simt; returns false when the
+// shape is not supported (the caller then uses gemm_simt).
+bool gemm_tc_supported(int M, int N, int K, int lda, int ldb, int ldc);
+void gemm_tc(int prec, int M, int N, int K, const void* A, int64_t sA, const int32_t* ia, int lda,
+             const void* B, int64_t sB, const int32_t* ib, int ldb, float* C, int64_t sC, const int32_t* ic,
+             int ldc, float alpha, float beta, int64_t batch, cudaStream_t st);
+void launch_to_lowp(int prec, const float* in, void* out, int64_t n, cudaStream_t st);
+void launch_to_lowp_d(int prec, const double* in, void* out, int64_t n, cudaStream_t st);
+
+// kernels_solve.cu: substitution (Eq. 24-31 and its mirror), H^2 matvec,
+// refinement vector operations
+template <typename T>
+void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st);
+template <typename T>
+void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st);
+template <typename T>
+void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, T* parent_vin, cudaStream_t st);
+template <typename T>
+void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st);
+template <typename T>
+void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st);
+template <typename T>
+void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st);  // y = M x, M n x n row-major
+
+void launch_matvec_up_leaf(const DevLevel& L, const double* x, double* xh, cudaStream_t st);
+void launch_matvec_up(const DevLevel& L, const double* xh_child, double* xh, cudaStream_t st);
+void launch_matvec_far(const DevLevel& L, const double* xh, double* yh, cudaStream_t st);
+void launch_matvec_down(const DevLevel& L, const double* yh, double* yh_child, cudaStream_t st);
+void launch_matvec_leaf(const DevLevel& L, const double* A, const double* x, const double* yh, double* y,
+                        cudaStream_t st);
+
+void launch_gather(const int64_t* slot, const double* src, double* dst, int64_t nslots, cudaStream_t st);
+void launch_scatter(const int64_t* slot, const double* src, double* dst, int64_t nslots, cudaStream_t st);
+void launch_residual(const double* b, const double* y, double* r, int64_t n, cudaStream_t st);
+void launch_norm2(const double* v, int64_t n, double* out, cudaStream_t st);  // out[0] = sum v^2
+template <typename T>
+void launch_scale_to(const double* in, const double* norm2, T* out, int64_t n, cudaStream_t st);
+template <typename T>
+void launch_axpy_from(const T* d, const double* norm2, double* x, int64_t n, cudaStream_t st);
+
+}  // namespace h2

@@ -1,0 +1,511 @@
+// Factorization kernels of the H^2-ULV library (sm_103a).
+//
+//   eval_blocks_kernel     dense kernel blocks G(B_i, B_j) of the leaf near
+//                          pairs and couplings G(SK_i, SK_j) (Algorithm 1
+//                          line 10-15), evaluated from the points
+//   gemm_batched_kernel    SIMT batched GEMM C = alpha op(A) op(B) + beta C
+//                          (FP64 path: projection Algorithm 4 line 3 / 10,
+//                          Schur update line 6, couplings)
+//   orth_input_kernel      X_p^orth = blockdiag(T_2p, T_2p+1) X_p (Eq. 6-7
+//                          above the leaves)
+//   qr_complement_kernel   Householder QR of X^orth: U = [U^R U^S], T
+//                          (Eq. 6-7), one CTA per box
+//   lu_inverse_kernel      partial-pivot LU of Ahat_ii^RR in FP64 (Algorithm
+//                          2 line 9 with LU in place of Cholesky) and the
+//                          explicit inverse (Ahat_ii^RR)^-1 used by the
+//                          Schur update and by the substitution of Eq. 31
+//   merge_kernel           children's SS blocks / couplings into the parent
+//                          near blocks (Algorithm 2 line 18-20)
+#include "h2_internal.h"
+#include "kernels.h"
+
+namespace h2 {
+
+// ------------------------------------------------------------------------
+// block evaluation
+// ------------------------------------------------------------------------
+template <typename T>
+__global__ void eval_blocks_kernel(KernelFn G, const double* __restrict__ pts, int64_t npairs,
+                                   const int32_t* __restrict__ pi, const int32_t* __restrict__ pj,
+                                   const int64_t* __restrict__ idx, int idx_stride, int rows, int cols,
+                                   T* __restrict__ out) {
+  int64_t per = (int64_t)rows * cols;
+  int64_t total = npairs * per;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t p = e / per;
+    int64_t rc = e - p * per;
+    int r = (int)(rc / cols), c = (int)(rc - (int64_t)r * cols);
+    int i = pi[p], j = pj[p];
+    int64_t a = idx[(int64_t)i * idx_stride + r], b = idx[(int64_t)j * idx_stride + c];
+    out[e] = (T)G.entry(pts, a, b, i == j && r == c);
+  }
+}
+
+void launch_eval_blocks(const KernelFn& G, const double* pts, int64_t npairs, const int32_t* pi,
+                        const int32_t* pj, const int64_t* idx, int idx_stride, int rows, int cols,
+                        double* out, cudaStream_t st) {
+  if (npairs == 0 || rows == 0 || cols == 0) return;
+  int64_t total = npairs * rows * cols;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 64);
+  ++g_launches;
+  eval_blocks_kernel<double><<<blocks, 256, 0, st>>>(G, pts, npairs, pi, pj, idx, idx_stride, rows, cols, out);
+}
+
+// ------------------------------------------------------------------------
+// conversions
+// ------------------------------------------------------------------------
+template <typename S, typename T>
+__global__ void convert_kernel(const S* __restrict__ in, T* __restrict__ out, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)in[e];
+}
+template <typename S, typename T>
+void launch_convert(const S* in, T* out, int64_t n, cudaStream_t st) {
+  if (n == 0) return;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+  ++g_launches;
+  convert_kernel<S, T><<<blocks, 256, 0, st>>>(in, out, n);
+}
+template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, int64_t, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+template void launch_convert<float, float>(const float*, float*, int64_t, cudaStream_t);
+
+// ------------------------------------------------------------------------
+// SIMT batched GEMM (row-major operands):
+//   op(A)(m,k) = tA ? A[k*lda+m] : A[m*lda+k]
+//   op(B)(k,n) = tB ? B[n*ldb+k] : B[k*ldb+n]
+//   C(m,n)     = C[m*ldc+n]
+// Batch b uses A + (ia ? ia[b] : b) * sA, likewise B and C.
+// ------------------------------------------------------------------------
+template <typename T, typename TB>
+__global__ void __launch_bounds__(256)
+gemm_batched_kernel(int M, int N, int K, const T* __restrict__ A, int64_t sA, const int32_t* __restrict__ ia,
+                    int lda, int tA, const TB* __restrict__ B, int64_t sB, const int32_t* __restrict__ ib,
+                    int ldb, int tB, T* __restrict__ C, int64_t sC, const int32_t* __restrict__ ic, int ldc,
+                    T alpha, T beta, int64_t batch) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  for (int64_t b = blockIdx.z; b < batch; b += gridDim.z) {
+    const T* Ab = A + (ia ? (int64_t)ia[b] : b) * sA;
+    const TB* Bb = B + (ib ? (int64_t)ib[b] : b) * sB;
+    T* Cb = C + (ic ? (int64_t)ic[b] : b) * sC;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      for (int e = threadIdx.x; e < BM * BK; e += 256) {
+        int mm, kk;
+        if (tA) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+        int gm = m0 + mm, gk = k0 + kk;
+        T v = T(0);
+        if (gm < M && gk < K) v = tA ? Ab[(int64_t)gk * lda + gm] : Ab[(int64_t)gm * lda + gk];
+        As[kk][mm] = v;
+      }
+      for (int e = threadIdx.x; e < BN * BK; e += 256) {
+        int nn, kk;
+        if (tB) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
+        int gn = n0 + nn, gk = k0 + kk;
+        T v = T(0);
+        if (gn < N && gk < K) v = (T)(tB ? Bb[(int64_t)gn * ldb + gk] : Bb[(int64_t)gk * ldb + gn]);
+        Bs[kk][nn] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int gm = m0 + ty + 16 * i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int gn = n0 + tx + 16 * j;
+        if (gn >= N) continue;
+        T* cp = Cb + (int64_t)gm * ldc + gn;
+        T r = alpha * acc[i][j];
+        if (beta != T(0)) r = fma(beta, *cp, r);
+        *cp = r;
+      }
+    }
+  }
+}
+
+template <typename T, typename TB>
+void gemm_simt(int M, int N, int K, const T* A, int64_t sA, const int32_t* ia, int lda, bool tA, const TB* B,
+               int64_t sB, const int32_t* ib, int ldb, bool tB, T* C, int64_t sC, const int32_t* ic, int ldc,
+               T alpha, T beta, int64_t batch, cudaStream_t st) {
+  if (batch == 0 || M == 0 || N == 0) return;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, (unsigned)std::min<int64_t>(batch, 65535));
+  ++g_launches;
+  gemm_batched_kernel<T, TB><<<grid, 256, 0, st>>>(M, N, K, A, sA, ia, lda, tA, B, sB, ib, ldb, tB, C, sC, ic, ldc,
+                                                   alpha, beta, batch);
+}
+template void gemm_simt<double, double>(int, int, int, const double*, int64_t, const int32_t*, int, bool,
+                                        const double*, int64_t, const int32_t*, int, bool, double*, int64_t,
+                                        const int32_t*, int, double, double, int64_t, cudaStream_t);
+template void gemm_simt<float, float>(int, int, int, const float*, int64_t, const int32_t*, int, bool,
+                                      const float*, int64_t, const int32_t*, int, bool, float*, int64_t,
+                                      const int32_t*, int, float, float, int64_t, cudaStream_t);
+template void gemm_simt<float, double>(int, int, int, const float*, int64_t, const int32_t*, int, bool,
+                                       const double*, int64_t, const int32_t*, int, bool, float*, int64_t,
+                                       const int32_t*, int, float, float, int64_t, cudaStream_t);
+
+// ------------------------------------------------------------------------
+// block-wide sum
+// ------------------------------------------------------------------------
+template <typename T>
+__device__ T block_sum(T v, T* sbuf) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sbuf[warp] = v;
+  __syncthreads();
+  T t = T(0);
+  for (int w = 0; w < nw; ++w) t += sbuf[w];
+  return t;
+}
+
+// ------------------------------------------------------------------------
+// a1: X^orth (column-major D x K per box)
+//   leaf:  X^orth = X
+//   upper: X^orth = blockdiag(T_2p, T_2p+1) X,  T row-major Kc x Kc
+// ------------------------------------------------------------------------
+template <typename T>
+__global__ void orth_input_kernel(int D, int K, int Kc, const double* __restrict__ X,
+                                  const T* __restrict__ Tc, T* __restrict__ Xo) {
+  int box = blockIdx.y;
+  const double* Xb = X + (int64_t)box * D * K;
+  T* Ob = Xo + (int64_t)box * D * K;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D * K; e += gridDim.x * blockDim.x) {
+    int a = e / D, r = e - a * D;  // output column a, row r (column-major)
+    T v;
+    if (Kc == 0) {
+      v = (T)Xb[(int64_t)r * K + a];
+    } else {
+      int half = r / Kc, rr = r - half * Kc;
+      const T* Tb = Tc + (int64_t)(2 * box + half) * Kc * Kc + (int64_t)rr * Kc;
+      const double* xcol = Xb + (int64_t)half * Kc * K + a;
+      T s = T(0);
+      for (int u = rr; u < Kc; ++u) s = fma(Tb[u], (T)xcol[(int64_t)u * K], s);  // T upper triangular
+      v = s;
+    }
+    Ob[e] = v;
+  }
+}
+
+template <typename T>
+void launch_orth_input(int nb, int D, int K, int Kc, const double* X, const T* Tc, T* Xo, cudaStream_t st) {
+  if (nb == 0 || D * K == 0) return;
+  dim3 grid((D * K + 255) / 256, nb);
+  ++g_launches;
+  orth_input_kernel<T><<<grid, 256, 0, st>>>(D, K, Kc, X, Tc, Xo);
+}
+template void launch_orth_input<double>(int, int, int, int, const double*, const double*, double*, cudaStream_t);
+template void launch_orth_input<float>(int, int, int, int, const double*, const float*, float*, cudaStream_t);
+
+// ------------------------------------------------------------------------
+// a1: Householder QR (LAPACK geqr2 + org2r conventions).
+//   Xo  column-major D x K (destroyed: reflectors)
+//   U   column-major D x D; Q column j goes to U column (j < K ? R + j : j - K)
+//   Tm  row-major K x K upper triangular: X^orth = U^S T
+// ------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) qr_complement_kernel(int D, int K, T* __restrict__ Xo, T* __restrict__ U,
+                                                            T* __restrict__ Tm) {
+  extern __shared__ unsigned char smraw[];
+  T* tau = reinterpret_cast<T*>(smraw);  // K
+  __shared__ T red[32];
+  __shared__ T s_tau, s_scal, s_beta;
+  const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  T* X = Xo + (int64_t)box * D * K;
+  T* Q = U + (int64_t)box * D * D;
+  const int R = D - K;
+  for (int k = 0; k < K; ++k) {
+    T* xk = X + (int64_t)k * D;
+    T part = T(0);
+    for (int r = k + 1 + tid; r < D; r += blockDim.x) part += xk[r] * xk[r];
+    T xn2 = block_sum(part, red);
+    if (tid == 0) {
+      T alpha = xk[k];
+      if (xn2 == T(0)) {
+        s_tau = T(0);
+      } else {
+        T beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        s_tau = (beta - alpha) / beta;
+        s_scal = T(1) / (alpha - beta);
+        s_beta = beta;
+      }
+    }
+    __syncthreads();
+    const T tk = s_tau;
+    if (tk != T(0)) {
+      const T scal = s_scal;
+      for (int r = k + 1 + tid; r < D; r += blockDim.x) xk[r] *= scal;
+      __syncthreads();
+      if (tid == 0) xk[k] = s_beta;
+      for (int j = k + 1 + warp; j < K; j += nw) {
+        T* xj = X + (int64_t)j * D;
+        T w = T(0);
+        for (int r = k + 1 + lane; r < D; r += 32) w += xk[r] * xj[r];
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        w = tk * (w + xj[k]);
+        if (lane == 0) xj[k] -= w;
+        for (int r = k + 1 + lane; r < D; r += 32) xj[r] -= w * xk[r];
+      }
+    }
+    if (tid == 0) tau[k] = tk;
+    __syncthreads();
+  }
+  // T = upper triangle of the first K rows
+  for (int e = tid; e < K * K; e += blockDim.x) {
+    int a = e / K, b = e - a * K;
+    Tm[(int64_t)box * K * K + e] = (b >= a) ? X[(int64_t)b * D + a] : T(0);
+  }
+  // Q = H_0 ... H_{K-1} applied to the identity (column j of Q in U column cmap(j))
+  auto cmap = [&](int j) { return j < K ? R + j : j - K; };
+  for (int e = tid; e < D * D; e += blockDim.x) {
+    int j = e / D, r = e - j * D;
+    Q[(int64_t)cmap(j) * D + r] = (r == j) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int k = K - 1; k >= 0; --k) {
+    const T tk = tau[k];
+    if (tk != T(0)) {
+      const T* v = X + (int64_t)k * D;  // v[k] = 1 implicit, v[r>k] stored
+      for (int j = k + warp; j < D; j += nw) {
+        T* qj = Q + (int64_t)cmap(j) * D;
+        T w = T(0);
+        for (int r = k + 1 + lane; r < D; r += 32) w += v[r] * qj[r];
+        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        w = tk * (w + qj[k]);
+        if (lane == 0) qj[k] -= w;
+        for (int r = k + 1 + lane; r < D; r += 32) qj[r] -= w * v[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+void launch_qr_complement(int nb, int D, int K, T* Xo, T* U, T* Tm, cudaStream_t st) {
+  if (nb == 0) return;
+  ++g_launches;
+  qr_complement_kernel<T><<<nb, 256, sizeof(T) * (K + 1), st>>>(D, K, Xo, U, Tm);
+}
+template void launch_qr_complement<double>(int, int, int, double*, double*, double*, cudaStream_t);
+template void launch_qr_complement<float>(int, int, int, float*, float*, float*, cudaStream_t);
+
+// ------------------------------------------------------------------------
+// a3: FP64 partial-pivot LU of Ahat_ii^RR (rows/cols 0..R of a D x D
+// row-major block) and the inverse (Ahat_ii^RR)^-1 (row-major R x R, in T).
+//   lu   column-major R x R FP64 (L unit lower, U upper), piv LAPACK-style
+//   M    working copy: shared memory (ld = R + 1) when it fits, else lu
+// A zero pivot records (level, box) in status[0..1] and leaves the rest of
+// that box's factorization undefined.
+// ------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_inverse_kernel(int D, int R, const T* __restrict__ Ablk, const int32_t* __restrict__ diag_idx,
+                  double* __restrict__ lu, int32_t* __restrict__ piv, T* __restrict__ Ainv,
+                  int32_t* __restrict__ status, int level, int use_smem) {
+  extern __shared__ double smd[];
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const T* A = Ablk + (int64_t)(diag_idx ? diag_idx[box] : box) * D * D;
+  double* G = lu + (int64_t)box * R * R;
+  double* M = use_smem ? smd : G;
+  const int ld = use_smem ? R + 1 : R;
+  int32_t* pv = piv + (int64_t)box * R;
+  if (tid == 0) s_bad = 0;
+  for (int e = tid; e < R * R; e += blockDim.x) {
+    int r = e / R, c = e - r * R;
+    M[(int64_t)c * ld + r] = (double)A[(int64_t)r * D + c];
+  }
+  __syncthreads();
+  for (int k = 0; k < R; ++k) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = k;
+      for (int r = k + lane; r < R; r += 32) {
+        double a = fabs(M[(int64_t)k * ld + r]);
+        if (a > best) { best = a; bi = r; }
+      }
+      for (int o = 16; o; o >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { s_p = bi; pv[k] = bi; }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != k)
+      for (int c = tid; c < R; c += blockDim.x) {
+        double t = M[(int64_t)c * ld + k];
+        M[(int64_t)c * ld + k] = M[(int64_t)c * ld + p];
+        M[(int64_t)c * ld + p] = t;
+      }
+    __syncthreads();
+    const double d = M[(int64_t)k * ld + k];
+    if (d == 0.0) {
+      if (tid == 0) {
+        s_bad = 1;
+        if (atomicCAS(status, 0, level + 1) == 0) status[1] = box;
+      }
+      break;
+    }
+    const double inv = 1.0 / d;
+    for (int r = k + 1 + tid; r < R; r += blockDim.x) M[(int64_t)k * ld + r] *= inv;
+    __syncthreads();
+    for (int c = k + 1 + warp; c < R; c += nw) {
+      const double f = M[(int64_t)c * ld + k];
+      if (f != 0.0)
+        for (int r = k + 1 + lane; r < R; r += 32) M[(int64_t)c * ld + r] -= M[(int64_t)k * ld + r] * f;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (s_bad) return;
+  if (use_smem)
+    for (int e = tid; e < R * R; e += blockDim.x) {
+      int c = e / R, r = e - c * R;
+      G[e] = M[(int64_t)c * ld + r];
+    }
+  // inverse Y = (P L U)^-1 = U^-1 L^-1 P^T, built by sweeps over all
+  // columns at once: Y = P^T I, then the unit-lower forward sweep, then the
+  // upper backward sweep (row k is final once step k starts; the division by
+  // U(k,k) is applied to the whole row at the end).  Y is row-major R x R,
+  // in shared memory after M when it fits, else in the output buffer.
+  T* Yout = Ainv + (int64_t)box * R * R;
+  T* Y = Yout;
+  int ldy = R;
+  if (use_smem == 2) {
+    Y = reinterpret_cast<T*>(smd + (size_t)R * (R + 1));
+    ldy = R;
+  }
+  __syncthreads();
+  for (int e = tid; e < R * R; e += blockDim.x) {
+    int r = e / R, b = e - r * R;
+    Y[(int64_t)r * ldy + b] = (r == b) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int k = 0; k < R; ++k) {
+    const int p = pv[k];
+    if (p != k)
+      for (int b = tid; b < R; b += blockDim.x) {
+        T t = Y[(int64_t)k * ldy + b];
+        Y[(int64_t)k * ldy + b] = Y[(int64_t)p * ldy + b];
+        Y[(int64_t)p * ldy + b] = t;
+      }
+    __syncthreads();
+  }
+  for (int k = 0; k < R - 1; ++k) {
+    const int n = (R - 1 - k) * R;
+    for (int e = tid; e < n; e += blockDim.x) {
+      int r = k + 1 + e / R, b = e % R;
+      const double l = M[(int64_t)k * ld + r];
+      if (l != 0.0) Y[(int64_t)r * ldy + b] = (T)((double)Y[(int64_t)r * ldy + b] - l * (double)Y[(int64_t)k * ldy + b]);
+    }
+    __syncthreads();
+  }
+  for (int k = R - 1; k > 0; --k) {
+    const double dk = M[(int64_t)k * ld + k];
+    const int n = k * R;
+    for (int e = tid; e < n; e += blockDim.x) {
+      int r = e / R, b = e - r * R;
+      const double u = M[(int64_t)k * ld + r];
+      if (u != 0.0)
+        Y[(int64_t)r * ldy + b] = (T)((double)Y[(int64_t)r * ldy + b] - u * ((double)Y[(int64_t)k * ldy + b] / dk));
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < R * R; e += blockDim.x) {
+    int r = e / R, b = e - r * R;
+    Yout[e] = (T)((double)Y[(int64_t)r * ldy + b] / M[(int64_t)r * ld + r]);
+  }
+}
+
+template <typename T>
+void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, int32_t* piv,
+                       T* Ainv, int32_t* status, int level, cudaStream_t st) {
+  if (nb == 0 || R == 0) return;
+  // use_smem: 0 = everything in global memory, 1 = LU in shared memory,
+  // 2 = LU and the inverse's working matrix in shared memory
+  size_t sm1 = sizeof(double) * (size_t)R * (R + 1);
+  size_t sm2 = sm1 + sizeof(T) * (size_t)R * R;
+  const size_t cap = 220 * 1024;
+  int use_smem = sm2 <= cap ? 2 : (sm1 <= cap ? 1 : 0);
+  size_t sm = use_smem == 2 ? sm2 : (use_smem == 1 ? sm1 : 0);
+  if (sm) cudaFuncSetAttribute(lu_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ++g_launches;
+  lu_inverse_kernel<T><<<nb, 256, sm, st>>>(D, R, Ablk, diag_idx, lu, piv, Ainv, status, level, use_smem);
+}
+template void launch_lu_inverse<double>(int, int, int, const double*, const int32_t*, double*, int32_t*, double*,
+                                        int32_t*, int, cudaStream_t);
+template void launch_lu_inverse<float>(int, int, int, const float*, const int32_t*, double*, int32_t*, float*,
+                                       int32_t*, int, cudaStream_t);
+
+// ------------------------------------------------------------------------
+// a6: merge.  Child pair q of level l (near: its SS part of Ahat; far: Shat)
+// goes to quadrant (i%2, j%2) of parent near block dst[q] (D_{l-1} = 2K).
+// ------------------------------------------------------------------------
+template <typename T>
+__global__ void merge_kernel(int D, int K, int64_t NP, const T* __restrict__ Ahat,
+                             const int32_t* __restrict__ ni, const int32_t* __restrict__ nj,
+                             const int32_t* __restrict__ ndst, int64_t FP, const T* __restrict__ Shat,
+                             const int32_t* __restrict__ fi, const int32_t* __restrict__ fj,
+                             const int32_t* __restrict__ fdst, T* __restrict__ Apar) {
+  const int R = D - K, Dp = 2 * K;
+  const int64_t q = blockIdx.y + (int64_t)blockIdx.z * gridDim.y;
+  if (q >= NP + FP) return;
+  const bool nr = q < NP;
+  const int64_t qq = nr ? q : q - NP;
+  const int i = nr ? ni[qq] : fi[qq], j = nr ? nj[qq] : fj[qq];
+  const int64_t dst = nr ? ndst[qq] : fdst[qq];
+  T* out = Apar + dst * Dp * Dp + (int64_t)(i & 1) * K * Dp + (j & 1) * K;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x) {
+    int a = e / K, b = e - a * K;
+    T v = nr ? Ahat[qq * D * D + (int64_t)(R + a) * D + R + b] : Shat[qq * K * K + e];
+    out[(int64_t)a * Dp + b] = v;
+  }
+}
+
+template <typename T>
+void launch_merge(int D, int K, int64_t NP, const T* Ahat, const int32_t* ni, const int32_t* nj,
+                  const int32_t* ndst, int64_t FP, const T* Shat, const int32_t* fi, const int32_t* fj,
+                  const int32_t* fdst, T* Apar, cudaStream_t st) {
+  int64_t n = NP + FP;
+  if (n == 0 || K == 0) return;
+  int gx = std::min(64, (K * K + 255) / 256);
+  int64_t gy = std::min<int64_t>(n, 65535), gz = (n + gy - 1) / gy;
+  ++g_launches;
+  merge_kernel<T><<<dim3(gx, (unsigned)gy, (unsigned)gz), 256, 0, st>>>(D, K, NP, Ahat, ni, nj, ndst, FP, Shat, fi,
+                                                                         fj, fdst, Apar);
+}
+template void launch_merge<double>(int, int, int64_t, const double*, const int32_t*, const int32_t*,
+                                   const int32_t*, int64_t, const double*, const int32_t*, const int32_t*,
+                                   const int32_t*, double*, cudaStream_t);
+template void launch_merge<float>(int, int, int64_t, const float*, const int32_t*, const int32_t*, const int32_t*,
+                                  int64_t, const float*, const int32_t*, const int32_t*, const int32_t*, float*,
+                                  cudaStream_t);
+
+}  // namespace h2

@@ -1,0 +1,462 @@
+// Substitution, H^2 matvec and refinement kernels (sm_103a).
+//
+// Parallel substitution (Eq. 24-31, Section 3.7) and its mirror image for the
+// backward pass.  With Ainv_i = (Ahat_ii^RR)^-1 = U'_ii^-1 (P_i L_ii)^-1, the
+// product form of L^-1 in Eq. 31 needs only whole-block inverses and
+// matrix-vector products, so every step below is a batched GEMV over all
+// boxes of a level (one CTA per box), with no serial triangular solve:
+//   fwd1  c_i = U_i^T b_i;                  u_i = Ainv_i c_i^R
+//   fwd2  v_i = Ainv_i (c_i^R - sum_{j<i near} Ahat_ij^RR u_j)
+//   fwd3  s_i = c_i^S - sum_{j near} Ahat_ij^SR v_j   -> parent input
+//   bwd1  om_i = v_i - Ainv_i sum_{j near} Ahat_ij^RS x_j^S
+//   bwd2  x_i^R = om_i - Ainv_i sum_{j>i near} Ahat_ij^RR om_j;
+//         x_i = U_i [x_i^R; x_i^S]
+// (fwd2 is L_ii^-1 (b_i^R - sum L(r)_ij L_jj^-1 b_j) followed by U'_ii^-1;
+// bwd1/bwd2 are the mirror with U(s)_ij = (P_i L_ii)^-1 Ahat_ij^RS and
+// U(r)_ij = (P_i L_ii)^-1 Ahat_ij^RR, multiplied through by U'_ii^-1.)
+//
+// H^2 matvec (FP64): upward pass x^_i = X_i^T x_i, couplings y^_i +=
+// S_ij x^_j on every level, downward pass, leaf y_i = X_i y^_i +
+// sum_near A_ij x_j.
+#include "h2_internal.h"
+#include "kernels.h"
+
+namespace h2 {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ys[r] += sign * sum_c M[r*ld + c] xs[c], r < nr, c < nc; row r is owned by
+// warp r % nwarps (so successive calls with the same nr never race).
+template <typename T>
+__device__ __forceinline__ void warp_rows_gemv(const T* __restrict__ M, int64_t ld, int nr, int nc,
+                                               const T* xs, T* ys, T sign) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int r = warp;
+  for (; r + 3 * nw < nr; r += 4 * nw) {
+    const T* m0 = M + (int64_t)r * ld;
+    const T* m1 = m0 + nw * ld;
+    const T* m2 = m1 + nw * ld;
+    const T* m3 = m2 + nw * ld;
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int c = lane; c < nc; c += 32) {
+      T x = xs[c];
+      s0 += m0[c] * x;
+      s1 += m1[c] * x;
+      s2 += m2[c] * x;
+      s3 += m3[c] * x;
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    s3 = warp_sum(s3);
+    if (lane == 0) {
+      ys[r] += sign * s0;
+      ys[r + nw] += sign * s1;
+      ys[r + 2 * nw] += sign * s2;
+      ys[r + 3 * nw] += sign * s3;
+    }
+  }
+  for (; r < nr; r += nw) {
+    const T* m0 = M + (int64_t)r * ld;
+    T s0 = 0;
+    for (int c = lane; c < nc; c += 32) s0 += m0[c] * xs[c];
+    s0 = warp_sum(s0);
+    if (lane == 0) ys[r] += sign * s0;
+  }
+}
+
+// ---------------------------------------------------------------- fwd1 ---
+template <typename T>
+__global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, const T* __restrict__ U, const T* __restrict__ Ainv,
+                                                   const T* __restrict__ vin, T* __restrict__ c, T* __restrict__ u) {
+  extern __shared__ unsigned char sm_raw[];
+  T* sv = reinterpret_cast<T*>(sm_raw);  // D
+  T* sc = sv + D;                        // D
+  T* su = sc + D;                        // R
+  const int i = blockIdx.x, tid = threadIdx.x;
+  for (int e = tid; e < D; e += blockDim.x) { sv[e] = vin[(int64_t)i * D + e]; sc[e] = 0; }
+  for (int e = tid; e < R; e += blockDim.x) su[e] = 0;
+  __syncthreads();
+  // c[n] = sum_k U(k, n) v[k]; U column-major: column n contiguous
+  warp_rows_gemv<T>(U + (int64_t)i * D * D, D, D, D, sv, sc, T(1));
+  __syncthreads();
+  warp_rows_gemv<T>(Ainv + (int64_t)i * R * R, R, R, R, sc, su, T(1));
+  __syncthreads();
+  for (int e = tid; e < D; e += blockDim.x) c[(int64_t)i * D + e] = sc[e];
+  for (int e = tid; e < R; e += blockDim.x) u[(int64_t)i * R + e] = su[e];
+}
+
+// ---------------------------------------------------------------- fwd2 ---
+template <typename T>
+__global__ void __launch_bounds__(256) fwd2_kernel(int D, int R, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
+                                                   const T* __restrict__ Ainv, const T* __restrict__ c,
+                                                   const T* __restrict__ u, T* __restrict__ v) {
+  extern __shared__ unsigned char sm_raw[];
+  T* sb = reinterpret_cast<T*>(sm_raw);  // R
+  T* sx = sb + R;                        // R
+  T* sv = sx + R;                        // R
+  const int i = blockIdx.x, tid = threadIdx.x;
+  for (int e = tid; e < R; e += blockDim.x) { sb[e] = c[(int64_t)i * D + e]; sv[e] = 0; }
+  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+    const int j = nj[p];
+    if (j >= i) break;  // sorted: only j < i
+    __syncthreads();
+    for (int e = tid; e < R; e += blockDim.x) sx[e] = u[(int64_t)j * R + e];
+    __syncthreads();
+    warp_rows_gemv<T>(Ahat + p * D * D, D, R, R, sx, sb, T(-1));
+  }
+  __syncthreads();
+  warp_rows_gemv<T>(Ainv + (int64_t)i * R * R, R, R, R, sb, sv, T(1));
+  __syncthreads();
+  for (int e = tid; e < R; e += blockDim.x) v[(int64_t)i * R + e] = sv[e];
+}
+
+// ---------------------------------------------------------------- fwd3 ---
+template <typename T>
+__global__ void __launch_bounds__(256) fwd3_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
+                                                   const T* __restrict__ c, const T* __restrict__ v,
+                                                   T* __restrict__ pvin) {
+  extern __shared__ unsigned char sm_raw[];
+  T* ss = reinterpret_cast<T*>(sm_raw);  // K
+  T* sx = ss + K;                        // R
+  const int i = blockIdx.x, tid = threadIdx.x;
+  for (int e = tid; e < K; e += blockDim.x) ss[e] = c[(int64_t)i * D + R + e];
+  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+    const int j = nj[p];
+    __syncthreads();
+    for (int e = tid; e < R; e += blockDim.x) sx[e] = v[(int64_t)j * R + e];
+    __syncthreads();
+    warp_rows_gemv<T>(Ahat + p * D * D + (int64_t)R * D, D, K, R, sx, ss, T(-1));
+  }
+  __syncthreads();
+  const int Dp = 2 * K;
+  for (int e = tid; e < K; e += blockDim.x) pvin[(int64_t)(i >> 1) * Dp + (i & 1) * K + e] = ss[e];
+}
+
+// ---------------------------------------------------------------- bwd1 ---
+template <typename T>
+__global__ void __launch_bounds__(256) bwd1_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
+                                                   const T* __restrict__ Ainv, const T* __restrict__ v,
+                                                   const T* __restrict__ px, T* __restrict__ om) {
+  extern __shared__ unsigned char sm_raw[];
+  T* st = reinterpret_cast<T*>(sm_raw);  // R
+  T* sx = st + R;                        // K
+  T* so = sx + K;                        // R
+  const int i = blockIdx.x, tid = threadIdx.x, Dp = 2 * K;
+  for (int e = tid; e < R; e += blockDim.x) { st[e] = 0; so[e] = v[(int64_t)i * R + e]; }
+  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+    const int j = nj[p];
+    __syncthreads();
+    for (int e = tid; e < K; e += blockDim.x) sx[e] = px[(int64_t)(j >> 1) * Dp + (j & 1) * K + e];
+    __syncthreads();
+    warp_rows_gemv<T>(Ahat + p * D * D + R, D, R, K, sx, st, T(1));
+  }
+  __syncthreads();
+  warp_rows_gemv<T>(Ainv + (int64_t)i * R * R, R, R, R, st, so, T(-1));
+  __syncthreads();
+  for (int e = tid; e < R; e += blockDim.x) om[(int64_t)i * R + e] = so[e];
+}
+
+// ---------------------------------------------------------------- bwd2 ---
+template <typename T>
+__global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
+                                                   const T* __restrict__ Ainv, const T* __restrict__ U,
+                                                   const T* __restrict__ om, const T* __restrict__ px,
+                                                   T* __restrict__ xs) {
+  extern __shared__ unsigned char sm_raw[];
+  T* sq = reinterpret_cast<T*>(sm_raw);  // R
+  T* sx = sq + R;                        // R  (om_j, then [x^R; x^S] of length D)
+  T* sz = sx + D;                        // D
+  const int i = blockIdx.x, tid = threadIdx.x, Dp = 2 * K;
+  for (int e = tid; e < R; e += blockDim.x) sq[e] = 0;
+  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+    const int j = nj[p];
+    if (j <= i) continue;
+    __syncthreads();
+    for (int e = tid; e < R; e += blockDim.x) sx[e] = om[(int64_t)j * R + e];
+    __syncthreads();
+    warp_rows_gemv<T>(Ahat + p * D * D, D, R, R, sx, sq, T(1));
+  }
+  __syncthreads();
+  for (int e = tid; e < R; e += blockDim.x) sz[e] = om[(int64_t)i * R + e];
+  for (int e = tid; e < K; e += blockDim.x) sz[R + e] = px[(int64_t)(i >> 1) * Dp + (i & 1) * K + e];
+  __syncthreads();
+  warp_rows_gemv<T>(Ainv + (int64_t)i * R * R, R, R, R, sq, sz, T(-1));
+  __syncthreads();
+  // x = U z, U column-major: x[m] = sum_n U[n*D + m] z[n]
+  const T* Ub = U + (int64_t)i * D * D;
+  for (int m = tid; m < D; m += blockDim.x) {
+    T s = 0;
+    for (int n = 0; n < D; ++n) s += Ub[(int64_t)n * D + m] * sz[n];
+    xs[(int64_t)i * D + m] = s;
+  }
+}
+
+template <typename T>
+void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st) {
+  size_t sm = sizeof(T) * (2 * L.D + L.R);
+  ++g_launches;
+  fwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, F.U, Ainv, F.vin, F.c, F.u);
+}
+template <typename T>
+void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st) {
+  size_t sm = sizeof(T) * 3 * L.R;
+  ++g_launches;
+  fwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.near_ptr, L.near_j, F.Ahat, Ainv, F.c, F.u, F.v);
+}
+template <typename T>
+void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, T* parent_vin, cudaStream_t st) {
+  size_t sm = sizeof(T) * (L.K + L.R);
+  ++g_launches;
+  fwd3_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, F.c, F.v, parent_vin);
+}
+template <typename T>
+void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st) {
+  size_t sm = sizeof(T) * (2 * L.R + L.K);
+  ++g_launches;
+  bwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, Ainv, F.v, parent_x, F.om);
+}
+template <typename T>
+void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st) {
+  size_t sm = sizeof(T) * (L.R + 2 * L.D);
+  ++g_launches;
+  bwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, Ainv, F.U, F.om, parent_x,
+                                        F.xs);
+}
+
+// y = M x for one n x n row-major matrix (root solve with the explicit inverse)
+template <typename T>
+__global__ void gemv_rows_kernel(int n, const T* __restrict__ M, const T* __restrict__ x, T* __restrict__ y) {
+  extern __shared__ unsigned char sm_raw[];
+  T* sx = reinterpret_cast<T*>(sm_raw);
+  T* sy = sx + n;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) { sx[e] = x[e]; sy[e] = 0; }
+  __syncthreads();
+  warp_rows_gemv<T>(M, n, n, n, sx, sy, T(1));
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) y[e] = sy[e];
+}
+template <typename T>
+void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st) {
+  if (n == 0) return;
+  const size_t sm = sizeof(T) * 2 * (size_t)n;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(gemv_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ++g_launches;
+  gemv_rows_kernel<T><<<1, 256, sm, st>>>(n, M, x, y);
+}
+
+#define H2_INST_SOLVE(T)                                                                              \
+  template void launch_fwd1<T>(const DevLevel&, const FacLevel<T>&, const T*, cudaStream_t);          \
+  template void launch_fwd2<T>(const DevLevel&, const FacLevel<T>&, const T*, cudaStream_t);          \
+  template void launch_fwd3<T>(const DevLevel&, const FacLevel<T>&, T*, cudaStream_t);                \
+  template void launch_bwd1<T>(const DevLevel&, const FacLevel<T>&, const T*, const T*, cudaStream_t); \
+  template void launch_bwd2<T>(const DevLevel&, const FacLevel<T>&, const T*, const T*, cudaStream_t); \
+  template void launch_gemv_rows<T>(int, const T*, const T*, T*, cudaStream_t);
+H2_INST_SOLVE(double)
+H2_INST_SOLVE(float)
+
+// ------------------------------------------------------------- matvec ---
+// upward, leaf: xh_i[a] = sum_d X_i[d*K + a] x_i[d]
+__global__ void mv_up_leaf_kernel(int D, int K, const double* __restrict__ X, const double* __restrict__ x,
+                                  double* __restrict__ xh) {
+  const int i = blockIdx.x;
+  const double* Xb = X + (int64_t)i * D * K;
+  const double* xb = x + (int64_t)i * D;
+  for (int a = threadIdx.x; a < K; a += blockDim.x) {
+    double s = 0;
+    for (int d = 0; d < D; ++d) s += Xb[(int64_t)d * K + a] * xb[d];
+    xh[(int64_t)i * K + a] = s;
+  }
+}
+void launch_matvec_up_leaf(const DevLevel& L, const double* x, double* xh, cudaStream_t st) {
+  ++g_launches;
+  mv_up_leaf_kernel<<<L.nb, 128, 0, st>>>(L.D, L.K, L.X, x, xh);
+}
+// upward above the leaves: xh_p = X_p^T [xh_2p; xh_2p+1] (children packed contiguously)
+void launch_matvec_up(const DevLevel& L, const double* xh_child, double* xh, cudaStream_t st) {
+  ++g_launches;
+  mv_up_leaf_kernel<<<L.nb, 128, 0, st>>>(L.D, L.K, L.X, xh_child, xh);
+}
+
+// couplings: yh_i = sum_{far j} S_f xh_j   (overwrites yh_i)
+__global__ void __launch_bounds__(256) mv_far_kernel(int K, const int64_t* __restrict__ ptr,
+                                                     const int32_t* __restrict__ fj, const double* __restrict__ S,
+                                                     const double* __restrict__ xh, double* __restrict__ yh) {
+  extern __shared__ double smv[];
+  double* sx = smv;      // K
+  double* sy = smv + K;  // K
+  const int i = blockIdx.x, tid = threadIdx.x;
+  for (int e = tid; e < K; e += blockDim.x) sy[e] = 0;
+  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+    const int j = fj[p];
+    __syncthreads();
+    for (int e = tid; e < K; e += blockDim.x) sx[e] = xh[(int64_t)j * K + e];
+    __syncthreads();
+    warp_rows_gemv<double>(S + p * K * K, K, K, K, sx, sy, 1.0);
+  }
+  __syncthreads();
+  for (int e = tid; e < K; e += blockDim.x) yh[(int64_t)i * K + e] = sy[e];
+}
+void launch_matvec_far(const DevLevel& L, const double* xh, double* yh, cudaStream_t st) {
+  ++g_launches;
+  mv_far_kernel<<<L.nb, 256, sizeof(double) * 2 * L.K, st>>>(L.K, L.far_ptr, L.far_j, L.S, xh, yh);
+}
+
+// downward: [yh_2p; yh_2p+1] += X_p yh_p   (rows d of X_p, D = 2 Kc)
+__global__ void mv_down_kernel(int D, int K, const double* __restrict__ X, const double* __restrict__ yh,
+                               double* __restrict__ yhc) {
+  const int p = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* Xb = X + (int64_t)p * D * K;
+  const double* yp = yh + (int64_t)p * K;
+  for (int d = warp; d < D; d += nw) {
+    double s = 0;
+    for (int a = lane; a < K; a += 32) s += Xb[(int64_t)d * K + a] * yp[a];
+    s = warp_sum(s);
+    if (lane == 0) yhc[(int64_t)p * D + d] += s;
+  }
+}
+void launch_matvec_down(const DevLevel& L, const double* yh, double* yh_child, cudaStream_t st) {
+  ++g_launches;
+  mv_down_kernel<<<L.nb, 256, 0, st>>>(L.D, L.K, L.X, yh, yh_child);
+}
+
+// leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j
+__global__ void __launch_bounds__(256) mv_leaf_kernel(int D, int K, const int64_t* __restrict__ ptr,
+                                                      const int32_t* __restrict__ nj, const double* __restrict__ A,
+                                                      const double* __restrict__ X, const double* __restrict__ x,
+                                                      const double* __restrict__ yh, double* __restrict__ y) {
+  extern __shared__ double smv[];
+  double* sx = smv;      // max(D, K)
+  double* sy = smv + D;  // D
+  const int i = blockIdx.x, tid = threadIdx.x;
+  for (int e = tid; e < D; e += blockDim.x) sy[e] = 0;
+  if (yh) {
+    for (int e = tid; e < K; e += blockDim.x) sx[e] = yh[(int64_t)i * K + e];
+    __syncthreads();
+    warp_rows_gemv<double>(X + (int64_t)i * D * K, K, D, K, sx, sy, 1.0);
+  }
+  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
+    const int j = nj[p];
+    __syncthreads();
+    for (int e = tid; e < D; e += blockDim.x) sx[e] = x[(int64_t)j * D + e];
+    __syncthreads();
+    warp_rows_gemv<double>(A + p * D * D, D, D, D, sx, sy, 1.0);
+  }
+  __syncthreads();
+  for (int e = tid; e < D; e += blockDim.x) y[(int64_t)i * D + e] = sy[e];
+}
+void launch_matvec_leaf(const DevLevel& L, const double* A, const double* x, const double* yh, double* y,
+                        cudaStream_t st) {
+  int sx = std::max(L.D, L.K);
+  const size_t sm = sizeof(double) * (size_t)(sx + L.D);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(mv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ++g_launches;
+  mv_leaf_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, A, L.X, x, yh, y);
+}
+
+// ------------------------------------------------------------ vectors ---
+__global__ void gather_kernel(const int64_t* __restrict__ slot, const double* __restrict__ src,
+                              double* __restrict__ dst, int64_t n) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = slot[s];
+    dst[s] = o >= 0 ? src[o] : 0.0;
+  }
+}
+__global__ void scatter_kernel(const int64_t* __restrict__ slot, const double* __restrict__ src,
+                               double* __restrict__ dst, int64_t n) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = slot[s];
+    if (o >= 0) dst[o] = src[s];
+  }
+}
+static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+void launch_gather(const int64_t* slot, const double* src, double* dst, int64_t n, cudaStream_t st) {
+  ++g_launches;
+  gather_kernel<<<grid_for(n), 256, 0, st>>>(slot, src, dst, n);
+}
+void launch_scatter(const int64_t* slot, const double* src, double* dst, int64_t n, cudaStream_t st) {
+  ++g_launches;
+  scatter_kernel<<<grid_for(n), 256, 0, st>>>(slot, src, dst, n);
+}
+__global__ void residual_kernel(const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r,
+                                int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    r[e] = b[e] - y[e];
+}
+void launch_residual(const double* b, const double* y, double* r, int64_t n, cudaStream_t st) {
+  ++g_launches;
+  residual_kernel<<<grid_for(n), 256, 0, st>>>(b, y, r, n);
+}
+// deterministic two-pass sum of squares: 256 partials, then one block
+__global__ void norm2_part_kernel(const double* __restrict__ v, int64_t n, double* __restrict__ part) {
+  __shared__ double sb[8];
+  double s = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s += v[e] * v[e];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < 8; ++w) t += sb[w];
+    part[blockIdx.x] = t;
+  }
+}
+__global__ void norm2_final_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
+  __shared__ double sb[8];
+  double s = 0;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) s += part[e];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < 8; ++w) t += sb[w];
+    out[0] = t;
+  }
+}
+void launch_norm2(const double* v, int64_t n, double* out, cudaStream_t st) {
+  ++g_launches;
+  norm2_part_kernel<<<256, 256, 0, st>>>(v, n, out + 1);
+  ++g_launches;
+  norm2_final_kernel<<<1, 256, 0, st>>>(out + 1, 256, out);
+}
+template <typename T>
+__global__ void scale_to_kernel(const double* __restrict__ in, const double* __restrict__ nrm2, T* __restrict__ out,
+                                int64_t n) {
+  const double s = nrm2[0] > 0 ? 1.0 / sqrt(nrm2[0]) : 1.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)(in[e] * s);
+}
+template <typename T>
+__global__ void axpy_from_kernel(const T* __restrict__ d, const double* __restrict__ nrm2, double* __restrict__ x,
+                                 int64_t n) {
+  const double s = nrm2[0] > 0 ? sqrt(nrm2[0]) : 1.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += s * (double)d[e];
+}
+template <typename T>
+void launch_scale_to(const double* in, const double* norm2, T* out, int64_t n, cudaStream_t st) {
+  ++g_launches;
+  scale_to_kernel<T><<<grid_for(n), 256, 0, st>>>(in, norm2, out, n);
+}
+template <typename T>
+void launch_axpy_from(const T* d, const double* norm2, double* x, int64_t n, cudaStream_t st) {
+  ++g_launches;
+  axpy_from_kernel<T><<<grid_for(n), 256, 0, st>>>(d, norm2, x, n);
+}
+template void launch_scale_to<double>(const double*, const double*, double*, int64_t, cudaStream_t);
+template void launch_scale_to<float>(const double*, const double*, float*, int64_t, cudaStream_t);
+template void launch_axpy_from<double>(const double*, const double*, double*, int64_t, cudaStream_t);
+template void launch_axpy_from<float>(const float*, const double*, double*, int64_t, cudaStream_t);
+
+}  // namespace h2
