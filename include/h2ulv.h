@@ -82,7 +82,7 @@ typedef struct {
   double eps;          /* softening of the *_EPS kernels (e.g. 1e-3) */
   double ell;          /* Gaussian length scale */
   double diag_shift;   /* added to the diagonal as described above */
-  int32_t leaf_size;   /* >= 1: maximum points per leaf box */
+  int32_t leaf_size;   /* 1..1024: maximum points per leaf box */
   double eta;          /* >= 0 */
   double tol;          /* > 0 */
   int32_t max_rank;    /* >= 0 */
@@ -138,7 +138,8 @@ typedef struct {
  * IDs are computed on the host; kernel blocks are evaluated on the GPU.
  * On success *out owns the instance.  Errors: H2_ERR_INVALID_ARG (N < 1,
  * leaf_size < 1, eta < 0, tol <= 0, a non-finite coordinate, unknown
- * kernel), H2_ERR_OOM, H2_ERR_CUDA. */
+ * kernel), H2_ERR_OOM, H2_ERR_CUDA.  Every box dimension (leaf size, or twice
+ * the children's rank above the leaves) must stay <= 1024. */
 h2_status h2_build(h2_ctx** out, const h2_params* p, const double* points, int64_t N);
 
 /* Plan without a GPU: run the host part of h2_build (cluster tree, near/far
@@ -169,13 +170,22 @@ h2_status h2_import(h2_ctx** out, const h2_params* p, const h2_instance* inst);
  * H2_ERR_OOM, H2_ERR_CUDA. */
 h2_status h2_factor(h2_ctx* c, int32_t prec);
 
-/* Solve A_H2 x = b by iterative refinement: x_0 = 0; repeat
- * { r = b - A_H2 x (FP64 h2_matvec); x += ULV^-1 r (parallel substitution of
- * Eq. 24-31 and its mirror, in the factorization's precision) } until
- * ||r|| / ||b|| <= target or max_iters corrections.  b and x hold nrhs = 1
- * vector of N doubles (host or device).  relres_out and iters_out (host,
- * may be NULL) receive the final relative residual and the number of
- * corrections.  target <= 0 makes exactly max_iters corrections.
+/* Solve A_H2 x = b by refinement with the factorization as preconditioner;
+ * every residual r = b - A_H2 x is computed in FP64 (h2_matvec) and every
+ * preconditioner application M^-1 v is the parallel substitution of
+ * Eq. 24-31 and its mirror, in the factorization's precision.  Two schemes
+ * (h2_set_refinement):
+ *   plain iterative refinement: x_0 = 0; repeat x += M^-1 (b - A_H2 x);
+ *   FGMRES-based refinement (default): restarted, right-preconditioned
+ *     flexible GMRES in FP64; after every cycle x += Z y and the true
+ *     residual is recomputed.  It needs no more preconditioner applications
+ *     than plain refinement and converges when the factorization's dropped
+ *     fill-ins make plain refinement contract slowly.
+ * Stops when ||r|| / ||b|| <= target or after max_iters preconditioner
+ * applications.  b and x hold one vector of N doubles (host or device).
+ * relres_out and iters_out (host, may be NULL) receive the final relative
+ * residual and the number of preconditioner applications.  target <= 0 runs
+ * exactly max_iters applications.
  * Errors: H2_ERR_STATE (no factorization), H2_ERR_INVALID_ARG,
  * H2_ERR_NOT_CONVERGED (x still holds the last iterate), H2_ERR_CUDA. */
 h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target,
@@ -190,6 +200,11 @@ h2_status h2_ulv_apply(h2_ctx* c, const double* b, double* x);
  * every level, downward pass and the dense near blocks of the leaves.
  * N doubles each, host or device.  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
 h2_status h2_matvec(h2_ctx* c, const double* x, double* y);
+
+/* Choose the refinement scheme of h2_solve: method 0 = plain iterative
+ * refinement, 1 = FGMRES-based refinement with the given restart length
+ * (1..1000; default 1 with restart 30).  Errors: H2_ERR_INVALID_ARG. */
+h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart);
 
 /* Issue all later work on the given cudaStream_t (NULL: legacy default). */
 h2_status h2_set_stream(h2_ctx* c, void* stream);

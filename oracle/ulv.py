@@ -332,6 +332,60 @@ def refine(F, H, b, target=1e-10, max_iters=50, solver=solve_parallel):
     return x, hist
 
 
+def refine_gmres(F, H, b, target=1e-10, max_iters=100, restart=30, solver=solve_parallel):
+    """GMRES-based iterative refinement: restarted, right-preconditioned
+    flexible GMRES on A_H2 x = b with the ULV factorization as the
+    preconditioner (z_j = ULV^-1 v_j, w = A_H2 z_j), modified Gram-Schmidt
+    and Givens rotations; after each cycle x += Z y and the true residual
+    r = b - A_H2 x is recomputed in FP64.  max_iters counts preconditioner
+    applications.  Returns (x, relative residual after every cycle, total
+    preconditioner applications)."""
+    bn = np.linalg.norm(b)
+    x = np.zeros_like(b)
+    r = b.copy()
+    beta = bn
+    hist = [1.0]
+    its = 0
+    while its < max_iters and beta > target * bn:
+        m = min(restart, max_iters - its)
+        V = [r / beta]
+        Z = []
+        Hs = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        k = 0
+        for j in range(m):
+            Z.append(solver(F, H, V[j]))
+            w = matvec(H, Z[j])
+            for i in range(j + 1):
+                Hs[i, j] = w @ V[i]
+                w = w - Hs[i, j] * V[i]
+            Hs[j + 1, j] = np.linalg.norm(w)
+            V.append(w / Hs[j + 1, j] if Hs[j + 1, j] > 0 else w)
+            for i in range(j):  # previous rotations
+                t = cs[i] * Hs[i, j] + sn[i] * Hs[i + 1, j]
+                Hs[i + 1, j] = -sn[i] * Hs[i, j] + cs[i] * Hs[i + 1, j]
+                Hs[i, j] = t
+            d = np.hypot(Hs[j, j], Hs[j + 1, j])
+            cs[j], sn[j] = Hs[j, j] / d, Hs[j + 1, j] / d
+            Hs[j, j] = d
+            Hs[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k = j + 1
+            its += 1
+            if abs(g[j + 1]) <= target * bn:
+                break
+        y = sla.solve_triangular(Hs[:k, :k], g[:k])
+        for i in range(k):
+            x = x + y[i] * Z[i]
+        r = b - matvec(H, x)
+        beta = np.linalg.norm(r)
+        hist.append(float(beta / bn))
+    return x, hist, its
+
+
 # ----------------------------------------------------------------------------
 # Eq. 21 diagnostics: the size of the fill-ins the factorization drops
 # ----------------------------------------------------------------------------

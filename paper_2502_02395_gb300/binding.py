@@ -28,7 +28,7 @@ STATUS = {0: "H2_OK", -1: "H2_ERR_INVALID_ARG", -2: "H2_ERR_OOM", -3: "H2_ERR_SI
 
 # every symbol include/h2ulv.h declares
 EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_ulv_apply", "h2_matvec",
-            "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
+            "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
 
 
 class H2Error(RuntimeError):
@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
             "h2_solve": (i32, [vp, vp, vp, dbl, i32, vp, vp]),
             "h2_ulv_apply": (i32, [vp, vp, vp]),
             "h2_matvec": (i32, [vp, vp, vp]),
+            "h2_set_refinement": (i32, [vp, i32, i32]),
             "h2_set_stream": (i32, [vp, vp]),
             "h2_stats": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
             "h2_export": (i32, [vp, ctypes.c_char_p, i32, vp, ctypes.c_size_t, vp, vp]),
@@ -183,6 +184,11 @@ def h2_matvec(ctx, x, y):
     _check(lib().h2_matvec(ctx, _ptr(x), _ptr(y)), ctx)
 
 
+def h2_set_refinement(ctx, method: str | int = "gmres", restart: int = 30):
+    m = {"ir": 0, "gmres": 1}.get(method, method)
+    _check(lib().h2_set_refinement(ctx, int(m), int(restart)), ctx)
+
+
 def h2_set_stream(ctx, stream):
     handle = getattr(stream, "cuda_stream", stream)
     _check(lib().h2_set_stream(ctx, ctypes.c_void_p(int(handle) if handle else 0)), ctx)
@@ -252,6 +258,9 @@ class H2Solver:
 
     def set_stream(self, stream):
         h2_set_stream(self.ctx, stream)
+
+    def set_refinement(self, method="gmres", restart=30):
+        h2_set_refinement(self.ctx, method, restart)
 
     def stats(self) -> dict:
         return h2_stats(self.ctx)

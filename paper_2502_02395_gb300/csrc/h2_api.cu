@@ -44,7 +44,7 @@ bool is_device_ptr(const void* p) {
 h2_status check_params(const h2_params* p, std::string& err) {
   if (!p) { err = "params is NULL"; return H2_ERR_INVALID_ARG; }
   if (p->kernel < 0 || p->kernel > H2_K_POLY2_TEST) { err = "unknown kernel"; return H2_ERR_INVALID_ARG; }
-  if (p->leaf_size < 1) { err = "leaf_size < 1"; return H2_ERR_INVALID_ARG; }
+  if (p->leaf_size < 1 || p->leaf_size > 1024) { err = "leaf_size outside 1..1024"; return H2_ERR_INVALID_ARG; }
   if (!(p->eta >= 0.0)) { err = "eta < 0"; return H2_ERR_INVALID_ARG; }
   if (!(p->tol > 0.0)) { err = "tol <= 0"; return H2_ERR_INVALID_ARG; }
   if (p->max_rank < 0) { err = "max_rank < 0"; return H2_ERR_INVALID_ARG; }
@@ -80,6 +80,10 @@ h2_status setup_device(h2_ctx* c) {
     d.D = h.D;
     d.K = l ? h.K : 0;
     d.R = d.D - d.K;
+    if (d.D > 1024) {
+      c->err = "box dimension " + std::to_string(d.D) + " at level " + std::to_string(l) + " exceeds 1024";
+      return H2_ERR_INVALID_ARG;
+    }
     d.NP = (int64_t)h.near.size() / 2;
     d.FP = (int64_t)h.far.size() / 2;
     d.h_near_ptr.assign(d.nb + 1, 0);
@@ -206,6 +210,8 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     CKC(dalloc(c, &f.Shat, (size_t)std::max<int64_t>(d.FP, 1) * K * K));
     CKC(dalloc(c, &f.Z, nb * R * K));
     CKC(dalloc(c, &f.lu, nb * R * R));
+    if (std::is_same<T, double>::value) f.luT = reinterpret_cast<T*>(f.lu);
+    else CKC(dalloc(c, &f.luT, nb * R * R));
     CKC(dalloc(c, &f.Ainv, nb * R * R));
     CKC(dalloc(c, &f.piv, nb * R));
     if (std::is_same<T, double>::value) f.Sc = reinterpret_cast<T*>(d.S);
@@ -216,6 +222,8 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   const int D0 = c->lv[0].D;
   CKC(dalloc(c, &F.Wk, wk));
   CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
+  if (std::is_same<T, double>::value) F.root_luT = reinterpret_cast<T*>(F.root_lu);
+  else CKC(dalloc(c, &F.root_luT, (size_t)D0 * D0));
   CKC(dalloc(c, &F.root_inv, (size_t)D0 * D0));
   CKC(dalloc(c, &F.root_piv, D0));
   CKC(dalloc(c, &F.root_vec, D0));
@@ -272,7 +280,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
             T(0), d.NP, st);
     mark();
     // a3: FP64 LU of Ahat_ii^RR and its inverse
-    launch_lu_inverse<T>(d.nb, D, R, f.Ahat, d.diag_pair, f.lu, f.piv, f.Ainv, c->status, l, st);
+    launch_lu_inverse<T>(d.nb, D, R, f.Ahat, d.diag_pair, f.lu, f.luT, f.piv, f.Ainv, c->status, l, st);
     mark();
     // a4 + a5: Z = Ainv Ahat_ii^RS; Ahat_ii^SS -= Ahat_ii^SR Z
     if (R > 0 && K > 0) {
@@ -300,7 +308,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   // a7: root
   const int D0 = c->lv[0].D;
   const T* Aroot = (L == 0) ? Aleaf : F.lv[0].Ain;
-  launch_lu_inverse<T>(1, D0, D0, Aroot, nullptr, F.root_lu, F.root_piv, F.root_inv, c->status, 0, st);
+  launch_lu_inverse<T>(1, D0, D0, Aroot, nullptr, F.root_lu, F.root_luT, F.root_piv, F.root_inv, c->status, 0, st);
   mark();
   CKC(cudaGetLastError());
   CKC(cudaStreamSynchronize(st));
@@ -410,6 +418,98 @@ h2_status vec_out(h2_ctx* c, const double* tree, double* dst) {
   if (!dev) {
     CKC(cudaMemcpyAsync(dst, ddst, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CKC(cudaStreamSynchronize(c->stream));
+  }
+  return H2_OK;
+}
+
+// FGMRES-based iterative refinement (restarted, right preconditioned by the
+// ULV factorization; classical Gram-Schmidt applied twice; Givens rotations on
+// the host).  On entry x64 = 0 and r64 = b64.  its counts preconditioner
+// applications.
+h2_status gmres_refine(h2_ctx* c, double bnorm, double target, int max_iters, int& its, double& rel) {
+  cudaStream_t st = c->stream;
+  const DevLevel& lf = c->lv[c->L];
+  const int64_t n = (int64_t)lf.nb * lf.D;
+  const int m0 = std::max(1, c->restart);
+  if (c->gm_cap < m0) {
+    CKC(dalloc(c, &c->gm_V, (size_t)(m0 + 1) * n));
+    CKC(dalloc(c, &c->gm_Z, (size_t)m0 * n));
+    CKC(dalloc(c, &c->gm_h, 3 * (size_t)(m0 + 2)));
+    CKC(dalloc(c, &c->gm_part, (size_t)(m0 + 1) * 128));
+    c->gm_cap = m0;
+  }
+  double* V = c->gm_V;
+  double* Z = c->gm_Z;
+  double* h1 = c->gm_h;
+  double* h2 = c->gm_h + (m0 + 2);
+  double* yv = c->gm_h + 2 * (m0 + 2);
+  double* nrm = c->red + 600;
+  std::vector<double> Hm((size_t)(m0 + 1) * m0), cs(m0), sn(m0), g(m0 + 1), a1(m0 + 2), a2(m0 + 2), y(m0);
+  double beta = bnorm;
+  rel = 1.0;
+  while (its < max_iters && (target <= 0 || beta > target * bnorm)) {
+    const int m = std::min(m0, max_iters - its);
+    launch_norm2(c->r64, n, nrm, st);
+    launch_normalize(c->r64, nrm, V, n, st);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (int64_t)j * n;
+      double* zj = Z + (int64_t)j * n;
+      double* w = V + (int64_t)(j + 1) * n;
+      CKC(cudaMemsetAsync(zj, 0, n * sizeof(double), st));
+      ulv_apply_any(c, vj, zj);
+      matvec_impl(c, zj, w);
+      launch_multi_dot(V, n, j + 1, w, n, c->gm_part, h1, false, st);
+      launch_multi_axpy(V, n, j + 1, h1, -1.0, w, n, st);
+      launch_multi_dot(V, n, j + 1, w, n, c->gm_part, h2, false, st);
+      launch_multi_axpy(V, n, j + 1, h2, -1.0, w, n, st);
+      launch_norm2(w, n, nrm, st);
+      double nw2 = 0;
+      CKC(cudaMemcpyAsync(a1.data(), h1, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CKC(cudaMemcpyAsync(a2.data(), h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CKC(cudaMemcpyAsync(&nw2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+      launch_normalize(w, nrm, w, n, st);
+      CKC(cudaStreamSynchronize(st));
+      double* col = &Hm[(size_t)j * (m0 + 1)];
+      for (int i = 0; i <= j; ++i) col[i] = a1[i] + a2[i];
+      col[j + 1] = std::sqrt(nw2);
+      for (int i = 0; i < j; ++i) {
+        double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+      }
+      double d = std::hypot(col[j], col[j + 1]);
+      cs[j] = d > 0 ? col[j] / d : 1.0;
+      sn[j] = d > 0 ? col[j + 1] / d : 0.0;
+      col[j] = d;
+      col[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      k = j + 1;
+      if (!std::isfinite(g[j + 1])) break;
+      if (target > 0 && std::fabs(g[j + 1]) <= target * bnorm) break;
+      if (nw2 == 0.0) break;  // the Krylov space is invariant: exact solution
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int q = i + 1; q < k; ++q) t -= Hm[(size_t)q * (m0 + 1) + i] * y[q];
+      y[i] = t / Hm[(size_t)i * (m0 + 1) + i];
+    }
+    CKC(cudaMemcpyAsync(yv, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_multi_axpy(Z, n, k, yv, 1.0, c->x64, n, st);
+    matvec_impl(c, c->x64, c->y64);
+    launch_residual(c->b64, c->y64, c->r64, n, st);
+    launch_norm2(c->r64, n, nrm, st);
+    double rn2 = 0;
+    CKC(cudaMemcpyAsync(&rn2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    beta = std::sqrt(rn2);
+    rel = beta / bnorm;
+    c->times.history.push_back(rel);
+    if (!std::isfinite(rel)) break;
   }
   return H2_OK;
 }
@@ -604,17 +704,23 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   const double bnorm = std::sqrt(bn2);
   double rel = bnorm > 0 ? 1.0 : 0.0;
   int it = 0;
-  while (it < max_iters && (target <= 0 || rel > target) && bnorm > 0) {
-    ulv_apply_any(c, c->r64, c->x64);
-    matvec_impl(c, c->x64, c->y64);
-    launch_residual(c->b64, c->y64, c->r64, nslot, st);
-    launch_norm2(c->r64, nslot, c->red + 600, st);
-    double rn2 = 0;
-    CKC(cudaMemcpyAsync(&rn2, c->red + 600, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CKC(cudaStreamSynchronize(st));
-    rel = std::sqrt(rn2) / bnorm;
-    ++it;
-    if (!std::isfinite(rel)) break;
+  c->times.history.clear();
+  if (bnorm > 0 && c->refine_method == 1) {
+    CKS(gmres_refine(c, bnorm, target, max_iters, it, rel));
+  } else {
+    while (it < max_iters && (target <= 0 || rel > target) && bnorm > 0) {
+      ulv_apply_any(c, c->r64, c->x64);
+      matvec_impl(c, c->x64, c->y64);
+      launch_residual(c->b64, c->y64, c->r64, nslot, st);
+      launch_norm2(c->r64, nslot, c->red + 600, st);
+      double rn2 = 0;
+      CKC(cudaMemcpyAsync(&rn2, c->red + 600, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CKC(cudaStreamSynchronize(st));
+      rel = std::sqrt(rn2) / bnorm;
+      c->times.history.push_back(rel);
+      ++it;
+      if (!std::isfinite(rel)) break;
+    }
   }
   CKC(cudaGetLastError());
   CKS(vec_out(c, c->x64, x));
@@ -633,6 +739,13 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
     c->err = "refinement stopped at relative residual " + std::to_string(rel);
     return H2_ERR_NOT_CONVERGED;
   }
+  return H2_OK;
+}
+
+h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart) {
+  if (!c || method < 0 || method > 1 || restart < 1 || restart > 1000) return H2_ERR_INVALID_ARG;
+  c->refine_method = method;
+  c->restart = restart;
   return H2_OK;
 }
 
@@ -671,7 +784,10 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     << ",\"a45_schur\":" << t.a5_schur << ",\"a2c_coupling\":" << t.a2c_coupling << ",\"a6_merge\":" << t.a6_merge
     << ",\"a7_root\":" << t.a7_root << ",\"factor\":" << t.total_factor << ",\"solve\":" << t.solve_total
     << "},\"iters\":" << t.iters << ",\"relres\":" << t.relres
-    << ",\"kernel_launches\":" << g_launches.load() << "}";
+    << ",\"kernel_launches\":" << g_launches.load() << ",\"refine_method\":" << c->refine_method
+    << ",\"restart\":" << c->restart << ",\"history\":[";
+  for (size_t k = 0; k < t.history.size(); ++k) o << (k ? "," : "") << t.history[k];
+  o << "]}";
   std::string s = o.str();
   if (s.size() + 1 > cap) return H2_ERR_INVALID_ARG;
   std::memcpy(json, s.c_str(), s.size() + 1);

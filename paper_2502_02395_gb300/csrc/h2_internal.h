@@ -125,6 +125,7 @@ struct FacLevel {
   T* Sc = nullptr;     // FP * K * K   couplings G(SK_i, SK_j) in T
   T* Z = nullptr;      // nb * R * K   (Ahat_ii^RR)^-1 Ahat_ii^RS
   double* lu = nullptr;    // nb * R * R  LU of Ahat_ii^RR, column-major, FP64
+  T* luT = nullptr;        // nb * R * R  the same factors in T (aliases lu when T is double)
   T* Ainv = nullptr;       // nb * R * R  (Ahat_ii^RR)^-1, row-major
   int32_t* piv = nullptr;  // nb * R (LAPACK-style row interchanges)
   // substitution vectors
@@ -136,6 +137,7 @@ struct Factor {
   bool ready = false;
   std::vector<FacLevel<T>> lv;
   double* root_lu = nullptr;  // D0 * D0 column-major
+  T* root_luT = nullptr;      // the same in T
   T* root_inv = nullptr;      // D0 * D0 row-major
   int32_t* root_piv = nullptr;
   T* root_vec = nullptr;      // D0
@@ -149,6 +151,7 @@ struct PhaseTimes {
   double solve_total = 0, subst = 0, matvec = 0;
   int iters = 0;
   double relres = 0;
+  std::vector<double> history;  // relative residual after every correction (IR) or cycle (GMRES)
 };
 
 }  // namespace h2
@@ -174,6 +177,13 @@ struct h2_ctx {
   double* red = nullptr;         // reduction scratch
   int32_t* status = nullptr;     // device error word(s)
   int prec = -1;                 // precision of the current factorization
+  int refine_method = 1;         // 0: plain iterative refinement, 1: FGMRES-based refinement
+  int restart = 30;              // FGMRES restart length
+  double* gm_V = nullptr;        // (restart + 1) * nslot Krylov basis
+  double* gm_Z = nullptr;        // restart * nslot preconditioned directions
+  double* gm_h = nullptr;        // 3 * (restart + 2) coefficients
+  double* gm_part = nullptr;     // (restart + 1) * 128 dot-product partials
+  int gm_cap = 0;                // restart the buffers were sized for
   h2::Factor<double> f64;
   h2::Factor<float> f32;
   h2::PhaseTimes times;

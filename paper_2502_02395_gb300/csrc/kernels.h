@@ -25,8 +25,8 @@ void launch_orth_input(int nb, int D, int K, int Kc, const double* X, const T* T
 template <typename T>
 void launch_qr_complement(int nb, int D, int K, T* Xo, T* U, T* Tm, cudaStream_t st);
 template <typename T>
-void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, int32_t* piv,
-                       T* Ainv, int32_t* status, int level, cudaStream_t st);
+void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
+                       int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st);
 template <typename T>
 void launch_merge(int D, int K, int64_t NP, const T* Ahat, const int32_t* ni, const int32_t* nj,
                   const int32_t* ndst, int64_t FP, const T* Shat, const int32_t* fi, const int32_t* fj,
@@ -72,5 +72,12 @@ template <typename T>
 void launch_scale_to(const double* in, const double* norm2, T* out, int64_t n, cudaStream_t st);
 template <typename T>
 void launch_axpy_from(const T* d, const double* norm2, double* x, int64_t n, cudaStream_t st);
+// GMRES: out[v] (+)= V_v . w for v < nv (part: nv * 128 scratch); w += sign sum_v coef[v] V_v;
+// w = src / sqrt(nrm2[0])
+void launch_multi_dot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* part, double* out,
+                      bool accumulate, cudaStream_t st);
+void launch_multi_axpy(const double* V, int64_t ldv, int nv, const double* coef, double sign, double* w, int64_t n,
+                       cudaStream_t st);
+void launch_normalize(const double* src, const double* nrm2, double* w, int64_t n, cudaStream_t st);
 
 }  // namespace h2

@@ -315,38 +315,38 @@ template void launch_qr_complement<float>(int, int, int, float*, float*, float*,
 
 // ------------------------------------------------------------------------
 // a3: FP64 partial-pivot LU of Ahat_ii^RR (rows/cols 0..R of a D x D
-// row-major block) and the inverse (Ahat_ii^RR)^-1 (row-major R x R, in T).
+// row-major block), LAPACK getf2 conventions (the first largest |pivot|;
+// whole-row interchanges).
 //   lu   column-major R x R FP64 (L unit lower, U upper), piv LAPACK-style
+//   luT  the same factors in T (skipped when T is double)
 //   M    working copy: shared memory (ld = R + 1) when it fits, else lu
-// A zero pivot records (level, box) in status[0..1] and leaves the rest of
-// that box's factorization undefined.
+// A zero pivot records (level, box) in status[0..1]; the rest of that box's
+// factorization is then undefined.
 // ------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
-lu_inverse_kernel(int D, int R, const T* __restrict__ Ablk, const int32_t* __restrict__ diag_idx,
-                  double* __restrict__ lu, int32_t* __restrict__ piv, T* __restrict__ Ainv,
-                  int32_t* __restrict__ status, int level, int use_smem) {
+lu_factor_kernel(int D, int R, const T* __restrict__ Ablk, const int32_t* __restrict__ diag_idx,
+                 double* __restrict__ lu, T* __restrict__ luT, int32_t* __restrict__ piv,
+                 int32_t* __restrict__ status, int level, int use_smem) {
   extern __shared__ double smd[];
   __shared__ int s_p;
-  __shared__ int s_bad;
-  const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  const T* A = Ablk + (int64_t)(diag_idx ? diag_idx[box] : box) * D * D;
-  double* G = lu + (int64_t)box * R * R;
+  __shared__ double s_inv;
+  const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
+  double* G = lu + (size_t)box * R * R;
   double* M = use_smem ? smd : G;
   const int ld = use_smem ? R + 1 : R;
-  int32_t* pv = piv + (int64_t)box * R;
-  if (tid == 0) s_bad = 0;
-  for (int e = tid; e < R * R; e += blockDim.x) {
-    int r = e / R, c = e - r * R;
-    M[(int64_t)c * ld + r] = (double)A[(int64_t)r * D + c];
-  }
+  int32_t* pv = piv + (size_t)box * R;
+  for (int r = warp; r < R; r += 8)
+    for (int c = lane; c < R; c += 32) M[c * ld + r] = (double)A[(size_t)r * D + c];
   __syncthreads();
+  int bad = 0;
   for (int k = 0; k < R; ++k) {
     if (warp == 0) {
       double best = -1.0;
       int bi = k;
       for (int r = k + lane; r < R; r += 32) {
-        double a = fabs(M[(int64_t)k * ld + r]);
+        double a = fabs(M[k * ld + r]);
         if (a > best) { best = a; bi = r; }
       }
       for (int o = 16; o; o >>= 1) {
@@ -354,115 +354,128 @@ lu_inverse_kernel(int D, int R, const T* __restrict__ Ablk, const int32_t* __res
         int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
-      if (lane == 0) { s_p = bi; pv[k] = bi; }
+      if (lane == 0) {
+        s_p = bi;
+        pv[k] = bi;
+        double d = M[k * ld + bi];
+        s_inv = d != 0.0 ? 1.0 / d : 0.0;
+      }
     }
     __syncthreads();
     const int p = s_p;
-    if (p != k)
-      for (int c = tid; c < R; c += blockDim.x) {
-        double t = M[(int64_t)c * ld + k];
-        M[(int64_t)c * ld + k] = M[(int64_t)c * ld + p];
-        M[(int64_t)c * ld + p] = t;
-      }
-    __syncthreads();
-    const double d = M[(int64_t)k * ld + k];
-    if (d == 0.0) {
-      if (tid == 0) {
-        s_bad = 1;
-        if (atomicCAS(status, 0, level + 1) == 0) status[1] = box;
-      }
+    const double inv = s_inv;
+    if (inv == 0.0) {
+      bad = 1;
       break;
     }
-    const double inv = 1.0 / d;
-    for (int r = k + 1 + tid; r < R; r += blockDim.x) M[(int64_t)k * ld + r] *= inv;
-    __syncthreads();
-    for (int c = k + 1 + warp; c < R; c += nw) {
-      const double f = M[(int64_t)c * ld + k];
-      if (f != 0.0)
-        for (int r = k + 1 + lane; r < R; r += 32) M[(int64_t)c * ld + r] -= M[(int64_t)k * ld + r] * f;
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-  if (s_bad) return;
-  if (use_smem)
-    for (int e = tid; e < R * R; e += blockDim.x) {
-      int c = e / R, r = e - c * R;
-      G[e] = M[(int64_t)c * ld + r];
-    }
-  // inverse Y = (P L U)^-1 = U^-1 L^-1 P^T, built by sweeps over all
-  // columns at once: Y = P^T I, then the unit-lower forward sweep, then the
-  // upper backward sweep (row k is final once step k starts; the division by
-  // U(k,k) is applied to the whole row at the end).  Y is row-major R x R,
-  // in shared memory after M when it fits, else in the output buffer.
-  T* Yout = Ainv + (int64_t)box * R * R;
-  T* Y = Yout;
-  int ldy = R;
-  if (use_smem == 2) {
-    Y = reinterpret_cast<T*>(smd + (size_t)R * (R + 1));
-    ldy = R;
-  }
-  __syncthreads();
-  for (int e = tid; e < R * R; e += blockDim.x) {
-    int r = e / R, b = e - r * R;
-    Y[(int64_t)r * ldy + b] = (r == b) ? T(1) : T(0);
-  }
-  __syncthreads();
-  for (int k = 0; k < R; ++k) {
-    const int p = pv[k];
     if (p != k)
-      for (int b = tid; b < R; b += blockDim.x) {
-        T t = Y[(int64_t)k * ldy + b];
-        Y[(int64_t)k * ldy + b] = Y[(int64_t)p * ldy + b];
-        Y[(int64_t)p * ldy + b] = t;
+      for (int c = tid; c < R; c += 256) {
+        double t = M[c * ld + k];
+        M[c * ld + k] = M[c * ld + p];
+        M[c * ld + p] = t;
       }
     __syncthreads();
-  }
-  for (int k = 0; k < R - 1; ++k) {
-    const int n = (R - 1 - k) * R;
-    for (int e = tid; e < n; e += blockDim.x) {
-      int r = k + 1 + e / R, b = e % R;
-      const double l = M[(int64_t)k * ld + r];
-      if (l != 0.0) Y[(int64_t)r * ldy + b] = (T)((double)Y[(int64_t)r * ldy + b] - l * (double)Y[(int64_t)k * ldy + b]);
+    for (int r = k + 1 + tid; r < R; r += 256) M[k * ld + r] *= inv;
+    __syncthreads();
+    for (int c = k + 1 + warp; c < R; c += 8) {
+      const double f = M[c * ld + k];
+      if (f != 0.0)
+        for (int r = k + 1 + lane; r < R; r += 32) M[c * ld + r] = fma(-M[k * ld + r], f, M[c * ld + r]);
     }
     __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0 && atomicCAS(status, 0, level + 1) == 0) status[1] = box;
+    return;
+  }
+  T* Gt = luT + (size_t)box * R * R;
+  for (int c = warp; c < R; c += 8)
+    for (int r = lane; r < R; r += 32) {
+      double v = M[c * ld + r];
+      if (use_smem) G[c * R + r] = v;
+      if ((void*)Gt != (void*)G) Gt[c * R + r] = (T)v;
+    }
+}
+
+// ------------------------------------------------------------------------
+// a3 (cont.): Ainv = (P L U)^-1 = U^-1 L^-1 P^T in T, from the factors luT.
+// Y starts as P^T (row r = e_perm[r]), then the unit-lower forward sweep and
+// the upper backward sweep over all columns at once (row k is final when
+// step k starts; the division by U(k,k) is applied to every row at the end).
+// mode 2: factors and Y in shared memory; 1: factors only; 0: neither.
+// ------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+lu_inverse_kernel(int R, const T* __restrict__ luT, const int32_t* __restrict__ piv, T* __restrict__ Ainv, int mode) {
+  extern __shared__ unsigned char sm_raw[];
+  __shared__ int s_perm[1024];
+  const int box = blockIdx.x, tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const T* src = luT + (size_t)box * R * R;
+  const int ld = mode ? R + 1 : R;
+  T* F = mode ? reinterpret_cast<T*>(sm_raw) : const_cast<T*>(src);
+  T* Yg = Ainv + (size_t)box * R * R;
+  T* Y = (mode == 2) ? F + R * (R + 1) : Yg;
+  if (mode)
+    for (int c = ty; c < R; c += 8)
+      for (int r = tx; r < R; r += 32) F[c * ld + r] = src[c * R + r];
+  if (tid == 0) {
+    for (int r = 0; r < R; ++r) s_perm[r] = r;
+    for (int k = 0; k < R; ++k) {
+      int p = piv[(size_t)box * R + k];
+      int t = s_perm[k];
+      s_perm[k] = s_perm[p];
+      s_perm[p] = t;
+    }
+  }
+  __syncthreads();
+  for (int r = ty; r < R; r += 8)
+    for (int b = tx; b < R; b += 32) Y[r * R + b] = (b == s_perm[r]) ? T(1) : T(0);
+  for (int k = 0; k < R - 1; ++k) {
+    __syncthreads();
+    for (int r = k + 1 + ty; r < R; r += 8) {
+      const T l = F[k * ld + r];
+      if (l != T(0))
+        for (int b = tx; b < R; b += 32) Y[r * R + b] = fma(-l, Y[k * R + b], Y[r * R + b]);
+    }
   }
   for (int k = R - 1; k > 0; --k) {
-    const double dk = M[(int64_t)k * ld + k];
-    const int n = k * R;
-    for (int e = tid; e < n; e += blockDim.x) {
-      int r = e / R, b = e - r * R;
-      const double u = M[(int64_t)k * ld + r];
-      if (u != 0.0)
-        Y[(int64_t)r * ldy + b] = (T)((double)Y[(int64_t)r * ldy + b] - u * ((double)Y[(int64_t)k * ldy + b] / dk));
-    }
     __syncthreads();
+    const T dk = T(1) / F[k * ld + k];
+    for (int r = ty; r < k; r += 8) {
+      const T u = F[k * ld + r] * dk;
+      if (u != T(0))
+        for (int b = tx; b < R; b += 32) Y[r * R + b] = fma(-u, Y[k * R + b], Y[r * R + b]);
+    }
   }
-  for (int e = tid; e < R * R; e += blockDim.x) {
-    int r = e / R, b = e - r * R;
-    Yout[e] = (T)((double)Y[(int64_t)r * ldy + b] / M[(int64_t)r * ld + r]);
+  __syncthreads();
+  for (int r = ty; r < R; r += 8) {
+    const T dr = T(1) / F[r * ld + r];
+    for (int b = tx; b < R; b += 32) Yg[r * R + b] = Y[r * R + b] * dr;
   }
 }
 
 template <typename T>
-void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, int32_t* piv,
-                       T* Ainv, int32_t* status, int level, cudaStream_t st) {
+void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
+                       int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st) {
   if (nb == 0 || R == 0) return;
-  // use_smem: 0 = everything in global memory, 1 = LU in shared memory,
-  // 2 = LU and the inverse's working matrix in shared memory
-  size_t sm1 = sizeof(double) * (size_t)R * (R + 1);
-  size_t sm2 = sm1 + sizeof(T) * (size_t)R * R;
   const size_t cap = 220 * 1024;
-  int use_smem = sm2 <= cap ? 2 : (sm1 <= cap ? 1 : 0);
-  size_t sm = use_smem == 2 ? sm2 : (use_smem == 1 ? sm1 : 0);
+  size_t sm1 = sizeof(double) * (size_t)R * (R + 1);
+  int use = sm1 <= cap;
+  if (use) cudaFuncSetAttribute(lu_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  ++g_launches;
+  lu_factor_kernel<T><<<nb, 256, use ? sm1 : 0, st>>>(D, R, Ablk, diag_idx, lu, luT, piv, status, level, use);
+  if (R > 1024) return;  // the permutation table holds 1024 rows; larger blocks are rejected by the caller
+  size_t f = sizeof(T) * (size_t)R * (R + 1), y = sizeof(T) * (size_t)R * R;
+  int mode = (f + y <= cap) ? 2 : (f <= cap ? 1 : 0);
+  size_t sm = mode == 2 ? f + y : (mode == 1 ? f : 0);
   if (sm) cudaFuncSetAttribute(lu_inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ++g_launches;
-  lu_inverse_kernel<T><<<nb, 256, sm, st>>>(D, R, Ablk, diag_idx, lu, piv, Ainv, status, level, use_smem);
+  lu_inverse_kernel<T><<<nb, 256, sm, st>>>(R, luT, piv, Ainv, mode);
 }
-template void launch_lu_inverse<double>(int, int, int, const double*, const int32_t*, double*, int32_t*, double*,
-                                        int32_t*, int, cudaStream_t);
-template void launch_lu_inverse<float>(int, int, int, const float*, const int32_t*, double*, int32_t*, float*,
-                                       int32_t*, int, cudaStream_t);
+template void launch_lu_inverse<double>(int, int, int, const double*, const int32_t*, double*, double*, int32_t*,
+                                        double*, int32_t*, int, cudaStream_t);
+template void launch_lu_inverse<float>(int, int, int, const float*, const int32_t*, double*, float*, int32_t*,
+                                       float*, int32_t*, int, cudaStream_t);
 
 // ------------------------------------------------------------------------
 // a6: merge.  Child pair q of level l (near: its SS part of Ahat; far: Shat)

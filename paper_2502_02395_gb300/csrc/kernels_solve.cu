@@ -454,6 +454,76 @@ void launch_axpy_from(const T* d, const double* norm2, double* x, int64_t n, cud
   ++g_launches;
   axpy_from_kernel<T><<<grid_for(n), 256, 0, st>>>(d, norm2, x, n);
 }
+// ---------------------------------------------------------- GMRES blocks ---
+// part[v * nblk + blk] = partial sums of V_v . w ; out[v] = sum over blocks
+__global__ void multi_dot_part_kernel(const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+                                      int64_t n, double* __restrict__ part) {
+  __shared__ double sb[8];
+  const int v = blockIdx.y;
+  const double* Vv = V + (int64_t)v * ldv;
+  double s = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s += Vv[e] * w[e];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < 8; ++k) t += sb[k];
+    part[(int64_t)v * gridDim.x + blockIdx.x] = t;
+  }
+}
+__global__ void multi_dot_final_kernel(const double* __restrict__ part, int nblk, double* __restrict__ out,
+                                       int accumulate) {
+  __shared__ double sb[8];
+  const int v = blockIdx.x;
+  double s = 0;
+  for (int k = threadIdx.x; k < nblk; k += blockDim.x) s += part[(int64_t)v * nblk + k];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < 8; ++k) t += sb[k];
+    out[v] = accumulate ? out[v] + t : t;
+  }
+}
+void launch_multi_dot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* part, double* out,
+                      bool accumulate, cudaStream_t st) {
+  if (nv == 0) return;
+  const int nblk = 128;
+  ++g_launches;
+  multi_dot_part_kernel<<<dim3(nblk, nv), 256, 0, st>>>(V, ldv, w, n, part);
+  ++g_launches;
+  multi_dot_final_kernel<<<nv, 256, 0, st>>>(part, nblk, out, accumulate ? 1 : 0);
+}
+// w += sign * sum_v coef[v] V_v
+__global__ void multi_axpy_kernel(const double* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ coef,
+                                  double sign, double* __restrict__ w, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int v = 0; v < nv; ++v) s += coef[v] * V[(int64_t)v * ldv + e];
+    w[e] += sign * s;
+  }
+}
+void launch_multi_axpy(const double* V, int64_t ldv, int nv, const double* coef, double sign, double* w, int64_t n,
+                       cudaStream_t st) {
+  if (nv == 0) return;
+  ++g_launches;
+  multi_axpy_kernel<<<grid_for(n), 256, 0, st>>>(V, ldv, nv, coef, sign, w, n);
+}
+// w = src / sqrt(nrm2[0])   (in place allowed)
+__global__ void normalize_kernel(const double* __restrict__ src, const double* __restrict__ nrm2,
+                                 double* __restrict__ w, int64_t n) {
+  const double s = nrm2[0] > 0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    w[e] = src[e] * s;
+}
+void launch_normalize(const double* src, const double* nrm2, double* w, int64_t n, cudaStream_t st) {
+  ++g_launches;
+  normalize_kernel<<<grid_for(n), 256, 0, st>>>(src, nrm2, w, n);
+}
+
 template void launch_scale_to<double>(const double*, const double*, double*, int64_t, cudaStream_t);
 template void launch_scale_to<float>(const double*, const double*, float*, int64_t, cudaStream_t);
 template void launch_axpy_from<double>(const double*, const double*, double*, int64_t, cudaStream_t);

@@ -123,17 +123,23 @@ def test_fp64_steps_match_oracle(B, name):
     S.close()
 
 
+@pytest.mark.parametrize("method", ["ir", "gmres"])
 @pytest.mark.parametrize("name", ["poly2_512", "cube2048_laplace", "sphere1000_ragged", "cube8192_yukawa"])
-def test_fp64_refined_solution_matches_oracle(B, name):
+def test_fp64_refined_solution_matches_oracle(B, name, method):
     from oracle import ulv
     H, F, flat, b = oracle_case(name)
     S = lib_case(B, name)
     S.factor("fp64")
-    x, r, its = S.solve(b, target=1e-12, max_iters=40)
+    S.set_refinement(method, 30)
+    x, r, its = S.solve(b, target=1e-12, max_iters=60)
     assert r <= 1e-12
-    x_ref, hist = ulv.refine(F, H, b, 1e-12, 40)
+    if method == "ir":
+        x_ref, hist = ulv.refine(F, H, b, 1e-12, 60)
+        n_ref = len(hist) - 1
+    else:
+        x_ref, hist, n_ref = ulv.refine_gmres(F, H, b, 1e-12, 60, 30)
     assert rel(x, x_ref) <= 1e-10
-    assert abs(its - (len(hist) - 1)) <= 1
+    assert abs(its - n_ref) <= 1
     S.close()
 
 
@@ -160,7 +166,7 @@ def test_mixed_refined_solution(B, name, prec):
     S.factor(prec)
     x, r, its = S.solve(b, target=1e-12, max_iters=60)
     assert r <= 1e-12
-    x_ref, _ = ulv.refine(F, H, b, 1e-12, 40)
+    x_ref, _, _ = ulv.refine_gmres(F, H, b, 1e-12, 60, 30)
     assert rel(x, x_ref) <= 1e-9
     st = S.stats()
     assert st["prec"] == {"fp16": 1, "bf16": 2}[prec]
@@ -177,8 +183,15 @@ def test_errors(B):
     with pytest.raises(B.H2Error) as e:
         S.solve(b, target=1e-15, max_iters=1)
     assert e.value.status == -4  # H2_ERR_NOT_CONVERGED
+    S.set_refinement("ir")
+    with pytest.raises(B.H2Error) as e:
+        S.solve(b, target=1e-15, max_iters=1)
+    assert e.value.status == -4  # H2_ERR_NOT_CONVERGED
     with pytest.raises(B.H2Error) as e:
         B.h2_factor(S.ctx, 7)
+    assert e.value.status == -1
+    with pytest.raises(B.H2Error) as e:
+        S.set_refinement(5)
     assert e.value.status == -1
     S.close()
 

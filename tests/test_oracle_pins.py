@@ -274,6 +274,26 @@ def test_refinement_reaches_target_and_dense_solution():
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= 100 * err_h2
 
 
+def test_gmres_refinement_matches_plain_refinement():
+    """FGMRES-based refinement reaches the same solution as plain refinement
+    with no more preconditioner applications; on the exact-rank kernel one
+    application suffices."""
+    wl = W.workload("cube2048_laplace")
+    P = wl.points()
+    H = construct(P, Kernel(wl.kernel), wl.leaf, wl.eta, wl.tol, 0, 512, 64)
+    F = ulv.factor(H)
+    b = wl.rhs()
+    x1, h1 = ulv.refine(F, H, b, 1e-11, 40)
+    x2, h2, its = ulv.refine_gmres(F, H, b, 1e-11, 40, 30)
+    assert h2[-1] <= 1e-11 and its <= len(h1) - 1
+    assert np.linalg.norm(x1 - x2) <= 1e-9 * np.linalg.norm(x1)
+    Hp = _poly2(512, 64)
+    Fp = ulv.factor(Hp)
+    bp = W.uniform_rhs(512, 3)
+    xp, hp, itp = ulv.refine_gmres(Fp, Hp, bp, 1e-11, 10, 5)
+    assert itp == 1 and hp[-1] <= 1e-11
+
+
 def test_residual_tracks_tolerance():
     """With no rank cap and no sampling, the dense residual ||Ax - b|| / ||b||
     of the refined H^2 solution falls with the truncation tolerance and stays
