@@ -66,6 +66,26 @@ h2_status upload(h2_ctx* c, V** dst, const std::vector<V>& src) {
   return H2_OK;
 }
 
+// The leaf blocks scaled by a power of two into FP16 (bf16 = 0) or BF16
+// (bf16 = 1): the operand of the leaf-level projection on the tensor cores.
+// Part of the H^2 instance; built once per context and type.
+h2_status make_leaf_lowp(h2_ctx* c, int bf16) {
+  if (c->A16[bf16]) return H2_OK;
+  const DevLevel& lf = c->lv[c->L];
+  const int64_t n = (int64_t)lf.NP * lf.D * lf.D;
+  unsigned int* amax = nullptr;
+  CKC(dalloc(c, &amax, 1));
+  CKC(dalloc(c, &c->A16_scale[bf16], 2));
+  CKC(dalloc(c, reinterpret_cast<uint16_t**>(&c->A16[bf16]), n));
+  CKC(cudaMemsetAsync(amax, 0, sizeof(unsigned int), c->stream));
+  launch_amax_blocks<double>(c->A64, lf.NP, (int64_t)lf.D * lf.D, lf.D, lf.D, lf.D, amax, c->stream);
+  launch_pow2_scale(amax, 128.0f, c->A16_scale[bf16], c->stream);
+  launch_to_lowp<double>(bf16, c->A64, c->A16[bf16], n, c->A16_scale[bf16], c->stream);
+  CKC(cudaGetLastError());
+  CKC(cudaStreamSynchronize(c->stream));
+  return H2_OK;
+}
+
 h2_status setup_device(h2_ctx* c) {
   HostH2& H = c->host;
   c->L = H.L;
@@ -178,6 +198,8 @@ h2_status setup_device(h2_ctx* c) {
   CKC(dalloc(c, &c->status, 4));
   CKC(cudaMemset(c->status, 0, 4 * sizeof(int32_t)));
   CKC(cudaDeviceSynchronize());
+  // the FP16 copy of the leaf blocks used by mixed-precision factorizations
+  if (L >= 1 && gemm_tc_supported(lf.D, lf.D, lf.D, lf.D, lf.D, lf.D)) CKS(make_leaf_lowp(c, 0));
   return H2_OK;
 }
 
@@ -193,16 +215,25 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   if (!F.lv.empty()) return H2_OK;
   const int L = c->L;
   F.lv.assign(L + 1, FacLevel<T>());
-  size_t wk = 0;
+  size_t wk = 0, wk16 = 0;
   for (int l = 0; l <= L; ++l) {
     const DevLevel& d = c->lv[l];
     FacLevel<T>& f = F.lv[l];
     const size_t nb = d.nb, D = d.D, K = d.K, R = d.R;
     wk = std::max(wk, (size_t)d.NP * D * D);
     wk = std::max(wk, (size_t)d.FP * K * K);
-    bool leaf64 = (l == L) && std::is_same<T, double>::value;
-    if (!leaf64) CKC(dalloc(c, &f.Ain, (size_t)d.NP * D * D));
+    const bool mixed = !std::is_same<T, double>::value;
+    f.tc = mixed && l >= 1 && gemm_tc_supported(d.D, d.D, d.D, d.D, d.D, d.D);
+    bool leaf64 = (l == L) && !mixed;
+    if (!leaf64 && !(f.tc && l == L)) {
+      if (f.tc) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&f.Ain16), (size_t)d.NP * D * D));
+      else CKC(dalloc(c, &f.Ain, (size_t)d.NP * D * D));
+    }
     if (l == 0) continue;
+    if (f.tc) {
+      CKC(dalloc(c, reinterpret_cast<uint16_t**>(&f.U16), nb * D * D));
+      wk16 = std::max(wk16, (size_t)d.NP * D * D);
+    }
     CKC(dalloc(c, &f.U, nb * D * D));
     CKC(dalloc(c, &f.Tm, nb * K * K));
     CKC(dalloc(c, &f.Xo, nb * D * K));
@@ -221,6 +252,9 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   }
   const int D0 = c->lv[0].D;
   CKC(dalloc(c, &F.Wk, wk));
+  if (wk16) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&F.W16), wk16));
+  CKC(dalloc(c, &F.scales, 2 * (size_t)(L + 1)));
+  CKC(dalloc(c, &F.amax, (size_t)(L + 1)));
   CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
   if (std::is_same<T, double>::value) F.root_luT = reinterpret_cast<T*>(F.root_lu);
   else CKC(dalloc(c, &F.root_luT, (size_t)D0 * D0));
@@ -254,10 +288,14 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   };
   // phase boundaries per level: [start, a1, a2, a3, a45, a2c, a6]
   mark();
+  const int bf16 = (prec == H2_PREC_BF16) ? 1 : 0;
+  const bool mixed = !std::is_same<T, double>::value;
+  if (mixed && L >= 1 && F.lv[L].tc) CKS(make_leaf_lowp(c, bf16));
+  mark();
   const T* Aleaf = nullptr;
-  if (std::is_same<T, double>::value) {
+  if (!mixed) {
     Aleaf = reinterpret_cast<const T*>(c->A64);
-  } else {
+  } else if (L == 0 || !F.lv[L].tc) {
     launch_convert<double, T>(c->A64, F.lv[L].Ain, (int64_t)c->lv[L].NP * c->lv[L].D * c->lv[L].D, st);
     Aleaf = F.lv[L].Ain;
   }
@@ -273,11 +311,26 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     launch_qr_complement<T>(d.nb, D, K, f.Xo, f.U, f.Tm, st);
     mark();
     // a2: Ahat_ij = U_i^T A_ij U_j
-    const T* Ain = (l == L) ? Aleaf : f.Ain;
-    gemm<T>(prec, D, D, D, Ain, DD, nullptr, D, false, f.U, DD, d.near_j, D, true, F.Wk, DD, nullptr, D, T(1), T(0),
-            d.NP, st);
-    gemm<T>(prec, D, D, D, f.U, DD, d.near_i, D, false, F.Wk, DD, nullptr, D, false, f.Ahat, DD, nullptr, D, T(1),
-            T(0), d.NP, st);
+    if (f.tc) {
+      // tensor cores: W^T = (s A_ij) U_j in 16 bits, then Ahat_ij = U_i^T W / s in FP32
+      const void* A16 = (l == L) ? c->A16[bf16] : f.Ain16;
+      const float* sc = (l == L) ? c->A16_scale[bf16] : F.scales + 2 * l;
+      launch_to_lowp<T>(bf16, f.U, f.U16, (int64_t)d.nb * DD, nullptr, st);
+      bool ok = gemm_tc(bf16, D, D, D, A16, d.NP, D, D, nullptr, f.U16, d.nb, D, D, d.near_j, F.W16, DD, nullptr, D,
+                        1, bf16, 1.0f, nullptr, d.NP, c->status + 2, st) &&
+                gemm_tc(bf16, D, D, D, f.U16, d.nb, D, D, d.near_i, F.W16, d.NP, D, D, nullptr, f.Ahat, DD, nullptr, D,
+                        0, 0, 1.0f, sc + 1, d.NP, c->status + 2, st);
+      if (!ok) {
+        c->err = "tensor-core GEMM setup failed at level " + std::to_string(l);
+        return H2_ERR_CUDA;
+      }
+    } else {
+      const T* Ain = (l == L) ? Aleaf : f.Ain;
+      gemm<T>(prec, D, D, D, Ain, DD, nullptr, D, false, f.U, DD, d.near_j, D, true, F.Wk, DD, nullptr, D, T(1),
+              T(0), d.NP, st);
+      gemm<T>(prec, D, D, D, f.U, DD, d.near_i, D, false, F.Wk, DD, nullptr, D, false, f.Ahat, DD, nullptr, D, T(1),
+              T(0), d.NP, st);
+    }
     mark();
     // a3: FP64 LU of Ahat_ii^RR and its inverse
     launch_lu_inverse<T>(d.nb, D, R, f.Ahat, d.diag_pair, f.lu, f.luT, f.piv, f.Ainv, c->status, l, st);
@@ -301,8 +354,24 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     }
     mark();
     // a6: merge into the parent level's near blocks
-    launch_merge<T>(D, K, d.NP, f.Ahat, d.near_i, d.near_j, d.near_dst, d.FP, f.Shat, d.far_i, d.far_j, d.far_dst,
-                    F.lv[l - 1].Ain, st);
+    FacLevel<T>& pf = F.lv[l - 1];
+    if (mixed && pf.tc) {
+      // 16-bit parent blocks with a fresh power-of-two scale
+      unsigned int* am = F.amax + (l - 1);
+      CKC(cudaMemsetAsync(am, 0, sizeof(unsigned int), st));
+      if (std::is_same<T, float>::value) {
+        const float* Ah = reinterpret_cast<const float*>(f.Ahat);
+        const float* Sh = reinterpret_cast<const float*>(f.Shat);
+        launch_amax_blocks<float>(Ah + (int64_t)R * D + R, d.NP, DD, K, K, D, am, st);
+        launch_amax_blocks<float>(Sh, d.FP, (int64_t)K * K, K, K, K, am, st);
+        launch_pow2_scale(am, 128.0f, F.scales + 2 * (l - 1), st);
+        launch_merge_lowp(D, K, d.NP, Ah, d.near_i, d.near_j, d.near_dst, d.FP, Sh, d.far_i, d.far_j, d.far_dst,
+                          pf.Ain16, F.scales + 2 * (l - 1), bf16, st);
+      }
+    } else {
+      launch_merge<T>(D, K, d.NP, f.Ahat, d.near_i, d.near_j, d.near_dst, d.FP, f.Shat, d.far_i, d.far_j, d.far_dst,
+                      pf.Ain, st);
+    }
     mark();
   }
   // a7: root
@@ -320,8 +389,8 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     cudaEventElapsedTime(&ms, ev[a], ev[b]);
     return (double)ms * 1e-3;
   };
-  t.a2_proj += el(0, 1);  // leaf conversion counted with the projection
-  int k = 1;
+  t.a2_proj += el(1, 2);  // leaf conversion counted with the projection
+  int k = 2;
   for (int l = L; l >= 1; --l) {
     t.a1_qr += el(k, k + 1);
     t.a2_proj += el(k + 1, k + 2);
@@ -332,15 +401,21 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     k += 6;
   }
   t.a7_root = el(k, k + 1);
-  t.total_factor = el(0, k + 1);
+  t.total_factor = el(1, k + 1);
   for (auto e : ev) cudaEventDestroy(e);
   int32_t stw[4];
   CKC(cudaMemcpy(stw, c->status, sizeof(stw), cudaMemcpyDeviceToHost));
+  if (stw[2] != 0) {
+    c->err = "a bounded wait in the tensor-core GEMM expired";
+    return H2_ERR_TIMEOUT;
+  }
   if (stw[0] != 0) {
     c->err = "zero pivot in the LU of level " + std::to_string(stw[0] - 1) + " box " + std::to_string(stw[1]);
     return H2_ERR_SINGULAR;
   }
   F.ready = true;
+  c->used_tc = false;
+  for (int l = 1; l <= L; ++l) c->used_tc = c->used_tc || F.lv[l].tc;
   return H2_OK;
 }
 
@@ -785,7 +860,8 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     << ",\"a7_root\":" << t.a7_root << ",\"factor\":" << t.total_factor << ",\"solve\":" << t.solve_total
     << "},\"iters\":" << t.iters << ",\"relres\":" << t.relres
     << ",\"kernel_launches\":" << g_launches.load() << ",\"refine_method\":" << c->refine_method
-    << ",\"restart\":" << c->restart << ",\"history\":[";
+    << ",\"restart\":" << c->restart << ",\"tensor_cores\":" << (c->used_tc ? "true" : "false")
+    << ",\"history\":[";
   for (size_t k = 0; k < t.history.size(); ++k) o << (k ? "," : "") << t.history[k];
   o << "]}";
   std::string s = o.str();

@@ -130,6 +130,10 @@ struct FacLevel {
   int32_t* piv = nullptr;  // nb * R (LAPACK-style row interchanges)
   // substitution vectors
   T *vin = nullptr, *c = nullptr, *u = nullptr, *v = nullptr, *om = nullptr, *xs = nullptr;
+  // tensor-core path (mixed precision): 16-bit scaled input blocks and bases
+  bool tc = false;
+  void* Ain16 = nullptr;  // NP * D * D (scale in Factor::scales[2l], inverse at [2l+1])
+  void* U16 = nullptr;    // nb * D * D, column-major like U
 };
 
 template <typename T>
@@ -143,6 +147,10 @@ struct Factor {
   T* root_vec = nullptr;      // D0
   T* root_x = nullptr;        // D0
   T* Wk = nullptr;            // workspace: max NP * D * D
+  void* W16 = nullptr;        // 16-bit workspace: max NP * D * D (tensor-core path)
+  float* scales = nullptr;    // 2 (L + 1): per-level operand scale and its inverse
+  unsigned int* amax = nullptr;  // L + 1 max-abs accumulators
+  int bf16 = -1;              // operand type the 16-bit buffers hold
 };
 
 struct PhaseTimes {
@@ -169,6 +177,8 @@ struct h2_ctx {
   double* pts = nullptr;         // N * 3
   int64_t* slot_pt = nullptr;    // nbL * DL: original index of each padded leaf slot, -1 pad
   double* A64 = nullptr;         // NP_L * DL * DL leaf near blocks (FP64, for the matvec)
+  void* A16[2] = {nullptr, nullptr};     // the leaf blocks scaled into FP16 [0] / BF16 [1]
+  float* A16_scale[2] = {nullptr, nullptr};  // their scale and inverse scale (device)
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr, *y64 = nullptr, *t64 = nullptr;  // padded tree vectors
   double *io_a = nullptr, *io_b = nullptr;  // original-order staging vectors (N)
   double* xhat = nullptr;  // matvec upward/downward scratch (sum over levels nb*K)
@@ -177,6 +187,7 @@ struct h2_ctx {
   double* red = nullptr;         // reduction scratch
   int32_t* status = nullptr;     // device error word(s)
   int prec = -1;                 // precision of the current factorization
+  bool used_tc = false;          // the last factorization ran contractions on the tensor cores
   int refine_method = 1;         // 0: plain iterative refinement, 1: FGMRES-based refinement
   int restart = 30;              // FGMRES restart length
   double* gm_V = nullptr;        // (restart + 1) * nslot Krylov basis

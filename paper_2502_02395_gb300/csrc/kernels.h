@@ -32,15 +32,25 @@ void launch_merge(int D, int K, int64_t NP, const T* Ahat, const int32_t* ni, co
                   const int32_t* ndst, int64_t FP, const T* Shat, const int32_t* fi, const int32_t* fj,
                   const int32_t* fdst, T* Apar, cudaStream_t st);
 
-// kernels_tc.cu: tensor-core (tcgen05) batched GEMM, FP16/BF16 inputs, FP32
-// accumulation and output.  Operands as in gemm_simt; returns false when the
-// shape is not supported (the caller then uses gemm_simt).
+// kernels_tc.cu: tensor-core (tcgen05 + TMA) batched GEMM
+//   C_b = alpha * (*alpha_dev) * A_b B_b^T, A_b = matrix ia[b] (rowsA x K,
+//   K-major, 16-bit) of the nA-matrix array A, B_b likewise, FP32
+//   accumulation; out_mode 0: FP32 row-major C, 1: 16-bit C^T.
+// gemm_tc returns false (and launches nothing) for unsupported shapes.
 bool gemm_tc_supported(int M, int N, int K, int lda, int ldb, int ldc);
-void gemm_tc(int prec, int M, int N, int K, const void* A, int64_t sA, const int32_t* ia, int lda,
-             const void* B, int64_t sB, const int32_t* ib, int ldb, float* C, int64_t sC, const int32_t* ic,
-             int ldc, float alpha, float beta, int64_t batch, cudaStream_t st);
-void launch_to_lowp(int prec, const float* in, void* out, int64_t n, cudaStream_t st);
-void launch_to_lowp_d(int prec, const double* in, void* out, int64_t n, cudaStream_t st);
+bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int rowsA, int lda, const int32_t* ia,
+             const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
+             const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
+             int64_t batch, int32_t* err, cudaStream_t st);
+template <typename S>
+void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
+                        cudaStream_t st);
+void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale, cudaStream_t st);
+template <typename S>
+void launch_to_lowp(int bf16, const S* in, void* out, int64_t n, const float* scale, cudaStream_t st);
+void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_t* ni, const int32_t* nj,
+                       const int32_t* ndst, int64_t FP, const float* Shat, const int32_t* fi, const int32_t* fj,
+                       const int32_t* fdst, void* Apar, const float* scale, int bf16, cudaStream_t st);
 
 // kernels_solve.cu: substitution (Eq. 24-31 and its mirror), H^2 matvec,
 // refinement vector operations

@@ -1,15 +1,456 @@
-// Tensor-core batched GEMM (tcgen05) for the mixed-precision contractions.
+// Tensor-core batched GEMM for the mixed-precision contractions (sm_103a,
+// tcgen05 + TMA), and the FP16/BF16 operand preparation around it.
+//
+//   C_b (M x N) = alpha * A_b (M x K) * B_b (N x K)^T
+//
+// A and B are K-major (row-major with K contiguous) FP16 or BF16 matrices
+// inside larger 2-D arrays; batch b uses matrix ia[b] of A and ib[b] of B.
+// One CTA computes a 128 x N tile (N <= 256) of one batch entry:
+//   * warp 0 (one thread) streams 64-wide K slices of A and B into shared
+//     memory with TMA (128-byte swizzle), two stages, mbarrier handshakes;
+//   * warp 1 allocates the FP32 accumulator in tensor memory (N columns) and
+//     one thread issues tcgen05.mma (M = 128, N, K = 16 per instruction);
+//     tcgen05.commit releases each stage and finally signals the epilogue;
+//   * all four warps read the accumulator back (tcgen05.ld, one TMEM lane per
+//     output row) and store it as FP32 row-major, or as FP16/BF16 transposed
+//     (C^T, K-major for a following GEMM), scaled by alpha * (*alpha_dev).
+// Every wait is bounded (2 s of global time); on expiry the CTA records the
+// failure in err[0], drains its own copies in flight, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "h2_internal.h"
 #include "kernels.h"
 
 namespace h2 {
 
-bool gemm_tc_supported(int, int, int, int, int, int) { return false; }
+namespace {
 
-void gemm_tc(int, int, int, int, const void*, int64_t, const int32_t*, int, const void*, int64_t, const int32_t*, int,
-             float*, int64_t, const int32_t*, int, float, float, int64_t, cudaStream_t) {}
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;  // one 128-byte swizzle atom of 16-bit elements
+constexpr int TC_STAGES = 2;
+constexpr unsigned long long TC_TIMEOUT_NS = 2000000000ull;
 
-void launch_to_lowp(int, const float*, void*, int64_t, cudaStream_t) {}
-void launch_to_lowp_d(int, const double*, void*, int64_t, cudaStream_t) {}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Wait for the phase of the given parity; false after TC_TIMEOUT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255u) == 255u && global_ns() - t0 > TC_TIMEOUT_NS) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand, 128-byte swizzle: rows of 128 bytes, 8-row atoms 1024
+// bytes apart (stride byte offset), descriptor version 1, layout type 2.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;            // leading byte offset (16 B; unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1u << 46;            // descriptor version
+  d |= (uint64_t)2u << 61;            // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor of kind::f16: D = F32, A/B = F16 (0) or BF16 (1),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int ab_bf16, int M, int N) {
+  return (1u << 4) | ((uint32_t)ab_bf16 << 7) | ((uint32_t)ab_bf16 << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+struct TcArgs {
+  int M, N, K;
+  int rowsA, rowsB;  // rows per matrix inside the A / B tensors
+  const int32_t* ia;
+  const int32_t* ib;
+  void* C;
+  int64_t sC;
+  const int32_t* ic;
+  int ldc;
+  int out_mode;  // 0: FP32 row-major; 1: 16-bit transposed (C^T row-major, ld = ldc)
+  int out_bf16;  // 16-bit output type for out_mode 1
+  float alpha;
+  const float* alpha_dev;
+  int32_t* err;
+  int ab_bf16;
+  uint32_t tmem_cols;
+};
+
+__global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                      const __grid_constant__ CUtensorMap tmB, TcArgs p,
+                                                      int64_t batch) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int fail_sh;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // 1024-byte aligned stage buffers
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint8_t* base = smem_raw + pad;
+  const uint32_t a_bytes = TC_BM * TC_BK * 2;
+  const uint32_t b_bytes = (uint32_t)p.N * TC_BK * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const int kblocks = p.K / TC_BK;
+
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    fail_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t idesc = idesc_f16(p.ab_bf16, TC_BM, p.N);
+
+  uint32_t it_count = 0;  // tiles processed by this CTA (phase bookkeeping)
+  for (int64_t b = blockIdx.y; b < batch; b += gridDim.y, ++it_count) {
+    // (the A / B row coordinates are < 2^31: the caller checks nA * rowsA)
+    const int m0 = blockIdx.x * TC_BM;
+    const int rowA = (p.ia ? p.ia[b] : (int)b) * p.rowsA + m0;
+    const int rowB = (p.ib ? p.ib[b] : (int)b) * p.rowsB;
+    // stage s is used kblocks/2 (rounded) times per tile; global use index
+    const uint32_t use0 = it_count * (uint32_t)kblocks;
+    if (warp == 0 && lane == 0) {
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const uint32_t u = use0 + kb;
+        const int s = u % TC_STAGES;
+        if (u >= TC_STAGES) {
+          if (!mbar_wait(&empty_bar[s], ((u / TC_STAGES) - 1) & 1)) { fail_sh = 1; break; }
+        }
+        uint8_t* sa = base + s * stage_bytes;
+        mbar_expect_tx(&full_bar[s], stage_bytes);
+        tma_load_2d(sa, &tmA, &full_bar[s], kb * TC_BK, rowA);
+        tma_load_2d(sa + a_bytes, &tmB, &full_bar[s], kb * TC_BK, rowB);
+      }
+    } else if (warp == 1 && lane == 0) {
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const uint32_t u = use0 + kb;
+        const int s = u % TC_STAGES;
+        if (!mbar_wait(&full_bar[s], (u / TC_STAGES) & 1)) { fail_sh = 1; break; }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(base + s * stage_bytes);
+        const uint64_t da = smem_desc_sw128(sa);
+        const uint64_t db = smem_desc_sw128(sa + a_bytes);
+#pragma unroll
+        for (int k = 0; k < TC_BK / 16; ++k) {
+          // advance 16 elements (32 bytes) along K inside the swizzle atom
+          const uint64_t off = (uint64_t)((k * 32) >> 4);
+          const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(da + off), "l"(db + off), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&empty_bar[s]))
+                     : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&done_bar))
+                   : "memory");
+    }
+    // epilogue: every thread owns output row m0 + tid (TMEM lane tid)
+    __syncwarp();
+    bool ok = mbar_wait(&done_bar, it_count & 1);
+    if (!ok) fail_sh = 1;
+    tc_fence_after();
+    const float alpha = p.alpha * (p.alpha_dev ? *p.alpha_dev : 1.0f);
+    const int m = m0 + tid;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    char* Cb = reinterpret_cast<char*>(p.C);
+    const int64_t cbase = (int64_t)(p.ic ? p.ic[b] : (int)b) * p.sC;
+    for (int n0 = 0; n0 < p.N; n0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(lane_addr + (uint32_t)n0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (!ok || m >= p.M) continue;
+      if (p.out_mode == 0) {
+        float* out = reinterpret_cast<float*>(Cb) + cbase + (int64_t)m * p.ldc + n0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          float4 v = make_float4(__uint_as_float(r[j]) * alpha, __uint_as_float(r[j + 1]) * alpha,
+                                 __uint_as_float(r[j + 2]) * alpha, __uint_as_float(r[j + 3]) * alpha);
+          *reinterpret_cast<float4*>(out + j) = v;
+        }
+      } else if (p.out_bf16) {
+        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Cb) + cbase;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          out[(int64_t)(n0 + j) * p.ldc + m] = __float2bfloat16_rn(__uint_as_float(r[j]) * alpha);
+      } else {
+        __half* out = reinterpret_cast<__half*>(Cb) + cbase;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) out[(int64_t)(n0 + j) * p.ldc + m] = __float2half_rn(__uint_as_float(r[j]) * alpha);
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (fail_sh) break;
+  }
+  // drain: the producer's last loads must land before the CTA exits
+  if (fail_sh && tid == 0) {
+    atomicExch(p.err, 1);
+    for (int s = 0; s < TC_STAGES; ++s) mbar_wait(&full_bar[s], 0), mbar_wait(&full_bar[s], 1);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------
+// host side: tensor maps
+// ------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* tm, const void* base, int bf16, uint64_t rows, uint64_t cols, uint64_t ld,
+              uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                  const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool gemm_tc_supported(int M, int N, int K, int lda, int ldb, int ldc) {
+  (void)ldc;
+  if (M <= 0 || N <= 0 || K <= 0) return false;
+  if (M % TC_BM || K % TC_BK || N % 16 || N > 256) return false;
+  if (lda % 8 || ldb % 8) return false;  // 16-byte row strides for TMA
+  return encode_fn() != nullptr;
+}
+
+// A: nA matrices of rowsA x lda (16-bit) starting at A; B likewise.
+bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int rowsA, int lda, const int32_t* ia,
+             const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
+             const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
+             int64_t batch, int32_t* err, cudaStream_t st) {
+  if (batch == 0) return true;
+  if (!gemm_tc_supported(M, N, K, lda, ldb, ldc)) return false;
+  if ((uint64_t)nA * rowsA >= (1ull << 31) || (uint64_t)nB * rowsB >= (1ull << 31)) return false;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, ab_bf16, (uint64_t)nA * rowsA, (uint64_t)K, (uint64_t)lda, TC_BM)) return false;
+  if (!make_map(&tb, B, ab_bf16, (uint64_t)nB * rowsB, (uint64_t)K, (uint64_t)ldb, (uint32_t)N)) return false;
+  TcArgs p{};
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  p.rowsA = rowsA;
+  p.rowsB = rowsB;
+  p.ia = ia;
+  p.ib = ib;
+  p.C = C;
+  p.sC = sC;
+  p.ic = ic;
+  p.ldc = ldc;
+  p.out_mode = out_mode;
+  p.out_bf16 = out_bf16;
+  p.alpha = alpha;
+  p.alpha_dev = alpha_dev;
+  p.err = err;
+  p.ab_bf16 = ab_bf16;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)N) cols <<= 1;
+  p.tmem_cols = cols;
+  size_t smem = (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + (size_t)N * TC_BK * 2) + 1024;
+  // at most 512 / cols CTAs may share an SM's tensor memory: pad shared memory
+  // so that no more fit (228 KB per SM)
+  const size_t per_sm = 228 * 1024;
+  const size_t max_ctas = 512 / cols;
+  smem = std::max(smem, per_sm / (max_ctas + 1) + 1024);
+  cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid(M / TC_BM, (unsigned)std::min<int64_t>(batch, 65535));
+  ++g_launches;
+  tc_gemm_kernel<<<grid, 128, smem, st>>>(ta, tb, p, batch);
+  return true;
+}
+
+// ------------------------------------------------------------------------
+// operand preparation
+// ------------------------------------------------------------------------
+// amax[0] = max |x| over n entries of several strided sub-blocks:
+// block q holds rows x cols entries at base + q*stride + r*ld + c
+template <typename S>
+__global__ void amax_blocks_kernel(const S* __restrict__ base, int64_t nblk, int64_t stride, int rows, int cols,
+                                   int ld, unsigned int* __restrict__ out) {
+  float m = 0.0f;
+  const int64_t per = (int64_t)rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nblk * per;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = e / per;
+    int64_t rc = e - q * per;
+    int r = (int)(rc / cols), c = (int)(rc - (int64_t)r * cols);
+    float v = fabsf((float)base[q * stride + (int64_t)r * ld + c]);
+    m = fmaxf(m, v);
+  }
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as uints
+}
+template <typename S>
+void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
+                        cudaStream_t st) {
+  if (nblk == 0 || rows == 0 || cols == 0) return;
+  int64_t n = nblk * rows * cols;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  ++g_launches;
+  amax_blocks_kernel<S><<<blocks, 256, 0, st>>>(base, nblk, stride, rows, cols, ld, out);
+}
+template void launch_amax_blocks<float>(const float*, int64_t, int64_t, int, int, int, unsigned int*, cudaStream_t);
+template void launch_amax_blocks<double>(const double*, int64_t, int64_t, int, int, int, unsigned int*, cudaStream_t);
+
+// scale[0] = 2^e with amax * 2^e <= target (largest such power of two),
+// scale[1] = 2^-e.  amax = 0 gives scale 1.
+__global__ void pow2_scale_kernel(const unsigned int* __restrict__ amax_bits, float target, float* __restrict__ scale) {
+  float a = __uint_as_float(amax_bits[0]);
+  float s = 1.0f;
+  if (a > 0.0f && isfinite(a)) {
+    int e = (int)floorf(log2f(target / a));
+    e = max(-100, min(100, e));
+    s = ldexpf(1.0f, e);
+    while (a * s > target) s *= 0.5f;
+  }
+  scale[0] = s;
+  scale[1] = 1.0f / s;
+}
+void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale, cudaStream_t st) {
+  ++g_launches;
+  pow2_scale_kernel<<<1, 1, 0, st>>>(amax_bits, target, scale);
+}
+
+// out16[e] = (16-bit) (in[e] * scale[0])
+template <typename S>
+__global__ void to_lowp_kernel(const S* __restrict__ in, void* __restrict__ out, int64_t n, const float* __restrict__ scale,
+                               int bf16) {
+  const float s = scale ? scale[0] : 1.0f;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    float v = (float)in[e] * s;
+    if (bf16) reinterpret_cast<__nv_bfloat16*>(out)[e] = __float2bfloat16_rn(v);
+    else reinterpret_cast<__half*>(out)[e] = __float2half_rn(v);
+  }
+}
+template <typename S>
+void launch_to_lowp(int bf16, const S* in, void* out, int64_t n, const float* scale, cudaStream_t st) {
+  if (n == 0) return;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+  ++g_launches;
+  to_lowp_kernel<S><<<blocks, 256, 0, st>>>(in, out, n, scale, bf16);
+}
+template void launch_to_lowp<float>(int, const float*, void*, int64_t, const float*, cudaStream_t);
+template void launch_to_lowp<double>(int, const double*, void*, int64_t, const float*, cudaStream_t);
+
+// 16-bit merge (Algorithm 2 line 18-20 in the scaled low-precision layout):
+// child SS blocks (FP32 Ahat, rows/cols R..D) and couplings (FP32 Shat) go
+// to the parent's 16-bit near blocks, multiplied by scale[0].
+__global__ void merge_lowp_kernel(int D, int K, int64_t NP, const float* __restrict__ Ahat,
+                                  const int32_t* __restrict__ ni, const int32_t* __restrict__ nj,
+                                  const int32_t* __restrict__ ndst, int64_t FP, const float* __restrict__ Shat,
+                                  const int32_t* __restrict__ fi, const int32_t* __restrict__ fj,
+                                  const int32_t* __restrict__ fdst, void* __restrict__ Apar,
+                                  const float* __restrict__ scale, int bf16) {
+  const int R = D - K, Dp = 2 * K;
+  const int64_t q = blockIdx.y + (int64_t)blockIdx.z * gridDim.y;
+  if (q >= NP + FP) return;
+  const bool nr = q < NP;
+  const int64_t qq = nr ? q : q - NP;
+  const int i = nr ? ni[qq] : fi[qq], j = nr ? nj[qq] : fj[qq];
+  const int64_t dst = nr ? ndst[qq] : fdst[qq];
+  const float s = scale[0];
+  const int64_t obase = dst * Dp * Dp + (int64_t)(i & 1) * K * Dp + (j & 1) * K;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x) {
+    int a = e / K, b = e - a * K;
+    float v = (nr ? Ahat[qq * D * D + (int64_t)(R + a) * D + R + b] : Shat[qq * K * K + e]) * s;
+    int64_t o = obase + (int64_t)a * Dp + b;
+    if (bf16) reinterpret_cast<__nv_bfloat16*>(Apar)[o] = __float2bfloat16_rn(v);
+    else reinterpret_cast<__half*>(Apar)[o] = __float2half_rn(v);
+  }
+}
+void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_t* ni, const int32_t* nj,
+                       const int32_t* ndst, int64_t FP, const float* Shat, const int32_t* fi, const int32_t* fj,
+                       const int32_t* fdst, void* Apar, const float* scale, int bf16, cudaStream_t st) {
+  int64_t n = NP + FP;
+  if (n == 0 || K == 0) return;
+  int gx = std::min(64, (K * K + 255) / 256);
+  int64_t gy = std::min<int64_t>(n, 65535), gz = (n + gy - 1) / gy;
+  ++g_launches;
+  merge_lowp_kernel<<<dim3(gx, (unsigned)gy, (unsigned)gz), 256, 0, st>>>(D, K, NP, Ahat, ni, nj, ndst, FP, Shat, fi,
+                                                                           fj, fdst, Apar, scale, bf16);
+}
 
 }  // namespace h2

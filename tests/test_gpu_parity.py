@@ -173,6 +173,38 @@ def test_mixed_refined_solution(B, name, prec):
     S.close()
 
 
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tensor_core_projection_leaf(B, prec):
+    """Leaf-level projected blocks of the mixed path (tcgen05 GEMMs with
+    16-bit inputs, FP32 accumulation) against U^T A U in FP64 with the
+    library's own FP32 bases: the error is the 16-bit rounding of the
+    operands, 2^-11 (FP16) or 2^-8 (BF16) relative, grown by at most a few
+    times over a 256-term sum."""
+    H, F, flat, b = oracle_case("cube8192_yukawa")
+    S = lib_case(B, "cube8192_yukawa")
+    S.factor(prec)
+    st = S.stats()
+    assert st["tensor_cores"] is True
+    L = H["L"]
+    D, K = H["D"][L], H["K"][L]
+    nb = 1 << L
+    U = S.export("U", L).reshape(nb, D, D).astype(np.float64)  # column-major per box
+    Ah = S.export("Ahat", L).reshape(-1, D, D).astype(np.float64)
+    tol = {"fp16": 4e-3, "bf16": 3e-2}[prec]
+    R = D - K
+    for q, (i, j) in enumerate(H["near"][L]):
+        ref = U[i] @ H["A"][(i, j)] @ U[j].T  # U stored transposed: U[i] = U_i^T
+        got = Ah[q].copy()
+        if i == j:  # the SS part of diagonal blocks holds the Schur update
+            got[R:, R:] = ref[R:, R:]
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= tol, (q, i, j, err)
+    # the bases are orthogonal to FP32 accuracy
+    for i in range(nb):
+        assert np.abs(U[i] @ U[i].T - np.eye(D)).max() <= 1e-5
+    S.close()
+
+
 def test_errors(B):
     H, F, flat, b = oracle_case("cube2048_laplace")
     S = lib_case(B, "cube2048_laplace")
