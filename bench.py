@@ -121,7 +121,7 @@ def oracle_sample(wl, n_sample: int, target: float):
                   wl.max_rank, wl.far_samples, wl.near_samples)
     t0 = time.perf_counter()
     F = ulv.factor(H)
-    x, hist = ulv.refine(F, H, b, target, 60)
+    x, hist, _ = ulv.refine_gmres(F, H, b, target, 200, 30)
     dt = time.perf_counter() - t0
     return dt, dt * (wl.n / n_sample), hist
 
@@ -143,7 +143,7 @@ def run_reference(args, wl):
         if k >= args.warmup:
             steps.append(scaled)
     value = float(np.mean(steps))
-    sample = (f"oracle factor + refinement to {args.target:g} at N={args.cpu_sample_n} (same kernel, leaf, eta, "
+    sample = (f"oracle factor + FGMRES refinement to {args.target:g} at N={args.cpu_sample_n} (same kernel, leaf, eta, "
               f"tol, cube geometry), time scaled by N/{args.cpu_sample_n} = {wl.n / args.cpu_sample_n:g}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
@@ -159,24 +159,57 @@ def run_reference(args, wl):
 
 # ---------------------------------------------------------------- our arm ---
 PHASES = ("a1_qr", "a2_proj", "a3_lu", "a45_schur", "a2c_coupling", "a6_merge", "a7_root")
+SOLVE_PHASES = ("solve_subst", "solve_matvec")
 
 
-def roofline_for(phase, stats, t_phase, peaks, prec, tc):
-    """Roofline of one factorization phase (algorithmic flops / CUDA-event time)."""
-    fl = stats["flops"]
-    key = {"a1_qr": "a1_qr", "a2_proj": "a2_proj", "a3_lu": "a3_lu", "a45_schur": "a45_schur",
-           "a2c_coupling": "a2c_coupling"}.get(phase)
-    if key is None or t_phase <= 0:
+def fp64_peak_tflops() -> float:
+    """FP64 dense GEMM rate measured now (torch.matmul 4096^3, best of 3)."""
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn_like(a)
+    a @ b
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * 4096 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def roofline_for(phase, stats, t_phase, calls, peaks, prec, tc, fp64_tf):
+    """Roofline of one phase: algorithmic flops or bytes / CUDA-event time."""
+    if t_phase <= 0:
         return None
-    achieved = fl[key] / t_phase / 1e12
-    if phase in ("a2_proj", "a45_schur", "a2c_coupling") and tc:
-        bound, peak, src = "tensor", peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops"), "measured"
+    if phase == "solve_subst":
+        achieved = stats["bytes_subst"] * calls["subst"] / t_phase / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "phase": phase, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    if phase == "solve_matvec":
+        # FP64 multiply-adds on the leaf near blocks: the FP64 ALU rate binds
+        # before HBM on this part (2 flops per 8-byte entry)
+        flops = stats["flops_matvec"] * calls["matvec"] / t_phase / 1e12
+        gbs = stats["bytes_matvec"] * calls["matvec"] / t_phase / 1e9
+        return {"bound": "alu", "achieved": flops, "peak": fp64_tf, "unit": "TFLOP/s", "frac": flops / fp64_tf,
+                "traffic": None, "phase": phase, "hbm_gbs": gbs, "hbm_frac": gbs / peaks.get("hbm_gbs", 6800.0),
+                "peak_source": "FP64 peak measured live (torch.matmul float64 4096^3)"}
+    fl = stats["flops"]
+    if phase not in fl:
+        return None
+    achieved = fl[phase] / t_phase / 1e12
+    if phase == "a2_proj" and tc:
+        bound, peak, src = "tensor", peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops"), \
+            "measured bf16 sustained (FP16 runs at the same dense rate)"
+    elif phase == "a3_lu" or prec == "fp64":
+        bound, peak, src = "alu", fp64_tf, "FP64 peak measured live"
     else:
-        # SIMT arithmetic: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
         bound = "alu"
-        fp32 = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        peak = fp32 if prec != "fp64" and phase != "a3_lu" else fp32 / 64.0
-        src = "derived"
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        src = "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "phase": phase, "peak_source": src}
 
@@ -237,7 +270,7 @@ def main():
     launches0 = S.stats()["kernel_launches"]
     sampler = ClockSampler(local)
     sampler.start()
-    ph = {p: 0.0 for p in PHASES}
+    ph = {p: 0.0 for p in PHASES + SOLVE_PHASES}
     ph["factor"] = 0.0
     ph["solve"] = 0.0
     e0 = torch.cuda.Event(enable_timing=True)
@@ -247,7 +280,7 @@ def main():
     for _ in range(args.steps):
         st, rel, its = step(args.prec)
         s = S.stats()
-        for p in PHASES:
+        for p in PHASES + SOLVE_PHASES:
             ph[p] += s["times"][p]
         ph["factor"] += s["times"]["factor"]
         ph["solve"] += s["times"]["solve"]
@@ -295,17 +328,20 @@ def main():
                 "iters": r64[-1][2], "factor_s": s64["times"]["factor"], "solve_s": s64["times"]["solve"],
                 "phases": {p: s64["times"][p] for p in PHASES}}
 
-    # dominant phase and its roofline
+    # dominant phase of the step and its roofline
     tc = stats.get("tensor_cores", False)
-    top = max(PHASES, key=lambda p: ph[p])
-    roof = roofline_for(top, stats, ph[top], peaks, args.prec, tc)
-    roof_proj = roofline_for("a2_proj", stats, ph["a2_proj"], peaks, args.prec, tc)
+    fp64_tf = fp64_peak_tflops()
+    calls = stats["calls"]
+    top = max(PHASES + SOLVE_PHASES, key=lambda p: ph[p])
+    roof = roofline_for(top, stats, ph[top], calls, peaks, args.prec, tc, fp64_tf)
+    roofs = {p: roofline_for(p, stats, ph[p], calls, peaks, args.prec, tc, fp64_tf)
+             for p in ("a2_proj", "a3_lu", "solve_subst", "solve_matvec")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, scaled, hist = oracle_sample(wl, args.cpu_sample_n, args.target)
         cpu = {"value": scaled, "unit": UNIT, "cores": threads_used(), "kind": "oracle",
-               "sample": f"oracle factor + refinement at N={args.cpu_sample_n} of the same workload took {dt:.2f} s; "
+               "sample": f"oracle factor + FGMRES refinement at N={args.cpu_sample_n} of the same workload took {dt:.2f} s; "
                          f"scaled by N/{args.cpu_sample_n} (the method is O(N))"}
 
     value = t_ms / 1e3
@@ -321,7 +357,7 @@ def main():
         "relres": float(np.max(rels)), "iters": int(np.max(its_all)),
         "phases_s": ph, "build_s": build_s, "fp64": fp64,
         "speedup_vs_fp64": (fp64["s_per_step"] / value) if fp64 else None,
-        "roofline": roof, "roofline_a2_proj": roof_proj,
+        "roofline": roof, "rooflines": roofs, "fp64_peak_tflops": fp64_tf, "calls": calls,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(b.nbytes), "d2h_bytes_per_step": int(b.nbytes)},
         "gpu_launches": int(launches), "clocks": clocks,

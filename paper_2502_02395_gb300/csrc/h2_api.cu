@@ -473,6 +473,50 @@ void ulv_apply_any(h2_ctx* c, const double* r, double* x) {
   else ulv_apply_impl<float>(c, c->f32, r, x);
 }
 
+// CUDA-event timing of the substitution and matvec calls inside a solve
+struct SolveTimer {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sub, mv;
+  cudaStream_t st;
+  explicit SolveTimer(cudaStream_t s) : st(s) {}
+  std::pair<cudaEvent_t, cudaEvent_t> begin() {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    return {a, b};
+  }
+  void end(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, std::pair<cudaEvent_t, cudaEvent_t> e) {
+    cudaEventRecord(e.second, st);
+    v.push_back(e);
+  }
+  static double total(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v) {
+    double t = 0;
+    for (auto& e : v) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e.first, e.second);
+      t += ms * 1e-3;
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    v.clear();
+    return t;
+  }
+};
+thread_local SolveTimer* g_timer = nullptr;
+
+void ulv_timed(h2_ctx* c, const double* r, double* x) {
+  if (!g_timer) return ulv_apply_any(c, r, x);
+  auto e = g_timer->begin();
+  ulv_apply_any(c, r, x);
+  g_timer->end(g_timer->sub, e);
+}
+void matvec_timed(h2_ctx* c, const double* x, double* y) {
+  if (!g_timer) return matvec_impl(c, x, y);
+  auto e = g_timer->begin();
+  matvec_impl(c, x, y);
+  g_timer->end(g_timer->mv, e);
+}
+
 // copy an N-vector in (orig order, host or device) to the padded tree vector
 h2_status vec_in(h2_ctx* c, const double* src, double* tree) {
   const double* dsrc = src;
@@ -534,8 +578,8 @@ h2_status gmres_refine(h2_ctx* c, double bnorm, double target, int max_iters, in
       double* zj = Z + (int64_t)j * n;
       double* w = V + (int64_t)(j + 1) * n;
       CKC(cudaMemsetAsync(zj, 0, n * sizeof(double), st));
-      ulv_apply_any(c, vj, zj);
-      matvec_impl(c, zj, w);
+      ulv_timed(c, vj, zj);
+      matvec_timed(c, zj, w);
       launch_multi_dot(V, n, j + 1, w, n, c->gm_part, h1, false, st);
       launch_multi_axpy(V, n, j + 1, h1, -1.0, w, n, st);
       launch_multi_dot(V, n, j + 1, w, n, c->gm_part, h2, false, st);
@@ -575,7 +619,7 @@ h2_status gmres_refine(h2_ctx* c, double bnorm, double target, int max_iters, in
     }
     CKC(cudaMemcpyAsync(yv, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
     launch_multi_axpy(Z, n, k, yv, 1.0, c->x64, n, st);
-    matvec_impl(c, c->x64, c->y64);
+    matvec_timed(c, c->x64, c->y64);
     launch_residual(c->b64, c->y64, c->r64, n, st);
     launch_norm2(c->r64, n, nrm, st);
     double rn2 = 0;
@@ -780,12 +824,22 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   double rel = bnorm > 0 ? 1.0 : 0.0;
   int it = 0;
   c->times.history.clear();
+  SolveTimer timer(st);
+  struct TimerGuard {
+    SolveTimer* t;
+    ~TimerGuard() {
+      g_timer = nullptr;
+      SolveTimer::total(t->sub);
+      SolveTimer::total(t->mv);
+    }
+  } guard{&timer};
+  g_timer = &timer;
   if (bnorm > 0 && c->refine_method == 1) {
     CKS(gmres_refine(c, bnorm, target, max_iters, it, rel));
   } else {
     while (it < max_iters && (target <= 0 || rel > target) && bnorm > 0) {
-      ulv_apply_any(c, c->r64, c->x64);
-      matvec_impl(c, c->x64, c->y64);
+      ulv_timed(c, c->r64, c->x64);
+      matvec_timed(c, c->x64, c->y64);
       launch_residual(c->b64, c->y64, c->r64, nslot, st);
       launch_norm2(c->r64, nslot, c->red + 600, st);
       double rn2 = 0;
@@ -806,6 +860,11 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->times.solve_total = ms * 1e-3;
+  g_timer = nullptr;
+  c->times.n_subst = (int)timer.sub.size();
+  c->times.n_matvec = (int)timer.mv.size();
+  c->times.subst = SolveTimer::total(timer.sub);
+  c->times.matvec = SolveTimer::total(timer.mv);  // the guard then finds both lists empty
   c->times.iters = it;
   c->times.relres = rel;
   if (relres_out) *relres_out = rel;
@@ -837,6 +896,7 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
   const PhaseTimes& t = c->times;
   double fl_proj = 0, fl_lu = 0, fl_schur = 0, fl_coup = 0, fl_qr = 0;
   o << "{\"N\":" << c->N << ",\"L\":" << c->L << ",\"prec\":" << c->prec << ",\"levels\":[";
+  // (per-level sizes; flop counts below use the actual ranks, not padded tiles)
   for (int l = 0; l <= c->L; ++l) {
     const DevLevel& d = c->lv[l];
     double D = d.D, K = d.K, R = d.R;
@@ -853,11 +913,30 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     fl_coup += d.FP * 4.0 * K * K * K;
     fl_qr += d.nb * (4.0 * D * K * K + 4.0 * D * D * K);
   }
-  o << "],\"flops\":{\"a1_qr\":" << fl_qr << ",\"a2_proj\":" << fl_proj << ",\"a3_lu\":" << fl_lu
+  // algorithmic traffic of one substitution (Eq. 31 form; storage width w)
+  // and one FP64 matvec
+  const double w = (c->prec == H2_PREC_FP64) ? 8.0 : 4.0;
+  double by_sub = 0, by_mv = 0, fl_mv = 0;
+  for (int l = 1; l <= c->L; ++l) {
+    const DevLevel& d = c->lv[l];
+    const double D = d.D, K = d.K, R = d.R;
+    by_sub += w * ((double)(d.NP - d.nb) * R * R + (double)d.NP * 2.0 * R * K + d.nb * (2.0 * D * D + 4.0 * R * R));
+    by_mv += 8.0 * (2.0 * d.nb * D * K + (double)d.FP * K * K);
+    fl_mv += 2.0 * (2.0 * d.nb * D * K + (double)d.FP * K * K);
+  }
+  {
+    const DevLevel& lf = c->lv[c->L];
+    by_mv += 8.0 * (double)lf.NP * lf.D * lf.D;
+    fl_mv += 2.0 * (double)lf.NP * lf.D * lf.D;
+  }
+  o << "],\"bytes_subst\":" << by_sub << ",\"bytes_matvec\":" << by_mv << ",\"flops_matvec\":" << fl_mv;
+  o << ",\"flops\":{\"a1_qr\":" << fl_qr << ",\"a2_proj\":" << fl_proj << ",\"a3_lu\":" << fl_lu
     << ",\"a45_schur\":" << fl_schur << ",\"a2c_coupling\":" << fl_coup << "}";
   o << ",\"times\":{\"a1_qr\":" << t.a1_qr << ",\"a2_proj\":" << t.a2_proj << ",\"a3_lu\":" << t.a3_lu
     << ",\"a45_schur\":" << t.a5_schur << ",\"a2c_coupling\":" << t.a2c_coupling << ",\"a6_merge\":" << t.a6_merge
     << ",\"a7_root\":" << t.a7_root << ",\"factor\":" << t.total_factor << ",\"solve\":" << t.solve_total
+    << ",\"solve_subst\":" << t.subst << ",\"solve_matvec\":" << t.matvec << "},\"calls\":{\"subst\":"
+    << t.n_subst << ",\"matvec\":" << t.n_matvec
     << "},\"iters\":" << t.iters << ",\"relres\":" << t.relres
     << ",\"kernel_launches\":" << g_launches.load() << ",\"refine_method\":" << c->refine_method
     << ",\"restart\":" << c->restart << ",\"tensor_cores\":" << (c->used_tc ? "true" : "false")

@@ -100,6 +100,9 @@ WORKLOADS = {
     # 65536 points on the unit sphere, 1/(r+1e-3), leaf 256, tol 1e-8, FP64.
     "sphere65536_laplace": Workload("sphere65536_laplace", 65536, "sphere", 3, 4,
                                     "laplace_eps", 256, 1.0, 1e-8),
+    # A quarter-size version of the next one (profiling captures).
+    "cube65536_yukawa": Workload("cube65536_yukawa", 65536, "cube", 5, 6,
+                                 "yukawa_eps", 256, 1.0, 1e-10, diag_shift=1.0),
     # 262144 points in the unit cube, Yukawa exp(-r)/(r+1e-3) + 1 on the
     # diagonal, leaf 256, eta 1, tol 1e-10 with the default rank cap.
     "cube262144_yukawa": Workload("cube262144_yukawa", 262144, "cube", 5, 6,
