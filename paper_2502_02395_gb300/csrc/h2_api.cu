@@ -122,6 +122,8 @@ h2_status setup_device(h2_ctx* c) {
       d.h_far_ptr[h.far[2 * q] + 1]++;
     }
     for (int i = 0; i < d.nb; ++i) {
+      d.max_near = std::max<int>(d.max_near, (int)d.h_near_ptr[i + 1]);
+      d.max_far = std::max<int>(d.max_far, (int)d.h_far_ptr[i + 1]);
       d.h_near_ptr[i + 1] += d.h_near_ptr[i];
       d.h_far_ptr[i + 1] += d.h_far_ptr[i];
       if (d.h_diag_pair[i] < 0) {
@@ -237,6 +239,11 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     CKC(dalloc(c, &f.U, nb * D * D));
     CKC(dalloc(c, &f.Tm, nb * K * K));
     CKC(dalloc(c, &f.Xo, nb * D * K));
+    CKC(dalloc(c, &f.Vq, nb * D * K));
+    CKC(dalloc(c, &f.tau, nb * std::max<size_t>(K, 1)));
+    CKC(dalloc(c, &f.Tw, nb * K * K));
+    if (sizeof(T) * D * K > 200 * 1024) CKC(dalloc(c, &f.Qs, nb * D * K));
+    wk = std::max(wk, nb * (K * K + D * K));
     CKC(dalloc(c, &f.Ahat, (size_t)d.NP * D * D));
     CKC(dalloc(c, &f.Shat, (size_t)std::max<int64_t>(d.FP, 1) * K * K));
     CKC(dalloc(c, &f.Z, nb * R * K));
@@ -305,10 +312,43 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     FacLevel<T>& f = F.lv[l];
     const int D = d.D, K = d.K, R = d.R;
     const int64_t DD = (int64_t)D * D;
-    // a1: complement bases
-    const int Kc = (l < L) ? c->lv[l + 1].K : 0;
-    launch_orth_input<T>(d.nb, D, K, Kc, d.X, (l < L) ? F.lv[l + 1].Tm : nullptr, f.Xo, st);
-    launch_qr_complement<T>(d.nb, D, K, f.Xo, f.U, f.Tm, st);
+    // a1: complement bases.  X^orth = X (leaf) or blockdiag(T_2p, T_2p+1) X,
+    // then Householder QR, the compact WY factor and U = P (I - V Tw V^T).
+    {
+      const int nb = d.nb;
+      const int64_t DK = (int64_t)D * K, KK = (int64_t)K * K;
+      T* Xc = F.Wk;  // X in T, row-major D x K per box
+      launch_convert<double, T>(d.X, Xc, nb * DK, st);
+      const T* Xin = Xc;
+      if (l < L) {
+        const int Kc = c->lv[l + 1].K;
+        const T* Tc = F.lv[l + 1].Tm;
+        const int64_t KcKc = (int64_t)Kc * Kc;
+        gemm<T>(prec, Kc, K, Kc, Tc, 2 * KcKc, nullptr, Kc, false, Xc, DK, nullptr, K, false, f.Xo, DK, nullptr, K,
+                T(1), T(0), nb, st);
+        gemm<T>(prec, Kc, K, Kc, Tc + KcKc, 2 * KcKc, nullptr, Kc, false, Xc + (int64_t)Kc * K, DK, nullptr, K,
+                false, f.Xo + (int64_t)Kc * K, DK, nullptr, K, T(1), T(0), nb, st);
+        Xin = f.Xo;
+      }
+      launch_qr_panel<T>(nb, D, K, Xin, f.Vq, f.tau, f.Tm, f.Qs, st);
+      T* Sb = F.Wk;
+      T* W1 = F.Wk + (int64_t)nb * KK;
+      if (K > 0) {
+        gemm<T>(prec, K, K, D, f.Vq, DK, nullptr, D, false, f.Vq, DK, nullptr, D, true, Sb, KK, nullptr, K, T(1), T(0),
+                nb, st);
+        launch_wy_tfactor<T>(nb, K, Sb, f.tau, f.Tw, st);
+        gemm<T>(prec, D, K, K, f.Vq, DK, nullptr, D, true, f.Tw, KK, nullptr, K, false, W1, DK, nullptr, K, T(1), T(0),
+                nb, st);
+      }
+      launch_perm_identity<T>(nb, D, K, f.U, st);
+      if (K > 0) {
+        if (R > 0)
+          gemm<T>(prec, R, D, K, f.Vq + K, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U, DD, nullptr, D, T(-1),
+                  T(1), nb, st);
+        gemm<T>(prec, K, D, K, f.Vq, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U + (int64_t)R * D, DD, nullptr,
+                D, T(-1), T(1), nb, st);
+      }
+    }
     mark();
     // a2: Ahat_ij = U_i^T A_ij U_j
     if (f.tc) {

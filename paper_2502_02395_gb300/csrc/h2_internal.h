@@ -97,6 +97,7 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
 struct DevLevel {
   int nb = 0, D = 0, K = 0, R = 0;
   int64_t NP = 0, FP = 0;
+  int max_near = 0, max_far = 0;  // largest near / far count of one box
   // pair lists (device)
   int32_t *near_i = nullptr, *near_j = nullptr;  // NP
   int64_t* near_ptr = nullptr;                   // nb + 1 (CSR over i)
@@ -118,7 +119,11 @@ template <typename T>
 struct FacLevel {
   T* U = nullptr;      // nb * D * D   [U^R U^S], column-major
   T* Tm = nullptr;     // nb * K * K   row-major, upper triangular
-  T* Xo = nullptr;     // nb * D * K   orthogonalisation workspace (column-major)
+  T* Xo = nullptr;     // nb * D * K   X^orth (row-major)
+  T* Vq = nullptr;     // nb * D * K   Householder reflectors (column-major, unit diagonal)
+  T* tau = nullptr;    // nb * K
+  T* Tw = nullptr;     // nb * K * K   compact-WY triangular factor
+  T* Qs = nullptr;     // nb * D * K   panel scratch when it does not fit in shared memory
   T* Ain = nullptr;    // NP * D * D   input near blocks of this level (row-major)
   T* Ahat = nullptr;   // NP * D * D   projected blocks (row-major)
   T* Shat = nullptr;   // FP * K * K   couplings in orthogonal coordinates

@@ -21,9 +21,11 @@ void gemm_simt(int M, int N, int K, const T* A, int64_t sA, const int32_t* ia, i
                int64_t sB, const int32_t* ib, int ldb, bool tB, T* C, int64_t sC, const int32_t* ic, int ldc,
                T alpha, T beta, int64_t batch, cudaStream_t st);
 template <typename T>
-void launch_orth_input(int nb, int D, int K, int Kc, const double* X, const T* Tc, T* Xo, cudaStream_t st);
+void launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm, T* gscr, cudaStream_t st);
 template <typename T>
-void launch_qr_complement(int nb, int D, int K, T* Xo, T* U, T* Tm, cudaStream_t st);
+void launch_wy_tfactor(int nb, int K, const T* S, const T* tau, T* Tw, cudaStream_t st);
+template <typename T>
+void launch_perm_identity(int nb, int D, int K, T* U, cudaStream_t st);
 template <typename T>
 void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
                        int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st);

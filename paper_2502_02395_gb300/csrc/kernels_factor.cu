@@ -6,10 +6,8 @@
 //   gemm_batched_kernel    SIMT batched GEMM C = alpha op(A) op(B) + beta C
 //                          (FP64 path: projection Algorithm 4 line 3 / 10,
 //                          Schur update line 6, couplings)
-//   orth_input_kernel      X_p^orth = blockdiag(T_2p, T_2p+1) X_p (Eq. 6-7
-//                          above the leaves)
-//   qr_complement_kernel   Householder QR of X^orth: U = [U^R U^S], T
-//                          (Eq. 6-7), one CTA per box
+//   qr_panel_kernel,       Householder QR of X^orth, its compact WY factor
+//   wy_tfactor_kernel      and the explicit U = [U^R U^S] (Eq. 6-7)
 //   lu_inverse_kernel      partial-pivot LU of Ahat_ii^RR in FP64 (Algorithm
 //                          2 line 9 with LU in place of Cholesky) and the
 //                          explicit inverse (Ahat_ii^RR)^-1 used by the
@@ -184,71 +182,57 @@ __device__ T block_sum(T v, T* sbuf) {
 }
 
 // ------------------------------------------------------------------------
-// a1: X^orth (column-major D x K per box)
-//   leaf:  X^orth = X
-//   upper: X^orth = blockdiag(T_2p, T_2p+1) X,  T row-major Kc x Kc
+// a1: complement bases (Eq. 6-7) in three steps:
+//   qr_panel_kernel   Householder QR of X^orth (LAPACK geqr2 conventions:
+//                     beta = -sign(alpha) |x|), one CTA per box, the panel in
+//                     shared memory when it fits.  Writes the reflectors V
+//                     (column-major D x K, unit diagonal stored), tau and
+//                     T_i = R (row-major K x K, X^orth = U^S T_i).
+//   wy_tfactor_kernel the triangular factor of the compact WY form
+//                     H_0 ... H_{K-1} = I - V Tw V^T (LAPACK larft, forward,
+//                     columnwise) from S = V^T V.
+//   identity + GEMMs  U = [Q[:, K:] Q[:, :K]] with Q = I - V Tw V^T, formed
+//                     by batched GEMMs (in the caller).
 // ------------------------------------------------------------------------
 template <typename T>
-__global__ void orth_input_kernel(int D, int K, int Kc, const double* __restrict__ X,
-                                  const T* __restrict__ Tc, T* __restrict__ Xo) {
-  int box = blockIdx.y;
-  const double* Xb = X + (int64_t)box * D * K;
-  T* Ob = Xo + (int64_t)box * D * K;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D * K; e += gridDim.x * blockDim.x) {
-    int a = e / D, r = e - a * D;  // output column a, row r (column-major)
-    T v;
-    if (Kc == 0) {
-      v = (T)Xb[(int64_t)r * K + a];
-    } else {
-      int half = r / Kc, rr = r - half * Kc;
-      const T* Tb = Tc + (int64_t)(2 * box + half) * Kc * Kc + (int64_t)rr * Kc;
-      const double* xcol = Xb + (int64_t)half * Kc * K + a;
-      T s = T(0);
-      for (int u = rr; u < Kc; ++u) s = fma(Tb[u], (T)xcol[(int64_t)u * K], s);  // T upper triangular
-      v = s;
-    }
-    Ob[e] = v;
-  }
+__device__ T block_sum2(T v, T* sbuf) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) sbuf[warp] = v;
+  __syncthreads();
+  T t = T(0);
+  for (int w = 0; w < nw; ++w) t += sbuf[w];
+  __syncthreads();
+  return t;
 }
 
+// Xin: row-major D x K per box.  Vout: column-major D x K per box.
 template <typename T>
-void launch_orth_input(int nb, int D, int K, int Kc, const double* X, const T* Tc, T* Xo, cudaStream_t st) {
-  if (nb == 0 || D * K == 0) return;
-  dim3 grid((D * K + 255) / 256, nb);
-  ++g_launches;
-  orth_input_kernel<T><<<grid, 256, 0, st>>>(D, K, Kc, X, Tc, Xo);
-}
-template void launch_orth_input<double>(int, int, int, int, const double*, const double*, double*, cudaStream_t);
-template void launch_orth_input<float>(int, int, int, int, const double*, const float*, float*, cudaStream_t);
-
-// ------------------------------------------------------------------------
-// a1: Householder QR (LAPACK geqr2 + org2r conventions).
-//   Xo  column-major D x K (destroyed: reflectors)
-//   U   column-major D x D; Q column j goes to U column (j < K ? R + j : j - K)
-//   Tm  row-major K x K upper triangular: X^orth = U^S T
-// ------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) qr_complement_kernel(int D, int K, T* __restrict__ Xo, T* __restrict__ U,
-                                                            T* __restrict__ Tm) {
-  extern __shared__ unsigned char smraw[];
-  T* tau = reinterpret_cast<T*>(smraw);  // K
+__global__ void __launch_bounds__(512) qr_panel_kernel(int D, int K, const T* __restrict__ Xin, T* __restrict__ Vout,
+                                                       T* __restrict__ tau_out, T* __restrict__ Tm, T* __restrict__ gscr,
+                                                       int use_smem) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ T red[32];
   __shared__ T s_tau, s_scal, s_beta;
   const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  T* X = Xo + (int64_t)box * D * K;
-  T* Q = U + (int64_t)box * D * D;
-  const int R = D - K;
+  T* X = use_smem ? reinterpret_cast<T*>(smraw) : gscr + (size_t)box * D * K;  // column-major, ld = D
+  const T* src = Xin + (size_t)box * D * K;
+  for (int e = tid; e < D * K; e += blockDim.x) {
+    const int r = e / K, a = e - r * K;
+    X[a * D + r] = src[e];
+  }
+  __syncthreads();
   for (int k = 0; k < K; ++k) {
-    T* xk = X + (int64_t)k * D;
+    T* xk = X + k * D;
     T part = T(0);
     for (int r = k + 1 + tid; r < D; r += blockDim.x) part += xk[r] * xk[r];
-    T xn2 = block_sum(part, red);
+    const T xn2 = block_sum2(part, red);
     if (tid == 0) {
-      T alpha = xk[k];
+      const T alpha = xk[k];
       if (xn2 == T(0)) {
         s_tau = T(0);
       } else {
-        T beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
+        const T beta = -copysign(sqrt(alpha * alpha + xn2), alpha);
         s_tau = (beta - alpha) / beta;
         s_scal = T(1) / (alpha - beta);
         s_beta = beta;
@@ -260,58 +244,108 @@ __global__ void __launch_bounds__(256) qr_complement_kernel(int D, int K, T* __r
       const T scal = s_scal;
       for (int r = k + 1 + tid; r < D; r += blockDim.x) xk[r] *= scal;
       __syncthreads();
-      if (tid == 0) xk[k] = s_beta;
       for (int j = k + 1 + warp; j < K; j += nw) {
-        T* xj = X + (int64_t)j * D;
+        T* xj = X + j * D;
+        const T xjk = xj[k];
         T w = T(0);
         for (int r = k + 1 + lane; r < D; r += 32) w += xk[r] * xj[r];
         for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        w = tk * (w + xj[k]);
-        if (lane == 0) xj[k] -= w;
+        w = tk * (w + xjk);
+        if (lane == 0) xj[k] = xjk - w;
         for (int r = k + 1 + lane; r < D; r += 32) xj[r] -= w * xk[r];
       }
+      if (tid == 0) xk[k] = s_beta;
     }
-    if (tid == 0) tau[k] = tk;
+    if (tid == 0) tau_out[(size_t)box * K + k] = tk;
     __syncthreads();
   }
-  // T = upper triangle of the first K rows
+  // R (row-major, upper) and V (column-major, unit diagonal, zeros above)
+  T* Rb = Tm + (size_t)box * K * K;
   for (int e = tid; e < K * K; e += blockDim.x) {
-    int a = e / K, b = e - a * K;
-    Tm[(int64_t)box * K * K + e] = (b >= a) ? X[(int64_t)b * D + a] : T(0);
+    const int a = e / K, b = e - a * K;
+    Rb[e] = (b >= a) ? X[b * D + a] : T(0);
   }
-  // Q = H_0 ... H_{K-1} applied to the identity (column j of Q in U column cmap(j))
-  auto cmap = [&](int j) { return j < K ? R + j : j - K; };
-  for (int e = tid; e < D * D; e += blockDim.x) {
-    int j = e / D, r = e - j * D;
-    Q[(int64_t)cmap(j) * D + r] = (r == j) ? T(1) : T(0);
+  T* Vb = Vout + (size_t)box * D * K;
+  for (int e = tid; e < D * K; e += blockDim.x) {
+    const int a = e / D, r = e - a * D;
+    Vb[e] = (r > a) ? X[a * D + r] : (r == a ? T(1) : T(0));
   }
+}
+
+// Tw (row-major K x K, upper): for i = 0..K-1:
+//   Tw[0:i, i] = -tau_i Tw[0:i, 0:i] S[0:i, i];  Tw[i, i] = tau_i
+// S = V^T V (row-major K x K per box).
+template <typename T>
+__global__ void __launch_bounds__(256) wy_tfactor_kernel(int K, const T* __restrict__ S, const T* __restrict__ tau,
+                                                         T* __restrict__ Tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Ts = reinterpret_cast<T*>(smraw);  // K x K row-major
+  T* w = Ts + K * K;                    // K
+  const int box = blockIdx.x, tid = threadIdx.x;
+  const T* Sb = S + (size_t)box * K * K;
+  const T* tb = tau + (size_t)box * K;
+  for (int e = tid; e < K * K; e += blockDim.x) Ts[e] = T(0);
   __syncthreads();
-  for (int k = K - 1; k >= 0; --k) {
-    const T tk = tau[k];
-    if (tk != T(0)) {
-      const T* v = X + (int64_t)k * D;  // v[k] = 1 implicit, v[r>k] stored
-      for (int j = k + warp; j < D; j += nw) {
-        T* qj = Q + (int64_t)cmap(j) * D;
-        T w = T(0);
-        for (int r = k + 1 + lane; r < D; r += 32) w += v[r] * qj[r];
-        for (int o = 16; o; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        w = tk * (w + qj[k]);
-        if (lane == 0) qj[k] -= w;
-        for (int r = k + 1 + lane; r < D; r += 32) qj[r] -= w * v[r];
-      }
-    }
+  for (int i = 0; i < K; ++i) {
+    for (int r = tid; r < i; r += blockDim.x) w[r] = Sb[r * K + i];
     __syncthreads();
+    const T ti = tb[i];
+    for (int r = tid; r < i; r += blockDim.x) {
+      T sacc = T(0);
+      for (int c = r; c < i; ++c) sacc += Ts[r * K + c] * w[c];
+      Ts[r * K + i] = -ti * sacc;
+    }
+    if (tid == 0) Ts[i * K + i] = ti;
+    __syncthreads();
+  }
+  T* out = Tw + (size_t)box * K * K;
+  for (int e = tid; e < K * K; e += blockDim.x) out[e] = Ts[e];
+}
+
+// U (column-major D x D): column c' holds e_{perm(c')}, perm(c') = K + c'
+// for c' < R = D - K, c' - R otherwise ([Q[:, K:] Q[:, :K]] of Q = I).
+template <typename T>
+__global__ void perm_identity_kernel(int nb, int D, int K, T* __restrict__ U) {
+  const int R = D - K;
+  const int64_t n = (int64_t)nb * D * D;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e % ((int64_t)D * D);
+    const int cp = (int)(q / D), r = (int)(q % D);
+    const int src = cp < R ? K + cp : cp - R;
+    U[e] = (r == src) ? T(1) : T(0);
   }
 }
 
 template <typename T>
-void launch_qr_complement(int nb, int D, int K, T* Xo, T* U, T* Tm, cudaStream_t st) {
-  if (nb == 0) return;
+void launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm, T* gscr, cudaStream_t st) {
+  if (nb == 0 || K == 0) return;
+  const size_t sm = sizeof(T) * (size_t)D * K;
+  const int use = sm <= 200 * 1024;
+  if (use) cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ++g_launches;
-  qr_complement_kernel<T><<<nb, 256, sizeof(T) * (K + 1), st>>>(D, K, Xo, U, Tm);
+  qr_panel_kernel<T><<<nb, 512, use ? sm : 0, st>>>(D, K, Xin, Vout, tau, Tm, gscr, use);
 }
-template void launch_qr_complement<double>(int, int, int, double*, double*, double*, cudaStream_t);
-template void launch_qr_complement<float>(int, int, int, float*, float*, float*, cudaStream_t);
+template <typename T>
+void launch_wy_tfactor(int nb, int K, const T* S, const T* tau, T* Tw, cudaStream_t st) {
+  if (nb == 0 || K == 0) return;
+  const size_t sm = sizeof(T) * ((size_t)K * K + K);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(wy_tfactor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ++g_launches;
+  wy_tfactor_kernel<T><<<nb, 256, sm, st>>>(K, S, tau, Tw);
+}
+template <typename T>
+void launch_perm_identity(int nb, int D, int K, T* U, cudaStream_t st) {
+  const int64_t n = (int64_t)nb * D * D;
+  if (n == 0) return;
+  ++g_launches;
+  perm_identity_kernel<T><<<(int)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(nb, D, K, U);
+}
+#define H2_INST_QR(T)                                                                                         \
+  template void launch_qr_panel<T>(int, int, int, const T*, T*, T*, T*, T*, cudaStream_t);                     \
+  template void launch_wy_tfactor<T>(int, int, const T*, const T*, T*, cudaStream_t);                          \
+  template void launch_perm_identity<T>(int, int, int, T*, cudaStream_t);
+H2_INST_QR(double)
+H2_INST_QR(float)
 
 // ------------------------------------------------------------------------
 // a3: FP64 partial-pivot LU of Ahat_ii^RR (rows/cols 0..R of a D x D

@@ -69,164 +69,292 @@ __device__ __forceinline__ void warp_rows_gemv(const T* __restrict__ M, int64_t 
   }
 }
 
+// ------------------------------------------------------------------------
+// Block-row GEMV core.  Warp w owns rows w, w + 8, ... (at most 8 * RPW
+// rows); each lane holds a partial sum per owned row over its column chunks
+// and keeps accumulating over all blocks of the block row, so the warp
+// reduction happens once per row at the end.  Rows are read with 16-byte
+// vector loads when the layout allows.
+// ------------------------------------------------------------------------
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int n = 4;
+  __device__ static V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ static float fma4(const V& a, const V& x, float s) {
+    s = fmaf(a.x, x.x, s);
+    s = fmaf(a.y, x.y, s);
+    s = fmaf(a.z, x.z, s);
+    return fmaf(a.w, x.w, s);
+  }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int n = 2;
+  __device__ static V zero() { return make_double2(0.0, 0.0); }
+  __device__ static double fma4(const V& a, const V& x, double s) { return fma(a.y, x.y, fma(a.x, x.x, s)); }
+};
+
+// acc[t] += sum_c M[r_t * ld + c] xs[c] for the rows r_t = r0 + warp + 8 t < nr.
+// For each column chunk every lane first issues the loads of all its rows,
+// then does the multiply-adds, so RPW independent 16-byte loads per lane are
+// in flight at once.
+template <typename T, int RPW>
+__device__ __forceinline__ void rows_acc(int r0, const T* __restrict__ M, int64_t ld, int nr, int nc,
+                                         const T* __restrict__ xs, T (&acc)[RPW]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  using VT = typename Vec16<T>::V;
+  constexpr int VN = Vec16<T>::n;
+  const bool vec = ((ld % VN) == 0) && ((nc % (32 * VN)) == 0) && ((reinterpret_cast<uintptr_t>(M) & 15) == 0);
+  const int rbase = r0 + warp;
+  if (vec) {
+    for (int c = lane; c < nc / VN; c += 32) {
+      VT v[RPW];
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) {
+        const int r = rbase + 8 * t;
+        v[t] = (r < nr) ? __ldg(reinterpret_cast<const VT*>(M + r * ld) + c) : Vec16<T>::zero();
+      }
+      const VT x = *reinterpret_cast<const VT*>(xs + c * VN);
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) acc[t] = Vec16<T>::fma4(v[t], x, acc[t]);
+    }
+  } else {
+    for (int c = lane; c < nc; c += 32) {
+      T v[RPW];
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) {
+        const int r = rbase + 8 * t;
+        v[t] = (r < nr) ? __ldg(M + r * ld + c) : T(0);
+      }
+      const T x = xs[c];
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) acc[t] = fma(v[t], x, acc[t]);
+    }
+  }
+}
+
+// out[r] = base[r] + sign * sum over lanes of acc (rows owned by this warp)
+template <typename T, int RPW>
+__device__ __forceinline__ void rows_finish(int r0, int nr, const T (&acc)[RPW], T sign, const T* base, T* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < RPW; ++t) {
+    const int r = r0 + warp + 8 * t;
+    T v = warp_sum(acc[t]);
+    if (lane == 0 && r < nr) out[r] = (base ? base[r] : T(0)) + sign * v;
+  }
+}
+
+template <typename T, int RPW>
+__device__ __forceinline__ void zero(T (&acc)[RPW]) {
+#pragma unroll
+  for (int t = 0; t < RPW; ++t) acc[t] = T(0);
+}
+
+constexpr int kRPW = 16;  // rows per warp per pass: 128-row chunks with 8 warps
+constexpr int kChunk = 8 * kRPW;
+
 // ---------------------------------------------------------------- fwd1 ---
 template <typename T>
-__global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, const T* __restrict__ U, const T* __restrict__ Ainv,
+__global__ void __launch_bounds__(256, 2) fwd1_kernel(int D, int R, const T* __restrict__ U, const T* __restrict__ Ainv,
                                                    const T* __restrict__ vin, T* __restrict__ c, T* __restrict__ u) {
-  extern __shared__ unsigned char sm_raw[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sv = reinterpret_cast<T*>(sm_raw);  // D
   T* sc = sv + D;                        // D
-  T* su = sc + D;                        // R
   const int i = blockIdx.x, tid = threadIdx.x;
-  for (int e = tid; e < D; e += blockDim.x) { sv[e] = vin[(int64_t)i * D + e]; sc[e] = 0; }
-  for (int e = tid; e < R; e += blockDim.x) su[e] = 0;
+  for (int e = tid; e < D; e += blockDim.x) sv[e] = vin[(int64_t)i * D + e];
   __syncthreads();
-  // c[n] = sum_k U(k, n) v[k]; U column-major: column n contiguous
-  warp_rows_gemv<T>(U + (int64_t)i * D * D, D, D, D, sv, sc, T(1));
+  T acc[kRPW];
+  // c[n] = sum_k U(k, n) v[k]; U column-major: column n is contiguous
+  for (int r0 = 0; r0 < D; r0 += kChunk) {
+    zero(acc);
+    rows_acc<T, kRPW>(r0, U + (int64_t)i * D * D, D, D, D, sv, acc);
+    rows_finish<T, kRPW>(r0, D, acc, T(1), nullptr, sc);
+  }
   __syncthreads();
-  warp_rows_gemv<T>(Ainv + (int64_t)i * R * R, R, R, R, sc, su, T(1));
-  __syncthreads();
+  for (int r0 = 0; r0 < R; r0 += kChunk) {
+    zero(acc);
+    rows_acc<T, kRPW>(r0, Ainv + (int64_t)i * R * R, R, R, R, sc, acc);
+    rows_finish<T, kRPW>(r0, R, acc, T(1), nullptr, u + (int64_t)i * R);
+  }
   for (int e = tid; e < D; e += blockDim.x) c[(int64_t)i * D + e] = sc[e];
-  for (int e = tid; e < R; e += blockDim.x) u[(int64_t)i * R + e] = su[e];
 }
 
 // ---------------------------------------------------------------- fwd2 ---
+// v_i = Ainv_i (c_i^R - sum_{j<i near} Ahat_ij^RR u_j)
 template <typename T>
-__global__ void __launch_bounds__(256) fwd2_kernel(int D, int R, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256, 2) fwd2_kernel(int D, int R, const int64_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
                                                    const T* __restrict__ Ainv, const T* __restrict__ c,
                                                    const T* __restrict__ u, T* __restrict__ v) {
-  extern __shared__ unsigned char sm_raw[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sb = reinterpret_cast<T*>(sm_raw);  // R
-  T* sx = sb + R;                        // R
-  T* sv = sx + R;                        // R
+  T* sx = sb + R;                        // nn * R
   const int i = blockIdx.x, tid = threadIdx.x;
-  for (int e = tid; e < R; e += blockDim.x) { sb[e] = c[(int64_t)i * D + e]; sv[e] = 0; }
-  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
-    const int j = nj[p];
-    if (j >= i) break;  // sorted: only j < i
-    __syncthreads();
-    for (int e = tid; e < R; e += blockDim.x) sx[e] = u[(int64_t)j * R + e];
-    __syncthreads();
-    warp_rows_gemv<T>(Ahat + p * D * D, D, R, R, sx, sb, T(-1));
+  const int64_t p0 = ptr[i];
+  int nlow = 0;
+  while (p0 + nlow < ptr[i + 1] && nj[p0 + nlow] < i) ++nlow;  // sorted neighbours: the j < i ones lead
+  for (int e = tid; e < nlow * R; e += blockDim.x) sx[e] = u[(int64_t)nj[p0 + e / R] * R + e % R];
+  __syncthreads();
+  T acc[kRPW];
+  for (int r0 = 0; r0 < R; r0 += kChunk) {
+    zero(acc);
+    for (int q = 0; q < nlow; ++q) rows_acc<T, kRPW>(r0, Ahat + (p0 + q) * D * D, D, R, R, sx + q * R, acc);
+    rows_finish<T, kRPW>(r0, R, acc, T(-1), c + (int64_t)i * D, sb);
   }
   __syncthreads();
-  warp_rows_gemv<T>(Ainv + (int64_t)i * R * R, R, R, R, sb, sv, T(1));
-  __syncthreads();
-  for (int e = tid; e < R; e += blockDim.x) v[(int64_t)i * R + e] = sv[e];
+  for (int r0 = 0; r0 < R; r0 += kChunk) {
+    zero(acc);
+    rows_acc<T, kRPW>(r0, Ainv + (int64_t)i * R * R, R, R, R, sb, acc);
+    rows_finish<T, kRPW>(r0, R, acc, T(1), nullptr, v + (int64_t)i * R);
+  }
 }
 
 // ---------------------------------------------------------------- fwd3 ---
+// s_i = c_i^S - sum_{j near} Ahat_ij^SR v_j  -> parent input slot
 template <typename T>
-__global__ void __launch_bounds__(256) fwd3_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256, 2) fwd3_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
                                                    const T* __restrict__ c, const T* __restrict__ v,
                                                    T* __restrict__ pvin) {
-  extern __shared__ unsigned char sm_raw[];
-  T* ss = reinterpret_cast<T*>(sm_raw);  // K
-  T* sx = ss + K;                        // R
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sx = reinterpret_cast<T*>(sm_raw);  // nn * R
   const int i = blockIdx.x, tid = threadIdx.x;
-  for (int e = tid; e < K; e += blockDim.x) ss[e] = c[(int64_t)i * D + R + e];
-  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
-    const int j = nj[p];
-    __syncthreads();
-    for (int e = tid; e < R; e += blockDim.x) sx[e] = v[(int64_t)j * R + e];
-    __syncthreads();
-    warp_rows_gemv<T>(Ahat + p * D * D + (int64_t)R * D, D, K, R, sx, ss, T(-1));
-  }
+  const int64_t p0 = ptr[i];
+  const int nn = (int)(ptr[i + 1] - p0);
+  for (int e = tid; e < nn * R; e += blockDim.x) sx[e] = v[(int64_t)nj[p0 + e / R] * R + e % R];
   __syncthreads();
+  T acc[kRPW];
   const int Dp = 2 * K;
-  for (int e = tid; e < K; e += blockDim.x) pvin[(int64_t)(i >> 1) * Dp + (i & 1) * K + e] = ss[e];
+  for (int r0 = 0; r0 < K; r0 += kChunk) {
+    zero(acc);
+    for (int q = 0; q < nn; ++q)
+      rows_acc<T, kRPW>(r0, Ahat + (p0 + q) * D * D + (int64_t)R * D, D, K, R, sx + q * R, acc);
+    rows_finish<T, kRPW>(r0, K, acc, T(-1), c + (int64_t)i * D + R, pvin + (int64_t)(i >> 1) * Dp + (i & 1) * K);
+  }
 }
 
 // ---------------------------------------------------------------- bwd1 ---
+// om_i = v_i - Ainv_i sum_{j near} Ahat_ij^RS x_j^S
 template <typename T>
-__global__ void __launch_bounds__(256) bwd1_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256, 2) bwd1_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
                                                    const T* __restrict__ Ainv, const T* __restrict__ v,
                                                    const T* __restrict__ px, T* __restrict__ om) {
-  extern __shared__ unsigned char sm_raw[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   T* st = reinterpret_cast<T*>(sm_raw);  // R
-  T* sx = st + R;                        // K
-  T* so = sx + K;                        // R
+  T* sx = st + R;                        // nn * K
   const int i = blockIdx.x, tid = threadIdx.x, Dp = 2 * K;
-  for (int e = tid; e < R; e += blockDim.x) { st[e] = 0; so[e] = v[(int64_t)i * R + e]; }
-  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
-    const int j = nj[p];
-    __syncthreads();
-    for (int e = tid; e < K; e += blockDim.x) sx[e] = px[(int64_t)(j >> 1) * Dp + (j & 1) * K + e];
-    __syncthreads();
-    warp_rows_gemv<T>(Ahat + p * D * D + R, D, R, K, sx, st, T(1));
+  const int64_t p0 = ptr[i];
+  const int nn = (int)(ptr[i + 1] - p0);
+  for (int e = tid; e < nn * K; e += blockDim.x) {
+    const int j = nj[p0 + e / K];
+    sx[e] = px[(int64_t)(j >> 1) * Dp + (j & 1) * K + e % K];
   }
   __syncthreads();
-  warp_rows_gemv<T>(Ainv + (int64_t)i * R * R, R, R, R, st, so, T(-1));
+  T acc[kRPW];
+  for (int r0 = 0; r0 < R; r0 += kChunk) {
+    zero(acc);
+    for (int q = 0; q < nn; ++q) rows_acc<T, kRPW>(r0, Ahat + (p0 + q) * D * D + R, D, R, K, sx + q * K, acc);
+    rows_finish<T, kRPW>(r0, R, acc, T(1), nullptr, st);
+  }
   __syncthreads();
-  for (int e = tid; e < R; e += blockDim.x) om[(int64_t)i * R + e] = so[e];
+  for (int r0 = 0; r0 < R; r0 += kChunk) {
+    zero(acc);
+    rows_acc<T, kRPW>(r0, Ainv + (int64_t)i * R * R, R, R, R, st, acc);
+    rows_finish<T, kRPW>(r0, R, acc, T(-1), v + (int64_t)i * R, om + (int64_t)i * R);
+  }
 }
 
 // ---------------------------------------------------------------- bwd2 ---
+// x_i^R = om_i - Ainv_i sum_{j>i near} Ahat_ij^RR om_j;  x_i = U_i [x_i^R; x_i^S]
 template <typename T>
-__global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256, 2) bwd2_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
                                                    const T* __restrict__ Ainv, const T* __restrict__ U,
                                                    const T* __restrict__ om, const T* __restrict__ px,
                                                    T* __restrict__ xs) {
-  extern __shared__ unsigned char sm_raw[];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sq = reinterpret_cast<T*>(sm_raw);  // R
-  T* sx = sq + R;                        // R  (om_j, then [x^R; x^S] of length D)
-  T* sz = sx + D;                        // D
+  T* sz = sq + R;                        // D
+  T* sx = sz + D;                        // nn * R
   const int i = blockIdx.x, tid = threadIdx.x, Dp = 2 * K;
-  for (int e = tid; e < R; e += blockDim.x) sq[e] = 0;
-  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
-    const int j = nj[p];
-    if (j <= i) continue;
-    __syncthreads();
-    for (int e = tid; e < R; e += blockDim.x) sx[e] = om[(int64_t)j * R + e];
-    __syncthreads();
-    warp_rows_gemv<T>(Ahat + p * D * D, D, R, R, sx, sq, T(1));
-  }
-  __syncthreads();
-  for (int e = tid; e < R; e += blockDim.x) sz[e] = om[(int64_t)i * R + e];
+  const int64_t p0 = ptr[i], p1 = ptr[i + 1];
+  int first = 0;
+  while (p0 + first < p1 && nj[p0 + first] <= i) ++first;  // neighbours j > i trail
+  const int nhi = (int)(p1 - p0) - first;
+  for (int e = tid; e < nhi * R; e += blockDim.x) sx[e] = om[(int64_t)nj[p0 + first + e / R] * R + e % R];
   for (int e = tid; e < K; e += blockDim.x) sz[R + e] = px[(int64_t)(i >> 1) * Dp + (i & 1) * K + e];
   __syncthreads();
-  warp_rows_gemv<T>(Ainv + (int64_t)i * R * R, R, R, R, sq, sz, T(-1));
+  T acc[kRPW];
+  for (int r0 = 0; r0 < R; r0 += kChunk) {
+    zero(acc);
+    for (int q = 0; q < nhi; ++q)
+      rows_acc<T, kRPW>(r0, Ahat + (p0 + first + q) * D * D, D, R, R, sx + q * R, acc);
+    rows_finish<T, kRPW>(r0, R, acc, T(1), nullptr, sq);
+  }
   __syncthreads();
-  // x = U z, U column-major: x[m] = sum_n U[n*D + m] z[n]
+  for (int r0 = 0; r0 < R; r0 += kChunk) {
+    zero(acc);
+    rows_acc<T, kRPW>(r0, Ainv + (int64_t)i * R * R, R, R, R, sq, acc);
+    rows_finish<T, kRPW>(r0, R, acc, T(-1), om + (int64_t)i * R, sz);
+  }
+  __syncthreads();
+  // x = U z, U column-major: x[m] = sum_n U[n*D + m] z[n] (coalesced over m)
   const T* Ub = U + (int64_t)i * D * D;
   for (int m = tid; m < D; m += blockDim.x) {
-    T s = 0;
-    for (int n = 0; n < D; ++n) s += Ub[(int64_t)n * D + m] * sz[n];
-    xs[(int64_t)i * D + m] = s;
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    int n = 0;
+    for (; n + 3 < D; n += 4) {
+      s0 = fma(Ub[(int64_t)n * D + m], sz[n], s0);
+      s1 = fma(Ub[(int64_t)(n + 1) * D + m], sz[n + 1], s1);
+      s2 = fma(Ub[(int64_t)(n + 2) * D + m], sz[n + 2], s2);
+      s3 = fma(Ub[(int64_t)(n + 3) * D + m], sz[n + 3], s3);
+    }
+    for (; n < D; ++n) s0 = fma(Ub[(int64_t)n * D + m], sz[n], s0);
+    xs[(int64_t)i * D + m] = (s0 + s1) + (s2 + s3);
   }
+}
+
+static void set_smem(const void* f, size_t sm) {
+  if (sm > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
 template <typename T>
 void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st) {
-  size_t sm = sizeof(T) * (2 * L.D + L.R);
+  size_t sm = sizeof(T) * 2 * L.D;
   ++g_launches;
   fwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, F.U, Ainv, F.vin, F.c, F.u);
 }
 template <typename T>
 void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st) {
-  size_t sm = sizeof(T) * 3 * L.R;
+  size_t sm = sizeof(T) * (size_t)L.R * (1 + L.max_near);
+  set_smem((const void*)fwd2_kernel<T>, sm);
   ++g_launches;
   fwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.near_ptr, L.near_j, F.Ahat, Ainv, F.c, F.u, F.v);
 }
 template <typename T>
 void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, T* parent_vin, cudaStream_t st) {
-  size_t sm = sizeof(T) * (L.K + L.R);
+  size_t sm = sizeof(T) * (size_t)L.R * L.max_near;
+  set_smem((const void*)fwd3_kernel<T>, sm);
   ++g_launches;
   fwd3_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, F.c, F.v, parent_vin);
 }
 template <typename T>
 void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st) {
-  size_t sm = sizeof(T) * (2 * L.R + L.K);
+  size_t sm = sizeof(T) * ((size_t)L.R + (size_t)L.K * L.max_near);
+  set_smem((const void*)bwd1_kernel<T>, sm);
   ++g_launches;
   bwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, Ainv, F.v, parent_x, F.om);
 }
 template <typename T>
 void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st) {
-  size_t sm = sizeof(T) * (L.R + 2 * L.D);
+  size_t sm = sizeof(T) * ((size_t)L.R + L.D + (size_t)L.R * L.max_near);
+  set_smem((const void*)bwd2_kernel<T>, sm);
   ++g_launches;
   bwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, Ainv, F.U, F.om, parent_x,
                                         F.xs);
@@ -287,27 +415,27 @@ void launch_matvec_up(const DevLevel& L, const double* xh_child, double* xh, cud
 }
 
 // couplings: yh_i = sum_{far j} S_f xh_j   (overwrites yh_i)
-__global__ void __launch_bounds__(256) mv_far_kernel(int K, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256, 2) mv_far_kernel(int K, const int64_t* __restrict__ ptr,
                                                      const int32_t* __restrict__ fj, const double* __restrict__ S,
                                                      const double* __restrict__ xh, double* __restrict__ yh) {
-  extern __shared__ double smv[];
-  double* sx = smv;      // K
-  double* sy = smv + K;  // K
+  extern __shared__ __align__(16) double smv[];  // nf * K
   const int i = blockIdx.x, tid = threadIdx.x;
-  for (int e = tid; e < K; e += blockDim.x) sy[e] = 0;
-  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
-    const int j = fj[p];
-    __syncthreads();
-    for (int e = tid; e < K; e += blockDim.x) sx[e] = xh[(int64_t)j * K + e];
-    __syncthreads();
-    warp_rows_gemv<double>(S + p * K * K, K, K, K, sx, sy, 1.0);
-  }
+  const int64_t p0 = ptr[i];
+  const int nf = (int)(ptr[i + 1] - p0);
+  for (int e = tid; e < nf * K; e += blockDim.x) smv[e] = xh[(int64_t)fj[p0 + e / K] * K + e % K];
   __syncthreads();
-  for (int e = tid; e < K; e += blockDim.x) yh[(int64_t)i * K + e] = sy[e];
+  double acc[kRPW];
+  for (int r0 = 0; r0 < K; r0 += kChunk) {
+    zero(acc);
+    for (int q = 0; q < nf; ++q) rows_acc<double, kRPW>(r0, S + (p0 + q) * K * K, K, K, K, smv + q * K, acc);
+    rows_finish<double, kRPW>(r0, K, acc, 1.0, nullptr, yh + (int64_t)i * K);
+  }
 }
 void launch_matvec_far(const DevLevel& L, const double* xh, double* yh, cudaStream_t st) {
+  size_t sm = sizeof(double) * (size_t)L.K * std::max(L.max_far, 1);
+  set_smem((const void*)mv_far_kernel, sm);
   ++g_launches;
-  mv_far_kernel<<<L.nb, 256, sizeof(double) * 2 * L.K, st>>>(L.K, L.far_ptr, L.far_j, L.S, xh, yh);
+  mv_far_kernel<<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, L.S, xh, yh);
 }
 
 // downward: [yh_2p; yh_2p+1] += X_p yh_p   (rows d of X_p, D = 2 Kc)
@@ -330,35 +458,32 @@ void launch_matvec_down(const DevLevel& L, const double* yh, double* yh_child, c
 }
 
 // leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j
-__global__ void __launch_bounds__(256) mv_leaf_kernel(int D, int K, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256, 2) mv_leaf_kernel(int D, int K, const int64_t* __restrict__ ptr,
                                                       const int32_t* __restrict__ nj, const double* __restrict__ A,
                                                       const double* __restrict__ X, const double* __restrict__ x,
                                                       const double* __restrict__ yh, double* __restrict__ y) {
-  extern __shared__ double smv[];
-  double* sx = smv;      // max(D, K)
-  double* sy = smv + D;  // D
+  extern __shared__ __align__(16) double smv[];  // K + nn * D
   const int i = blockIdx.x, tid = threadIdx.x;
-  for (int e = tid; e < D; e += blockDim.x) sy[e] = 0;
-  if (yh) {
-    for (int e = tid; e < K; e += blockDim.x) sx[e] = yh[(int64_t)i * K + e];
-    __syncthreads();
-    warp_rows_gemv<double>(X + (int64_t)i * D * K, K, D, K, sx, sy, 1.0);
-  }
-  for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
-    const int j = nj[p];
-    __syncthreads();
-    for (int e = tid; e < D; e += blockDim.x) sx[e] = x[(int64_t)j * D + e];
-    __syncthreads();
-    warp_rows_gemv<double>(A + p * D * D, D, D, D, sx, sy, 1.0);
-  }
+  const int64_t p0 = ptr[i];
+  const int nn = (int)(ptr[i + 1] - p0);
+  double* sh = smv;
+  double* sx = smv + ((K + 1) & ~1);
+  if (yh)
+    for (int e = tid; e < K; e += blockDim.x) sh[e] = yh[(int64_t)i * K + e];
+  for (int e = tid; e < nn * D; e += blockDim.x) sx[e] = x[(int64_t)nj[p0 + e / D] * D + e % D];
   __syncthreads();
-  for (int e = tid; e < D; e += blockDim.x) y[(int64_t)i * D + e] = sy[e];
+  double acc[kRPW];
+  for (int r0 = 0; r0 < D; r0 += kChunk) {
+    zero(acc);
+    if (yh) rows_acc<double, kRPW>(r0, X + (int64_t)i * D * K, K, D, K, sh, acc);
+    for (int q = 0; q < nn; ++q) rows_acc<double, kRPW>(r0, A + (p0 + q) * D * D, D, D, D, sx + q * D, acc);
+    rows_finish<double, kRPW>(r0, D, acc, 1.0, nullptr, y + (int64_t)i * D);
+  }
 }
 void launch_matvec_leaf(const DevLevel& L, const double* A, const double* x, const double* yh, double* y,
                         cudaStream_t st) {
-  int sx = std::max(L.D, L.K);
-  const size_t sm = sizeof(double) * (size_t)(sx + L.D);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(mv_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = sizeof(double) * ((size_t)((L.K + 1) & ~1) + (size_t)L.D * L.max_near);
+  set_smem((const void*)mv_leaf_kernel, sm);
   ++g_launches;
   mv_leaf_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, A, L.X, x, yh, y);
 }
