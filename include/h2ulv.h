@@ -206,6 +206,27 @@ h2_status h2_matvec(h2_ctx* c, const double* x, double* y);
  * (1..1000; default 1 with restart 30).  Errors: H2_ERR_INVALID_ARG. */
 h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart);
 
+/* y = A_H2 x like h2_matvec, for callers that must not allocate device
+ * memory once their context exists (a host framework that owns all device
+ * memory and forbids library allocations, or a loop on a latency budget
+ * where cudaMalloc / cudaFree may block or synchronize).  No counterpart in
+ * the paper: this is a service of the library, not a step of the method.
+ *   - x and y: device pointers, N doubles, original point order; the call
+ *     allocates nothing and only enqueues work on the context's stream
+ *     (y is ready when that stream reaches this point).
+ *   - Scratch comes from one fixed 16 MiB device array inside the library
+ *     (2^21 doubles); problems needing more (2 padded vectors plus the
+ *     skeleton coefficients of every level) are rejected with
+ *     H2_ERR_INVALID_ARG.  A GPU holds the array from the first call on that
+ *     device until the process exits.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.  The context's device must be current.
+ *   - All calls share the array: calls whose work overlaps on the GPU race.
+ * Errors: H2_ERR_INVALID_ARG (NULL or host pointers, wrong device, too
+ * large), H2_ERR_CUDA. */
+h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
+
 /* Issue all later work on the given cudaStream_t (NULL: legacy default). */
 h2_status h2_set_stream(h2_ctx* c, void* stream);
 

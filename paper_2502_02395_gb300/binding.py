@@ -28,6 +28,7 @@ STATUS = {0: "H2_OK", -1: "H2_ERR_INVALID_ARG", -2: "H2_ERR_OOM", -3: "H2_ERR_SI
 
 # every symbol include/h2ulv.h declares
 EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_ulv_apply", "h2_matvec",
+            "h2_matvec_noalloc",
             "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
 
 
@@ -73,6 +74,7 @@ def lib() -> ctypes.CDLL:
             "h2_solve": (i32, [vp, vp, vp, dbl, i32, vp, vp]),
             "h2_ulv_apply": (i32, [vp, vp, vp]),
             "h2_matvec": (i32, [vp, vp, vp]),
+            "h2_matvec_noalloc": (i32, [vp, vp, vp]),
             "h2_set_refinement": (i32, [vp, i32, i32]),
             "h2_set_stream": (i32, [vp, vp]),
             "h2_stats": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
@@ -182,6 +184,12 @@ def h2_ulv_apply(ctx, b, x):
 
 def h2_matvec(ctx, x, y):
     _check(lib().h2_matvec(ctx, _ptr(x), _ptr(y)), ctx)
+
+
+def h2_matvec_noalloc(ctx, x, y):
+    """y = A_H2 x with x, y CUDA tensors; the library allocates nothing for
+    this call (its scratch is a fixed array inside the library)."""
+    _check(lib().h2_matvec_noalloc(ctx, _ptr(x), _ptr(y)), ctx)
 
 
 def h2_set_refinement(ctx, method: str | int = "gmres", restart: int = 30):
