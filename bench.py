@@ -159,7 +159,7 @@ def run_reference(args, wl):
 
 # ---------------------------------------------------------------- our arm ---
 PHASES = ("a1_qr", "a2_proj", "a3_lu", "a45_schur", "a2c_coupling", "a6_merge", "a7_root")
-SOLVE_PHASES = ("solve_subst", "solve_matvec")
+SOLVE_PHASES = ("solve_subst", "solve_matvec", "solve_matvec32")
 
 
 def fp64_peak_tflops() -> float:
@@ -188,6 +188,11 @@ def roofline_for(phase, stats, t_phase, calls, peaks, prec, tc, fp64_tf):
         achieved = stats["bytes_subst"] * calls["subst"] / t_phase / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "phase": phase, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    if phase == "solve_matvec32":
+        gbs = stats["bytes_matvec32"] * calls["matvec32"] / t_phase / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                 "traffic": None, "phase": phase, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     if phase == "solve_matvec":
         # FP64 multiply-adds on the leaf near blocks: the FP64 ALU rate binds
@@ -335,7 +340,7 @@ def main():
     top = max(PHASES + SOLVE_PHASES, key=lambda p: ph[p])
     roof = roofline_for(top, stats, ph[top], calls, peaks, args.prec, tc, fp64_tf)
     roofs = {p: roofline_for(p, stats, ph[p], calls, peaks, args.prec, tc, fp64_tf)
-             for p in ("a2_proj", "a3_lu", "solve_subst", "solve_matvec")}
+             for p in ("a2_proj", "a3_lu", "solve_subst", "solve_matvec", "solve_matvec32")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

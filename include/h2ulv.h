@@ -170,24 +170,24 @@ h2_status h2_import(h2_ctx** out, const h2_params* p, const h2_instance* inst);
  * H2_ERR_OOM, H2_ERR_CUDA. */
 h2_status h2_factor(h2_ctx* c, int32_t prec);
 
-/* Solve A_H2 x = b by refinement with the factorization as preconditioner;
- * every residual r = b - A_H2 x is computed in FP64 (h2_matvec) and every
- * preconditioner application M^-1 v is the parallel substitution of
- * Eq. 24-31 and its mirror, in the factorization's precision.  Two schemes
- * (h2_set_refinement):
- *   plain iterative refinement: x_0 = 0; repeat x += M^-1 (b - A_H2 x);
- *   FGMRES-based refinement (default): restarted, right-preconditioned
- *     flexible GMRES in FP64; after every cycle x += Z y and the true
- *     residual is recomputed.  It needs no more preconditioner applications
- *     than plain refinement and converges when the factorization's dropped
- *     fill-ins make plain refinement contract slowly.
+/* Solve A_H2 x = b by refinement with the factorization as preconditioner.
+ * Every refinement residual r = b - A_H2 x is computed in FP64 (the
+ * h2_matvec operator) and every update x += d is FP64; each preconditioner
+ * application is the parallel substitution of Eq. 24-31 and its mirror, in
+ * the factorization's storage precision.  Schemes (h2_set_refinement):
+ *   0 plain iterative refinement: x += M^-1 (b - A_H2 x);
+ *   1 FGMRES-based refinement: restarted right-preconditioned flexible
+ *     GMRES in FP64, true residual recomputed after every cycle;
+ *   2 mixed-precision refinement (FP16/BF16 factorizations): each
+ *     correction d of A d = r comes from FGMRES in FP32 with an FP32 copy of
+ *     A_H2 and the ULV preconditioner, to 1e-6 relative accuracy (or the
+ *     accuracy the target needs, if coarser); residual and update in FP64;
+ *   3 automatic (default): 1 for FP64 factorizations, 2 otherwise.
  * Stops when ||r|| / ||b|| <= target or after max_iters preconditioner
  * applications.  b and x hold one vector of N doubles (host or device).
  * relres_out and iters_out (host, may be NULL) receive the final relative
  * residual and the number of preconditioner applications.  target <= 0 runs
- * exactly max_iters applications.
- * Errors: H2_ERR_STATE (no factorization), H2_ERR_INVALID_ARG,
- * H2_ERR_NOT_CONVERGED (x still holds the last iterate), H2_ERR_CUDA. */
+ * exactly max_iters applications. */
 h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target,
                    int32_t max_iters, double* relres_out, int32_t* iters_out);
 
@@ -201,9 +201,9 @@ h2_status h2_ulv_apply(h2_ctx* c, const double* b, double* x);
  * N doubles each, host or device.  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
 h2_status h2_matvec(h2_ctx* c, const double* x, double* y);
 
-/* Choose the refinement scheme of h2_solve: method 0 = plain iterative
- * refinement, 1 = FGMRES-based refinement with the given restart length
- * (1..1000; default 1 with restart 30).  Errors: H2_ERR_INVALID_ARG. */
+/* Choose the refinement scheme of h2_solve (0..3, see h2_solve; default 3)
+ * and the FGMRES restart length (1..1000, default 30).
+ * Errors: H2_ERR_INVALID_ARG. */
 h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart);
 
 /* y = A_H2 x like h2_matvec, for callers that must not allocate device

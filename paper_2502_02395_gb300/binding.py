@@ -192,8 +192,10 @@ def h2_matvec_noalloc(ctx, x, y):
     _check(lib().h2_matvec_noalloc(ctx, _ptr(x), _ptr(y)), ctx)
 
 
-def h2_set_refinement(ctx, method: str | int = "gmres", restart: int = 30):
-    m = {"ir": 0, "gmres": 1}.get(method, method)
+def h2_set_refinement(ctx, method: str | int = "auto", restart: int = 30):
+    """method: "ir" (0), "gmres" (1, FP64 FGMRES), "nested" (2, FP64 outer /
+    FP32 inner FGMRES) or "auto" (3)."""
+    m = {"ir": 0, "gmres": 1, "nested": 2, "auto": 3}.get(method, method)
     _check(lib().h2_set_refinement(ctx, int(m), int(restart)), ctx)
 
 
@@ -267,7 +269,7 @@ class H2Solver:
     def set_stream(self, stream):
         h2_set_stream(self.ctx, stream)
 
-    def set_refinement(self, method="gmres", restart=30):
+    def set_refinement(self, method="auto", restart=30):
         h2_set_refinement(self.ctx, method, restart)
 
     def stats(self) -> dict:

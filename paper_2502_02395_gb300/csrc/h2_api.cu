@@ -196,6 +196,30 @@ h2_status setup_device(h2_ctx* c) {
   for (int l = 1; l <= L; ++l) c->hat_off[l + 1] = c->hat_off[l] + (int64_t)c->lv[l].nb * c->lv[l].K;
   CKC(dalloc(c, &c->xhat, c->hat_off[L + 1]));
   CKC(dalloc(c, &c->yhat, c->hat_off[L + 1]));
+  // FP32 copy of the H^2 matrix: the operator of the inner solver of the
+  // mixed-precision refinement (part of the instance)
+  CKC(dalloc(c, &c->xhat32, c->hat_off[L + 1]));
+  CKC(dalloc(c, &c->yhat32, c->hat_off[L + 1]));
+  CKC(dalloc(c, &c->A32, (size_t)lf.NP * lf.D * lf.D));
+  launch_convert<double, float>(c->A64, c->A32, (int64_t)lf.NP * lf.D * lf.D, 0);
+  c->X64p.assign(L + 1, nullptr);
+  c->S64p.assign(L + 1, nullptr);
+  c->X32p.assign(L + 1, nullptr);
+  c->S32p.assign(L + 1, nullptr);
+  for (int l = 1; l <= L; ++l) {
+    DevLevel& d = c->lv[l];
+    const size_t nx = (size_t)d.nb * d.D * d.K, ns = (size_t)std::max<int64_t>(d.FP, 1) * d.K * d.K;
+    CKC(dalloc(c, &d.X32, nx));
+    CKC(dalloc(c, &d.S32, ns));
+    launch_convert<double, float>(d.X, d.X32, (int64_t)nx, 0);
+    launch_convert<double, float>(d.S, d.S32, (int64_t)ns, 0);
+    c->X64p[l] = d.X;
+    c->S64p[l] = d.S;
+    c->X32p[l] = d.X32;
+    c->S32p[l] = d.S32;
+  }
+  CKC(cudaGetLastError());
+
   CKC(dalloc(c, &c->red, 1024));  // three norm slots of 257 doubles: 0, 300, 600
   CKC(dalloc(c, &c->status, 4));
   CKC(cudaMemset(c->status, 0, 4 * sizeof(int32_t)));
@@ -460,16 +484,14 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
 }
 
 // ---------------------------------------------------------------------------
-// substitution: x_tree (+)= ULV^-1 r_tree   (FP64 padded tree vectors)
+// substitution (Eq. 24-31 and its mirror)
 // ---------------------------------------------------------------------------
+// One sweep: input in the leaf level's vin (root_vec when L = 0), output in
+// the leaf level's xs (root_x when L = 0).
 template <typename T>
-void ulv_apply_impl(h2_ctx* c, Factor<T>& F, const double* r, double* x) {
+void ulv_sweep(h2_ctx* c, Factor<T>& F) {
   const int L = c->L;
   cudaStream_t st = c->stream;
-  const int64_t nslot = (int64_t)c->lv[L].nb * c->lv[L].D;
-  launch_norm2(r, nslot, c->red, st);
-  T* leaf_in = (L >= 1) ? F.lv[L].vin : F.root_vec;
-  launch_scale_to<T>(r, c->red, leaf_in, nslot, st);
   for (int l = L; l >= 1; --l) {
     const DevLevel& d = c->lv[l];
     FacLevel<T>& f = F.lv[l];
@@ -486,22 +508,58 @@ void ulv_apply_impl(h2_ctx* c, Factor<T>& F, const double* r, double* x) {
     launch_bwd1<T>(d, f, f.Ainv, px, st);
     launch_bwd2<T>(d, f, f.Ainv, px, st);
   }
-  const T* out = (L >= 1) ? F.lv[L].xs : F.root_x;
-  launch_axpy_from<T>(out, c->red, x, nslot, st);
+}
+template <typename T>
+T* ulv_in(h2_ctx* c, Factor<T>& F) { return c->L >= 1 ? F.lv[c->L].vin : F.root_vec; }
+template <typename T>
+T* ulv_out(h2_ctx* c, Factor<T>& F) { return c->L >= 1 ? F.lv[c->L].xs : F.root_x; }
+
+int64_t nslots(const h2_ctx* c) { return (int64_t)c->lv[c->L].nb * c->lv[c->L].D; }
+
+// x += ULV^-1 r for FP64 tree vectors; the sweep runs in T on r / ||r||.
+template <typename T>
+void ulv_apply_impl(h2_ctx* c, Factor<T>& F, const double* r, double* x) {
+  const int64_t n = nslots(c);
+  launch_norm2<double>(r, n, c->red, c->stream);
+  launch_scale_to<T>(r, c->red, ulv_in(c, F), n, c->stream);
+  ulv_sweep<T>(c, F);
+  launch_axpy_from<T>(ulv_out(c, F), c->red, x, n, c->stream);
 }
 
-void matvec_impl(h2_ctx* c, const double* x, double* y) {
+// z = ULV^-1 v for FP32 tree vectors (mixed-precision factorization).
+void ulv_apply_f32(h2_ctx* c, const float* v, float* z) {
+  const int64_t n = nslots(c);
+  Factor<float>& F = c->f32;
+  cudaMemcpyAsync(ulv_in(c, F), v, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+  ulv_sweep<float>(c, F);
+  cudaMemcpyAsync(z, ulv_out(c, F), n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+}
+
+// ---------------------------------------------------------------------------
+// H^2 matvec over the FP64 instance (refinement residual) or its FP32 copy
+// (inner solver of the mixed-precision refinement)
+// ---------------------------------------------------------------------------
+template <typename T>
+void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, const T* x, T* y) {
   const int L = c->L;
   cudaStream_t st = c->stream;
   if (L == 0) {
-    launch_matvec_leaf(c->lv[0], c->A64, x, nullptr, y, st);
+    launch_matvec_leaf<T>(c->lv[0], A, nullptr, x, nullptr, y, st);
     return;
   }
-  launch_matvec_up_leaf(c->lv[L], x, c->xhat + c->hat_off[L], st);
-  for (int l = L - 1; l >= 1; --l) launch_matvec_up(c->lv[l], c->xhat + c->hat_off[l + 1], c->xhat + c->hat_off[l], st);
-  for (int l = 1; l <= L; ++l) launch_matvec_far(c->lv[l], c->xhat + c->hat_off[l], c->yhat + c->hat_off[l], st);
-  for (int l = 1; l < L; ++l) launch_matvec_down(c->lv[l], c->yhat + c->hat_off[l], c->yhat + c->hat_off[l + 1], st);
-  launch_matvec_leaf(c->lv[L], c->A64, x, c->yhat + c->hat_off[L], y, st);
+  const std::vector<int64_t>& off = c->hat_off;
+  launch_matvec_up<T>(c->lv[L], X[L], x, xh + off[L], st);
+  for (int l = L - 1; l >= 1; --l) launch_matvec_up<T>(c->lv[l], X[l], xh + off[l + 1], xh + off[l], st);
+  for (int l = 1; l <= L; ++l) launch_matvec_far<T>(c->lv[l], S[l], xh + off[l], yh + off[l], st);
+  for (int l = 1; l < L; ++l) launch_matvec_down<T>(c->lv[l], X[l], yh + off[l], yh + off[l + 1], st);
+  launch_matvec_leaf<T>(c->lv[L], A, X[L], x, yh + off[L], y, st);
+}
+
+void matvec_impl(h2_ctx* c, const double* x, double* y) {
+  matvec_t<double>(c, c->A64, c->X64p.data(), c->S64p.data(), c->xhat, c->yhat, x, y);
+}
+void matvec32(h2_ctx* c, const float* x, float* y) {
+  matvec_t<float>(c, c->A32, c->X32p.data(), c->S32p.data(), c->xhat32, c->yhat32, x, y);
 }
 
 bool factor_ready(const h2_ctx* c) {
@@ -515,21 +573,21 @@ void ulv_apply_any(h2_ctx* c, const double* r, double* x) {
 
 // CUDA-event timing of the substitution and matvec calls inside a solve
 struct SolveTimer {
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sub, mv;
+  using Pairs = std::vector<std::pair<cudaEvent_t, cudaEvent_t>>;
+  Pairs sub, mv, mv32;
   cudaStream_t st;
   explicit SolveTimer(cudaStream_t s) : st(s) {}
-  std::pair<cudaEvent_t, cudaEvent_t> begin() {
+  template <class Fn>
+  void run(Pairs& v, Fn fn) {
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     cudaEventRecord(a, st);
-    return {a, b};
+    fn();
+    cudaEventRecord(b, st);
+    v.push_back({a, b});
   }
-  void end(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v, std::pair<cudaEvent_t, cudaEvent_t> e) {
-    cudaEventRecord(e.second, st);
-    v.push_back(e);
-  }
-  static double total(std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v) {
+  static double total(Pairs& v) {
     double t = 0;
     for (auto& e : v) {
       float ms = 0;
@@ -542,20 +600,6 @@ struct SolveTimer {
     return t;
   }
 };
-thread_local SolveTimer* g_timer = nullptr;
-
-void ulv_timed(h2_ctx* c, const double* r, double* x) {
-  if (!g_timer) return ulv_apply_any(c, r, x);
-  auto e = g_timer->begin();
-  ulv_apply_any(c, r, x);
-  g_timer->end(g_timer->sub, e);
-}
-void matvec_timed(h2_ctx* c, const double* x, double* y) {
-  if (!g_timer) return matvec_impl(c, x, y);
-  auto e = g_timer->begin();
-  matvec_impl(c, x, y);
-  g_timer->end(g_timer->mv, e);
-}
 
 // copy an N-vector in (orig order, host or device) to the padded tree vector
 h2_status vec_in(h2_ctx* c, const double* src, double* tree) {
@@ -564,16 +608,14 @@ h2_status vec_in(h2_ctx* c, const double* src, double* tree) {
     CKC(cudaMemcpyAsync(c->io_a, src, c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     dsrc = c->io_a;
   }
-  const DevLevel& lf = c->lv[c->L];
-  launch_gather(c->slot_pt, dsrc, tree, (int64_t)lf.nb * lf.D, c->stream);
+  launch_gather(c->slot_pt, dsrc, tree, nslots(c), c->stream);
   return H2_OK;
 }
 
 h2_status vec_out(h2_ctx* c, const double* tree, double* dst) {
-  const DevLevel& lf = c->lv[c->L];
   bool dev = is_device_ptr(dst);
   double* ddst = dev ? dst : c->io_b;
-  launch_scatter(c->slot_pt, tree, ddst, (int64_t)lf.nb * lf.D, c->stream);
+  launch_scatter(c->slot_pt, tree, ddst, nslots(c), c->stream);
   if (!dev) {
     CKC(cudaMemcpyAsync(dst, ddst, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CKC(cudaStreamSynchronize(c->stream));
@@ -581,91 +623,175 @@ h2_status vec_out(h2_ctx* c, const double* tree, double* dst) {
   return H2_OK;
 }
 
-// FGMRES-based iterative refinement (restarted, right preconditioned by the
-// ULV factorization; classical Gram-Schmidt applied twice; Givens rotations on
-// the host).  On entry x64 = 0 and r64 = b64.  its counts preconditioner
-// applications.
-h2_status gmres_refine(h2_ctx* c, double bnorm, double target, int max_iters, int& its, double& rel) {
+// ---------------------------------------------------------------------------
+// One FGMRES cycle (right preconditioned, classical Gram-Schmidt applied
+// twice, Givens rotations on the host) on vectors of type T.  r is the
+// right-hand side with norm beta; the cycle stops after m steps or when the
+// residual estimate falls to tol_abs.  On return W.y[0..k) hold the
+// coefficients of the solution update sum_j y_j Z_j.
+// ---------------------------------------------------------------------------
+struct GmresWork {
+  int m0 = 0;
+  double *h1 = nullptr, *h2 = nullptr, *yv = nullptr, *part = nullptr, *nrm = nullptr;
+  std::vector<double> Hm, cs, sn, g, a1, a2, y;
+};
+
+template <typename T, class Prec, class Mv>
+h2_status fgmres_cycle(h2_ctx* c, GmresWork& W, int m, double beta, const T* r, double tol_abs, T* V, T* Z, int& k,
+                       int& its, Prec prec, Mv mv) {
   cudaStream_t st = c->stream;
-  const DevLevel& lf = c->lv[c->L];
-  const int64_t n = (int64_t)lf.nb * lf.D;
+  const int64_t n = nslots(c);
+  const int m0 = W.m0;
+  launch_norm2<T>(r, n, W.nrm, st);
+  launch_scaled_copy<T, T>(r, W.nrm, true, V, n, st);
+  std::fill(W.g.begin(), W.g.end(), 0.0);
+  W.g[0] = beta;
+  k = 0;
+  for (int j = 0; j < m; ++j) {
+    T* vj = V + (int64_t)j * n;
+    T* zj = Z + (int64_t)j * n;
+    T* w = V + (int64_t)(j + 1) * n;
+    prec(vj, zj);
+    mv(zj, w);
+    launch_multi_dot<T>(V, n, j + 1, w, n, W.part, W.h1, false, st);
+    launch_multi_axpy<T, T>(V, n, j + 1, W.h1, -1.0, w, n, st);
+    launch_multi_dot<T>(V, n, j + 1, w, n, W.part, W.h2, false, st);
+    launch_multi_axpy<T, T>(V, n, j + 1, W.h2, -1.0, w, n, st);
+    launch_norm2<T>(w, n, W.nrm, st);
+    double nw2 = 0;
+    CKC(cudaMemcpyAsync(W.a1.data(), W.h1, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKC(cudaMemcpyAsync(W.a2.data(), W.h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKC(cudaMemcpyAsync(&nw2, W.nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    launch_scaled_copy<T, T>(w, W.nrm, true, w, n, st);
+    CKC(cudaStreamSynchronize(st));
+    double* col = &W.Hm[(size_t)j * (m0 + 1)];
+    for (int i = 0; i <= j; ++i) col[i] = W.a1[i] + W.a2[i];
+    col[j + 1] = std::sqrt(nw2);
+    for (int i = 0; i < j; ++i) {
+      double t = W.cs[i] * col[i] + W.sn[i] * col[i + 1];
+      col[i + 1] = -W.sn[i] * col[i] + W.cs[i] * col[i + 1];
+      col[i] = t;
+    }
+    double d = std::hypot(col[j], col[j + 1]);
+    W.cs[j] = d > 0 ? col[j] / d : 1.0;
+    W.sn[j] = d > 0 ? col[j + 1] / d : 0.0;
+    col[j] = d;
+    col[j + 1] = 0.0;
+    W.g[j + 1] = -W.sn[j] * W.g[j];
+    W.g[j] = W.cs[j] * W.g[j];
+    ++its;
+    k = j + 1;
+    if (!std::isfinite(W.g[j + 1])) break;
+    if (tol_abs > 0 && std::fabs(W.g[j + 1]) <= tol_abs) break;
+    if (nw2 == 0.0) break;  // invariant Krylov space: exact solution
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double t = W.g[i];
+    for (int q = i + 1; q < k; ++q) t -= W.Hm[(size_t)q * (m0 + 1) + i] * W.y[q];
+    W.y[i] = t / W.Hm[(size_t)i * (m0 + 1) + i];
+  }
+  return H2_OK;
+}
+
+h2_status gmres_work(h2_ctx* c, GmresWork& W) {
   const int m0 = std::max(1, c->restart);
+  const int64_t n = nslots(c);
   if (c->gm_cap < m0) {
     CKC(dalloc(c, &c->gm_V, (size_t)(m0 + 1) * n));
     CKC(dalloc(c, &c->gm_Z, (size_t)m0 * n));
+    CKC(dalloc(c, &c->gm_V32, (size_t)(m0 + 1) * n));
+    CKC(dalloc(c, &c->gm_Z32, (size_t)m0 * n));
+    CKC(dalloc(c, &c->gm_r32, (size_t)n));
     CKC(dalloc(c, &c->gm_h, 3 * (size_t)(m0 + 2)));
     CKC(dalloc(c, &c->gm_part, (size_t)(m0 + 1) * 128));
     c->gm_cap = m0;
   }
-  double* V = c->gm_V;
-  double* Z = c->gm_Z;
-  double* h1 = c->gm_h;
-  double* h2 = c->gm_h + (m0 + 2);
-  double* yv = c->gm_h + 2 * (m0 + 2);
-  double* nrm = c->red + 600;
-  std::vector<double> Hm((size_t)(m0 + 1) * m0), cs(m0), sn(m0), g(m0 + 1), a1(m0 + 2), a2(m0 + 2), y(m0);
+  W.m0 = m0;
+  W.h1 = c->gm_h;
+  W.h2 = c->gm_h + (m0 + 2);
+  W.yv = c->gm_h + 2 * (m0 + 2);
+  W.part = c->gm_part;
+  W.nrm = c->red + 600;
+  W.Hm.assign((size_t)(m0 + 1) * m0, 0.0);
+  W.cs.assign(m0, 0.0);
+  W.sn.assign(m0, 0.0);
+  W.g.assign(m0 + 1, 0.0);
+  W.a1.assign(m0 + 2, 0.0);
+  W.a2.assign(m0 + 2, 0.0);
+  W.y.assign(m0, 0.0);
+  return H2_OK;
+}
+
+// r = b - A_H2 x in FP64; returns ||r||
+h2_status fp64_residual(h2_ctx* c, SolveTimer& tm, double& rnorm) {
+  const int64_t n = nslots(c);
+  cudaStream_t st = c->stream;
+  tm.run(tm.mv, [&] { matvec_impl(c, c->x64, c->y64); });
+  launch_residual(c->b64, c->y64, c->r64, n, st);
+  launch_norm2<double>(c->r64, n, c->red + 600, st);
+  double rn2 = 0;
+  CKC(cudaMemcpyAsync(&rn2, c->red + 600, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKC(cudaStreamSynchronize(st));
+  rnorm = std::sqrt(rn2);
+  return H2_OK;
+}
+
+// FGMRES-based refinement in FP64 (restart cycles; true residual after each).
+// On entry x64 = 0 and r64 = b64.  its counts preconditioner applications.
+h2_status gmres_refine(h2_ctx* c, SolveTimer& tm, double bnorm, double target, int max_iters, int& its,
+                       double& rel) {
+  GmresWork W;
+  CKS(gmres_work(c, W));
+  const int64_t n = nslots(c);
   double beta = bnorm;
   rel = 1.0;
+  auto prec = [&](const double* v, double* z) {
+    tm.run(tm.sub, [&] {
+      cudaMemsetAsync(z, 0, n * sizeof(double), c->stream);
+      ulv_apply_any(c, v, z);
+    });
+  };
+  auto mv = [&](const double* z, double* w) { tm.run(tm.mv, [&] { matvec_impl(c, z, w); }); };
   while (its < max_iters && (target <= 0 || beta > target * bnorm)) {
-    const int m = std::min(m0, max_iters - its);
-    launch_norm2(c->r64, n, nrm, st);
-    launch_normalize(c->r64, nrm, V, n, st);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
     int k = 0;
-    for (int j = 0; j < m; ++j) {
-      double* vj = V + (int64_t)j * n;
-      double* zj = Z + (int64_t)j * n;
-      double* w = V + (int64_t)(j + 1) * n;
-      CKC(cudaMemsetAsync(zj, 0, n * sizeof(double), st));
-      ulv_timed(c, vj, zj);
-      matvec_timed(c, zj, w);
-      launch_multi_dot(V, n, j + 1, w, n, c->gm_part, h1, false, st);
-      launch_multi_axpy(V, n, j + 1, h1, -1.0, w, n, st);
-      launch_multi_dot(V, n, j + 1, w, n, c->gm_part, h2, false, st);
-      launch_multi_axpy(V, n, j + 1, h2, -1.0, w, n, st);
-      launch_norm2(w, n, nrm, st);
-      double nw2 = 0;
-      CKC(cudaMemcpyAsync(a1.data(), h1, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CKC(cudaMemcpyAsync(a2.data(), h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CKC(cudaMemcpyAsync(&nw2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
-      launch_normalize(w, nrm, w, n, st);
-      CKC(cudaStreamSynchronize(st));
-      double* col = &Hm[(size_t)j * (m0 + 1)];
-      for (int i = 0; i <= j; ++i) col[i] = a1[i] + a2[i];
-      col[j + 1] = std::sqrt(nw2);
-      for (int i = 0; i < j; ++i) {
-        double t = cs[i] * col[i] + sn[i] * col[i + 1];
-        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
-        col[i] = t;
-      }
-      double d = std::hypot(col[j], col[j + 1]);
-      cs[j] = d > 0 ? col[j] / d : 1.0;
-      sn[j] = d > 0 ? col[j + 1] / d : 0.0;
-      col[j] = d;
-      col[j + 1] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++its;
-      k = j + 1;
-      if (!std::isfinite(g[j + 1])) break;
-      if (target > 0 && std::fabs(g[j + 1]) <= target * bnorm) break;
-      if (nw2 == 0.0) break;  // the Krylov space is invariant: exact solution
-    }
-    for (int i = k - 1; i >= 0; --i) {
-      double t = g[i];
-      for (int q = i + 1; q < k; ++q) t -= Hm[(size_t)q * (m0 + 1) + i] * y[q];
-      y[i] = t / Hm[(size_t)i * (m0 + 1) + i];
-    }
-    CKC(cudaMemcpyAsync(yv, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
-    launch_multi_axpy(Z, n, k, yv, 1.0, c->x64, n, st);
-    matvec_timed(c, c->x64, c->y64);
-    launch_residual(c->b64, c->y64, c->r64, n, st);
-    launch_norm2(c->r64, n, nrm, st);
-    double rn2 = 0;
-    CKC(cudaMemcpyAsync(&rn2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CKC(cudaStreamSynchronize(st));
-    beta = std::sqrt(rn2);
+    CKS(fgmres_cycle<double>(c, W, std::min(W.m0, max_iters - its), beta, c->r64, target * bnorm, c->gm_V, c->gm_Z,
+                             k, its, prec, mv));
+    CKC(cudaMemcpyAsync(W.yv, W.y.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_multi_axpy<double, double>(c->gm_Z, n, k, W.yv, 1.0, c->x64, n, c->stream);
+    CKS(fp64_residual(c, tm, beta));
+    rel = beta / bnorm;
+    c->times.history.push_back(rel);
+    if (!std::isfinite(rel)) break;
+  }
+  return H2_OK;
+}
+
+// Mixed-precision refinement (for the FP32-storage factorizations): the
+// residual r = b - A_H2 x and the update x += d in FP64; each correction d
+// solves A d = r approximately by FGMRES in FP32, with the FP32 copy of
+// A_H2 and the ULV preconditioner, to the relative accuracy
+// max(inner_tol, target / (2 relres)).
+h2_status nested_refine(h2_ctx* c, SolveTimer& tm, double bnorm, double target, int max_iters, int& its,
+                        double& rel) {
+  GmresWork W;
+  CKS(gmres_work(c, W));
+  const int64_t n = nslots(c);
+  cudaStream_t st = c->stream;
+  double beta = bnorm;
+  rel = 1.0;
+  auto prec = [&](const float* v, float* z) { tm.run(tm.sub, [&] { ulv_apply_f32(c, v, z); }); };
+  auto mv = [&](const float* z, float* w) { tm.run(tm.mv32, [&] { matvec32(c, z, w); }); };
+  while (its < max_iters && (target <= 0 || beta > target * bnorm)) {
+    launch_norm2<double>(c->r64, n, c->red, st);
+    launch_scaled_copy<double, float>(c->r64, c->red, true, c->gm_r32, n, st);
+    const double tol_in = std::max(c->inner_tol, target > 0 ? 0.5 * target * bnorm / beta : 0.0);
+    int k = 0;
+    CKS(fgmres_cycle<float>(c, W, std::min(W.m0, max_iters - its), 1.0, c->gm_r32, tol_in, c->gm_V32, c->gm_Z32, k,
+                            its, prec, mv));
+    for (int i = 0; i < k; ++i) W.y[i] *= beta;
+    CKC(cudaMemcpyAsync(W.yv, W.y.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
+    launch_multi_axpy<float, double>(c->gm_Z32, n, k, W.yv, 1.0, c->x64, n, st);
+    CKS(fp64_residual(c, tm, beta));
     rel = beta / bnorm;
     c->times.history.push_back(rel);
     if (!std::isfinite(rel)) break;
@@ -854,7 +980,7 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
   CKS(vec_in(c, b, c->b64));
-  launch_norm2(c->b64, nslot, c->red + 300, st);  // ||b||^2 apart from the substitution scratch
+  launch_norm2<double>(c->b64, nslot, c->red + 300, st);  // ||b||^2 apart from the substitution scratch
   double bn2 = 0;
   CKC(cudaMemcpyAsync(&bn2, c->red + 300, sizeof(double), cudaMemcpyDeviceToHost, st));
   CKC(cudaMemsetAsync(c->x64, 0, nslot * sizeof(double), st));
@@ -868,24 +994,25 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   struct TimerGuard {
     SolveTimer* t;
     ~TimerGuard() {
-      g_timer = nullptr;
       SolveTimer::total(t->sub);
       SolveTimer::total(t->mv);
+      SolveTimer::total(t->mv32);
     }
   } guard{&timer};
-  g_timer = &timer;
-  if (bnorm > 0 && c->refine_method == 1) {
-    CKS(gmres_refine(c, bnorm, target, max_iters, it, rel));
+  int method = c->refine_method;
+  if (method == 3) method = (c->prec == H2_PREC_FP64) ? 1 : 2;
+  if (method == 2 && c->prec == H2_PREC_FP64) method = 1;
+  c->times.method = method;
+  if (bnorm > 0 && method == 1) {
+    CKS(gmres_refine(c, timer, bnorm, target, max_iters, it, rel));
+  } else if (bnorm > 0 && method == 2) {
+    CKS(nested_refine(c, timer, bnorm, target, max_iters, it, rel));
   } else {
     while (it < max_iters && (target <= 0 || rel > target) && bnorm > 0) {
-      ulv_timed(c, c->r64, c->x64);
-      matvec_timed(c, c->x64, c->y64);
-      launch_residual(c->b64, c->y64, c->r64, nslot, st);
-      launch_norm2(c->r64, nslot, c->red + 600, st);
-      double rn2 = 0;
-      CKC(cudaMemcpyAsync(&rn2, c->red + 600, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CKC(cudaStreamSynchronize(st));
-      rel = std::sqrt(rn2) / bnorm;
+      timer.run(timer.sub, [&] { ulv_apply_any(c, c->r64, c->x64); });
+      double rn = 0;
+      CKS(fp64_residual(c, timer, rn));
+      rel = rn / bnorm;
       c->times.history.push_back(rel);
       ++it;
       if (!std::isfinite(rel)) break;
@@ -900,11 +1027,12 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->times.solve_total = ms * 1e-3;
-  g_timer = nullptr;
   c->times.n_subst = (int)timer.sub.size();
   c->times.n_matvec = (int)timer.mv.size();
+  c->times.n_matvec32 = (int)timer.mv32.size();
   c->times.subst = SolveTimer::total(timer.sub);
-  c->times.matvec = SolveTimer::total(timer.mv);  // the guard then finds both lists empty
+  c->times.matvec = SolveTimer::total(timer.mv);
+  c->times.matvec32 = SolveTimer::total(timer.mv32);  // the guard then finds the lists empty
   c->times.iters = it;
   c->times.relres = rel;
   if (relres_out) *relres_out = rel;
@@ -917,7 +1045,7 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
 }
 
 h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart) {
-  if (!c || method < 0 || method > 1 || restart < 1 || restart > 1000) return H2_ERR_INVALID_ARG;
+  if (!c || method < 0 || method > 3 || restart < 1 || restart > 1000) return H2_ERR_INVALID_ARG;
   c->refine_method = method;
   c->restart = restart;
   return H2_OK;
@@ -969,15 +1097,17 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     by_mv += 8.0 * (double)lf.NP * lf.D * lf.D;
     fl_mv += 2.0 * (double)lf.NP * lf.D * lf.D;
   }
-  o << "],\"bytes_subst\":" << by_sub << ",\"bytes_matvec\":" << by_mv << ",\"flops_matvec\":" << fl_mv;
+  o << "],\"bytes_subst\":" << by_sub << ",\"bytes_matvec\":" << by_mv << ",\"flops_matvec\":" << fl_mv
+    << ",\"bytes_matvec32\":" << by_mv / 2;
   o << ",\"flops\":{\"a1_qr\":" << fl_qr << ",\"a2_proj\":" << fl_proj << ",\"a3_lu\":" << fl_lu
     << ",\"a45_schur\":" << fl_schur << ",\"a2c_coupling\":" << fl_coup << "}";
   o << ",\"times\":{\"a1_qr\":" << t.a1_qr << ",\"a2_proj\":" << t.a2_proj << ",\"a3_lu\":" << t.a3_lu
     << ",\"a45_schur\":" << t.a5_schur << ",\"a2c_coupling\":" << t.a2c_coupling << ",\"a6_merge\":" << t.a6_merge
     << ",\"a7_root\":" << t.a7_root << ",\"factor\":" << t.total_factor << ",\"solve\":" << t.solve_total
-    << ",\"solve_subst\":" << t.subst << ",\"solve_matvec\":" << t.matvec << "},\"calls\":{\"subst\":"
-    << t.n_subst << ",\"matvec\":" << t.n_matvec
-    << "},\"iters\":" << t.iters << ",\"relres\":" << t.relres
+    << ",\"solve_subst\":" << t.subst << ",\"solve_matvec\":" << t.matvec << ",\"solve_matvec32\":" << t.matvec32
+    << "},\"calls\":{\"subst\":" << t.n_subst << ",\"matvec\":" << t.n_matvec << ",\"matvec32\":" << t.n_matvec32
+    << "},\"method\":" << t.method
+    << ",\"iters\":" << t.iters << ",\"relres\":" << t.relres
     << ",\"kernel_launches\":" << g_launches.load() << ",\"refine_method\":" << c->refine_method
     << ",\"restart\":" << c->restart << ",\"tensor_cores\":" << (c->used_tc ? "true" : "false")
     << ",\"history\":[";

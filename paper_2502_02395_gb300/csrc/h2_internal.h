@@ -112,6 +112,8 @@ struct DevLevel {
   double* X = nullptr;    // nb * D * K
   int64_t* SK = nullptr;  // nb * K
   double* S = nullptr;    // FP * K * K couplings G(SK_i, SK_j)
+  float* X32 = nullptr;   // FP32 copies for the inner solver of the mixed refinement
+  float* S32 = nullptr;
 };
 
 // Factorization storage of one level in storage type T (double or float).
@@ -162,7 +164,8 @@ struct PhaseTimes {
   double a1_qr = 0, a2_proj = 0, a3_lu = 0, a5_schur = 0, a2c_coupling = 0, a6_merge = 0,
          a7_root = 0, total_factor = 0;
   double solve_total = 0, subst = 0, matvec = 0;
-  int iters = 0, n_subst = 0, n_matvec = 0;
+  double matvec32 = 0;
+  int iters = 0, n_subst = 0, n_matvec = 0, n_matvec32 = 0, method = 0;
   double relres = 0;
   std::vector<double> history;  // relative residual after every correction (IR) or cycle (GMRES)
 };
@@ -188,17 +191,26 @@ struct h2_ctx {
   double *io_a = nullptr, *io_b = nullptr;  // original-order staging vectors (N)
   double* xhat = nullptr;  // matvec upward/downward scratch (sum over levels nb*K)
   double* yhat = nullptr;
+  float* A32 = nullptr;    // FP32 copy of the leaf near blocks (inner solver)
+  float *xhat32 = nullptr, *yhat32 = nullptr;
+  std::vector<double*> X64p, S64p;  // per-level pointers (index l; [0] unused)
+  std::vector<float*> X32p, S32p;
   std::vector<int64_t> hat_off;  // per-level offsets into xhat / yhat
   double* red = nullptr;         // reduction scratch
   int32_t* status = nullptr;     // device error word(s)
   int prec = -1;                 // precision of the current factorization
   bool used_tc = false;          // the last factorization ran contractions on the tensor cores
-  int refine_method = 1;         // 0: plain iterative refinement, 1: FGMRES-based refinement
+  int refine_method = 3;         // 0: plain IR, 1: FGMRES-IR in FP64, 2: FP64 outer / FP32 FGMRES inner,
+                                 // 3: automatic (1 for FP64 factorizations, 2 otherwise)
+  double inner_tol = 1e-6;       // relative accuracy of the FP32 inner solves
   int restart = 30;              // FGMRES restart length
   double* gm_V = nullptr;        // (restart + 1) * nslot Krylov basis
   double* gm_Z = nullptr;        // restart * nslot preconditioned directions
   double* gm_h = nullptr;        // 3 * (restart + 2) coefficients
   double* gm_part = nullptr;     // (restart + 1) * 128 dot-product partials
+  float* gm_V32 = nullptr;       // FP32 Krylov basis / directions of the inner solver
+  float* gm_Z32 = nullptr;
+  float* gm_r32 = nullptr;
   int gm_cap = 0;                // restart the buffers were sized for
   h2::Factor<double> f64;
   h2::Factor<float> f32;

@@ -95,14 +95,14 @@ extern "C" h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y) {
   cudaStream_t st = c->stream;
   h2::launch_gather(c->slot_pt, x, xt, (int64_t)nslot, st);
   if (L == 0) {
-    h2::launch_matvec_leaf(c->lv[0], c->A64, xt, nullptr, yt, st);
+    h2::launch_matvec_leaf<double>(c->lv[0], c->A64, nullptr, xt, nullptr, yt, st);
   } else {
     const std::vector<int64_t>& off = c->hat_off;
-    h2::launch_matvec_up_leaf(c->lv[L], xt, xh + off[L], st);
-    for (int l = L - 1; l >= 1; --l) h2::launch_matvec_up(c->lv[l], xh + off[l + 1], xh + off[l], st);
-    for (int l = 1; l <= L; ++l) h2::launch_matvec_far(c->lv[l], xh + off[l], yh + off[l], st);
-    for (int l = 1; l < L; ++l) h2::launch_matvec_down(c->lv[l], yh + off[l], yh + off[l + 1], st);
-    h2::launch_matvec_leaf(c->lv[L], c->A64, xt, yh + off[L], yt, st);
+    h2::launch_matvec_up<double>(c->lv[L], c->lv[L].X, xt, xh + off[L], st);
+    for (int l = L - 1; l >= 1; --l) h2::launch_matvec_up<double>(c->lv[l], c->lv[l].X, xh + off[l + 1], xh + off[l], st);
+    for (int l = 1; l <= L; ++l) h2::launch_matvec_far<double>(c->lv[l], c->lv[l].S, xh + off[l], yh + off[l], st);
+    for (int l = 1; l < L; ++l) h2::launch_matvec_down<double>(c->lv[l], c->lv[l].X, yh + off[l], yh + off[l + 1], st);
+    h2::launch_matvec_leaf<double>(c->lv[L], c->A64, c->lv[L].X, xt, yh + off[L], yt, st);
   }
   h2::launch_scatter(c->slot_pt, yt, y, (int64_t)nslot, st);
   cudaError_t e = cudaGetLastError();

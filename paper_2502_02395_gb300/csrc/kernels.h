@@ -69,27 +69,33 @@ void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T
 template <typename T>
 void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st);  // y = M x, M n x n row-major
 
-void launch_matvec_up_leaf(const DevLevel& L, const double* x, double* xh, cudaStream_t st);
-void launch_matvec_up(const DevLevel& L, const double* xh_child, double* xh, cudaStream_t st);
-void launch_matvec_far(const DevLevel& L, const double* xh, double* yh, cudaStream_t st);
-void launch_matvec_down(const DevLevel& L, const double* yh, double* yh_child, cudaStream_t st);
-void launch_matvec_leaf(const DevLevel& L, const double* A, const double* x, const double* yh, double* y,
-                        cudaStream_t st);
+template <typename T>
+void launch_matvec_up(const DevLevel& L, const T* X, const T* x, T* xh, cudaStream_t st);
+template <typename T>
+void launch_matvec_far(const DevLevel& L, const T* S, const T* xh, T* yh, cudaStream_t st);
+template <typename T>
+void launch_matvec_down(const DevLevel& L, const T* X, const T* yh, T* yh_child, cudaStream_t st);
+template <typename T>
+void launch_matvec_leaf(const DevLevel& L, const T* A, const T* X, const T* x, const T* yh, T* y, cudaStream_t st);
 
 void launch_gather(const int64_t* slot, const double* src, double* dst, int64_t nslots, cudaStream_t st);
 void launch_scatter(const int64_t* slot, const double* src, double* dst, int64_t nslots, cudaStream_t st);
 void launch_residual(const double* b, const double* y, double* r, int64_t n, cudaStream_t st);
-void launch_norm2(const double* v, int64_t n, double* out, cudaStream_t st);  // out[0] = sum v^2
+template <typename T>
+void launch_norm2(const T* v, int64_t n, double* out, cudaStream_t st);  // out[0] = sum v^2 (FP64), out[1..256] scratch
+template <typename Ti, typename To>
+void launch_scaled_copy(const Ti* in, const double* nrm2, bool inverse, To* out, int64_t n, cudaStream_t st);
 template <typename T>
 void launch_scale_to(const double* in, const double* norm2, T* out, int64_t n, cudaStream_t st);
 template <typename T>
 void launch_axpy_from(const T* d, const double* norm2, double* x, int64_t n, cudaStream_t st);
 // GMRES: out[v] (+)= V_v . w for v < nv (part: nv * 128 scratch); w += sign sum_v coef[v] V_v;
 // w = src / sqrt(nrm2[0])
-void launch_multi_dot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* part, double* out,
+template <typename T>
+void launch_multi_dot(const T* V, int64_t ldv, int nv, const T* w, int64_t n, double* part, double* out,
                       bool accumulate, cudaStream_t st);
-void launch_multi_axpy(const double* V, int64_t ldv, int nv, const double* coef, double sign, double* w, int64_t n,
+template <typename T, typename TW>
+void launch_multi_axpy(const T* V, int64_t ldv, int nv, const double* coef, double sign, TW* w, int64_t n,
                        cudaStream_t st);
-void launch_normalize(const double* src, const double* nrm2, double* w, int64_t n, cudaStream_t st);
 
 }  // namespace h2

@@ -392,101 +392,121 @@ H2_INST_SOLVE(double)
 H2_INST_SOLVE(float)
 
 // ------------------------------------------------------------- matvec ---
-// upward, leaf: xh_i[a] = sum_d X_i[d*K + a] x_i[d]
-__global__ void mv_up_leaf_kernel(int D, int K, const double* __restrict__ X, const double* __restrict__ x,
-                                  double* __restrict__ xh) {
+// Element type T: double for the refinement residual, float for the inner
+// solver of the mixed-precision refinement.  X, S and A are that level's
+// bases, couplings and leaf near blocks in T.
+
+// upward: xh_i[a] = sum_d X_i[d*K + a] x_i[d] (x_i: the box's D inputs)
+template <typename T>
+__global__ void mv_up_kernel(int D, int K, const T* __restrict__ X, const T* __restrict__ x, T* __restrict__ xh) {
   const int i = blockIdx.x;
-  const double* Xb = X + (int64_t)i * D * K;
-  const double* xb = x + (int64_t)i * D;
+  const T* Xb = X + (int64_t)i * D * K;
+  const T* xb = x + (int64_t)i * D;
   for (int a = threadIdx.x; a < K; a += blockDim.x) {
-    double s = 0;
-    for (int d = 0; d < D; ++d) s += Xb[(int64_t)d * K + a] * xb[d];
-    xh[(int64_t)i * K + a] = s;
+    T s0 = 0, s1 = 0;
+    int d = 0;
+    for (; d + 1 < D; d += 2) {
+      s0 = fma(Xb[(int64_t)d * K + a], xb[d], s0);
+      s1 = fma(Xb[(int64_t)(d + 1) * K + a], xb[d + 1], s1);
+    }
+    if (d < D) s0 = fma(Xb[(int64_t)d * K + a], xb[d], s0);
+    xh[(int64_t)i * K + a] = s0 + s1;
   }
 }
-void launch_matvec_up_leaf(const DevLevel& L, const double* x, double* xh, cudaStream_t st) {
+template <typename T>
+void launch_matvec_up(const DevLevel& L, const T* X, const T* x, T* xh, cudaStream_t st) {
   ++g_launches;
-  mv_up_leaf_kernel<<<L.nb, 128, 0, st>>>(L.D, L.K, L.X, x, xh);
-}
-// upward above the leaves: xh_p = X_p^T [xh_2p; xh_2p+1] (children packed contiguously)
-void launch_matvec_up(const DevLevel& L, const double* xh_child, double* xh, cudaStream_t st) {
-  ++g_launches;
-  mv_up_leaf_kernel<<<L.nb, 128, 0, st>>>(L.D, L.K, L.X, xh_child, xh);
+  mv_up_kernel<T><<<L.nb, 128, 0, st>>>(L.D, L.K, X, x, xh);
 }
 
 // couplings: yh_i = sum_{far j} S_f xh_j   (overwrites yh_i)
+template <typename T>
 __global__ void __launch_bounds__(256, 2) mv_far_kernel(int K, const int64_t* __restrict__ ptr,
-                                                     const int32_t* __restrict__ fj, const double* __restrict__ S,
-                                                     const double* __restrict__ xh, double* __restrict__ yh) {
-  extern __shared__ __align__(16) double smv[];  // nf * K
+                                                        const int32_t* __restrict__ fj, const T* __restrict__ S,
+                                                        const T* __restrict__ xh, T* __restrict__ yh) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* smv = reinterpret_cast<T*>(smraw);  // nf * K
   const int i = blockIdx.x, tid = threadIdx.x;
   const int64_t p0 = ptr[i];
   const int nf = (int)(ptr[i + 1] - p0);
   for (int e = tid; e < nf * K; e += blockDim.x) smv[e] = xh[(int64_t)fj[p0 + e / K] * K + e % K];
   __syncthreads();
-  double acc[kRPW];
+  T acc[kRPW];
   for (int r0 = 0; r0 < K; r0 += kChunk) {
     zero(acc);
-    for (int q = 0; q < nf; ++q) rows_acc<double, kRPW>(r0, S + (p0 + q) * K * K, K, K, K, smv + q * K, acc);
-    rows_finish<double, kRPW>(r0, K, acc, 1.0, nullptr, yh + (int64_t)i * K);
+    for (int q = 0; q < nf; ++q) rows_acc<T, kRPW>(r0, S + (p0 + q) * K * K, K, K, K, smv + q * K, acc);
+    rows_finish<T, kRPW>(r0, K, acc, T(1), nullptr, yh + (int64_t)i * K);
   }
 }
-void launch_matvec_far(const DevLevel& L, const double* xh, double* yh, cudaStream_t st) {
-  size_t sm = sizeof(double) * (size_t)L.K * std::max(L.max_far, 1);
-  set_smem((const void*)mv_far_kernel, sm);
+template <typename T>
+void launch_matvec_far(const DevLevel& L, const T* S, const T* xh, T* yh, cudaStream_t st) {
+  size_t sm = sizeof(T) * (size_t)L.K * std::max(L.max_far, 1);
+  set_smem((const void*)mv_far_kernel<T>, sm);
   ++g_launches;
-  mv_far_kernel<<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, L.S, xh, yh);
+  mv_far_kernel<T><<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, S, xh, yh);
 }
 
 // downward: [yh_2p; yh_2p+1] += X_p yh_p   (rows d of X_p, D = 2 Kc)
-__global__ void mv_down_kernel(int D, int K, const double* __restrict__ X, const double* __restrict__ yh,
-                               double* __restrict__ yhc) {
+template <typename T>
+__global__ void mv_down_kernel(int D, int K, const T* __restrict__ X, const T* __restrict__ yh, T* __restrict__ yhc) {
   const int p = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double* Xb = X + (int64_t)p * D * K;
-  const double* yp = yh + (int64_t)p * K;
+  const T* Xb = X + (int64_t)p * D * K;
+  const T* yp = yh + (int64_t)p * K;
   for (int d = warp; d < D; d += nw) {
-    double s = 0;
-    for (int a = lane; a < K; a += 32) s += Xb[(int64_t)d * K + a] * yp[a];
+    T s = 0;
+    for (int a = lane; a < K; a += 32) s = fma(Xb[(int64_t)d * K + a], yp[a], s);
     s = warp_sum(s);
     if (lane == 0) yhc[(int64_t)p * D + d] += s;
   }
 }
-void launch_matvec_down(const DevLevel& L, const double* yh, double* yh_child, cudaStream_t st) {
+template <typename T>
+void launch_matvec_down(const DevLevel& L, const T* X, const T* yh, T* yh_child, cudaStream_t st) {
   ++g_launches;
-  mv_down_kernel<<<L.nb, 256, 0, st>>>(L.D, L.K, L.X, yh, yh_child);
+  mv_down_kernel<T><<<L.nb, 256, 0, st>>>(L.D, L.K, X, yh, yh_child);
 }
 
 // leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j
+template <typename T>
 __global__ void __launch_bounds__(256, 2) mv_leaf_kernel(int D, int K, const int64_t* __restrict__ ptr,
-                                                      const int32_t* __restrict__ nj, const double* __restrict__ A,
-                                                      const double* __restrict__ X, const double* __restrict__ x,
-                                                      const double* __restrict__ yh, double* __restrict__ y) {
-  extern __shared__ __align__(16) double smv[];  // K + nn * D
+                                                         const int32_t* __restrict__ nj, const T* __restrict__ A,
+                                                         const T* __restrict__ X, const T* __restrict__ x,
+                                                         const T* __restrict__ yh, T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* smv = reinterpret_cast<T*>(smraw);  // K (rounded up to 16 bytes) + nn * D
   const int i = blockIdx.x, tid = threadIdx.x;
   const int64_t p0 = ptr[i];
   const int nn = (int)(ptr[i + 1] - p0);
-  double* sh = smv;
-  double* sx = smv + ((K + 1) & ~1);
+  const int kpad = (K + 3) & ~3;
+  T* sh = smv;
+  T* sx = smv + kpad;
   if (yh)
     for (int e = tid; e < K; e += blockDim.x) sh[e] = yh[(int64_t)i * K + e];
   for (int e = tid; e < nn * D; e += blockDim.x) sx[e] = x[(int64_t)nj[p0 + e / D] * D + e % D];
   __syncthreads();
-  double acc[kRPW];
+  T acc[kRPW];
   for (int r0 = 0; r0 < D; r0 += kChunk) {
     zero(acc);
-    if (yh) rows_acc<double, kRPW>(r0, X + (int64_t)i * D * K, K, D, K, sh, acc);
-    for (int q = 0; q < nn; ++q) rows_acc<double, kRPW>(r0, A + (p0 + q) * D * D, D, D, D, sx + q * D, acc);
-    rows_finish<double, kRPW>(r0, D, acc, 1.0, nullptr, y + (int64_t)i * D);
+    if (yh) rows_acc<T, kRPW>(r0, X + (int64_t)i * D * K, K, D, K, sh, acc);
+    for (int q = 0; q < nn; ++q) rows_acc<T, kRPW>(r0, A + (p0 + q) * D * D, D, D, D, sx + q * D, acc);
+    rows_finish<T, kRPW>(r0, D, acc, T(1), nullptr, y + (int64_t)i * D);
   }
 }
-void launch_matvec_leaf(const DevLevel& L, const double* A, const double* x, const double* yh, double* y,
-                        cudaStream_t st) {
-  const size_t sm = sizeof(double) * ((size_t)((L.K + 1) & ~1) + (size_t)L.D * L.max_near);
-  set_smem((const void*)mv_leaf_kernel, sm);
+template <typename T>
+void launch_matvec_leaf(const DevLevel& L, const T* A, const T* X, const T* x, const T* yh, T* y, cudaStream_t st) {
+  const size_t sm = sizeof(T) * ((size_t)((L.K + 3) & ~3) + (size_t)L.D * L.max_near);
+  set_smem((const void*)mv_leaf_kernel<T>, sm);
   ++g_launches;
-  mv_leaf_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, A, L.X, x, yh, y);
+  mv_leaf_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, A, X, x, yh, y);
 }
+
+#define H2_INST_MV(T)                                                                                           \
+  template void launch_matvec_up<T>(const DevLevel&, const T*, const T*, T*, cudaStream_t);                      \
+  template void launch_matvec_far<T>(const DevLevel&, const T*, const T*, T*, cudaStream_t);                     \
+  template void launch_matvec_down<T>(const DevLevel&, const T*, const T*, T*, cudaStream_t);                    \
+  template void launch_matvec_leaf<T>(const DevLevel&, const T*, const T*, const T*, const T*, T*, cudaStream_t);
+H2_INST_MV(double)
+H2_INST_MV(float)
 
 // ------------------------------------------------------------ vectors ---
 __global__ void gather_kernel(const int64_t* __restrict__ slot, const double* __restrict__ src,
@@ -521,12 +541,16 @@ void launch_residual(const double* b, const double* y, double* r, int64_t n, cud
   ++g_launches;
   residual_kernel<<<grid_for(n), 256, 0, st>>>(b, y, r, n);
 }
-// deterministic two-pass sum of squares: 256 partials, then one block
-__global__ void norm2_part_kernel(const double* __restrict__ v, int64_t n, double* __restrict__ part) {
+// deterministic two-pass sum of squares (accumulated in FP64): 256 partials,
+// then one block
+template <typename T>
+__global__ void norm2_part_kernel(const T* __restrict__ v, int64_t n, double* __restrict__ part) {
   __shared__ double sb[8];
   double s = 0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    s += v[e] * v[e];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double x = (double)v[e];
+    s = fma(x, x, s);
+  }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -549,12 +573,39 @@ __global__ void norm2_final_kernel(const double* __restrict__ part, int np, doub
     out[0] = t;
   }
 }
-void launch_norm2(const double* v, int64_t n, double* out, cudaStream_t st) {
+template <typename T>
+void launch_norm2(const T* v, int64_t n, double* out, cudaStream_t st) {
   ++g_launches;
-  norm2_part_kernel<<<256, 256, 0, st>>>(v, n, out + 1);
+  norm2_part_kernel<T><<<256, 256, 0, st>>>(v, n, out + 1);
   ++g_launches;
   norm2_final_kernel<<<1, 256, 0, st>>>(out + 1, 256, out);
 }
+template void launch_norm2<double>(const double*, int64_t, double*, cudaStream_t);
+template void launch_norm2<float>(const float*, int64_t, double*, cudaStream_t);
+
+// out[e] = (To)(in[e] * scale), scale = 1/sqrt(nrm2[0]) (or sqrt(nrm2[0]) when
+// inverse == 0); nrm2 == NULL: plain conversion
+template <typename Ti, typename To>
+__global__ void scaled_copy_kernel(const Ti* __restrict__ in, const double* __restrict__ nrm2, int inverse,
+                                   To* __restrict__ out, int64_t n) {
+  double s = 1.0;
+  if (nrm2) {
+    const double r = sqrt(nrm2[0]);
+    s = inverse ? (r > 0 ? 1.0 / r : 0.0) : r;
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (To)((double)in[e] * s);
+}
+template <typename Ti, typename To>
+void launch_scaled_copy(const Ti* in, const double* nrm2, bool inverse, To* out, int64_t n, cudaStream_t st) {
+  ++g_launches;
+  scaled_copy_kernel<Ti, To><<<grid_for(n), 256, 0, st>>>(in, nrm2, inverse ? 1 : 0, out, n);
+}
+template void launch_scaled_copy<double, float>(const double*, const double*, bool, float*, int64_t, cudaStream_t);
+template void launch_scaled_copy<float, double>(const float*, const double*, bool, double*, int64_t, cudaStream_t);
+template void launch_scaled_copy<float, float>(const float*, const double*, bool, float*, int64_t, cudaStream_t);
+template void launch_scaled_copy<double, double>(const double*, const double*, bool, double*, int64_t,
+                                                 cudaStream_t);
 template <typename T>
 __global__ void scale_to_kernel(const double* __restrict__ in, const double* __restrict__ nrm2, T* __restrict__ out,
                                 int64_t n) {
@@ -580,15 +631,16 @@ void launch_axpy_from(const T* d, const double* norm2, double* x, int64_t n, cud
   axpy_from_kernel<T><<<grid_for(n), 256, 0, st>>>(d, norm2, x, n);
 }
 // ---------------------------------------------------------- GMRES blocks ---
-// part[v * nblk + blk] = partial sums of V_v . w ; out[v] = sum over blocks
-__global__ void multi_dot_part_kernel(const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
-                                      int64_t n, double* __restrict__ part) {
+// part[v * nblk + blk] = partial sums of V_v . w (FP64); out[v] (+)= the sum
+template <typename T>
+__global__ void multi_dot_part_kernel(const T* __restrict__ V, int64_t ldv, const T* __restrict__ w, int64_t n,
+                                      double* __restrict__ part) {
   __shared__ double sb[8];
   const int v = blockIdx.y;
-  const double* Vv = V + (int64_t)v * ldv;
+  const T* Vv = V + (int64_t)v * ldv;
   double s = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    s += Vv[e] * w[e];
+    s = fma((double)Vv[e], (double)w[e], s);
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sb[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -613,41 +665,43 @@ __global__ void multi_dot_final_kernel(const double* __restrict__ part, int nblk
     out[v] = accumulate ? out[v] + t : t;
   }
 }
-void launch_multi_dot(const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* part, double* out,
+template <typename T>
+void launch_multi_dot(const T* V, int64_t ldv, int nv, const T* w, int64_t n, double* part, double* out,
                       bool accumulate, cudaStream_t st) {
   if (nv == 0) return;
   const int nblk = 128;
   ++g_launches;
-  multi_dot_part_kernel<<<dim3(nblk, nv), 256, 0, st>>>(V, ldv, w, n, part);
+  multi_dot_part_kernel<T><<<dim3(nblk, nv), 256, 0, st>>>(V, ldv, w, n, part);
   ++g_launches;
   multi_dot_final_kernel<<<nv, 256, 0, st>>>(part, nblk, out, accumulate ? 1 : 0);
 }
-// w += sign * sum_v coef[v] V_v
-__global__ void multi_axpy_kernel(const double* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ coef,
-                                  double sign, double* __restrict__ w, int64_t n) {
+// w += sign * sum_v coef[v] V_v   (coefficients in FP64)
+template <typename T, typename TW>
+__global__ void multi_axpy_kernel(const T* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ coef,
+                                  double sign, TW* __restrict__ w, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     double s = 0;
-    for (int v = 0; v < nv; ++v) s += coef[v] * V[(int64_t)v * ldv + e];
-    w[e] += sign * s;
+    for (int v = 0; v < nv; ++v) s = fma(coef[v], (double)V[(int64_t)v * ldv + e], s);
+    w[e] = (TW)((double)w[e] + sign * s);
   }
 }
-void launch_multi_axpy(const double* V, int64_t ldv, int nv, const double* coef, double sign, double* w, int64_t n,
+template <typename T, typename TW>
+void launch_multi_axpy(const T* V, int64_t ldv, int nv, const double* coef, double sign, TW* w, int64_t n,
                        cudaStream_t st) {
   if (nv == 0) return;
   ++g_launches;
-  multi_axpy_kernel<<<grid_for(n), 256, 0, st>>>(V, ldv, nv, coef, sign, w, n);
+  multi_axpy_kernel<T, TW><<<grid_for(n), 256, 0, st>>>(V, ldv, nv, coef, sign, w, n);
 }
-// w = src / sqrt(nrm2[0])   (in place allowed)
-__global__ void normalize_kernel(const double* __restrict__ src, const double* __restrict__ nrm2,
-                                 double* __restrict__ w, int64_t n) {
-  const double s = nrm2[0] > 0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    w[e] = src[e] * s;
-}
-void launch_normalize(const double* src, const double* nrm2, double* w, int64_t n, cudaStream_t st) {
-  ++g_launches;
-  normalize_kernel<<<grid_for(n), 256, 0, st>>>(src, nrm2, w, n);
-}
+template void launch_multi_dot<double>(const double*, int64_t, int, const double*, int64_t, double*, double*, bool,
+                                       cudaStream_t);
+template void launch_multi_dot<float>(const float*, int64_t, int, const float*, int64_t, double*, double*, bool,
+                                      cudaStream_t);
+template void launch_multi_axpy<double, double>(const double*, int64_t, int, const double*, double, double*, int64_t,
+                                                cudaStream_t);
+template void launch_multi_axpy<float, float>(const float*, int64_t, int, const double*, double, float*, int64_t,
+                                              cudaStream_t);
+template void launch_multi_axpy<float, double>(const float*, int64_t, int, const double*, double, double*, int64_t,
+                                               cudaStream_t);
 
 template void launch_scale_to<double>(const double*, const double*, double*, int64_t, cudaStream_t);
 template void launch_scale_to<float>(const double*, const double*, float*, int64_t, cudaStream_t);

@@ -154,9 +154,10 @@ def test_poly2_equals_dense_solve(B):
     S.close()
 
 
+@pytest.mark.parametrize("method", ["auto", "gmres"])
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("name", ["cube2048_laplace", "sphere1000_ragged", "cube8192_yukawa"])
-def test_mixed_refined_solution(B, name, prec):
+def test_mixed_refined_solution(B, name, prec, method):
     """Low-precision contractions + FP64 refinement reach the FP64 answer:
     the refined solution matches the oracle's to the refinement target times
     the conditioning slack."""
@@ -164,8 +165,10 @@ def test_mixed_refined_solution(B, name, prec):
     H, F, flat, b = oracle_case(name)
     S = lib_case(B, name)
     S.factor(prec)
-    x, r, its = S.solve(b, target=1e-12, max_iters=60)
+    S.set_refinement(method)
+    x, r, its = S.solve(b, target=1e-12, max_iters=120)
     assert r <= 1e-12
+    assert S.stats()["method"] == (2 if method == "auto" else 1)
     x_ref, _, _ = ulv.refine_gmres(F, H, b, 1e-12, 60, 30)
     assert rel(x, x_ref) <= 1e-9
     st = S.stats()
