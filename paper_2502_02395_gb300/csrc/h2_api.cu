@@ -276,8 +276,6 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     else CKC(dalloc(c, &f.luT, nb * R * R));
     CKC(dalloc(c, &f.Ainv, nb * R * R));
     CKC(dalloc(c, &f.piv, nb * R));
-    if (std::is_same<T, double>::value) f.Sc = reinterpret_cast<T*>(d.S);
-    else CKC(dalloc(c, &f.Sc, (size_t)std::max<int64_t>(d.FP, 1) * K * K));
     for (T** p : {&f.vin, &f.c, &f.xs}) CKC(dalloc(c, p, nb * D));
     for (T** p : {&f.u, &f.v, &f.om}) CKC(dalloc(c, p, nb * std::max<size_t>(R, 1)));
   }
@@ -341,8 +339,8 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     {
       const int nb = d.nb;
       const int64_t DK = (int64_t)D * K, KK = (int64_t)K * K;
-      T* Xc = F.Wk;  // X in T, row-major D x K per box
-      launch_convert<double, T>(d.X, Xc, nb * DK, st);
+      // X in T, row-major D x K per box (the instance keeps FP64 and FP32 copies)
+      const T* Xc = std::is_same<T, double>::value ? reinterpret_cast<const T*>(d.X) : reinterpret_cast<const T*>(d.X32);
       const T* Xin = Xc;
       if (l < L) {
         const int Kc = c->lv[l + 1].K;
@@ -410,8 +408,8 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     // a2': couplings Shat_ij = T_i S_ij T_j^T
     if (d.FP > 0 && K > 0) {
       const int64_t KK = (int64_t)K * K;
-      if (!std::is_same<T, double>::value) launch_convert<double, T>(d.S, f.Sc, d.FP * KK, st);
-      gemm<T>(prec, K, K, K, f.Sc, KK, nullptr, K, false, f.Tm, KK, d.far_j, K, true, F.Wk, KK, nullptr, K, T(1),
+      const T* Sc = std::is_same<T, double>::value ? reinterpret_cast<const T*>(d.S) : reinterpret_cast<const T*>(d.S32);
+      gemm<T>(prec, K, K, K, Sc, KK, nullptr, K, false, f.Tm, KK, d.far_j, K, true, F.Wk, KK, nullptr, K, T(1),
               T(0), d.FP, st);
       gemm<T>(prec, K, K, K, f.Tm, KK, d.far_i, K, false, F.Wk, KK, nullptr, K, false, f.Shat, KK, nullptr, K, T(1),
               T(0), d.FP, st);

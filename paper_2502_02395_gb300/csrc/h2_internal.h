@@ -129,7 +129,6 @@ struct FacLevel {
   T* Ain = nullptr;    // NP * D * D   input near blocks of this level (row-major)
   T* Ahat = nullptr;   // NP * D * D   projected blocks (row-major)
   T* Shat = nullptr;   // FP * K * K   couplings in orthogonal coordinates
-  T* Sc = nullptr;     // FP * K * K   couplings G(SK_i, SK_j) in T
   T* Z = nullptr;      // nb * R * K   (Ahat_ii^RR)^-1 Ahat_ii^RS
   double* lu = nullptr;    // nb * R * R  LU of Ahat_ii^RR, column-major, FP64
   T* luT = nullptr;        // nb * R * R  the same factors in T (aliases lu when T is double)

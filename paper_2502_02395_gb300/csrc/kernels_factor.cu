@@ -14,6 +14,8 @@
 //                          Schur update and by the substitution of Eq. 31
 //   merge_kernel           children's SS blocks / couplings into the parent
 //                          near blocks (Algorithm 2 line 18-20)
+#include <type_traits>
+
 #include "h2_internal.h"
 #include "kernels.h"
 
@@ -488,6 +490,87 @@ lu_inverse_kernel(int R, const T* __restrict__ luT, const int32_t* __restrict__ 
   }
 }
 
+// ------------------------------------------------------------------------
+// a3 (cont., FP32 storage): Ainv from the factors with one thread per column
+// b of the inverse.  Column b of P^T is e_{perm^-1(b)}; each thread runs the
+// unit-lower forward and the upper backward substitution on its own column,
+// left-looking in blocks of 32 rows held in registers, reading the factors
+// (row-major in shared memory, identity-padded to Rp = 32 ceil(R/32)) with
+// 16-byte broadcast loads.  No barrier is needed between columns.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) lu_inverse_f32_kernel(int R, int Rp, const float* __restrict__ luT,
+                                                              const int32_t* __restrict__ piv,
+                                                              float* __restrict__ Ainv) {
+  extern __shared__ __align__(16) float smf[];
+  __shared__ int s_perm[1024];
+  float* F = smf;            // Rp x Rp row-major factors
+  float* Y = F + Rp * Rp;    // Rp x Rp row-major; column b belongs to thread b
+  const int box = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const float* src = luT + (size_t)box * R * R;
+  for (int e = tid; e < Rp * Rp; e += nt) {
+    const int r = e / Rp, cc = e - r * Rp;
+    F[e] = (r < R && cc < R) ? src[cc * R + r] : (r == cc ? 1.f : 0.f);
+  }
+  if (tid == 0) {
+    for (int r = 0; r < Rp; ++r) s_perm[r] = r;
+    for (int k = 0; k < R; ++k) {
+      const int p = piv[(size_t)box * R + k];
+      const int t = s_perm[k];
+      s_perm[k] = s_perm[p];
+      s_perm[p] = t;
+    }
+  }
+  __syncthreads();
+  const int b = tid;
+  for (int r = 0; r < Rp; ++r) Y[r * Rp + b] = (s_perm[r] == b) ? 1.f : 0.f;
+  float y[32];
+  // forward: L unit lower
+  for (int i0 = 0; i0 < Rp; i0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) y[q] = Y[(i0 + q) * Rp + b];
+    for (int k = 0; k < i0; k += 4) {
+      const float y0 = Y[k * Rp + b], y1 = Y[(k + 1) * Rp + b], y2 = Y[(k + 2) * Rp + b], y3 = Y[(k + 3) * Rp + b];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float4 l = *reinterpret_cast<const float4*>(F + (i0 + q) * Rp + k);
+        y[q] = fmaf(-l.x, y0, fmaf(-l.y, y1, fmaf(-l.z, y2, fmaf(-l.w, y3, y[q]))));
+      }
+    }
+#pragma unroll
+    for (int q = 1; q < 32; ++q) {
+#pragma unroll
+      for (int c = 0; c < q; ++c) y[q] = fmaf(-F[(i0 + q) * Rp + i0 + c], y[c], y[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) Y[(i0 + q) * Rp + b] = y[q];
+  }
+  // backward: U upper
+  for (int i0 = Rp - 32; i0 >= 0; i0 -= 32) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) y[q] = Y[(i0 + q) * Rp + b];
+    for (int k = i0 + 32; k < Rp; k += 4) {
+      const float y0 = Y[k * Rp + b], y1 = Y[(k + 1) * Rp + b], y2 = Y[(k + 2) * Rp + b], y3 = Y[(k + 3) * Rp + b];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float4 u = *reinterpret_cast<const float4*>(F + (i0 + q) * Rp + k);
+        y[q] = fmaf(-u.x, y0, fmaf(-u.y, y1, fmaf(-u.z, y2, fmaf(-u.w, y3, y[q]))));
+      }
+    }
+#pragma unroll
+    for (int q = 31; q >= 0; --q) {
+#pragma unroll
+      for (int c = q + 1; c < 32; ++c) y[q] = fmaf(-F[(i0 + q) * Rp + i0 + c], y[c], y[q]);
+      y[q] = y[q] / F[(i0 + q) * Rp + i0 + q];
+    }
+#pragma unroll
+    for (int q = 0; q < 32; ++q) Y[(i0 + q) * Rp + b] = y[q];
+  }
+  if (b < R) {
+    float* out = Ainv + (size_t)box * R * R;
+    for (int r = 0; r < R; ++r) out[(size_t)r * R + b] = Y[r * Rp + b];
+  }
+}
+
 template <typename T>
 void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
                        int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st) {
@@ -499,6 +582,17 @@ void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_
   ++g_launches;
   lu_factor_kernel<T><<<nb, 256, use ? sm1 : 0, st>>>(D, R, Ablk, diag_idx, lu, luT, piv, status, level, use);
   if (R > 1024) return;  // the permutation table holds 1024 rows; larger blocks are rejected by the caller
+  if (std::is_same<T, float>::value) {
+    const int Rp = (R + 31) / 32 * 32;
+    const size_t smf = sizeof(float) * 2 * (size_t)Rp * Rp;
+    if (smf <= 200 * 1024 && Rp <= 256) {
+      cudaFuncSetAttribute(lu_inverse_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
+      ++g_launches;
+      lu_inverse_f32_kernel<<<nb, Rp, smf, st>>>(R, Rp, reinterpret_cast<const float*>(luT), piv,
+                                                  reinterpret_cast<float*>(Ainv));
+      return;
+    }
+  }
   size_t f = sizeof(T) * (size_t)R * (R + 1), y = sizeof(T) * (size_t)R * R;
   int mode = (f + y <= cap) ? 2 : (f <= cap ? 1 : 0);
   size_t sm = mode == 2 ? f + y : (mode == 1 ? f : 0);

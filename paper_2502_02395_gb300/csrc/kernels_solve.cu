@@ -396,27 +396,53 @@ H2_INST_SOLVE(float)
 // solver of the mixed-precision refinement.  X, S and A are that level's
 // bases, couplings and leaf near blocks in T.
 
-// upward: xh_i[a] = sum_d X_i[d*K + a] x_i[d] (x_i: the box's D inputs)
+// upward: xh_i[a] = sum_d X_i[d*K + a] x_i[d] (x_i: the box's D inputs).
+// Warp w takes the rows d = w, w + 8, ...; lanes take the columns a; each
+// warp accumulates its partial sums in its own row of shared memory, then
+// the 8 partial rows are added.
 template <typename T>
-__global__ void mv_up_kernel(int D, int K, const T* __restrict__ X, const T* __restrict__ x, T* __restrict__ xh) {
-  const int i = blockIdx.x;
+__global__ void __launch_bounds__(256) mv_up_kernel(int D, int K, const T* __restrict__ X, const T* __restrict__ x,
+                                                    T* __restrict__ xh) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* part = reinterpret_cast<T*>(smraw);  // 8 * K
+  T* sx = part + 8 * K;                   // D
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* Xb = X + (int64_t)i * D * K;
-  const T* xb = x + (int64_t)i * D;
-  for (int a = threadIdx.x; a < K; a += blockDim.x) {
-    T s0 = 0, s1 = 0;
-    int d = 0;
-    for (; d + 1 < D; d += 2) {
-      s0 = fma(Xb[(int64_t)d * K + a], xb[d], s0);
-      s1 = fma(Xb[(int64_t)(d + 1) * K + a], xb[d + 1], s1);
+  for (int e = tid; e < D; e += 256) sx[e] = x[(int64_t)i * D + e];
+  for (int e = tid; e < 8 * K; e += 256) part[e] = T(0);
+  __syncthreads();
+  T* mine = part + warp * K;
+  for (int a0 = 0; a0 < K; a0 += 128) {
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    for (int d = warp; d < D; d += 8) {
+      const T xd = sx[d];
+      const T* row = Xb + (int64_t)d * K + a0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int a = a0 + lane + 32 * q;
+        if (a < K) acc[q] = fma(__ldg(row + lane + 32 * q), xd, acc[q]);
+      }
     }
-    if (d < D) s0 = fma(Xb[(int64_t)d * K + a], xb[d], s0);
-    xh[(int64_t)i * K + a] = s0 + s1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int a = a0 + lane + 32 * q;
+      if (a < K) mine[a] = acc[q];
+    }
+  }
+  __syncthreads();
+  for (int a = tid; a < K; a += 256) {
+    T s = T(0);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += part[w * K + a];
+    xh[(int64_t)i * K + a] = s;
   }
 }
 template <typename T>
 void launch_matvec_up(const DevLevel& L, const T* X, const T* x, T* xh, cudaStream_t st) {
+  const size_t sm = sizeof(T) * (8 * (size_t)L.K + L.D);
+  set_smem((const void*)mv_up_kernel<T>, sm);
   ++g_launches;
-  mv_up_kernel<T><<<L.nb, 128, 0, st>>>(L.D, L.K, X, x, xh);
+  mv_up_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.K, X, x, xh);
 }
 
 // couplings: yh_i = sum_{far j} S_f xh_j   (overwrites yh_i)
@@ -446,24 +472,28 @@ void launch_matvec_far(const DevLevel& L, const T* S, const T* xh, T* yh, cudaSt
   mv_far_kernel<T><<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, S, xh, yh);
 }
 
-// downward: [yh_2p; yh_2p+1] += X_p yh_p   (rows d of X_p, D = 2 Kc)
+// downward: [yh_2p; yh_2p+1] += X_p yh_p   (rows d of X_p, D = 2 Kc): a
+// block-row GEMV per parent box
 template <typename T>
-__global__ void mv_down_kernel(int D, int K, const T* __restrict__ X, const T* __restrict__ yh, T* __restrict__ yhc) {
+__global__ void __launch_bounds__(256, 2) mv_down_kernel(int D, int K, const T* __restrict__ X,
+                                                         const T* __restrict__ yh, T* __restrict__ yhc) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sy = reinterpret_cast<T*>(smraw);  // K
   const int p = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T* Xb = X + (int64_t)p * D * K;
-  const T* yp = yh + (int64_t)p * K;
-  for (int d = warp; d < D; d += nw) {
-    T s = 0;
-    for (int a = lane; a < K; a += 32) s = fma(Xb[(int64_t)d * K + a], yp[a], s);
-    s = warp_sum(s);
-    if (lane == 0) yhc[(int64_t)p * D + d] += s;
+  for (int e = threadIdx.x; e < K; e += 256) sy[e] = yh[(int64_t)p * K + e];
+  __syncthreads();
+  T acc[kRPW];
+  T* out = yhc + (int64_t)p * D;
+  for (int r0 = 0; r0 < D; r0 += kChunk) {
+    zero(acc);
+    rows_acc<T, kRPW>(r0, X + (int64_t)p * D * K, K, D, K, sy, acc);
+    rows_finish<T, kRPW>(r0, D, acc, T(1), out, out);
   }
 }
 template <typename T>
 void launch_matvec_down(const DevLevel& L, const T* X, const T* yh, T* yh_child, cudaStream_t st) {
   ++g_launches;
-  mv_down_kernel<T><<<L.nb, 256, 0, st>>>(L.D, L.K, X, yh, yh_child);
+  mv_down_kernel<T><<<L.nb, 256, sizeof(T) * ((L.K + 3) & ~3), st>>>(L.D, L.K, X, yh, yh_child);
 }
 
 // leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j

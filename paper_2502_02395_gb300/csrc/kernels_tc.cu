@@ -345,30 +345,27 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
 // ------------------------------------------------------------------------
 // operand preparation
 // ------------------------------------------------------------------------
-// amax[0] = max |x| over n entries of several strided sub-blocks:
-// block q holds rows x cols entries at base + q*stride + r*ld + c
+// amax[0] = max |x| over nblk strided sub-blocks: block q holds rows x cols
+// entries at base + q*stride + r*ld + c.  One CTA per block; warps over
+// rows, lanes over columns.
 template <typename S>
-__global__ void amax_blocks_kernel(const S* __restrict__ base, int64_t nblk, int64_t stride, int rows, int cols,
-                                   int ld, unsigned int* __restrict__ out) {
+__global__ void __launch_bounds__(256) amax_blocks_kernel(const S* __restrict__ base, int64_t nblk, int64_t stride,
+                                                          int rows, int cols, int ld, unsigned int* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float m = 0.0f;
-  const int64_t per = (int64_t)rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nblk * per;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t q = e / per;
-    int64_t rc = e - q * per;
-    int r = (int)(rc / cols), c = (int)(rc - (int64_t)r * cols);
-    float v = fabsf((float)base[q * stride + (int64_t)r * ld + c]);
-    m = fmaxf(m, v);
+  for (int64_t q = blockIdx.x; q < nblk; q += gridDim.x) {
+    const S* B = base + q * stride;
+    for (int r = warp; r < rows; r += 8)
+      for (int c = lane; c < cols; c += 32) m = fmaxf(m, fabsf((float)__ldg(B + (int64_t)r * ld + c)));
   }
   for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as uints
+  if (lane == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as uints
 }
 template <typename S>
 void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
                         cudaStream_t st) {
   if (nblk == 0 || rows == 0 || cols == 0) return;
-  int64_t n = nblk * rows * cols;
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  const int blocks = (int)std::min<int64_t>(nblk, 152 * 16);
   ++g_launches;
   amax_blocks_kernel<S><<<blocks, 256, 0, st>>>(base, nblk, stride, rows, cols, ld, out);
 }
@@ -417,40 +414,45 @@ template void launch_to_lowp<double>(int, const double*, void*, int64_t, const f
 
 // 16-bit merge (Algorithm 2 line 18-20 in the scaled low-precision layout):
 // child SS blocks (FP32 Ahat, rows/cols R..D) and couplings (FP32 Shat) go
-// to the parent's 16-bit near blocks, multiplied by scale[0].
-__global__ void merge_lowp_kernel(int D, int K, int64_t NP, const float* __restrict__ Ahat,
-                                  const int32_t* __restrict__ ni, const int32_t* __restrict__ nj,
-                                  const int32_t* __restrict__ ndst, int64_t FP, const float* __restrict__ Shat,
-                                  const int32_t* __restrict__ fi, const int32_t* __restrict__ fj,
-                                  const int32_t* __restrict__ fdst, void* __restrict__ Apar,
-                                  const float* __restrict__ scale, int bf16) {
+// to the parent's 16-bit near blocks, multiplied by scale[0].  One CTA per
+// child pair; warps over rows, lanes over columns.
+__global__ void __launch_bounds__(256) merge_lowp_kernel(int D, int K, int64_t NP, const float* __restrict__ Ahat,
+                                                         const int32_t* __restrict__ ni, const int32_t* __restrict__ nj,
+                                                         const int32_t* __restrict__ ndst, int64_t FP,
+                                                         const float* __restrict__ Shat, const int32_t* __restrict__ fi,
+                                                         const int32_t* __restrict__ fj, const int32_t* __restrict__ fdst,
+                                                         void* __restrict__ Apar, const float* __restrict__ scale,
+                                                         int bf16) {
   const int R = D - K, Dp = 2 * K;
-  const int64_t q = blockIdx.y + (int64_t)blockIdx.z * gridDim.y;
-  if (q >= NP + FP) return;
-  const bool nr = q < NP;
-  const int64_t qq = nr ? q : q - NP;
-  const int i = nr ? ni[qq] : fi[qq], j = nr ? nj[qq] : fj[qq];
-  const int64_t dst = nr ? ndst[qq] : fdst[qq];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float s = scale[0];
-  const int64_t obase = dst * Dp * Dp + (int64_t)(i & 1) * K * Dp + (j & 1) * K;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * K; e += gridDim.x * blockDim.x) {
-    int a = e / K, b = e - a * K;
-    float v = (nr ? Ahat[qq * D * D + (int64_t)(R + a) * D + R + b] : Shat[qq * K * K + e]) * s;
-    int64_t o = obase + (int64_t)a * Dp + b;
-    if (bf16) reinterpret_cast<__nv_bfloat16*>(Apar)[o] = __float2bfloat16_rn(v);
-    else reinterpret_cast<__half*>(Apar)[o] = __float2half_rn(v);
+  for (int64_t q = blockIdx.x; q < NP + FP; q += gridDim.x) {
+    const bool nr = q < NP;
+    const int64_t qq = nr ? q : q - NP;
+    const int i = nr ? ni[qq] : fi[qq], j = nr ? nj[qq] : fj[qq];
+    const int64_t dst = nr ? ndst[qq] : fdst[qq];
+    const float* src = nr ? Ahat + qq * D * D + (int64_t)R * D + R : Shat + qq * K * K;
+    const int lds = nr ? D : K;
+    const int64_t obase = dst * Dp * Dp + (int64_t)(i & 1) * K * Dp + (j & 1) * K;
+    for (int a = warp; a < K; a += 8) {
+      const float* row = src + (int64_t)a * lds;
+      const int64_t o = obase + (int64_t)a * Dp;
+      for (int b = lane; b < K; b += 32) {
+        const float v = __ldg(row + b) * s;
+        if (bf16) reinterpret_cast<__nv_bfloat16*>(Apar)[o + b] = __float2bfloat16_rn(v);
+        else reinterpret_cast<__half*>(Apar)[o + b] = __float2half_rn(v);
+      }
+    }
   }
 }
 void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_t* ni, const int32_t* nj,
                        const int32_t* ndst, int64_t FP, const float* Shat, const int32_t* fi, const int32_t* fj,
                        const int32_t* fdst, void* Apar, const float* scale, int bf16, cudaStream_t st) {
-  int64_t n = NP + FP;
+  const int64_t n = NP + FP;
   if (n == 0 || K == 0) return;
-  int gx = std::min(64, (K * K + 255) / 256);
-  int64_t gy = std::min<int64_t>(n, 65535), gz = (n + gy - 1) / gy;
+  const int blocks = (int)std::min<int64_t>(n, 152 * 16);
   ++g_launches;
-  merge_lowp_kernel<<<dim3(gx, (unsigned)gy, (unsigned)gz), 256, 0, st>>>(D, K, NP, Ahat, ni, nj, ndst, FP, Shat, fi,
-                                                                           fj, fdst, Apar, scale, bf16);
+  merge_lowp_kernel<<<blocks, 256, 0, st>>>(D, K, NP, Ahat, ni, nj, ndst, FP, Shat, fi, fj, fdst, Apar, scale, bf16);
 }
 
 }  // namespace h2
