@@ -81,6 +81,19 @@ h2_status make_leaf_lowp(h2_ctx* c, int bf16) {
   launch_amax_blocks<double>(c->A64, lf.NP, (int64_t)lf.D * lf.D, lf.D, lf.D, lf.D, amax, c->stream);
   launch_pow2_scale(amax, 128.0f, c->A16_scale[bf16], c->stream);
   launch_to_lowp<double>(bf16, c->A64, c->A16[bf16], n, c->A16_scale[bf16], c->stream);
+  // couplings, per level, with max |S| scaled to sqrt(32768 / K): the
+  // tensor-core coupling products then stay inside FP16 (|S T^T| <= 32768)
+  for (int l = 1; l <= c->L; ++l) {
+    DevLevel& d = c->lv[l];
+    if (d.FP == 0 || d.K == 0) continue;
+    const int64_t ns = d.FP * (int64_t)d.K * d.K;
+    CKC(dalloc(c, &d.S16_scale[bf16], 2));
+    CKC(dalloc(c, reinterpret_cast<uint16_t**>(&d.S16[bf16]), ns));
+    CKC(cudaMemsetAsync(amax, 0, sizeof(unsigned int), c->stream));
+    launch_amax_blocks<double>(d.S, d.FP, (int64_t)d.K * d.K, d.K, d.K, d.K, amax, c->stream);
+    launch_pow2_scale(amax, std::sqrt(32768.0f / d.K), d.S16_scale[bf16], c->stream);
+    launch_to_lowp<double>(bf16, d.S, d.S16[bf16], ns, d.S16_scale[bf16], c->stream);
+  }
   CKC(cudaGetLastError());
   CKC(cudaStreamSynchronize(c->stream));
   return H2_OK;
@@ -260,6 +273,11 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
       CKC(dalloc(c, reinterpret_cast<uint16_t**>(&f.U16), nb * D * D));
       wk16 = std::max(wk16, (size_t)d.NP * D * D);
     }
+    f.tc_coup = mixed && d.FP > 0 && gemm_tc_supported(d.K, d.K, d.K, d.K, d.K, d.K);
+    if (f.tc_coup) {
+      CKC(dalloc(c, reinterpret_cast<uint16_t**>(&f.T16), nb * K * K));
+      wk16 = std::max(wk16, (size_t)d.FP * K * K);
+    }
     CKC(dalloc(c, &f.U, nb * D * D));
     CKC(dalloc(c, &f.Tm, nb * K * K));
     CKC(dalloc(c, &f.Xo, nb * D * K));
@@ -283,6 +301,8 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   CKC(dalloc(c, &F.Wk, wk));
   if (wk16) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&F.W16), wk16));
   CKC(dalloc(c, &F.scales, 2 * (size_t)(L + 1)));
+  CKC(dalloc(c, &F.tscale, 2 * (size_t)(L + 1)));
+  CKC(dalloc(c, &F.cscale, (size_t)(L + 1)));
   CKC(dalloc(c, &F.amax, (size_t)(L + 1)));
   CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
   if (std::is_same<T, double>::value) F.root_luT = reinterpret_cast<T*>(F.root_lu);
@@ -319,7 +339,9 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   mark();
   const int bf16 = (prec == H2_PREC_BF16) ? 1 : 0;
   const bool mixed = !std::is_same<T, double>::value;
-  if (mixed && L >= 1 && F.lv[L].tc) CKS(make_leaf_lowp(c, bf16));
+  bool any_tc = false;
+  for (int l = 1; l <= L; ++l) any_tc = any_tc || F.lv[l].tc || F.lv[l].tc_coup;
+  if (mixed && any_tc) CKS(make_leaf_lowp(c, bf16));
   mark();
   const T* Aleaf = nullptr;
   if (!mixed) {
@@ -406,7 +428,24 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     }
     mark();
     // a2': couplings Shat_ij = T_i S_ij T_j^T
-    if (d.FP > 0 && K > 0) {
+    if (d.FP > 0 && K > 0 && f.tc_coup) {
+      // tensor cores: V^T = (S_s T_j,s^T)^T in 16 bits, then Shat = T_i,s V / (s_S s_T^2)
+      const int64_t KK = (int64_t)K * K;
+      unsigned int* am = F.amax + l;
+      CKC(cudaMemsetAsync(am, 0, sizeof(unsigned int), st));
+      launch_amax_blocks<T>(f.Tm, d.nb, KK, K, K, K, am, st);
+      launch_pow2_scale(am, std::sqrt(32768.0f / K), F.tscale + 2 * l, st);
+      launch_to_lowp<T>(bf16, f.Tm, f.T16, d.nb * KK, F.tscale + 2 * l, st);
+      launch_inv_scale_product(d.S16_scale[bf16], F.tscale + 2 * l, F.cscale + l, st);
+      bool ok = gemm_tc(bf16, K, K, K, d.S16[bf16], d.FP, K, K, nullptr, f.T16, d.nb, K, K, d.far_j, F.W16, KK,
+                        nullptr, K, 1, bf16, 1.0f, nullptr, d.FP, c->status + 2, st) &&
+                gemm_tc(bf16, K, K, K, f.T16, d.nb, K, K, d.far_i, F.W16, d.FP, K, K, nullptr, f.Shat, KK, nullptr, K,
+                        0, 0, 1.0f, F.cscale + l, d.FP, c->status + 2, st);
+      if (!ok) {
+        c->err = "tensor-core coupling GEMM setup failed at level " + std::to_string(l);
+        return H2_ERR_CUDA;
+      }
+    } else if (d.FP > 0 && K > 0) {
       const int64_t KK = (int64_t)K * K;
       const T* Sc = std::is_same<T, double>::value ? reinterpret_cast<const T*>(d.S) : reinterpret_cast<const T*>(d.S32);
       gemm<T>(prec, K, K, K, Sc, KK, nullptr, K, false, f.Tm, KK, d.far_j, K, true, F.Wk, KK, nullptr, K, T(1),

@@ -114,6 +114,8 @@ struct DevLevel {
   double* S = nullptr;    // FP * K * K couplings G(SK_i, SK_j)
   float* X32 = nullptr;   // FP32 copies for the inner solver of the mixed refinement
   float* S32 = nullptr;
+  void* S16[2] = {nullptr, nullptr};        // couplings scaled into FP16 [0] / BF16 [1]
+  float* S16_scale[2] = {nullptr, nullptr};  // their scale and inverse scale (device)
 };
 
 // Factorization storage of one level in storage type T (double or float).
@@ -140,6 +142,8 @@ struct FacLevel {
   bool tc = false;
   void* Ain16 = nullptr;  // NP * D * D (scale in Factor::scales[2l], inverse at [2l+1])
   void* U16 = nullptr;    // nb * D * D, column-major like U
+  bool tc_coup = false;   // couplings on the tensor cores
+  void* T16 = nullptr;    // nb * K * K scaled 16-bit T (scale in Factor::tscale[2l])
 };
 
 template <typename T>
@@ -155,6 +159,8 @@ struct Factor {
   T* Wk = nullptr;            // workspace: max NP * D * D
   void* W16 = nullptr;        // 16-bit workspace: max NP * D * D (tensor-core path)
   float* scales = nullptr;    // 2 (L + 1): per-level operand scale and its inverse
+  float* tscale = nullptr;    // 2 (L + 1): scale of T16 and its inverse
+  float* cscale = nullptr;    // L + 1: 1 / (scale(S16) scale(T16)^2) for the couplings
   unsigned int* amax = nullptr;  // L + 1 max-abs accumulators
   int bf16 = -1;              // operand type the 16-bit buffers hold
 };

@@ -48,6 +48,7 @@ template <typename S>
 void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
                         cudaStream_t st);
 void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale, cudaStream_t st);
+void launch_inv_scale_product(const float* a, const float* b, float* out, cudaStream_t st);
 template <typename S>
 void launch_to_lowp(int bf16, const S* in, void* out, int64_t n, const float* scale, cudaStream_t st);
 void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_t* ni, const int32_t* nj,

@@ -391,6 +391,16 @@ void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale
   pow2_scale_kernel<<<1, 1, 0, st>>>(amax_bits, target, scale);
 }
 
+// out[0] = 1 / (a[0] * b[0] * b[0])  (the inverse scale of a product A B B^T)
+__global__ void inv_scale_product_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                         float* __restrict__ out) {
+  out[0] = 1.0f / (a[0] * b[0] * b[0]);
+}
+void launch_inv_scale_product(const float* a, const float* b, float* out, cudaStream_t st) {
+  ++g_launches;
+  inv_scale_product_kernel<<<1, 1, 0, st>>>(a, b, out);
+}
+
 // out16[e] = (16-bit) (in[e] * scale[0])
 template <typename S>
 __global__ void to_lowp_kernel(const S* __restrict__ in, void* __restrict__ out, int64_t n, const float* __restrict__ scale,

@@ -205,6 +205,11 @@ def test_tensor_core_projection_leaf(B, prec):
     # the bases are orthogonal to FP32 accuracy
     for i in range(nb):
         assert np.abs(U[i] @ U[i].T - np.eye(D)).max() <= 1e-5
+    # couplings T_i S_ij T_j^T on the tensor cores (16-bit operands)
+    Sh = S.export("Shat", L).reshape(-1, K, K).astype(np.float64)
+    for q, p in enumerate(H["far"][L]):
+        ref = F["Shat"][L][p]
+        assert np.linalg.norm(Sh[q] - ref) <= tol * np.linalg.norm(ref), (q, p)
     S.close()
 
 
