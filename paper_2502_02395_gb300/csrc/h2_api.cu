@@ -147,6 +147,20 @@ h2_status setup_device(h2_ctx* c) {
     CKS(upload(c, &d.near_i, d.h_near_i));
     CKS(upload(c, &d.near_j, d.h_near_j));
     CKS(upload(c, &d.near_ptr, d.h_near_ptr));
+    {
+      std::vector<int32_t> lo, hi, loc(d.nb, 0), hic(d.nb, 0);
+      for (int64_t q = 0; q < d.NP; ++q) {
+        const int i = d.h_near_i[q], j = d.h_near_j[q];
+        if (j <= i) lo.push_back((int32_t)q), ++loc[i];
+        if (j >= i) hi.push_back((int32_t)q), ++hic[i];
+      }
+      d.n_lo = (int64_t)lo.size();
+      d.n_hi = (int64_t)hi.size();
+      CKS(upload(c, &d.lo_pairs, lo));
+      CKS(upload(c, &d.hi_pairs, hi));
+      CKS(upload(c, &d.lo_cnt, loc));
+      CKS(upload(c, &d.hi_cnt, hic));
+    }
     CKS(upload(c, &d.diag_pair, d.h_diag_pair));
     CKS(upload(c, &d.far_i, d.h_far_i));
     CKS(upload(c, &d.far_j, d.h_far_j));
@@ -287,6 +301,7 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     if (sizeof(T) * D * K > 200 * 1024) CKC(dalloc(c, &f.Qs, nb * D * K));
     wk = std::max(wk, nb * (K * K + D * K));
     CKC(dalloc(c, &f.Ahat, (size_t)d.NP * D * D));
+    if (f.tc) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&f.Ahat16), (size_t)d.NP * D * D));
     CKC(dalloc(c, &f.Shat, (size_t)std::max<int64_t>(d.FP, 1) * K * K));
     CKC(dalloc(c, &f.Z, nb * R * K));
     CKC(dalloc(c, &f.lu, nb * R * R));
@@ -298,6 +313,13 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     for (T** p : {&f.u, &f.v, &f.om}) CKC(dalloc(c, p, nb * std::max<size_t>(R, 1)));
   }
   const int D0 = c->lv[0].D;
+  size_t npart = 1;
+  for (int l = 1; l <= L; ++l) {
+    const DevLevel& d = c->lv[l];
+    npart = std::max(npart, (size_t)d.NP * (size_t)std::max(d.R, d.K));
+  }
+  CKC(dalloc(c, &F.part, npart));
+  for (int l = 1; l <= L; ++l) F.lv[l].part = F.part;
   CKC(dalloc(c, &F.Wk, wk));
   if (wk16) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&F.W16), wk16));
   CKC(dalloc(c, &F.scales, 2 * (size_t)(L + 1)));
@@ -338,6 +360,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   // phase boundaries per level: [start, a1, a2, a3, a45, a2c, a6]
   mark();
   const int bf16 = (prec == H2_PREC_BF16) ? 1 : 0;
+  F.bf16 = bf16;
   const bool mixed = !std::is_same<T, double>::value;
   bool any_tc = false;
   for (int l = 1; l <= L; ++l) any_tc = any_tc || F.lv[l].tc || F.lv[l].tc_coup;
@@ -400,10 +423,15 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       const void* A16 = (l == L) ? c->A16[bf16] : f.Ain16;
       const float* sc = (l == L) ? c->A16_scale[bf16] : F.scales + 2 * l;
       launch_to_lowp<T>(bf16, f.U, f.U16, (int64_t)d.nb * DD, nullptr, st);
+      // The second GEMM also writes its raw accumulator s * Ahat in 16 bits
+      // for the substitution.  |s Ahat_ij| <= ||s A_ij||_2 <= 128 D, inside
+      // the FP16 range for D <= 256 (BF16 has the FP32 exponent range).
+      const bool sub16 = bf16 || D <= 256;
+      f.ahat_isc = sub16 ? sc + 1 : nullptr;
       bool ok = gemm_tc(bf16, D, D, D, A16, d.NP, D, D, nullptr, f.U16, d.nb, D, D, d.near_j, F.W16, DD, nullptr, D,
                         1, bf16, 1.0f, nullptr, d.NP, c->status + 2, st) &&
                 gemm_tc(bf16, D, D, D, f.U16, d.nb, D, D, d.near_i, F.W16, d.NP, D, D, nullptr, f.Ahat, DD, nullptr, D,
-                        0, 0, 1.0f, sc + 1, d.NP, c->status + 2, st);
+                        0, 0, 1.0f, sc + 1, d.NP, c->status + 2, st, sub16 ? f.Ahat16 : nullptr);
       if (!ok) {
         c->err = "tensor-core GEMM setup failed at level " + std::to_string(l);
         return H2_ERR_CUDA;
@@ -525,6 +553,21 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
 // ---------------------------------------------------------------------------
 // One sweep: input in the leaf level's vin (root_vec when L = 0), output in
 // the leaf level's xs (root_x when L = 0).
+// Calls fn(Ahat, iscale) with the level's projected blocks in the type the
+// substitution reads them in: the 16-bit copy s * Ahat with 1 / s where the
+// factorization wrote one, else Ahat itself with no scale.
+template <typename T, typename Fn>
+void with_ahat(const FacLevel<T>& f, int bf16, Fn&& fn) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (f.Ahat16 && f.ahat_isc) {
+      if (bf16) fn(reinterpret_cast<const __nv_bfloat16*>(f.Ahat16), f.ahat_isc);
+      else fn(reinterpret_cast<const __half*>(f.Ahat16), f.ahat_isc);
+      return;
+    }
+  }
+  fn(static_cast<const T*>(f.Ahat), static_cast<const float*>(nullptr));
+}
+
 template <typename T>
 void ulv_sweep(h2_ctx* c, Factor<T>& F) {
   const int L = c->L;
@@ -534,16 +577,22 @@ void ulv_sweep(h2_ctx* c, Factor<T>& F) {
     FacLevel<T>& f = F.lv[l];
     T* pv = (l > 1) ? F.lv[l - 1].vin : F.root_vec;
     launch_fwd1<T>(d, f, f.Ainv, st);
-    launch_fwd2<T>(d, f, f.Ainv, st);
-    launch_fwd3<T>(d, f, pv, st);
+    with_ahat(f, F.bf16, [&](auto A, const float* isc) {
+      using TS = std::remove_const_t<std::remove_pointer_t<decltype(A)>>;
+      launch_fwd2<T, TS>(d, f, A, isc, st);
+      launch_fwd3<T, TS>(d, f, A, isc, pv, st);
+    });
   }
   launch_gemv_rows<T>(c->lv[0].D, F.root_inv, F.root_vec, F.root_x, st);
   for (int l = 1; l <= L; ++l) {
     const DevLevel& d = c->lv[l];
     FacLevel<T>& f = F.lv[l];
     const T* px = (l > 1) ? F.lv[l - 1].xs : F.root_x;
-    launch_bwd1<T>(d, f, f.Ainv, px, st);
-    launch_bwd2<T>(d, f, f.Ainv, px, st);
+    with_ahat(f, F.bf16, [&](auto A, const float* isc) {
+      using TS = std::remove_const_t<std::remove_pointer_t<decltype(A)>>;
+      launch_bwd1<T, TS>(d, f, A, isc, px, st);
+      launch_bwd2<T, TS>(d, f, A, isc, px, st);
+    });
   }
 }
 template <typename T>
@@ -1125,7 +1174,10 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
   for (int l = 1; l <= c->L; ++l) {
     const DevLevel& d = c->lv[l];
     const double D = d.D, K = d.K, R = d.R;
-    by_sub += w * ((double)(d.NP - d.nb) * R * R + (double)d.NP * 2.0 * R * K + d.nb * (2.0 * D * D + 4.0 * R * R));
+    // Ahat read in 16 bits where the factorization kept a 16-bit copy
+    const bool a16 = c->prec != H2_PREC_FP64 && (int)c->f32.lv.size() > l && c->f32.lv[l].ahat_isc;
+    const double wa = a16 ? 2.0 : w;
+    by_sub += wa * ((double)(d.NP - d.nb) * R * R + (double)d.NP * 2.0 * R * K) + w * d.nb * (2.0 * D * D + 4.0 * R * R);
     by_mv += 8.0 * (2.0 * d.nb * D * K + (double)d.FP * K * K);
     fl_mv += 2.0 * (2.0 * d.nb * D * K + (double)d.FP * K * K);
   }

@@ -105,6 +105,11 @@ struct DevLevel {
   int32_t *far_i = nullptr, *far_j = nullptr;    // FP
   int64_t* far_ptr = nullptr;                    // nb + 1
   int32_t *near_dst = nullptr, *far_dst = nullptr;  // parent near-pair index of each pair
+  // sub-lists of the near pairs for the substitution: j <= i (lo) and j >= i
+  // (hi), in pair order, with their count per box
+  int32_t *lo_pairs = nullptr, *hi_pairs = nullptr;
+  int32_t *lo_cnt = nullptr, *hi_cnt = nullptr;
+  int64_t n_lo = 0, n_hi = 0;
   // host copies
   std::vector<int32_t> h_near_i, h_near_j, h_far_i, h_far_j, h_diag_pair, h_near_dst, h_far_dst;
   std::vector<int64_t> h_near_ptr, h_far_ptr;
@@ -138,12 +143,20 @@ struct FacLevel {
   int32_t* piv = nullptr;  // nb * R (LAPACK-style row interchanges)
   // substitution vectors
   T *vin = nullptr, *c = nullptr, *u = nullptr, *v = nullptr, *om = nullptr, *xs = nullptr;
+  // per-pair partial products of the substitution (Factor::part, shared by
+  // all levels)
+  T* part = nullptr;
   // tensor-core path (mixed precision): 16-bit scaled input blocks and bases
   bool tc = false;
   void* Ain16 = nullptr;  // NP * D * D (scale in Factor::scales[2l], inverse at [2l+1])
   void* U16 = nullptr;    // nb * D * D, column-major like U
   bool tc_coup = false;   // couplings on the tensor cores
   void* T16 = nullptr;    // nb * K * K scaled 16-bit T (scale in Factor::tscale[2l])
+  // s * Ahat in 16 bits (same layout as Ahat), read by the substitution in
+  // place of the FP32 Ahat; ahat_isc -> 1 / s on the device.  NULL where the
+  // level keeps the substitution on the FP32 Ahat.
+  void* Ahat16 = nullptr;
+  const float* ahat_isc = nullptr;
 };
 
 template <typename T>
@@ -158,6 +171,7 @@ struct Factor {
   T* root_x = nullptr;        // D0
   T* Wk = nullptr;            // workspace: max NP * D * D
   void* W16 = nullptr;        // 16-bit workspace: max NP * D * D (tensor-core path)
+  T* part = nullptr;          // max NP * max(R, K): partial products of the substitution
   float* scales = nullptr;    // 2 (L + 1): per-level operand scale and its inverse
   float* tscale = nullptr;    // 2 (L + 1): scale of T16 and its inverse
   float* cscale = nullptr;    // L + 1: 1 / (scale(S16) scale(T16)^2) for the couplings

@@ -43,7 +43,7 @@ bool gemm_tc_supported(int M, int N, int K, int lda, int ldb, int ldc);
 bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int rowsA, int lda, const int32_t* ia,
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
-             int64_t batch, int32_t* err, cudaStream_t st);
+             int64_t batch, int32_t* err, cudaStream_t st, void* C2 = nullptr);
 template <typename S>
 void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
                         cudaStream_t st);
@@ -57,16 +57,21 @@ void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_
 
 // kernels_solve.cu: substitution (Eq. 24-31 and its mirror), H^2 matvec,
 // refinement vector operations
+// Ahat of level L in storage type TS (T itself, or 16-bit scaled by s with
+// iscale -> 1/s on the device; iscale NULL means 1)
 template <typename T>
 void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st);
-template <typename T>
-void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st);
-template <typename T>
-void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, T* parent_vin, cudaStream_t st);
-template <typename T>
-void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st);
-template <typename T>
-void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st);
+template <typename T, typename TS>
+void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, cudaStream_t st);
+template <typename T, typename TS>
+void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, T* parent_vin,
+                 cudaStream_t st);
+template <typename T, typename TS>
+void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
+                 cudaStream_t st);
+template <typename T, typename TS>
+void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
+                 cudaStream_t st);
 template <typename T>
 void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st);  // y = M x, M n x n row-major
 

@@ -76,65 +76,130 @@ __device__ __forceinline__ void warp_rows_gemv(const T* __restrict__ M, int64_t 
 // reduction happens once per row at the end.  Rows are read with 16-byte
 // vector loads when the layout allows.
 // ------------------------------------------------------------------------
-template <typename T>
-struct Vec16;
+// Vector loads of the stored matrix entries, converted to the compute type:
+// 16 bytes of FP32 / FP64, 8 bytes (4 entries) of FP16 / BF16.
+template <typename TS>
+struct Ld;
 template <>
-struct Vec16<float> {
-  using V = float4;
-  static constexpr int n = 4;
-  __device__ static V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-  __device__ static float fma4(const V& a, const V& x, float s) {
-    s = fmaf(a.x, x.x, s);
-    s = fmaf(a.y, x.y, s);
-    s = fmaf(a.z, x.z, s);
-    return fmaf(a.w, x.w, s);
+struct Ld<float> {
+  static constexpr int VN = 4;
+  template <typename T>
+  __device__ static void get(const float* p, T (&o)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
   }
 };
 template <>
-struct Vec16<double> {
-  using V = double2;
-  static constexpr int n = 2;
-  __device__ static V zero() { return make_double2(0.0, 0.0); }
-  __device__ static double fma4(const V& a, const V& x, double s) { return fma(a.y, x.y, fma(a.x, x.x, s)); }
+struct Ld<double> {
+  static constexpr int VN = 2;
+  template <typename T>
+  __device__ static void get(const double* p, T (&o)[2]) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    o[0] = v.x, o[1] = v.y;
+  }
+};
+template <>
+struct Ld<__half> {
+  static constexpr int VN = 4;
+  template <typename T>
+  __device__ static void get(const __half* p, T (&o)[4]) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+  }
+};
+template <>
+struct Ld<__nv_bfloat16> {
+  static constexpr int VN = 4;
+  template <typename T>
+  __device__ static void get(const __nv_bfloat16* p, T (&o)[4]) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&v.y));
+    o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+  }
+};
+// exact conversion of one stored entry to the compute type
+template <typename T, typename TS>
+struct Cvt {
+  __device__ static T go(TS v) { return (T)v; }
+};
+template <typename T>
+struct Cvt<T, __half> {
+  __device__ static T go(__half v) { return (T)__half2float(v); }
+};
+template <typename T>
+struct Cvt<T, __nv_bfloat16> {
+  __device__ static T go(__nv_bfloat16 v) { return (T)__bfloat162float(v); }
 };
 
-// acc[t] += sum_c M[r_t * ld + c] xs[c] for the rows r_t = r0 + warp + 8 t < nr.
-// For each column chunk every lane first issues the loads of all its rows,
-// then does the multiply-adds, so RPW independent 16-byte loads per lane are
-// in flight at once.
+// acc[t] += sum_{c0 <= c < c1} M[r_t * ld + c] xs[c], one column per lane
+template <typename TS, typename T, int RPW>
+__device__ __forceinline__ void rows_acc_scalar(int rbase, int c0, int c1, const TS* __restrict__ M, int64_t ld,
+                                                int nr, const T* __restrict__ xs, T (&acc)[RPW]) {
+  const int lane = threadIdx.x & 31;
+  for (int c = c0 + lane; c < c1; c += 32) {
+    T v[RPW];
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      const int r = rbase + 8 * t;
+      v[t] = (r < nr) ? Cvt<T, TS>::go(M[r * ld + c]) : T(0);
+    }
+    const T x = xs[c];
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) acc[t] = fma(v[t], x, acc[t]);
+  }
+}
+
+// acc[t] += sum_c M[r_t * ld + c] xs[c] for the rows r_t = r0 + warp + 8 t < nr
+// (M stored as TS, accumulation in T).  Columns are read with vector loads
+// (a few leading and trailing columns one by one where M's alignment or nc
+// asks for it).  For each column chunk every lane first issues the loads of
+// all its rows, then does the multiply-adds, so RPW independent vector loads
+// per lane are in flight at once.
+template <typename TS, typename T, int RPW>
+__device__ __forceinline__ void rows_acc2(int r0, const TS* __restrict__ M, int64_t ld, int nr, int nc,
+                                          const T* __restrict__ xs, T (&acc)[RPW]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int VN = Ld<TS>::VN;
+  const int rbase = r0 + warp;
+  const uintptr_t addr = reinterpret_cast<uintptr_t>(M);
+  if ((ld % VN) != 0 || (addr % sizeof(TS)) != 0) {
+    rows_acc_scalar<TS, T, RPW>(rbase, 0, nc, M, ld, nr, xs, acc);
+    return;
+  }
+  const int mis = (int)((addr / sizeof(TS)) % VN);
+  const int head = min(nc, (VN - mis) % VN);
+  const int cv1 = head + (nc - head) / VN * VN;
+  if (head > 0) rows_acc_scalar<TS, T, RPW>(rbase, 0, head, M, ld, nr, xs, acc);
+  for (int c = head + lane * VN; c < cv1; c += 32 * VN) {
+    T v[RPW][VN];
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      const int r = rbase + 8 * t;
+      if (r < nr) {
+        Ld<TS>::get(M + r * ld + c, v[t]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VN; ++e) v[t][e] = T(0);
+      }
+    }
+    T x[VN];
+#pragma unroll
+    for (int e = 0; e < VN; ++e) x[e] = xs[c + e];
+#pragma unroll
+    for (int t = 0; t < RPW; ++t)
+#pragma unroll
+      for (int e = 0; e < VN; ++e) acc[t] = fma(v[t][e], x[e], acc[t]);
+  }
+  if (cv1 < nc) rows_acc_scalar<TS, T, RPW>(rbase, cv1, nc, M, ld, nr, xs, acc);
+}
+
 template <typename T, int RPW>
 __device__ __forceinline__ void rows_acc(int r0, const T* __restrict__ M, int64_t ld, int nr, int nc,
                                          const T* __restrict__ xs, T (&acc)[RPW]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  using VT = typename Vec16<T>::V;
-  constexpr int VN = Vec16<T>::n;
-  const bool vec = ((ld % VN) == 0) && ((nc % (32 * VN)) == 0) && ((reinterpret_cast<uintptr_t>(M) & 15) == 0);
-  const int rbase = r0 + warp;
-  if (vec) {
-    for (int c = lane; c < nc / VN; c += 32) {
-      VT v[RPW];
-#pragma unroll
-      for (int t = 0; t < RPW; ++t) {
-        const int r = rbase + 8 * t;
-        v[t] = (r < nr) ? __ldg(reinterpret_cast<const VT*>(M + r * ld) + c) : Vec16<T>::zero();
-      }
-      const VT x = *reinterpret_cast<const VT*>(xs + c * VN);
-#pragma unroll
-      for (int t = 0; t < RPW; ++t) acc[t] = Vec16<T>::fma4(v[t], x, acc[t]);
-    }
-  } else {
-    for (int c = lane; c < nc; c += 32) {
-      T v[RPW];
-#pragma unroll
-      for (int t = 0; t < RPW; ++t) {
-        const int r = rbase + 8 * t;
-        v[t] = (r < nr) ? __ldg(M + r * ld + c) : T(0);
-      }
-      const T x = xs[c];
-#pragma unroll
-      for (int t = 0; t < RPW; ++t) acc[t] = fma(v[t], x, acc[t]);
-    }
-  }
+  rows_acc2<T, T, RPW>(r0, M, ld, nr, nc, xs, acc);
 }
 
 // out[r] = base[r] + sign * sum over lanes of acc (rows owned by this warp)
@@ -158,170 +223,369 @@ __device__ __forceinline__ void zero(T (&acc)[RPW]) {
 constexpr int kRPW = 16;  // rows per warp per pass: 128-row chunks with 8 warps
 constexpr int kChunk = 8 * kRPW;
 
+// ------------------------------------------------------------------------
+// CTA-wide GEMV on 16-byte chunks.
+// ------------------------------------------------------------------------
+// One 16-byte chunk of stored entries (VN of them) converted to T.
+template <typename TS>
+struct Chunk;
+template <>
+struct Chunk<float> {
+  static constexpr int VN = 4;
+  template <typename T>
+  __device__ static void cvt(const uint4& u, T (&o)[4]) {
+    o[0] = __uint_as_float(u.x), o[1] = __uint_as_float(u.y), o[2] = __uint_as_float(u.z), o[3] = __uint_as_float(u.w);
+  }
+};
+template <>
+struct Chunk<double> {
+  static constexpr int VN = 2;
+  template <typename T>
+  __device__ static void cvt(const uint4& u, T (&o)[2]) {
+    o[0] = __hiloint2double((int)u.y, (int)u.x), o[1] = __hiloint2double((int)u.w, (int)u.z);
+  }
+};
+template <>
+struct Chunk<__half> {
+  static constexpr int VN = 8;
+  template <typename T>
+  __device__ static void cvt(const uint4& u, T (&o)[8]) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+      o[2 * k] = f.x, o[2 * k + 1] = f.y;
+    }
+  }
+};
+template <>
+struct Chunk<__nv_bfloat16> {
+  static constexpr int VN = 8;
+  template <typename T>
+  __device__ static void cvt(const uint4& u, T (&o)[8]) {
+    // a BF16 value is the upper half of the FP32 with the same bits
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+
+// 16-byte loads each lane keeps in flight: 128 rows of 256 bytes per pass
+// of a 256-thread CTA (a 128 x 128 block in 16 bits or a 128 x 64 one in
+// 32 bits) ...
+template <typename TS>
+struct Unr {
+  static constexpr int v = 8;
+};
+// ... and 128 rows of 512 bytes for 4- and 8-byte entries
+template <>
+struct Unr<float> {
+  static constexpr int v = 16;
+};
+template <>
+struct Unr<double> {
+  static constexpr int v = 16;
+};
+
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
+// y[r] = (base ? base[r] : 0) + alpha * sum_{c < nc} M[r * ld + c] xs[c] for
+// r < nr, by all threads of the CTA (M stored as TS, arithmetic in T; xs in
+// shared memory; nc <= ld).  A row's 16-byte chunks are spread over cpr lanes
+// (the smallest power of two covering them, at most 32), so one warp load
+// covers 32 / cpr rows; each lane issues UNR such loads before it uses them.
+// A chunk that runs past column nc (but, as nc <= ld and ld is a multiple of
+// the chunk, not past the row) is loaded whole and its extra entries are
+// zeroed.  hook() runs once, in every thread, after the first loads have been
+// issued and before xs is read: it is where the caller fills xs (and
+// synchronizes), so that filling xs overlaps the first round trip to memory.
+// Rows of a misaligned M are read entry by entry.  y is written by one lane
+// per row, with no barrier afterwards.
+template <typename TS, typename T, int UNR, typename Hook = NoHook>
+__device__ __forceinline__ void cta_gemv(const TS* __restrict__ M, int64_t ld, int nr, int nc,
+                                         const T* xs, T alpha, const T* base, T* y, Hook hook = Hook()) {
+  constexpr int VN = Chunk<TS>::VN;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool vec = ((reinterpret_cast<uintptr_t>(M) & 15) == 0) && ((ld * (int64_t)sizeof(TS)) % 16 == 0);
+  if (!vec || nr <= 0 || nc <= 0) {
+    hook();
+    for (int r = warp; r < nr; r += nw) {
+      T s = T(0);
+      for (int c = lane; c < nc; c += 32) s = fma(Cvt<T, TS>::go(M[r * ld + c]), xs[c], s);
+      s = warp_sum(s);
+      if (lane == 0) y[r] = (base ? base[r] : T(0)) + alpha * s;
+    }
+    return;
+  }
+  const int nch = (nc + VN - 1) / VN;
+  int cpr = 32;
+  while (cpr > 1 && cpr / 2 >= nch) cpr >>= 1;
+  const int rpi = 32 / cpr, sub = lane / cpr, cl = lane & (cpr - 1);
+  const int rows_pass = nw * UNR * rpi;
+  const int nit = (nch + cpr - 1) / cpr;  // chunk rounds per pass (the same in every lane)
+  bool first = true;
+  for (int rb = 0; rb < nr; rb += rows_pass) {
+    T acc[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) acc[u] = T(0);
+    for (int it = 0; it < nit; ++it) {
+      const int ch = cl + it * cpr;
+      const int c = ch * VN;
+      uint4 raw[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int r = rb + (u * nw + warp) * rpi + sub;
+        raw[u] = (ch < nch && r < nr) ? __ldg(reinterpret_cast<const uint4*>(M + r * ld + c)) : make_uint4(0, 0, 0, 0);
+      }
+      if (first) {
+        hook();
+        first = false;
+      }
+      if (ch < nch) {
+        const int lim = nc - c;  // valid entries of this chunk
+        T xv[VN];
+#pragma unroll
+        for (int e = 0; e < VN; ++e) xv[e] = (e < lim) ? xs[c + e] : T(0);
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          T v[VN];
+          Chunk<TS>::cvt(raw[u], v);
+          if (lim < VN) {
+#pragma unroll
+            for (int e = 0; e < VN; ++e) v[e] = (e < lim) ? v[e] : T(0);
+          }
+#pragma unroll
+          for (int e = 0; e < VN; ++e) acc[u] = fma(v[e], xv[e], acc[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      for (int o = cpr >> 1; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+      const int r = rb + (u * nw + warp) * rpi + sub;
+      if (cl == 0 && r < nr) y[r] = (base ? base[r] : T(0)) + alpha * acc[u];
+    }
+  }
+}
+
+// y[m] = sum_{n < nn} M[n * ld + m] z[n] for m < nm (M column-major: the
+// columns are contiguous).  Warps take columns n, lanes take 16-byte chunks
+// of m; the per-warp partial vectors (part: nwarps * nm entries of shared
+// memory) are added at the end.  Ends with the result in y and a barrier.
+template <typename TS, typename T>
+__device__ __forceinline__ void cta_gemv_cols(const TS* __restrict__ M, int64_t ld, int nm, int nn,
+                                              const T* __restrict__ z, T* part, T* y) {
+  constexpr int VN = Chunk<TS>::VN;
+  constexpr int NU = 8;  // columns in flight per lane
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const bool vec = ((reinterpret_cast<uintptr_t>(M) & 15) == 0) && ((ld * (int64_t)sizeof(TS)) % 16 == 0);
+  for (int m0 = lane * VN; m0 < nm; m0 += 32 * VN) {
+    T acc[VN];
+#pragma unroll
+    for (int e = 0; e < VN; ++e) acc[e] = T(0);
+    if (vec && m0 + VN <= nm) {
+      int n = warp;
+      for (; n + (NU - 1) * nw < nn; n += NU * nw) {
+        uint4 raw[NU];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) raw[u] = __ldg(reinterpret_cast<const uint4*>(M + (int64_t)(n + u * nw) * ld + m0));
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          T v[VN];
+          Chunk<TS>::cvt(raw[u], v);
+          const T zn = z[n + u * nw];
+#pragma unroll
+          for (int e = 0; e < VN; ++e) acc[e] = fma(v[e], zn, acc[e]);
+        }
+      }
+      for (; n < nn; n += nw) {
+        T v[VN];
+        Chunk<TS>::cvt(__ldg(reinterpret_cast<const uint4*>(M + (int64_t)n * ld + m0)), v);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) acc[e] = fma(v[e], z[n], acc[e]);
+      }
+    } else {
+      for (int n = warp; n < nn; n += nw) {
+#pragma unroll
+        for (int e = 0; e < VN; ++e)
+          if (m0 + e < nm) acc[e] = fma(Cvt<T, TS>::go(M[(int64_t)n * ld + m0 + e]), z[n], acc[e]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < VN; ++e)
+      if (m0 + e < nm) part[warp * nm + m0 + e] = acc[e];
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < nm; m += blockDim.x) {
+    T s = T(0);
+    for (int w = 0; w < nw; ++w) s += part[w * nm + m];
+    y[m] = s;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- fwd1 ---
+// c_i = U_i^T b_i;  u_i = Ainv_i c_i^R   (one CTA per box)
 template <typename T>
-__global__ void __launch_bounds__(256, 2) fwd1_kernel(int D, int R, const T* __restrict__ U, const T* __restrict__ Ainv,
+__global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, const T* __restrict__ U, const T* __restrict__ Ainv,
                                                    const T* __restrict__ vin, T* __restrict__ c, T* __restrict__ u) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sv = reinterpret_cast<T*>(sm_raw);  // D
   T* sc = sv + D;                        // D
   const int i = blockIdx.x, tid = threadIdx.x;
-  for (int e = tid; e < D; e += blockDim.x) sv[e] = vin[(int64_t)i * D + e];
-  __syncthreads();
-  T acc[kRPW];
   // c[n] = sum_k U(k, n) v[k]; U column-major: column n is contiguous
-  for (int r0 = 0; r0 < D; r0 += kChunk) {
-    zero(acc);
-    rows_acc<T, kRPW>(r0, U + (int64_t)i * D * D, D, D, D, sv, acc);
-    rows_finish<T, kRPW>(r0, D, acc, T(1), nullptr, sc);
-  }
+  cta_gemv<T, T, Unr<T>::v>(U + (int64_t)i * D * D, D, D, D, sv, T(1), nullptr, sc, [&] {
+    for (int e = tid; e < D; e += blockDim.x) sv[e] = vin[(int64_t)i * D + e];
+    __syncthreads();
+  });
   __syncthreads();
-  for (int r0 = 0; r0 < R; r0 += kChunk) {
-    zero(acc);
-    rows_acc<T, kRPW>(r0, Ainv + (int64_t)i * R * R, R, R, R, sc, acc);
-    rows_finish<T, kRPW>(r0, R, acc, T(1), nullptr, u + (int64_t)i * R);
-  }
+  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, sc, T(1), nullptr, u + (int64_t)i * R);
   for (int e = tid; e < D; e += blockDim.x) c[(int64_t)i * D + e] = sc[e];
 }
 
+// The pair kernel runs one CTA per near pair p = (i, j) of a level (or of a
+// sub-list of them) and writes one block-vector product into part[p]:
+//   PH_RR: Ahat_ij^RR x_j (x_j = xv[j R ..], R entries)        fwd2 / bwd2
+//   PH_SR: Ahat_ij^SR x_j (x_j = xv[j R ..], R entries)        fwd3
+//   PH_RS: Ahat_ij^RS x_j^S (x_j^S: box j's slot of the parent
+//          vector xv, K entries)                                bwd1
+// Ahat is stored as TS: T itself, or 16 bits holding s * Ahat (the per-box
+// kernels apply 1 / s to the sums).  The block's loads are issued before the
+// pair's indices and x_j are read.
+enum { PH_RR = 0, PH_SR = 1, PH_RS = 2 };
+
+template <typename T, typename TS, int PH>
+__global__ void __launch_bounds__(256, sizeof(TS) == 2 ? 3 : 2) pair_kernel(int D, int R, int K, const int32_t* __restrict__ list,
+                                                   const int32_t* __restrict__ nj, const TS* __restrict__ Ahat,
+                                                   const T* __restrict__ xv, T* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sx = reinterpret_cast<T*>(sm_raw);  // nc
+  const int64_t p = list ? list[blockIdx.x] : blockIdx.x;
+  const int nr = (PH == PH_SR) ? K : R;
+  const int nc = (PH == PH_RS) ? K : R;
+  const TS* M = Ahat + p * D * D + (PH == PH_SR ? (int64_t)R * D : (PH == PH_RS ? R : 0));
+  cta_gemv<TS, T, Unr<TS>::v>(M, D, nr, nc, sx, T(1), nullptr, part + p * nr, [&] {
+    const int j = nj[p];
+    const T* x = (PH == PH_RS) ? xv + (int64_t)(j >> 1) * 2 * K + (j & 1) * K : xv + (int64_t)j * R;
+    for (int e = threadIdx.x; e < nc; e += blockDim.x) sx[e] = x[e];
+    __syncthreads();
+  });
+}
+
+// sum over the pairs q in [q0, q1) of box i that pass sel(j) of part[q][r]
+template <typename T, typename Sel>
+__device__ __forceinline__ T sum_pairs(const T* __restrict__ part, int nr, int64_t q0, int64_t q1,
+                                       const int32_t* __restrict__ nj, int r, Sel sel) {
+  T s = T(0);
+  for (int64_t q = q0; q < q1; ++q)
+    if (sel(nj[q])) s += part[q * nr + r];
+  return s;
+}
+
 // ---------------------------------------------------------------- fwd2 ---
-// v_i = Ainv_i (c_i^R - sum_{j<i near} Ahat_ij^RR u_j)
+// v_i = Ainv_i (c_i^R - sum_{j<i near} Ahat_ij^RR u_j)   (one CTA per box)
 template <typename T>
-__global__ void __launch_bounds__(256, 2) fwd2_kernel(int D, int R, const int64_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
+__global__ void __launch_bounds__(256) fwd2_kernel(int D, int R, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ nj, const float* __restrict__ iscale,
                                                    const T* __restrict__ Ainv, const T* __restrict__ c,
-                                                   const T* __restrict__ u, T* __restrict__ v) {
+                                                   const T* __restrict__ part, T* __restrict__ v) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sb = reinterpret_cast<T*>(sm_raw);  // R
-  T* sx = sb + R;                        // nn * R
-  const int i = blockIdx.x, tid = threadIdx.x;
-  const int64_t p0 = ptr[i];
-  int nlow = 0;
-  while (p0 + nlow < ptr[i + 1] && nj[p0 + nlow] < i) ++nlow;  // sorted neighbours: the j < i ones lead
-  for (int e = tid; e < nlow * R; e += blockDim.x) sx[e] = u[(int64_t)nj[p0 + e / R] * R + e % R];
-  __syncthreads();
-  T acc[kRPW];
-  for (int r0 = 0; r0 < R; r0 += kChunk) {
-    zero(acc);
-    for (int q = 0; q < nlow; ++q) rows_acc<T, kRPW>(r0, Ahat + (p0 + q) * D * D, D, R, R, sx + q * R, acc);
-    rows_finish<T, kRPW>(r0, R, acc, T(-1), c + (int64_t)i * D, sb);
-  }
-  __syncthreads();
-  for (int r0 = 0; r0 < R; r0 += kChunk) {
-    zero(acc);
-    rows_acc<T, kRPW>(r0, Ainv + (int64_t)i * R * R, R, R, R, sb, acc);
-    rows_finish<T, kRPW>(r0, R, acc, T(1), nullptr, v + (int64_t)i * R);
-  }
+  const int i = blockIdx.x;
+  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, sb, T(1), nullptr, v + (int64_t)i * R, [&] {
+    const T isc = iscale ? T(iscale[0]) : T(1);
+    const int64_t q0 = ptr[i], q1 = ptr[i + 1];
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      sb[r] = c[(int64_t)i * D + r] - isc * sum_pairs(part, R, q0, q1, nj, r, [i](int j) { return j < i; });
+    __syncthreads();
+  });
 }
 
 // ---------------------------------------------------------------- fwd3 ---
-// s_i = c_i^S - sum_{j near} Ahat_ij^SR v_j  -> parent input slot
+// s_i = c_i^S - sum_{j near} Ahat_ij^SR v_j  -> parent input slot   (one CTA per box)
 template <typename T>
-__global__ void __launch_bounds__(256, 2) fwd3_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
-                                                   const T* __restrict__ c, const T* __restrict__ v,
-                                                   T* __restrict__ pvin) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sx = reinterpret_cast<T*>(sm_raw);  // nn * R
-  const int i = blockIdx.x, tid = threadIdx.x;
-  const int64_t p0 = ptr[i];
-  const int nn = (int)(ptr[i + 1] - p0);
-  for (int e = tid; e < nn * R; e += blockDim.x) sx[e] = v[(int64_t)nj[p0 + e / R] * R + e % R];
-  __syncthreads();
-  T acc[kRPW];
-  const int Dp = 2 * K;
-  for (int r0 = 0; r0 < K; r0 += kChunk) {
-    zero(acc);
-    for (int q = 0; q < nn; ++q)
-      rows_acc<T, kRPW>(r0, Ahat + (p0 + q) * D * D + (int64_t)R * D, D, K, R, sx + q * R, acc);
-    rows_finish<T, kRPW>(r0, K, acc, T(-1), c + (int64_t)i * D + R, pvin + (int64_t)(i >> 1) * Dp + (i & 1) * K);
+__global__ void __launch_bounds__(128) fwd3_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+                                                   const float* __restrict__ iscale, const T* __restrict__ c,
+                                                   const T* __restrict__ part, T* __restrict__ pvin) {
+  const int i = blockIdx.x;
+  const T isc = iscale ? T(iscale[0]) : T(1);
+  const int64_t q0 = ptr[i], q1 = ptr[i + 1];
+  T* out = pvin + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
+  for (int r = threadIdx.x; r < K; r += blockDim.x) {
+    T s = T(0);
+    for (int64_t q = q0; q < q1; ++q) s += part[q * K + r];
+    out[r] = c[(int64_t)i * D + R + r] - isc * s;
   }
 }
 
 // ---------------------------------------------------------------- bwd1 ---
-// om_i = v_i - Ainv_i sum_{j near} Ahat_ij^RS x_j^S
+// om_i = v_i - Ainv_i sum_{j near} Ahat_ij^RS x_j^S   (one CTA per box)
 template <typename T>
-__global__ void __launch_bounds__(256, 2) bwd1_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
-                                                   const T* __restrict__ Ainv, const T* __restrict__ v,
-                                                   const T* __restrict__ px, T* __restrict__ om) {
+__global__ void __launch_bounds__(256) bwd1_kernel(int R, const int64_t* __restrict__ ptr,
+                                                   const float* __restrict__ iscale, const T* __restrict__ Ainv,
+                                                   const T* __restrict__ v, const T* __restrict__ part,
+                                                   T* __restrict__ om) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* st = reinterpret_cast<T*>(sm_raw);  // R
-  T* sx = st + R;                        // nn * K
-  const int i = blockIdx.x, tid = threadIdx.x, Dp = 2 * K;
-  const int64_t p0 = ptr[i];
-  const int nn = (int)(ptr[i + 1] - p0);
-  for (int e = tid; e < nn * K; e += blockDim.x) {
-    const int j = nj[p0 + e / K];
-    sx[e] = px[(int64_t)(j >> 1) * Dp + (j & 1) * K + e % K];
-  }
-  __syncthreads();
-  T acc[kRPW];
-  for (int r0 = 0; r0 < R; r0 += kChunk) {
-    zero(acc);
-    for (int q = 0; q < nn; ++q) rows_acc<T, kRPW>(r0, Ahat + (p0 + q) * D * D + R, D, R, K, sx + q * K, acc);
-    rows_finish<T, kRPW>(r0, R, acc, T(1), nullptr, st);
-  }
-  __syncthreads();
-  for (int r0 = 0; r0 < R; r0 += kChunk) {
-    zero(acc);
-    rows_acc<T, kRPW>(r0, Ainv + (int64_t)i * R * R, R, R, R, st, acc);
-    rows_finish<T, kRPW>(r0, R, acc, T(-1), v + (int64_t)i * R, om + (int64_t)i * R);
-  }
+  const int i = blockIdx.x;
+  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, st, T(-1), v + (int64_t)i * R, om + (int64_t)i * R,
+                            [&] {
+                              const T isc = iscale ? T(iscale[0]) : T(1);
+                              const int64_t q0 = ptr[i], q1 = ptr[i + 1];
+                              for (int r = threadIdx.x; r < R; r += blockDim.x) {
+                                T s = T(0);
+                                for (int64_t q = q0; q < q1; ++q) s += part[q * R + r];
+                                st[r] = isc * s;
+                              }
+                              __syncthreads();
+                            });
 }
 
 // ---------------------------------------------------------------- bwd2 ---
 // x_i^R = om_i - Ainv_i sum_{j>i near} Ahat_ij^RR om_j;  x_i = U_i [x_i^R; x_i^S]
+// (one CTA per box)
 template <typename T>
-__global__ void __launch_bounds__(256, 2) bwd2_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ nj, const T* __restrict__ Ahat,
+__global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ nj, const float* __restrict__ iscale,
                                                    const T* __restrict__ Ainv, const T* __restrict__ U,
                                                    const T* __restrict__ om, const T* __restrict__ px,
-                                                   T* __restrict__ xs) {
+                                                   const T* __restrict__ part, T* __restrict__ xs) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sq = reinterpret_cast<T*>(sm_raw);  // R
   T* sz = sq + R;                        // D
-  T* sx = sz + D;                        // nn * R
-  const int i = blockIdx.x, tid = threadIdx.x, Dp = 2 * K;
-  const int64_t p0 = ptr[i], p1 = ptr[i + 1];
-  int first = 0;
-  while (p0 + first < p1 && nj[p0 + first] <= i) ++first;  // neighbours j > i trail
-  const int nhi = (int)(p1 - p0) - first;
-  for (int e = tid; e < nhi * R; e += blockDim.x) sx[e] = om[(int64_t)nj[p0 + first + e / R] * R + e % R];
-  for (int e = tid; e < K; e += blockDim.x) sz[R + e] = px[(int64_t)(i >> 1) * Dp + (i & 1) * K + e];
+  T* sp = sz + D;                        // 8 * D
+  const int i = blockIdx.x;
+  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, sq, T(-1), om + (int64_t)i * R, sz, [&] {
+    const T isc = iscale ? T(iscale[0]) : T(1);
+    const int64_t q0 = ptr[i], q1 = ptr[i + 1];
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      sq[r] = isc * sum_pairs(part, R, q0, q1, nj, r, [i](int j) { return j > i; });
+    const T* xi = px + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
+    for (int e = threadIdx.x; e < K; e += blockDim.x) sz[R + e] = xi[e];
+    __syncthreads();
+  });
   __syncthreads();
-  T acc[kRPW];
-  for (int r0 = 0; r0 < R; r0 += kChunk) {
-    zero(acc);
-    for (int q = 0; q < nhi; ++q)
-      rows_acc<T, kRPW>(r0, Ahat + (p0 + first + q) * D * D, D, R, R, sx + q * R, acc);
-    rows_finish<T, kRPW>(r0, R, acc, T(1), nullptr, sq);
-  }
-  __syncthreads();
-  for (int r0 = 0; r0 < R; r0 += kChunk) {
-    zero(acc);
-    rows_acc<T, kRPW>(r0, Ainv + (int64_t)i * R * R, R, R, R, sq, acc);
-    rows_finish<T, kRPW>(r0, R, acc, T(-1), om + (int64_t)i * R, sz);
-  }
-  __syncthreads();
-  // x = U z, U column-major: x[m] = sum_n U[n*D + m] z[n] (coalesced over m)
-  const T* Ub = U + (int64_t)i * D * D;
-  for (int m = tid; m < D; m += blockDim.x) {
-    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int n = 0;
-    for (; n + 3 < D; n += 4) {
-      s0 = fma(Ub[(int64_t)n * D + m], sz[n], s0);
-      s1 = fma(Ub[(int64_t)(n + 1) * D + m], sz[n + 1], s1);
-      s2 = fma(Ub[(int64_t)(n + 2) * D + m], sz[n + 2], s2);
-      s3 = fma(Ub[(int64_t)(n + 3) * D + m], sz[n + 3], s3);
-    }
-    for (; n < D; ++n) s0 = fma(Ub[(int64_t)n * D + m], sz[n], s0);
-    xs[(int64_t)i * D + m] = (s0 + s1) + (s2 + s3);
-  }
+  cta_gemv_cols<T, T>(U + (int64_t)i * D * D, D, D, D, sz, sp, xs + (int64_t)i * D);
 }
 
 static void set_smem(const void* f, size_t sm) {
   if (sm > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+template <typename T, typename TS, int PH>
+static void launch_pairs(const DevLevel& L, const int32_t* list, int64_t n, const TS* Ahat, const T* xv, T* part,
+                         cudaStream_t st) {
+  if (n <= 0) return;
+  const int nc = (PH == PH_RS) ? L.K : L.R;
+  const size_t sm = sizeof(T) * (size_t)std::max(nc, 1);
+  set_smem((const void*)pair_kernel<T, TS, PH>, sm);
+  ++g_launches;
+  pair_kernel<T, TS, PH><<<(unsigned)n, 256, sm, st>>>(L.D, L.R, L.K, list, L.near_j, Ahat, xv, part);
 }
 
 template <typename T>
@@ -330,34 +594,39 @@ void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStr
   ++g_launches;
   fwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, F.U, Ainv, F.vin, F.c, F.u);
 }
-template <typename T>
-void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st) {
-  size_t sm = sizeof(T) * (size_t)L.R * (1 + L.max_near);
-  set_smem((const void*)fwd2_kernel<T>, sm);
+template <typename T, typename TS>
+void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, cudaStream_t st) {
+  // pairs j < i only (the lo list also holds the diagonal pairs, which the
+  // per-box kernel skips)
+  launch_pairs<T, TS, PH_RR>(L, L.lo_pairs, L.n_lo, Ahat, F.u, F.part, st);
+  size_t sm = sizeof(T) * (size_t)std::max(L.R, 1);
   ++g_launches;
-  fwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.near_ptr, L.near_j, F.Ahat, Ainv, F.c, F.u, F.v);
+  fwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.near_ptr, L.near_j, iscale, F.Ainv, F.c, F.part, F.v);
 }
-template <typename T>
-void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, T* parent_vin, cudaStream_t st) {
-  size_t sm = sizeof(T) * (size_t)L.R * L.max_near;
-  set_smem((const void*)fwd3_kernel<T>, sm);
+template <typename T, typename TS>
+void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, T* parent_vin,
+                 cudaStream_t st) {
+  launch_pairs<T, TS, PH_SR>(L, nullptr, L.NP, Ahat, F.v, F.part, st);
   ++g_launches;
-  fwd3_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, F.c, F.v, parent_vin);
+  fwd3_kernel<T><<<L.nb, 128, 0, st>>>(L.D, L.R, L.K, L.near_ptr, iscale, F.c, F.part, parent_vin);
 }
-template <typename T>
-void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st) {
-  size_t sm = sizeof(T) * ((size_t)L.R + (size_t)L.K * L.max_near);
-  set_smem((const void*)bwd1_kernel<T>, sm);
+template <typename T, typename TS>
+void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
+                 cudaStream_t st) {
+  launch_pairs<T, TS, PH_RS>(L, nullptr, L.NP, Ahat, parent_x, F.part, st);
+  size_t sm = sizeof(T) * (size_t)std::max(L.R, 1);
   ++g_launches;
-  bwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, Ainv, F.v, parent_x, F.om);
+  bwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.R, L.near_ptr, iscale, F.Ainv, F.v, F.part, F.om);
 }
-template <typename T>
-void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, const T* parent_x, cudaStream_t st) {
-  size_t sm = sizeof(T) * ((size_t)L.R + L.D + (size_t)L.R * L.max_near);
+template <typename T, typename TS>
+void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
+                 cudaStream_t st) {
+  launch_pairs<T, TS, PH_RR>(L, L.hi_pairs, L.n_hi, Ahat, F.om, F.part, st);
+  size_t sm = sizeof(T) * ((size_t)L.R + 9 * (size_t)L.D);
   set_smem((const void*)bwd2_kernel<T>, sm);
   ++g_launches;
-  bwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, F.Ahat, Ainv, F.U, F.om, parent_x,
-                                        F.xs);
+  bwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, iscale, F.Ainv, F.U, F.om, parent_x,
+                                        F.part, F.xs);
 }
 
 // y = M x for one n x n row-major matrix (root solve with the explicit inverse)
@@ -381,15 +650,23 @@ void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st) {
   gemv_rows_kernel<T><<<1, 256, sm, st>>>(n, M, x, y);
 }
 
-#define H2_INST_SOLVE(T)                                                                              \
-  template void launch_fwd1<T>(const DevLevel&, const FacLevel<T>&, const T*, cudaStream_t);          \
-  template void launch_fwd2<T>(const DevLevel&, const FacLevel<T>&, const T*, cudaStream_t);          \
-  template void launch_fwd3<T>(const DevLevel&, const FacLevel<T>&, T*, cudaStream_t);                \
-  template void launch_bwd1<T>(const DevLevel&, const FacLevel<T>&, const T*, const T*, cudaStream_t); \
-  template void launch_bwd2<T>(const DevLevel&, const FacLevel<T>&, const T*, const T*, cudaStream_t); \
+#define H2_INST_SOLVE(T)                                                                     \
+  template void launch_fwd1<T>(const DevLevel&, const FacLevel<T>&, const T*, cudaStream_t); \
   template void launch_gemv_rows<T>(int, const T*, const T*, T*, cudaStream_t);
 H2_INST_SOLVE(double)
 H2_INST_SOLVE(float)
+#define H2_INST_SUBST(T, TS)                                                                                   \
+  template void launch_fwd2<T, TS>(const DevLevel&, const FacLevel<T>&, const TS*, const float*, cudaStream_t); \
+  template void launch_fwd3<T, TS>(const DevLevel&, const FacLevel<T>&, const TS*, const float*, T*,            \
+                                   cudaStream_t);                                                              \
+  template void launch_bwd1<T, TS>(const DevLevel&, const FacLevel<T>&, const TS*, const float*, const T*,      \
+                                   cudaStream_t);                                                              \
+  template void launch_bwd2<T, TS>(const DevLevel&, const FacLevel<T>&, const TS*, const float*, const T*,      \
+                                   cudaStream_t);
+H2_INST_SUBST(double, double)
+H2_INST_SUBST(float, float)
+H2_INST_SUBST(float, __half)
+H2_INST_SUBST(float, __nv_bfloat16)
 
 // ------------------------------------------------------------- matvec ---
 // Element type T: double for the refinement residual, float for the inner

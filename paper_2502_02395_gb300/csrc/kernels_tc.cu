@@ -111,6 +111,8 @@ struct TcArgs {
   int32_t* err;
   int ab_bf16;
   uint32_t tmem_cols;
+  void* C2;  // optional second output for out_mode 0: 16-bit copy of the raw accumulator (row-major, ldc)
+  int c2_bf16;
 };
 
 __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -229,6 +231,23 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
                                  __uint_as_float(r[j + 2]) * alpha, __uint_as_float(r[j + 3]) * alpha);
           *reinterpret_cast<float4*>(out + j) = v;
         }
+        if (p.C2) {
+          uint32_t h[8];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const float a0 = __uint_as_float(r[j]), a1 = __uint_as_float(r[j + 1]);
+            if (p.c2_bf16) {
+              __nv_bfloat162 t = __floats2bfloat162_rn(a0, a1);
+              h[j / 2] = *reinterpret_cast<uint32_t*>(&t);
+            } else {
+              __half2 t = __floats2half2_rn(a0, a1);
+              h[j / 2] = *reinterpret_cast<uint32_t*>(&t);
+            }
+          }
+          uint4* o2 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(p.C2) + cbase + (int64_t)m * p.ldc + n0);
+          o2[0] = make_uint4(h[0], h[1], h[2], h[3]);
+          o2[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        }
       } else if (p.out_bf16) {
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Cb) + cbase;
 #pragma unroll
@@ -301,7 +320,7 @@ bool gemm_tc_supported(int M, int N, int K, int lda, int ldb, int ldc) {
 bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int rowsA, int lda, const int32_t* ia,
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
-             int64_t batch, int32_t* err, cudaStream_t st) {
+             int64_t batch, int32_t* err, cudaStream_t st, void* C2) {
   if (batch == 0) return true;
   if (!gemm_tc_supported(M, N, K, lda, ldb, ldc)) return false;
   if ((uint64_t)nA * rowsA >= (1ull << 31) || (uint64_t)nB * rowsB >= (1ull << 31)) return false;
@@ -326,6 +345,8 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
   p.alpha_dev = alpha_dev;
   p.err = err;
   p.ab_bf16 = ab_bf16;
+  p.C2 = (out_mode == 0) ? C2 : nullptr;
+  p.c2_bf16 = ab_bf16;
   uint32_t cols = 32;
   while (cols < (uint32_t)N) cols <<= 1;
   p.tmem_cols = cols;
