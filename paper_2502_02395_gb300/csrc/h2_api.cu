@@ -151,8 +151,8 @@ h2_status setup_device(h2_ctx* c) {
       std::vector<int32_t> lo, hi, loc(d.nb, 0), hic(d.nb, 0);
       for (int64_t q = 0; q < d.NP; ++q) {
         const int i = d.h_near_i[q], j = d.h_near_j[q];
-        if (j <= i) lo.push_back((int32_t)q), ++loc[i];
-        if (j >= i) hi.push_back((int32_t)q), ++hic[i];
+        if (j < i) lo.push_back((int32_t)q), ++loc[i];
+        if (j > i) hi.push_back((int32_t)q), ++hic[i];
       }
       d.n_lo = (int64_t)lo.size();
       d.n_hi = (int64_t)hi.size();
@@ -293,6 +293,7 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
       wk16 = std::max(wk16, (size_t)d.FP * K * K);
     }
     CKC(dalloc(c, &f.U, nb * D * D));
+    CKC(dalloc(c, &f.Ur, nb * D * D));
     CKC(dalloc(c, &f.Tm, nb * K * K));
     CKC(dalloc(c, &f.Xo, nb * D * K));
     CKC(dalloc(c, &f.Vq, nb * D * K));
@@ -304,12 +305,16 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     if (f.tc) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&f.Ahat16), (size_t)d.NP * D * D));
     CKC(dalloc(c, &f.Shat, (size_t)std::max<int64_t>(d.FP, 1) * K * K));
     CKC(dalloc(c, &f.Z, nb * R * K));
-    CKC(dalloc(c, &f.lu, nb * R * R));
-    if (std::is_same<T, double>::value) f.luT = reinterpret_cast<T*>(f.lu);
-    else CKC(dalloc(c, &f.luT, nb * R * R));
+    // LU factors in the factorization's precision (FP64: the lu array)
+    if (std::is_same<T, double>::value) {
+      CKC(dalloc(c, &f.lu, nb * R * R));
+      f.luT = reinterpret_cast<T*>(f.lu);
+    } else {
+      CKC(dalloc(c, &f.luT, nb * R * R));
+    }
     CKC(dalloc(c, &f.Ainv, nb * R * R));
     CKC(dalloc(c, &f.piv, nb * R));
-    for (T** p : {&f.vin, &f.c, &f.xs}) CKC(dalloc(c, p, nb * D));
+    for (T** p : {&f.vin, &f.c, &f.xs, &f.z}) CKC(dalloc(c, p, nb * D));
     for (T** p : {&f.u, &f.v, &f.om}) CKC(dalloc(c, p, nb * std::max<size_t>(R, 1)));
   }
   const int D0 = c->lv[0].D;
@@ -326,9 +331,12 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   CKC(dalloc(c, &F.tscale, 2 * (size_t)(L + 1)));
   CKC(dalloc(c, &F.cscale, (size_t)(L + 1)));
   CKC(dalloc(c, &F.amax, (size_t)(L + 1)));
-  CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
-  if (std::is_same<T, double>::value) F.root_luT = reinterpret_cast<T*>(F.root_lu);
-  else CKC(dalloc(c, &F.root_luT, (size_t)D0 * D0));
+  if (std::is_same<T, double>::value) {
+    CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
+    F.root_luT = reinterpret_cast<T*>(F.root_lu);
+  } else {
+    CKC(dalloc(c, &F.root_luT, (size_t)D0 * D0));
+  }
   CKC(dalloc(c, &F.root_inv, (size_t)D0 * D0));
   CKC(dalloc(c, &F.root_piv, D0));
   CKC(dalloc(c, &F.root_vec, D0));
@@ -415,6 +423,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
         gemm<T>(prec, K, D, K, f.Vq, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U + (int64_t)R * D, DD, nullptr,
                 D, T(-1), T(1), nb, st);
       }
+      launch_transpose_blocks<T>(nb, D, f.U, f.Ur, st);
     }
     mark();
     // a2: Ahat_ij = U_i^T A_ij U_j
@@ -1256,14 +1265,18 @@ h2_status h2_export(const h2_ctx* c, const char* name, int32_t level, void* dst,
   } else if (level >= 1 && (n == "lu" || n == "piv")) {
     if (!ready) return H2_ERR_STATE;
     const bool p64 = f64;
-    src = (n == "lu") ? (const void*)(p64 ? c->f64.lv[level].lu : c->f32.lv[level].lu)
+    src = (n == "lu") ? (const void*)(p64 ? c->f64.lv[level].lu : (const double*)(const void*)c->f32.lv[level].luT)
                       : (const void*)(p64 ? c->f64.lv[level].piv : c->f32.lv[level].piv);
-    es = (n == "lu") ? 8 : 4;
+    es = (n == "lu") ? (p64 ? 8 : 4) : 4;
     cnt = (n == "lu") ? nb * R * R : nb * R;
   } else if (n == "root" || n == "root_piv" || n == "root_inv") {
     if (!ready) return H2_ERR_STATE;
     const size_t D0 = c->lv[0].D;
-    if (n == "root") { src = f64 ? (const void*)c->f64.root_lu : (const void*)c->f32.root_lu; es = 8; cnt = D0 * D0; }
+    if (n == "root") {
+      src = f64 ? (const void*)c->f64.root_lu : (const void*)c->f32.root_luT;
+      es = f64 ? 8 : 4;
+      cnt = D0 * D0;
+    }
     if (n == "root_piv") { src = f64 ? (const void*)c->f64.root_piv : (const void*)c->f32.root_piv; es = 4; cnt = D0; }
     if (n == "root_inv") s = pick(c->f64.root_inv, c->f32.root_inv, D0 * D0, true);
   } else {

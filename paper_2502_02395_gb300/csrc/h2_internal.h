@@ -105,7 +105,7 @@ struct DevLevel {
   int32_t *far_i = nullptr, *far_j = nullptr;    // FP
   int64_t* far_ptr = nullptr;                    // nb + 1
   int32_t *near_dst = nullptr, *far_dst = nullptr;  // parent near-pair index of each pair
-  // sub-lists of the near pairs for the substitution: j <= i (lo) and j >= i
+  // sub-lists of the near pairs for the substitution: j < i (lo) and j > i
   // (hi), in pair order, with their count per box
   int32_t *lo_pairs = nullptr, *hi_pairs = nullptr;
   int32_t *lo_cnt = nullptr, *hi_cnt = nullptr;
@@ -127,6 +127,7 @@ struct DevLevel {
 template <typename T>
 struct FacLevel {
   T* U = nullptr;      // nb * D * D   [U^R U^S], column-major
+  T* Ur = nullptr;     // nb * D * D   the same, row-major (for x = U z in the substitution)
   T* Tm = nullptr;     // nb * K * K   row-major, upper triangular
   T* Xo = nullptr;     // nb * D * K   X^orth (row-major)
   T* Vq = nullptr;     // nb * D * K   Householder reflectors (column-major, unit diagonal)
@@ -137,12 +138,13 @@ struct FacLevel {
   T* Ahat = nullptr;   // NP * D * D   projected blocks (row-major)
   T* Shat = nullptr;   // FP * K * K   couplings in orthogonal coordinates
   T* Z = nullptr;      // nb * R * K   (Ahat_ii^RR)^-1 Ahat_ii^RS
-  double* lu = nullptr;    // nb * R * R  LU of Ahat_ii^RR, column-major, FP64
+  double* lu = nullptr;    // nb * R * R  LU of Ahat_ii^RR, column-major (FP64 factorization only)
   T* luT = nullptr;        // nb * R * R  the same factors in T (aliases lu when T is double)
   T* Ainv = nullptr;       // nb * R * R  (Ahat_ii^RR)^-1, row-major
   int32_t* piv = nullptr;  // nb * R (LAPACK-style row interchanges)
   // substitution vectors
   T *vin = nullptr, *c = nullptr, *u = nullptr, *v = nullptr, *om = nullptr, *xs = nullptr;
+  T* z = nullptr;  // nb * D: [x^R; x^S] of each box before x = U z
   // per-pair partial products of the substitution (Factor::part, shared by
   // all levels)
   T* part = nullptr;
@@ -163,7 +165,7 @@ template <typename T>
 struct Factor {
   bool ready = false;
   std::vector<FacLevel<T>> lv;
-  double* root_lu = nullptr;  // D0 * D0 column-major
+  double* root_lu = nullptr;  // D0 * D0 column-major (FP64 factorization only)
   T* root_luT = nullptr;      // the same in T
   T* root_inv = nullptr;      // D0 * D0 row-major
   int32_t* root_piv = nullptr;

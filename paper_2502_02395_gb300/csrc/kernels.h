@@ -73,7 +73,9 @@ template <typename T, typename TS>
 void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
                  cudaStream_t st);
 template <typename T>
-void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st);  // y = M x, M n x n row-major
+void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st);
+template <typename T>
+void launch_transpose_blocks(int64_t nb, int D, const T* in, T* out, cudaStream_t st);  // out_b = in_b^T (D x D)  // y = M x, M n x n row-major
 
 template <typename T>
 void launch_matvec_up(const DevLevel& L, const T* X, const T* x, T* xh, cudaStream_t st);

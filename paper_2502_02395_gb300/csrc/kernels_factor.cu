@@ -350,63 +350,64 @@ H2_INST_QR(double)
 H2_INST_QR(float)
 
 // ------------------------------------------------------------------------
-// a3: FP64 partial-pivot LU of Ahat_ii^RR (rows/cols 0..R of a D x D
-// row-major block), LAPACK getf2 conventions (the first largest |pivot|;
-// whole-row interchanges).
-//   lu   column-major R x R FP64 (L unit lower, U upper), piv LAPACK-style
-//   luT  the same factors in T (skipped when T is double)
-//   M    working copy: shared memory (ld = R + 1) when it fits, else lu
+// a3: partial-pivot LU of Ahat_ii^RR (rows/cols 0..R of a D x D row-major
+// block), LAPACK getf2 conventions (the first largest |pivot|; whole-row
+// interchanges), in the factorization's precision T (FP64 for the FP64
+// factorization, FP32 for the mixed-precision one).
+//   luT  column-major R x R in T (L unit lower, U upper), piv LAPACK-style
+//        (for T = double this is the lu array itself)
+//   M    working copy: shared memory (ld = R + 1) when it fits, else luT
 // A zero pivot records (level, box) in status[0..1]; the rest of that box's
 // factorization is then undefined.
 // ------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256)
 lu_factor_kernel(int D, int R, const T* __restrict__ Ablk, const int32_t* __restrict__ diag_idx,
-                 double* __restrict__ lu, T* __restrict__ luT, int32_t* __restrict__ piv,
-                 int32_t* __restrict__ status, int level, int use_smem) {
-  extern __shared__ double smd[];
+                 T* __restrict__ luT, int32_t* __restrict__ piv, int32_t* __restrict__ status, int level,
+                 int use_smem) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int s_p;
-  __shared__ double s_inv;
+  __shared__ T s_inv;
   const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
-  double* G = lu + (size_t)box * R * R;
-  double* M = use_smem ? smd : G;
+  T* G = luT + (size_t)box * R * R;
+  T* M = use_smem ? reinterpret_cast<T*>(sm_raw) : G;
   const int ld = use_smem ? R + 1 : R;
   int32_t* pv = piv + (size_t)box * R;
   for (int r = warp; r < R; r += 8)
-    for (int c = lane; c < R; c += 32) M[c * ld + r] = (double)A[(size_t)r * D + c];
+    for (int c = lane; c < R; c += 32) M[c * ld + r] = A[(size_t)r * D + c];
   __syncthreads();
   int bad = 0;
   for (int k = 0; k < R; ++k) {
     if (warp == 0) {
-      double best = -1.0;
+      T best = T(-1);
       int bi = k;
       for (int r = k + lane; r < R; r += 32) {
-        double a = fabs(M[k * ld + r]);
+        T a = fabs(M[k * ld + r]);
         if (a > best) { best = a; bi = r; }
       }
       for (int o = 16; o; o >>= 1) {
-        double ob = __shfl_down_sync(0xffffffffu, best, o);
+        T ob = __shfl_down_sync(0xffffffffu, best, o);
         int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
       if (lane == 0) {
         s_p = bi;
         pv[k] = bi;
-        double d = M[k * ld + bi];
-        s_inv = d != 0.0 ? 1.0 / d : 0.0;
+        T d = M[k * ld + bi];
+        s_inv = d != T(0) ? T(1) / d : T(0);
       }
     }
     __syncthreads();
     const int p = s_p;
-    const double inv = s_inv;
-    if (inv == 0.0) {
+    const T inv = s_inv;
+    if (inv == T(0)) {
       bad = 1;
       break;
     }
     if (p != k)
       for (int c = tid; c < R; c += 256) {
-        double t = M[c * ld + k];
+        T t = M[c * ld + k];
         M[c * ld + k] = M[c * ld + p];
         M[c * ld + p] = t;
       }
@@ -414,8 +415,8 @@ lu_factor_kernel(int D, int R, const T* __restrict__ Ablk, const int32_t* __rest
     for (int r = k + 1 + tid; r < R; r += 256) M[k * ld + r] *= inv;
     __syncthreads();
     for (int c = k + 1 + warp; c < R; c += 8) {
-      const double f = M[c * ld + k];
-      if (f != 0.0)
+      const T f = M[c * ld + k];
+      if (f != T(0))
         for (int r = k + 1 + lane; r < R; r += 32) M[c * ld + r] = fma(-M[k * ld + r], f, M[c * ld + r]);
     }
     __syncthreads();
@@ -424,13 +425,9 @@ lu_factor_kernel(int D, int R, const T* __restrict__ Ablk, const int32_t* __rest
     if (tid == 0 && atomicCAS(status, 0, level + 1) == 0) status[1] = box;
     return;
   }
-  T* Gt = luT + (size_t)box * R * R;
-  for (int c = warp; c < R; c += 8)
-    for (int r = lane; r < R; r += 32) {
-      double v = M[c * ld + r];
-      if (use_smem) G[c * R + r] = v;
-      if ((void*)Gt != (void*)G) Gt[c * R + r] = (T)v;
-    }
+  if (use_smem)
+    for (int c = warp; c < R; c += 8)
+      for (int r = lane; r < R; r += 32) G[c * R + r] = M[c * ld + r];
 }
 
 // ------------------------------------------------------------------------
@@ -575,12 +572,13 @@ template <typename T>
 void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
                        int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st) {
   if (nb == 0 || R == 0) return;
+  (void)lu;  // for T = double, luT is the lu array
   const size_t cap = 220 * 1024;
-  size_t sm1 = sizeof(double) * (size_t)R * (R + 1);
+  size_t sm1 = sizeof(T) * (size_t)R * (R + 1);
   int use = sm1 <= cap;
   if (use) cudaFuncSetAttribute(lu_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
   ++g_launches;
-  lu_factor_kernel<T><<<nb, 256, use ? sm1 : 0, st>>>(D, R, Ablk, diag_idx, lu, luT, piv, status, level, use);
+  lu_factor_kernel<T><<<nb, 256, use ? sm1 : 0, st>>>(D, R, Ablk, diag_idx, luT, piv, status, level, use);
   if (R > 1024) return;  // the permutation table holds 1024 rows; larger blocks are rejected by the caller
   if (std::is_same<T, float>::value) {
     const int Rp = (R + 31) / 32 * 32;

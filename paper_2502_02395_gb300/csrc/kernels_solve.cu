@@ -429,24 +429,33 @@ __device__ __forceinline__ void cta_gemv_cols(const TS* __restrict__ M, int64_t 
   __syncthreads();
 }
 
-// ---------------------------------------------------------------- fwd1 ---
-// c_i = U_i^T b_i;  u_i = Ainv_i c_i^R   (one CTA per box)
+// sum over the pairs q in [q0, q1) of part[q][r], in pair order; eight
+// independent loads are issued before they are added
 template <typename T>
-__global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, const T* __restrict__ U, const T* __restrict__ Ainv,
-                                                   const T* __restrict__ vin, T* __restrict__ c, T* __restrict__ u) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sv = reinterpret_cast<T*>(sm_raw);  // D
-  T* sc = sv + D;                        // D
-  const int i = blockIdx.x, tid = threadIdx.x;
-  // c[n] = sum_k U(k, n) v[k]; U column-major: column n is contiguous
-  cta_gemv<T, T, Unr<T>::v>(U + (int64_t)i * D * D, D, D, D, sv, T(1), nullptr, sc, [&] {
-    for (int e = tid; e < D; e += blockDim.x) sv[e] = vin[(int64_t)i * D + e];
-    __syncthreads();
-  });
-  __syncthreads();
-  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, sc, T(1), nullptr, u + (int64_t)i * R);
-  for (int e = tid; e < D; e += blockDim.x) c[(int64_t)i * D + e] = sc[e];
+__device__ __forceinline__ T sum_pairs(const T* __restrict__ part, int nr, int64_t q0, int64_t q1, int r) {
+  T s = T(0);
+  int64_t q = q0;
+  for (; q + 8 <= q1; q += 8) {
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = part[(q + k) * nr + r];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += v[k];
+  }
+  for (; q < q1; ++q) s += part[q * nr + r];
+  return s;
 }
+
+// Programmatic dependent launch: the substitution kernels are launched so
+// that they may start while their predecessor in the stream drains.  Each
+// issues its loads of factorization data (fixed during a solve) first, then
+// waits here until the predecessor has finished and its writes are visible,
+// and only then reads vectors or writes anything.  (Launched without the
+// attribute, the wait returns at once.)
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// lets the next kernel in the stream begin launching once every CTA of this
+// one has started
+__device__ __forceinline__ void griddep_launch_next() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // The pair kernel runs one CTA per near pair p = (i, j) of a level (or of a
 // sub-list of them) and writes one block-vector product into part[p]:
@@ -471,43 +480,89 @@ __global__ void __launch_bounds__(256, sizeof(TS) == 2 ? 3 : 2) pair_kernel(int 
   const TS* M = Ahat + p * D * D + (PH == PH_SR ? (int64_t)R * D : (PH == PH_RS ? R : 0));
   cta_gemv<TS, T, Unr<TS>::v>(M, D, nr, nc, sx, T(1), nullptr, part + p * nr, [&] {
     const int j = nj[p];
+    griddep_wait();
+    griddep_launch_next();
     const T* x = (PH == PH_RS) ? xv + (int64_t)(j >> 1) * 2 * K + (j & 1) * K : xv + (int64_t)j * R;
     for (int e = threadIdx.x; e < nc; e += blockDim.x) sx[e] = x[e];
     __syncthreads();
   });
 }
 
-// sum over the pairs q in [q0, q1) of box i that pass sel(j) of part[q][r]
-template <typename T, typename Sel>
-__device__ __forceinline__ T sum_pairs(const T* __restrict__ part, int nr, int64_t q0, int64_t q1,
-                                       const int32_t* __restrict__ nj, int r, Sel sel) {
-  T s = T(0);
-  for (int64_t q = q0; q < q1; ++q)
-    if (sel(nj[q])) s += part[q * nr + r];
-  return s;
+// The per-box kernels below split a box's output rows over ns CTAs
+// (grid = nb * ns; CTA b takes box b / ns and row slice b % ns), so that a
+// level with few boxes still spreads its rows over the GPU.
+struct Slice {
+  int i, r0, nr;
+};
+__device__ __forceinline__ Slice slice_of(int ns, int nrows) {
+  const int i = blockIdx.x / ns, s = blockIdx.x % ns;
+  const int per = ((nrows + ns - 1) / ns + 7) & ~7;
+  const int r0 = min(s * per, nrows);
+  return {i, r0, min(per, nrows - r0)};
 }
 
-// ---------------------------------------------------------------- fwd2 ---
-// v_i = Ainv_i (c_i^R - sum_{j<i near} Ahat_ij^RR u_j)   (one CTA per box)
+// ---------------------------------------------------------------- fwd1 ---
+// c_i = U_i^T b_i (U column-major: column n of U is row n of U^T)
 template <typename T>
-__global__ void __launch_bounds__(256) fwd2_kernel(int D, int R, const int64_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ nj, const float* __restrict__ iscale,
+__global__ void __launch_bounds__(256) fwd1_kernel(int D, int ns, const T* __restrict__ U, const T* __restrict__ vin,
+                                                   T* __restrict__ c) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sv = reinterpret_cast<T*>(sm_raw);  // D
+  const Slice sl = slice_of(ns, D);
+  const int i = sl.i;
+  cta_gemv<T, T, Unr<T>::v>(U + ((int64_t)i * D + sl.r0) * D, D, sl.nr, D, sv, T(1), nullptr,
+                            c + (int64_t)i * D + sl.r0, [&] {
+                              griddep_wait();
+                              griddep_launch_next();
+                              for (int e = threadIdx.x; e < D; e += blockDim.x) sv[e] = vin[(int64_t)i * D + e];
+                              __syncthreads();
+                            });
+}
+
+// u_i = Ainv_i c_i^R
+template <typename T>
+__global__ void __launch_bounds__(256) fwd1u_kernel(int D, int R, int ns, const T* __restrict__ Ainv,
+                                                    const T* __restrict__ c, T* __restrict__ u) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sc = reinterpret_cast<T*>(sm_raw);  // R
+  const Slice sl = slice_of(ns, R);
+  const int i = sl.i;
+  cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, sc, T(1), nullptr,
+                            u + (int64_t)i * R + sl.r0, [&] {
+                              griddep_wait();
+                              griddep_launch_next();
+                              for (int e = threadIdx.x; e < R; e += blockDim.x) sc[e] = c[(int64_t)i * D + e];
+                              __syncthreads();
+                            });
+}
+
+
+// ---------------------------------------------------------------- fwd2 ---
+// v_i = Ainv_i (c_i^R - sum_{j<i near} Ahat_ij^RR u_j)
+template <typename T>
+__global__ void __launch_bounds__(256) fwd2_kernel(int D, int R, int ns, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ lo_cnt, const float* __restrict__ iscale,
                                                    const T* __restrict__ Ainv, const T* __restrict__ c,
                                                    const T* __restrict__ part, T* __restrict__ v) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sb = reinterpret_cast<T*>(sm_raw);  // R
-  const int i = blockIdx.x;
-  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, sb, T(1), nullptr, v + (int64_t)i * R, [&] {
-    const T isc = iscale ? T(iscale[0]) : T(1);
-    const int64_t q0 = ptr[i], q1 = ptr[i + 1];
-    for (int r = threadIdx.x; r < R; r += blockDim.x)
-      sb[r] = c[(int64_t)i * D + r] - isc * sum_pairs(part, R, q0, q1, nj, r, [i](int j) { return j < i; });
-    __syncthreads();
-  });
+  const Slice sl = slice_of(ns, R);
+  const int i = sl.i;
+  cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, sb, T(1), nullptr,
+                            v + (int64_t)i * R + sl.r0, [&] {
+                              const T isc = iscale ? T(iscale[0]) : T(1);
+                              // the pairs j < i lead the box's sorted range
+                              const int64_t q0 = ptr[i], q1 = q0 + lo_cnt[i];
+                              griddep_wait();
+                              griddep_launch_next();
+                              for (int r = threadIdx.x; r < R; r += blockDim.x)
+                                sb[r] = c[(int64_t)i * D + r] - isc * sum_pairs(part, R, q0, q1, r);
+                              __syncthreads();
+                            });
 }
 
 // ---------------------------------------------------------------- fwd3 ---
-// s_i = c_i^S - sum_{j near} Ahat_ij^SR v_j  -> parent input slot   (one CTA per box)
+// s_i = c_i^S - sum_{j near} Ahat_ij^SR v_j  -> parent input slot
 template <typename T>
 __global__ void __launch_bounds__(128) fwd3_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
                                                    const float* __restrict__ iscale, const T* __restrict__ c,
@@ -516,65 +571,138 @@ __global__ void __launch_bounds__(128) fwd3_kernel(int D, int R, int K, const in
   const T isc = iscale ? T(iscale[0]) : T(1);
   const int64_t q0 = ptr[i], q1 = ptr[i + 1];
   T* out = pvin + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
-  for (int r = threadIdx.x; r < K; r += blockDim.x) {
-    T s = T(0);
-    for (int64_t q = q0; q < q1; ++q) s += part[q * K + r];
-    out[r] = c[(int64_t)i * D + R + r] - isc * s;
-  }
+  griddep_wait();
+  griddep_launch_next();
+  for (int r = threadIdx.x; r < K; r += blockDim.x) out[r] = c[(int64_t)i * D + R + r] - isc * sum_pairs(part, K, q0, q1, r);
 }
 
 // ---------------------------------------------------------------- bwd1 ---
-// om_i = v_i - Ainv_i sum_{j near} Ahat_ij^RS x_j^S   (one CTA per box)
+// om_i = v_i - Ainv_i sum_{j near} Ahat_ij^RS x_j^S
 template <typename T>
-__global__ void __launch_bounds__(256) bwd1_kernel(int R, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256) bwd1_kernel(int R, int ns, const int64_t* __restrict__ ptr,
                                                    const float* __restrict__ iscale, const T* __restrict__ Ainv,
                                                    const T* __restrict__ v, const T* __restrict__ part,
                                                    T* __restrict__ om) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* st = reinterpret_cast<T*>(sm_raw);  // R
-  const int i = blockIdx.x;
-  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, st, T(-1), v + (int64_t)i * R, om + (int64_t)i * R,
-                            [&] {
+  const Slice sl = slice_of(ns, R);
+  const int i = sl.i;
+  cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, st, T(-1), v + (int64_t)i * R + sl.r0,
+                            om + (int64_t)i * R + sl.r0, [&] {
                               const T isc = iscale ? T(iscale[0]) : T(1);
                               const int64_t q0 = ptr[i], q1 = ptr[i + 1];
-                              for (int r = threadIdx.x; r < R; r += blockDim.x) {
-                                T s = T(0);
-                                for (int64_t q = q0; q < q1; ++q) s += part[q * R + r];
-                                st[r] = isc * s;
-                              }
+                              griddep_wait();
+                              griddep_launch_next();
+                              for (int r = threadIdx.x; r < R; r += blockDim.x) st[r] = isc * sum_pairs(part, R, q0, q1, r);
                               __syncthreads();
                             });
 }
 
 // ---------------------------------------------------------------- bwd2 ---
-// x_i^R = om_i - Ainv_i sum_{j>i near} Ahat_ij^RR om_j;  x_i = U_i [x_i^R; x_i^S]
-// (one CTA per box)
+// z_i = [x_i^R; x_i^S] with x_i^R = om_i - Ainv_i sum_{j>i near} Ahat_ij^RR om_j
 template <typename T>
-__global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ nj, const float* __restrict__ iscale,
-                                                   const T* __restrict__ Ainv, const T* __restrict__ U,
-                                                   const T* __restrict__ om, const T* __restrict__ px,
-                                                   const T* __restrict__ part, T* __restrict__ xs) {
+__global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, int ns, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ hi_cnt, const float* __restrict__ iscale,
+                                                   const T* __restrict__ Ainv, const T* __restrict__ om,
+                                                   const T* __restrict__ px, const T* __restrict__ part,
+                                                   T* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sq = reinterpret_cast<T*>(sm_raw);  // R
-  T* sz = sq + R;                        // D
-  T* sp = sz + D;                        // 8 * D
-  const int i = blockIdx.x;
-  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, sq, T(-1), om + (int64_t)i * R, sz, [&] {
-    const T isc = iscale ? T(iscale[0]) : T(1);
-    const int64_t q0 = ptr[i], q1 = ptr[i + 1];
-    for (int r = threadIdx.x; r < R; r += blockDim.x)
-      sq[r] = isc * sum_pairs(part, R, q0, q1, nj, r, [i](int j) { return j > i; });
-    const T* xi = px + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
-    for (int e = threadIdx.x; e < K; e += blockDim.x) sz[R + e] = xi[e];
-    __syncthreads();
-  });
+  const Slice sl = slice_of(ns, R);
+  const int i = sl.i;
+  cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, sq, T(-1), om + (int64_t)i * R + sl.r0,
+                            z + (int64_t)i * D + sl.r0, [&] {
+                              const T isc = iscale ? T(iscale[0]) : T(1);
+                              // the pairs j > i trail the box's sorted range
+                              const int64_t q1 = ptr[i + 1], q0 = q1 - hi_cnt[i];
+                              griddep_wait();
+                              griddep_launch_next();
+                              if (blockIdx.x % ns == 0) {
+                                const T* xi = px + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
+                                for (int e = threadIdx.x; e < K; e += blockDim.x) z[(int64_t)i * D + R + e] = xi[e];
+                              }
+                              for (int r = threadIdx.x; r < R; r += blockDim.x) sq[r] = isc * sum_pairs(part, R, q0, q1, r);
+                              __syncthreads();
+                            });
+}
+
+// x_i = U_i z_i (Ur: U_i row-major)
+template <typename T>
+__global__ void __launch_bounds__(256) bwd2u_kernel(int D, int ns, const T* __restrict__ Ur, const T* __restrict__ z,
+                                                    T* __restrict__ xs) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  T* sz = reinterpret_cast<T*>(sm_raw);  // D
+  const Slice sl = slice_of(ns, D);
+  const int i = sl.i;
+  cta_gemv<T, T, Unr<T>::v>(Ur + ((int64_t)i * D + sl.r0) * D, D, sl.nr, D, sz, T(1), nullptr,
+                            xs + (int64_t)i * D + sl.r0, [&] {
+                              griddep_wait();
+                              griddep_launch_next();
+                              for (int e = threadIdx.x; e < D; e += blockDim.x) sz[e] = z[(int64_t)i * D + e];
+                              __syncthreads();
+                            });
+}
+
+// out_b = (in_b)^T for nb square D x D blocks (32 x 32 tiles through shared memory)
+template <typename T>
+__global__ void transpose_blocks_kernel(int D, const T* __restrict__ in, T* __restrict__ out) {
+  __shared__ T tile[32][33];
+  const int64_t b = blockIdx.z;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const T* src = in + b * D * D;
+  T* dst = out + b * D * D;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int r = by + y, c = bx + threadIdx.x;
+    if (r < D && c < D) tile[y][threadIdx.x] = src[(int64_t)r * D + c];
+  }
   __syncthreads();
-  cta_gemv_cols<T, T>(U + (int64_t)i * D * D, D, D, D, sz, sp, xs + (int64_t)i * D);
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int r = bx + y, c = by + threadIdx.x;
+    if (r < D && c < D) dst[(int64_t)r * D + c] = tile[threadIdx.x][y];
+  }
+}
+template <typename T>
+void launch_transpose_blocks(int64_t nb, int D, const T* in, T* out, cudaStream_t st) {
+  if (nb == 0 || D == 0) return;
+  ++g_launches;
+  dim3 grid((D + 31) / 32, (D + 31) / 32, (unsigned)nb);
+  transpose_blocks_kernel<T><<<grid, dim3(32, 8), 0, st>>>(D, in, out);
 }
 
 static void set_smem(const void* f, size_t sm) {
   if (sm > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+}
+
+// Launch with programmatic stream serialization (see griddep_wait).
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++g_launches;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// row slices per box: enough CTAs for two per SM, at least 32 rows each
+static int row_splits(int nb, int nrows) {
+  static int nsm = 0;
+  if (!nsm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
+  }
+  if (nb <= 0) return 1;
+  int ns = (2 * nsm + nb - 1) / nb;
+  ns = std::min(ns, std::max(1, nrows / 32));
+  return std::max(ns, 1);
 }
 
 template <typename T, typename TS, int PH>
@@ -584,49 +712,50 @@ static void launch_pairs(const DevLevel& L, const int32_t* list, int64_t n, cons
   const int nc = (PH == PH_RS) ? L.K : L.R;
   const size_t sm = sizeof(T) * (size_t)std::max(nc, 1);
   set_smem((const void*)pair_kernel<T, TS, PH>, sm);
-  ++g_launches;
-  pair_kernel<T, TS, PH><<<(unsigned)n, 256, sm, st>>>(L.D, L.R, L.K, list, L.near_j, Ahat, xv, part);
+  launch_pdl(pair_kernel<T, TS, PH>, (unsigned)n, 256, sm, st, L.D, L.R, L.K, list, L.near_j, Ahat, xv, part);
 }
 
 template <typename T>
 void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st) {
-  size_t sm = sizeof(T) * 2 * L.D;
-  ++g_launches;
-  fwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, F.U, Ainv, F.vin, F.c, F.u);
+  const int ns = row_splits(L.nb, L.D);
+  launch_pdl(fwd1_kernel<T>, L.nb * ns, 256, sizeof(T) * L.D, st, L.D, ns, F.U, F.vin, F.c);
+  if (L.R == 0) return;
+  const int nu = row_splits(L.nb, L.R);
+  launch_pdl(fwd1u_kernel<T>, L.nb * nu, 256, sizeof(T) * L.R, st, L.D, L.R, nu, Ainv, F.c, F.u);
 }
 template <typename T, typename TS>
 void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, cudaStream_t st) {
-  // pairs j < i only (the lo list also holds the diagonal pairs, which the
-  // per-box kernel skips)
+  if (L.R == 0) return;
   launch_pairs<T, TS, PH_RR>(L, L.lo_pairs, L.n_lo, Ahat, F.u, F.part, st);
-  size_t sm = sizeof(T) * (size_t)std::max(L.R, 1);
-  ++g_launches;
-  fwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.near_ptr, L.near_j, iscale, F.Ainv, F.c, F.part, F.v);
+  const int ns = row_splits(L.nb, L.R);
+  launch_pdl(fwd2_kernel<T>, L.nb * ns, 256, sizeof(T) * L.R, st, L.D, L.R, ns, L.near_ptr, L.lo_cnt, iscale, F.Ainv,
+             F.c, F.part, F.v);
 }
 template <typename T, typename TS>
 void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, T* parent_vin,
                  cudaStream_t st) {
+  if (L.K == 0) return;
   launch_pairs<T, TS, PH_SR>(L, nullptr, L.NP, Ahat, F.v, F.part, st);
-  ++g_launches;
-  fwd3_kernel<T><<<L.nb, 128, 0, st>>>(L.D, L.R, L.K, L.near_ptr, iscale, F.c, F.part, parent_vin);
+  launch_pdl(fwd3_kernel<T>, L.nb, 128, 0, st, L.D, L.R, L.K, L.near_ptr, iscale, F.c, F.part, parent_vin);
 }
 template <typename T, typename TS>
 void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
                  cudaStream_t st) {
+  if (L.R == 0) return;
   launch_pairs<T, TS, PH_RS>(L, nullptr, L.NP, Ahat, parent_x, F.part, st);
-  size_t sm = sizeof(T) * (size_t)std::max(L.R, 1);
-  ++g_launches;
-  bwd1_kernel<T><<<L.nb, 256, sm, st>>>(L.R, L.near_ptr, iscale, F.Ainv, F.v, F.part, F.om);
+  const int ns = row_splits(L.nb, L.R);
+  launch_pdl(bwd1_kernel<T>, L.nb * ns, 256, sizeof(T) * L.R, st, L.R, ns, L.near_ptr, iscale, F.Ainv, F.v, F.part,
+             F.om);
 }
 template <typename T, typename TS>
 void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
                  cudaStream_t st) {
-  launch_pairs<T, TS, PH_RR>(L, L.hi_pairs, L.n_hi, Ahat, F.om, F.part, st);
-  size_t sm = sizeof(T) * ((size_t)L.R + 9 * (size_t)L.D);
-  set_smem((const void*)bwd2_kernel<T>, sm);
-  ++g_launches;
-  bwd2_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.R, L.K, L.near_ptr, L.near_j, iscale, F.Ainv, F.U, F.om, parent_x,
-                                        F.part, F.xs);
+  const int ns = row_splits(L.nb, std::max(L.R, 1));
+  if (L.R > 0) launch_pairs<T, TS, PH_RR>(L, L.hi_pairs, L.n_hi, Ahat, F.om, F.part, st);
+  launch_pdl(bwd2_kernel<T>, L.nb * ns, 256, sizeof(T) * std::max(L.R, 1), st, L.D, L.R, L.K, ns, L.near_ptr,
+             L.hi_cnt, iscale, F.Ainv, F.om, parent_x, F.part, F.z);
+  const int nx = row_splits(L.nb, L.D);
+  launch_pdl(bwd2u_kernel<T>, L.nb * nx, 256, sizeof(T) * L.D, st, L.D, nx, F.Ur, F.z, F.xs);
 }
 
 // y = M x for one n x n row-major matrix (root solve with the explicit inverse)
@@ -652,6 +781,7 @@ void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st) {
 
 #define H2_INST_SOLVE(T)                                                                     \
   template void launch_fwd1<T>(const DevLevel&, const FacLevel<T>&, const T*, cudaStream_t); \
+  template void launch_transpose_blocks<T>(int64_t, int, const T*, T*, cudaStream_t);         \
   template void launch_gemv_rows<T>(int, const T*, const T*, T*, cudaStream_t);
 H2_INST_SOLVE(double)
 H2_INST_SOLVE(float)
