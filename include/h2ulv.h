@@ -243,7 +243,9 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap);
  * factorizations and for "X"/"A"-FP64, 4-byte floats otherwise); *elem_size
  * receives that size.  With dst == NULL only *count (elements) and
  * *elem_size are set.  Errors: H2_ERR_INVALID_ARG (unknown name or level,
- * cap too small), H2_ERR_STATE (not computed yet). */
+ * cap too small; "lu" and "root" after a mixed-precision factorization,
+ * which inverts the blocks by Gauss-Jordan elimination and keeps no LU
+ * factors), H2_ERR_STATE (not computed yet). */
 h2_status h2_export(const h2_ctx* c, const char* name, int32_t level, void* dst,
                     size_t cap_bytes, size_t* count, int32_t* elem_size);
 

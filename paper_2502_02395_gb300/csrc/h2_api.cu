@@ -634,12 +634,24 @@ void ulv_apply_f32(h2_ctx* c, const float* v, float* z) {
 // H^2 matvec over the FP64 instance (refinement residual) or its FP32 copy
 // (inner solver of the mixed-precision refinement)
 // ---------------------------------------------------------------------------
+using EventPairs = std::vector<std::pair<cudaEvent_t, cudaEvent_t>>;
+
+// y = A_H2 x; with leaf_ev set, the leaf-level kernel (near blocks plus the
+// leaf basis) is bracketed by a pair of events appended there.
 template <typename T>
-void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, const T* x, T* y) {
+void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, const T* x, T* y,
+              EventPairs* leaf_ev = nullptr) {
   const int L = c->L;
   cudaStream_t st = c->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (leaf_ev) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+  }
   if (L == 0) {
+    if (leaf_ev) cudaEventRecord(e0, st);
     launch_matvec_leaf<T>(c->lv[0], A, nullptr, x, nullptr, y, st);
+    if (leaf_ev) cudaEventRecord(e1, st), leaf_ev->push_back({e0, e1});
     return;
   }
   const std::vector<int64_t>& off = c->hat_off;
@@ -647,14 +659,16 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
   for (int l = L - 1; l >= 1; --l) launch_matvec_up<T>(c->lv[l], X[l], xh + off[l + 1], xh + off[l], st);
   for (int l = 1; l <= L; ++l) launch_matvec_far<T>(c->lv[l], S[l], xh + off[l], yh + off[l], st);
   for (int l = 1; l < L; ++l) launch_matvec_down<T>(c->lv[l], X[l], yh + off[l], yh + off[l + 1], st);
+  if (leaf_ev) cudaEventRecord(e0, st);
   launch_matvec_leaf<T>(c->lv[L], A, X[L], x, yh + off[L], y, st);
+  if (leaf_ev) cudaEventRecord(e1, st), leaf_ev->push_back({e0, e1});
 }
 
 void matvec_impl(h2_ctx* c, const double* x, double* y) {
   matvec_t<double>(c, c->A64, c->X64p.data(), c->S64p.data(), c->xhat, c->yhat, x, y);
 }
-void matvec32(h2_ctx* c, const float* x, float* y) {
-  matvec_t<float>(c, c->A32, c->X32p.data(), c->S32p.data(), c->xhat32, c->yhat32, x, y);
+void matvec32(h2_ctx* c, const float* x, float* y, EventPairs* leaf_ev = nullptr) {
+  matvec_t<float>(c, c->A32, c->X32p.data(), c->S32p.data(), c->xhat32, c->yhat32, x, y, leaf_ev);
 }
 
 bool factor_ready(const h2_ctx* c) {
@@ -668,8 +682,8 @@ void ulv_apply_any(h2_ctx* c, const double* r, double* x) {
 
 // CUDA-event timing of the substitution and matvec calls inside a solve
 struct SolveTimer {
-  using Pairs = std::vector<std::pair<cudaEvent_t, cudaEvent_t>>;
-  Pairs sub, mv, mv32;
+  using Pairs = EventPairs;
+  Pairs sub, mv, mv32, leaf32;  // leaf32: the leaf kernel inside each FP32 matvec
   cudaStream_t st;
   explicit SolveTimer(cudaStream_t s) : st(s) {}
   template <class Fn>
@@ -875,7 +889,7 @@ h2_status nested_refine(h2_ctx* c, SolveTimer& tm, double bnorm, double target, 
   double beta = bnorm;
   rel = 1.0;
   auto prec = [&](const float* v, float* z) { tm.run(tm.sub, [&] { ulv_apply_f32(c, v, z); }); };
-  auto mv = [&](const float* z, float* w) { tm.run(tm.mv32, [&] { matvec32(c, z, w); }); };
+  auto mv = [&](const float* z, float* w) { tm.run(tm.mv32, [&] { matvec32(c, z, w, &tm.leaf32); }); };
   while (its < max_iters && (target <= 0 || beta > target * bnorm)) {
     launch_norm2<double>(c->r64, n, c->red, st);
     launch_scaled_copy<double, float>(c->r64, c->red, true, c->gm_r32, n, st);
@@ -1092,6 +1106,7 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
       SolveTimer::total(t->sub);
       SolveTimer::total(t->mv);
       SolveTimer::total(t->mv32);
+      SolveTimer::total(t->leaf32);
     }
   } guard{&timer};
   int method = c->refine_method;
@@ -1125,6 +1140,8 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   c->times.n_subst = (int)timer.sub.size();
   c->times.n_matvec = (int)timer.mv.size();
   c->times.n_matvec32 = (int)timer.mv32.size();
+  c->times.n_leaf32 = (int)timer.leaf32.size();
+  c->times.leaf32 = SolveTimer::total(timer.leaf32);
   c->times.subst = SolveTimer::total(timer.sub);
   c->times.matvec = SolveTimer::total(timer.mv);
   c->times.matvec32 = SolveTimer::total(timer.mv32);  // the guard then finds the lists empty
@@ -1190,20 +1207,26 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     by_mv += 8.0 * (2.0 * d.nb * D * K + (double)d.FP * K * K);
     fl_mv += 2.0 * (2.0 * d.nb * D * K + (double)d.FP * K * K);
   }
+  double by_leaf32 = 0;
   {
     const DevLevel& lf = c->lv[c->L];
     by_mv += 8.0 * (double)lf.NP * lf.D * lf.D;
     fl_mv += 2.0 * (double)lf.NP * lf.D * lf.D;
+    // leaf kernel of the FP32 matvec: the near blocks, the leaf basis, x and
+    // the skeleton coefficients read once, y written once
+    const double K = c->L ? lf.K : 0;
+    by_leaf32 = 4.0 * ((double)lf.NP * lf.D * lf.D + (double)lf.nb * lf.D * K + 2.0 * lf.nb * lf.D + lf.nb * K);
   }
   o << "],\"bytes_subst\":" << by_sub << ",\"bytes_matvec\":" << by_mv << ",\"flops_matvec\":" << fl_mv
-    << ",\"bytes_matvec32\":" << by_mv / 2;
+    << ",\"bytes_matvec32\":" << by_mv / 2 << ",\"bytes_matvec32_leaf\":" << by_leaf32;
   o << ",\"flops\":{\"a1_qr\":" << fl_qr << ",\"a2_proj\":" << fl_proj << ",\"a3_lu\":" << fl_lu
     << ",\"a45_schur\":" << fl_schur << ",\"a2c_coupling\":" << fl_coup << "}";
   o << ",\"times\":{\"a1_qr\":" << t.a1_qr << ",\"a2_proj\":" << t.a2_proj << ",\"a3_lu\":" << t.a3_lu
     << ",\"a45_schur\":" << t.a5_schur << ",\"a2c_coupling\":" << t.a2c_coupling << ",\"a6_merge\":" << t.a6_merge
     << ",\"a7_root\":" << t.a7_root << ",\"factor\":" << t.total_factor << ",\"solve\":" << t.solve_total
     << ",\"solve_subst\":" << t.subst << ",\"solve_matvec\":" << t.matvec << ",\"solve_matvec32\":" << t.matvec32
-    << "},\"calls\":{\"subst\":" << t.n_subst << ",\"matvec\":" << t.n_matvec << ",\"matvec32\":" << t.n_matvec32
+    << ",\"matvec32_leaf\":" << t.leaf32
+    << "},\"calls\":{\"subst\":" << t.n_subst << ",\"matvec\":" << t.n_matvec << ",\"matvec32\":" << t.n_matvec32 << ",\"matvec32_leaf\":" << t.n_leaf32
     << "},\"method\":" << t.method
     << ",\"iters\":" << t.iters << ",\"relres\":" << t.relres
     << ",\"kernel_launches\":" << g_launches.load() << ",\"refine_method\":" << c->refine_method
@@ -1265,6 +1288,7 @@ h2_status h2_export(const h2_ctx* c, const char* name, int32_t level, void* dst,
   } else if (level >= 1 && (n == "lu" || n == "piv")) {
     if (!ready) return H2_ERR_STATE;
     const bool p64 = f64;
+    if (n == "lu" && !p64) return H2_ERR_INVALID_ARG;  // the mixed factorization keeps only the inverses
     src = (n == "lu") ? (const void*)(p64 ? c->f64.lv[level].lu : (const double*)(const void*)c->f32.lv[level].luT)
                       : (const void*)(p64 ? c->f64.lv[level].piv : c->f32.lv[level].piv);
     es = (n == "lu") ? (p64 ? 8 : 4) : 4;
@@ -1272,6 +1296,7 @@ h2_status h2_export(const h2_ctx* c, const char* name, int32_t level, void* dst,
   } else if (n == "root" || n == "root_piv" || n == "root_inv") {
     if (!ready) return H2_ERR_STATE;
     const size_t D0 = c->lv[0].D;
+    if (n == "root" && !f64) return H2_ERR_INVALID_ARG;  // as for "lu"
     if (n == "root") {
       src = f64 ? (const void*)c->f64.root_lu : (const void*)c->f32.root_luT;
       es = f64 ? 8 : 4;

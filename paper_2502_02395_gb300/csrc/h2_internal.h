@@ -185,8 +185,8 @@ struct PhaseTimes {
   double a1_qr = 0, a2_proj = 0, a3_lu = 0, a5_schur = 0, a2c_coupling = 0, a6_merge = 0,
          a7_root = 0, total_factor = 0;
   double solve_total = 0, subst = 0, matvec = 0;
-  double matvec32 = 0;
-  int iters = 0, n_subst = 0, n_matvec = 0, n_matvec32 = 0, method = 0;
+  double matvec32 = 0, leaf32 = 0;
+  int iters = 0, n_subst = 0, n_matvec = 0, n_matvec32 = 0, n_leaf32 = 0, method = 0;
   double relres = 0;
   std::vector<double> history;  // relative residual after every correction (IR) or cycle (GMRES)
 };

@@ -568,11 +568,202 @@ __global__ void __launch_bounds__(256) lu_inverse_f32_kernel(int R, int Rp, cons
   }
 }
 
+// ------------------------------------------------------------------------
+// a3, mixed precision: (Ahat_ii^RR)^-1 by Gauss-Jordan elimination with
+// partial pivoting, in FP32, with the block held in registers.  Thread
+// (tr, tc) of an (Rp/TR) x (Rp/TC) grid keeps the TR x TC tile at rows
+// TR tr.., columns TC tc.. (Rp = R rounded up to the tile sizes; padding
+// rows never pivot).  Step k: the owners of column k propose their largest
+// |entry| among rows not yet used as pivots (LAPACK's choice: the first
+// largest); the chosen row p is scaled so that its column-k entry becomes
+// 1 / a_pk (the in-place form that stores the inverse where the eliminated
+// column was), and every other row r takes a_r -= a_rk * (scaled row p)
+// with its column-k entry zeroed first.  Rows are never moved, so at the end
+//   Ainv[k][pivot(j)] = a[pivot(k)][j],  pivot(k) = the row chosen at step k.
+// The row-interchange sequence LAPACK's getrf would record (the same pivots:
+// the unused rows of column k are the Schur complement column) is written to
+// piv.  A zero or non-finite pivot column records (level, box) in
+// status[0..1] and leaves the box's output undefined.
+// Tiles: 8 x 8 (256 threads) for R <= 128, 12 x 6 (512 threads) for
+// R <= 192; the register file of one SM sub-partition bounds both.
+// ------------------------------------------------------------------------
+constexpr int kGjMaxR = 192;
+
+struct GjShared {
+  float P[kGjMaxR];
+  float fcol[kGjMaxR];
+  float cv[32], cs[32];
+  int cr[32];
+  int prow[kGjMaxR], pinv[kGjMaxR], rowat[kGjMaxR];
+  int p;
+  float pv;
+};
+
+// One elimination step for column k = TC kc + J (J fixed at compile time so
+// that the tile stays in registers).  Returns false on a zero pivot column.
+template <int TR, int TC, int J>
+__device__ __forceinline__ bool gj_step(GjShared& sh, float (&a)[TR][TC], unsigned& used, int kc, int ntr,
+                                        bool has, int tr, int tc, int r0, int c0) {
+  const int t = threadIdx.x, k = kc * TC + J;
+  // (a) pivot candidates from the owners of column k
+  if (has && tc == kc) {
+    float best = -1.0f, sv = 0.0f;
+    int bi = -1;
+#pragma unroll
+    for (int i = 0; i < TR; ++i) {
+      const float v = fabsf(a[i][J]);
+      if (!((used >> i) & 1u) && v > best) best = v, sv = a[i][J], bi = r0 + i;
+    }
+    sh.cv[tr] = best, sh.cs[tr] = sv, sh.cr[tr] = bi;
+  }
+  __syncthreads();
+  if (t < 32) {
+    float best = t < ntr ? sh.cv[t] : -1.0f, sv = t < ntr ? sh.cs[t] : 0.0f;
+    int bi = t < ntr ? sh.cr[t] : -1;
+    for (int o = 16; o; o >>= 1) {
+      const float ob = __shfl_down_sync(0xffffffffu, best, o), os = __shfl_down_sync(0xffffffffu, sv, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) best = ob, sv = os, bi = oi;
+    }
+    if (t == 0) {
+      sh.p = bi, sh.pv = sv;
+      if (bi >= 0) sh.prow[k] = bi;
+    }
+  }
+  __syncthreads();
+  const int p = sh.p;
+  const float pv = sh.pv;
+  if (p < 0 || pv == 0.0f || !isfinite(pv)) return false;
+  const float inv = 1.0f / pv;
+  // (b) scaled pivot row -> P, column k -> fcol
+  if (has && tr == p / TR) {
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+      if (r0 + i == p) {
+#pragma unroll
+        for (int jj = 0; jj < TC; ++jj) {
+          const float v = ((jj == J && c0 + jj == k) ? 1.0f : a[i][jj]) * inv;
+          a[i][jj] = v;
+          sh.P[c0 + jj] = v;
+        }
+        used |= 1u << i;
+      }
+  }
+  if (has && tc == kc) {
+#pragma unroll
+    for (int i = 0; i < TR; ++i) sh.fcol[r0 + i] = a[i][J];
+  }
+  __syncthreads();
+  // (c) eliminate column k from every other row
+  if (has) {
+    float pr[TC];
+#pragma unroll
+    for (int jj = 0; jj < TC; ++jj) pr[jj] = sh.P[c0 + jj];
+    const bool own = (tc == kc);
+#pragma unroll
+    for (int i = 0; i < TR; ++i) {
+      const float f = (r0 + i == p) ? 0.0f : sh.fcol[r0 + i];
+      if (own && r0 + i != p) a[i][J] = 0.0f;
+#pragma unroll
+      for (int jj = 0; jj < TC; ++jj) a[i][jj] = fmaf(-f, pr[jj], a[i][jj]);
+    }
+  }
+  return true;
+}
+
+template <int TR, int TC, int J>
+__device__ __forceinline__ void gj_steps(bool& ok, GjShared& sh, float (&a)[TR][TC], unsigned& used, int kc,
+                                         int ntr, int left, bool has, int tr, int tc, int r0, int c0) {
+  if constexpr (J < TC) {
+    if (ok && left > J) ok = gj_step<TR, TC, J>(sh, a, used, kc, ntr, has, tr, tc, r0, c0);
+    gj_steps<TR, TC, J + 1>(ok, sh, a, used, kc, ntr, left, has, tr, tc, r0, c0);
+  }
+}
+
+template <int TR, int TC, int NT>
+__global__ void __launch_bounds__(NT) gj_inverse_kernel(int D, int R, const float* __restrict__ Ablk,
+                                                        const int32_t* __restrict__ diag_idx,
+                                                        float* __restrict__ Ainv, int32_t* __restrict__ piv,
+                                                        int32_t* __restrict__ status, int level) {
+  __shared__ GjShared sh;
+  constexpr int TL = (TR > TC ? TR : TC);  // Rp is a multiple of both tile edges
+  static_assert(TL % TR == 0 && TL % TC == 0, "tile edges must divide the larger one");
+  const int box = blockIdx.x, t = threadIdx.x;
+  const int Rp = (R + TL - 1) / TL * TL, ntr = Rp / TR, ntc = Rp / TC;
+  const bool has = t < ntr * ntc;
+  const int tr = has ? t / ntc : 0, tc = has ? t % ntc : 0;
+  const int r0 = tr * TR, c0 = tc * TC;
+  const float* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
+  float a[TR][TC];
+  unsigned used = 0;
+#pragma unroll
+  for (int i = 0; i < TR; ++i) {
+    const int r = r0 + i;
+    if (!has || r >= R) used |= 1u << i;
+#pragma unroll
+    for (int j = 0; j < TC; ++j) {
+      const int c = c0 + j;
+      a[i][j] = (has && r < R && c < R) ? A[(size_t)r * D + c] : 0.0f;
+    }
+  }
+  bool ok = true;
+  for (int kc = 0; kc < ntc && ok; ++kc)
+    gj_steps<TR, TC, 0>(ok, sh, a, used, kc, ntr, R - kc * TC, has, tr, tc, r0, c0);
+  if (!ok) {
+    if (t == 0 && atomicCAS(status, 0, level + 1) == 0) status[1] = box;
+    return;
+  }
+  // unscramble: Ainv[k][prow[j]] = a[prow[k]][j]
+  for (int k = t; k < R; k += blockDim.x) sh.pinv[sh.prow[k]] = k;
+  __syncthreads();
+  if (has) {
+    float* out = Ainv + (size_t)box * R * R;
+#pragma unroll
+    for (int i = 0; i < TR; ++i) {
+      const int r = r0 + i;
+      if (r >= R) continue;
+      const size_t row = (size_t)sh.pinv[r] * R;
+#pragma unroll
+      for (int jj = 0; jj < TC; ++jj)
+        if (c0 + jj < R) out[row + sh.prow[c0 + jj]] = a[i][jj];
+    }
+  }
+  // LAPACK-style interchange sequence of the same pivots: pos[r] is the
+  // current position of original row r, rowat[q] the row at position q
+  __syncthreads();
+  if (t == 0) {
+    int* pos = sh.pinv;
+    for (int q = 0; q < R; ++q) pos[q] = q, sh.rowat[q] = q;
+    int32_t* pv_out = piv + (size_t)box * R;
+    for (int k = 0; k < R; ++k) {
+      const int r = sh.prow[k], q = pos[r], rk = sh.rowat[k];
+      pv_out[k] = q;
+      sh.rowat[k] = r, sh.rowat[q] = rk;
+      pos[r] = k, pos[rk] = q;
+    }
+  }
+}
+
 template <typename T>
 void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
                        int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st) {
   if (nb == 0 || R == 0) return;
   (void)lu;  // for T = double, luT is the lu array
+  if (std::is_same<T, float>::value && R <= kGjMaxR) {
+    // mixed precision: the inverse directly, no LU factors kept
+    const float* Af = reinterpret_cast<const float*>(Ablk);
+    float* Af_inv = reinterpret_cast<float*>(Ainv);
+    ++g_launches;
+    if (R <= 128) {
+      const int n = (R + 7) / 8, threads = std::max(32, (n * n + 31) / 32 * 32);
+      gj_inverse_kernel<8, 8, 256><<<nb, threads, 0, st>>>(D, R, Af, diag_idx, Af_inv, piv, status, level);
+    } else {
+      const int Rp = (R + 11) / 12 * 12, threads = (Rp / 12) * (Rp / 6);
+      gj_inverse_kernel<12, 6, 512><<<nb, (threads + 31) / 32 * 32, 0, st>>>(D, R, Af, diag_idx, Af_inv, piv, status,
+                                                                               level);
+    }
+    return;
+  }
   const size_t cap = 220 * 1024;
   size_t sm1 = sizeof(T) * (size_t)R * (R + 1);
   int use = sm1 <= cap;
