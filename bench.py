@@ -184,7 +184,8 @@ def fp64_peak_tflops() -> float:
 # DRAM traffic of one launch of the FP32 leaf matvec kernel (the step's
 # largest kernel) from an ncu capture of this bench's workload, valid while
 # the kernel's source is the one captured (digest of its text below).
-LEAF_TRAFFIC = None  # {"digest": ..., "bytes_per_launch": ..., "profile": ...}
+LEAF_TRAFFIC = {"digest": "f0e1536c62ad997a", "bytes_per_launch": 6.62e9 + 4.50e6,
+                "profile": "profiles/mv_leaf_kernel_cube262144_yukawa.md"}
 
 
 def leaf_kernel_digest() -> str:
