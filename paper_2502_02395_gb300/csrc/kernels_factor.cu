@@ -318,9 +318,129 @@ __global__ void perm_identity_kernel(int nb, int D, int K, T* __restrict__ U) {
   }
 }
 
+// The same factorization in FP32 with the panel in registers: warp w owns
+// columns w, w + 16, ... and lane l rows l, l + 32, ... (D <= 32 RPL,
+// K <= 16 CPW).  Step k: the owner warp of column k forms the reflector
+// (warp reductions only), publishes v and tau through a double-buffered
+// shared vector, and after one barrier every warp updates its columns
+// j > k: w = tau v^T x_j (lane-local products, one warp reduction),
+// x_j -= w v.  The rank-1 updates stay in registers; shared memory carries
+// only v.
+template <int RPL, int CPW>
+__global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* __restrict__ Xin,
+                                                     float* __restrict__ Vout, float* __restrict__ tau_out,
+                                                     float* __restrict__ Tm) {
+  constexpr int NW = 16;
+  __shared__ __align__(16) float vs[2][RPL * 32];
+  __shared__ float s_tau[2];
+  __shared__ float tile[32][NW * CPW + 1];
+  const int box = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* src = Xin + (size_t)box * D * K;  // row-major D x K
+  float x[CPW][RPL];
+  // load through shared memory, 32 rows at a time (coalesced reads)
+#pragma unroll
+  for (int s = 0; s < RPL; ++s) {
+    for (int e = threadIdx.x; e < 32 * K; e += blockDim.x) {
+      const int rr = e / K, cc = e - rr * K, r = 32 * s + rr;
+      tile[rr][cc] = (r < D) ? src[(size_t)r * K + cc] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      const int j = warp + NW * c;
+      x[c][s] = (j < K) ? tile[lane][j] : 0.0f;
+    }
+    __syncthreads();
+  }
+  int buf = 0;
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+    for (int w = 0; w < NW; ++w) {
+      const int k = c * NW + w;
+      if (k >= K) break;
+      float* vb = vs[buf];
+      if (warp == w) {
+        float alpha = 0.0f, part = 0.0f;
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+          const int r = lane + 32 * s;
+          if (r == k) alpha = x[c][s];
+          if (r > k) part += x[c][s] * x[c][s];
+        }
+        for (int o = 16; o; o >>= 1) {
+          part += __shfl_xor_sync(0xffffffffu, part, o);
+          alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+        }
+        float tau = 0.0f, beta = alpha, scal = 0.0f;
+        if (part != 0.0f) {
+          beta = -copysignf(sqrtf(alpha * alpha + part), alpha);
+          tau = (beta - alpha) / beta;
+          scal = 1.0f / (alpha - beta);
+        }
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+          const int r = lane + 32 * s;
+          float vv = 0.0f;
+          if (r == k) {
+            vv = 1.0f;
+            x[c][s] = beta;
+          } else if (r > k && tau != 0.0f) {
+            vv = x[c][s] * scal;
+            x[c][s] = vv;
+          }
+          vb[r] = vv;
+        }
+        if (lane == 0) s_tau[buf] = tau;
+      }
+      __syncthreads();
+      const float tk = s_tau[buf];
+      if (tk != 0.0f) {
+        float v[RPL];
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) v[s] = vb[lane + 32 * s];
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+          const int j = warp + NW * cc;
+          if (j > k && j < K) {
+            float d = 0.0f;
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) d = fmaf(v[s], x[cc][s], d);
+            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            d *= tk;
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) x[cc][s] = fmaf(-d, v[s], x[cc][s]);
+          }
+        }
+      }
+      if (threadIdx.x == 0) tau_out[(size_t)box * K + k] = tk;
+      buf ^= 1;
+    }
+  }
+  // R (row-major, upper) and V (column-major, unit diagonal, zeros above)
+  float* Rb = Tm + (size_t)box * K * K;
+  float* Vb = Vout + (size_t)box * D * K;
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+    const int j = warp + NW * c;
+    if (j >= K) continue;
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) {
+      const int r = lane + 32 * s;
+      if (r < K) Rb[(size_t)r * K + j] = (r <= j) ? x[c][s] : 0.0f;
+      if (r < D) Vb[(size_t)j * D + r] = (r > j) ? x[c][s] : (r == j ? 1.0f : 0.0f);
+    }
+  }
+}
+
 template <typename T>
 void launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm, T* gscr, cudaStream_t st) {
   if (nb == 0 || K == 0) return;
+  if (std::is_same<T, float>::value && D <= 256 && K <= 128) {
+    ++g_launches;
+    qr_reg_kernel<8, 8><<<nb, 512, 0, st>>>(D, K, reinterpret_cast<const float*>(Xin), reinterpret_cast<float*>(Vout),
+                                            reinterpret_cast<float*>(tau), reinterpret_cast<float*>(Tm));
+    return;
+  }
   const size_t sm = sizeof(T) * (size_t)D * K;
   const int use = sm <= 200 * 1024;
   if (use) cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -176,6 +176,29 @@ def test_mixed_refined_solution(B, name, prec, method):
     S.close()
 
 
+@pytest.mark.parametrize("name", ["cube2048_laplace", "sphere1000_ragged", "cube8192_yukawa"])
+def test_mixed_complement_bases(B, name):
+    """FP32 complement bases (register-resident Householder QR of X^orth,
+    compact WY form) against the FP64 oracle's at every level: orthogonal to
+    FP32 accuracy, and equal to the oracle's U and T up to FP32 rounding
+    carried through the levels (X^orth of a parent is built from its
+    children's T)."""
+    H, F, flat, b = oracle_case(name)
+    S = lib_case(B, name)
+    S.factor("fp16")
+    for l in range(H["L"], 0, -1):
+        D, K = H["D"][l], H["K"][l]
+        nb = 1 << l
+        U = S.export("U", l).reshape(nb, D, D).astype(np.float64)  # column-major per box
+        T = S.export("T", l).reshape(nb, K, K).astype(np.float64)
+        for i in range(nb):
+            assert np.abs(U[i] @ U[i].T - np.eye(D)).max() <= 1e-5, (l, i)
+            assert np.abs(U[i].T - F["U"][l][i]).max() <= 1e-3, (l, i)
+            Tr = F["T"][l][i]
+            assert np.abs(T[i] - Tr).max() <= 1e-3 * max(1.0, np.abs(Tr).max()), (l, i)
+    S.close()
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_tensor_core_projection_leaf(B, prec):
     """Leaf-level projected blocks of the mixed path (tcgen05 GEMMs with
