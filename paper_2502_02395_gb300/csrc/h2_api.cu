@@ -437,6 +437,17 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       // the FP16 range for D <= 256 (BF16 has the FP32 exponent range).
       const bool sub16 = bf16 || D <= 256;
       f.ahat_isc = sub16 ? sc + 1 : nullptr;
+      f.err = c->status + 3;
+      // tensor maps over the 16-bit copy for the TMA-fed substitution: the
+      // quadrants must start on 16-byte columns and fit one pass of a CTA
+      f.tma = false;
+      if (sub16 && R > 0 && K > 0 && R % 8 == 0 && K % 8 == 0 && R <= 128 && K <= 128 &&
+          (uint64_t)d.NP * D < (1ull << 31)) {
+        const uint64_t rows = (uint64_t)d.NP * D;
+        f.tma = make_tile_map(&f.tm_rr, f.Ahat16, bf16, rows, D, D, R, R) &&
+                make_tile_map(&f.tm_sr, f.Ahat16, bf16, rows, D, D, K, R) &&
+                make_tile_map(&f.tm_rs, f.Ahat16, bf16, rows, D, D, R, K);
+      }
       bool ok = gemm_tc(bf16, D, D, D, A16, d.NP, D, D, nullptr, f.U16, d.nb, D, D, d.near_j, F.W16, DD, nullptr, D,
                         1, bf16, 1.0f, nullptr, d.NP, c->status + 2, st) &&
                 gemm_tc(bf16, D, D, D, f.U16, d.nb, D, D, d.near_i, F.W16, d.NP, D, D, nullptr, f.Ahat, DD, nullptr, D,
@@ -669,6 +680,23 @@ void matvec_impl(h2_ctx* c, const double* x, double* y) {
 }
 void matvec32(h2_ctx* c, const float* x, float* y, EventPairs* leaf_ev = nullptr) {
   matvec_t<float>(c, c->A32, c->X32p.data(), c->S32p.data(), c->xhat32, c->yhat32, x, y, leaf_ev);
+}
+
+// The substitution's TMA-fed kernels set status[3] when a bounded wait
+// gives up: clear it before a solve, read it after.
+h2_status subst_clear(h2_ctx* c) {
+  CKC(cudaMemsetAsync(c->status + 3, 0, sizeof(int32_t), c->stream));
+  return H2_OK;
+}
+h2_status subst_check(h2_ctx* c) {
+  int32_t w = 0;
+  CKC(cudaMemcpyAsync(&w, c->status + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+  CKC(cudaStreamSynchronize(c->stream));
+  if (w != 0) {
+    c->err = "a substitution kernel's wait for its tensor copies timed out";
+    return H2_ERR_TIMEOUT;
+  }
+  return H2_OK;
 }
 
 bool factor_ready(const h2_ctx* c) {
@@ -1058,11 +1086,12 @@ h2_status h2_ulv_apply(h2_ctx* c, const double* b, double* x) {
   const int64_t nslot = (int64_t)lf.nb * lf.D;
   CKS(vec_in(c, b, c->r64));
   CKC(cudaMemsetAsync(c->x64, 0, nslot * sizeof(double), c->stream));
+  CKS(subst_clear(c));
   ulv_apply_any(c, c->r64, c->x64);
   CKC(cudaGetLastError());
   CKS(vec_out(c, c->x64, x));
   CKC(cudaStreamSynchronize(c->stream));
-  return H2_OK;
+  return subst_check(c);
 }
 
 h2_status h2_matvec(h2_ctx* c, const double* x, double* y) {
@@ -1094,6 +1123,7 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   CKC(cudaMemcpyAsync(&bn2, c->red + 300, sizeof(double), cudaMemcpyDeviceToHost, st));
   CKC(cudaMemsetAsync(c->x64, 0, nslot * sizeof(double), st));
   CKC(cudaMemcpyAsync(c->r64, c->b64, nslot * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CKS(subst_clear(c));
   CKC(cudaStreamSynchronize(st));
   const double bnorm = std::sqrt(bn2);
   double rel = bnorm > 0 ? 1.0 : 0.0;
@@ -1149,6 +1179,7 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   c->times.relres = rel;
   if (relres_out) *relres_out = rel;
   if (iters_out) *iters_out = it;
+  CKS(subst_check(c));
   if (target > 0 && !(rel <= target)) {
     c->err = "refinement stopped at relative residual " + std::to_string(rel);
     return H2_ERR_NOT_CONVERGED;

@@ -1,6 +1,7 @@
 // Internal declarations of the H^2-ULV library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -159,6 +160,12 @@ struct FacLevel {
   // level keeps the substitution on the FP32 Ahat.
   void* Ahat16 = nullptr;
   const float* ahat_isc = nullptr;
+  // tensor maps over Ahat16 (rows NP * D, cols D) with the RR, SR and RS
+  // quadrants as tiles, for the TMA-fed pair kernels; tma is false where
+  // the shapes do not allow them
+  bool tma = false;
+  CUtensorMap tm_rr, tm_sr, tm_rs;
+  int32_t* err = nullptr;  // device word set by a substitution kernel whose wait timed out
 };
 
 template <typename T>

@@ -20,6 +20,7 @@
 // sum_near A_ij x_j.
 #include "h2_internal.h"
 #include "kernels.h"
+#include "ptx_util.h"
 
 namespace h2 {
 
@@ -488,6 +489,216 @@ __global__ void __launch_bounds__(256, sizeof(TS) == 2 ? 3 : 2) pair_kernel(int 
   });
 }
 
+// Persistent form of the pair kernel for blocks that one pass of the CTA
+// covers (rows <= 8 * UNR * 32 / cpr, a row's chunks <= 32): each CTA walks
+// the pairs t = blockIdx.x, + gridDim.x, ... and issues the block loads of
+// its next pair before it reduces and stores the current one, so that every
+// CTA keeps a block's worth of loads in flight.  x_j is staged in a
+// double-buffered shared vector.
+template <typename T, typename TS, int PH>
+__global__ void __launch_bounds__(256, sizeof(TS) == 2 ? 3 : 2)
+    pair_persist_kernel(int D, int R, int K, int64_t n, const int32_t* __restrict__ list,
+                        const int32_t* __restrict__ nj, const TS* __restrict__ Ahat, const T* __restrict__ xv,
+                        T* __restrict__ part) {
+  constexpr int VN = Chunk<TS>::VN;
+  constexpr int UNR = Unr<TS>::v;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int nr = (PH == PH_SR) ? K : R;
+  const int nc = (PH == PH_RS) ? K : R;
+  const int ncp = (nc + 3) & ~3;
+  T* sxb[2] = {reinterpret_cast<T*>(sm_raw), reinterpret_cast<T*>(sm_raw) + ncp};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nch = (nc + VN - 1) / VN;
+  int cpr = 32;
+  while (cpr > 1 && cpr / 2 >= nch) cpr >>= 1;
+  const int rpi = 32 / cpr, sub = lane / cpr, cl = lane & (cpr - 1);
+  const int c = cl * VN;
+  const bool chunk_ok = cl < nch;
+  const int lim = nc - c;
+  const int64_t off = (PH == PH_SR ? (int64_t)R * D : (PH == PH_RS ? R : 0));
+  int64_t t = blockIdx.x;
+  if (t >= n) return;
+  int64_t p = list ? list[t] : t;
+  uint4 raw[UNR];
+  auto issue = [&](int64_t pp) {
+    const TS* M = Ahat + pp * D * D + off;
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int r = (u * nw + warp) * rpi + sub;
+      raw[u] = (chunk_ok && r < nr) ? __ldg(reinterpret_cast<const uint4*>(M + (int64_t)r * D + c))
+                                    : make_uint4(0, 0, 0, 0);
+    }
+  };
+  issue(p);
+  griddep_wait();
+  griddep_launch_next();
+  int buf = 0;
+  while (true) {
+    const int j = nj[p];
+    T* sx = sxb[buf];
+    const T* x = (PH == PH_RS) ? xv + (int64_t)(j >> 1) * 2 * K + (j & 1) * K : xv + (int64_t)j * R;
+    for (int e = threadIdx.x; e < nc; e += blockDim.x) sx[e] = x[e];
+    __syncthreads();
+    T acc[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) acc[u] = T(0);
+    if (chunk_ok) {
+      T xvv[VN];
+#pragma unroll
+      for (int e = 0; e < VN; ++e) xvv[e] = (e < lim) ? sx[c + e] : T(0);
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        T v[VN];
+        Chunk<TS>::cvt(raw[u], v);
+        if (lim < VN) {
+#pragma unroll
+          for (int e = 0; e < VN; ++e) v[e] = (e < lim) ? v[e] : T(0);
+        }
+#pragma unroll
+        for (int e = 0; e < VN; ++e) acc[u] = fma(v[e], xvv[e], acc[u]);
+      }
+    }
+    // the next pair's loads go out before this pair's reduction and stores
+    const int64_t tn = t + gridDim.x;
+    int64_t pn = -1;
+    if (tn < n) {
+      pn = list ? list[tn] : tn;
+      issue(pn);
+    }
+    T* out = part + p * nr;
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      for (int o = cpr >> 1; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+      const int r = (u * nw + warp) * rpi + sub;
+      if (cl == 0 && r < nr) out[r] = acc[u];
+    }
+    if (tn >= n) break;
+    t = tn, p = pn, buf ^= 1;
+  }
+}
+
+// TMA-fed form for 16-bit blocks: a persistent CTA keeps kPairStages tiles
+// (the quadrant of s * Ahat_ij, nr x nc, dense row-major) in flight in a
+// shared-memory ring; thread 0 issues one 2-D tensor copy per tile.  A tile
+// is consumed as in the register form (cpr lanes per row, 16-byte chunks)
+// with this lane's x_j chunk in registers, then its stage is refilled with
+// the tile kPairStages pairs ahead.  Waits are bounded (2 s); on expiry
+// every thread leaves together, thread 0 having waited (bounded) for the
+// copies still in flight and set *err.
+constexpr int kPairStages = 3;
+constexpr unsigned long long kPairTimeoutNs = 2000000000ull;
+
+template <typename TS, int PH>
+__global__ void __launch_bounds__(256, 2)
+    pair_tma_kernel(const __grid_constant__ CUtensorMap tm, int D, int R, int K, int64_t n,
+                    const int32_t* __restrict__ list, const int32_t* __restrict__ nj, const float* __restrict__ xv,
+                    float* __restrict__ part, int32_t* __restrict__ err) {
+  constexpr int VN = 8;
+  constexpr int UNR = 8;  // rows per lane: nr <= 8 warps * UNR * (32 / cpr)
+  extern __shared__ __align__(128) unsigned char sm_dyn[];
+  __shared__ __align__(8) uint64_t full[kPairStages];
+  const int nr = (PH == PH_SR) ? K : R;
+  const int nc = (PH == PH_RS) ? K : R;
+  const uint32_t tile_bytes = (uint32_t)nr * nc * 2;
+  const uint32_t stage_stride = (tile_bytes + 127u) & ~127u;
+  // tensor copies need 128-byte aligned destinations: the ring starts at the
+  // first such address (the launch adds 128 bytes of room)
+  unsigned char* sm_raw = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
+  if (smem_u32(sm_raw) & 127u) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
+  const int row_off = (PH == PH_SR) ? R : 0, col_off = (PH == PH_RS) ? R : 0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int nch = nc / VN;
+  int cpr = 32;
+  while (cpr > 1 && cpr / 2 >= nch) cpr >>= 1;
+  const int rpi = 32 / cpr, sub = lane / cpr, cl = lane & (cpr - 1);
+  const int64_t G = gridDim.x;
+  if (tid == 0) {
+    for (int s = 0; s < kPairStages; ++s) mbar_init(&full[s], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int s, int64_t t) {
+    const int64_t p = list ? list[t] : t;
+    mbar_expect_tx(&full[s], tile_bytes);
+    tma_load_2d(sm_raw + s * stage_stride, &tm, &full[s], col_off, (int)(p * D + row_off));
+  };
+  if (tid == 0)
+    for (int s = 0; s < kPairStages; ++s)
+      if (blockIdx.x + s * G < n) issue(s, blockIdx.x + s * G);
+  // x_j of a pair: this lane's 8-entry chunk, in registers
+  auto load_x = [&](int j, float (&xr)[VN]) {
+    const float* x = (PH == PH_RS) ? xv + (int64_t)(j >> 1) * 2 * K + (j & 1) * K : xv + (int64_t)j * R;
+    if (cl < nch) {
+      const float4 a = *reinterpret_cast<const float4*>(x + cl * VN);
+      const float4 b = *reinterpret_cast<const float4*>(x + cl * VN + 4);
+      xr[0] = a.x, xr[1] = a.y, xr[2] = a.z, xr[3] = a.w, xr[4] = b.x, xr[5] = b.y, xr[6] = b.z, xr[7] = b.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < VN; ++e) xr[e] = 0.0f;
+    }
+  };
+  // a pair's x_j is loaded one pair ahead of its use and the pair indices
+  // two pairs ahead, so that no dependent load sits between two tiles
+  int64_t t = blockIdx.x;
+  int64_t p = list ? list[t] : t;
+  int j = nj[p];
+  int64_t p1 = -1;
+  int j1 = 0;
+  if (t + G < n) p1 = list ? list[t + G] : t + G, j1 = nj[p1];
+  griddep_wait();
+  griddep_launch_next();
+  float xr[VN];
+  load_x(j, xr);
+  for (int it = 0; t < n; t += G, ++it) {
+    const int s = it % kPairStages;
+    int64_t p2 = -1;
+    int j2 = 0;
+    if (t + 2 * G < n) p2 = list ? list[t + 2 * G] : t + 2 * G, j2 = nj[p2];
+    const bool ok = mbar_wait(&full[s], (uint32_t)(it / kPairStages) & 1u, kPairTimeoutNs);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(err, 1);
+        // copies issued for this and the next stages may still be in flight
+        for (int k = 0; k < kPairStages; ++k) {
+          const int64_t tk = t + k * G;
+          if (tk < n) mbar_wait(&full[(it + k) % kPairStages], (uint32_t)((it + k) / kPairStages) & 1u, kPairTimeoutNs);
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    const unsigned char* tile = sm_raw + s * stage_stride;
+    float acc[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      acc[u] = 0.0f;
+      const int r = (u * nw + warp) * rpi + sub;
+      if (r < nr && cl < nch) {
+        const uint4 v4 = *reinterpret_cast<const uint4*>(tile + ((size_t)r * nc + cl * VN) * 2);
+        float v[VN];
+        Chunk<TS>::cvt(v4, v);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) acc[u] = fmaf(v[e], xr[e], acc[u]);
+      }
+    }
+    __syncthreads();  // every thread is done with stage s
+    if (tid == 0 && t + kPairStages * G < n) issue(s, t + kPairStages * G);
+    if (p1 >= 0) load_x(j1, xr);  // the next pair's x_j, before this pair's reduction
+    float* out = part + p * nr;
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      for (int o = cpr >> 1; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+      const int r = (u * nw + warp) * rpi + sub;
+      if (cl == 0 && r < nr) out[r] = acc[u];
+    }
+    p = p1, j = j1, p1 = p2, j1 = j2;
+  }
+}
+
+
 // The per-box kernels below split a box's output rows over ns CTAs
 // (grid = nb * ns; CTA b takes box b / ns and row slice b % ns), so that a
 // level with few boxes still spreads its rows over the GPU.
@@ -691,14 +902,19 @@ static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, si
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-// row slices per box: enough CTAs for two per SM, at least 32 rows each
-static int row_splits(int nb, int nrows) {
+static int num_sms() {
   static int nsm = 0;
   if (!nsm) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 152;
   }
+  return nsm;
+}
+
+// row slices per box: enough CTAs for two per SM, at least 32 rows each
+static int row_splits(int nb, int nrows) {
+  const int nsm = num_sms();
   if (nb <= 0) return 1;
   int ns = (2 * nsm + nb - 1) / nb;
   ns = std::min(ns, std::max(1, nrows / 32));
@@ -706,10 +922,41 @@ static int row_splits(int nb, int nrows) {
 }
 
 template <typename T, typename TS, int PH>
-static void launch_pairs(const DevLevel& L, const int32_t* list, int64_t n, const TS* Ahat, const T* xv, T* part,
-                         cudaStream_t st) {
+static void launch_pairs(const DevLevel& L, const FacLevel<T>& F, const int32_t* list, int64_t n, const TS* Ahat,
+                         const T* xv, T* part, cudaStream_t st) {
   if (n <= 0) return;
+  const int nr = (PH == PH_SR) ? L.K : L.R;
   const int nc = (PH == PH_RS) ? L.K : L.R;
+  if constexpr (sizeof(TS) == 2 && std::is_same<T, float>::value) {
+    if (F.tma) {
+      const CUtensorMap& tm = (PH == PH_RR) ? F.tm_rr : (PH == PH_SR ? F.tm_sr : F.tm_rs);
+      const size_t stage = ((size_t)nr * nc * 2 + 127) & ~(size_t)127;
+      const size_t sm = kPairStages * stage + 128;  // + room to align the ring
+      const int64_t grid = std::min<int64_t>(n, 2 * (int64_t)num_sms());
+      set_smem((const void*)pair_tma_kernel<TS, PH>, sm);
+      launch_pdl(pair_tma_kernel<TS, PH>, (unsigned)grid, 256, sm, st, tm, L.D, L.R, L.K, n, list, L.near_j,
+                 reinterpret_cast<const float*>(xv), reinterpret_cast<float*>(part), F.err);
+      return;
+    }
+  }
+  // the persistent form when one pass covers the block and its rows load as
+  // aligned 16-byte chunks
+  constexpr int VN = Chunk<TS>::VN;
+  const int nch = (nc + VN - 1) / VN;
+  int cpr = 32;
+  while (cpr > 1 && cpr / 2 >= nch) cpr >>= 1;
+  const int64_t off = (PH == PH_SR ? (int64_t)L.R * L.D : (PH == PH_RS ? L.R : 0));
+  const bool aligned = ((L.D * sizeof(TS)) % 16 == 0) && ((off * (int64_t)sizeof(TS)) % 16 == 0) &&
+                       ((reinterpret_cast<uintptr_t>(Ahat) & 15) == 0);
+  if (aligned && nch <= 32 && nr <= 8 * Unr<TS>::v * (32 / cpr) && nc > 0) {
+    const int per_sm = sizeof(TS) == 2 ? 3 : 2;
+    const int64_t grid = std::min<int64_t>(n, (int64_t)per_sm * num_sms());
+    const size_t sm = sizeof(T) * 2 * (size_t)((nc + 3) & ~3);
+    set_smem((const void*)pair_persist_kernel<T, TS, PH>, sm);
+    launch_pdl(pair_persist_kernel<T, TS, PH>, (unsigned)grid, 256, sm, st, L.D, L.R, L.K, n, list, L.near_j, Ahat,
+               xv, part);
+    return;
+  }
   const size_t sm = sizeof(T) * (size_t)std::max(nc, 1);
   set_smem((const void*)pair_kernel<T, TS, PH>, sm);
   launch_pdl(pair_kernel<T, TS, PH>, (unsigned)n, 256, sm, st, L.D, L.R, L.K, list, L.near_j, Ahat, xv, part);
@@ -726,7 +973,7 @@ void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStr
 template <typename T, typename TS>
 void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, cudaStream_t st) {
   if (L.R == 0) return;
-  launch_pairs<T, TS, PH_RR>(L, L.lo_pairs, L.n_lo, Ahat, F.u, F.part, st);
+  launch_pairs<T, TS, PH_RR>(L, F, L.lo_pairs, L.n_lo, Ahat, F.u, F.part, st);
   const int ns = row_splits(L.nb, L.R);
   launch_pdl(fwd2_kernel<T>, L.nb * ns, 256, sizeof(T) * L.R, st, L.D, L.R, ns, L.near_ptr, L.lo_cnt, iscale, F.Ainv,
              F.c, F.part, F.v);
@@ -735,14 +982,14 @@ template <typename T, typename TS>
 void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, T* parent_vin,
                  cudaStream_t st) {
   if (L.K == 0) return;
-  launch_pairs<T, TS, PH_SR>(L, nullptr, L.NP, Ahat, F.v, F.part, st);
+  launch_pairs<T, TS, PH_SR>(L, F, nullptr, L.NP, Ahat, F.v, F.part, st);
   launch_pdl(fwd3_kernel<T>, L.nb, 128, 0, st, L.D, L.R, L.K, L.near_ptr, iscale, F.c, F.part, parent_vin);
 }
 template <typename T, typename TS>
 void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
                  cudaStream_t st) {
   if (L.R == 0) return;
-  launch_pairs<T, TS, PH_RS>(L, nullptr, L.NP, Ahat, parent_x, F.part, st);
+  launch_pairs<T, TS, PH_RS>(L, F, nullptr, L.NP, Ahat, parent_x, F.part, st);
   const int ns = row_splits(L.nb, L.R);
   launch_pdl(bwd1_kernel<T>, L.nb * ns, 256, sizeof(T) * L.R, st, L.R, ns, L.near_ptr, iscale, F.Ainv, F.v, F.part,
              F.om);
@@ -751,7 +998,7 @@ template <typename T, typename TS>
 void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
                  cudaStream_t st) {
   const int ns = row_splits(L.nb, std::max(L.R, 1));
-  if (L.R > 0) launch_pairs<T, TS, PH_RR>(L, L.hi_pairs, L.n_hi, Ahat, F.om, F.part, st);
+  if (L.R > 0) launch_pairs<T, TS, PH_RR>(L, F, L.hi_pairs, L.n_hi, Ahat, F.om, F.part, st);
   launch_pdl(bwd2_kernel<T>, L.nb * ns, 256, sizeof(T) * std::max(L.R, 1), st, L.D, L.R, L.K, ns, L.near_ptr,
              L.hi_cnt, iscale, F.Ainv, F.om, parent_x, F.part, F.z);
   const int nx = row_splits(L.nb, L.D);
