@@ -451,7 +451,11 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       bool ok = gemm_tc(bf16, D, D, D, A16, d.NP, D, D, nullptr, f.U16, d.nb, D, D, d.near_j, F.W16, DD, nullptr, D,
                         1, bf16, 1.0f, nullptr, d.NP, c->status + 2, st) &&
                 gemm_tc(bf16, D, D, D, f.U16, d.nb, D, D, d.near_i, F.W16, d.NP, D, D, nullptr, f.Ahat, DD, nullptr, D,
-                        0, 0, 1.0f, sc + 1, d.NP, c->status + 2, st, sub16 ? f.Ahat16 : nullptr);
+                        0, 0, 1.0f, sc + 1, d.NP, c->status + 2, st, sub16 ? f.Ahat16 : nullptr,
+                        sub16 ? R : -1, d.near_i, d.near_j);
+      // off-diagonal pairs then keep only SS in FP32 (the merge's input);
+      // their RR, RS and SR live in the 16-bit copy (the substitution's)
+      f.ahat_ss_only = sub16 && R % 16 == 0;
       if (!ok) {
         c->err = "tensor-core GEMM setup failed at level " + std::to_string(l);
         return H2_ERR_CUDA;
@@ -695,6 +699,40 @@ h2_status subst_check(h2_ctx* c) {
   if (w != 0) {
     c->err = "a substitution kernel's wait for its tensor copies timed out";
     return H2_ERR_TIMEOUT;
+  }
+  return H2_OK;
+}
+
+// Fill the RR, RS and SR quadrants of the off-diagonal pairs of an exported
+// mixed-precision Ahat (host, FP32) from the 16-bit copy.
+h2_status export_ahat_quadrants(const h2_ctx* c, int level, float* out) {
+  const FacLevel<float>& f = c->f32.lv[level];
+  const DevLevel& d = c->lv[level];
+  const size_t D = d.D, R = d.R, n = (size_t)d.NP * D * D;
+  std::vector<uint16_t> h(n);
+  float isc = 1.0f;
+  if (cudaMemcpy(h.data(), f.Ahat16, n * 2, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&isc, f.ahat_isc, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return H2_ERR_CUDA;
+  const bool bf = c->f32.bf16 == 1;
+  for (int64_t q = 0; q < d.NP; ++q) {
+    if (d.h_near_i[q] == d.h_near_j[q]) continue;
+    for (size_t r = 0; r < D; ++r)
+      for (size_t col = 0; col < D; ++col) {
+        if (r >= R && col >= R) continue;
+        const size_t e = (size_t)q * D * D + r * D + col;
+        float v;
+        if (bf) {
+          __nv_bfloat16_raw raw;
+          raw.x = h[e];
+          v = __bfloat162float(__nv_bfloat16(raw));
+        } else {
+          __half_raw raw;
+          raw.x = h[e];
+          v = __half2float(__half(raw));
+        }
+        out[e] = v * isc;
+      }
   }
   return H2_OK;
 }
@@ -1345,6 +1383,9 @@ h2_status h2_export(const h2_ctx* c, const char* name, int32_t level, void* dst,
     if (!src) return H2_ERR_STATE;
     if (cap_bytes < cnt * es) return H2_ERR_INVALID_ARG;
     if (cudaMemcpy(dst, src, cnt * es, cudaMemcpyDeviceToHost) != cudaSuccess) return H2_ERR_CUDA;
+    // mixed levels whose off-diagonal pairs keep only SS in FP32: the other
+    // quadrants come from the 16-bit copy s * Ahat, times 1 / s
+    if (n == "Ahat" && !f64 && c->f32.lv[level].ahat_ss_only) return export_ahat_quadrants(c, level, (float*)dst);
   }
   return H2_OK;
 }

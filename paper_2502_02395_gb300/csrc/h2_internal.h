@@ -160,6 +160,7 @@ struct FacLevel {
   // level keeps the substitution on the FP32 Ahat.
   void* Ahat16 = nullptr;
   const float* ahat_isc = nullptr;
+  bool ahat_ss_only = false;  // FP32 Ahat of off-diagonal pairs holds only the SS quadrant
   // tensor maps over Ahat16 (rows NP * D, cols D) with the RR, SR and RS
   // quadrants as tiles, for the TMA-fed pair kernels; tma is false where
   // the shapes do not allow them

@@ -43,7 +43,8 @@ bool gemm_tc_supported(int M, int N, int K, int lda, int ldb, int ldc);
 bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int rowsA, int lda, const int32_t* ia,
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
-             int64_t batch, int32_t* err, cudaStream_t st, void* C2 = nullptr);
+             int64_t batch, int32_t* err, cudaStream_t st, void* C2 = nullptr, int qsplit = -1,
+             const int32_t* qi = nullptr, const int32_t* qj = nullptr);
 // 2-D tensor map over a rows x cols 16-bit array (row stride ld elements)
 // with box_rows x box_cols tiles, no swizzle (dense row-major tiles in
 // shared memory).  False if the driver or the shape does not allow it.

@@ -657,7 +657,12 @@ __global__ void __launch_bounds__(256, 2)
     int64_t p2 = -1;
     int j2 = 0;
     if (t + 2 * G < n) p2 = list ? list[t + 2 * G] : t + 2 * G, j2 = nj[p2];
-    const bool ok = mbar_wait(&full[s], (uint32_t)(it / kPairStages) & 1u, kPairTimeoutNs);
+    // thread 0 waits (bounded) while the others sit at the barrier; then
+    // every thread observes the completed phase itself (one poll) before
+    // it reads the tile
+    const uint32_t par = (uint32_t)(it / kPairStages) & 1u;
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait(&full[s], par, kPairTimeoutNs);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicExch(err, 1);
@@ -670,6 +675,9 @@ __global__ void __launch_bounds__(256, 2)
       __syncthreads();
       return;
     }
+    // (the phase stays complete until thread 0 re-arms the stage after the
+    // next barrier, so this poll succeeds at once)
+    if (!mbar_test(&full[s], par)) mbar_wait(&full[s], par, kPairTimeoutNs);
     const unsigned char* tile = sm_raw + s * stage_stride;
     float acc[UNR];
 #pragma unroll

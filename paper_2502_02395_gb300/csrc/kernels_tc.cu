@@ -79,6 +79,13 @@ struct TcArgs {
   uint32_t tmem_cols;
   void* C2;  // optional second output for out_mode 0: 16-bit copy of the raw accumulator (row-major, ldc)
   int c2_bf16;
+  // Quadrant split (out_mode 0 with C2): rows and columns >= qsplit form the
+  // SS quadrant.  For a batch entry whose pair (qi[b], qj[b]) is off the
+  // diagonal, the FP32 output keeps only SS and C2 everything but SS; a
+  // diagonal entry gets the full FP32 output.  qsplit < 0: no split.
+  int qsplit;
+  const int32_t* qi;
+  const int32_t* qj;
 };
 
 __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -180,6 +187,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     char* Cb = reinterpret_cast<char*>(p.C);
     const int64_t cbase = (int64_t)(p.ic ? p.ic[b] : (int)b) * p.sC;
+    const bool split = p.qsplit >= 0 && p.qi[b] != p.qj[b];
     for (int n0 = 0; n0 < p.N; n0 += 16) {
       uint32_t r[16];
       asm volatile(
@@ -190,14 +198,17 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       if (!ok || m >= p.M) continue;
       if (p.out_mode == 0) {
-        float* out = reinterpret_cast<float*>(Cb) + cbase + (int64_t)m * p.ldc + n0;
+        const bool ss = (m >= p.qsplit) && (n0 >= p.qsplit);
+        if (!split || ss) {
+          float* out = reinterpret_cast<float*>(Cb) + cbase + (int64_t)m * p.ldc + n0;
 #pragma unroll
-        for (int j = 0; j < 16; j += 4) {
-          float4 v = make_float4(__uint_as_float(r[j]) * alpha, __uint_as_float(r[j + 1]) * alpha,
-                                 __uint_as_float(r[j + 2]) * alpha, __uint_as_float(r[j + 3]) * alpha);
-          *reinterpret_cast<float4*>(out + j) = v;
+          for (int j = 0; j < 16; j += 4) {
+            float4 v = make_float4(__uint_as_float(r[j]) * alpha, __uint_as_float(r[j + 1]) * alpha,
+                                   __uint_as_float(r[j + 2]) * alpha, __uint_as_float(r[j + 3]) * alpha);
+            *reinterpret_cast<float4*>(out + j) = v;
+          }
         }
-        if (p.C2) {
+        if (p.C2 && !(p.qsplit >= 0 && ss)) {
           uint32_t h[8];
 #pragma unroll
           for (int j = 0; j < 16; j += 2) {
@@ -303,7 +314,8 @@ bool gemm_tc_supported(int M, int N, int K, int lda, int ldb, int ldc) {
 bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int rowsA, int lda, const int32_t* ia,
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
-             int64_t batch, int32_t* err, cudaStream_t st, void* C2) {
+             int64_t batch, int32_t* err, cudaStream_t st, void* C2, int qsplit, const int32_t* qi,
+             const int32_t* qj) {
   if (batch == 0) return true;
   if (!gemm_tc_supported(M, N, K, lda, ldb, ldc)) return false;
   if ((uint64_t)nA * rowsA >= (1ull << 31) || (uint64_t)nB * rowsB >= (1ull << 31)) return false;
@@ -330,6 +342,12 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
   p.ab_bf16 = ab_bf16;
   p.C2 = (out_mode == 0) ? C2 : nullptr;
   p.c2_bf16 = ab_bf16;
+  // the split needs the pair lists, a 16-bit copy and quadrant edges on the
+  // epilogue's 16-column chunks
+  const bool split = p.C2 && qsplit >= 0 && qsplit % 16 == 0 && qi && qj;
+  p.qsplit = split ? qsplit : -1;
+  p.qi = split ? qi : nullptr;
+  p.qj = split ? qj : nullptr;
   uint32_t cols = 32;
   while (cols < (uint32_t)N) cols <<= 1;
   p.tmem_cols = cols;

@@ -25,10 +25,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 // Wait for the phase of the given parity; false once timeout_ns of global
-// time have passed.
+// time have passed.  The timer is first read after 1024 unsuccessful polls
+// (and then every 1024), so a wait that succeeds early never touches it.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long timeout_ns) {
   const uint32_t addr = smem_u32(bar);
-  const unsigned long long t0 = global_ns();
+  unsigned long long t0 = 0;
   for (uint32_t it = 0;; ++it) {
     uint32_t done;
     asm volatile(
@@ -39,8 +40,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 255u) == 255u && global_ns() - t0 > timeout_ns) return false;
+    if ((it & 1023u) == 1023u) {
+      const unsigned long long t = global_ns();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > timeout_ns) return false;
+    }
   }
+}
+// One poll of the phase of the given parity (true once it has completed).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
 }
 // 2-D tiled tensor copy global -> shared, completing on an mbarrier.  c0 is
 // the inner (column) coordinate, c1 the row.
