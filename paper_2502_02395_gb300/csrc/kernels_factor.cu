@@ -148,11 +148,179 @@ gemm_batched_kernel(int M, int N, int K, const T* __restrict__ A, int64_t sA, co
   }
 }
 
+// FP32 form for tile-sized problems: 128 x 128 tiles, BK = 8, 256 threads
+// each holding an 8 x 8 block of C (rows ty*4 + {0..3, 64..67}, columns
+// tx*4 + {0..3, 64..67}) so that every shared-memory read is a 16-byte
+// vector; the next k-slice is fetched into registers while the current one
+// is used, and two shared buffers leave one barrier per slice.
+constexpr int G2_BM = 128, G2_BN = 128, G2_BK = 8, G2_LD = 132;
+
+__device__ __forceinline__ void g2_load_a(const float* __restrict__ Ab, int lda, int tA, int M, int K, int m0, int k0,
+                                          bool vec, float (&ra)[4]) {
+  const int t = threadIdx.x;
+  if (!tA) {  // A[m * lda + k]: 4 consecutive k of row m
+    const int m = m0 + (t >> 1), k = k0 + (t & 1) * 4;
+    if (vec && m < M && k + 3 < K) {
+      const float4 v = *reinterpret_cast<const float4*>(Ab + (int64_t)m * lda + k);
+      ra[0] = v.x, ra[1] = v.y, ra[2] = v.z, ra[3] = v.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) ra[e] = (m < M && k + e < K) ? Ab[(int64_t)m * lda + k + e] : 0.0f;
+    }
+  } else {  // A[k * lda + m]: 4 consecutive m of row k
+    const int k = k0 + (t >> 5), m = m0 + (t & 31) * 4;
+    if (vec && k < K && m + 3 < M) {
+      const float4 v = *reinterpret_cast<const float4*>(Ab + (int64_t)k * lda + m);
+      ra[0] = v.x, ra[1] = v.y, ra[2] = v.z, ra[3] = v.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) ra[e] = (k < K && m + e < M) ? Ab[(int64_t)k * lda + m + e] : 0.0f;
+    }
+  }
+}
+__device__ __forceinline__ void g2_store_a(float (*As)[G2_LD], int tA, const float (&ra)[4]) {
+  const int t = threadIdx.x;
+  if (!tA) {
+    const int m = t >> 1, k = (t & 1) * 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) As[k + e][m] = ra[e];
+  } else {
+    const int k = t >> 5, m = (t & 31) * 4;
+    *reinterpret_cast<float4*>(&As[k][m]) = make_float4(ra[0], ra[1], ra[2], ra[3]);
+  }
+}
+
+template <typename TB>
+__global__ void __launch_bounds__(256)
+gemm_f32_tile_kernel(int M, int N, int K, const float* __restrict__ A, int64_t sA, const int32_t* __restrict__ ia,
+                     int lda, int tA, const TB* __restrict__ B, int64_t sB, const int32_t* __restrict__ ib, int ldb,
+                     int tB, float* __restrict__ C, int64_t sC, const int32_t* __restrict__ ic, int ldc, float alpha,
+                     float beta, int64_t batch, int vecA, int vecB, int vecC) {
+  __shared__ __align__(16) float As[2][G2_BK][G2_LD];
+  __shared__ __align__(16) float Bs[2][G2_BK][G2_LD];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int m0 = blockIdx.y * G2_BM, n0 = blockIdx.x * G2_BN;
+  for (int64_t b = blockIdx.z; b < batch; b += gridDim.z) {
+    const float* Ab = A + (ia ? (int64_t)ia[b] : b) * sA;
+    const TB* Bb = B + (ib ? (int64_t)ib[b] : b) * sB;
+    float* Cb = C + (ic ? (int64_t)ic[b] : b) * sC;
+    // op(B)(k, n) tile: B[k * ldb + n] (!tB) or B[n * ldb + k] (tB), stored as
+    // Bs[k][n]; the same code as A with the roles of m and n exchanged
+    auto load_b = [&](int k0, float (&rb)[4]) {
+      if (tB) {  // B[n * ldb + k]: 4 consecutive k of row n
+        const int n = n0 + (t >> 1), k = k0 + (t & 1) * 4;
+        if (vecB && n < N && k + 3 < K) {
+          const float4 v = *reinterpret_cast<const float4*>(Bb + (int64_t)n * ldb + k);
+          rb[0] = v.x, rb[1] = v.y, rb[2] = v.z, rb[3] = v.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) rb[e] = (n < N && k + e < K) ? (float)Bb[(int64_t)n * ldb + k + e] : 0.0f;
+        }
+      } else {  // B[k * ldb + n]: 4 consecutive n of row k
+        const int k = k0 + (t >> 5), n = n0 + (t & 31) * 4;
+        if (vecB && k < K && n + 3 < N) {
+          const float4 v = *reinterpret_cast<const float4*>(Bb + (int64_t)k * ldb + n);
+          rb[0] = v.x, rb[1] = v.y, rb[2] = v.z, rb[3] = v.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) rb[e] = (k < K && n + e < N) ? (float)Bb[(int64_t)k * ldb + n + e] : 0.0f;
+        }
+      }
+    };
+    auto store_b = [&](float (*Bsb)[G2_LD], const float (&rb)[4]) {
+      if (tB) {
+        const int n = t >> 1, k = (t & 1) * 4;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) Bsb[k + e][n] = rb[e];
+      } else {
+        const int k = t >> 5, n = (t & 31) * 4;
+        *reinterpret_cast<float4*>(&Bsb[k][n]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+      }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    float ra[4], rb[4];
+    g2_load_a(Ab, lda, tA, M, K, m0, 0, vecA, ra);
+    load_b(0, rb);
+    g2_store_a(As[0], tA, ra);
+    store_b(Bs[0], rb);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += G2_BK) {
+      const bool more = k0 + G2_BK < K;
+      if (more) {
+        g2_load_a(Ab, lda, tA, M, K, m0, k0 + G2_BK, vecA, ra);
+        load_b(k0 + G2_BK, rb);
+      }
+#pragma unroll
+      for (int kk = 0; kk < G2_BK; ++kk) {
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + 64]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4 + 64]);
+        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      }
+      if (more) {
+        g2_store_a(As[buf ^ 1], tA, ra);
+        store_b(Bs[buf ^ 1], rb);
+      }
+      __syncthreads();
+      buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int m = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;
+      if (m >= M) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int n = n0 + tx * 4 + h * 64;
+        float* cp = Cb + (int64_t)m * ldc + n;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = alpha * acc[i][h * 4 + e];
+        if (vecC && n + 3 < N) {
+          if (beta != 0.0f) {
+            const float4 o = *reinterpret_cast<const float4*>(cp);
+            v[0] = fmaf(beta, o.x, v[0]), v[1] = fmaf(beta, o.y, v[1]), v[2] = fmaf(beta, o.z, v[2]),
+            v[3] = fmaf(beta, o.w, v[3]);
+          }
+          *reinterpret_cast<float4*>(cp) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (n + e < N) cp[e] = (beta != 0.0f) ? fmaf(beta, cp[e], v[e]) : v[e];
+        }
+      }
+    }
+  }
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 template <typename T, typename TB>
 void gemm_simt(int M, int N, int K, const T* A, int64_t sA, const int32_t* ia, int lda, bool tA, const TB* B,
                int64_t sB, const int32_t* ib, int ldb, bool tB, T* C, int64_t sC, const int32_t* ic, int ldc,
                T alpha, T beta, int64_t batch, cudaStream_t st) {
   if (batch == 0 || M == 0 || N == 0) return;
+  if constexpr (std::is_same<T, float>::value && std::is_same<TB, float>::value) {
+    // 16-byte vector access needs 4-element strides and aligned bases
+    const int vecA = (lda % 4 == 0) && (sA % 4 == 0) && aligned16(A);
+    const int vecB = (ldb % 4 == 0) && (sB % 4 == 0) && aligned16(B);
+    const int vecC = (ldc % 4 == 0) && (sC % 4 == 0) && aligned16(C);
+    dim3 g2((N + G2_BN - 1) / G2_BN, (M + G2_BM - 1) / G2_BM, (unsigned)std::min<int64_t>(batch, 65535));
+    ++g_launches;
+    gemm_f32_tile_kernel<float><<<g2, 256, 0, st>>>(M, N, K, A, sA, ia, lda, tA, B, sB, ib, ldb, tB, C, sC, ic, ldc,
+                                                    alpha, beta, batch, vecA, vecB, vecC);
+    return;
+  }
   dim3 grid((N + 63) / 64, (M + 63) / 64, (unsigned)std::min<int64_t>(batch, 65535));
   ++g_launches;
   gemm_batched_kernel<T, TB><<<grid, 256, 0, st>>>(M, N, K, A, sA, ia, lda, tA, B, sB, ib, ldb, tB, C, sC, ic, ldc,
@@ -276,14 +444,16 @@ __global__ void __launch_bounds__(512) qr_panel_kernel(int D, int K, const T* __
 
 // Tw (row-major K x K, upper): for i = 0..K-1:
 //   Tw[0:i, i] = -tau_i Tw[0:i, 0:i] S[0:i, i];  Tw[i, i] = tau_i
-// S = V^T V (row-major K x K per box).
+// S = V^T V (row-major K x K per box).  Step i: warp w computes the rows
+// r = w, w + nwarps, ... of the new column, its lanes splitting the dot
+// product over c in [r, i) (Tw is upper triangular).
 template <typename T>
 __global__ void __launch_bounds__(256) wy_tfactor_kernel(int K, const T* __restrict__ S, const T* __restrict__ tau,
                                                          T* __restrict__ Tw) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Ts = reinterpret_cast<T*>(smraw);  // K x K row-major
   T* w = Ts + K * K;                    // K
-  const int box = blockIdx.x, tid = threadIdx.x;
+  const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const T* Sb = S + (size_t)box * K * K;
   const T* tb = tau + (size_t)box * K;
   for (int e = tid; e < K * K; e += blockDim.x) Ts[e] = T(0);
@@ -292,16 +462,101 @@ __global__ void __launch_bounds__(256) wy_tfactor_kernel(int K, const T* __restr
     for (int r = tid; r < i; r += blockDim.x) w[r] = Sb[r * K + i];
     __syncthreads();
     const T ti = tb[i];
-    for (int r = tid; r < i; r += blockDim.x) {
+    for (int r = warp; r < i; r += nw) {
       T sacc = T(0);
-      for (int c = r; c < i; ++c) sacc += Ts[r * K + c] * w[c];
-      Ts[r * K + i] = -ti * sacc;
+      for (int c = r + lane; c < i; c += 32) sacc += Ts[r * K + c] * w[c];
+      for (int o = 16; o; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) Ts[r * K + i] = -ti * sacc;
     }
     if (tid == 0) Ts[i * K + i] = ti;
     __syncthreads();
   }
   T* out = Tw + (size_t)box * K * K;
   for (int e = tid; e < K * K; e += blockDim.x) out[e] = Ts[e];
+}
+
+// The same factor from the identity Tw^-1 = striu(S) + diag(1 / tau) of the
+// compact WY form (tau_k = 0, a reflector equal to I, gives a zero row and
+// column k of Tw: M is made the identity there and Tw_kk set to 0).  M is
+// padded to Kp (a power of two, 8 <= Kp <= 128) with the identity and
+// inverted in shared memory by recursive 2 x 2 blocking: the 8 x 8
+// diagonal blocks by back substitution (one thread per column), then for
+// b = 16 .. Kp every diagonal block [T11 T12; 0 T22] gets
+// T12 = -T11 (M12 T22) from its two already inverted halves.
+template <typename T>
+__global__ void __launch_bounds__(256) wy_tinv_kernel(int K, int Kp, const T* __restrict__ S,
+                                                      const T* __restrict__ tau, T* __restrict__ Tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ld = Kp + 1;
+  T* Ms = reinterpret_cast<T*>(smraw);  // Kp x ld
+  T* Xs = Ms + (size_t)Kp * ld;           // Kp * Kp / 4 scratch
+  const int box = blockIdx.x, tid = threadIdx.x;
+  const T* Sb = S + (size_t)box * K * K;
+  const T* tb = tau + (size_t)box * K;
+  for (int e = tid; e < Kp * Kp; e += blockDim.x) {
+    const int r = e / Kp, c = e - r * Kp;
+    T v = T(0);
+    if (r >= K || c >= K) {
+      v = (r == c) ? T(1) : T(0);
+    } else {
+      const bool zr = tb[r] == T(0), zc = tb[c] == T(0);
+      if (r == c) v = zr ? T(1) : T(1) / tb[r];
+      else if (c > r && !zr && !zc) v = Sb[r * K + c];
+    }
+    Ms[r * ld + c] = v;
+  }
+  __syncthreads();
+  // 8 x 8 diagonal blocks: thread (q, j) solves M_qq x = e_j
+  {
+    const int nq = Kp / 8;
+    T x[8];
+    const int q = tid >> 3, j = tid & 7;
+    if (q < nq) {
+      const T* Mq = Ms + (size_t)(q * 8) * ld + q * 8;
+#pragma unroll
+      for (int i = 7; i >= 0; --i) {
+        T acc = (i == j) ? T(1) : T(0);
+#pragma unroll
+        for (int k = i + 1; k < 8; ++k) acc -= Mq[i * ld + k] * x[k];
+        x[i] = (i <= j) ? acc / Mq[i * ld + i] : T(0);
+      }
+    }
+    __syncthreads();
+    if (q < nq) {
+      T* Mq = Ms + (size_t)(q * 8) * ld + q * 8;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) Mq[i * ld + j] = x[i];
+    }
+    __syncthreads();
+  }
+  for (int b = 16; b <= Kp; b *= 2) {
+    const int h = b / 2, nb = Kp / b, hh = h * h;
+    // X_q = M12 T22 (T22 upper triangular)
+    for (int e = tid; e < nb * hh; e += blockDim.x) {
+      const int q = e / hh, rc = e - q * hh, r = rc / h, c = rc - r * h;
+      const T* M12 = Ms + (size_t)(q * b) * ld + q * b + h;
+      const T* T22 = Ms + (size_t)(q * b + h) * ld + q * b + h;
+      T acc = T(0);
+      for (int k = 0; k <= c; ++k) acc += M12[r * ld + k] * T22[k * ld + c];
+      Xs[e] = acc;
+    }
+    __syncthreads();
+    // T12 = -T11 X_q (T11 upper triangular), in place of M12
+    for (int e = tid; e < nb * hh; e += blockDim.x) {
+      const int q = e / hh, rc = e - q * hh, r = rc / h, c = rc - r * h;
+      const T* T11 = Ms + (size_t)(q * b) * ld + q * b;
+      const T* X = Xs + (size_t)q * hh;
+      T acc = T(0);
+      for (int k = r; k < h; ++k) acc += T11[r * ld + k] * X[k * h + c];
+      Ms[(size_t)(q * b + r) * ld + q * b + h + c] = -acc;
+    }
+    __syncthreads();
+  }
+  T* out = Tw + (size_t)box * K * K;
+  for (int e = tid; e < K * K; e += blockDim.x) {
+    const int r = e / K, c = e - r * K;
+    out[e] = (r == c && tb[r] == T(0)) ? T(0) : Ms[r * ld + c];
+  }
 }
 
 // U (column-major D x D): column c' holds e_{perm(c')}, perm(c') = K + c'
@@ -450,6 +705,15 @@ void launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm,
 template <typename T>
 void launch_wy_tfactor(int nb, int K, const T* S, const T* tau, T* Tw, cudaStream_t st) {
   if (nb == 0 || K == 0) return;
+  if (K <= 128) {
+    int Kp = 8;
+    while (Kp < K) Kp *= 2;
+    const size_t sm = sizeof(T) * ((size_t)Kp * (Kp + 1) + (size_t)Kp * Kp / 4);
+    if (sm > 48 * 1024) cudaFuncSetAttribute(wy_tinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    ++g_launches;
+    wy_tinv_kernel<T><<<nb, 256, sm, st>>>(K, Kp, S, tau, Tw);
+    return;
+  }
   const size_t sm = sizeof(T) * ((size_t)K * K + K);
   if (sm > 48 * 1024) cudaFuncSetAttribute(wy_tfactor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ++g_launches;
