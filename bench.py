@@ -227,6 +227,13 @@ def roofline_for(phase, stats, t_phase, calls, peaks, prec, tc, fp64_tf):
         peak = peaks.get("hbm_gbs", 6800.0)
         return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                 "traffic": None, "phase": phase, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    if phase == "solve_matvec" and prec != "fp64":
+        # the mixed refinement's residual: FP32-pair arithmetic on the FP32
+        # split of the FP64 matrix, 8 bytes per entry read
+        gbs = stats["bytes_matvec"] * calls["matvec"] / t_phase / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                "traffic": None, "phase": phase, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     if phase == "solve_matvec":
         # FP64 multiply-adds on the leaf near blocks: the FP64 ALU rate binds
         # before HBM on this part (2 flops per 8-byte entry)

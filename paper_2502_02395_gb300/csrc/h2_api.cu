@@ -229,17 +229,26 @@ h2_status setup_device(h2_ctx* c) {
   CKC(dalloc(c, &c->yhat32, c->hat_off[L + 1]));
   CKC(dalloc(c, &c->A32, (size_t)lf.NP * lf.D * lf.D));
   launch_convert<double, float>(c->A64, c->A32, (int64_t)lf.NP * lf.D * lf.D, 0);
+  CKC(dalloc(c, &c->Alo, (size_t)lf.NP * lf.D * lf.D));
+  launch_split_lo(c->A64, c->A32, c->Alo, (int64_t)lf.NP * lf.D * lf.D, 0);
   c->X64p.assign(L + 1, nullptr);
   c->S64p.assign(L + 1, nullptr);
   c->X32p.assign(L + 1, nullptr);
   c->S32p.assign(L + 1, nullptr);
+  c->Slo.assign(L + 1, nullptr);
   for (int l = 1; l <= L; ++l) {
     DevLevel& d = c->lv[l];
     const size_t nx = (size_t)d.nb * d.D * d.K, ns = (size_t)std::max<int64_t>(d.FP, 1) * d.K * d.K;
     CKC(dalloc(c, &d.X32, nx));
     CKC(dalloc(c, &d.S32, ns));
+    CKC(dalloc(c, &c->Slo[l], ns));
     launch_convert<double, float>(d.X, d.X32, (int64_t)nx, 0);
     launch_convert<double, float>(d.S, d.S32, (int64_t)ns, 0);
+    launch_split_lo(d.S, d.S32, c->Slo[l], (int64_t)d.FP * d.K * d.K, 0);
+    if (l == L) {
+      CKC(dalloc(c, &c->Xlo, nx));
+      launch_split_lo(d.X, d.X32, c->Xlo, (int64_t)nx, 0);
+    }
     c->X64p[l] = d.X;
     c->S64p[l] = d.S;
     c->X32p[l] = d.X32;
@@ -682,6 +691,24 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
 void matvec_impl(h2_ctx* c, const double* x, double* y) {
   matvec_t<double>(c, c->A64, c->X64p.data(), c->S64p.data(), c->xhat, c->yhat, x, y);
 }
+// The same product with the couplings and the leaf step in FP32-pair
+// arithmetic on the FP32 split of the FP64 matrix (about 2^-48 per entry);
+// the upward and downward passes stay FP64.
+void matvec_df(h2_ctx* c, const double* x, double* y) {
+  const int L = c->L;
+  cudaStream_t st = c->stream;
+  if (L == 0) {
+    launch_matvec_leaf_df(c->lv[0], c->A32, c->Alo, nullptr, nullptr, x, nullptr, y, st);
+    return;
+  }
+  const std::vector<int64_t>& off = c->hat_off;
+  launch_matvec_up<double>(c->lv[L], c->X64p[L], x, c->xhat + off[L], st);
+  for (int l = L - 1; l >= 1; --l) launch_matvec_up<double>(c->lv[l], c->X64p[l], c->xhat + off[l + 1], c->xhat + off[l], st);
+  for (int l = 1; l <= L; ++l)
+    launch_matvec_far_df(c->lv[l], c->S32p[l], c->Slo[l], c->xhat + off[l], c->yhat + off[l], st);
+  for (int l = 1; l < L; ++l) launch_matvec_down<double>(c->lv[l], c->X64p[l], c->yhat + off[l], c->yhat + off[l + 1], st);
+  launch_matvec_leaf_df(c->lv[L], c->A32, c->Alo, c->X32p[L], c->Xlo, x, c->yhat + off[L], y, st);
+}
 void matvec32(h2_ctx* c, const float* x, float* y, EventPairs* leaf_ev = nullptr) {
   matvec_t<float>(c, c->A32, c->X32p.data(), c->S32p.data(), c->xhat32, c->yhat32, x, y, leaf_ev);
 }
@@ -898,10 +925,15 @@ h2_status gmres_work(h2_ctx* c, GmresWork& W) {
 }
 
 // r = b - A_H2 x in FP64; returns ||r||
-h2_status fp64_residual(h2_ctx* c, SolveTimer& tm, double& rnorm) {
+// r = b - A_H2 x in FP64 and its norm; pairs: the matvec in FP32-pair
+// arithmetic (matvec_df) instead of FP64 instructions.
+h2_status fp64_residual(h2_ctx* c, SolveTimer& tm, double& rnorm, bool pairs = false) {
   const int64_t n = nslots(c);
   cudaStream_t st = c->stream;
-  tm.run(tm.mv, [&] { matvec_impl(c, c->x64, c->y64); });
+  tm.run(tm.mv, [&] {
+    if (pairs) matvec_df(c, c->x64, c->y64);
+    else matvec_impl(c, c->x64, c->y64);
+  });
   launch_residual(c->b64, c->y64, c->r64, n, st);
   launch_norm2<double>(c->r64, n, c->red + 600, st);
   double rn2 = 0;
@@ -966,7 +998,7 @@ h2_status nested_refine(h2_ctx* c, SolveTimer& tm, double bnorm, double target, 
     for (int i = 0; i < k; ++i) W.y[i] *= beta;
     CKC(cudaMemcpyAsync(W.yv, W.y.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
     launch_multi_axpy<float, double>(c->gm_Z32, n, k, W.yv, 1.0, c->x64, n, st);
-    CKS(fp64_residual(c, tm, beta));
+    CKS(fp64_residual(c, tm, beta, true));
     rel = beta / bnorm;
     c->times.history.push_back(rel);
     if (!std::isfinite(rel)) break;

@@ -221,6 +221,12 @@ struct h2_ctx {
   double* xhat = nullptr;  // matvec upward/downward scratch (sum over levels nb*K)
   double* yhat = nullptr;
   float* A32 = nullptr;    // FP32 copy of the leaf near blocks (inner solver)
+  // fl32(A64 - A32), and the same for the couplings and the leaf basis: with
+  // the FP32 copies, the FP64 matrix as FP32 pairs (the mixed refinement's
+  // residual)
+  float* Alo = nullptr;
+  float* Xlo = nullptr;      // leaf level
+  std::vector<float*> Slo;   // per level (index l; [0] unused)
   float *xhat32 = nullptr, *yhat32 = nullptr;
   std::vector<double*> X64p, S64p;  // per-level pointers (index l; [0] unused)
   std::vector<float*> X32p, S32p;

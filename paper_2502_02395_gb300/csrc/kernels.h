@@ -91,6 +91,13 @@ template <typename T>
 void launch_matvec_down(const DevLevel& L, const T* X, const T* yh, T* yh_child, cudaStream_t st);
 template <typename T>
 void launch_matvec_leaf(const DevLevel& L, const T* A, const T* X, const T* x, const T* yh, T* y, cudaStream_t st);
+// The FP64 matvec's far and leaf steps with each FP64 matrix held as an FP32
+// pair (hi = fl32, lo = fl32 of the rest) and FP32 pair arithmetic.
+void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const double* xh, double* yh,
+                          cudaStream_t st);
+void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, const float* Xh, const float* Xl,
+                           const double* x, const double* yh, double* y, cudaStream_t st);
+void launch_split_lo(const double* a, const float* hi, float* lo, int64_t n, cudaStream_t st);  // lo = fl32(a - hi)
 
 void launch_gather(const int64_t* slot, const double* src, double* dst, int64_t nslots, cudaStream_t st);
 void launch_scatter(const int64_t* slot, const double* src, double* dst, int64_t nslots, cudaStream_t st);

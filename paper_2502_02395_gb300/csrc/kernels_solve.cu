@@ -1200,6 +1200,180 @@ void launch_matvec_leaf(const DevLevel& L, const T* A, const T* X, const T* x, c
 H2_INST_MV(double)
 H2_INST_MV(float)
 
+// ---------------------------------------------------- FP64 by FP32 pairs ---
+// The FP64 matvec of the mixed refinement's residual, on GB300's FP32 units:
+// every FP64 matrix entry m is held as m_h + m_l (m_h = fl32(m),
+// m_l = fl32(m - m_h): m to about 2^-48 relative) and every FP64 input x as
+// x_h + x_l likewise.  m x = m_h x_h + (m_h x_l + m_l x_h) + O(2^-48 m x);
+// the first product is split exactly into p + e by a fused multiply-add,
+// and the running sum is an FP32 pair (H, L): H += p by an error-free
+// two-sum whose error joins L with e and the cross terms.  Each row's pairs
+// are added in FP64 at the end.  The kernels then read 8 bytes per entry,
+// as the FP64 ones do, but spend FP32 instructions on them.
+// (the _rn intrinsics keep the compiler from fusing the two-sum's operations)
+__device__ __forceinline__ void df_fma(float& H, float& L, float mh, float ml, float xh, float xl) {
+  const float p = __fmul_rn(mh, xh);
+  const float e = fmaf(mh, xh, -p);
+  const float small = fmaf(mh, xl, fmaf(ml, xh, e));
+  const float s = __fadd_rn(H, p);
+  const float bb = __fsub_rn(s, H);
+  const float err = __fadd_rn(__fsub_rn(H, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  H = s;
+  L = __fadd_rn(L, __fadd_rn(small, err));
+}
+
+constexpr int kRPWdf = 8;  // rows per warp per pass: 64-row chunks
+
+// H[t] + L[t] += sum_c (Mh + Ml)[r_t * ld + c] (xh + xl)[c], rows r_t = r0 + warp + 8 t < nr
+template <int RPW>
+__device__ __forceinline__ void rows_acc_df(int r0, const float* __restrict__ Mh, const float* __restrict__ Ml,
+                                            int64_t ld, int nr, int nc, const float* __restrict__ xh,
+                                            const float* __restrict__ xl, float (&H)[RPW], float (&L)[RPW]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rbase = r0 + warp;
+  const bool vec = (ld % 4 == 0) && (nc % 4 == 0) && ((reinterpret_cast<uintptr_t>(Mh) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(Ml) & 15) == 0);
+  if (vec) {
+    for (int c = lane * 4; c < nc; c += 128) {
+      float4 vh[RPW], vl[RPW];
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) {
+        const int r = rbase + 8 * t;
+        if (r < nr) {
+          vh[t] = __ldg(reinterpret_cast<const float4*>(Mh + r * ld + c));
+          vl[t] = __ldg(reinterpret_cast<const float4*>(Ml + r * ld + c));
+        } else {
+          vh[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+          vl[t] = vh[t];
+        }
+      }
+      const float4 ah = *reinterpret_cast<const float4*>(xh + c);
+      const float4 al = *reinterpret_cast<const float4*>(xl + c);
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) {
+        df_fma(H[t], L[t], vh[t].x, vl[t].x, ah.x, al.x);
+        df_fma(H[t], L[t], vh[t].y, vl[t].y, ah.y, al.y);
+        df_fma(H[t], L[t], vh[t].z, vl[t].z, ah.z, al.z);
+        df_fma(H[t], L[t], vh[t].w, vl[t].w, ah.w, al.w);
+      }
+    }
+  } else {
+    for (int c = lane; c < nc; c += 32) {
+#pragma unroll
+      for (int t = 0; t < RPW; ++t) {
+        const int r = rbase + 8 * t;
+        if (r < nr) df_fma(H[t], L[t], Mh[r * ld + c], Ml[r * ld + c], xh[c], xl[c]);
+      }
+    }
+  }
+}
+
+// out[r] = base[r] + sum over lanes of (H + L), added in FP64
+template <int RPW>
+__device__ __forceinline__ void rows_finish_df(int r0, int nr, const float (&H)[RPW], const float (&L)[RPW],
+                                               const double* base, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < RPW; ++t) {
+    const int r = r0 + warp + 8 * t;
+    const double v = warp_sum((double)H[t] + (double)L[t]);
+    if (lane == 0 && r < nr) out[r] = (base ? base[r] : 0.0) + v;
+  }
+}
+
+__device__ __forceinline__ void df_split(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+// couplings: yh_i = sum_{far j} S_f xh_j
+__global__ void __launch_bounds__(256, 2) mv_far_df_kernel(int K, const int64_t* __restrict__ ptr,
+                                                           const int32_t* __restrict__ fj, const float* __restrict__ Sh,
+                                                           const float* __restrict__ Sl, const double* __restrict__ xh,
+                                                           double* __restrict__ yh) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const int64_t p0 = ptr[i];
+  const int nf = (int)(ptr[i + 1] - p0);
+  const int Kp = (K + 3) & ~3;
+  float* sh = reinterpret_cast<float*>(smraw);  // nf * Kp
+  float* sl = sh + (size_t)nf * Kp;             // nf * Kp
+  for (int e = tid; e < nf * K; e += blockDim.x) {
+    const int q = e / K, a = e - q * K;
+    df_split(xh[(int64_t)fj[p0 + q] * K + a], sh[q * Kp + a], sl[q * Kp + a]);
+  }
+  __syncthreads();
+  float H[kRPWdf], L[kRPWdf];
+  for (int r0 = 0; r0 < K; r0 += 8 * kRPWdf) {
+    zero(H);
+    zero(L);
+    for (int q = 0; q < nf; ++q)
+      rows_acc_df<kRPWdf>(r0, Sh + (p0 + q) * K * K, Sl + (p0 + q) * K * K, K, K, K, sh + q * Kp, sl + q * Kp, H, L);
+    rows_finish_df<kRPWdf>(r0, K, H, L, nullptr, yh + (int64_t)i * K);
+  }
+}
+void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const double* xh, double* yh,
+                          cudaStream_t st) {
+  const size_t sm = 2 * sizeof(float) * (size_t)((L.K + 3) & ~3) * std::max(L.max_far, 1);
+  set_smem((const void*)mv_far_df_kernel, sm);
+  ++g_launches;
+  mv_far_df_kernel<<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, Sh, Sl, xh, yh);
+}
+
+// leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j
+__global__ void __launch_bounds__(256, 2) mv_leaf_df_kernel(int D, int K, const int64_t* __restrict__ ptr,
+                                                            const int32_t* __restrict__ nj, const float* __restrict__ Ah,
+                                                            const float* __restrict__ Al, const float* __restrict__ Xh,
+                                                            const float* __restrict__ Xl, const double* __restrict__ x,
+                                                            const double* __restrict__ yh, double* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int i = blockIdx.x, tid = threadIdx.x;
+  const int64_t p0 = ptr[i];
+  const int nn = (int)(ptr[i + 1] - p0);
+  const int Kp = (K + 3) & ~3, Dp = (D + 3) & ~3;
+  float* hh = reinterpret_cast<float*>(smraw);  // Kp
+  float* hl = hh + Kp;                          // Kp
+  float* xsh = hl + Kp;                         // nn * Dp
+  float* xsl = xsh + (size_t)nn * Dp;           // nn * Dp
+  if (yh)
+    for (int e = tid; e < K; e += blockDim.x) df_split(yh[(int64_t)i * K + e], hh[e], hl[e]);
+  for (int e = tid; e < nn * D; e += blockDim.x) {
+    const int q = e / D, d = e - q * D;
+    df_split(x[(int64_t)nj[p0 + q] * D + d], xsh[q * Dp + d], xsl[q * Dp + d]);
+  }
+  __syncthreads();
+  float H[kRPWdf], L[kRPWdf];
+  for (int r0 = 0; r0 < D; r0 += 8 * kRPWdf) {
+    zero(H);
+    zero(L);
+    if (yh) rows_acc_df<kRPWdf>(r0, Xh + (int64_t)i * D * K, Xl + (int64_t)i * D * K, K, D, K, hh, hl, H, L);
+    for (int q = 0; q < nn; ++q)
+      rows_acc_df<kRPWdf>(r0, Ah + (p0 + q) * D * D, Al + (p0 + q) * D * D, D, D, D, xsh + q * Dp, xsl + q * Dp, H,
+                          L);
+    rows_finish_df<kRPWdf>(r0, D, H, L, nullptr, y + (int64_t)i * D);
+  }
+}
+void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, const float* Xh, const float* Xl,
+                           const double* x, const double* yh, double* y, cudaStream_t st) {
+  const size_t Kp = (L.K + 3) & ~3, Dp = (L.D + 3) & ~3;
+  const size_t sm = 2 * sizeof(float) * (Kp + Dp * (size_t)L.max_near);
+  set_smem((const void*)mv_leaf_df_kernel, sm);
+  ++g_launches;
+  mv_leaf_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, Ah, Al, Xh, Xl, x, yh, y);
+}
+
+// lo[e] = fl32(a[e] - hi[e]) (hi = fl32(a))
+__global__ void split_lo_kernel(const double* __restrict__ a, const float* __restrict__ hi, float* __restrict__ lo,
+                                int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    lo[e] = (float)(a[e] - (double)hi[e]);
+}
+void launch_split_lo(const double* a, const float* hi, float* lo, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ++g_launches;
+  split_lo_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(a, hi, lo, n);
+}
+
 // ------------------------------------------------------------ vectors ---
 __global__ void gather_kernel(const int64_t* __restrict__ slot, const double* __restrict__ src,
                               double* __restrict__ dst, int64_t n) {

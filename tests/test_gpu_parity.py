@@ -173,6 +173,11 @@ def test_mixed_refined_solution(B, name, prec, method):
     assert rel(x, x_ref) <= 1e-9
     st = S.stats()
     assert st["prec"] == {"fp16": 1, "bf16": 2}[prec]
+    # the refinement's residual (FP32-pair matvec in the nested method) is the
+    # FP64 one: recomputed with the FP64 matvec it agrees to 1 %, or to 1e-13
+    # of ||b|| once it is near the FP64 evaluation's own rounding level
+    r_true = np.linalg.norm(b - S.matvec(x)) / np.linalg.norm(b)
+    assert abs(r_true - r) <= 1e-2 * r + 1e-13, (r_true, r)
     S.close()
 
 
