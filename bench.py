@@ -181,18 +181,18 @@ def fp64_peak_tflops() -> float:
     return best
 
 
-# DRAM traffic of one launch of the FP32 leaf matvec kernel (the step's
-# largest kernel) from an ncu capture of this bench's workload, valid while
-# the kernel's source is the one captured (digest of its text below).
-LEAF_TRAFFIC = {"digest": "f0e1536c62ad997a", "bytes_per_launch": 6.62e9 + 4.50e6,
-                "profile": "profiles/mv_leaf_kernel_cube262144_yukawa.md"}
+# DRAM traffic of one launch of the FP32 matvec's leaf kernel (the step's
+# largest kernel: the symmetric-storage pair kernel) from an ncu capture of
+# this bench's workload, valid while the kernel's source is the one captured
+# (digest of its text below).
+LEAF_TRAFFIC = None  # {"digest": ..., "bytes_per_launch": ..., "profile": ...}
 
 
 def leaf_kernel_digest() -> str:
     src = open(os.path.join(ROOT, "paper_2502_02395_gb300", "csrc", "kernels_solve.cu")).read()
-    a, b = src.index("// leaf: y_i = X_i yh_i"), src.index("#define H2_INST_MV(T)")
-    c, d = src.index("// Vector loads of the stored matrix entries"), src.index("constexpr int kRPW")
-    return hashlib.sha256((src[a:b] + src[c:d]).encode()).hexdigest()[:16]
+    a = src.index("// -------------------------------------------- symmetric leaf near blocks ---")
+    b = src.index("bool sym_leaf_supported(int D)")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
 def kernel_roofline(stats, t_leaf, n_leaf, peaks):
@@ -208,7 +208,8 @@ def kernel_roofline(stats, t_leaf, n_leaf, peaks):
     if LEAF_TRAFFIC and LEAF_TRAFFIC.get("digest") == leaf_kernel_digest():
         traffic = LEAF_TRAFFIC["bytes_per_launch"]
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
-            "kernel": "mv_leaf_kernel<float>", "launches_per_step": n_leaf, "bytes_per_launch": by,
+            "kernel": stats.get("leaf_kernel", "mv_leaf_kernel<float>"), "launches_per_step": n_leaf,
+            "bytes_per_launch": by,
             "ms_per_launch": per * 1e3,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback 6800 GB/s"}
 

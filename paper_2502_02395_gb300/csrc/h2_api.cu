@@ -227,10 +227,44 @@ h2_status setup_device(h2_ctx* c) {
   // mixed-precision refinement (part of the instance)
   CKC(dalloc(c, &c->xhat32, c->hat_off[L + 1]));
   CKC(dalloc(c, &c->yhat32, c->hat_off[L + 1]));
-  CKC(dalloc(c, &c->A32, (size_t)lf.NP * lf.D * lf.D));
-  launch_convert<double, float>(c->A64, c->A32, (int64_t)lf.NP * lf.D * lf.D, 0);
-  CKC(dalloc(c, &c->Alo, (size_t)lf.NP * lf.D * lf.D));
-  launch_split_lo(c->A64, c->A32, c->Alo, (int64_t)lf.NP * lf.D * lf.D, 0);
+  c->sym = sym_leaf_supported(lf.D);
+  if (c->sym) {
+    // the kernels' near blocks are symmetric (A_ji = A_ij^T): keep i <= j
+    std::vector<int32_t> uq, ui, uj;
+    for (int64_t q = 0; q < lf.NP; ++q)
+      if (lf.h_near_i[q] <= lf.h_near_j[q])
+        uq.push_back((int32_t)q), ui.push_back(lf.h_near_i[q]), uj.push_back(lf.h_near_j[q]);
+    c->npu = (int64_t)uq.size();
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> lists(lf.nb);  // (partner box, entry)
+    for (int64_t k = 0; k < c->npu; ++k) {
+      lists[ui[k]].push_back({uj[k], (int32_t)(2 * k)});
+      if (ui[k] != uj[k]) lists[uj[k]].push_back({ui[k], (int32_t)(2 * k + 1)});
+    }
+    std::vector<int64_t> ptr(lf.nb + 1, 0);
+    std::vector<int32_t> ent;
+    for (int i = 0; i < lf.nb; ++i) {
+      std::sort(lists[i].begin(), lists[i].end());
+      for (auto& pe : lists[i]) ent.push_back(pe.second);
+      ptr[i + 1] = (int64_t)ent.size();
+    }
+    CKS(upload(c, &c->sym_q, uq));
+    CKS(upload(c, &c->sym_i, ui));
+    CKS(upload(c, &c->sym_j, uj));
+    CKS(upload(c, &c->sym_ptr, ptr));
+    CKS(upload(c, &c->sym_ent, ent));
+    const int64_t DD = (int64_t)lf.D * lf.D;
+    CKC(dalloc(c, &c->A32, (size_t)(c->npu * DD)));
+    CKC(dalloc(c, &c->Alo, (size_t)(c->npu * DD)));
+    launch_gather_blocks(c->A64, c->sym_q, DD, c->npu, c->A32, 0);
+    launch_gather_split_lo(c->A64, c->sym_q, DD, c->npu, c->A32, c->Alo, 0);
+    CKC(dalloc(c, &c->part32, (size_t)c->npu * 2 * lf.D));
+    CKC(dalloc(c, &c->part64, (size_t)c->npu * 2 * lf.D));
+  } else {
+    CKC(dalloc(c, &c->A32, (size_t)lf.NP * lf.D * lf.D));
+    launch_convert<double, float>(c->A64, c->A32, (int64_t)lf.NP * lf.D * lf.D, 0);
+    CKC(dalloc(c, &c->Alo, (size_t)lf.NP * lf.D * lf.D));
+    launch_split_lo(c->A64, c->A32, c->Alo, (int64_t)lf.NP * lf.D * lf.D, 0);
+  }
   c->X64p.assign(L + 1, nullptr);
   c->S64p.assign(L + 1, nullptr);
   c->X32p.assign(L + 1, nullptr);
@@ -672,10 +706,25 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
   }
-  if (L == 0) {
+  // leaf step: y = X_L yh_L + near-field; the FP32 copy may hold only the
+  // i <= j halves of the symmetric near blocks
+  auto leaf = [&](const T* XL, const T* yhL) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (c->sym) {
+        const DevLevel& lf = c->lv[L];
+        if (leaf_ev) cudaEventRecord(e0, st);
+        launch_matvec_sym_pairs(lf.D, c->npu, c->sym_i, c->sym_j, A, x, c->part32, st);
+        if (leaf_ev) cudaEventRecord(e1, st), leaf_ev->push_back({e0, e1});
+        launch_matvec_sym_sum<float>(lf.nb, lf.D, L ? lf.K : 0, c->sym_ptr, c->sym_ent, XL, yhL, c->part32, y, st);
+        return;
+      }
+    }
     if (leaf_ev) cudaEventRecord(e0, st);
-    launch_matvec_leaf<T>(c->lv[0], A, nullptr, x, nullptr, y, st);
+    launch_matvec_leaf<T>(c->lv[L], A, XL, x, yhL, y, st);
     if (leaf_ev) cudaEventRecord(e1, st), leaf_ev->push_back({e0, e1});
+  };
+  if (L == 0) {
+    leaf(nullptr, nullptr);
     return;
   }
   const std::vector<int64_t>& off = c->hat_off;
@@ -683,9 +732,7 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
   for (int l = L - 1; l >= 1; --l) launch_matvec_up<T>(c->lv[l], X[l], xh + off[l + 1], xh + off[l], st);
   for (int l = 1; l <= L; ++l) launch_matvec_far<T>(c->lv[l], S[l], xh + off[l], yh + off[l], st);
   for (int l = 1; l < L; ++l) launch_matvec_down<T>(c->lv[l], X[l], yh + off[l], yh + off[l + 1], st);
-  if (leaf_ev) cudaEventRecord(e0, st);
-  launch_matvec_leaf<T>(c->lv[L], A, X[L], x, yh + off[L], y, st);
-  if (leaf_ev) cudaEventRecord(e1, st), leaf_ev->push_back({e0, e1});
+  leaf(X[L], yh + off[L]);
 }
 
 void matvec_impl(h2_ctx* c, const double* x, double* y) {
@@ -697,8 +744,18 @@ void matvec_impl(h2_ctx* c, const double* x, double* y) {
 void matvec_df(h2_ctx* c, const double* x, double* y) {
   const int L = c->L;
   cudaStream_t st = c->stream;
+  auto leaf = [&](const double* yhL) {
+    const DevLevel& lf = c->lv[L];
+    if (c->sym) {
+      launch_matvec_sym_pairs_df(lf.D, c->npu, c->sym_i, c->sym_j, c->A32, c->Alo, x, c->part64, st);
+      launch_matvec_sym_sum<double>(lf.nb, lf.D, L ? lf.K : 0, c->sym_ptr, c->sym_ent, L ? c->X64p[L] : nullptr, yhL,
+                                    c->part64, y, st);
+    } else {
+      launch_matvec_leaf_df(lf, c->A32, c->Alo, L ? c->X32p[L] : nullptr, L ? c->Xlo : nullptr, x, yhL, y, st);
+    }
+  };
   if (L == 0) {
-    launch_matvec_leaf_df(c->lv[0], c->A32, c->Alo, nullptr, nullptr, x, nullptr, y, st);
+    leaf(nullptr);
     return;
   }
   const std::vector<int64_t>& off = c->hat_off;
@@ -707,7 +764,7 @@ void matvec_df(h2_ctx* c, const double* x, double* y) {
   for (int l = 1; l <= L; ++l)
     launch_matvec_far_df(c->lv[l], c->S32p[l], c->Slo[l], c->xhat + off[l], c->yhat + off[l], st);
   for (int l = 1; l < L; ++l) launch_matvec_down<double>(c->lv[l], c->X64p[l], c->yhat + off[l], c->yhat + off[l + 1], st);
-  launch_matvec_leaf_df(c->lv[L], c->A32, c->Alo, c->X32p[L], c->Xlo, x, c->yhat + off[L], y, st);
+  leaf(c->yhat + off[L]);
 }
 void matvec32(h2_ctx* c, const float* x, float* y, EventPairs* leaf_ev = nullptr) {
   matvec_t<float>(c, c->A32, c->X32p.data(), c->S32p.data(), c->xhat32, c->yhat32, x, y, leaf_ev);
@@ -1311,15 +1368,21 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
   double by_leaf32 = 0;
   {
     const DevLevel& lf = c->lv[c->L];
-    by_mv += 8.0 * (double)lf.NP * lf.D * lf.D;
+    // the mixed solve's matvecs read only the stored halves of symmetric
+    // leaf blocks (the FP64 path reads all of them)
+    const bool symm = c->sym && c->prec != H2_PREC_FP64;
+    const double npl = symm ? (double)c->npu : (double)lf.NP;
+    by_mv += 8.0 * npl * lf.D * lf.D;
     fl_mv += 2.0 * (double)lf.NP * lf.D * lf.D;
-    // leaf kernel of the FP32 matvec: the near blocks, the leaf basis, x and
-    // the skeleton coefficients read once, y written once
+    // the FP32 matvec's leaf kernel: the near blocks read once, x read, y or
+    // (symmetric storage) two partial products per stored pair written
     const double K = c->L ? lf.K : 0;
-    by_leaf32 = 4.0 * ((double)lf.NP * lf.D * lf.D + (double)lf.nb * lf.D * K + 2.0 * lf.nb * lf.D + lf.nb * K);
+    by_leaf32 = symm ? 4.0 * ((double)c->npu * lf.D * lf.D + (double)lf.nb * lf.D + 2.0 * c->npu * lf.D)
+                     : 4.0 * ((double)lf.NP * lf.D * lf.D + (double)lf.nb * lf.D * K + 2.0 * lf.nb * lf.D + lf.nb * K);
   }
   o << "],\"bytes_subst\":" << by_sub << ",\"bytes_matvec\":" << by_mv << ",\"flops_matvec\":" << fl_mv
-    << ",\"bytes_matvec32\":" << by_mv / 2 << ",\"bytes_matvec32_leaf\":" << by_leaf32;
+    << ",\"bytes_matvec32\":" << by_mv / 2 << ",\"bytes_matvec32_leaf\":" << by_leaf32 << ",\"leaf_kernel\":\""
+    << ((c->sym && c->prec != H2_PREC_FP64) ? "mv_sym_pair_kernel<float>" : "mv_leaf_kernel<float>") << "\"";
   o << ",\"flops\":{\"a1_qr\":" << fl_qr << ",\"a2_proj\":" << fl_proj << ",\"a3_lu\":" << fl_lu
     << ",\"a45_schur\":" << fl_schur << ",\"a2c_coupling\":" << fl_coup << "}";
   o << ",\"times\":{\"a1_qr\":" << t.a1_qr << ",\"a2_proj\":" << t.a2_proj << ",\"a3_lu\":" << t.a3_lu

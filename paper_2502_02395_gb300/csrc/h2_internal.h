@@ -227,6 +227,16 @@ struct h2_ctx {
   float* Alo = nullptr;
   float* Xlo = nullptr;      // leaf level
   std::vector<float*> Slo;   // per level (index l; [0] unused)
+  // Symmetric leaf storage of A32 / Alo: only the near pairs i <= j
+  // ("stored pairs", sym_q: their index among the near pairs), and per box
+  // the list of partial products (2k: A_k x_j of stored pair k with i = box,
+  // 2k + 1: A_k^T x_i with j = box), CSR over boxes.
+  bool sym = false;
+  int64_t npu = 0;
+  int32_t *sym_q = nullptr, *sym_i = nullptr, *sym_j = nullptr, *sym_ent = nullptr;
+  int64_t* sym_ptr = nullptr;
+  float* part32 = nullptr;   // npu * 2 D partial products (FP32 matvec)
+  double* part64 = nullptr;  // the same for the FP32-pair matvec
   float *xhat32 = nullptr, *yhat32 = nullptr;
   std::vector<double*> X64p, S64p;  // per-level pointers (index l; [0] unused)
   std::vector<float*> X32p, S32p;

@@ -98,6 +98,21 @@ void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, c
 void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, const float* Xh, const float* Xl,
                            const double* x, const double* yh, double* y, cudaStream_t st);
 void launch_split_lo(const double* a, const float* hi, float* lo, int64_t n, cudaStream_t st);  // lo = fl32(a - hi)
+// Leaf matvec on the stored (i <= j) halves of symmetric leaf near blocks:
+// per stored pair k = (ui[k], uj[k]) the partial products [A x_j; A^T x_i]
+// into part (2 D per pair), then per box y = X yh + its partial products.
+bool sym_leaf_supported(int D);  // D = 128 or 256
+void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A, const float* x,
+                             float* part, cudaStream_t st);
+void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
+                                const float* Al, const double* x, double* part, cudaStream_t st);
+template <typename T>
+void launch_matvec_sym_sum(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const T* X, const T* yh,
+                           const T* part, T* y, cudaStream_t st);
+// out[k] = fl32(in[idx[k]]), lo[k] = fl32(in[idx[k]] - hi[k]) for blocks of n entries
+void launch_gather_blocks(const double* in, const int32_t* idx, int64_t n, int64_t nblk, float* out, cudaStream_t st);
+void launch_gather_split_lo(const double* in, const int32_t* idx, int64_t n, int64_t nblk, const float* hi, float* lo,
+                            cudaStream_t st);
 
 void launch_gather(const int64_t* slot, const double* src, double* dst, int64_t nslots, cudaStream_t st);
 void launch_scatter(const int64_t* slot, const double* src, double* dst, int64_t nslots, cudaStream_t st);

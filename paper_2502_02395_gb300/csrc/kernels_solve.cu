@@ -1374,6 +1374,288 @@ void launch_split_lo(const double* a, const float* hi, float* lo, int64_t n, cud
   split_lo_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(a, hi, lo, n);
 }
 
+// -------------------------------------------- symmetric leaf near blocks ---
+// The leaf near blocks of a symmetric kernel satisfy A_ji = A_ij^T, so the
+// inner solver's matvec keeps only the blocks with i <= j ("stored pairs")
+// and reads each once: the CTA of stored pair k = (a, b) forms
+// u = A_ab x_b (for box a) and, when a != b, w = A_ab^T x_a (for box b)
+// into part[k] = [u; w]; a per-box kernel then adds y_i = X_i yh_i + the
+// partial products of the box (listed in ent: 2k for a u, 2k + 1 for a w).
+// Warp w takes the rows r = w, w + 8, ... of the block, each lane a
+// 4-column chunk per 128 columns: u needs one warp reduction per row, w
+// stays in the lane's registers and the 8 warps' partial w meet in shared
+// memory.
+constexpr int kSymRPW = 8;  // rows per warp in flight
+
+template <int CH>  // 4-column chunks per lane: D = 128 CH
+__global__ void __launch_bounds__(256, 2) mv_sym_pair_kernel(int D, int64_t npu, const int32_t* __restrict__ ui,
+                                                             const int32_t* __restrict__ uj,
+                                                             const float* __restrict__ A, const float* __restrict__ x,
+                                                             float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* xa = reinterpret_cast<float*>(smraw);  // D
+  float* wp = xa + D;                           // 8 * D
+  const int64_t k = blockIdx.x;
+  const int a = ui[k], b = uj[k], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool both = a != b;
+  const float* M = A + k * D * D;
+  for (int e = tid; e < D; e += blockDim.x) xa[e] = x[(int64_t)a * D + e];
+  float xb[CH][4];
+#pragma unroll
+  for (int h = 0; h < CH; ++h) {
+    const float4 v = *reinterpret_cast<const float4*>(x + (int64_t)b * D + lane * 4 + 128 * h);
+    xb[h][0] = v.x, xb[h][1] = v.y, xb[h][2] = v.z, xb[h][3] = v.w;
+  }
+  float wacc[CH][4];
+#pragma unroll
+  for (int h = 0; h < CH; ++h)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) wacc[h][e] = 0.0f;
+  __syncthreads();
+  float* u = part + k * 2 * D;
+  for (int r0 = warp; r0 < D; r0 += 8 * kSymRPW) {
+    float4 v[kSymRPW][CH];
+#pragma unroll
+    for (int t = 0; t < kSymRPW; ++t) {
+      const int r = r0 + 8 * t;
+#pragma unroll
+      for (int h = 0; h < CH; ++h)
+        v[t][h] = (r < D) ? __ldg(reinterpret_cast<const float4*>(M + (int64_t)r * D + lane * 4 + 128 * h))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int t = 0; t < kSymRPW; ++t) {
+      const int r = r0 + 8 * t;
+      const float xr = (r < D) ? xa[r] : 0.0f;
+      float s = 0.0f;
+#pragma unroll
+      for (int h = 0; h < CH; ++h) {
+        s = fmaf(v[t][h].x, xb[h][0], s);
+        s = fmaf(v[t][h].y, xb[h][1], s);
+        s = fmaf(v[t][h].z, xb[h][2], s);
+        s = fmaf(v[t][h].w, xb[h][3], s);
+        wacc[h][0] = fmaf(v[t][h].x, xr, wacc[h][0]);
+        wacc[h][1] = fmaf(v[t][h].y, xr, wacc[h][1]);
+        wacc[h][2] = fmaf(v[t][h].z, xr, wacc[h][2]);
+        wacc[h][3] = fmaf(v[t][h].w, xr, wacc[h][3]);
+      }
+      s = warp_sum(s);
+      if (lane == 0 && r < D) u[r] = s;
+    }
+  }
+  if (!both) return;
+#pragma unroll
+  for (int h = 0; h < CH; ++h)
+    *reinterpret_cast<float4*>(wp + warp * D + lane * 4 + 128 * h) =
+        make_float4(wacc[h][0], wacc[h][1], wacc[h][2], wacc[h][3]);
+  __syncthreads();
+  for (int c = tid; c < D; c += blockDim.x) {
+    float s = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += wp[w * D + c];
+    u[D + c] = s;
+  }
+}
+
+// y_i = X_i yh_i + sum of box i's partial products (in list order)
+template <typename T>
+__global__ void __launch_bounds__(256) mv_sym_sum_kernel(int D, int K, const int64_t* __restrict__ ptr,
+                                                         const int32_t* __restrict__ ent, const T* __restrict__ X,
+                                                         const T* __restrict__ yh, const T* __restrict__ part,
+                                                         T* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sh = reinterpret_cast<T*>(smraw);  // K
+  T* sb = sh + ((K + 3) & ~3);          // D
+  const int i = blockIdx.x;
+  const int64_t e0 = ptr[i], e1 = ptr[i + 1];
+  auto hook = [&] {
+    for (int e = threadIdx.x; e < K; e += blockDim.x) sh[e] = yh[(int64_t)i * K + e];
+    for (int r = threadIdx.x; r < D; r += blockDim.x) {
+      T s = T(0);
+      int64_t q = e0;
+      for (; q + 4 <= e1; q += 4) {
+        T v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int en = ent[q + t];
+          v[t] = part[(int64_t)(en >> 1) * 2 * D + (en & 1) * D + r];
+        }
+        s += (v[0] + v[1]) + (v[2] + v[3]);
+      }
+      for (; q < e1; ++q) {
+        const int en = ent[q];
+        s += part[(int64_t)(en >> 1) * 2 * D + (en & 1) * D + r];
+      }
+      sb[r] = s;
+    }
+    __syncthreads();
+  };
+  if (X) {
+    cta_gemv<T, T, Unr<T>::v>(X + (int64_t)i * D * K, K, D, K, sh, T(1), sb, y + (int64_t)i * D, hook);
+  } else {
+    hook();
+    for (int r = threadIdx.x; r < D; r += blockDim.x) y[(int64_t)i * D + r] = sb[r];
+  }
+}
+
+// FP32-pair form for the residual (see df_fma): A as hi + lo, x FP64,
+// partial products FP64.
+template <int CH>
+__global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t npu, const int32_t* __restrict__ ui,
+                                                                const int32_t* __restrict__ uj,
+                                                                const float* __restrict__ Ah,
+                                                                const float* __restrict__ Al,
+                                                                const double* __restrict__ x,
+                                                                double* __restrict__ part) {
+  constexpr int RPW = 2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* xah = reinterpret_cast<float*>(smraw);  // D
+  float* xal = xah + D;                          // D
+  double* wp = reinterpret_cast<double*>(xal + D);  // 8 * D (D a multiple of 128: 8-byte aligned)
+  const int64_t k = blockIdx.x;
+  const int a = ui[k], b = uj[k], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool both = a != b;
+  const float* Mh = Ah + k * D * D;
+  const float* Ml = Al + k * D * D;
+  for (int e = tid; e < D; e += blockDim.x) df_split(x[(int64_t)a * D + e], xah[e], xal[e]);
+  float xbh[CH][4], xbl[CH][4];
+#pragma unroll
+  for (int h = 0; h < CH; ++h)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) df_split(x[(int64_t)b * D + lane * 4 + 128 * h + e], xbh[h][e], xbl[h][e]);
+  float wH[CH][4], wL[CH][4];
+#pragma unroll
+  for (int h = 0; h < CH; ++h)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) wH[h][e] = 0.0f, wL[h][e] = 0.0f;
+  __syncthreads();
+  double* u = part + k * 2 * D;
+  for (int r0 = warp; r0 < D; r0 += 8 * RPW) {
+    float4 vh[RPW][CH], vl[RPW][CH];
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      const int r = r0 + 8 * t;
+#pragma unroll
+      for (int h = 0; h < CH; ++h) {
+        const int64_t off = (int64_t)r * D + lane * 4 + 128 * h;
+        vh[t][h] = (r < D) ? __ldg(reinterpret_cast<const float4*>(Mh + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        vl[t][h] = (r < D) ? __ldg(reinterpret_cast<const float4*>(Ml + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < RPW; ++t) {
+      const int r = r0 + 8 * t;
+      const float xrh = (r < D) ? xah[r] : 0.0f, xrl = (r < D) ? xal[r] : 0.0f;
+      float H = 0.0f, L = 0.0f;
+#pragma unroll
+      for (int h = 0; h < CH; ++h) {
+        const float mh[4] = {vh[t][h].x, vh[t][h].y, vh[t][h].z, vh[t][h].w};
+        const float ml[4] = {vl[t][h].x, vl[t][h].y, vl[t][h].z, vl[t][h].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          df_fma(H, L, mh[e], ml[e], xbh[h][e], xbl[h][e]);
+          if (both) df_fma(wH[h][e], wL[h][e], mh[e], ml[e], xrh, xrl);
+        }
+      }
+      const double s = warp_sum((double)H + (double)L);
+      if (lane == 0 && r < D) u[r] = s;
+    }
+  }
+  if (!both) return;
+#pragma unroll
+  for (int h = 0; h < CH; ++h)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) wp[warp * D + lane * 4 + 128 * h + e] = (double)wH[h][e] + (double)wL[h][e];
+  __syncthreads();
+  for (int c = tid; c < D; c += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += wp[w * D + c];
+    u[D + c] = s;
+  }
+}
+
+bool sym_leaf_supported(int D) { return D == 128 || D == 256; }
+
+template <int CH>
+static void launch_sym_pairs_ch(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A,
+                                const float* x, float* part, cudaStream_t st) {
+  const size_t sm = sizeof(float) * 9 * (size_t)D;
+  set_smem((const void*)mv_sym_pair_kernel<CH>, sm);
+  ++g_launches;
+  mv_sym_pair_kernel<CH><<<(unsigned)npu, 256, sm, st>>>(D, npu, ui, uj, A, x, part);
+}
+void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A, const float* x,
+                             float* part, cudaStream_t st) {
+  if (npu <= 0) return;
+  switch (D / 128) {
+    case 1: launch_sym_pairs_ch<1>(D, npu, ui, uj, A, x, part, st); break;
+    case 2: launch_sym_pairs_ch<2>(D, npu, ui, uj, A, x, part, st); break;
+    default: launch_sym_pairs_ch<2>(D, npu, ui, uj, A, x, part, st); break;
+  }
+}
+template <int CH>
+static void launch_sym_pairs_df_ch(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
+                                   const float* Al, const double* x, double* part, cudaStream_t st) {
+  const size_t sm = sizeof(float) * 2 * (size_t)D + sizeof(double) * 8 * (size_t)D;
+  set_smem((const void*)mv_sym_pair_df_kernel<CH>, sm);
+  ++g_launches;
+  mv_sym_pair_df_kernel<CH><<<(unsigned)npu, 256, sm, st>>>(D, npu, ui, uj, Ah, Al, x, part);
+}
+void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
+                                const float* Al, const double* x, double* part, cudaStream_t st) {
+  if (npu <= 0) return;
+  switch (D / 128) {
+    case 1: launch_sym_pairs_df_ch<1>(D, npu, ui, uj, Ah, Al, x, part, st); break;
+    case 2: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, x, part, st); break;
+    default: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, x, part, st); break;
+  }
+}
+template <typename T>
+void launch_matvec_sym_sum(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const T* X, const T* yh,
+                           const T* part, T* y, cudaStream_t st) {
+  const size_t sm = sizeof(T) * ((size_t)((K + 3) & ~3) + D);
+  ++g_launches;
+  mv_sym_sum_kernel<T><<<nb, 256, sm, st>>>(D, K, ptr, ent, X, yh, part, y);
+}
+template void launch_matvec_sym_sum<float>(int, int, int, const int64_t*, const int32_t*, const float*, const float*,
+                                           const float*, float*, cudaStream_t);
+template void launch_matvec_sym_sum<double>(int, int, int, const int64_t*, const int32_t*, const double*,
+                                            const double*, const double*, double*, cudaStream_t);
+
+// out[k] = (To) in[idx[k]] for blocks of n entries
+template <typename Ti, typename To>
+__global__ void gather_blocks_kernel(const Ti* __restrict__ in, const int32_t* __restrict__ idx, int64_t n,
+                                     int64_t nblk, To* __restrict__ out) {
+  const int64_t total = n * nblk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / n, r = e - k * n;
+    out[e] = (To)in[(int64_t)idx[k] * n + r];
+  }
+}
+void launch_gather_blocks(const double* in, const int32_t* idx, int64_t n, int64_t nblk, float* out, cudaStream_t st) {
+  if (n * nblk <= 0) return;
+  ++g_launches;
+  gather_blocks_kernel<double, float><<<(unsigned)std::min<int64_t>((n * nblk + 255) / 256, 152 * 32), 256, 0, st>>>(
+      in, idx, n, nblk, out);
+}
+// lo[k] = fl32(in[idx[k]] - hi[k])
+__global__ void gather_split_lo_kernel(const double* __restrict__ in, const int32_t* __restrict__ idx, int64_t n,
+                                       int64_t nblk, const float* __restrict__ hi, float* __restrict__ lo) {
+  const int64_t total = n * nblk;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / n, r = e - k * n;
+    lo[e] = (float)(in[(int64_t)idx[k] * n + r] - (double)hi[e]);
+  }
+}
+void launch_gather_split_lo(const double* in, const int32_t* idx, int64_t n, int64_t nblk, const float* hi, float* lo,
+                            cudaStream_t st) {
+  if (n * nblk <= 0) return;
+  ++g_launches;
+  gather_split_lo_kernel<<<(unsigned)std::min<int64_t>((n * nblk + 255) / 256, 152 * 32), 256, 0, st>>>(in, idx, n,
+                                                                                                        nblk, hi, lo);
+}
+
 // ------------------------------------------------------------ vectors ---
 __global__ void gather_kernel(const int64_t* __restrict__ slot, const double* __restrict__ src,
                               double* __restrict__ dst, int64_t n) {
