@@ -573,6 +573,39 @@ __global__ void perm_identity_kernel(int nb, int D, int K, T* __restrict__ U) {
   }
 }
 
+// Sums of CPW (8) per-lane values over the warp, left in d in every lane.  A transposed butterfly: at xor-distance 16, 8 and 4
+// each lane keeps half of its remaining values and adds its partner's copy
+// of them (4 + 2 + 1 shuffles), two plain steps finish one column per group
+// of four lanes, and one shuffle per column brings every sum back.
+template <int CPW>
+__device__ __forceinline__ void qr_reduce_cols(float (&d)[CPW]) {
+  static_assert(CPW == 8, "the butterfly is written for 8 columns");
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool up = lane & 16;
+    const float mine = up ? d[q + 4] : d[q], other = up ? d[q] : d[q + 4];
+    d[q] = mine + __shfl_xor_sync(0xffffffffu, other, 16);
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const bool up = lane & 8;
+    const float mine = up ? d[q + 2] : d[q], other = up ? d[q] : d[q + 2];
+    d[q] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+  }
+  {
+    const bool up = lane & 4;
+    const float mine = up ? d[1] : d[0], other = up ? d[0] : d[1];
+    d[0] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
+  }
+  d[0] += __shfl_xor_sync(0xffffffffu, d[0], 2);
+  d[0] += __shfl_xor_sync(0xffffffffu, d[0], 1);
+  // lane l now holds the sum of column 4 * bit4(l) + 2 * bit3(l) + bit2(l)
+  const float t = d[0];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) d[c] = __shfl_sync(0xffffffffu, t, ((c >> 2) << 4) | (((c >> 1) & 1) << 3) | ((c & 1) << 2));
+}
+
 // The same factorization in FP32 with the panel in registers: warp w owns
 // columns w, w + 16, ... and lane l rows l, l + 32, ... (D <= 32 RPL,
 // K <= 16 CPW).  Step k: the owner warp of column k forms the reflector
@@ -653,17 +686,25 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
         float v[RPL];
 #pragma unroll
         for (int s = 0; s < RPL; ++s) v[s] = vb[lane + 32 * s];
+        // lane partial products of the warp's columns (0 for j <= k)
+        float d[CPW];
+#pragma unroll
+        for (int cc = 0; cc < CPW; ++cc) {
+          const int j = warp + NW * cc;
+          d[cc] = 0.0f;
+          if (j > k && j < K) {
+#pragma unroll
+            for (int s = 0; s < RPL; ++s) d[cc] = fmaf(v[s], x[cc][s], d[cc]);
+          }
+        }
+        qr_reduce_cols<CPW>(d);
 #pragma unroll
         for (int cc = 0; cc < CPW; ++cc) {
           const int j = warp + NW * cc;
           if (j > k && j < K) {
-            float d = 0.0f;
+            const float dj = d[cc] * tk;
 #pragma unroll
-            for (int s = 0; s < RPL; ++s) d = fmaf(v[s], x[cc][s], d);
-            for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            d *= tk;
-#pragma unroll
-            for (int s = 0; s < RPL; ++s) x[cc][s] = fmaf(-d, v[s], x[cc][s]);
+            for (int s = 0; s < RPL; ++s) x[cc][s] = fmaf(-dj, v[s], x[cc][s]);
           }
         }
       }
@@ -976,40 +1017,38 @@ constexpr int kGjMaxR = 192;
 struct GjShared {
   float P[kGjMaxR];
   float fcol[kGjMaxR];
-  float cv[32], cs[32];
-  int cr[32];
   int prow[kGjMaxR], pinv[kGjMaxR], rowat[kGjMaxR];
   int p;
   float pv;
 };
 
-// One elimination step for column k = TC kc + J (J fixed at compile time so
-// that the tile stays in registers).  Returns false on a zero pivot column.
+// Thread t holds tile (tr, tc) = (t % G, t / G) with G = ntr rounded up to a
+// power of two (G divides 32): the owners of a tile column are one lane
+// group of one warp, so the pivot search is a shuffle reduction in that
+// warp.  One elimination step for column k = TC kc + J (J fixed at compile
+// time so that the tile stays in registers); false on a zero pivot column.
 template <int TR, int TC, int J>
-__device__ __forceinline__ bool gj_step(GjShared& sh, float (&a)[TR][TC], unsigned& used, int kc, int ntr,
+__device__ __forceinline__ bool gj_step(GjShared& sh, float (&a)[TR][TC], unsigned& used, int kc, int G,
                                         bool has, int tr, int tc, int r0, int c0) {
   const int t = threadIdx.x, k = kc * TC + J;
-  // (a) pivot candidates from the owners of column k
-  if (has && tc == kc) {
+  // (a) the owner warp of column k finds the pivot: the first largest |a_rk|
+  // over rows not yet used
+  if ((t >> 5) == ((kc * G) >> 5)) {
     float best = -1.0f, sv = 0.0f;
     int bi = -1;
+    if (has && tc == kc) {
 #pragma unroll
-    for (int i = 0; i < TR; ++i) {
-      const float v = fabsf(a[i][J]);
-      if (!((used >> i) & 1u) && v > best) best = v, sv = a[i][J], bi = r0 + i;
+      for (int i = 0; i < TR; ++i) {
+        const float v = fabsf(a[i][J]);
+        if (!((used >> i) & 1u) && v > best) best = v, sv = a[i][J], bi = r0 + i;
+      }
     }
-    sh.cv[tr] = best, sh.cs[tr] = sv, sh.cr[tr] = bi;
-  }
-  __syncthreads();
-  if (t < 32) {
-    float best = t < ntr ? sh.cv[t] : -1.0f, sv = t < ntr ? sh.cs[t] : 0.0f;
-    int bi = t < ntr ? sh.cr[t] : -1;
-    for (int o = 16; o; o >>= 1) {
-      const float ob = __shfl_down_sync(0xffffffffu, best, o), os = __shfl_down_sync(0xffffffffu, sv, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    for (int o = G >> 1; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o), os = __shfl_xor_sync(0xffffffffu, sv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) best = ob, sv = os, bi = oi;
     }
-    if (t == 0) {
+    if (tc == kc && tr == 0) {
       sh.p = bi, sh.pv = sv;
       if (bi >= 0) sh.prow[k] = bi;
     }
@@ -1018,7 +1057,7 @@ __device__ __forceinline__ bool gj_step(GjShared& sh, float (&a)[TR][TC], unsign
   const int p = sh.p;
   const float pv = sh.pv;
   if (p < 0 || pv == 0.0f || !isfinite(pv)) return false;
-  const float inv = 1.0f / pv;
+  const float inv = __frcp_rn(pv);
   // (b) scaled pivot row -> P, column k -> fcol
   if (has && tr == p / TR) {
 #pragma unroll
@@ -1056,12 +1095,19 @@ __device__ __forceinline__ bool gj_step(GjShared& sh, float (&a)[TR][TC], unsign
 }
 
 template <int TR, int TC, int J>
-__device__ __forceinline__ void gj_steps(bool& ok, GjShared& sh, float (&a)[TR][TC], unsigned& used, int kc,
-                                         int ntr, int left, bool has, int tr, int tc, int r0, int c0) {
+__device__ __forceinline__ void gj_steps(bool& ok, GjShared& sh, float (&a)[TR][TC], unsigned& used, int kc, int G,
+                                         int left, bool has, int tr, int tc, int r0, int c0) {
   if constexpr (J < TC) {
-    if (ok && left > J) ok = gj_step<TR, TC, J>(sh, a, used, kc, ntr, has, tr, tc, r0, c0);
-    gj_steps<TR, TC, J + 1>(ok, sh, a, used, kc, ntr, left, has, tr, tc, r0, c0);
+    if (ok && left > J) ok = gj_step<TR, TC, J>(sh, a, used, kc, G, has, tr, tc, r0, c0);
+    gj_steps<TR, TC, J + 1>(ok, sh, a, used, kc, G, left, has, tr, tc, r0, c0);
   }
+}
+
+// group size of the kernel's thread mapping (a power of two >= ntr, <= 32)
+__host__ __device__ inline int gj_group(int ntr) {
+  int g = 1;
+  while (g < ntr) g <<= 1;
+  return g;
 }
 
 template <int TR, int TC, int NT>
@@ -1073,9 +1119,9 @@ __global__ void __launch_bounds__(NT) gj_inverse_kernel(int D, int R, const floa
   constexpr int TL = (TR > TC ? TR : TC);  // Rp is a multiple of both tile edges
   static_assert(TL % TR == 0 && TL % TC == 0, "tile edges must divide the larger one");
   const int box = blockIdx.x, t = threadIdx.x;
-  const int Rp = (R + TL - 1) / TL * TL, ntr = Rp / TR, ntc = Rp / TC;
-  const bool has = t < ntr * ntc;
-  const int tr = has ? t / ntc : 0, tc = has ? t % ntc : 0;
+  const int Rp = (R + TL - 1) / TL * TL, ntr = Rp / TR, ntc = Rp / TC, G = gj_group(ntr);
+  const int tr = t % G, tc = t / G;
+  const bool has = tr < ntr && tc < ntc;
   const int r0 = tr * TR, c0 = tc * TC;
   const float* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
   float a[TR][TC];
@@ -1092,7 +1138,7 @@ __global__ void __launch_bounds__(NT) gj_inverse_kernel(int D, int R, const floa
   }
   bool ok = true;
   for (int kc = 0; kc < ntc && ok; ++kc)
-    gj_steps<TR, TC, 0>(ok, sh, a, used, kc, ntr, R - kc * TC, has, tr, tc, r0, c0);
+    gj_steps<TR, TC, 0>(ok, sh, a, used, kc, G, R - kc * TC, has, tr, tc, r0, c0);
   if (!ok) {
     if (t == 0 && atomicCAS(status, 0, level + 1) == 0) status[1] = box;
     return;
@@ -1139,10 +1185,11 @@ void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_
     float* Af_inv = reinterpret_cast<float*>(Ainv);
     ++g_launches;
     if (R <= 128) {
-      const int n = (R + 7) / 8, threads = std::max(32, (n * n + 31) / 32 * 32);
-      gj_inverse_kernel<8, 8, 256><<<nb, threads, 0, st>>>(D, R, Af, diag_idx, Af_inv, piv, status, level);
+      const int n = (R + 7) / 8, threads = std::max(32, gj_group(n) * n);
+      gj_inverse_kernel<8, 8, 256><<<nb, (threads + 31) / 32 * 32, 0, st>>>(D, R, Af, diag_idx, Af_inv, piv, status,
+                                                                             level);
     } else {
-      const int Rp = (R + 11) / 12 * 12, threads = (Rp / 12) * (Rp / 6);
+      const int Rp = (R + 11) / 12 * 12, threads = gj_group(Rp / 12) * (Rp / 6);
       gj_inverse_kernel<12, 6, 512><<<nb, (threads + 31) / 32 * 32, 0, st>>>(D, R, Af, diag_idx, Af_inv, piv, status,
                                                                                level);
     }
