@@ -585,11 +585,11 @@ __global__ void __launch_bounds__(256, sizeof(TS) == 2 ? 3 : 2)
 // the tile kPairStages pairs ahead.  Waits are bounded (2 s); on expiry
 // every thread leaves together, thread 0 having waited (bounded) for the
 // copies still in flight and set *err.
-constexpr int kPairStages = 3;
+constexpr int kPairStages = 2;
 constexpr unsigned long long kPairTimeoutNs = 2000000000ull;
 
 template <typename TS, int PH>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     pair_tma_kernel(const __grid_constant__ CUtensorMap tm, int D, int R, int K, int64_t n,
                     const int32_t* __restrict__ list, const int32_t* __restrict__ nj, const float* __restrict__ xv,
                     float* __restrict__ part, int32_t* __restrict__ err) {
@@ -696,11 +696,39 @@ __global__ void __launch_bounds__(256, 2)
     if (tid == 0 && t + kPairStages * G < n) issue(s, t + kPairStages * G);
     if (p1 >= 0) load_x(j1, xr);  // the next pair's x_j, before this pair's reduction
     float* out = part + p * nr;
+    if (cpr == 16) {
+      // transposed butterfly over the 16 lanes of a row group: at xor 8, 4
+      // and 2 each lane keeps half of its remaining rows and adds its
+      // partner's copies of them; xor 1 finishes.  Lane bits (3, 2, 1) then
+      // name the row u the lane holds.
 #pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      for (int o = cpr >> 1; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+      for (int q = 0; q < 4; ++q) {
+        const bool up = lane & 8;
+        const float mine = up ? acc[q + 4] : acc[q], other = up ? acc[q] : acc[q + 4];
+        acc[q] = mine + __shfl_xor_sync(0xffffffffu, other, 8);
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const bool up = lane & 4;
+        const float mine = up ? acc[q + 2] : acc[q], other = up ? acc[q] : acc[q + 2];
+        acc[q] = mine + __shfl_xor_sync(0xffffffffu, other, 4);
+      }
+      {
+        const bool up = lane & 2;
+        const float mine = up ? acc[1] : acc[0], other = up ? acc[0] : acc[1];
+        acc[0] = mine + __shfl_xor_sync(0xffffffffu, other, 2);
+      }
+      acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+      const int u = (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) | ((lane >> 1) & 1);
       const int r = (u * nw + warp) * rpi + sub;
-      if (cl == 0 && r < nr) out[r] = acc[u];
+      if ((lane & 1) == 0 && r < nr) out[r] = acc[0];
+    } else {
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        for (int o = cpr >> 1; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+        const int r = (u * nw + warp) * rpi + sub;
+        if (cl == 0 && r < nr) out[r] = acc[u];
+      }
     }
     p = p1, j = j1, p1 = p2, j1 = j2;
   }
@@ -940,7 +968,7 @@ static void launch_pairs(const DevLevel& L, const FacLevel<T>& F, const int32_t*
       const CUtensorMap& tm = (PH == PH_RR) ? F.tm_rr : (PH == PH_SR ? F.tm_sr : F.tm_rs);
       const size_t stage = ((size_t)nr * nc * 2 + 127) & ~(size_t)127;
       const size_t sm = kPairStages * stage + 128;  // + room to align the ring
-      const int64_t grid = std::min<int64_t>(n, 2 * (int64_t)num_sms());
+      const int64_t grid = std::min<int64_t>(n, 3 * (int64_t)num_sms());
       set_smem((const void*)pair_tma_kernel<TS, PH>, sm);
       launch_pdl(pair_tma_kernel<TS, PH>, (unsigned)grid, 256, sm, st, tm, L.D, L.R, L.K, n, list, L.near_j,
                  reinterpret_cast<const float*>(xv), reinterpret_cast<float*>(part), F.err);
