@@ -30,6 +30,45 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Transposed warp sum: every lane holds N values (N a power of two no larger
+// than G, the width of an aligned lane group, a power of two <= 32).  At
+// xor-distance G/2, G/4, ... each lane keeps half of its remaining values
+// and adds its partner's copies of them, then plain steps finish: lane l
+// ends with the group sum of value tsum_index<N, G>(l), after N - 1 + the
+// remaining plain shuffles (instead of N log2 G for N separate sums).
+template <int N, int G, typename T>
+__device__ __forceinline__ T tsum(const T (&v)[N]) {
+  if constexpr (N == 1) {
+    T x = v[0];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  } else {
+    const bool up = threadIdx.x & (G / 2);
+    T w[N / 2];
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) {
+      const T mine = up ? v[q + N / 2] : v[q], other = up ? v[q] : v[q + N / 2];
+      w[q] = mine + __shfl_xor_sync(0xffffffffu, other, G / 2);
+    }
+    return tsum<N / 2, G / 2, T>(w);
+  }
+}
+template <int N, int G>
+__device__ __forceinline__ int tsum_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int n = N, g = G; n > 1; n >>= 1, g >>= 1)
+    if (lane & (g / 2)) idx += n / 2;
+  return idx;
+}
+// lanes holding a distinct tsum result: the first lane of each group of
+// G / N lanes with equal index
+template <int N, int G>
+__device__ __forceinline__ bool tsum_leader(int lane) {
+  return (lane & (G / N - 1)) == 0;
+}
+
 // ys[r] += sign * sum_c M[r*ld + c] xs[c], r < nr, c < nc; row r is owned by
 // warp r % nwarps (so successive calls with the same nr never race).
 template <typename T>
@@ -207,11 +246,17 @@ __device__ __forceinline__ void rows_acc(int r0, const T* __restrict__ M, int64_
 template <typename T, int RPW>
 __device__ __forceinline__ void rows_finish(int r0, int nr, const T (&acc)[RPW], T sign, const T* base, T* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if constexpr (RPW == 16 || RPW == 8) {
+    const T v = tsum<RPW, 32, T>(acc);
+    const int t = tsum_index<RPW, 32>(lane), r = r0 + warp + 8 * t;
+    if (tsum_leader<RPW, 32>(lane) && r < nr) out[r] = (base ? base[r] : T(0)) + sign * v;
+  } else {
 #pragma unroll
-  for (int t = 0; t < RPW; ++t) {
-    const int r = r0 + warp + 8 * t;
-    T v = warp_sum(acc[t]);
-    if (lane == 0 && r < nr) out[r] = (base ? base[r] : T(0)) + sign * v;
+    for (int t = 0; t < RPW; ++t) {
+      const int r = r0 + warp + 8 * t;
+      T v = warp_sum(acc[t]);
+      if (lane == 0 && r < nr) out[r] = (base ? base[r] : T(0)) + sign * v;
+    }
   }
 }
 
@@ -365,11 +410,21 @@ __device__ __forceinline__ void cta_gemv(const TS* __restrict__ M, int64_t ld, i
         }
       }
     }
+    if (cpr == 32) {
+      const T v = tsum<UNR, 32, T>(acc);
+      const int r = rb + tsum_index<UNR, 32>(lane) * nw + warp;
+      if (tsum_leader<UNR, 32>(lane) && r < nr) y[r] = (base ? base[r] : T(0)) + alpha * v;
+    } else if (cpr == 16 && UNR <= 16) {
+      const T v = tsum<UNR, 16, T>(acc);
+      const int r = rb + (tsum_index<UNR, 16>(lane) * nw + warp) * 2 + sub;
+      if (tsum_leader<UNR, 16>(lane) && r < nr) y[r] = (base ? base[r] : T(0)) + alpha * v;
+    } else {
 #pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      for (int o = cpr >> 1; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
-      const int r = rb + (u * nw + warp) * rpi + sub;
-      if (cl == 0 && r < nr) y[r] = (base ? base[r] : T(0)) + alpha * acc[u];
+      for (int u = 0; u < UNR; ++u) {
+        for (int o = cpr >> 1; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+        const int r = rb + (u * nw + warp) * rpi + sub;
+        if (cl == 0 && r < nr) y[r] = (base ? base[r] : T(0)) + alpha * acc[u];
+      }
     }
   }
 }
@@ -1301,12 +1356,12 @@ template <int RPW>
 __device__ __forceinline__ void rows_finish_df(int r0, int nr, const float (&H)[RPW], const float (&L)[RPW],
                                                const double* base, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double d[RPW];
 #pragma unroll
-  for (int t = 0; t < RPW; ++t) {
-    const int r = r0 + warp + 8 * t;
-    const double v = warp_sum((double)H[t] + (double)L[t]);
-    if (lane == 0 && r < nr) out[r] = (base ? base[r] : 0.0) + v;
-  }
+  for (int t = 0; t < RPW; ++t) d[t] = (double)H[t] + (double)L[t];
+  const double v = tsum<RPW, 32, double>(d);
+  const int r = r0 + warp + 8 * tsum_index<RPW, 32>(lane);
+  if (tsum_leader<RPW, 32>(lane) && r < nr) out[r] = (base ? base[r] : 0.0) + v;
 }
 
 __device__ __forceinline__ void df_split(double v, float& h, float& l) {
@@ -1451,6 +1506,7 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_kernel(int D, int64_t npu,
         v[t][h] = (r < D) ? __ldg(reinterpret_cast<const float4*>(M + (int64_t)r * D + lane * 4 + 128 * h))
                           : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    float su[kSymRPW];
 #pragma unroll
     for (int t = 0; t < kSymRPW; ++t) {
       const int r = r0 + 8 * t;
@@ -1467,8 +1523,12 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_kernel(int D, int64_t npu,
         wacc[h][2] = fmaf(v[t][h].z, xr, wacc[h][2]);
         wacc[h][3] = fmaf(v[t][h].w, xr, wacc[h][3]);
       }
-      s = warp_sum(s);
-      if (lane == 0 && r < D) u[r] = s;
+      su[t] = s;
+    }
+    {
+      const float sv = tsum<kSymRPW, 32, float>(su);
+      const int r = r0 + 8 * tsum_index<kSymRPW, 32>(lane);
+      if (tsum_leader<kSymRPW, 32>(lane) && r < D) u[r] = sv;
     }
   }
   if (!both) return;
