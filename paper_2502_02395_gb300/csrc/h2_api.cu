@@ -257,8 +257,6 @@ h2_status setup_device(h2_ctx* c) {
     CKC(dalloc(c, &c->Alo, (size_t)(c->npu * DD)));
     launch_gather_blocks(c->A64, c->sym_q, DD, c->npu, c->A32, 0);
     launch_gather_split_lo(c->A64, c->sym_q, DD, c->npu, c->A32, c->Alo, 0);
-    CKC(dalloc(c, &c->part32, (size_t)c->npu * 2 * lf.D));
-    CKC(dalloc(c, &c->part64, (size_t)c->npu * 2 * lf.D));
   } else {
     CKC(dalloc(c, &c->A32, (size_t)lf.NP * lf.D * lf.D));
     launch_convert<double, float>(c->A64, c->A32, (int64_t)lf.NP * lf.D * lf.D, 0);
@@ -270,14 +268,46 @@ h2_status setup_device(h2_ctx* c) {
   c->X32p.assign(L + 1, nullptr);
   c->S32p.assign(L + 1, nullptr);
   c->Slo.assign(L + 1, nullptr);
+  size_t npart = c->sym ? (size_t)c->npu * 2 * lf.D : 0;
   for (int l = 1; l <= L; ++l) {
     DevLevel& d = c->lv[l];
     const size_t nx = (size_t)d.nb * d.D * d.K, ns = (size_t)std::max<int64_t>(d.FP, 1) * d.K * d.K;
     CKC(dalloc(c, &d.X32, nx));
     CKC(dalloc(c, &d.S32, ns));
-    CKC(dalloc(c, &c->Slo[l], ns));
     launch_convert<double, float>(d.X, d.X32, (int64_t)nx, 0);
     launch_convert<double, float>(d.S, d.S32, (int64_t)ns, 0);
+    d.far_sym = d.FP > 0 && sym_leaf_supported(d.K);
+    if (d.far_sym) {
+      // couplings of a symmetric kernel: S_ji = S_ij^T; keep i < j
+      std::vector<int32_t> fq, fi, fj;
+      for (int64_t q = 0; q < d.FP; ++q)
+        if (d.h_far_i[q] < d.h_far_j[q]) fq.push_back((int32_t)q), fi.push_back(d.h_far_i[q]), fj.push_back(d.h_far_j[q]);
+      d.fpu = (int64_t)fq.size();
+      std::vector<std::vector<std::pair<int32_t, int32_t>>> lists(d.nb);
+      for (int64_t k = 0; k < d.fpu; ++k) {
+        lists[fi[k]].push_back({fj[k], (int32_t)(2 * k)});
+        lists[fj[k]].push_back({fi[k], (int32_t)(2 * k + 1)});
+      }
+      std::vector<int64_t> ptr(d.nb + 1, 0);
+      std::vector<int32_t> ent;
+      for (int i = 0; i < d.nb; ++i) {
+        std::sort(lists[i].begin(), lists[i].end());
+        for (auto& pe : lists[i]) ent.push_back(pe.second);
+        ptr[i + 1] = (int64_t)ent.size();
+      }
+      int32_t* fsq = nullptr;
+      CKS(upload(c, &fsq, fq));
+      CKS(upload(c, &d.fs_i, fi));
+      CKS(upload(c, &d.fs_j, fj));
+      CKS(upload(c, &d.fs_ptr, ptr));
+      CKS(upload(c, &d.fs_ent, ent));
+      const int64_t KK = (int64_t)d.K * d.K;
+      CKC(dalloc(c, &d.S32u, (size_t)(d.fpu * KK)));
+      launch_gather_blocks(d.S, fsq, KK, d.fpu, d.S32u, 0);
+      npart = std::max(npart, (size_t)d.fpu * 2 * d.K);
+    }
+    // the residual's FP32-pair matvec reads the couplings in full
+    CKC(dalloc(c, &c->Slo[l], ns));
     launch_split_lo(d.S, d.S32, c->Slo[l], (int64_t)d.FP * d.K * d.K, 0);
     if (l == L) {
       CKC(dalloc(c, &c->Xlo, nx));
@@ -287,6 +317,10 @@ h2_status setup_device(h2_ctx* c) {
     c->S64p[l] = d.S;
     c->X32p[l] = d.X32;
     c->S32p[l] = d.S32;
+  }
+  if (npart) {
+    CKC(dalloc(c, &c->part32, npart));
+    CKC(dalloc(c, &c->part64, npart));
   }
   CKC(cudaGetLastError());
 
@@ -730,7 +764,17 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
   const std::vector<int64_t>& off = c->hat_off;
   launch_matvec_up<T>(c->lv[L], X[L], x, xh + off[L], st);
   for (int l = L - 1; l >= 1; --l) launch_matvec_up<T>(c->lv[l], X[l], xh + off[l + 1], xh + off[l], st);
-  for (int l = 1; l <= L; ++l) launch_matvec_far<T>(c->lv[l], S[l], xh + off[l], yh + off[l], st);
+  for (int l = 1; l <= L; ++l) {
+    const DevLevel& d = c->lv[l];
+    if constexpr (std::is_same<T, float>::value) {
+      if (d.far_sym) {  // stored halves of the symmetric couplings
+        launch_matvec_sym_pairs(d.K, d.fpu, d.fs_i, d.fs_j, d.S32u, xh + off[l], c->part32, st);
+        launch_matvec_sym_sum<float>(d.nb, d.K, 0, d.fs_ptr, d.fs_ent, nullptr, nullptr, c->part32, yh + off[l], st);
+        continue;
+      }
+    }
+    launch_matvec_far<T>(d, S[l], xh + off[l], yh + off[l], st);
+  }
   for (int l = 1; l < L; ++l) launch_matvec_down<T>(c->lv[l], X[l], yh + off[l], yh + off[l + 1], st);
   leaf(X[L], yh + off[L]);
 }
@@ -761,6 +805,8 @@ void matvec_df(h2_ctx* c, const double* x, double* y) {
   const std::vector<int64_t>& off = c->hat_off;
   launch_matvec_up<double>(c->lv[L], c->X64p[L], x, c->xhat + off[L], st);
   for (int l = L - 1; l >= 1; --l) launch_matvec_up<double>(c->lv[l], c->X64p[l], c->xhat + off[l + 1], c->xhat + off[l], st);
+  // (the couplings in full: the symmetric pair form is slower in FP32-pair
+  // arithmetic at these sizes)
   for (int l = 1; l <= L; ++l)
     launch_matvec_far_df(c->lv[l], c->S32p[l], c->Slo[l], c->xhat + off[l], c->yhat + off[l], st);
   for (int l = 1; l < L; ++l) launch_matvec_down<double>(c->lv[l], c->X64p[l], c->yhat + off[l], c->yhat + off[l + 1], st);

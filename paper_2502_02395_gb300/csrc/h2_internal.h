@@ -120,6 +120,15 @@ struct DevLevel {
   double* S = nullptr;    // FP * K * K couplings G(SK_i, SK_j)
   float* X32 = nullptr;   // FP32 copies for the inner solver of the mixed refinement
   float* S32 = nullptr;
+  // symmetric coupling storage for the FP32 matvec (S_ji = S_ij^T): the far
+  // pairs i < j ("stored"), their FP32 couplings, and per box the list of
+  // partial products (2k: S_k xh_j for i = box, 2k + 1: S_k^T xh_i for
+  // j = box), CSR over boxes
+  bool far_sym = false;
+  int64_t fpu = 0;
+  int32_t *fs_i = nullptr, *fs_j = nullptr, *fs_ent = nullptr;
+  int64_t* fs_ptr = nullptr;
+  float* S32u = nullptr;
   void* S16[2] = {nullptr, nullptr};        // couplings scaled into FP16 [0] / BF16 [1]
   float* S16_scale[2] = {nullptr, nullptr};  // their scale and inverse scale (device)
 };
