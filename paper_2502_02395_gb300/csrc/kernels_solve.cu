@@ -1141,46 +1141,19 @@ H2_INST_SUBST(float, __nv_bfloat16)
 // solver of the mixed-precision refinement.  X, S and A are that level's
 // bases, couplings and leaf near blocks in T.
 
-// upward: xh_i[a] = sum_d X_i[d*K + a] x_i[d] (x_i: the box's D inputs).
-// Warp w takes the rows d = w, w + 8, ...; lanes take the columns a; each
-// warp accumulates its partial sums in its own row of shared memory, then
-// the 8 partial rows are added.
+// upward: xh_i[a] = sum_d X_i[d*K + a] x_i[d] (x_i: the box's D inputs):
+// the column form of the CTA GEMV (warps over d, lanes over 16-byte chunks
+// of a, eight rows of X in flight per lane).
 template <typename T>
 __global__ void __launch_bounds__(256) mv_up_kernel(int D, int K, const T* __restrict__ X, const T* __restrict__ x,
                                                     T* __restrict__ xh) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* part = reinterpret_cast<T*>(smraw);  // 8 * K
   T* sx = part + 8 * K;                   // D
-  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T* Xb = X + (int64_t)i * D * K;
+  const int i = blockIdx.x, tid = threadIdx.x;
   for (int e = tid; e < D; e += 256) sx[e] = x[(int64_t)i * D + e];
-  for (int e = tid; e < 8 * K; e += 256) part[e] = T(0);
   __syncthreads();
-  T* mine = part + warp * K;
-  for (int a0 = 0; a0 < K; a0 += 128) {
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    for (int d = warp; d < D; d += 8) {
-      const T xd = sx[d];
-      const T* row = Xb + (int64_t)d * K + a0;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int a = a0 + lane + 32 * q;
-        if (a < K) acc[q] = fma(__ldg(row + lane + 32 * q), xd, acc[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int a = a0 + lane + 32 * q;
-      if (a < K) mine[a] = acc[q];
-    }
-  }
-  __syncthreads();
-  for (int a = tid; a < K; a += 256) {
-    T s = T(0);
-#pragma unroll
-    for (int w = 0; w < 8; ++w) s += part[w * K + a];
-    xh[(int64_t)i * K + a] = s;
-  }
+  cta_gemv_cols<T, T>(X + (int64_t)i * D * K, K, K, D, sx, part, xh + (int64_t)i * K);
 }
 template <typename T>
 void launch_matvec_up(const DevLevel& L, const T* X, const T* x, T* xh, cudaStream_t st) {
@@ -1630,6 +1603,7 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
         vl[t][h] = (r < D) ? __ldg(reinterpret_cast<const float4*>(Ml + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+    double su[RPW];
 #pragma unroll
     for (int t = 0; t < RPW; ++t) {
       const int r = r0 + 8 * t;
@@ -1645,8 +1619,12 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
           if (both) df_fma(wH[h][e], wL[h][e], mh[e], ml[e], xrh, xrl);
         }
       }
-      const double s = warp_sum((double)H + (double)L);
-      if (lane == 0 && r < D) u[r] = s;
+      su[t] = (double)H + (double)L;
+    }
+    {
+      const double sv = tsum<RPW, 32, double>(su);
+      const int r = r0 + 8 * tsum_index<RPW, 32>(lane);
+      if (tsum_leader<RPW, 32>(lane) && r < D) u[r] = sv;
     }
   }
   if (!both) return;
