@@ -319,6 +319,7 @@ def main():
     sampler.start()
     ph = {p: 0.0 for p in PHASES + SOLVE_PHASES}
     ph["factor"] = 0.0
+    ph["factor_wait_basis"] = 0.0
     ph["solve"] = 0.0
     t_leaf = 0.0
     e0 = torch.cuda.Event(enable_timing=True)
@@ -335,6 +336,7 @@ def main():
         for p in PHASES + SOLVE_PHASES:
             ph[p] += s["times"][p]
         ph["factor"] += s["times"]["factor"]
+        ph["factor_wait_basis"] += s["times"].get("wait_basis", 0.0)
         t_leaf += s["times"]["matvec32_leaf"]
         ph["solve"] += s["times"]["solve"]
         rels.append(rel)

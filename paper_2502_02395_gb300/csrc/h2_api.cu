@@ -345,13 +345,12 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   if (!F.lv.empty()) return H2_OK;
   const int L = c->L;
   F.lv.assign(L + 1, FacLevel<T>());
-  size_t wk = 0, wk16 = 0;
+  size_t wk = 0, wk16 = 0, wq = 0, wc = 0, wc16 = 0;
   for (int l = 0; l <= L; ++l) {
     const DevLevel& d = c->lv[l];
     FacLevel<T>& f = F.lv[l];
     const size_t nb = d.nb, D = d.D, K = d.K, R = d.R;
     wk = std::max(wk, (size_t)d.NP * D * D);
-    wk = std::max(wk, (size_t)d.FP * K * K);
     const bool mixed = !std::is_same<T, double>::value;
     f.tc = mixed && l >= 1 && gemm_tc_supported(d.D, d.D, d.D, d.D, d.D, d.D);
     bool leaf64 = (l == L) && !mixed;
@@ -367,7 +366,9 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     f.tc_coup = mixed && d.FP > 0 && gemm_tc_supported(d.K, d.K, d.K, d.K, d.K, d.K);
     if (f.tc_coup) {
       CKC(dalloc(c, reinterpret_cast<uint16_t**>(&f.T16), nb * K * K));
-      wk16 = std::max(wk16, (size_t)d.FP * K * K);
+      wc16 = std::max(wc16, (size_t)d.FP * K * K);
+    } else {
+      wc = std::max(wc, (size_t)d.FP * K * K);
     }
     CKC(dalloc(c, &f.U, nb * D * D));
     CKC(dalloc(c, &f.Ur, nb * D * D));
@@ -377,7 +378,7 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     CKC(dalloc(c, &f.tau, nb * std::max<size_t>(K, 1)));
     CKC(dalloc(c, &f.Tw, nb * K * K));
     if (sizeof(T) * D * K > 200 * 1024) CKC(dalloc(c, &f.Qs, nb * D * K));
-    wk = std::max(wk, nb * (K * K + D * K));
+    wq = std::max(wq, nb * (K * K + D * K));
     CKC(dalloc(c, &f.Ahat, (size_t)d.NP * D * D));
     if (f.tc) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&f.Ahat16), (size_t)d.NP * D * D));
     CKC(dalloc(c, &f.Shat, (size_t)std::max<int64_t>(d.FP, 1) * K * K));
@@ -391,7 +392,8 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
     }
     CKC(dalloc(c, &f.Ainv, nb * R * R));
     CKC(dalloc(c, &f.piv, nb * R));
-    for (T** p : {&f.vin, &f.c, &f.xs, &f.z}) CKC(dalloc(c, p, nb * D));
+    for (T** p : {&f.vin, &f.c, &f.xs}) CKC(dalloc(c, p, nb * D));
+    CKC(dalloc(c, &f.M1, std::max<size_t>(nb * R * D, 1)));
     for (T** p : {&f.u, &f.v, &f.om}) CKC(dalloc(c, p, nb * std::max<size_t>(R, 1)));
   }
   const int D0 = c->lv[0].D;
@@ -404,10 +406,13 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   for (int l = 1; l <= L; ++l) F.lv[l].part = F.part;
   CKC(dalloc(c, &F.Wk, wk));
   if (wk16) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&F.W16), wk16));
+  CKC(dalloc(c, &F.Wq, std::max<size_t>(wq, 1)));
+  if (wc) CKC(dalloc(c, &F.Wc, wc));
+  if (wc16) CKC(dalloc(c, reinterpret_cast<uint16_t**>(&F.W16c), wc16));
   CKC(dalloc(c, &F.scales, 2 * (size_t)(L + 1)));
   CKC(dalloc(c, &F.tscale, 2 * (size_t)(L + 1)));
   CKC(dalloc(c, &F.cscale, (size_t)(L + 1)));
-  CKC(dalloc(c, &F.amax, (size_t)(L + 1)));
+  CKC(dalloc(c, &F.amax, 2 * (size_t)(L + 1)));
   if (std::is_same<T, double>::value) {
     CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
     F.root_luT = reinterpret_cast<T*>(F.root_lu);
@@ -429,20 +434,59 @@ void gemm(int prec, int M, int N, int K, const T* A, int64_t sA, const int32_t* 
   gemm_simt<T, T>(M, N, K, A, sA, ia, lda, tA, B, sB, ib, ldb, tB, C, sC, ic, ldc, alpha, beta, batch, st);
 }
 
+// The factorization runs on two streams.  The basis stream computes, level
+// by level, what depends only on the bases: the complement bases (a1: QR of
+// X^orth, which needs the children's T only), their 16-bit copy and the
+// projected couplings (a2': T_i S_ij T_j^T).  The context's stream runs the
+// chain through the matrix entries (a2 projection, a3 inverses, a4/a5
+// Schur updates, a6 merge), waiting for level l's bases before a2 and for
+// its couplings before a6.  The two chains share no buffer.
 template <typename T>
 h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   CKS(alloc_factor(c, F));
   const int L = c->L;
   cudaStream_t st = c->stream;
+  if (!c->basis_stream) {
+    // the highest priority: the other chain waits for each level's bases
+    int least = 0, greatest = 0;
+    CKC(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CKC(cudaStreamCreateWithPriority(&c->basis_stream, cudaStreamNonBlocking, greatest));
+    CKC(cudaStreamCreateWithPriority(&c->coupling_stream, cudaStreamNonBlocking, greatest));
+    CKC(cudaStreamCreateWithPriority(&c->product_stream, cudaStreamNonBlocking, least));
+  }
+  cudaStream_t sb = c->basis_stream, sc = c->coupling_stream, sp = c->product_stream;
   CKC(cudaMemsetAsync(c->status, 0, 4 * sizeof(int32_t), st));
-  std::vector<cudaEvent_t> ev;
-  auto mark = [&]() {
+  // timing marks: ev on the context's stream, evb on the basis stream
+  std::vector<cudaEvent_t> ev, evb, sync;
+  auto mark_on = [&](std::vector<cudaEvent_t>& v, cudaStream_t s) {
     cudaEvent_t e;
     cudaEventCreate(&e);
-    cudaEventRecord(e, st);
-    ev.push_back(e);
+    cudaEventRecord(e, s);
+    v.push_back(e);
   };
-  // phase boundaries per level: [start, a1, a2, a3, a45, a2c, a6]
+  auto mark = [&]() { mark_on(ev, st); };
+  // s2 waits for everything issued so far on s1
+  auto wait_for = [&](cudaStream_t s1, cudaStream_t s2) {
+    cudaEvent_t e;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventRecord(e, s1);
+    cudaStreamWaitEvent(s2, e, 0);
+    sync.push_back(e);
+  };
+  auto release = [&]() {
+    for (auto e : ev) cudaEventDestroy(e);
+    for (auto e : evb) cudaEventDestroy(e);
+    for (auto e : sync) cudaEventDestroy(e);
+  };
+  auto fail = [&](h2_status code, const std::string& msg) {
+    c->err = msg;
+    cudaStreamSynchronize(sb);
+    cudaStreamSynchronize(sc);
+    cudaStreamSynchronize(sp);
+    cudaStreamSynchronize(st);
+    release();
+    return code;
+  };
   mark();
   const int bf16 = (prec == H2_PREC_BF16) ? 1 : 0;
   F.bf16 = bf16;
@@ -450,6 +494,11 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   bool any_tc = false;
   for (int l = 1; l <= L; ++l) any_tc = any_tc || F.lv[l].tc || F.lv[l].tc_coup;
   if (mixed && any_tc) CKS(make_leaf_lowp(c, bf16));
+  // the basis stream starts after earlier work on the context's stream (a
+  // solve may still read U; the 16-bit couplings are made there)
+  wait_for(st, sb);
+  wait_for(st, sc);
+  wait_for(st, sp);
   mark();
   const T* Aleaf = nullptr;
   if (!mixed) {
@@ -459,11 +508,15 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     Aleaf = F.lv[L].Ain;
   }
   mark();
+
+  // ---- basis stream: a1 (and the 16-bit copy of U), a2' per level
+  std::string coup_err;
   for (int l = L; l >= 1; --l) {
     const DevLevel& d = c->lv[l];
     FacLevel<T>& f = F.lv[l];
     const int D = d.D, K = d.K, R = d.R;
     const int64_t DD = (int64_t)D * D;
+    mark_on(evb, sb);
     // a1: complement bases.  X^orth = X (leaf) or blockdiag(T_2p, T_2p+1) X,
     // then Householder QR, the compact WY factor and U = P (I - V Tw V^T).
     {
@@ -477,38 +530,83 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
         const T* Tc = F.lv[l + 1].Tm;
         const int64_t KcKc = (int64_t)Kc * Kc;
         gemm<T>(prec, Kc, K, Kc, Tc, 2 * KcKc, nullptr, Kc, false, Xc, DK, nullptr, K, false, f.Xo, DK, nullptr, K,
-                T(1), T(0), nb, st);
+                T(1), T(0), nb, sb);
         gemm<T>(prec, Kc, K, Kc, Tc + KcKc, 2 * KcKc, nullptr, Kc, false, Xc + (int64_t)Kc * K, DK, nullptr, K,
-                false, f.Xo + (int64_t)Kc * K, DK, nullptr, K, T(1), T(0), nb, st);
+                false, f.Xo + (int64_t)Kc * K, DK, nullptr, K, T(1), T(0), nb, sb);
         Xin = f.Xo;
       }
-      launch_qr_panel<T>(nb, D, K, Xin, f.Vq, f.tau, f.Tm, f.Qs, st);
-      T* Sb = F.Wk;
-      T* W1 = F.Wk + (int64_t)nb * KK;
+      launch_qr_panel<T>(nb, D, K, Xin, f.Vq, f.tau, f.Tm, f.Qs, sb);
+      T* Sb = F.Wq;
+      T* W1 = F.Wq + (int64_t)nb * KK;
       if (K > 0) {
         gemm<T>(prec, K, K, D, f.Vq, DK, nullptr, D, false, f.Vq, DK, nullptr, D, true, Sb, KK, nullptr, K, T(1), T(0),
-                nb, st);
-        launch_wy_tfactor<T>(nb, K, Sb, f.tau, f.Tw, st);
+                nb, sb);
+        launch_wy_tfactor<T>(nb, K, Sb, f.tau, f.Tw, sb);
         gemm<T>(prec, D, K, K, f.Vq, DK, nullptr, D, true, f.Tw, KK, nullptr, K, false, W1, DK, nullptr, K, T(1), T(0),
-                nb, st);
+                nb, sb);
       }
-      launch_perm_identity<T>(nb, D, K, f.U, st);
+      launch_perm_identity<T>(nb, D, K, f.U, sb);
       if (K > 0) {
         if (R > 0)
           gemm<T>(prec, R, D, K, f.Vq + K, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U, DD, nullptr, D, T(-1),
-                  T(1), nb, st);
+                  T(1), nb, sb);
         gemm<T>(prec, K, D, K, f.Vq, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U + (int64_t)R * D, DD, nullptr,
-                D, T(-1), T(1), nb, st);
+                D, T(-1), T(1), nb, sb);
       }
-      launch_transpose_blocks<T>(nb, D, f.U, f.Ur, st);
+      launch_transpose_blocks<T>(nb, D, f.U, f.Ur, sb);
+      if (f.tc) launch_to_lowp<T>(bf16, f.U, f.U16, (int64_t)d.nb * DD, nullptr, sb);
     }
+    mark_on(evb, sb);
+    // the couplings of level l follow its bases on the coupling stream
+    CKC(cudaStreamWaitEvent(sc, evb.back(), 0));
+    mark_on(evb, sc);
+    // a2': couplings Shat_ij = T_i S_ij T_j^T
+    if (d.FP > 0 && K > 0 && f.tc_coup) {
+      // tensor cores: V^T = (S_s T_j,s^T)^T in 16 bits, then Shat = T_i,s V / (s_S s_T^2)
+      const int64_t KK = (int64_t)K * K;
+      unsigned int* am = F.amax + (L + 1) + l;
+      CKC(cudaMemsetAsync(am, 0, sizeof(unsigned int), sc));
+      launch_amax_blocks<T>(f.Tm, d.nb, KK, K, K, K, am, sc);
+      launch_pow2_scale(am, std::sqrt(32768.0f / K), F.tscale + 2 * l, sc);
+      launch_to_lowp<T>(bf16, f.Tm, f.T16, d.nb * KK, F.tscale + 2 * l, sc);
+      launch_inv_scale_product(d.S16_scale[bf16], F.tscale + 2 * l, F.cscale + l, sc);
+      bool ok = gemm_tc(bf16, K, K, K, d.S16[bf16], d.FP, K, K, nullptr, f.T16, d.nb, K, K, d.far_j, F.W16c, KK,
+                        nullptr, K, 1, bf16, 1.0f, nullptr, d.FP, c->status + 2, sc) &&
+                gemm_tc(bf16, K, K, K, f.T16, d.nb, K, K, d.far_i, F.W16c, d.FP, K, K, nullptr, f.Shat, KK, nullptr, K,
+                        0, 0, 1.0f, F.cscale + l, d.FP, c->status + 2, sc);
+      if (!ok) {
+        coup_err = "tensor-core coupling GEMM setup failed at level " + std::to_string(l);
+        break;
+      }
+    } else if (d.FP > 0 && K > 0) {
+      const int64_t KK = (int64_t)K * K;
+      const T* Sc = std::is_same<T, double>::value ? reinterpret_cast<const T*>(d.S) : reinterpret_cast<const T*>(d.S32);
+      gemm<T>(prec, K, K, K, Sc, KK, nullptr, K, false, f.Tm, KK, d.far_j, K, true, F.Wc, KK, nullptr, K, T(1),
+              T(0), d.FP, sc);
+      gemm<T>(prec, K, K, K, f.Tm, KK, d.far_i, K, false, F.Wc, KK, nullptr, K, false, f.Shat, KK, nullptr, K, T(1),
+              T(0), d.FP, sc);
+    }
+    mark_on(evb, sc);
+  }
+  if (!coup_err.empty()) return fail(H2_ERR_CUDA, coup_err);
+  // evb holds four marks per level: [a1 start, a1 end = bases ready (basis
+  // stream), a2' start, a2' end = couplings ready (coupling stream)]
+  auto evb_at = [&](int l, int k) { return evb[(size_t)(L - l) * 4 + k]; };
+
+  // ---- the context's stream: a2, a3, a4/a5, a6 per level
+  for (int l = L; l >= 1; --l) {
+    const DevLevel& d = c->lv[l];
+    FacLevel<T>& f = F.lv[l];
+    const int D = d.D, K = d.K, R = d.R;
+    const int64_t DD = (int64_t)D * D;
+    mark();
+    CKC(cudaStreamWaitEvent(st, evb_at(l, 1), 0));
     mark();
     // a2: Ahat_ij = U_i^T A_ij U_j
     if (f.tc) {
       // tensor cores: W^T = (s A_ij) U_j in 16 bits, then Ahat_ij = U_i^T W / s in FP32
       const void* A16 = (l == L) ? c->A16[bf16] : f.Ain16;
       const float* sc = (l == L) ? c->A16_scale[bf16] : F.scales + 2 * l;
-      launch_to_lowp<T>(bf16, f.U, f.U16, (int64_t)d.nb * DD, nullptr, st);
       // The second GEMM also writes its raw accumulator s * Ahat in 16 bits
       // for the substitution.  |s Ahat_ij| <= ||s A_ij||_2 <= 128 D, inside
       // the FP16 range for D <= 256 (BF16 has the FP32 exponent range).
@@ -533,10 +631,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       // off-diagonal pairs then keep only SS in FP32 (the merge's input);
       // their RR, RS and SR live in the 16-bit copy (the substitution's)
       f.ahat_ss_only = sub16 && R % 16 == 0;
-      if (!ok) {
-        c->err = "tensor-core GEMM setup failed at level " + std::to_string(l);
-        return H2_ERR_CUDA;
-      }
+      if (!ok) return fail(H2_ERR_CUDA, "tensor-core GEMM setup failed at level " + std::to_string(l));
     } else {
       const T* Ain = (l == L) ? Aleaf : f.Ain;
       gemm<T>(prec, D, D, D, Ain, DD, nullptr, D, false, f.U, DD, d.near_j, D, true, F.Wk, DD, nullptr, D, T(1),
@@ -545,9 +640,16 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
               T(0), d.NP, st);
     }
     mark();
-    // a3: FP64 LU of Ahat_ii^RR and its inverse
+    // a3: LU of Ahat_ii^RR and its inverse
     launch_lu_inverse<T>(d.nb, D, R, f.Ahat, d.diag_pair, f.lu, f.luT, f.piv, f.Ainv, c->status, l, st);
     mark();
+    // the substitution's first product M1 = Ainv (U^R)^T, beside the chain
+    // ((U^R)^T: the first R columns of the column-major U, as rows)
+    if (R > 0) {
+      wait_for(st, sp);
+      gemm<T>(prec, R, D, R, f.Ainv, (int64_t)R * R, nullptr, R, false, f.U, DD, nullptr, D, false, f.M1,
+              (int64_t)R * D, nullptr, D, T(1), T(0), d.nb, sp);
+    }
     // a4 + a5: Z = Ainv Ahat_ii^RS; Ahat_ii^SS -= Ahat_ii^SR Z
     if (R > 0 && K > 0) {
       gemm<T>(prec, R, K, R, f.Ainv, (int64_t)R * R, nullptr, R, false, f.Ahat + R, DD, d.diag_pair, D, false, f.Z,
@@ -556,32 +658,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
               false, f.Ahat + (int64_t)R * D + R, DD, d.diag_pair, D, T(-1), T(1), d.nb, st);
     }
     mark();
-    // a2': couplings Shat_ij = T_i S_ij T_j^T
-    if (d.FP > 0 && K > 0 && f.tc_coup) {
-      // tensor cores: V^T = (S_s T_j,s^T)^T in 16 bits, then Shat = T_i,s V / (s_S s_T^2)
-      const int64_t KK = (int64_t)K * K;
-      unsigned int* am = F.amax + l;
-      CKC(cudaMemsetAsync(am, 0, sizeof(unsigned int), st));
-      launch_amax_blocks<T>(f.Tm, d.nb, KK, K, K, K, am, st);
-      launch_pow2_scale(am, std::sqrt(32768.0f / K), F.tscale + 2 * l, st);
-      launch_to_lowp<T>(bf16, f.Tm, f.T16, d.nb * KK, F.tscale + 2 * l, st);
-      launch_inv_scale_product(d.S16_scale[bf16], F.tscale + 2 * l, F.cscale + l, st);
-      bool ok = gemm_tc(bf16, K, K, K, d.S16[bf16], d.FP, K, K, nullptr, f.T16, d.nb, K, K, d.far_j, F.W16, KK,
-                        nullptr, K, 1, bf16, 1.0f, nullptr, d.FP, c->status + 2, st) &&
-                gemm_tc(bf16, K, K, K, f.T16, d.nb, K, K, d.far_i, F.W16, d.FP, K, K, nullptr, f.Shat, KK, nullptr, K,
-                        0, 0, 1.0f, F.cscale + l, d.FP, c->status + 2, st);
-      if (!ok) {
-        c->err = "tensor-core coupling GEMM setup failed at level " + std::to_string(l);
-        return H2_ERR_CUDA;
-      }
-    } else if (d.FP > 0 && K > 0) {
-      const int64_t KK = (int64_t)K * K;
-      const T* Sc = std::is_same<T, double>::value ? reinterpret_cast<const T*>(d.S) : reinterpret_cast<const T*>(d.S32);
-      gemm<T>(prec, K, K, K, Sc, KK, nullptr, K, false, f.Tm, KK, d.far_j, K, true, F.Wk, KK, nullptr, K, T(1),
-              T(0), d.FP, st);
-      gemm<T>(prec, K, K, K, f.Tm, KK, d.far_i, K, false, F.Wk, KK, nullptr, K, false, f.Shat, KK, nullptr, K, T(1),
-              T(0), d.FP, st);
-    }
+    CKC(cudaStreamWaitEvent(st, evb_at(l, 3), 0));
     mark();
     // a6: merge into the parent level's near blocks
     FacLevel<T>& pf = F.lv[l - 1];
@@ -604,6 +681,8 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     }
     mark();
   }
+  if (L >= 1) CKC(cudaStreamWaitEvent(st, evb.back(), 0));
+  wait_for(sp, st);
   // a7: root
   const int D0 = c->lv[0].D;
   const T* Aroot = (L == 0) ? Aleaf : F.lv[0].Ain;
@@ -619,20 +698,31 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     cudaEventElapsedTime(&ms, ev[a], ev[b]);
     return (double)ms * 1e-3;
   };
+  auto elb = [&](int a, int b) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, evb[a], evb[b]);
+    return (double)ms * 1e-3;
+  };
+  // main-stream marks: [start, leaf copies, leaf conversion], then per level
+  // [wait start, a2 start, a2 end, a3 end, a4/a5 end, a6 start, a6 end], then
+  // the root.  The basis-stream phases (a1, a2') overlap the others; the
+  // main stream's waits for them are wait_basis.
   t.a2_proj += el(1, 2);  // leaf conversion counted with the projection
-  int k = 2;
+  int k = 3;
   for (int l = L; l >= 1; --l) {
-    t.a1_qr += el(k, k + 1);
+    const int kb = (L - l) * 4;
+    t.a1_qr += elb(kb, kb + 1);
+    t.a2c_coupling += elb(kb + 2, kb + 3);
+    t.wait_basis += el(k, k + 1) + el(k + 4, k + 5);
     t.a2_proj += el(k + 1, k + 2);
     t.a3_lu += el(k + 2, k + 3);
     t.a5_schur += el(k + 3, k + 4);
-    t.a2c_coupling += el(k + 4, k + 5);
     t.a6_merge += el(k + 5, k + 6);
-    k += 6;
+    k += 7;
   }
-  t.a7_root = el(k, k + 1);
-  t.total_factor = el(1, k + 1);
-  for (auto e : ev) cudaEventDestroy(e);
+  t.a7_root = el(k - 1, k);
+  t.total_factor = el(1, k);
+  release();
   int32_t stw[4];
   CKC(cudaMemcpy(stw, c->status, sizeof(stw), cudaMemcpyDeviceToHost));
   if (stw[2] != 0) {
@@ -676,12 +766,22 @@ void ulv_sweep(h2_ctx* c, Factor<T>& F) {
   for (int l = L; l >= 1; --l) {
     const DevLevel& d = c->lv[l];
     FacLevel<T>& f = F.lv[l];
-    T* pv = (l > 1) ? F.lv[l - 1].vin : F.root_vec;
-    launch_fwd1<T>(d, f, f.Ainv, st);
+    // below the leaf level the input comes from the children's SR sums
+    ChildIn<T> ch;
+    if (l < L) {
+      const DevLevel& dc = c->lv[l + 1];
+      const FacLevel<T>& fc = F.lv[l + 1];
+      ch.c = fc.c;
+      ch.part = fc.part;
+      ch.ptr = dc.near_ptr;
+      with_ahat(fc, F.bf16, [&](auto, const float* isc) { ch.iscale = isc; });
+      ch.D = dc.D, ch.R = dc.R, ch.K = dc.K;
+    }
+    launch_fwd1<T>(d, f, ch, st);
     with_ahat(f, F.bf16, [&](auto A, const float* isc) {
       using TS = std::remove_const_t<std::remove_pointer_t<decltype(A)>>;
       launch_fwd2<T, TS>(d, f, A, isc, st);
-      launch_fwd3<T, TS>(d, f, A, isc, pv, st);
+      launch_fwd3<T, TS>(d, f, A, isc, l == 1 ? F.root_vec : nullptr, st);
     });
   }
   launch_gemv_rows<T>(c->lv[0].D, F.root_inv, F.root_vec, F.root_x, st);
@@ -747,7 +847,7 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
       if (c->sym) {
         const DevLevel& lf = c->lv[L];
         if (leaf_ev) cudaEventRecord(e0, st);
-        launch_matvec_sym_pairs(lf.D, c->npu, c->sym_i, c->sym_j, A, x, c->part32, st);
+        launch_matvec_sym_pairs(lf.D, c->npu, c->sym_i, c->sym_j, A, x, c->part32, false, st);
         if (leaf_ev) cudaEventRecord(e1, st), leaf_ev->push_back({e0, e1});
         launch_matvec_sym_sum<float>(lf.nb, lf.D, L ? lf.K : 0, c->sym_ptr, c->sym_ent, XL, yhL, c->part32, y, st);
         return;
@@ -768,7 +868,7 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
     const DevLevel& d = c->lv[l];
     if constexpr (std::is_same<T, float>::value) {
       if (d.far_sym) {  // stored halves of the symmetric couplings
-        launch_matvec_sym_pairs(d.K, d.fpu, d.fs_i, d.fs_j, d.S32u, xh + off[l], c->part32, st);
+        launch_matvec_sym_pairs(d.K, d.fpu, d.fs_i, d.fs_j, d.S32u, xh + off[l], c->part32, true, st);
         launch_matvec_sym_sum<float>(d.nb, d.K, 0, d.fs_ptr, d.fs_ent, nullptr, nullptr, c->part32, yh + off[l], st);
         continue;
       }
@@ -1433,7 +1533,7 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     << ",\"a45_schur\":" << fl_schur << ",\"a2c_coupling\":" << fl_coup << "}";
   o << ",\"times\":{\"a1_qr\":" << t.a1_qr << ",\"a2_proj\":" << t.a2_proj << ",\"a3_lu\":" << t.a3_lu
     << ",\"a45_schur\":" << t.a5_schur << ",\"a2c_coupling\":" << t.a2c_coupling << ",\"a6_merge\":" << t.a6_merge
-    << ",\"a7_root\":" << t.a7_root << ",\"factor\":" << t.total_factor << ",\"solve\":" << t.solve_total
+    << ",\"a7_root\":" << t.a7_root << ",\"wait_basis\":" << t.wait_basis << ",\"factor\":" << t.total_factor << ",\"solve\":" << t.solve_total
     << ",\"solve_subst\":" << t.subst << ",\"solve_matvec\":" << t.matvec << ",\"solve_matvec32\":" << t.matvec32
     << ",\"matvec32_leaf\":" << t.leaf32
     << "},\"calls\":{\"subst\":" << t.n_subst << ",\"matvec\":" << t.n_matvec << ",\"matvec32\":" << t.n_matvec32 << ",\"matvec32_leaf\":" << t.n_leaf32
@@ -1535,6 +1635,11 @@ const char* h2_last_error(const h2_ctx* c) { return c ? c->err.c_str() : g_last_
 
 void h2_destroy(h2_ctx* c) {
   if (!c) return;
+  for (cudaStream_t s : {c->basis_stream, c->coupling_stream, c->product_stream}) {
+    if (!s) continue;
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
   for (void* p : c->allocs) cudaFree(p);
   delete c;
 }

@@ -151,10 +151,10 @@ struct FacLevel {
   double* lu = nullptr;    // nb * R * R  LU of Ahat_ii^RR, column-major (FP64 factorization only)
   T* luT = nullptr;        // nb * R * R  the same factors in T (aliases lu when T is double)
   T* Ainv = nullptr;       // nb * R * R  (Ahat_ii^RR)^-1, row-major
+  T* M1 = nullptr;         // nb * R * D  Ainv (U^R)^T, row-major (the substitution's first product)
   int32_t* piv = nullptr;  // nb * R (LAPACK-style row interchanges)
   // substitution vectors
   T *vin = nullptr, *c = nullptr, *u = nullptr, *v = nullptr, *om = nullptr, *xs = nullptr;
-  T* z = nullptr;  // nb * D: [x^R; x^S] of each box before x = U z
   // per-pair partial products of the substitution (Factor::part, shared by
   // all levels)
   T* part = nullptr;
@@ -190,17 +190,23 @@ struct Factor {
   T* root_x = nullptr;        // D0
   T* Wk = nullptr;            // workspace: max NP * D * D
   void* W16 = nullptr;        // 16-bit workspace: max NP * D * D (tensor-core path)
+  // workspaces of the basis stream (complement bases and couplings run
+  // there, beside the projection / LU / merge chain)
+  T* Wq = nullptr;            // max nb * (K * K + D * K): Gram matrix and V Tw
+  T* Wc = nullptr;            // max FP * K * K: SIMT coupling products
+  void* W16c = nullptr;       // max FP * K * K: 16-bit coupling products
   T* part = nullptr;          // max NP * max(R, K): partial products of the substitution
   float* scales = nullptr;    // 2 (L + 1): per-level operand scale and its inverse
   float* tscale = nullptr;    // 2 (L + 1): scale of T16 and its inverse
   float* cscale = nullptr;    // L + 1: 1 / (scale(S16) scale(T16)^2) for the couplings
-  unsigned int* amax = nullptr;  // L + 1 max-abs accumulators
+  unsigned int* amax = nullptr;  // 2 (L + 1) max-abs accumulators: [l] merge, [L + 1 + l] couplings
   int bf16 = -1;              // operand type the 16-bit buffers hold
 };
 
 struct PhaseTimes {
   double a1_qr = 0, a2_proj = 0, a3_lu = 0, a5_schur = 0, a2c_coupling = 0, a6_merge = 0,
          a7_root = 0, total_factor = 0;
+  double wait_basis = 0;  // the main factorization stream waiting for the basis stream
   double solve_total = 0, subst = 0, matvec = 0;
   double matvec32 = 0, leaf32 = 0;
   int iters = 0, n_subst = 0, n_matvec = 0, n_matvec32 = 0, n_leaf32 = 0, method = 0;
@@ -219,6 +225,9 @@ struct h2_ctx {
   int64_t N = 0;
   int dev = 0;
   cudaStream_t stream = nullptr;
+  // the factorization's basis, coupling and substitution-product streams
+  // (created on first use)
+  cudaStream_t basis_stream = nullptr, coupling_stream = nullptr, product_stream = nullptr;
   // device geometry and vectors
   double* pts = nullptr;         // N * 3
   int64_t* slot_pt = nullptr;    // nbL * DL: original index of each padded leaf slot, -1 pad

@@ -65,8 +65,20 @@ void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_
 // refinement vector operations
 // Ahat of level L in storage type TS (T itself, or 16-bit scaled by s with
 // iscale -> 1/s on the device; iscale NULL means 1)
+// The children of a level's boxes as the first forward step reads them:
+// c (nb_c * D), the SR pair sums in part, the near-pair ranges ptr, the
+// 16-bit scale of Ahat (NULL: 1) and the child level's D, R, K.  c NULL:
+// the input is the level's own vin (leaf level).
 template <typename T>
-void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st);
+struct ChildIn {
+  const T* c = nullptr;
+  const T* part = nullptr;
+  const int64_t* ptr = nullptr;
+  const float* iscale = nullptr;
+  int D = 0, R = 0, K = 0;
+};
+template <typename T>
+void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const ChildIn<T>& ch, cudaStream_t st);
 template <typename T, typename TS>
 void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, cudaStream_t st);
 template <typename T, typename TS>
@@ -102,8 +114,9 @@ void launch_split_lo(const double* a, const float* hi, float* lo, int64_t n, cud
 // per stored pair k = (ui[k], uj[k]) the partial products [A x_j; A^T x_i]
 // into part (2 D per pair), then per box y = X yh + its partial products.
 bool sym_leaf_supported(int D);  // D = 128 or 256
+// (pdl: launched to overlap its predecessor; off where events bracket it)
 void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A, const float* x,
-                             float* part, cudaStream_t st);
+                             float* part, bool pdl, cudaStream_t st);
 void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
                                 const float* Al, const double* x, double* part, cudaStream_t st);
 template <typename T>

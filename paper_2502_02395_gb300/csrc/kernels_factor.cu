@@ -475,6 +475,35 @@ __global__ void __launch_bounds__(256) wy_tfactor_kernel(int K, const T* __restr
   for (int e = tid; e < K * K; e += blockDim.x) out[e] = Ts[e];
 }
 
+// C[r0.., c0..] = alpha A B for the 4 x 4 tile at (r0, c0) of an h x h
+// product of shared-memory operands (row-major, leading dimensions lda, ldb,
+// ldc).
+template <typename T>
+__device__ __forceinline__ void smem_mm4(const T* A, int lda, const T* B, int ldb, T* C, int ldc, int h, T alpha,
+                                         int r0, int c0) {
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 4
+  for (int k = 0; k < h; ++k) {
+    T a[4], bv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = A[(r0 + i) * lda + k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bv[j] = B[k * ldb + c0 + j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) C[(r0 + i) * ldc + c0 + j] = alpha * acc[i][j];
+}
+
 // The same factor from the identity Tw^-1 = striu(S) + diag(1 / tau) of the
 // compact WY form (tau_k = 0, a reflector equal to I, gives a zero row and
 // column k of Tw: M is made the identity there and Tw_kk set to 0).  M is
@@ -482,7 +511,8 @@ __global__ void __launch_bounds__(256) wy_tfactor_kernel(int K, const T* __restr
 // inverted in shared memory by recursive 2 x 2 blocking: the 8 x 8
 // diagonal blocks by back substitution (one thread per column), then for
 // b = 16 .. Kp every diagonal block [T11 T12; 0 T22] gets
-// T12 = -T11 (M12 T22) from its two already inverted halves.
+// T12 = -T11 (M12 T22) from its two already inverted halves (dense 4 x 4
+// register-tiled products; the zeros of the triangles are multiplied too).
 template <typename T>
 __global__ void __launch_bounds__(256) wy_tinv_kernel(int K, int Kp, const T* __restrict__ S,
                                                       const T* __restrict__ tau, T* __restrict__ Tw) {
@@ -529,26 +559,21 @@ __global__ void __launch_bounds__(256) wy_tinv_kernel(int K, int Kp, const T* __
     }
     __syncthreads();
   }
+  // the block products in 4 x 4 register tiles, one per thread
   for (int b = 16; b <= Kp; b *= 2) {
-    const int h = b / 2, nb = Kp / b, hh = h * h;
-    // X_q = M12 T22 (T22 upper triangular)
-    for (int e = tid; e < nb * hh; e += blockDim.x) {
-      const int q = e / hh, rc = e - q * hh, r = rc / h, c = rc - r * h;
-      const T* M12 = Ms + (size_t)(q * b) * ld + q * b + h;
-      const T* T22 = Ms + (size_t)(q * b + h) * ld + q * b + h;
-      T acc = T(0);
-      for (int k = 0; k <= c; ++k) acc += M12[r * ld + k] * T22[k * ld + c];
-      Xs[e] = acc;
+    const int h = b / 2, nb = Kp / b, hh = h * h, tw = h / 4, tpb = tw * tw;
+    // X_q = M12 T22
+    for (int e = tid; e < nb * tpb; e += blockDim.x) {
+      const int q = e / tpb, rc = e - q * tpb, r0 = (rc / tw) * 4, c0 = (rc % tw) * 4;
+      smem_mm4<T>(Ms + (size_t)(q * b) * ld + q * b + h, ld, Ms + (size_t)(q * b + h) * ld + q * b + h, ld,
+                  Xs + (size_t)q * hh, h, h, T(1), r0, c0);
     }
     __syncthreads();
-    // T12 = -T11 X_q (T11 upper triangular), in place of M12
-    for (int e = tid; e < nb * hh; e += blockDim.x) {
-      const int q = e / hh, rc = e - q * hh, r = rc / h, c = rc - r * h;
-      const T* T11 = Ms + (size_t)(q * b) * ld + q * b;
-      const T* X = Xs + (size_t)q * hh;
-      T acc = T(0);
-      for (int k = r; k < h; ++k) acc += T11[r * ld + k] * X[k * h + c];
-      Ms[(size_t)(q * b + r) * ld + q * b + h + c] = -acc;
+    // T12 = -T11 X_q, in place of M12
+    for (int e = tid; e < nb * tpb; e += blockDim.x) {
+      const int q = e / tpb, rc = e - q * tpb, r0 = (rc / tw) * 4, c0 = (rc % tw) * 4;
+      smem_mm4<T>(Ms + (size_t)(q * b) * ld + q * b, ld, Xs + (size_t)q * hh, h,
+                  Ms + (size_t)(q * b) * ld + q * b + h, ld, h, T(-1), r0, c0);
     }
     __syncthreads();
   }
@@ -606,14 +631,71 @@ __device__ __forceinline__ void qr_reduce_cols(float (&d)[CPW]) {
   for (int c = 0; c < 8; ++c) d[c] = __shfl_sync(0xffffffffu, t, ((c >> 2) << 4) | (((c >> 1) & 1) << 3) | ((c & 1) << 2));
 }
 
+// Householder reflector of one register-held column (rows lane + 32 s) at
+// pivot row k, by the warp that owns it: the column becomes beta at row k and
+// v below it (v_k = 1 implied); v (zeros above k) goes to vb, tau to *stau.
+template <int RPL>
+__device__ __forceinline__ void qr_reflector(float (&xc)[RPL], int k, int lane, float* vb, float* stau) {
+  float alpha = 0.0f, part = 0.0f;
+#pragma unroll
+  for (int s = 0; s < RPL; ++s) {
+    const int r = lane + 32 * s;
+    if (r == k) alpha = xc[s];
+    if (r > k) part += xc[s] * xc[s];
+  }
+  for (int o = 16; o; o >>= 1) {
+    part += __shfl_xor_sync(0xffffffffu, part, o);
+    alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+  }
+  float tau = 0.0f, beta = alpha, scal = 0.0f;
+  if (part != 0.0f) {
+    beta = -copysignf(sqrtf(alpha * alpha + part), alpha);
+    tau = (beta - alpha) / beta;
+    scal = 1.0f / (alpha - beta);
+  }
+#pragma unroll
+  for (int s = 0; s < RPL; ++s) {
+    const int r = lane + 32 * s;
+    float vv = 0.0f;
+    if (r == k) {
+      vv = 1.0f;
+      xc[s] = beta;
+    } else if (r > k && tau != 0.0f) {
+      vv = xc[s] * scal;
+      xc[s] = vv;
+    }
+    vb[r] = vv;
+  }
+  if (lane == 0) *stau = tau;
+}
+
+// Apply reflector (v, tk) to the owner warp's column xn, then form the
+// reflector of that column at row kn.
+template <int RPL>
+__device__ __forceinline__ void qr_ahead(float (&xn)[RPL], const float (&v)[RPL], float tk, int kn, int lane,
+                                         float* vb, float* stau) {
+  if (tk != 0.0f) {
+    float dn = 0.0f;
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) dn = fmaf(v[s], xn[s], dn);
+    for (int o = 16; o; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    dn *= tk;
+#pragma unroll
+    for (int s = 0; s < RPL; ++s) xn[s] = fmaf(-dn, v[s], xn[s]);
+  }
+  qr_reflector<RPL>(xn, kn, lane, vb, stau);
+}
+
 // The same factorization in FP32 with the panel in registers: warp w owns
 // columns w, w + 16, ... and lane l rows l, l + 32, ... (D <= 32 RPL,
-// K <= 16 CPW).  Step k: the owner warp of column k forms the reflector
-// (warp reductions only), publishes v and tau through a double-buffered
-// shared vector, and after one barrier every warp updates its columns
-// j > k: w = tau v^T x_j (lane-local products, one warp reduction),
-// x_j -= w v.  The rank-1 updates stay in registers; shared memory carries
-// only v.
+// K <= 16 CPW).  Reflector k is published through a double-buffered shared
+// vector; after one barrier every warp applies it to its columns j > k:
+// w = tau v^T x_j (lane-local products, one warp reduction), x_j -= w v.
+// Lookahead: the owner of column k + 1 applies reflector k to that column
+// first and publishes reflector k + 1 before it updates its other columns,
+// so that the chain from one barrier to the next is one column update and
+// one reflector.  The rank-1 updates stay in registers; shared memory
+// carries only v.
 template <int RPL, int CPW>
 __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* __restrict__ Xin,
                                                      float* __restrict__ Vout, float* __restrict__ tau_out,
@@ -640,59 +722,37 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
     }
     __syncthreads();
   }
-  int buf = 0;
+  if (K > 0 && warp == 0) qr_reflector<RPL>(x[0], 0, lane, vs[0], &s_tau[0]);
 #pragma unroll
   for (int c = 0; c < CPW; ++c) {
     for (int w = 0; w < NW; ++w) {
       const int k = c * NW + w;
       if (k >= K) break;
-      float* vb = vs[buf];
-      if (warp == w) {
-        float alpha = 0.0f, part = 0.0f;
-#pragma unroll
-        for (int s = 0; s < RPL; ++s) {
-          const int r = lane + 32 * s;
-          if (r == k) alpha = x[c][s];
-          if (r > k) part += x[c][s] * x[c][s];
-        }
-        for (int o = 16; o; o >>= 1) {
-          part += __shfl_xor_sync(0xffffffffu, part, o);
-          alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
-        }
-        float tau = 0.0f, beta = alpha, scal = 0.0f;
-        if (part != 0.0f) {
-          beta = -copysignf(sqrtf(alpha * alpha + part), alpha);
-          tau = (beta - alpha) / beta;
-          scal = 1.0f / (alpha - beta);
-        }
-#pragma unroll
-        for (int s = 0; s < RPL; ++s) {
-          const int r = lane + 32 * s;
-          float vv = 0.0f;
-          if (r == k) {
-            vv = 1.0f;
-            x[c][s] = beta;
-          } else if (r > k && tau != 0.0f) {
-            vv = x[c][s] * scal;
-            x[c][s] = vv;
-          }
-          vb[r] = vv;
-        }
-        if (lane == 0) s_tau[buf] = tau;
-      }
-      __syncthreads();
+      const int buf = k & 1;
+      __syncthreads();  // reflector k is in vs[buf]
       const float tk = s_tau[buf];
-      if (tk != 0.0f) {
-        float v[RPL];
+      // owner and register slot of column k + 1
+      const int wn = (w + 1 < NW) ? w + 1 : 0;
+      constexpr int kLast = CPW - 1;
+      const int cn = (w + 1 < NW) ? c : c + 1;
+      const bool ahead = (warp == wn) && (k + 1 < K);
+      float v[RPL];
 #pragma unroll
-        for (int s = 0; s < RPL; ++s) v[s] = vb[lane + 32 * s];
-        // lane partial products of the warp's columns (0 for j <= k)
+      for (int s = 0; s < RPL; ++s) v[s] = vs[buf][lane + 32 * s];
+      if (ahead) {
+        // column k + 1 first, then its reflector into the other buffer (the
+        // two register slots it can sit in are named statically)
+        if (w + 1 < NW) qr_ahead<RPL>(x[c], v, tk, k + 1, lane, vs[buf ^ 1], &s_tau[buf ^ 1]);
+        else qr_ahead<RPL>(x[c < kLast ? c + 1 : kLast], v, tk, k + 1, lane, vs[buf ^ 1], &s_tau[buf ^ 1]);
+      }
+      if (tk != 0.0f) {
+        // lane partial products of the warp's other columns j > k (0 elsewhere)
         float d[CPW];
 #pragma unroll
         for (int cc = 0; cc < CPW; ++cc) {
           const int j = warp + NW * cc;
           d[cc] = 0.0f;
-          if (j > k && j < K) {
+          if (j > k && j < K && !(ahead && cc == cn)) {
 #pragma unroll
             for (int s = 0; s < RPL; ++s) d[cc] = fmaf(v[s], x[cc][s], d[cc]);
           }
@@ -701,7 +761,7 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
 #pragma unroll
         for (int cc = 0; cc < CPW; ++cc) {
           const int j = warp + NW * cc;
-          if (j > k && j < K) {
+          if (j > k && j < K && !(ahead && cc == cn)) {
             const float dj = d[cc] * tk;
 #pragma unroll
             for (int s = 0; s < RPL; ++s) x[cc][s] = fmaf(-dj, v[s], x[cc][s]);
@@ -709,7 +769,6 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
         }
       }
       if (threadIdx.x == 0) tau_out[(size_t)box * K + k] = tk;
-      buf ^= 1;
     }
   }
   // R (row-major, upper) and V (column-major, unit diagonal, zeros above)
@@ -1174,6 +1233,211 @@ __global__ void __launch_bounds__(NT) gj_inverse_kernel(int D, int R, const floa
   }
 }
 
+// The same elimination for R <= 128 in 16-column panels.  Thread t of warp
+// w holds the 8 x 8 tile at rows 8 (lane % 16), columns 16 w + 8 (lane / 16),
+// so warp w holds panel w (columns 16 w .. 16 w + 15) for every row.  Per
+// panel: (1) its warp runs the 16 in-place steps on the panel columns only
+// (pivot search, pivot row and column multipliers by shuffles and a
+// warp-private shared row), leaving in column 16 w + a the column p_a of
+// the combined elimination E of the 16 steps (p_a: pivot row of step a);
+// (2) the rows p_a of every other column are published; (3) every other
+// column takes E's effect at once, a_c += (E - I)[:, P] a_old[P, c]: a rank-16
+// update.  The pivots are those of the one-column form (the same row order
+// of choice); the sums are grouped differently.
+constexpr int kGbP = 16;  // panel width
+
+struct GbShared {
+  float WmT[2][kGbP][128];   // (E - I)[:, p_a], transposed: WmT[a][r]
+  float Prow[2][kGbP][128];  // rows p_a of the matrix before the panel
+  float prs[8][kGbP];        // per warp: the current pivot row of its panel
+  int pidx[2][128];          // panel slot a of row r, -1 for rows that are no pivot of the panel
+  unsigned char used[128];   // rows already chosen as pivots
+  int prow[128], pinv[128], rowat[128];
+  int bad;
+};
+
+__global__ void __launch_bounds__(256, 2) gj_blocked_kernel(int D, int R, const float* __restrict__ Ablk,
+                                                            const int32_t* __restrict__ diag_idx,
+                                                            float* __restrict__ Ainv, int32_t* __restrict__ piv,
+                                                            int32_t* __restrict__ status, int level) {
+  __shared__ __align__(16) GbShared sh;
+  const int box = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int tr = lane & 15, h = lane >> 4;
+  const int r0 = 8 * tr, c0 = 16 * warp + 8 * h;
+  const int npan = (R + kGbP - 1) / kGbP;
+  const float* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
+  float x[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = r0 + i;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + j;
+      x[i][j] = (r < R && c < R) ? A[(size_t)r * D + c] : 0.0f;
+    }
+  }
+  for (int e = t; e < 128; e += blockDim.x) sh.used[e] = (e >= R);
+  if (t == 0) sh.bad = 0;
+  __syncthreads();
+  for (int pn = 0; pn < npan; ++pn) {
+    const int b = pn & 1;
+    if (warp == pn) {
+      // (1) the panel's 16 steps
+      unsigned used = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) used |= (unsigned)sh.used[r0 + i] << i;
+      for (int e = lane; e < 128; e += 32) sh.pidx[b][e] = -1;
+      __syncwarp();
+      float* prs = sh.prs[warp];
+      bool bad = false;
+#pragma unroll 1
+      for (int ha = 0; ha < 2; ++ha)
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int a = 8 * ha + jj;
+        const int k = kGbP * pn + a;
+        if (k >= R || bad) break;
+        float best = -1.0f;
+        int bi = -1;
+        if (h == ha) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float v = fabsf(x[i][jj]);
+            if (!((used >> i) & 1u) && v > best) best = v, bi = r0 + i;
+          }
+        }
+#pragma unroll
+        for (int o = 1; o < 16; o <<= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) best = ob, bi = oi;
+        }
+        const int p = __shfl_sync(0xffffffffu, bi, 16 * ha);
+        if (p < 0) {
+          bad = true;
+          break;
+        }
+        // pivot row p into the warp's shared row (both column halves)
+        if (tr == (p >> 3)) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (r0 + i == p) {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) prs[8 * h + j] = x[i][j];
+            }
+        }
+        __syncwarp();
+        float pr[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pr[j] = prs[8 * h + j];
+        const float pv = prs[a];
+        __syncwarp();
+        if (pv == 0.0f || !isfinite(pv)) {
+          bad = true;
+          break;
+        }
+        const float inv = __frcp_rn(pv);
+        // scaled pivot row; its column-k entry becomes 1 / pv
+#pragma unroll
+        for (int j = 0; j < 8; ++j) pr[j] = (h == ha && j == jj) ? inv : pr[j] * inv;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float f = __shfl_sync(0xffffffffu, x[i][jj], tr + 16 * ha);
+          if (r0 + i == p) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[i][j] = pr[j];
+            used |= 1u << i;
+          } else {
+            if (h == ha) x[i][jj] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[i][j] = fmaf(-f, pr[j], x[i][j]);
+          }
+        }
+        if (lane == 0) {
+          sh.prow[k] = p;
+          sh.used[p] = 1;
+          sh.pidx[b][p] = a;
+        }
+      }
+      if (bad && lane == 0) sh.bad = 1;
+      __syncwarp();
+      // (E - I)[:, p_a] = the panel columns minus 1 at the pivot rows
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = r0 + i;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int a = 8 * h + j;
+          const bool pivot_entry = (sh.pidx[b][r] == a);
+          sh.WmT[b][a][r] = x[i][j] - (pivot_entry ? 1.0f : 0.0f);
+        }
+      }
+    }
+    __syncthreads();
+    if (sh.bad) break;
+    const int kn = min(kGbP, R - kGbP * pn);  // steps of this panel
+    // (2) rows p_a of the other columns, before the update
+    if (warp != pn) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int a = sh.pidx[b][r0 + i];
+        if (a >= 0) {
+          float4* dst = reinterpret_cast<float4*>(&sh.Prow[b][a][c0]);
+          dst[0] = make_float4(x[i][0], x[i][1], x[i][2], x[i][3]);
+          dst[1] = make_float4(x[i][4], x[i][5], x[i][6], x[i][7]);
+        }
+      }
+    }
+    __syncthreads();
+    // (3) rank-kn update of the other columns
+    if (warp != pn) {
+#pragma unroll 1
+      for (int a = 0; a < kn; ++a) {
+        const float4 w0 = *reinterpret_cast<const float4*>(&sh.WmT[b][a][r0]);
+        const float4 w1 = *reinterpret_cast<const float4*>(&sh.WmT[b][a][r0 + 4]);
+        const float4 p0 = *reinterpret_cast<const float4*>(&sh.Prow[b][a][c0]);
+        const float4 p1 = *reinterpret_cast<const float4*>(&sh.Prow[b][a][c0 + 4]);
+        const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const float q[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) x[i][j] = fmaf(w[i], q[j], x[i][j]);
+      }
+    }
+  }
+  if (sh.bad) {
+    if (t == 0 && atomicCAS(status, 0, level + 1) == 0) status[1] = box;
+    return;
+  }
+  // unscramble: Ainv[k][prow[j]] = a[prow[k]][j]
+  for (int k = t; k < R; k += blockDim.x) sh.pinv[sh.prow[k]] = k;
+  __syncthreads();
+  float* out = Ainv + (size_t)box * R * R;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = r0 + i;
+    if (r >= R) continue;
+    const size_t row = (size_t)sh.pinv[r] * R;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (c0 + j < R) out[row + sh.prow[c0 + j]] = x[i][j];
+  }
+  // LAPACK-style interchange sequence of the same pivots
+  __syncthreads();
+  if (t == 0) {
+    int* pos = sh.pinv;
+    for (int q = 0; q < R; ++q) pos[q] = q, sh.rowat[q] = q;
+    int32_t* pv_out = piv + (size_t)box * R;
+    for (int k = 0; k < R; ++k) {
+      const int r = sh.prow[k], q = pos[r], rk = sh.rowat[k];
+      pv_out[k] = q;
+      sh.rowat[k] = r, sh.rowat[q] = rk;
+      pos[r] = k, pos[rk] = q;
+    }
+  }
+}
+
 template <typename T>
 void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
                        int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st) {
@@ -1185,9 +1449,8 @@ void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_
     float* Af_inv = reinterpret_cast<float*>(Ainv);
     ++g_launches;
     if (R <= 128) {
-      const int n = (R + 7) / 8, threads = std::max(32, gj_group(n) * n);
-      gj_inverse_kernel<8, 8, 256><<<nb, (threads + 31) / 32 * 32, 0, st>>>(D, R, Af, diag_idx, Af_inv, piv, status,
-                                                                             level);
+      const int warps = (R + kGbP - 1) / kGbP;
+      gj_blocked_kernel<<<nb, 32 * warps, 0, st>>>(D, R, Af, diag_idx, Af_inv, piv, status, level);
     } else {
       const int Rp = (R + 11) / 12 * 12, threads = gj_group(Rp / 12) * (Rp / 6);
       gj_inverse_kernel<12, 6, 512><<<nb, (threads + 31) / 32 * 32, 0, st>>>(D, R, Af, diag_idx, Af_inv, piv, status,

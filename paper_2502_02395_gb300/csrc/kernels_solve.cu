@@ -512,6 +512,14 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 // lets the next kernel in the stream begin launching once every CTA of this
 // one has started
 __device__ __forceinline__ void griddep_launch_next() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+// asks L2 for the 128-byte lines of [p, p + bytes) (the CTA's threads share
+// the lines): a kernel whose second matrix is read only after a dependent
+// step has it on chip by then
+__device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes) {
+  const char* b = static_cast<const char*>(p);
+  for (int64_t o = (int64_t)threadIdx.x * 128; o < bytes; o += (int64_t)blockDim.x * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(b + o));
+}
 
 // The pair kernel runs one CTA per near pair p = (i, j) of a level (or of a
 // sub-list of them) and writes one block-vector product into part[p]:
@@ -804,53 +812,60 @@ __device__ __forceinline__ Slice slice_of(int ns, int nrows) {
 }
 
 // ---------------------------------------------------------------- fwd1 ---
-// c_i = U_i^T b_i (U column-major: column n of U is row n of U^T)
+// [u_i; c_i^S]: u_i = Ainv_i c_i^R = M1_i b_i with M1_i = Ainv_i (U_i^R)^T
+// (row-major R x D, formed by the factorization) and c_i^S = (U_i^S)^T b_i
+// (rows R.. of U^T, i.e. columns R.. of the column-major U).  Above the leaf
+// level the box input b_i is assembled first from its two children c:
+// b_i = [s_2i; s_2i+1], s_c = c_c^S - sum_{j near c} Ahat_cj^SR v_j (the
+// pair sums of the children's SR products).
 template <typename T>
-__global__ void __launch_bounds__(256) fwd1_kernel(int D, int ns, const T* __restrict__ U, const T* __restrict__ vin,
-                                                   T* __restrict__ c) {
+__global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, int ns, const T* __restrict__ M1,
+                                                   const T* __restrict__ U, const T* __restrict__ vin,
+                                                   ChildIn<T> ch, T* __restrict__ u, T* __restrict__ c) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sv = reinterpret_cast<T*>(sm_raw);  // D
   const Slice sl = slice_of(ns, D);
   const int i = sl.i;
-  cta_gemv<T, T, Unr<T>::v>(U + ((int64_t)i * D + sl.r0) * D, D, sl.nr, D, sv, T(1), nullptr,
-                            c + (int64_t)i * D + sl.r0, [&] {
-                              griddep_wait();
-                              griddep_launch_next();
-                              for (int e = threadIdx.x; e < D; e += blockDim.x) sv[e] = vin[(int64_t)i * D + e];
-                              __syncthreads();
-                            });
+  bool loaded = false;
+  auto hook = [&] {
+    if (loaded) return;
+    loaded = true;
+    griddep_wait();
+    griddep_launch_next();
+    if (ch.c) {
+      const T isc = ch.iscale ? T(ch.iscale[0]) : T(1);
+      for (int e = threadIdx.x; e < D; e += blockDim.x) {
+        const int cc = 2 * i + e / ch.K, r = e % ch.K;
+        sv[e] = ch.c[(int64_t)cc * ch.D + ch.R + r] - isc * sum_pairs(ch.part, ch.K, ch.ptr[cc], ch.ptr[cc + 1], r);
+      }
+    } else {
+      for (int e = threadIdx.x; e < D; e += blockDim.x) sv[e] = vin[(int64_t)i * D + e];
+    }
+    __syncthreads();
+  };
+  const int a0 = sl.r0, a1 = min(sl.r0 + sl.nr, R), b0 = max(sl.r0, R), b1 = sl.r0 + sl.nr;
+  if (a1 > a0 && b1 > b0) prefetch_l2(U + ((int64_t)i * D + b0) * D, (int64_t)(b1 - b0) * D * sizeof(T));
+  if (a1 > a0)
+    cta_gemv<T, T, Unr<T>::v>(M1 + ((int64_t)i * R + a0) * D, D, a1 - a0, D, sv, T(1), nullptr,
+                              u + (int64_t)i * R + a0, hook);
+  if (b1 > b0)
+    cta_gemv<T, T, Unr<T>::v>(U + ((int64_t)i * D + b0) * D, D, b1 - b0, D, sv, T(1), nullptr,
+                              c + (int64_t)i * D + b0, hook);
 }
-
-// u_i = Ainv_i c_i^R
-template <typename T>
-__global__ void __launch_bounds__(256) fwd1u_kernel(int D, int R, int ns, const T* __restrict__ Ainv,
-                                                    const T* __restrict__ c, T* __restrict__ u) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sc = reinterpret_cast<T*>(sm_raw);  // R
-  const Slice sl = slice_of(ns, R);
-  const int i = sl.i;
-  cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, sc, T(1), nullptr,
-                            u + (int64_t)i * R + sl.r0, [&] {
-                              griddep_wait();
-                              griddep_launch_next();
-                              for (int e = threadIdx.x; e < R; e += blockDim.x) sc[e] = c[(int64_t)i * D + e];
-                              __syncthreads();
-                            });
-}
-
 
 // ---------------------------------------------------------------- fwd2 ---
 // v_i = Ainv_i (c_i^R - sum_{j<i near} Ahat_ij^RR u_j)
+//     = u_i - Ainv_i sum_{j<i near} Ahat_ij^RR u_j
 template <typename T>
-__global__ void __launch_bounds__(256) fwd2_kernel(int D, int R, int ns, const int64_t* __restrict__ ptr,
+__global__ void __launch_bounds__(256) fwd2_kernel(int R, int ns, const int64_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ lo_cnt, const float* __restrict__ iscale,
-                                                   const T* __restrict__ Ainv, const T* __restrict__ c,
+                                                   const T* __restrict__ Ainv, const T* __restrict__ u,
                                                    const T* __restrict__ part, T* __restrict__ v) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sb = reinterpret_cast<T*>(sm_raw);  // R
   const Slice sl = slice_of(ns, R);
   const int i = sl.i;
-  cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, sb, T(1), nullptr,
+  cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, sb, T(-1), u + (int64_t)i * R + sl.r0,
                             v + (int64_t)i * R + sl.r0, [&] {
                               const T isc = iscale ? T(iscale[0]) : T(1);
                               // the pairs j < i lead the box's sorted range
@@ -858,7 +873,7 @@ __global__ void __launch_bounds__(256) fwd2_kernel(int D, int R, int ns, const i
                               griddep_wait();
                               griddep_launch_next();
                               for (int r = threadIdx.x; r < R; r += blockDim.x)
-                                sb[r] = c[(int64_t)i * D + r] - isc * sum_pairs(part, R, q0, q1, r);
+                                sb[r] = isc * sum_pairs(part, R, q0, q1, r);
                               __syncthreads();
                             });
 }
@@ -901,48 +916,36 @@ __global__ void __launch_bounds__(256) bwd1_kernel(int R, int ns, const int64_t*
 }
 
 // ---------------------------------------------------------------- bwd2 ---
-// z_i = [x_i^R; x_i^S] with x_i^R = om_i - Ainv_i sum_{j>i near} Ahat_ij^RR om_j
+// x_i = U_i z_i, z_i = [x_i^R; x_i^S] with
+// x_i^R = om_i - Ainv_i sum_{j>i near} Ahat_ij^RR om_j and x_i^S from the
+// parent.  Every CTA of box i forms the whole x_i^R (Ainv_i is read once
+// from memory and then from L2 when the rows are split), then its slice of
+// the rows of U_i z_i (Ur: U_i row-major).
 template <typename T>
 __global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, int ns, const int64_t* __restrict__ ptr,
                                                    const int32_t* __restrict__ hi_cnt, const float* __restrict__ iscale,
                                                    const T* __restrict__ Ainv, const T* __restrict__ om,
                                                    const T* __restrict__ px, const T* __restrict__ part,
-                                                   T* __restrict__ z) {
+                                                   const T* __restrict__ Ur, T* __restrict__ xs) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sq = reinterpret_cast<T*>(sm_raw);  // R
-  const Slice sl = slice_of(ns, R);
-  const int i = sl.i;
-  cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, sq, T(-1), om + (int64_t)i * R + sl.r0,
-                            z + (int64_t)i * D + sl.r0, [&] {
-                              const T isc = iscale ? T(iscale[0]) : T(1);
-                              // the pairs j > i trail the box's sorted range
-                              const int64_t q1 = ptr[i + 1], q0 = q1 - hi_cnt[i];
-                              griddep_wait();
-                              griddep_launch_next();
-                              if (blockIdx.x % ns == 0) {
-                                const T* xi = px + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
-                                for (int e = threadIdx.x; e < K; e += blockDim.x) z[(int64_t)i * D + R + e] = xi[e];
-                              }
-                              for (int r = threadIdx.x; r < R; r += blockDim.x) sq[r] = isc * sum_pairs(part, R, q0, q1, r);
-                              __syncthreads();
-                            });
-}
-
-// x_i = U_i z_i (Ur: U_i row-major)
-template <typename T>
-__global__ void __launch_bounds__(256) bwd2u_kernel(int D, int ns, const T* __restrict__ Ur, const T* __restrict__ z,
-                                                    T* __restrict__ xs) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  T* sz = reinterpret_cast<T*>(sm_raw);  // D
+  T* zs = reinterpret_cast<T*>(sm_raw);  // D
+  T* sq = zs + ((D + 3) & ~3);           // R
   const Slice sl = slice_of(ns, D);
   const int i = sl.i;
-  cta_gemv<T, T, Unr<T>::v>(Ur + ((int64_t)i * D + sl.r0) * D, D, sl.nr, D, sz, T(1), nullptr,
-                            xs + (int64_t)i * D + sl.r0, [&] {
-                              griddep_wait();
-                              griddep_launch_next();
-                              for (int e = threadIdx.x; e < D; e += blockDim.x) sz[e] = z[(int64_t)i * D + e];
-                              __syncthreads();
-                            });
+  prefetch_l2(Ur + ((int64_t)i * D + sl.r0) * D, (int64_t)sl.nr * D * sizeof(T));
+  cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, sq, T(-1), om + (int64_t)i * R, zs, [&] {
+    const T isc = iscale ? T(iscale[0]) : T(1);
+    // the pairs j > i trail the box's sorted range
+    const int64_t q1 = ptr[i + 1], q0 = q1 - hi_cnt[i];
+    griddep_wait();
+    griddep_launch_next();
+    const T* xi = px + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
+    for (int e = threadIdx.x; e < K; e += blockDim.x) zs[R + e] = xi[e];
+    for (int r = threadIdx.x; r < R; r += blockDim.x) sq[r] = isc * sum_pairs(part, R, q0, q1, r);
+    __syncthreads();
+  });
+  cta_gemv<T, T, Unr<T>::v>(Ur + ((int64_t)i * D + sl.r0) * D, D, sl.nr, D, zs, T(1), nullptr,
+                            xs + (int64_t)i * D + sl.r0, [] { __syncthreads(); });
 }
 
 // out_b = (in_b)^T for nb square D x D blocks (32 x 32 tiles through shared memory)
@@ -1004,6 +1007,10 @@ static int num_sms() {
 }
 
 // row slices per box: enough CTAs for two per SM, at least 32 rows each
+// a launch of at most one CTA per SM: its CTAs stream their blocks alone,
+// so they ask L2 for them before waiting on the previous kernel
+static bool small_level(int64_t nblocks) { return nblocks <= num_sms(); }
+
 static int row_splits(int nb, int nrows) {
   const int nsm = num_sms();
   if (nb <= 0) return 1;
@@ -1054,27 +1061,25 @@ static void launch_pairs(const DevLevel& L, const FacLevel<T>& F, const int32_t*
 }
 
 template <typename T>
-void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const T* Ainv, cudaStream_t st) {
+void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const ChildIn<T>& ch, cudaStream_t st) {
   const int ns = row_splits(L.nb, L.D);
-  launch_pdl(fwd1_kernel<T>, L.nb * ns, 256, sizeof(T) * L.D, st, L.D, ns, F.U, F.vin, F.c);
-  if (L.R == 0) return;
-  const int nu = row_splits(L.nb, L.R);
-  launch_pdl(fwd1u_kernel<T>, L.nb * nu, 256, sizeof(T) * L.R, st, L.D, L.R, nu, Ainv, F.c, F.u);
+  launch_pdl(fwd1_kernel<T>, L.nb * ns, 256, sizeof(T) * L.D, st, L.D, L.R, ns, F.M1, F.U, F.vin, ch, F.u, F.c);
 }
 template <typename T, typename TS>
 void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, cudaStream_t st) {
   if (L.R == 0) return;
   launch_pairs<T, TS, PH_RR>(L, F, L.lo_pairs, L.n_lo, Ahat, F.u, F.part, st);
   const int ns = row_splits(L.nb, L.R);
-  launch_pdl(fwd2_kernel<T>, L.nb * ns, 256, sizeof(T) * L.R, st, L.D, L.R, ns, L.near_ptr, L.lo_cnt, iscale, F.Ainv,
-             F.c, F.part, F.v);
+  launch_pdl(fwd2_kernel<T>, L.nb * ns, 256, sizeof(T) * L.R, st, L.R, ns, L.near_ptr, L.lo_cnt, iscale, F.Ainv, F.u,
+             F.part, F.v);
 }
 template <typename T, typename TS>
 void launch_fwd3(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, T* parent_vin,
                  cudaStream_t st) {
   if (L.K == 0) return;
   launch_pairs<T, TS, PH_SR>(L, F, nullptr, L.NP, Ahat, F.v, F.part, st);
-  launch_pdl(fwd3_kernel<T>, L.nb, 128, 0, st, L.D, L.R, L.K, L.near_ptr, iscale, F.c, F.part, parent_vin);
+  // above level 1 the parent's fwd1 sums these pair products itself
+  if (parent_vin) launch_pdl(fwd3_kernel<T>, L.nb, 128, 0, st, L.D, L.R, L.K, L.near_ptr, iscale, F.c, F.part, parent_vin);
 }
 template <typename T, typename TS>
 void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
@@ -1088,12 +1093,11 @@ void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const 
 template <typename T, typename TS>
 void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
                  cudaStream_t st) {
-  const int ns = row_splits(L.nb, std::max(L.R, 1));
   if (L.R > 0) launch_pairs<T, TS, PH_RR>(L, F, L.hi_pairs, L.n_hi, Ahat, F.om, F.part, st);
-  launch_pdl(bwd2_kernel<T>, L.nb * ns, 256, sizeof(T) * std::max(L.R, 1), st, L.D, L.R, L.K, ns, L.near_ptr,
-             L.hi_cnt, iscale, F.Ainv, F.om, parent_x, F.part, F.z);
-  const int nx = row_splits(L.nb, L.D);
-  launch_pdl(bwd2u_kernel<T>, L.nb * nx, 256, sizeof(T) * L.D, st, L.D, nx, F.Ur, F.z, F.xs);
+  const int ns = row_splits(L.nb, L.D);
+  const size_t sm = sizeof(T) * ((size_t)((L.D + 3) & ~3) + std::max(L.R, 1));
+  launch_pdl(bwd2_kernel<T>, L.nb * ns, 256, sm, st, L.D, L.R, L.K, ns, L.near_ptr, L.hi_cnt, iscale, F.Ainv, F.om,
+             parent_x, F.part, F.Ur, F.xs);
 }
 
 // y = M x for one n x n row-major matrix (root solve with the explicit inverse)
@@ -1118,7 +1122,7 @@ void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st) {
 }
 
 #define H2_INST_SOLVE(T)                                                                     \
-  template void launch_fwd1<T>(const DevLevel&, const FacLevel<T>&, const T*, cudaStream_t); \
+  template void launch_fwd1<T>(const DevLevel&, const FacLevel<T>&, const ChildIn<T>&, cudaStream_t); \
   template void launch_transpose_blocks<T>(int64_t, int, const T*, T*, cudaStream_t);         \
   template void launch_gemv_rows<T>(int, const T*, const T*, T*, cudaStream_t);
 H2_INST_SOLVE(double)
@@ -1146,11 +1150,14 @@ H2_INST_SUBST(float, __nv_bfloat16)
 // of a, eight rows of X in flight per lane).
 template <typename T>
 __global__ void __launch_bounds__(256) mv_up_kernel(int D, int K, const T* __restrict__ X, const T* __restrict__ x,
-                                                    T* __restrict__ xh) {
+                                                    T* __restrict__ xh, int pf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* part = reinterpret_cast<T*>(smraw);  // 8 * K
   T* sx = part + 8 * K;                   // D
   const int i = blockIdx.x, tid = threadIdx.x;
+  if (pf) prefetch_l2(X + (int64_t)i * D * K, (int64_t)D * K * sizeof(T));
+  griddep_wait();
+  griddep_launch_next();
   for (int e = tid; e < D; e += 256) sx[e] = x[(int64_t)i * D + e];
   __syncthreads();
   cta_gemv_cols<T, T>(X + (int64_t)i * D * K, K, K, D, sx, part, xh + (int64_t)i * K);
@@ -1159,8 +1166,7 @@ template <typename T>
 void launch_matvec_up(const DevLevel& L, const T* X, const T* x, T* xh, cudaStream_t st) {
   const size_t sm = sizeof(T) * (8 * (size_t)L.K + L.D);
   set_smem((const void*)mv_up_kernel<T>, sm);
-  ++g_launches;
-  mv_up_kernel<T><<<L.nb, 256, sm, st>>>(L.D, L.K, X, x, xh);
+  launch_pdl(mv_up_kernel<T>, L.nb, 256, sm, st, L.D, L.K, X, x, xh, small_level(L.nb) ? 1 : 0);
 }
 
 // couplings: yh_i = sum_{far j} S_f xh_j   (overwrites yh_i)
@@ -1173,6 +1179,8 @@ __global__ void __launch_bounds__(256, 2) mv_far_kernel(int K, const int64_t* __
   const int i = blockIdx.x, tid = threadIdx.x;
   const int64_t p0 = ptr[i];
   const int nf = (int)(ptr[i + 1] - p0);
+  griddep_wait();
+  griddep_launch_next();
   for (int e = tid; e < nf * K; e += blockDim.x) smv[e] = xh[(int64_t)fj[p0 + e / K] * K + e % K];
   __syncthreads();
   T acc[kRPW];
@@ -1186,18 +1194,20 @@ template <typename T>
 void launch_matvec_far(const DevLevel& L, const T* S, const T* xh, T* yh, cudaStream_t st) {
   size_t sm = sizeof(T) * (size_t)L.K * std::max(L.max_far, 1);
   set_smem((const void*)mv_far_kernel<T>, sm);
-  ++g_launches;
-  mv_far_kernel<T><<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, S, xh, yh);
+  launch_pdl(mv_far_kernel<T>, L.nb, 256, sm, st, L.K, L.far_ptr, L.far_j, S, xh, yh);
 }
 
 // downward: [yh_2p; yh_2p+1] += X_p yh_p   (rows d of X_p, D = 2 Kc): a
 // block-row GEMV per parent box
 template <typename T>
 __global__ void __launch_bounds__(256, 2) mv_down_kernel(int D, int K, const T* __restrict__ X,
-                                                         const T* __restrict__ yh, T* __restrict__ yhc) {
+                                                         const T* __restrict__ yh, T* __restrict__ yhc, int pf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sy = reinterpret_cast<T*>(smraw);  // K
   const int p = blockIdx.x;
+  if (pf) prefetch_l2(X + (int64_t)p * D * K, (int64_t)D * K * sizeof(T));
+  griddep_wait();
+  griddep_launch_next();
   for (int e = threadIdx.x; e < K; e += 256) sy[e] = yh[(int64_t)p * K + e];
   __syncthreads();
   T acc[kRPW];
@@ -1210,8 +1220,8 @@ __global__ void __launch_bounds__(256, 2) mv_down_kernel(int D, int K, const T* 
 }
 template <typename T>
 void launch_matvec_down(const DevLevel& L, const T* X, const T* yh, T* yh_child, cudaStream_t st) {
-  ++g_launches;
-  mv_down_kernel<T><<<L.nb, 256, sizeof(T) * ((L.K + 3) & ~3), st>>>(L.D, L.K, X, yh, yh_child);
+  launch_pdl(mv_down_kernel<T>, L.nb, 256, sizeof(T) * ((L.K + 3) & ~3), st, L.D, L.K, X, yh, yh_child,
+             small_level(L.nb) ? 1 : 0);
 }
 
 // leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j
@@ -1226,6 +1236,8 @@ __global__ void __launch_bounds__(256, 2) mv_leaf_kernel(int D, int K, const int
   const int64_t p0 = ptr[i];
   const int nn = (int)(ptr[i + 1] - p0);
   const int kpad = (K + 3) & ~3;
+  griddep_wait();
+  griddep_launch_next();
   T* sh = smv;
   T* sx = smv + kpad;
   if (yh)
@@ -1447,7 +1459,7 @@ template <int CH>  // 4-column chunks per lane: D = 128 CH
 __global__ void __launch_bounds__(256, 2) mv_sym_pair_kernel(int D, int64_t npu, const int32_t* __restrict__ ui,
                                                              const int32_t* __restrict__ uj,
                                                              const float* __restrict__ A, const float* __restrict__ x,
-                                                             float* __restrict__ part) {
+                                                             float* __restrict__ part, int pf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* xa = reinterpret_cast<float*>(smraw);  // D
   float* wp = xa + D;                           // 8 * D
@@ -1455,6 +1467,9 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_kernel(int D, int64_t npu,
   const int a = ui[k], b = uj[k], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool both = a != b;
   const float* M = A + k * D * D;
+  if (pf) prefetch_l2(M, (int64_t)D * D * sizeof(float));
+  griddep_wait();
+  griddep_launch_next();
   for (int e = tid; e < D; e += blockDim.x) xa[e] = x[(int64_t)a * D + e];
   float xb[CH][4];
 #pragma unroll
@@ -1530,6 +1545,8 @@ __global__ void __launch_bounds__(256) mv_sym_sum_kernel(int D, int K, const int
   const int i = blockIdx.x;
   const int64_t e0 = ptr[i], e1 = ptr[i + 1];
   auto hook = [&] {
+    griddep_wait();
+    griddep_launch_next();
     for (int e = threadIdx.x; e < K; e += blockDim.x) sh[e] = yh[(int64_t)i * K + e];
     for (int r = threadIdx.x; r < D; r += blockDim.x) {
       T s = T(0);
@@ -1645,19 +1662,24 @@ bool sym_leaf_supported(int D) { return D == 128 || D == 256; }
 
 template <int CH>
 static void launch_sym_pairs_ch(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A,
-                                const float* x, float* part, cudaStream_t st) {
+                                const float* x, float* part, bool pdl, cudaStream_t st) {
   const size_t sm = sizeof(float) * 9 * (size_t)D;
   set_smem((const void*)mv_sym_pair_kernel<CH>, sm);
-  ++g_launches;
-  mv_sym_pair_kernel<CH><<<(unsigned)npu, 256, sm, st>>>(D, npu, ui, uj, A, x, part);
+  const int pf = small_level(npu) ? 1 : 0;
+  if (pdl) {
+    launch_pdl(mv_sym_pair_kernel<CH>, (unsigned)npu, 256, sm, st, D, npu, ui, uj, A, x, part, pf);
+  } else {
+    ++g_launches;
+    mv_sym_pair_kernel<CH><<<(unsigned)npu, 256, sm, st>>>(D, npu, ui, uj, A, x, part, pf);
+  }
 }
 void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A, const float* x,
-                             float* part, cudaStream_t st) {
+                             float* part, bool pdl, cudaStream_t st) {
   if (npu <= 0) return;
   switch (D / 128) {
-    case 1: launch_sym_pairs_ch<1>(D, npu, ui, uj, A, x, part, st); break;
-    case 2: launch_sym_pairs_ch<2>(D, npu, ui, uj, A, x, part, st); break;
-    default: launch_sym_pairs_ch<2>(D, npu, ui, uj, A, x, part, st); break;
+    case 1: launch_sym_pairs_ch<1>(D, npu, ui, uj, A, x, part, pdl, st); break;
+    case 2: launch_sym_pairs_ch<2>(D, npu, ui, uj, A, x, part, pdl, st); break;
+    default: launch_sym_pairs_ch<2>(D, npu, ui, uj, A, x, part, pdl, st); break;
   }
 }
 template <int CH>
@@ -1681,8 +1703,7 @@ template <typename T>
 void launch_matvec_sym_sum(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const T* X, const T* yh,
                            const T* part, T* y, cudaStream_t st) {
   const size_t sm = sizeof(T) * ((size_t)((K + 3) & ~3) + D);
-  ++g_launches;
-  mv_sym_sum_kernel<T><<<nb, 256, sm, st>>>(D, K, ptr, ent, X, yh, part, y);
+  launch_pdl(mv_sym_sum_kernel<T>, nb, 256, sm, st, D, K, ptr, ent, X, yh, part, y);
 }
 template void launch_matvec_sym_sum<float>(int, int, int, const int64_t*, const int32_t*, const float*, const float*,
                                            const float*, float*, cudaStream_t);
