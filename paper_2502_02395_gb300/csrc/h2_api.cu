@@ -263,6 +263,38 @@ h2_status setup_device(h2_ctx* c) {
     CKC(dalloc(c, &c->Alo, (size_t)lf.NP * lf.D * lf.D));
     launch_split_lo(c->A64, c->A32, c->Alo, (int64_t)lf.NP * lf.D * lf.D, 0);
   }
+  // upper / lower split of each level's near list (symmetric kernels)
+  for (int l = 1; l <= L && c->sym; ++l) {
+    DevLevel& d = c->lv[l];
+    std::map<std::pair<int32_t, int32_t>, int32_t> at;
+    for (int64_t q = 0; q < d.NP; ++q) at[{d.h_near_i[q], d.h_near_j[q]}] = (int32_t)q;
+    d.h_mirror.assign(d.NP, -1);
+    bool closed = true;
+    std::vector<int32_t> uq, ui, uj, lq, lm;
+    for (int64_t q = 0; q < d.NP; ++q) {
+      const int32_t i = d.h_near_i[q], j = d.h_near_j[q];
+      auto it = at.find({j, i});
+      if (it == at.end()) {
+        closed = false;
+        break;
+      }
+      d.h_mirror[q] = it->second;
+      if (i <= j) uq.push_back((int32_t)q), ui.push_back(i), uj.push_back(j);
+      else lq.push_back((int32_t)q), lm.push_back(it->second);
+    }
+    if (!closed) continue;
+    d.near_sym = true;
+    d.n_up = (int64_t)uq.size();
+    d.n_lw = (int64_t)lq.size();
+    CKS(upload(c, &d.su_q, uq));
+    CKS(upload(c, &d.su_i, ui));
+    CKS(upload(c, &d.su_j, uj));
+    CKS(upload(c, &d.mirror, d.h_mirror));
+    if (d.n_lw) {
+      CKS(upload(c, &d.lw_q, lq));
+      CKS(upload(c, &d.lw_m, lm));
+    }
+  }
   c->X64p.assign(L + 1, nullptr);
   c->S64p.assign(L + 1, nullptr);
   c->X32p.assign(L + 1, nullptr);
@@ -593,6 +625,16 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   // stream), a2' start, a2' end = couplings ready (coupling stream)]
   auto evb_at = [&](int l, int k) { return evb[(size_t)(L - l) * 4 + k]; };
 
+  // levels whose projection covers the upper pairs only: symmetric near
+  // lists on the tensor cores with the 16-bit substitution copy, R a
+  // multiple of 32 (the transposed copy's tiles) and a parent merged in 16
+  // bits (the merge reads the lower pairs' SS from their mirrors)
+  for (int l = 0; l <= L; ++l) F.lv[l].proj_sym = false;
+  for (int l = 2; l <= L; ++l) {
+    const DevLevel& d = c->lv[l];
+    F.lv[l].proj_sym = d.near_sym && F.lv[l].tc && F.lv[l - 1].tc && (bf16 || d.D <= 256) && d.R > 0 &&
+                       d.R % 32 == 0 && d.K > 0;
+  }
   // ---- the context's stream: a2, a3, a4/a5, a6 per level
   for (int l = L; l >= 1; --l) {
     const DevLevel& d = c->lv[l];
@@ -623,14 +665,26 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
                 make_tile_map(&f.tm_sr, f.Ahat16, bf16, rows, D, D, K, R) &&
                 make_tile_map(&f.tm_rs, f.Ahat16, bf16, rows, D, D, R, K);
       }
-      bool ok = gemm_tc(bf16, D, D, D, A16, d.NP, D, D, nullptr, f.U16, d.nb, D, D, d.near_j, F.W16, DD, nullptr, D,
-                        1, bf16, 1.0f, nullptr, d.NP, c->status + 2, st) &&
-                gemm_tc(bf16, D, D, D, f.U16, d.nb, D, D, d.near_i, F.W16, d.NP, D, D, nullptr, f.Ahat, DD, nullptr, D,
-                        0, 0, 1.0f, sc + 1, d.NP, c->status + 2, st, sub16 ? f.Ahat16 : nullptr,
-                        sub16 ? R : -1, d.near_i, d.near_j);
+      // symmetric kernels: Ahat_ji = Ahat_ij^T, so only the upper pairs
+      // (i <= j) are projected; the lower pairs' 16-bit blocks are their
+      // mirrors transposed (beside the chain) and the merge reads their FP32
+      // SS from the mirror (f.proj_sym, set before the loop).
+      const int64_t np_proj = f.proj_sym ? d.n_up : d.NP;
+      const int32_t* pq = f.proj_sym ? d.su_q : nullptr;
+      const int32_t* pi = f.proj_sym ? d.su_i : d.near_i;
+      const int32_t* pj = f.proj_sym ? d.su_j : d.near_j;
+      bool ok = gemm_tc(bf16, D, D, D, A16, d.NP, D, D, pq, f.U16, d.nb, D, D, pj, F.W16, DD, nullptr, D, 1, bf16,
+                        1.0f, nullptr, np_proj, c->status + 2, st) &&
+                gemm_tc(bf16, D, D, D, f.U16, d.nb, D, D, pi, F.W16, np_proj, D, D, nullptr, f.Ahat, DD, pq, D, 0, 0,
+                        1.0f, sc + 1, np_proj, c->status + 2, st, sub16 ? f.Ahat16 : nullptr, sub16 ? R : -1, pi,
+                        pj);
       // off-diagonal pairs then keep only SS in FP32 (the merge's input);
       // their RR, RS and SR live in the 16-bit copy (the substitution's)
       f.ahat_ss_only = sub16 && R % 16 == 0;
+      if (ok && f.proj_sym && d.n_lw) {
+        wait_for(st, sp);
+        launch_transpose16_blocks(D, R, d.n_lw, d.lw_q, d.lw_m, f.Ahat16, sp);
+      }
       if (!ok) return fail(H2_ERR_CUDA, "tensor-core GEMM setup failed at level " + std::to_string(l));
     } else {
       const T* Ain = (l == L) ? Aleaf : f.Ain;
@@ -669,11 +723,17 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       if (std::is_same<T, float>::value) {
         const float* Ah = reinterpret_cast<const float*>(f.Ahat);
         const float* Sh = reinterpret_cast<const float*>(f.Shat);
-        launch_amax_blocks<float>(Ah + (int64_t)R * D + R, d.NP, DD, K, K, D, am, st);
+        // (the lower pairs' SS are their mirrors' transposed: the upper ones
+        // cover every value)
+        launch_amax_blocks<float>(Ah + (int64_t)R * D + R, f.proj_sym ? d.n_up : d.NP, DD, K, K, D, am, st,
+                                  f.proj_sym ? d.su_q : nullptr);
         launch_amax_blocks<float>(Sh, d.FP, (int64_t)K * K, K, K, K, am, st);
         launch_pow2_scale(am, 128.0f, F.scales + 2 * (l - 1), st);
+        // (pairs bound for a lower parent pair are skipped when the parent
+        // projects its upper pairs only)
         launch_merge_lowp(D, K, d.NP, Ah, d.near_i, d.near_j, d.near_dst, d.FP, Sh, d.far_i, d.far_j, d.far_dst,
-                          pf.Ain16, F.scales + 2 * (l - 1), bf16, st);
+                          pf.Ain16, F.scales + 2 * (l - 1), bf16, st, f.proj_sym ? d.mirror : nullptr,
+                          pf.proj_sym ? 1 : 0);
       }
     } else {
       launch_merge<T>(D, K, d.NP, f.Ahat, d.near_i, d.near_j, d.near_dst, d.FP, f.Shat, d.far_i, d.far_j, d.far_dst,
@@ -945,6 +1005,15 @@ h2_status export_ahat_quadrants(const h2_ctx* c, int level, float* out) {
       cudaMemcpy(&isc, f.ahat_isc, sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
     return H2_ERR_CUDA;
   const bool bf = c->f32.bf16 == 1;
+  // upper-pair projection: a lower pair's FP32 SS is its mirror's transposed
+  if (f.proj_sym) {
+    for (int64_t q = 0; q < d.NP; ++q) {
+      if (d.h_near_i[q] <= d.h_near_j[q]) continue;
+      const size_t m = (size_t)d.h_mirror[q];
+      for (size_t r = R; r < D; ++r)
+        for (size_t col = R; col < D; ++col) out[(size_t)q * D * D + r * D + col] = out[m * D * D + col * D + r];
+    }
+  }
   for (int64_t q = 0; q < d.NP; ++q) {
     if (d.h_near_i[q] == d.h_near_j[q]) continue;
     for (size_t r = 0; r < D; ++r)

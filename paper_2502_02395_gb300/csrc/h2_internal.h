@@ -131,6 +131,14 @@ struct DevLevel {
   float* S32u = nullptr;
   void* S16[2] = {nullptr, nullptr};        // couplings scaled into FP16 [0] / BF16 [1]
   float* S16_scale[2] = {nullptr, nullptr};  // their scale and inverse scale (device)
+  // symmetric near list (pair (j, i) present for every (i, j)): the pairs
+  // i <= j ("upper", su_*: their index, i, j) and the others (lw_q) with the
+  // index of their mirror (lw_m); h_mirror[q] on the host (-1: no mirror)
+  bool near_sym = false;
+  int64_t n_up = 0, n_lw = 0;
+  int32_t *su_q = nullptr, *su_i = nullptr, *su_j = nullptr;
+  int32_t *lw_q = nullptr, *lw_m = nullptr, *mirror = nullptr;
+  std::vector<int32_t> h_mirror;
 };
 
 // Factorization storage of one level in storage type T (double or float).
@@ -164,6 +172,9 @@ struct FacLevel {
   void* U16 = nullptr;    // nb * D * D, column-major like U
   bool tc_coup = false;   // couplings on the tensor cores
   void* T16 = nullptr;    // nb * K * K scaled 16-bit T (scale in Factor::tscale[2l])
+  // projection of the upper pairs only (Ahat_ji = Ahat_ij^T): the FP32 SS of
+  // a lower off-diagonal pair is then its mirror's, transposed
+  bool proj_sym = false;
   // s * Ahat in 16 bits (same layout as Ahat), read by the substitution in
   // place of the FP32 Ahat; ahat_isc -> 1 / s on the device.  NULL where the
   // level keeps the substitution on the FP32 Ahat.

@@ -52,14 +52,18 @@ bool make_tile_map(CUtensorMap* tm, const void* base, int bf16, uint64_t rows, u
                    uint32_t box_rows, uint32_t box_cols);
 template <typename S>
 void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
-                        cudaStream_t st);
+                        cudaStream_t st, const int32_t* idx = nullptr);  // idx: block q is base + idx[q] stride
 void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale, cudaStream_t st);
 void launch_inv_scale_product(const float* a, const float* b, float* out, cudaStream_t st);
 template <typename S>
 void launch_to_lowp(int bf16, const S* in, void* out, int64_t n, const float* scale, cudaStream_t st);
 void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_t* ni, const int32_t* nj,
                        const int32_t* ndst, int64_t FP, const float* Shat, const int32_t* fi, const int32_t* fj,
-                       const int32_t* fdst, void* Apar, const float* scale, int bf16, cudaStream_t st);
+                       const int32_t* fdst, void* Apar, const float* scale, int bf16, cudaStream_t st,
+                       const int32_t* mirror = nullptr, int skip_lower = 0);
+// 16-bit D x D blocks dst[k] = (block src[k])^T outside the SS quadrant
+void launch_transpose16_blocks(int D, int R, int64_t n, const int32_t* dst, const int32_t* src, void* A,
+                               cudaStream_t st);
 
 // kernels_solve.cu: substitution (Eq. 24-31 and its mirror), H^2 matvec,
 // refinement vector operations

@@ -669,38 +669,20 @@ __device__ __forceinline__ void qr_reflector(float (&xc)[RPL], int k, int lane, 
   if (lane == 0) *stau = tau;
 }
 
-// Apply reflector (v, tk) to the owner warp's column xn, then form the
-// reflector of that column at row kn.
-template <int RPL>
-__device__ __forceinline__ void qr_ahead(float (&xn)[RPL], const float (&v)[RPL], float tk, int kn, int lane,
-                                         float* vb, float* stau) {
-  if (tk != 0.0f) {
-    float dn = 0.0f;
-#pragma unroll
-    for (int s = 0; s < RPL; ++s) dn = fmaf(v[s], xn[s], dn);
-    for (int o = 16; o; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
-    dn *= tk;
-#pragma unroll
-    for (int s = 0; s < RPL; ++s) xn[s] = fmaf(-dn, v[s], xn[s]);
-  }
-  qr_reflector<RPL>(xn, kn, lane, vb, stau);
-}
-
 // The same factorization in FP32 with the panel in registers: warp w owns
-// columns w, w + 16, ... and lane l rows l, l + 32, ... (D <= 32 RPL,
-// K <= 16 CPW).  Reflector k is published through a double-buffered shared
-// vector; after one barrier every warp applies it to its columns j > k:
-// w = tau v^T x_j (lane-local products, one warp reduction), x_j -= w v.
-// Lookahead: the owner of column k + 1 applies reflector k to that column
-// first and publishes reflector k + 1 before it updates its other columns,
-// so that the chain from one barrier to the next is one column update and
-// one reflector.  The rank-1 updates stay in registers; shared memory
-// carries only v.
-template <int RPL, int CPW>
+// the contiguous columns 8 w .. 8 w + 7 and lane l rows l, l + 32, ...
+// (D <= 32 RPL, K <= 128).  Step k: the owner warp of column k forms the
+// reflector (warp reductions only) and publishes v and tau through a
+// double-buffered shared vector; after one barrier the warps that still
+// hold columns j > k update them: w = tau v^T x_j (lane-local products, one
+// warp reduction), x_j -= w v.  Warps whose columns are all finished skip
+// the step, so the issued work shrinks with k.  The rank-1 updates stay in
+// registers; shared memory carries only v.
+template <int RPL>
 __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* __restrict__ Xin,
                                                      float* __restrict__ Vout, float* __restrict__ tau_out,
                                                      float* __restrict__ Tm) {
-  constexpr int NW = 16;
+  constexpr int NW = 16, CPW = 8;
   __shared__ __align__(16) float vs[2][RPL * 32];
   __shared__ float s_tau[2];
   __shared__ float tile[32][NW * CPW + 1];
@@ -717,58 +699,51 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
-      const int j = warp + NW * c;
+      const int j = CPW * warp + c;
       x[c][s] = (j < K) ? tile[lane][j] : 0.0f;
     }
     __syncthreads();
   }
-  if (K > 0 && warp == 0) qr_reflector<RPL>(x[0], 0, lane, vs[0], &s_tau[0]);
+  // warp-uniform update of this warp's columns c >= c_lo with reflector (vb, tk)
+  auto update = [&](int c_lo, const float* vb, float tk) {
+    float v[RPL];
 #pragma unroll
-  for (int c = 0; c < CPW; ++c) {
-    for (int w = 0; w < NW; ++w) {
-      const int k = c * NW + w;
-      if (k >= K) break;
-      const int buf = k & 1;
-      __syncthreads();  // reflector k is in vs[buf]
-      const float tk = s_tau[buf];
-      // owner and register slot of column k + 1
-      const int wn = (w + 1 < NW) ? w + 1 : 0;
-      constexpr int kLast = CPW - 1;
-      const int cn = (w + 1 < NW) ? c : c + 1;
-      const bool ahead = (warp == wn) && (k + 1 < K);
-      float v[RPL];
+    for (int s = 0; s < RPL; ++s) v[s] = vb[lane + 32 * s];
+    float d[CPW];
 #pragma unroll
-      for (int s = 0; s < RPL; ++s) v[s] = vs[buf][lane + 32 * s];
-      if (ahead) {
-        // column k + 1 first, then its reflector into the other buffer (the
-        // two register slots it can sit in are named statically)
-        if (w + 1 < NW) qr_ahead<RPL>(x[c], v, tk, k + 1, lane, vs[buf ^ 1], &s_tau[buf ^ 1]);
-        else qr_ahead<RPL>(x[c < kLast ? c + 1 : kLast], v, tk, k + 1, lane, vs[buf ^ 1], &s_tau[buf ^ 1]);
+    for (int c = 0; c < CPW; ++c) {
+      d[c] = 0.0f;
+      if (c >= c_lo && CPW * warp + c < K) {
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) d[c] = fmaf(v[s], x[c][s], d[c]);
       }
+    }
+    qr_reduce_cols<CPW>(d);
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      if (c >= c_lo && CPW * warp + c < K) {
+        const float dj = d[c] * tk;
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) x[c][s] = fmaf(-dj, v[s], x[c][s]);
+      }
+    }
+  };
+  int buf = 0;
+  for (int cw = 0; cw < NW; ++cw) {
+#pragma unroll
+    for (int cc = 0; cc < CPW; ++cc) {
+      const int k = CPW * cw + cc;
+      if (k >= K) break;
+      float* vb = vs[buf];
+      if (warp == cw) qr_reflector<RPL>(x[cc], k, lane, vb, &s_tau[buf]);
+      __syncthreads();
+      const float tk = s_tau[buf];
       if (tk != 0.0f) {
-        // lane partial products of the warp's other columns j > k (0 elsewhere)
-        float d[CPW];
-#pragma unroll
-        for (int cc = 0; cc < CPW; ++cc) {
-          const int j = warp + NW * cc;
-          d[cc] = 0.0f;
-          if (j > k && j < K && !(ahead && cc == cn)) {
-#pragma unroll
-            for (int s = 0; s < RPL; ++s) d[cc] = fmaf(v[s], x[cc][s], d[cc]);
-          }
-        }
-        qr_reduce_cols<CPW>(d);
-#pragma unroll
-        for (int cc = 0; cc < CPW; ++cc) {
-          const int j = warp + NW * cc;
-          if (j > k && j < K && !(ahead && cc == cn)) {
-            const float dj = d[cc] * tk;
-#pragma unroll
-            for (int s = 0; s < RPL; ++s) x[cc][s] = fmaf(-dj, v[s], x[cc][s]);
-          }
-        }
+        if (warp > cw) update(0, vb, tk);
+        else if (warp == cw) update(cc + 1, vb, tk);
       }
       if (threadIdx.x == 0) tau_out[(size_t)box * K + k] = tk;
+      buf ^= 1;
     }
   }
   // R (row-major, upper) and V (column-major, unit diagonal, zeros above)
@@ -776,7 +751,7 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
   float* Vb = Vout + (size_t)box * D * K;
 #pragma unroll
   for (int c = 0; c < CPW; ++c) {
-    const int j = warp + NW * c;
+    const int j = CPW * warp + c;
     if (j >= K) continue;
 #pragma unroll
     for (int s = 0; s < RPL; ++s) {
@@ -792,7 +767,7 @@ void launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm,
   if (nb == 0 || K == 0) return;
   if (std::is_same<T, float>::value && D <= 256 && K <= 128) {
     ++g_launches;
-    qr_reg_kernel<8, 8><<<nb, 512, 0, st>>>(D, K, reinterpret_cast<const float*>(Xin), reinterpret_cast<float*>(Vout),
+    qr_reg_kernel<8><<<nb, 512, 0, st>>>(D, K, reinterpret_cast<const float*>(Xin), reinterpret_cast<float*>(Vout),
                                             reinterpret_cast<float*>(tau), reinterpret_cast<float*>(Tm));
     return;
   }

@@ -372,11 +372,12 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
 // rows, lanes over columns.
 template <typename S>
 __global__ void __launch_bounds__(256) amax_blocks_kernel(const S* __restrict__ base, int64_t nblk, int64_t stride,
-                                                          int rows, int cols, int ld, unsigned int* __restrict__ out) {
+                                                          int rows, int cols, int ld, const int32_t* __restrict__ idx,
+                                                          unsigned int* __restrict__ out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float m = 0.0f;
   for (int64_t q = blockIdx.x; q < nblk; q += gridDim.x) {
-    const S* B = base + q * stride;
+    const S* B = base + (idx ? (int64_t)idx[q] : q) * stride;
     for (int r = warp; r < rows; r += 8)
       for (int c = lane; c < cols; c += 32) m = fmaxf(m, fabsf((float)__ldg(B + (int64_t)r * ld + c)));
   }
@@ -385,14 +386,16 @@ __global__ void __launch_bounds__(256) amax_blocks_kernel(const S* __restrict__ 
 }
 template <typename S>
 void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int32_t* idx) {
   if (nblk == 0 || rows == 0 || cols == 0) return;
   const int blocks = (int)std::min<int64_t>(nblk, 152 * 16);
   ++g_launches;
-  amax_blocks_kernel<S><<<blocks, 256, 0, st>>>(base, nblk, stride, rows, cols, ld, out);
+  amax_blocks_kernel<S><<<blocks, 256, 0, st>>>(base, nblk, stride, rows, cols, ld, idx, out);
 }
-template void launch_amax_blocks<float>(const float*, int64_t, int64_t, int, int, int, unsigned int*, cudaStream_t);
-template void launch_amax_blocks<double>(const double*, int64_t, int64_t, int, int, int, unsigned int*, cudaStream_t);
+template void launch_amax_blocks<float>(const float*, int64_t, int64_t, int, int, int, unsigned int*, cudaStream_t,
+                                        const int32_t*);
+template void launch_amax_blocks<double>(const double*, int64_t, int64_t, int, int, int, unsigned int*, cudaStream_t,
+                                         const int32_t*);
 
 // scale[0] = 2^e with amax * 2^e <= target (largest such power of two),
 // scale[1] = 2^-e.  amax = 0 gives scale 1.
@@ -447,14 +450,17 @@ template void launch_to_lowp<double>(int, const double*, void*, int64_t, const f
 // 16-bit merge (Algorithm 2 line 18-20 in the scaled low-precision layout):
 // child SS blocks (FP32 Ahat, rows/cols R..D) and couplings (FP32 Shat) go
 // to the parent's 16-bit near blocks, multiplied by scale[0].  One CTA per
-// child pair; warps over rows, lanes over columns.
+// child pair; warps over rows, lanes over columns.  mirror (non-NULL when
+// only the upper pairs were projected): a lower near pair (i > j) takes its
+// mirror's SS transposed.  skip_lower: the parent level projects its upper
+// pairs only, so pairs bound for a lower parent pair are skipped.
 __global__ void __launch_bounds__(256) merge_lowp_kernel(int D, int K, int64_t NP, const float* __restrict__ Ahat,
                                                          const int32_t* __restrict__ ni, const int32_t* __restrict__ nj,
                                                          const int32_t* __restrict__ ndst, int64_t FP,
                                                          const float* __restrict__ Shat, const int32_t* __restrict__ fi,
                                                          const int32_t* __restrict__ fj, const int32_t* __restrict__ fdst,
                                                          void* __restrict__ Apar, const float* __restrict__ scale,
-                                                         int bf16) {
+                                                         int bf16, const int32_t* __restrict__ mirror, int skip_lower) {
   const int R = D - K, Dp = 2 * K;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float s = scale[0];
@@ -462,29 +468,70 @@ __global__ void __launch_bounds__(256) merge_lowp_kernel(int D, int K, int64_t N
     const bool nr = q < NP;
     const int64_t qq = nr ? q : q - NP;
     const int i = nr ? ni[qq] : fi[qq], j = nr ? nj[qq] : fj[qq];
+    if (skip_lower && (i >> 1) > (j >> 1)) continue;
+    const bool tr = nr && mirror && i > j;
     const int64_t dst = nr ? ndst[qq] : fdst[qq];
-    const float* src = nr ? Ahat + qq * D * D + (int64_t)R * D + R : Shat + qq * K * K;
+    const int64_t sq = tr ? (int64_t)mirror[qq] : qq;
+    const float* src = nr ? Ahat + sq * D * D + (int64_t)R * D + R : Shat + qq * K * K;
     const int lds = nr ? D : K;
     const int64_t obase = dst * Dp * Dp + (int64_t)(i & 1) * K * Dp + (j & 1) * K;
     for (int a = warp; a < K; a += 8) {
-      const float* row = src + (int64_t)a * lds;
       const int64_t o = obase + (int64_t)a * Dp;
       for (int b = lane; b < K; b += 32) {
-        const float v = __ldg(row + b) * s;
+        // entry (a, b): the mirror's (b, a) for a lower pair (L1 holds the
+        // block's columns across the CTA's rows)
+        const float v = __ldg(tr ? src + (int64_t)b * lds + a : src + (int64_t)a * lds + b) * s;
         if (bf16) reinterpret_cast<__nv_bfloat16*>(Apar)[o + b] = __float2bfloat16_rn(v);
         else reinterpret_cast<__half*>(Apar)[o + b] = __float2half_rn(v);
       }
     }
   }
 }
+
+// 16-bit blocks of the lower pairs as their mirrors transposed:
+// A[dst[k]] = A[src[k]]^T (D x D), outside the trailing R.. x R.. (SS)
+// quadrant.  32 x 32 tiles through shared memory; blockIdx.x is the tile,
+// blockIdx.y + 65535 blockIdx.z the pair.
+__global__ void __launch_bounds__(256) transpose16_blocks_kernel(int D, int R, int64_t n, const int32_t* __restrict__ dst,
+                                                                 const int32_t* __restrict__ src,
+                                                                 uint16_t* __restrict__ A) {
+  __shared__ uint16_t t[32][34];
+  const int64_t k = blockIdx.y + (int64_t)blockIdx.z * 65535;
+  if (k >= n) return;
+  const int nt = (D + 31) / 32;
+  const int tr = blockIdx.x / nt, tc = blockIdx.x % nt;  // output tile
+  if (tr * 32 >= R && tc * 32 >= R) return;              // inside SS (R a multiple of 32) or past it
+  const uint16_t* in = A + (int64_t)src[k] * D * D;
+  uint16_t* out = A + (int64_t)dst[k] * D * D;
+  const int x = threadIdx.x & 31, y0 = threadIdx.x >> 5;
+  for (int y = y0; y < 32; y += 8) {  // input tile (tc, tr): rows tc*32 + y, columns tr*32 + x
+    const int r = tc * 32 + y, c = tr * 32 + x;
+    t[y][x] = (r < D && c < D) ? in[(int64_t)r * D + c] : 0;
+  }
+  __syncthreads();
+  for (int y = y0; y < 32; y += 8) {
+    const int r = tr * 32 + y, c = tc * 32 + x;
+    if (r < D && c < D && !(r >= R && c >= R)) out[(int64_t)r * D + c] = t[x][y];
+  }
+}
+void launch_transpose16_blocks(int D, int R, int64_t n, const int32_t* dst, const int32_t* src, void* A,
+                               cudaStream_t st) {
+  if (n <= 0) return;
+  const int nt = (D + 31) / 32;
+  dim3 grid(nt * nt, (unsigned)std::min<int64_t>(n, 65535), (unsigned)((n + 65534) / 65535));
+  ++g_launches;
+  transpose16_blocks_kernel<<<grid, 256, 0, st>>>(D, R, n, dst, src, reinterpret_cast<uint16_t*>(A));
+}
 void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_t* ni, const int32_t* nj,
                        const int32_t* ndst, int64_t FP, const float* Shat, const int32_t* fi, const int32_t* fj,
-                       const int32_t* fdst, void* Apar, const float* scale, int bf16, cudaStream_t st) {
+                       const int32_t* fdst, void* Apar, const float* scale, int bf16, cudaStream_t st,
+                       const int32_t* mirror, int skip_lower) {
   const int64_t n = NP + FP;
   if (n == 0 || K == 0) return;
   const int blocks = (int)std::min<int64_t>(n, 152 * 16);
   ++g_launches;
-  merge_lowp_kernel<<<blocks, 256, 0, st>>>(D, K, NP, Ahat, ni, nj, ndst, FP, Shat, fi, fj, fdst, Apar, scale, bf16);
+  merge_lowp_kernel<<<blocks, 256, 0, st>>>(D, K, NP, Ahat, ni, nj, ndst, FP, Shat, fi, fj, fdst, Apar, scale, bf16,
+                                            mirror, skip_lower);
 }
 
 }  // namespace h2
