@@ -444,7 +444,7 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   CKC(dalloc(c, &F.scales, 2 * (size_t)(L + 1)));
   CKC(dalloc(c, &F.tscale, 2 * (size_t)(L + 1)));
   CKC(dalloc(c, &F.cscale, (size_t)(L + 1)));
-  CKC(dalloc(c, &F.amax, 2 * (size_t)(L + 1)));
+  CKC(dalloc(c, &F.amax, 3 * (size_t)(L + 1)));
   if (std::is_same<T, double>::value) {
     CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
     F.root_luT = reinterpret_cast<T*>(F.root_lu);
@@ -618,6 +618,12 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       gemm<T>(prec, K, K, K, f.Tm, KK, d.far_i, K, false, F.Wc, KK, nullptr, K, false, f.Shat, KK, nullptr, K, T(1),
               T(0), d.FP, sc);
     }
+    // max |Shat| for the 16-bit merge's scale, beside the main chain
+    if (mixed && F.lv[l - 1].tc && std::is_same<T, float>::value) {
+      unsigned int* am = F.amax + 2 * (L + 1) + l;
+      CKC(cudaMemsetAsync(am, 0, sizeof(unsigned int), sc));
+      launch_amax_blocks<float>(reinterpret_cast<const float*>(f.Shat), d.FP, (int64_t)K * K, K, K, K, am, sc);
+    }
     mark_on(evb, sc);
   }
   if (!coup_err.empty()) return fail(H2_ERR_CUDA, coup_err);
@@ -673,14 +679,21 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       const int32_t* pq = f.proj_sym ? d.su_q : nullptr;
       const int32_t* pi = f.proj_sym ? d.su_i : d.near_i;
       const int32_t* pj = f.proj_sym ? d.su_j : d.near_j;
+      // off-diagonal pairs keep only SS in FP32 (the merge's input); their
+      // RR, RS and SR live in the 16-bit copy (the substitution's).  The
+      // GEMM's epilogue also takes max |SS| of those pairs for the 16-bit
+      // merge's scale.
+      f.ahat_ss_only = sub16 && R % 16 == 0;
+      unsigned int* am_ss = nullptr;
+      if (f.ahat_ss_only && F.lv[l - 1].tc) {
+        am_ss = F.amax + (l - 1);
+        CKC(cudaMemsetAsync(am_ss, 0, sizeof(unsigned int), st));
+      }
       bool ok = gemm_tc(bf16, D, D, D, A16, d.NP, D, D, pq, f.U16, d.nb, D, D, pj, F.W16, DD, nullptr, D, 1, bf16,
                         1.0f, nullptr, np_proj, c->status + 2, st) &&
                 gemm_tc(bf16, D, D, D, f.U16, d.nb, D, D, pi, F.W16, np_proj, D, D, nullptr, f.Ahat, DD, pq, D, 0, 0,
                         1.0f, sc + 1, np_proj, c->status + 2, st, sub16 ? f.Ahat16 : nullptr, sub16 ? R : -1, pi,
-                        pj);
-      // off-diagonal pairs then keep only SS in FP32 (the merge's input);
-      // their RR, RS and SR live in the 16-bit copy (the substitution's)
-      f.ahat_ss_only = sub16 && R % 16 == 0;
+                        pj, am_ss);
       if (ok && f.proj_sym && d.n_lw) {
         wait_for(st, sp);
         launch_transpose16_blocks(D, R, d.n_lw, d.lw_q, d.lw_m, f.Ahat16, sp);
@@ -717,18 +730,23 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
     // a6: merge into the parent level's near blocks
     FacLevel<T>& pf = F.lv[l - 1];
     if (mixed && pf.tc) {
-      // 16-bit parent blocks with a fresh power-of-two scale
+      // 16-bit parent blocks with a fresh power-of-two scale from max |SS|
+      // (off-diagonal pairs: the projection's epilogue; diagonal pairs,
+      // after their Schur update: here) and max |Shat| (coupling stream)
       unsigned int* am = F.amax + (l - 1);
-      CKC(cudaMemsetAsync(am, 0, sizeof(unsigned int), st));
       if (std::is_same<T, float>::value) {
         const float* Ah = reinterpret_cast<const float*>(f.Ahat);
         const float* Sh = reinterpret_cast<const float*>(f.Shat);
-        // (the lower pairs' SS are their mirrors' transposed: the upper ones
-        // cover every value)
-        launch_amax_blocks<float>(Ah + (int64_t)R * D + R, f.proj_sym ? d.n_up : d.NP, DD, K, K, D, am, st,
-                                  f.proj_sym ? d.su_q : nullptr);
-        launch_amax_blocks<float>(Sh, d.FP, (int64_t)K * K, K, K, K, am, st);
-        launch_pow2_scale(am, 128.0f, F.scales + 2 * (l - 1), st);
+        if (f.tc && f.ahat_ss_only) {
+          launch_amax_blocks<float>(Ah + (int64_t)R * D + R, d.nb, DD, K, K, D, am, st, d.diag_pair);
+        } else {
+          // (the lower pairs' SS are their mirrors' transposed: the upper
+          // ones cover every value)
+          CKC(cudaMemsetAsync(am, 0, sizeof(unsigned int), st));
+          launch_amax_blocks<float>(Ah + (int64_t)R * D + R, f.proj_sym ? d.n_up : d.NP, DD, K, K, D, am, st,
+                                    f.proj_sym ? d.su_q : nullptr);
+        }
+        launch_pow2_scale(am, 128.0f, F.scales + 2 * (l - 1), st, d.FP > 0 && K > 0 ? F.amax + 2 * (L + 1) + l : nullptr);
         // (pairs bound for a lower parent pair are skipped when the parent
         // projects its upper pairs only)
         launch_merge_lowp(D, K, d.NP, Ah, d.near_i, d.near_j, d.near_dst, d.FP, Sh, d.far_i, d.far_j, d.far_dst,

@@ -44,7 +44,7 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
              int64_t batch, int32_t* err, cudaStream_t st, void* C2 = nullptr, int qsplit = -1,
-             const int32_t* qi = nullptr, const int32_t* qj = nullptr);
+             const int32_t* qi = nullptr, const int32_t* qj = nullptr, unsigned int* amax_ss = nullptr);
 // 2-D tensor map over a rows x cols 16-bit array (row stride ld elements)
 // with box_rows x box_cols tiles, no swizzle (dense row-major tiles in
 // shared memory).  False if the driver or the shape does not allow it.
@@ -53,7 +53,8 @@ bool make_tile_map(CUtensorMap* tm, const void* base, int bf16, uint64_t rows, u
 template <typename S>
 void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
                         cudaStream_t st, const int32_t* idx = nullptr);  // idx: block q is base + idx[q] stride
-void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale, cudaStream_t st);
+void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale, cudaStream_t st,
+                       const unsigned int* amax2 = nullptr);
 void launch_inv_scale_product(const float* a, const float* b, float* out, cudaStream_t st);
 template <typename S>
 void launch_to_lowp(int bf16, const S* in, void* out, int64_t n, const float* scale, cudaStream_t st);

@@ -86,6 +86,9 @@ struct TcArgs {
   int qsplit;
   const int32_t* qi;
   const int32_t* qj;
+  // optional: max |FP32 output| over the SS quadrants of the off-diagonal
+  // entries, accumulated by atomicMax on the float bits (the merge's scale)
+  unsigned int* amax_ss;
 };
 
 __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -188,6 +191,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
     char* Cb = reinterpret_cast<char*>(p.C);
     const int64_t cbase = (int64_t)(p.ic ? p.ic[b] : (int)b) * p.sC;
     const bool split = p.qsplit >= 0 && p.qi[b] != p.qj[b];
+    float ss_max = 0.0f;
     for (int n0 = 0; n0 < p.N; n0 += 16) {
       uint32_t r[16];
       asm volatile(
@@ -206,6 +210,8 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
             float4 v = make_float4(__uint_as_float(r[j]) * alpha, __uint_as_float(r[j + 1]) * alpha,
                                    __uint_as_float(r[j + 2]) * alpha, __uint_as_float(r[j + 3]) * alpha);
             *reinterpret_cast<float4*>(out + j) = v;
+            if (split)
+              ss_max = fmaxf(ss_max, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
           }
         }
         if (p.C2 && !(p.qsplit >= 0 && ss)) {
@@ -235,6 +241,10 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
 #pragma unroll
         for (int j = 0; j < 16; ++j) out[(int64_t)(n0 + j) * p.ldc + m] = __float2half_rn(__uint_as_float(r[j]) * alpha);
       }
+    }
+    if (p.amax_ss && split) {
+      for (int o = 16; o; o >>= 1) ss_max = fmaxf(ss_max, __shfl_xor_sync(0xffffffffu, ss_max, o));
+      if (lane == 0 && ss_max > 0.0f) atomicMax(p.amax_ss, __float_as_uint(ss_max));
     }
     tc_fence_before();
     __syncthreads();
@@ -315,7 +325,7 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
              int64_t batch, int32_t* err, cudaStream_t st, void* C2, int qsplit, const int32_t* qi,
-             const int32_t* qj) {
+             const int32_t* qj, unsigned int* amax_ss) {
   if (batch == 0) return true;
   if (!gemm_tc_supported(M, N, K, lda, ldb, ldc)) return false;
   if ((uint64_t)nA * rowsA >= (1ull << 31) || (uint64_t)nB * rowsB >= (1ull << 31)) return false;
@@ -348,6 +358,7 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
   p.qsplit = split ? qsplit : -1;
   p.qi = split ? qi : nullptr;
   p.qj = split ? qj : nullptr;
+  p.amax_ss = split ? amax_ss : nullptr;
   uint32_t cols = 32;
   while (cols < (uint32_t)N) cols <<= 1;
   p.tmem_cols = cols;
@@ -398,9 +409,12 @@ template void launch_amax_blocks<double>(const double*, int64_t, int64_t, int, i
                                          const int32_t*);
 
 // scale[0] = 2^e with amax * 2^e <= target (largest such power of two),
-// scale[1] = 2^-e.  amax = 0 gives scale 1.
-__global__ void pow2_scale_kernel(const unsigned int* __restrict__ amax_bits, float target, float* __restrict__ scale) {
+// scale[1] = 2^-e.  amax = 0 gives scale 1.  amax is the larger of the two
+// accumulators (the second optional).
+__global__ void pow2_scale_kernel(const unsigned int* __restrict__ amax_bits, const unsigned int* __restrict__ amax2,
+                                  float target, float* __restrict__ scale) {
   float a = __uint_as_float(amax_bits[0]);
+  if (amax2) a = fmaxf(a, __uint_as_float(amax2[0]));
   float s = 1.0f;
   if (a > 0.0f && isfinite(a)) {
     int e = (int)floorf(log2f(target / a));
@@ -411,9 +425,10 @@ __global__ void pow2_scale_kernel(const unsigned int* __restrict__ amax_bits, fl
   scale[0] = s;
   scale[1] = 1.0f / s;
 }
-void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale, cudaStream_t st) {
+void launch_pow2_scale(const unsigned int* amax_bits, float target, float* scale, cudaStream_t st,
+                       const unsigned int* amax2) {
   ++g_launches;
-  pow2_scale_kernel<<<1, 1, 0, st>>>(amax_bits, target, scale);
+  pow2_scale_kernel<<<1, 1, 0, st>>>(amax_bits, amax2, target, scale);
 }
 
 // out[0] = 1 / (a[0] * b[0] * b[0])  (the inverse scale of a product A B B^T)
@@ -514,9 +529,43 @@ __global__ void __launch_bounds__(256) transpose16_blocks_kernel(int D, int R, i
     if (r < D && c < D && !(r >= R && c >= R)) out[(int64_t)r * D + c] = t[x][y];
   }
 }
+// The same with 64 x 64 tiles moved as 32-bit words (two 16-bit entries),
+// for D and R multiples of 64: word x of shared row y holds input entries
+// (y, 2x), (y, 2x + 1); an output word takes entry y of input rows 2x and
+// 2x + 1.
+__global__ void __launch_bounds__(256) transpose16_blocks64_kernel(int D, int R, int64_t n,
+                                                                   const int32_t* __restrict__ dst,
+                                                                   const int32_t* __restrict__ src,
+                                                                   uint16_t* __restrict__ A) {
+  __shared__ uint32_t t[64][33];
+  const int64_t k = blockIdx.y + (int64_t)blockIdx.z * 65535;
+  if (k >= n) return;
+  const int nt = D / 64;
+  const int tr = blockIdx.x / nt, tc = blockIdx.x % nt;  // output tile
+  if (tr * 64 >= R && tc * 64 >= R) return;              // the SS quadrant
+  const uint32_t* in = reinterpret_cast<const uint32_t*>(A + (int64_t)src[k] * D * D);
+  uint32_t* out = reinterpret_cast<uint32_t*>(A + (int64_t)dst[k] * D * D);
+  const int x = threadIdx.x & 31, y0 = threadIdx.x >> 5;
+  const int Dw = D / 2;  // words per row
+  for (int y = y0; y < 64; y += 8) t[y][x] = in[(int64_t)(tc * 64 + y) * Dw + tr * 32 + x];
+  __syncthreads();
+  for (int y = y0; y < 64; y += 8) {
+    const uint32_t a = t[2 * x][y >> 1], b = t[2 * x + 1][y >> 1];
+    const uint32_t lo = (y & 1) ? (a >> 16) : (a & 0xffffu), hi = (y & 1) ? (b >> 16) : (b & 0xffffu);
+    out[(int64_t)(tr * 64 + y) * Dw + tc * 32 + x] = lo | (hi << 16);
+  }
+}
+
 void launch_transpose16_blocks(int D, int R, int64_t n, const int32_t* dst, const int32_t* src, void* A,
                                cudaStream_t st) {
   if (n <= 0) return;
+  if (D % 64 == 0 && R % 64 == 0) {
+    const int nt = D / 64;
+    dim3 grid(nt * nt, (unsigned)std::min<int64_t>(n, 65535), (unsigned)((n + 65534) / 65535));
+    ++g_launches;
+    transpose16_blocks64_kernel<<<grid, 256, 0, st>>>(D, R, n, dst, src, reinterpret_cast<uint16_t*>(A));
+    return;
+  }
   const int nt = (D + 31) / 32;
   dim3 grid(nt * nt, (unsigned)std::min<int64_t>(n, 65535), (unsigned)((n + 65534) / 65535));
   ++g_launches;
