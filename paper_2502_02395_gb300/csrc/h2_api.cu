@@ -577,16 +577,34 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
         gemm<T>(prec, D, K, K, f.Vq, DK, nullptr, D, true, f.Tw, KK, nullptr, K, false, W1, DK, nullptr, K, T(1), T(0),
                 nb, sb);
       }
-      launch_perm_identity<T>(nb, D, K, f.U, sb);
-      if (K > 0) {
-        if (R > 0)
-          gemm<T>(prec, R, D, K, f.Vq + K, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U, DD, nullptr, D, T(-1),
-                  T(1), nb, sb);
-        gemm<T>(prec, K, D, K, f.Vq, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U + (int64_t)R * D, DD, nullptr,
-                D, T(-1), T(1), nb, sb);
+      if constexpr (std::is_same<T, float>::value) {
+        // one pass: U, its row-major copy and the 16-bit copy
+        if (K > 0 && D % 4 == 0 && K % 4 == 0) {
+          launch_form_u(nb, D, K, W1, f.Vq, f.U, f.Ur, f.tc ? f.U16 : nullptr, bf16, sb);
+        } else {
+          launch_perm_identity<T>(nb, D, K, f.U, sb);
+          if (K > 0) {
+            if (R > 0)
+              gemm<T>(prec, R, D, K, f.Vq + K, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U, DD, nullptr, D,
+                      T(-1), T(1), nb, sb);
+            gemm<T>(prec, K, D, K, f.Vq, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U + (int64_t)R * D, DD,
+                    nullptr, D, T(-1), T(1), nb, sb);
+          }
+          launch_transpose_blocks<T>(nb, D, f.U, f.Ur, sb);
+          if (f.tc) launch_to_lowp<T>(bf16, f.U, f.U16, (int64_t)d.nb * DD, nullptr, sb);
+        }
+      } else {
+        launch_perm_identity<T>(nb, D, K, f.U, sb);
+        if (K > 0) {
+          if (R > 0)
+            gemm<T>(prec, R, D, K, f.Vq + K, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U, DD, nullptr, D,
+                    T(-1), T(1), nb, sb);
+          gemm<T>(prec, K, D, K, f.Vq, DK, nullptr, D, true, W1, DK, nullptr, K, true, f.U + (int64_t)R * D, DD,
+                  nullptr, D, T(-1), T(1), nb, sb);
+        }
+        launch_transpose_blocks<T>(nb, D, f.U, f.Ur, sb);
+        if (f.tc) launch_to_lowp<T>(bf16, f.U, f.U16, (int64_t)d.nb * DD, nullptr, sb);
       }
-      launch_transpose_blocks<T>(nb, D, f.U, f.Ur, sb);
-      if (f.tc) launch_to_lowp<T>(bf16, f.U, f.U16, (int64_t)d.nb * DD, nullptr, sb);
     }
     mark_on(evb, sb);
     // the couplings of level l follow its bases on the coupling stream

@@ -26,6 +26,10 @@ template <typename T>
 void launch_wy_tfactor(int nb, int K, const T* S, const T* tau, T* Tw, cudaStream_t st);
 template <typename T>
 void launch_perm_identity(int nb, int D, int K, T* U, cudaStream_t st);
+// U = [Q[:, K:] Q[:, :K]], Q = I - W1 V^T (W1 D x K row-major, V D x K
+// column-major), as column-major U, row-major Ur and 16-bit U16 (NULL: none)
+void launch_form_u(int64_t nb, int D, int K, const float* W1, const float* V, float* U, float* Ur, void* u16,
+                   int bf16, cudaStream_t st);
 template <typename T>
 void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
                        int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st);

@@ -190,8 +190,88 @@ __device__ __forceinline__ void g2_store_a(float (*As)[G2_LD], int tA, const flo
   }
 }
 
+// acc = op(A)[m0.., :] op(B)[:, n0..] for one 128 x 128 tile (thread layout
+// of the tile kernel below); As / Bs are the CTA's two shared buffers.
 template <typename TB>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void g2_mainloop(int M, int N, int K, const float* __restrict__ Ab, int lda, int tA,
+                                            const TB* __restrict__ Bb, int ldb, int tB, int m0, int n0, int vecA,
+                                            int vecB, float (*As)[G2_BK][G2_LD], float (*Bs)[G2_BK][G2_LD],
+                                            float (&acc)[8][8]) {
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  // op(B)(k, n) tile: B[k * ldb + n] (!tB) or B[n * ldb + k] (tB), stored as
+  // Bs[k][n]; the same code as A with the roles of m and n exchanged
+  auto load_b = [&](int k0, float (&rb)[4]) {
+    if (tB) {  // B[n * ldb + k]: 4 consecutive k of row n
+      const int n = n0 + (t >> 1), k = k0 + (t & 1) * 4;
+      if (vecB && n < N && k + 3 < K) {
+        const float4 v = *reinterpret_cast<const float4*>(Bb + (int64_t)n * ldb + k);
+        rb[0] = v.x, rb[1] = v.y, rb[2] = v.z, rb[3] = v.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) rb[e] = (n < N && k + e < K) ? (float)Bb[(int64_t)n * ldb + k + e] : 0.0f;
+      }
+    } else {  // B[k * ldb + n]: 4 consecutive n of row k
+      const int k = k0 + (t >> 5), n = n0 + (t & 31) * 4;
+      if (vecB && k < K && n + 3 < N) {
+        const float4 v = *reinterpret_cast<const float4*>(Bb + (int64_t)k * ldb + n);
+        rb[0] = v.x, rb[1] = v.y, rb[2] = v.z, rb[3] = v.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) rb[e] = (k < K && n + e < N) ? (float)Bb[(int64_t)k * ldb + n + e] : 0.0f;
+      }
+    }
+  };
+  auto store_b = [&](float (*Bsb)[G2_LD], const float (&rb)[4]) {
+    if (tB) {
+      const int n = t >> 1, k = (t & 1) * 4;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) Bsb[k + e][n] = rb[e];
+    } else {
+      const int k = t >> 5, n = (t & 31) * 4;
+      *reinterpret_cast<float4*>(&Bsb[k][n]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    }
+  };
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+  float ra[4], rb[4];
+  g2_load_a(Ab, lda, tA, M, K, m0, 0, vecA, ra);
+  load_b(0, rb);
+  g2_store_a(As[0], tA, ra);
+  store_b(Bs[0], rb);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += G2_BK) {
+    const bool more = k0 + G2_BK < K;
+    if (more) {
+      g2_load_a(Ab, lda, tA, M, K, m0, k0 + G2_BK, vecA, ra);
+      load_b(k0 + G2_BK, rb);
+    }
+#pragma unroll
+    for (int kk = 0; kk < G2_BK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + 64]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4 + 64]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+      g2_store_a(As[buf ^ 1], tA, ra);
+      store_b(Bs[buf ^ 1], rb);
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+}
+
+template <typename TB>
+__global__ void __launch_bounds__(256, 2)
 gemm_f32_tile_kernel(int M, int N, int K, const float* __restrict__ A, int64_t sA, const int32_t* __restrict__ ia,
                      int lda, int tA, const TB* __restrict__ B, int64_t sB, const int32_t* __restrict__ ib, int ldb,
                      int tB, float* __restrict__ C, int64_t sC, const int32_t* __restrict__ ic, int ldc, float alpha,
@@ -204,77 +284,8 @@ gemm_f32_tile_kernel(int M, int N, int K, const float* __restrict__ A, int64_t s
     const float* Ab = A + (ia ? (int64_t)ia[b] : b) * sA;
     const TB* Bb = B + (ib ? (int64_t)ib[b] : b) * sB;
     float* Cb = C + (ic ? (int64_t)ic[b] : b) * sC;
-    // op(B)(k, n) tile: B[k * ldb + n] (!tB) or B[n * ldb + k] (tB), stored as
-    // Bs[k][n]; the same code as A with the roles of m and n exchanged
-    auto load_b = [&](int k0, float (&rb)[4]) {
-      if (tB) {  // B[n * ldb + k]: 4 consecutive k of row n
-        const int n = n0 + (t >> 1), k = k0 + (t & 1) * 4;
-        if (vecB && n < N && k + 3 < K) {
-          const float4 v = *reinterpret_cast<const float4*>(Bb + (int64_t)n * ldb + k);
-          rb[0] = v.x, rb[1] = v.y, rb[2] = v.z, rb[3] = v.w;
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) rb[e] = (n < N && k + e < K) ? (float)Bb[(int64_t)n * ldb + k + e] : 0.0f;
-        }
-      } else {  // B[k * ldb + n]: 4 consecutive n of row k
-        const int k = k0 + (t >> 5), n = n0 + (t & 31) * 4;
-        if (vecB && k < K && n + 3 < N) {
-          const float4 v = *reinterpret_cast<const float4*>(Bb + (int64_t)k * ldb + n);
-          rb[0] = v.x, rb[1] = v.y, rb[2] = v.z, rb[3] = v.w;
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e) rb[e] = (k < K && n + e < N) ? (float)Bb[(int64_t)k * ldb + n + e] : 0.0f;
-        }
-      }
-    };
-    auto store_b = [&](float (*Bsb)[G2_LD], const float (&rb)[4]) {
-      if (tB) {
-        const int n = t >> 1, k = (t & 1) * 4;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) Bsb[k + e][n] = rb[e];
-      } else {
-        const int k = t >> 5, n = (t & 31) * 4;
-        *reinterpret_cast<float4*>(&Bsb[k][n]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
-      }
-    };
     float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    float ra[4], rb[4];
-    g2_load_a(Ab, lda, tA, M, K, m0, 0, vecA, ra);
-    load_b(0, rb);
-    g2_store_a(As[0], tA, ra);
-    store_b(Bs[0], rb);
-    __syncthreads();
-    int buf = 0;
-    for (int k0 = 0; k0 < K; k0 += G2_BK) {
-      const bool more = k0 + G2_BK < K;
-      if (more) {
-        g2_load_a(Ab, lda, tA, M, K, m0, k0 + G2_BK, vecA, ra);
-        load_b(k0 + G2_BK, rb);
-      }
-#pragma unroll
-      for (int kk = 0; kk < G2_BK; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + 64]);
-        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4 + 64]);
-        const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-      }
-      if (more) {
-        g2_store_a(As[buf ^ 1], tA, ra);
-        store_b(Bs[buf ^ 1], rb);
-      }
-      __syncthreads();
-      buf ^= 1;
-    }
+    g2_mainloop<TB>(M, N, K, Ab, lda, tA, Bb, ldb, tB, m0, n0, vecA, vecB, As, Bs, acc);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int m = m0 + ty * 4 + (i & 3) + (i >> 2) * 64;
@@ -301,6 +312,79 @@ gemm_f32_tile_kernel(int M, int N, int K, const float* __restrict__ A, int64_t s
       }
     }
   }
+}
+
+// U from the compact WY form in one pass: Q = I - W1 V^T (W1 = V Tw, D x K
+// row-major; V column-major D x K) and U = [Q[:, K:] Q[:, :K]] written three
+// ways: column-major U, row-major Ur and the 16-bit column-major copy U16
+// (u16 NULL: none).  Tiles and main loop of the tile GEMM; column n of Q is
+// column n - K of U for n >= K and n + R otherwise.  D and K are multiples
+// of 4, so each thread's 4 x 4 groups lie wholly inside or outside the
+// block and on one side of column K.
+__global__ void __launch_bounds__(256, 2) form_u_kernel(int D, int K, const float* __restrict__ W1,
+                                                        const float* __restrict__ V, float* __restrict__ U,
+                                                        float* __restrict__ Ur, void* __restrict__ u16, int bf16,
+                                                        int64_t nb) {
+  __shared__ __align__(16) float As[2][G2_BK][G2_LD];
+  __shared__ __align__(16) float Bs[2][G2_BK][G2_LD];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int m0 = blockIdx.y * G2_BM, n0 = blockIdx.x * G2_BN;
+  const int R = D - K;
+  for (int64_t b = blockIdx.z; b < nb; b += gridDim.z) {
+    const float* Ab = W1 + b * (int64_t)D * K;
+    const float* Bb = V + b * (int64_t)D * K;  // V^T row-major K x D
+    float acc[8][8];
+    g2_mainloop<float>(D, D, K, Ab, K, 0, Bb, D, 0, m0, n0, 1, 1, As, Bs, acc);
+    float* Ub = U + b * (int64_t)D * D;
+    float* Urb = Ur + b * (int64_t)D * D;
+    uint16_t* U16b = u16 ? reinterpret_cast<uint16_t*>(u16) + b * (int64_t)D * D : nullptr;
+    // three passes over the thread's four 4 x 4 groups (rows mb.., columns
+    // nbase..), one output each, to keep few addresses live
+#pragma unroll
+    for (int pass = 0; pass < 3; ++pass) {
+      if (pass == 2 && !U16b) break;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int q4 = g >> 1, h = g & 1;
+        const int mb = m0 + ty * 4 + q4 * 64, nbase = n0 + tx * 4 + h * 64;
+        if (mb >= D || nbase >= D) continue;
+        const int cb = nbase >= K ? nbase - K : nbase + R;  // U column of Q column nbase
+        auto q = [&](int r, int e) {
+          return (mb + r == nbase + e ? 1.0f : 0.0f) - acc[q4 * 4 + r][h * 4 + e];
+        };
+        if (pass == 0) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            *reinterpret_cast<float4*>(Urb + (int64_t)(mb + r) * D + cb) =
+                make_float4(q(r, 0), q(r, 1), q(r, 2), q(r, 3));
+        } else if (pass == 1) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            *reinterpret_cast<float4*>(Ub + (int64_t)(cb + e) * D + mb) = make_float4(q(0, e), q(1, e), q(2, e), q(3, e));
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            uint32_t w0, w1;
+            if (bf16) {
+              __nv_bfloat162 x0 = __floats2bfloat162_rn(q(0, e), q(1, e)), x1 = __floats2bfloat162_rn(q(2, e), q(3, e));
+              w0 = *reinterpret_cast<uint32_t*>(&x0), w1 = *reinterpret_cast<uint32_t*>(&x1);
+            } else {
+              __half2 x0 = __floats2half2_rn(q(0, e), q(1, e)), x1 = __floats2half2_rn(q(2, e), q(3, e));
+              w0 = *reinterpret_cast<uint32_t*>(&x0), w1 = *reinterpret_cast<uint32_t*>(&x1);
+            }
+            *reinterpret_cast<uint2*>(U16b + (int64_t)(cb + e) * D + mb) = make_uint2(w0, w1);
+          }
+        }
+      }
+    }
+  }
+}
+void launch_form_u(int64_t nb, int D, int K, const float* W1, const float* V, float* U, float* Ur, void* u16,
+                   int bf16, cudaStream_t st) {
+  if (nb == 0 || D == 0) return;
+  dim3 g((D + G2_BN - 1) / G2_BN, (D + G2_BM - 1) / G2_BM, (unsigned)std::min<int64_t>(nb, 65535));
+  ++g_launches;
+  form_u_kernel<<<g, 256, 0, st>>>(D, K, W1, V, U, Ur, u16, bf16, nb);
 }
 
 static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
