@@ -301,6 +301,29 @@ h2_status setup_device(h2_ctx* c) {
   c->S32p.assign(L + 1, nullptr);
   c->Slo.assign(L + 1, nullptr);
   size_t npart = c->sym ? (size_t)c->npu * 2 * lf.D : 0;
+  // one batch of all levels' stored coupling pairs when every level with
+  // couplings qualifies for the symmetric form with one common rank
+  std::vector<int64_t> goff(L + 1, 0);
+  {
+    bool ok = true;
+    int K0 = -1;
+    int64_t tot = 0;
+    for (int l = 1; l <= L && ok; ++l) {
+      const DevLevel& d = c->lv[l];
+      if (d.FP == 0) continue;
+      if (!sym_leaf_supported(d.K) || (K0 >= 0 && d.K != K0) || c->hat_off[l] % d.K != 0) ok = false;
+      K0 = d.K;
+      goff[l] = tot;
+      for (int64_t q = 0; q < d.FP; ++q) tot += d.h_far_i[q] < d.h_far_j[q];
+    }
+    c->cb_ok = ok && tot > 0;
+    if (c->cb_ok) {
+      c->cb_K = K0;
+      c->cb_n = tot;
+      CKC(dalloc(c, &c->S32u_all, (size_t)tot * K0 * K0));
+    }
+  }
+  std::vector<int32_t> cbi, cbj;
   for (int l = 1; l <= L; ++l) {
     DevLevel& d = c->lv[l];
     const size_t nx = (size_t)d.nb * d.D * d.K, ns = (size_t)std::max<int64_t>(d.FP, 1) * d.K * d.K;
@@ -334,7 +357,14 @@ h2_status setup_device(h2_ctx* c) {
       CKS(upload(c, &d.fs_ptr, ptr));
       CKS(upload(c, &d.fs_ent, ent));
       const int64_t KK = (int64_t)d.K * d.K;
-      CKC(dalloc(c, &d.S32u, (size_t)(d.fpu * KK)));
+      if (c->cb_ok) {
+        d.fs_goff = goff[l];
+        d.S32u = c->S32u_all + goff[l] * KK;
+        const int32_t s0 = (int32_t)(c->hat_off[l] / d.K);
+        for (int64_t k = 0; k < d.fpu; ++k) cbi.push_back(s0 + fi[k]), cbj.push_back(s0 + fj[k]);
+      } else {
+        CKC(dalloc(c, &d.S32u, (size_t)(d.fpu * KK)));
+      }
       launch_gather_blocks(d.S, fsq, KK, d.fpu, d.S32u, 0);
       npart = std::max(npart, (size_t)d.fpu * 2 * d.K);
     }
@@ -349,6 +379,11 @@ h2_status setup_device(h2_ctx* c) {
     c->S64p[l] = d.S;
     c->X32p[l] = d.X32;
     c->S32p[l] = d.S32;
+  }
+  if (c->cb_ok) {
+    CKS(upload(c, &c->cb_i, cbi));
+    CKS(upload(c, &c->cb_j, cbj));
+    npart = std::max(npart, (size_t)c->cb_n * 2 * c->cb_K);
   }
   if (npart) {
     CKC(dalloc(c, &c->part32, npart));
@@ -960,6 +995,27 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
   const std::vector<int64_t>& off = c->hat_off;
   launch_matvec_up<T>(c->lv[L], X[L], x, xh + off[L], st);
   for (int l = L - 1; l >= 1; --l) launch_matvec_up<T>(c->lv[l], X[l], xh + off[l + 1], xh + off[l], st);
+  if constexpr (std::is_same<T, float>::value) {
+    if (c->cb_ok) {
+      // every level's coupling products in one launch, then the downward
+      // pass adds each level's sums as it goes
+      launch_matvec_sym_pairs(c->cb_K, c->cb_n, c->cb_i, c->cb_j, c->S32u_all, xh, c->part32, true, st);
+      const DevLevel& d1 = c->lv[1];
+      if (d1.FP > 0 && d1.K > 0)
+        launch_matvec_sym_sum<float>(d1.nb, d1.K, 0, d1.fs_ptr, d1.fs_ent, nullptr, nullptr,
+                                     c->part32 + d1.fs_goff * 2 * d1.K, yh + off[1], st);
+      else
+        cudaMemsetAsync(yh + off[1], 0, sizeof(T) * (size_t)d1.nb * d1.K, st);
+      for (int l = 1; l < L; ++l) {
+        const DevLevel& dc = c->lv[l + 1];
+        const bool has = dc.FP > 0 && dc.K > 0;
+        launch_matvec_down_far<float>(c->lv[l], X[l], yh + off[l], yh + off[l + 1], has ? dc.fs_ptr : nullptr,
+                                      has ? dc.fs_ent : nullptr, c->part32 + dc.fs_goff * 2 * dc.K, st);
+      }
+      leaf(X[L], yh + off[L]);
+      return;
+    }
+  }
   for (int l = 1; l <= L; ++l) {
     const DevLevel& d = c->lv[l];
     if constexpr (std::is_same<T, float>::value) {

@@ -126,6 +126,7 @@ struct DevLevel {
   // j = box), CSR over boxes
   bool far_sym = false;
   int64_t fpu = 0;
+  int64_t fs_goff = 0;  // first index of this level's stored pairs in the all-level batch
   int32_t *fs_i = nullptr, *fs_j = nullptr, *fs_ent = nullptr;
   int64_t* fs_ptr = nullptr;
   float* S32u = nullptr;
@@ -267,6 +268,14 @@ struct h2_ctx {
   float* part32 = nullptr;   // npu * 2 D partial products (FP32 matvec)
   double* part64 = nullptr;  // the same for the FP32-pair matvec
   float *xhat32 = nullptr, *yhat32 = nullptr;
+  // the stored coupling pairs of every level as one batch (levels with the
+  // same rank cb_K): the FP32 matvec forms all levels' coupling products in
+  // one launch; cb_i / cb_j index K-slots of xhat32
+  bool cb_ok = false;
+  int cb_K = 0;
+  int64_t cb_n = 0;
+  int32_t *cb_i = nullptr, *cb_j = nullptr;
+  float* S32u_all = nullptr;
   std::vector<double*> X64p, S64p;  // per-level pointers (index l; [0] unused)
   std::vector<float*> X32p, S32p;
   std::vector<int64_t> hat_off;  // per-level offsets into xhat / yhat

@@ -123,6 +123,12 @@ void launch_split_lo(const double* a, const float* hi, float* lo, int64_t n, cud
 // per stored pair k = (ui[k], uj[k]) the partial products [A x_j; A^T x_i]
 // into part (2 D per pair), then per box y = X yh + its partial products.
 bool sym_leaf_supported(int D);  // D = 128 or 256
+// Downward step [yh_2p; yh_2p+1] = X_p yh_p + (the children's coupling
+// products summed over their CSR lists cptr / cent into part, Kc = D / 2
+// entries per product; cptr NULL: none)
+template <typename T>
+void launch_matvec_down_far(const DevLevel& L, const T* X, const T* yh, T* yh_child, const int64_t* cptr,
+                            const int32_t* cent, const T* part, cudaStream_t st);
 // (pdl: launched to overlap its predecessor; off where events bracket it)
 void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A, const float* x,
                              float* part, bool pdl, cudaStream_t st);

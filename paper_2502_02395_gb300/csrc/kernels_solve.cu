@@ -1224,6 +1224,53 @@ void launch_matvec_down(const DevLevel& L, const T* X, const T* yh, T* yh_child,
              small_level(L.nb) ? 1 : 0);
 }
 
+// downward step that also adds the children's coupling products:
+// [yh_2p; yh_2p+1] = X_p yh_p + f, f[h Kc + r] = sum over the partial
+// products of child c = 2p + h (CSR cptr / cent over the child level; entry
+// e = 2k (+1) is part[(2k (+1)) Kc ..]).  cptr NULL: f = 0.  Overwrites the
+// children's yh (the per-level sums of the coupling products are folded in).
+template <typename T>
+__global__ void __launch_bounds__(256, 2) mv_down_far_kernel(int D, int K, const T* __restrict__ X,
+                                                             const T* __restrict__ yh, T* __restrict__ yhc,
+                                                             const int64_t* __restrict__ cptr,
+                                                             const int32_t* __restrict__ cent,
+                                                             const T* __restrict__ part, int pf) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sy = reinterpret_cast<T*>(smraw);  // K
+  T* sf = sy + ((K + 3) & ~3);          // D
+  const int p = blockIdx.x;
+  const int Kc = D / 2;
+  if (pf) prefetch_l2(X + (int64_t)p * D * K, (int64_t)D * K * sizeof(T));
+  griddep_wait();
+  griddep_launch_next();
+  for (int e = threadIdx.x; e < K; e += 256) sy[e] = yh[(int64_t)p * K + e];
+  for (int r = threadIdx.x; r < D; r += 256) {
+    T s = T(0);
+    if (cptr) {
+      const int c = 2 * p + r / Kc, rr = r % Kc;
+      for (int64_t q = cptr[c]; q < cptr[c + 1]; ++q) s += part[(int64_t)cent[q] * Kc + rr];
+    }
+    sf[r] = s;
+  }
+  __syncthreads();
+  T acc[kRPW];
+  T* out = yhc + (int64_t)p * D;
+  for (int r0 = 0; r0 < D; r0 += kChunk) {
+    zero(acc);
+    rows_acc<T, kRPW>(r0, X + (int64_t)p * D * K, K, D, K, sy, acc);
+    rows_finish<T, kRPW>(r0, D, acc, T(1), sf, out);
+  }
+}
+template <typename T>
+void launch_matvec_down_far(const DevLevel& L, const T* X, const T* yh, T* yh_child, const int64_t* cptr,
+                            const int32_t* cent, const T* part, cudaStream_t st) {
+  const size_t sm = sizeof(T) * ((size_t)((L.K + 3) & ~3) + L.D);
+  launch_pdl(mv_down_far_kernel<T>, L.nb, 256, sm, st, L.D, L.K, X, yh, yh_child, cptr, cent, part,
+             small_level(L.nb) ? 1 : 0);
+}
+template void launch_matvec_down_far<float>(const DevLevel&, const float*, const float*, float*, const int64_t*,
+                                            const int32_t*, const float*, cudaStream_t);
+
 // leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j
 template <typename T>
 __global__ void __launch_bounds__(256, 2) mv_leaf_kernel(int D, int K, const int64_t* __restrict__ ptr,
@@ -1608,8 +1655,9 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
     for (int e = 0; e < 4; ++e) wH[h][e] = 0.0f, wL[h][e] = 0.0f;
   __syncthreads();
   double* u = part + k * 2 * D;
-  for (int r0 = warp; r0 < D; r0 += 8 * RPW) {
-    float4 vh[RPW][CH], vl[RPW][CH];
+  // rows r0 + 8 t (t < RPW) of this warp; the next group's loads are issued
+  // before the current group is used
+  auto load_rows = [&](int r0, float4 (&vh)[RPW][CH], float4 (&vl)[RPW][CH]) {
 #pragma unroll
     for (int t = 0; t < RPW; ++t) {
       const int r = r0 + 8 * t;
@@ -1620,6 +1668,16 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
         vl[t][h] = (r < D) ? __ldg(reinterpret_cast<const float4*>(Ml + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
+  };
+  float4 nh[RPW][CH], nl[RPW][CH];
+  load_rows(warp, nh, nl);
+  for (int r0 = warp; r0 < D; r0 += 8 * RPW) {
+    float4 vh[RPW][CH], vl[RPW][CH];
+#pragma unroll
+    for (int t = 0; t < RPW; ++t)
+#pragma unroll
+      for (int h = 0; h < CH; ++h) vh[t][h] = nh[t][h], vl[t][h] = nl[t][h];
+    if (r0 + 8 * RPW < D) load_rows(r0 + 8 * RPW, nh, nl);
     double su[RPW];
 #pragma unroll
     for (int t = 0; t < RPW; ++t) {
