@@ -894,10 +894,8 @@ template <typename T>
 void ulv_sweep(h2_ctx* c, Factor<T>& F) {
   const int L = c->L;
   cudaStream_t st = c->stream;
-  for (int l = L; l >= 1; --l) {
-    const DevLevel& d = c->lv[l];
-    FacLevel<T>& f = F.lv[l];
-    // below the leaf level the input comes from the children's SR sums
+  // the children's input of level l (below the leaf level: their SR sums)
+  auto child_in = [&](int l) {
     ChildIn<T> ch;
     if (l < L) {
       const DevLevel& dc = c->lv[l + 1];
@@ -908,15 +906,19 @@ void ulv_sweep(h2_ctx* c, Factor<T>& F) {
       with_ahat(fc, F.bf16, [&](auto, const float* isc) { ch.iscale = isc; });
       ch.D = dc.D, ch.R = dc.R, ch.K = dc.K;
     }
-    launch_fwd1<T>(d, f, ch, st);
+    return ch;
+  };
+  auto fwd = [&](int l) {
+    const DevLevel& d = c->lv[l];
+    FacLevel<T>& f = F.lv[l];
+    launch_fwd1<T>(d, f, child_in(l), st);
     with_ahat(f, F.bf16, [&](auto A, const float* isc) {
       using TS = std::remove_const_t<std::remove_pointer_t<decltype(A)>>;
       launch_fwd2<T, TS>(d, f, A, isc, st);
       launch_fwd3<T, TS>(d, f, A, isc, l == 1 ? F.root_vec : nullptr, st);
     });
-  }
-  launch_gemv_rows<T>(c->lv[0].D, F.root_inv, F.root_vec, F.root_x, st);
-  for (int l = 1; l <= L; ++l) {
+  };
+  auto bwd = [&](int l) {
     const DevLevel& d = c->lv[l];
     FacLevel<T>& f = F.lv[l];
     const T* px = (l > 1) ? F.lv[l - 1].xs : F.root_x;
@@ -925,7 +927,10 @@ void ulv_sweep(h2_ctx* c, Factor<T>& F) {
       launch_bwd1<T, TS>(d, f, A, isc, px, st);
       launch_bwd2<T, TS>(d, f, A, isc, px, st);
     });
-  }
+  };
+  for (int l = L; l >= 1; --l) fwd(l);
+  launch_gemv_rows<T>(c->lv[0].D, F.root_inv, F.root_vec, F.root_x, st);
+  for (int l = 1; l <= L; ++l) bwd(l);
 }
 template <typename T>
 T* ulv_in(h2_ctx* c, Factor<T>& F) { return c->L >= 1 ? F.lv[c->L].vin : F.root_vec; }

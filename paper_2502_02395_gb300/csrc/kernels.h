@@ -88,6 +88,7 @@ struct ChildIn {
 };
 template <typename T>
 void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const ChildIn<T>& ch, cudaStream_t st);
+
 template <typename T, typename TS>
 void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, cudaStream_t st);
 template <typename T, typename TS>

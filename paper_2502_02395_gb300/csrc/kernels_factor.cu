@@ -1308,7 +1308,7 @@ constexpr int kGbP = 16;  // panel width
 struct GbShared {
   float WmT[2][kGbP][128];   // (E - I)[:, p_a], transposed: WmT[a][r]
   float Prow[2][kGbP][128];  // rows p_a of the matrix before the panel
-  float prs[8][kGbP];        // per warp: the current pivot row of its panel
+  float pan[128][kGbP + 1];   // the panel warp's columns, moved between its tile and row layouts
   int pidx[2][128];          // panel slot a of row r, -1 for rows that are no pivot of the panel
   unsigned char used[128];   // rows already chosen as pivots
   int prow[128], pinv[128], rowat[128];
@@ -1341,96 +1341,102 @@ __global__ void __launch_bounds__(256, 2) gj_blocked_kernel(int D, int R, const 
   for (int pn = 0; pn < npan; ++pn) {
     const int b = pn & 1;
     if (warp == pn) {
-      // (1) the panel's 16 steps
-      unsigned used = 0;
+      // (1) the panel's 16 steps, in a row layout: lane l holds rows
+      // l + 32 k (k < 4) of the 16 panel columns
 #pragma unroll
-      for (int i = 0; i < 8; ++i) used |= (unsigned)sh.used[r0 + i] << i;
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sh.pan[r0 + i][8 * h + j] = x[i][j], x[i][j] = 0.0f;  // (x reloaded below)
       for (int e = lane; e < 128; e += 32) sh.pidx[b][e] = -1;
       __syncwarp();
-      float* prs = sh.prs[warp];
+      float y[4][kGbP];
+      unsigned used = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        used |= (unsigned)sh.used[lane + 32 * k] << k;
+#pragma unroll
+        for (int c = 0; c < kGbP; ++c) y[k][c] = sh.pan[lane + 32 * k][c];
+      }
       bool bad = false;
-#pragma unroll 1
-      for (int ha = 0; ha < 2; ++ha)
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        const int a = 8 * ha + jj;
-        const int k = kGbP * pn + a;
-        if (k >= R || bad) break;
-        float best = -1.0f;
+      for (int a = 0; a < kGbP; ++a) {
+        const int kcol = kGbP * pn + a;
+        if (kcol >= R || bad) break;
+        // pivot: the first largest |y| of column a over unused rows
+        float best = -1.0f, sv = 0.0f;
         int bi = -1;
-        if (h == ha) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float v = fabsf(x[i][jj]);
-            if (!((used >> i) & 1u) && v > best) best = v, bi = r0 + i;
-          }
+        for (int k = 0; k < 4; ++k) {
+          const float v = fabsf(y[k][a]);
+          if (!((used >> k) & 1u) && v > best) best = v, sv = y[k][a], bi = lane + 32 * k;
         }
 #pragma unroll
-        for (int o = 1; o < 16; o <<= 1) {
-          const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        for (int o = 1; o < 32; o <<= 1) {
+          const float ob = __shfl_xor_sync(0xffffffffu, best, o), os = __shfl_xor_sync(0xffffffffu, sv, o);
           const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) best = ob, bi = oi;
+          if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) best = ob, sv = os, bi = oi;
         }
-        const int p = __shfl_sync(0xffffffffu, bi, 16 * ha);
-        if (p < 0) {
+        const int p = bi;
+        if (p < 0 || sv == 0.0f || !isfinite(sv)) {
           bad = true;
           break;
         }
-        // pivot row p into the warp's shared row (both column halves)
-        if (tr == (p >> 3)) {
+        const float inv = __frcp_rn(sv);
+        const int owner = p & 31, slot = p >> 5;
+        float f[4];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (r0 + i == p) {
+        for (int k = 0; k < 4; ++k) f[k] = y[k][a];
+        // eight columns at a time: the pivot row's entries from its owner lane
+        // (slot p / 32 picked by selects), scaled (its column-a entry
+        // becomes 1 / pv), then every row updated
 #pragma unroll
-              for (int j = 0; j < 8; ++j) prs[8 * h + j] = x[i][j];
+        for (int hc = 0; hc < kGbP / 8; ++hc) {
+          float pr[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int cc = 8 * hc + q;
+            const float t01 = (slot & 1) ? y[1][cc] : y[0][cc], t23 = (slot & 1) ? y[3][cc] : y[2][cc];
+            const float v = __shfl_sync(0xffffffffu, (slot & 2) ? t23 : t01, owner);
+            pr[q] = (cc == a) ? inv : v * inv;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const bool piv = (lane + 32 * k == p);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int cc = 8 * hc + q;
+              y[k][cc] = piv ? pr[q] : fmaf(-f[k], pr[q], cc == a ? 0.0f : y[k][cc]);
             }
-        }
-        __syncwarp();
-        float pr[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) pr[j] = prs[8 * h + j];
-        const float pv = prs[a];
-        __syncwarp();
-        if (pv == 0.0f || !isfinite(pv)) {
-          bad = true;
-          break;
-        }
-        const float inv = __frcp_rn(pv);
-        // scaled pivot row; its column-k entry becomes 1 / pv
-#pragma unroll
-        for (int j = 0; j < 8; ++j) pr[j] = (h == ha && j == jj) ? inv : pr[j] * inv;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float f = __shfl_sync(0xffffffffu, x[i][jj], tr + 16 * ha);
-          if (r0 + i == p) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[i][j] = pr[j];
-            used |= 1u << i;
-          } else {
-            if (h == ha) x[i][jj] = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[i][j] = fmaf(-f, pr[j], x[i][j]);
           }
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (lane + 32 * k == p) used |= 1u << k;
         if (lane == 0) {
-          sh.prow[k] = p;
+          sh.prow[kcol] = p;
           sh.used[p] = 1;
           sh.pidx[b][p] = a;
         }
       }
       if (bad && lane == 0) sh.bad = 1;
       __syncwarp();
-      // (E - I)[:, p_a] = the panel columns minus 1 at the pivot rows
+      // (E - I)[:, p_a] = the panel columns minus 1 at the pivot rows; the
+      // panel back to the tile layout
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int r = r0 + i;
+      for (int k = 0; k < 4; ++k) {
+        const int r = lane + 32 * k;
+        const int pa = sh.pidx[b][r];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int a = 8 * h + j;
-          const bool pivot_entry = (sh.pidx[b][r] == a);
-          sh.WmT[b][a][r] = x[i][j] - (pivot_entry ? 1.0f : 0.0f);
+        for (int c = 0; c < kGbP; ++c) {
+          sh.WmT[b][c][r] = y[k][c] - (pa == c ? 1.0f : 0.0f);
+          sh.pan[r][c] = y[k][c];
         }
       }
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[i][j] = sh.pan[r0 + i][8 * h + j];
     }
     __syncthreads();
     if (sh.bad) break;

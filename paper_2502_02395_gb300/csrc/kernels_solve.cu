@@ -351,7 +351,8 @@ struct NoHook {
 // issued and before xs is read: it is where the caller fills xs (and
 // synchronizes), so that filling xs overlaps the first round trip to memory.
 // Rows of a misaligned M are read entry by entry.  y is written by one lane
-// per row, with no barrier afterwards.
+// per row, with no barrier afterwards.  base and y may be global or shared
+// (generic loads and stores).
 template <typename TS, typename T, int UNR, typename Hook = NoHook>
 __device__ __forceinline__ void cta_gemv(const TS* __restrict__ M, int64_t ld, int nr, int nc,
                                          const T* xs, T alpha, const T* base, T* y, Hook hook = Hook()) {
@@ -488,7 +489,7 @@ __device__ __forceinline__ void cta_gemv_cols(const TS* __restrict__ M, int64_t 
 // sum over the pairs q in [q0, q1) of part[q][r], in pair order; eight
 // independent loads are issued before they are added
 template <typename T>
-__device__ __forceinline__ T sum_pairs(const T* __restrict__ part, int nr, int64_t q0, int64_t q1, int r) {
+__device__ __forceinline__ T sum_pairs(const T* part, int nr, int64_t q0, int64_t q1, int r) {
   T s = T(0);
   int64_t q = q0;
   for (; q + 8 <= q1; q += 8) {
@@ -532,24 +533,34 @@ __device__ __forceinline__ void prefetch_l2(const void* p, int64_t bytes) {
 // pair's indices and x_j are read.
 enum { PH_RR = 0, PH_SR = 1, PH_RS = 2 };
 
+// One pair's product (entry t of list, or pair t); dep: launched as a
+// programmatic dependent (wait for the predecessor before reading x).
 template <typename T, typename TS, int PH>
-__global__ void __launch_bounds__(256, sizeof(TS) == 2 ? 3 : 2) pair_kernel(int D, int R, int K, const int32_t* __restrict__ list,
-                                                   const int32_t* __restrict__ nj, const TS* __restrict__ Ahat,
-                                                   const T* __restrict__ xv, T* __restrict__ part) {
+__device__ __forceinline__ void pair_body(int64_t t, int D, int R, int K, const int32_t* __restrict__ list,
+                                          const int32_t* __restrict__ nj, const TS* __restrict__ Ahat,
+                                          const T* xv, T* part, bool dep) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sx = reinterpret_cast<T*>(sm_raw);  // nc
-  const int64_t p = list ? list[blockIdx.x] : blockIdx.x;
+  const int64_t p = list ? list[t] : t;
   const int nr = (PH == PH_SR) ? K : R;
   const int nc = (PH == PH_RS) ? K : R;
   const TS* M = Ahat + p * D * D + (PH == PH_SR ? (int64_t)R * D : (PH == PH_RS ? R : 0));
   cta_gemv<TS, T, Unr<TS>::v>(M, D, nr, nc, sx, T(1), nullptr, part + p * nr, [&] {
     const int j = nj[p];
-    griddep_wait();
-    griddep_launch_next();
+    if (dep) {
+      griddep_wait();
+      griddep_launch_next();
+    }
     const T* x = (PH == PH_RS) ? xv + (int64_t)(j >> 1) * 2 * K + (j & 1) * K : xv + (int64_t)j * R;
     for (int e = threadIdx.x; e < nc; e += blockDim.x) sx[e] = x[e];
     __syncthreads();
   });
+}
+template <typename T, typename TS, int PH>
+__global__ void __launch_bounds__(256, sizeof(TS) == 2 ? 3 : 2) pair_kernel(int D, int R, int K, const int32_t* __restrict__ list,
+                                                   const int32_t* __restrict__ nj, const TS* __restrict__ Ahat,
+                                                   const T* __restrict__ xv, T* __restrict__ part) {
+  pair_body<T, TS, PH>(blockIdx.x, D, R, K, list, nj, Ahat, xv, part, true);
 }
 
 // Persistent form of the pair kernel for blocks that one pass of the CTA
@@ -804,8 +815,8 @@ __global__ void __launch_bounds__(256, 3)
 struct Slice {
   int i, r0, nr;
 };
-__device__ __forceinline__ Slice slice_of(int ns, int nrows) {
-  const int i = blockIdx.x / ns, s = blockIdx.x % ns;
+__device__ __forceinline__ Slice slice_of(int64_t b, int ns, int nrows) {
+  const int i = (int)(b / ns), s = (int)(b % ns);
   const int per = ((nrows + ns - 1) / ns + 7) & ~7;
   const int r0 = min(s * per, nrows);
   return {i, r0, min(per, nrows - r0)};
@@ -818,20 +829,25 @@ __device__ __forceinline__ Slice slice_of(int ns, int nrows) {
 // level the box input b_i is assembled first from its two children c:
 // b_i = [s_2i; s_2i+1], s_c = c_c^S - sum_{j near c} Ahat_cj^SR v_j (the
 // pair sums of the children's SR products).
+// Each step below is a body over one work item (box and row slice, or
+// pair) called by its kernel (dep: launched as a programmatic dependent, so
+// wait for the predecessor before reading its output).
 template <typename T>
-__global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, int ns, const T* __restrict__ M1,
-                                                   const T* __restrict__ U, const T* __restrict__ vin,
-                                                   ChildIn<T> ch, T* __restrict__ u, T* __restrict__ c) {
+__device__ __forceinline__ void fwd1_body(int64_t t, int D, int R, int ns, const T* __restrict__ M1,
+                                          const T* __restrict__ U, const T* vin, const ChildIn<T>& ch, T* u, T* c,
+                                          bool dep) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sv = reinterpret_cast<T*>(sm_raw);  // D
-  const Slice sl = slice_of(ns, D);
+  const Slice sl = slice_of(t, ns, D);
   const int i = sl.i;
   bool loaded = false;
   auto hook = [&] {
     if (loaded) return;
     loaded = true;
-    griddep_wait();
-    griddep_launch_next();
+    if (dep) {
+      griddep_wait();
+      griddep_launch_next();
+    }
     if (ch.c) {
       const T isc = ch.iscale ? T(ch.iscale[0]) : T(1);
       for (int e = threadIdx.x; e < D; e += blockDim.x) {
@@ -852,67 +868,98 @@ __global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, int ns, const T
     cta_gemv<T, T, Unr<T>::v>(U + ((int64_t)i * D + b0) * D, D, b1 - b0, D, sv, T(1), nullptr,
                               c + (int64_t)i * D + b0, hook);
 }
+template <typename T>
+__global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, int ns, const T* __restrict__ M1,
+                                                   const T* __restrict__ U, const T* __restrict__ vin,
+                                                   ChildIn<T> ch, T* __restrict__ u, T* __restrict__ c) {
+  fwd1_body<T>(blockIdx.x, D, R, ns, M1, U, vin, ch, u, c, true);
+}
 
 // ---------------------------------------------------------------- fwd2 ---
 // v_i = Ainv_i (c_i^R - sum_{j<i near} Ahat_ij^RR u_j)
 //     = u_i - Ainv_i sum_{j<i near} Ahat_ij^RR u_j
 template <typename T>
-__global__ void __launch_bounds__(256) fwd2_kernel(int R, int ns, const int64_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ lo_cnt, const float* __restrict__ iscale,
-                                                   const T* __restrict__ Ainv, const T* __restrict__ u,
-                                                   const T* __restrict__ part, T* __restrict__ v) {
+__device__ __forceinline__ void fwd2_body(int64_t t, int R, int ns, const int64_t* __restrict__ ptr,
+                                          const int32_t* __restrict__ lo_cnt, const float* __restrict__ iscale,
+                                          const T* __restrict__ Ainv, const T* u, const T* part, T* v,
+                                          bool dep) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* sb = reinterpret_cast<T*>(sm_raw);  // R
-  const Slice sl = slice_of(ns, R);
+  const Slice sl = slice_of(t, ns, R);
   const int i = sl.i;
   cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, sb, T(-1), u + (int64_t)i * R + sl.r0,
                             v + (int64_t)i * R + sl.r0, [&] {
                               const T isc = iscale ? T(iscale[0]) : T(1);
                               // the pairs j < i lead the box's sorted range
                               const int64_t q0 = ptr[i], q1 = q0 + lo_cnt[i];
-                              griddep_wait();
-                              griddep_launch_next();
+                              if (dep) {
+                                griddep_wait();
+                                griddep_launch_next();
+                              }
                               for (int r = threadIdx.x; r < R; r += blockDim.x)
                                 sb[r] = isc * sum_pairs(part, R, q0, q1, r);
                               __syncthreads();
                             });
 }
+template <typename T>
+__global__ void __launch_bounds__(256) fwd2_kernel(int R, int ns, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ lo_cnt, const float* __restrict__ iscale,
+                                                   const T* __restrict__ Ainv, const T* __restrict__ u,
+                                                   const T* __restrict__ part, T* __restrict__ v) {
+  fwd2_body<T>(blockIdx.x, R, ns, ptr, lo_cnt, iscale, Ainv, u, part, v, true);
+}
 
 // ---------------------------------------------------------------- fwd3 ---
 // s_i = c_i^S - sum_{j near} Ahat_ij^SR v_j  -> parent input slot
 template <typename T>
-__global__ void __launch_bounds__(128) fwd3_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
-                                                   const float* __restrict__ iscale, const T* __restrict__ c,
-                                                   const T* __restrict__ part, T* __restrict__ pvin) {
-  const int i = blockIdx.x;
+__device__ __forceinline__ void fwd3_body(int i, int D, int R, int K, const int64_t* __restrict__ ptr,
+                                          const float* __restrict__ iscale, const T* c, const T* part, T* pvin,
+                                          bool dep) {
   const T isc = iscale ? T(iscale[0]) : T(1);
   const int64_t q0 = ptr[i], q1 = ptr[i + 1];
   T* out = pvin + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
-  griddep_wait();
-  griddep_launch_next();
-  for (int r = threadIdx.x; r < K; r += blockDim.x) out[r] = c[(int64_t)i * D + R + r] - isc * sum_pairs(part, K, q0, q1, r);
+  if (dep) {
+    griddep_wait();
+    griddep_launch_next();
+  }
+  for (int r = threadIdx.x; r < K; r += blockDim.x)
+    out[r] = c[(int64_t)i * D + R + r] - isc * sum_pairs(part, K, q0, q1, r);
+}
+template <typename T>
+__global__ void __launch_bounds__(128) fwd3_kernel(int D, int R, int K, const int64_t* __restrict__ ptr,
+                                                   const float* __restrict__ iscale, const T* __restrict__ c,
+                                                   const T* __restrict__ part, T* __restrict__ pvin) {
+  fwd3_body<T>(blockIdx.x, D, R, K, ptr, iscale, c, part, pvin, true);
 }
 
 // ---------------------------------------------------------------- bwd1 ---
 // om_i = v_i - Ainv_i sum_{j near} Ahat_ij^RS x_j^S
 template <typename T>
-__global__ void __launch_bounds__(256) bwd1_kernel(int R, int ns, const int64_t* __restrict__ ptr,
-                                                   const float* __restrict__ iscale, const T* __restrict__ Ainv,
-                                                   const T* __restrict__ v, const T* __restrict__ part,
-                                                   T* __restrict__ om) {
+__device__ __forceinline__ void bwd1_body(int64_t t, int R, int ns, const int64_t* __restrict__ ptr,
+                                          const float* __restrict__ iscale, const T* __restrict__ Ainv,
+                                          const T* v, const T* part, T* om, bool dep) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* st = reinterpret_cast<T*>(sm_raw);  // R
-  const Slice sl = slice_of(ns, R);
+  const Slice sl = slice_of(t, ns, R);
   const int i = sl.i;
   cta_gemv<T, T, Unr<T>::v>(Ainv + ((int64_t)i * R + sl.r0) * R, R, sl.nr, R, st, T(-1), v + (int64_t)i * R + sl.r0,
                             om + (int64_t)i * R + sl.r0, [&] {
                               const T isc = iscale ? T(iscale[0]) : T(1);
                               const int64_t q0 = ptr[i], q1 = ptr[i + 1];
-                              griddep_wait();
-                              griddep_launch_next();
+                              if (dep) {
+                                griddep_wait();
+                                griddep_launch_next();
+                              }
                               for (int r = threadIdx.x; r < R; r += blockDim.x) st[r] = isc * sum_pairs(part, R, q0, q1, r);
                               __syncthreads();
                             });
+}
+template <typename T>
+__global__ void __launch_bounds__(256) bwd1_kernel(int R, int ns, const int64_t* __restrict__ ptr,
+                                                   const float* __restrict__ iscale, const T* __restrict__ Ainv,
+                                                   const T* __restrict__ v, const T* __restrict__ part,
+                                                   T* __restrict__ om) {
+  bwd1_body<T>(blockIdx.x, R, ns, ptr, iscale, Ainv, v, part, om, true);
 }
 
 // ---------------------------------------------------------------- bwd2 ---
@@ -922,23 +969,24 @@ __global__ void __launch_bounds__(256) bwd1_kernel(int R, int ns, const int64_t*
 // from memory and then from L2 when the rows are split), then its slice of
 // the rows of U_i z_i (Ur: U_i row-major).
 template <typename T>
-__global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, int ns, const int64_t* __restrict__ ptr,
-                                                   const int32_t* __restrict__ hi_cnt, const float* __restrict__ iscale,
-                                                   const T* __restrict__ Ainv, const T* __restrict__ om,
-                                                   const T* __restrict__ px, const T* __restrict__ part,
-                                                   const T* __restrict__ Ur, T* __restrict__ xs) {
+__device__ __forceinline__ void bwd2_body(int64_t t, int D, int R, int K, int ns, const int64_t* __restrict__ ptr,
+                                          const int32_t* __restrict__ hi_cnt, const float* __restrict__ iscale,
+                                          const T* __restrict__ Ainv, const T* om, const T* px, const T* part,
+                                          const T* __restrict__ Ur, T* xs, bool dep) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   T* zs = reinterpret_cast<T*>(sm_raw);  // D
   T* sq = zs + ((D + 3) & ~3);           // R
-  const Slice sl = slice_of(ns, D);
+  const Slice sl = slice_of(t, ns, D);
   const int i = sl.i;
   prefetch_l2(Ur + ((int64_t)i * D + sl.r0) * D, (int64_t)sl.nr * D * sizeof(T));
   cta_gemv<T, T, Unr<T>::v>(Ainv + (int64_t)i * R * R, R, R, R, sq, T(-1), om + (int64_t)i * R, zs, [&] {
     const T isc = iscale ? T(iscale[0]) : T(1);
     // the pairs j > i trail the box's sorted range
     const int64_t q1 = ptr[i + 1], q0 = q1 - hi_cnt[i];
-    griddep_wait();
-    griddep_launch_next();
+    if (dep) {
+      griddep_wait();
+      griddep_launch_next();
+    }
     const T* xi = px + (int64_t)(i >> 1) * 2 * K + (i & 1) * K;
     for (int e = threadIdx.x; e < K; e += blockDim.x) zs[R + e] = xi[e];
     for (int r = threadIdx.x; r < R; r += blockDim.x) sq[r] = isc * sum_pairs(part, R, q0, q1, r);
@@ -946,6 +994,14 @@ __global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, int ns, 
   });
   cta_gemv<T, T, Unr<T>::v>(Ur + ((int64_t)i * D + sl.r0) * D, D, sl.nr, D, zs, T(1), nullptr,
                             xs + (int64_t)i * D + sl.r0, [] { __syncthreads(); });
+}
+template <typename T>
+__global__ void __launch_bounds__(256) bwd2_kernel(int D, int R, int K, int ns, const int64_t* __restrict__ ptr,
+                                                   const int32_t* __restrict__ hi_cnt, const float* __restrict__ iscale,
+                                                   const T* __restrict__ Ainv, const T* __restrict__ om,
+                                                   const T* __restrict__ px, const T* __restrict__ part,
+                                                   const T* __restrict__ Ur, T* __restrict__ xs) {
+  bwd2_body<T>(blockIdx.x, D, R, K, ns, ptr, hi_cnt, iscale, Ainv, om, px, part, Ur, xs, true);
 }
 
 // out_b = (in_b)^T for nb square D x D blocks (32 x 32 tiles through shared memory)
