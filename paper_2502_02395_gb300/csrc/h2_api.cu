@@ -602,13 +602,16 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
                 false, f.Xo + (int64_t)Kc * K, DK, nullptr, K, T(1), T(0), nb, sb);
         Xin = f.Xo;
       }
-      launch_qr_panel<T>(nb, D, K, Xin, f.Vq, f.tau, f.Tm, f.Qs, sb);
+      // (the FP32 register form also forms the compact-WY factor Tw)
+      const bool tw_done = launch_qr_panel<T>(nb, D, K, Xin, f.Vq, f.tau, f.Tm, f.Qs, sb, f.Tw);
       T* Sb = F.Wq;
       T* W1 = F.Wq + (int64_t)nb * KK;
       if (K > 0) {
-        gemm<T>(prec, K, K, D, f.Vq, DK, nullptr, D, false, f.Vq, DK, nullptr, D, true, Sb, KK, nullptr, K, T(1), T(0),
-                nb, sb);
-        launch_wy_tfactor<T>(nb, K, Sb, f.tau, f.Tw, sb);
+        if (!tw_done) {
+          gemm<T>(prec, K, K, D, f.Vq, DK, nullptr, D, false, f.Vq, DK, nullptr, D, true, Sb, KK, nullptr, K, T(1),
+                  T(0), nb, sb);
+          launch_wy_tfactor<T>(nb, K, Sb, f.tau, f.Tw, sb);
+        }
         gemm<T>(prec, D, K, K, f.Vq, DK, nullptr, D, true, f.Tw, KK, nullptr, K, false, W1, DK, nullptr, K, T(1), T(0),
                 nb, sb);
       }
@@ -1204,7 +1207,8 @@ h2_status vec_out(h2_ctx* c, const double* tree, double* dst) {
 struct GmresWork {
   int m0 = 0;
   double *h1 = nullptr, *h2 = nullptr, *yv = nullptr, *part = nullptr, *nrm = nullptr;
-  std::vector<double> Hm, cs, sn, g, a1, a2, y;
+  double* host = nullptr;  // pinned: h1, h2, ||w||^2 as laid out on the device
+  std::vector<double> Hm, cs, sn, g, y;
 };
 
 template <typename T, class Prec, class Mv>
@@ -1229,14 +1233,15 @@ h2_status fgmres_cycle(h2_ctx* c, GmresWork& W, int m, double beta, const T* r, 
     launch_multi_dot<T>(V, n, j + 1, w, n, W.part, W.h2, false, st);
     launch_multi_axpy<T, T>(V, n, j + 1, W.h2, -1.0, w, n, st);
     launch_norm2<T>(w, n, W.nrm, st);
-    double nw2 = 0;
-    CKC(cudaMemcpyAsync(W.a1.data(), W.h1, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CKC(cudaMemcpyAsync(W.a2.data(), W.h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CKC(cudaMemcpyAsync(&nw2, W.nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // h1, h2 and ||w||^2 lie next to each other: one read
+    CKC(cudaMemcpyAsync(W.host, W.h1, (2 * (size_t)(m0 + 2) + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
     launch_scaled_copy<T, T>(w, W.nrm, true, w, n, st);
     CKC(cudaStreamSynchronize(st));
+    const double* a1 = W.host;
+    const double* a2 = W.host + (m0 + 2);
+    const double nw2 = W.host[2 * (m0 + 2)];
     double* col = &W.Hm[(size_t)j * (m0 + 1)];
-    for (int i = 0; i <= j; ++i) col[i] = W.a1[i] + W.a2[i];
+    for (int i = 0; i <= j; ++i) col[i] = a1[i] + a2[i];
     col[j + 1] = std::sqrt(nw2);
     for (int i = 0; i < j; ++i) {
       double t = W.cs[i] * col[i] + W.sn[i] * col[i + 1];
@@ -1273,22 +1278,23 @@ h2_status gmres_work(h2_ctx* c, GmresWork& W) {
     CKC(dalloc(c, &c->gm_V32, (size_t)(m0 + 1) * n));
     CKC(dalloc(c, &c->gm_Z32, (size_t)m0 * n));
     CKC(dalloc(c, &c->gm_r32, (size_t)n));
-    CKC(dalloc(c, &c->gm_h, 3 * (size_t)(m0 + 2)));
+    CKC(dalloc(c, &c->gm_h, 3 * (size_t)(m0 + 2) + 257));
+    if (c->gm_host) cudaFreeHost(c->gm_host);
+    CKC(cudaMallocHost(&c->gm_host, (2 * (size_t)(m0 + 2) + 1) * sizeof(double)));
     CKC(dalloc(c, &c->gm_part, (size_t)(m0 + 1) * 128));
     c->gm_cap = m0;
   }
   W.m0 = m0;
   W.h1 = c->gm_h;
   W.h2 = c->gm_h + (m0 + 2);
-  W.yv = c->gm_h + 2 * (m0 + 2);
+  W.nrm = c->gm_h + 2 * (m0 + 2);  // 257 doubles: the norm kernels' slot
+  W.yv = c->gm_h + 2 * (m0 + 2) + 257;
+  W.host = c->gm_host;
   W.part = c->gm_part;
-  W.nrm = c->red + 600;
   W.Hm.assign((size_t)(m0 + 1) * m0, 0.0);
   W.cs.assign(m0, 0.0);
   W.sn.assign(m0, 0.0);
   W.g.assign(m0 + 1, 0.0);
-  W.a1.assign(m0 + 2, 0.0);
-  W.a2.assign(m0 + 2, 0.0);
   W.y.assign(m0, 0.0);
   return H2_OK;
 }
@@ -1807,6 +1813,7 @@ void h2_destroy(h2_ctx* c) {
     cudaStreamDestroy(s);
   }
   for (void* p : c->allocs) cudaFree(p);
+  if (c->gm_host) cudaFreeHost(c->gm_host);
   delete c;
 }
 

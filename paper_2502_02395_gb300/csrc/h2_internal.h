@@ -289,7 +289,8 @@ struct h2_ctx {
   int restart = 30;              // FGMRES restart length
   double* gm_V = nullptr;        // (restart + 1) * nslot Krylov basis
   double* gm_Z = nullptr;        // restart * nslot preconditioned directions
-  double* gm_h = nullptr;        // 3 * (restart + 2) coefficients
+  double* gm_h = nullptr;        // h1, h2 (restart + 2 each), the norm slot (257), y (restart + 2)
+  double* gm_host = nullptr;     // pinned copy of h1, h2 and the norm (one read per FGMRES step)
   double* gm_part = nullptr;     // (restart + 1) * 128 dot-product partials
   float* gm_V32 = nullptr;       // FP32 Krylov basis / directions of the inner solver
   float* gm_Z32 = nullptr;

@@ -21,7 +21,9 @@ void gemm_simt(int M, int N, int K, const T* A, int64_t sA, const int32_t* ia, i
                int64_t sB, const int32_t* ib, int ldb, bool tB, T* C, int64_t sC, const int32_t* ic, int ldc,
                T alpha, T beta, int64_t batch, cudaStream_t st);
 template <typename T>
-void launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm, T* gscr, cudaStream_t st);
+// true when the compact-WY factor Tw was formed too (Tw non-NULL, FP32 register form)
+bool launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm, T* gscr, cudaStream_t st,
+                     T* Tw = nullptr);
 template <typename T>
 void launch_wy_tfactor(int nb, int K, const T* S, const T* tau, T* Tw, cudaStream_t st);
 template <typename T>

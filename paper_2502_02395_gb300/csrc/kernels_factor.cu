@@ -597,29 +597,12 @@ __device__ __forceinline__ void smem_mm4(const T* A, int lda, const T* B, int ld
 // b = 16 .. Kp every diagonal block [T11 T12; 0 T22] gets
 // T12 = -T11 (M12 T22) from its two already inverted halves (dense 4 x 4
 // register-tiled products; the zeros of the triangles are multiplied too).
+// In place: Ms (Kp x Kp upper triangular, leading dimension Kp + 1) becomes
+// its inverse; Xs is Kp * Kp / 4 scratch; every thread of the CTA calls it
+// (Kp a power of two, 8 <= Kp <= 128; at least Kp threads).
 template <typename T>
-__global__ void __launch_bounds__(256) wy_tinv_kernel(int K, int Kp, const T* __restrict__ S,
-                                                      const T* __restrict__ tau, T* __restrict__ Tw) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int ld = Kp + 1;
-  T* Ms = reinterpret_cast<T*>(smraw);  // Kp x ld
-  T* Xs = Ms + (size_t)Kp * ld;           // Kp * Kp / 4 scratch
-  const int box = blockIdx.x, tid = threadIdx.x;
-  const T* Sb = S + (size_t)box * K * K;
-  const T* tb = tau + (size_t)box * K;
-  for (int e = tid; e < Kp * Kp; e += blockDim.x) {
-    const int r = e / Kp, c = e - r * Kp;
-    T v = T(0);
-    if (r >= K || c >= K) {
-      v = (r == c) ? T(1) : T(0);
-    } else {
-      const bool zr = tb[r] == T(0), zc = tb[c] == T(0);
-      if (r == c) v = zr ? T(1) : T(1) / tb[r];
-      else if (c > r && !zr && !zc) v = Sb[r * K + c];
-    }
-    Ms[r * ld + c] = v;
-  }
-  __syncthreads();
+__device__ void tri_inverse_smem(int Kp, T* Ms, T* Xs) {
+  const int ld = Kp + 1, tid = threadIdx.x;
   // 8 x 8 diagonal blocks: thread (q, j) solves M_qq x = e_j
   {
     const int nq = Kp / 8;
@@ -661,6 +644,32 @@ __global__ void __launch_bounds__(256) wy_tinv_kernel(int K, int Kp, const T* __
     }
     __syncthreads();
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) wy_tinv_kernel(int K, int Kp, const T* __restrict__ S,
+                                                      const T* __restrict__ tau, T* __restrict__ Tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int ld = Kp + 1;
+  T* Ms = reinterpret_cast<T*>(smraw);  // Kp x ld
+  T* Xs = Ms + (size_t)Kp * ld;           // Kp * Kp / 4 scratch
+  const int box = blockIdx.x, tid = threadIdx.x;
+  const T* Sb = S + (size_t)box * K * K;
+  const T* tb = tau + (size_t)box * K;
+  for (int e = tid; e < Kp * Kp; e += blockDim.x) {
+    const int r = e / Kp, c = e - r * Kp;
+    T v = T(0);
+    if (r >= K || c >= K) {
+      v = (r == c) ? T(1) : T(0);
+    } else {
+      const bool zr = tb[r] == T(0), zc = tb[c] == T(0);
+      if (r == c) v = zr ? T(1) : T(1) / tb[r];
+      else if (c > r && !zr && !zc) v = Sb[r * K + c];
+    }
+    Ms[r * ld + c] = v;
+  }
+  __syncthreads();
+  tri_inverse_smem<T>(Kp, Ms, Xs);
   T* out = Tw + (size_t)box * K * K;
   for (int e = tid; e < K * K; e += blockDim.x) {
     const int r = e / K, c = e - r * K;
@@ -759,17 +768,26 @@ __device__ __forceinline__ void qr_reflector(float (&xc)[RPL], int k, int lane, 
 // reflector (warp reductions only) and publishes v and tau through a
 // double-buffered shared vector; after one barrier the warps that still
 // hold columns j > k update them: w = tau v^T x_j (lane-local products, one
-// warp reduction), x_j -= w v.  Warps whose columns are all finished skip
-// the step, so the issued work shrinks with k.  The rank-1 updates stay in
-// registers; shared memory carries only v.
+// warp reduction), x_j -= w v.  The warps whose columns are finished
+// reflectors (j < k) form the Gram entries v_j^T v_k instead, so that after
+// the last step the compact-WY factor Tw = (striu(V^T V) + diag(1 / tau))^-1
+// (zero-tau rows and columns masked, as in wy_tinv_kernel) is inverted in
+// shared memory by the same CTA (Tw NULL: no factor).  The rank-1 updates
+// stay in registers; shared memory carries v, the Gram matrix and Tw.
 template <int RPL>
-__global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* __restrict__ Xin,
+__global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, int Kp, const float* __restrict__ Xin,
                                                      float* __restrict__ Vout, float* __restrict__ tau_out,
-                                                     float* __restrict__ Tm) {
+                                                     float* __restrict__ Tm, float* __restrict__ Tw) {
   constexpr int NW = 16, CPW = 8;
-  __shared__ __align__(16) float vs[2][RPL * 32];
-  __shared__ float s_tau[2];
-  __shared__ float tile[32][NW * CPW + 1];
+  extern __shared__ __align__(16) unsigned char qsm[];
+  float* vsb = reinterpret_cast<float*>(qsm);          // 2 x RPL * 32
+  float* s_tau = vsb + 2 * RPL * 32;                    // 2 (+2 pad)
+  float* tau_s = s_tau + 4;                             // Kp
+  float* scr = tau_s + Kp;                              // max(32 x 129, Kp^2 / 4): load tile, then Xs
+  const int nscr = (32 * 129 > Kp * Kp / 4) ? 32 * 129 : Kp * Kp / 4;
+  float* Gm = scr + nscr;                               // Kp x (Kp + 1): Gram entries, then Tw
+  const int ldg = Kp + 1;
+  float(*tile)[NW * CPW + 1] = reinterpret_cast<float(*)[NW * CPW + 1]>(scr);
   const int box = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float* src = Xin + (size_t)box * D * K;  // row-major D x K
   float x[CPW][RPL];
@@ -788,8 +806,9 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
     }
     __syncthreads();
   }
-  // warp-uniform update of this warp's columns c >= c_lo with reflector (vb, tk)
-  auto update = [&](int c_lo, const float* vb, float tk) {
+  // columns c >= c_lo of this warp take the update with reflector (vb, tk);
+  // columns c < c_gram (finished reflectors j < k) give G[j][k] = v_j^T v_k
+  auto update = [&](int c_lo, int c_gram, const float* vb, float tk, int k) {
     float v[RPL];
 #pragma unroll
     for (int s = 0; s < RPL; ++s) v[s] = vb[lane + 32 * s];
@@ -797,7 +816,7 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
 #pragma unroll
     for (int c = 0; c < CPW; ++c) {
       d[c] = 0.0f;
-      if (c >= c_lo && CPW * warp + c < K) {
+      if ((c >= c_lo || c < c_gram) && CPW * warp + c < K) {
 #pragma unroll
         for (int s = 0; s < RPL; ++s) d[c] = fmaf(v[s], x[c][s], d[c]);
       }
@@ -811,22 +830,29 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
         for (int s = 0; s < RPL; ++s) x[c][s] = fmaf(-dj, v[s], x[c][s]);
       }
     }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < CPW; ++c)
+        if (c < c_gram && CPW * warp + c < K) Gm[(CPW * warp + c) * ldg + k] = d[c];
+    }
   };
+  const bool gram = Tw != nullptr;
   int buf = 0;
   for (int cw = 0; cw < NW; ++cw) {
 #pragma unroll
     for (int cc = 0; cc < CPW; ++cc) {
       const int k = CPW * cw + cc;
       if (k >= K) break;
-      float* vb = vs[buf];
+      float* vb = vsb + buf * RPL * 32;
       if (warp == cw) qr_reflector<RPL>(x[cc], k, lane, vb, &s_tau[buf]);
       __syncthreads();
       const float tk = s_tau[buf];
       if (tk != 0.0f) {
-        if (warp > cw) update(0, vb, tk);
-        else if (warp == cw) update(cc + 1, vb, tk);
+        if (warp > cw) update(0, 0, vb, tk, k);
+        else if (warp == cw) update(cc + 1, gram ? cc : 0, vb, tk, k);
+        else if (gram) update(CPW, CPW, vb, tk, k);
       }
-      if (threadIdx.x == 0) tau_out[(size_t)box * K + k] = tk;
+      if (threadIdx.x == 0) tau_out[(size_t)box * K + k] = tk, tau_s[k] = tk;
       buf ^= 1;
     }
   }
@@ -844,22 +870,51 @@ __global__ void __launch_bounds__(512) qr_reg_kernel(int D, int K, const float* 
       if (r < D) Vb[(size_t)j * D + r] = (r > j) ? x[c][s] : (r == j ? 1.0f : 0.0f);
     }
   }
+  if (!gram) return;
+  // M = striu(G) + diag(1 / tau), padded to Kp with the identity, in place
+  __syncthreads();
+  for (int e = threadIdx.x; e < Kp * Kp; e += blockDim.x) {
+    const int r = e / Kp, c = e - r * Kp;
+    float v = 0.0f;
+    if (r >= K || c >= K) {
+      v = (r == c) ? 1.0f : 0.0f;
+    } else {
+      const bool zr = tau_s[r] == 0.0f, zc = tau_s[c] == 0.0f;
+      if (r == c) v = zr ? 1.0f : 1.0f / tau_s[r];
+      else if (c > r && !zr && !zc) v = Gm[r * ldg + c];
+    }
+    Gm[r * ldg + c] = v;
+  }
+  __syncthreads();
+  tri_inverse_smem<float>(Kp, Gm, scr);
+  float* out = Tw + (size_t)box * K * K;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int r = e / K, c = e - r * K;
+    out[e] = (r == c && tau_s[r] == 0.0f) ? 0.0f : Gm[r * ldg + c];
+  }
 }
 
 template <typename T>
-void launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm, T* gscr, cudaStream_t st) {
-  if (nb == 0 || K == 0) return;
+bool launch_qr_panel(int nb, int D, int K, const T* Xin, T* Vout, T* tau, T* Tm, T* gscr, cudaStream_t st, T* Tw) {
+  if (nb == 0 || K == 0) return false;
   if (std::is_same<T, float>::value && D <= 256 && K <= 128) {
+    int Kp = 8;
+    while (Kp < K) Kp *= 2;
+    const size_t nscr = std::max<size_t>(32 * 129, (size_t)Kp * Kp / 4);
+    const size_t sm = sizeof(float) * (2 * 256 + 4 + Kp + nscr + (Tw ? (size_t)Kp * (Kp + 1) : 0));
+    if (sm > 48 * 1024) cudaFuncSetAttribute(qr_reg_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     ++g_launches;
-    qr_reg_kernel<8><<<nb, 512, 0, st>>>(D, K, reinterpret_cast<const float*>(Xin), reinterpret_cast<float*>(Vout),
-                                            reinterpret_cast<float*>(tau), reinterpret_cast<float*>(Tm));
-    return;
+    qr_reg_kernel<8><<<nb, 512, sm, st>>>(D, K, Kp, reinterpret_cast<const float*>(Xin),
+                                          reinterpret_cast<float*>(Vout), reinterpret_cast<float*>(tau),
+                                          reinterpret_cast<float*>(Tm), reinterpret_cast<float*>(Tw));
+    return Tw != nullptr;
   }
   const size_t sm = sizeof(T) * (size_t)D * K;
   const int use = sm <= 200 * 1024;
   if (use) cudaFuncSetAttribute(qr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ++g_launches;
   qr_panel_kernel<T><<<nb, 512, use ? sm : 0, st>>>(D, K, Xin, Vout, tau, Tm, gscr, use);
+  return false;
 }
 template <typename T>
 void launch_wy_tfactor(int nb, int K, const T* S, const T* tau, T* Tw, cudaStream_t st) {
@@ -886,7 +941,7 @@ void launch_perm_identity(int nb, int D, int K, T* U, cudaStream_t st) {
   perm_identity_kernel<T><<<(int)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(nb, D, K, U);
 }
 #define H2_INST_QR(T)                                                                                         \
-  template void launch_qr_panel<T>(int, int, int, const T*, T*, T*, T*, T*, cudaStream_t);                     \
+  template bool launch_qr_panel<T>(int, int, int, const T*, T*, T*, T*, T*, cudaStream_t, T*);                \
   template void launch_wy_tfactor<T>(int, int, const T*, const T*, T*, cudaStream_t);                          \
   template void launch_perm_identity<T>(int, int, int, T*, cudaStream_t);
 H2_INST_QR(double)
