@@ -1679,7 +1679,8 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     // Ahat read in 16 bits where the factorization kept a 16-bit copy
     const bool a16 = c->prec != H2_PREC_FP64 && (int)c->f32.lv.size() > l && c->f32.lv[l].ahat_isc;
     const double wa = a16 ? 2.0 : w;
-    by_sub += wa * ((double)(d.NP - d.nb) * R * R + (double)d.NP * 2.0 * R * K) + w * d.nb * (2.0 * D * D + 4.0 * R * R);
+    // per box: M1 and U^S (fwd1), U (bwd2) and three reads of the inverse
+    by_sub += wa * ((double)(d.NP - d.nb) * R * R + (double)d.NP * 2.0 * R * K) + w * d.nb * (2.0 * D * D + 3.0 * R * R);
     by_mv += 8.0 * (2.0 * d.nb * D * K + (double)d.FP * K * K);
     fl_mv += 2.0 * (2.0 * d.nb * D * K + (double)d.FP * K * K);
   }
