@@ -101,6 +101,45 @@ def test_lists_partition_every_entry_once(eta):
             assert near[l] == [(i, i) for i in range(1 << l)]
 
 
+@pytest.mark.parametrize("eta", [0.0, 1.0, 2.0])
+def test_lists_closed_under_transposition(eta):
+    """Admissibility is symmetric in the two boxes, so every level's near and
+    far lists hold (j, i) with (i, j): the library's symmetric storage and
+    upper-pair projection pair each block with its mirror."""
+    n, leaf = 600, 40
+    P = W.cube_points(n, 11)
+    perm, ranges = build_tree(P, leaf)
+    near, far = interaction_lists(P, perm, ranges, eta)
+    for l in range(1, len(ranges)):
+        assert set(near[l]) == {(j, i) for (i, j) in near[l]}
+        assert set(far[l]) == {(j, i) for (i, j) in far[l]}
+
+
+def test_projected_blocks_of_symmetric_kernel_are_mirrors():
+    """For a symmetric kernel every projected block is its mirror's
+    transpose, Ahat_ji = Ahat_ij^T and Shat_ji = Shat_ij^T, on every level
+    (the identity behind projecting the pairs i <= j only), while a
+    non-symmetric change of one block breaks it."""
+    P = W.cube_points(800, 4)
+    H = construct(P, Kernel("yukawa_eps", diag_shift=1.0), 50, 1.0, 1e-8, 0, 256, 32)
+    F = ulv.factor(H)
+    for l in range(1, H["L"] + 1):
+        A = F["Ahat"][l]
+        for (i, j) in H["near"][l]:
+            if i < j:
+                scale = max(np.abs(A[(i, j)]).max(), 1e-300)
+                assert np.abs(A[(j, i)] - A[(i, j)].T).max() <= 1e-12 * scale, (l, i, j)
+        S = F["Shat"][l]
+        for (i, j) in H["far"][l]:
+            if i < j:
+                scale = max(np.abs(S[(i, j)]).max(), 1e-300)
+                assert np.abs(S[(j, i)] - S[(i, j)].T).max() <= 1e-12 * scale, (l, i, j)
+    # the check is not vacuous: an off-diagonal block is not symmetric itself
+    L = H["L"]
+    (i, j) = next(p for p in H["near"][L] if p[0] < p[1])
+    assert np.abs(F["Ahat"][L][(i, j)] - F["Ahat"][L][(i, j)].T).max() > 1e-6
+
+
 # ------------------------------------------------------------ dense / LU ---
 def test_dense_lu_matches_numpy():
     rng = np.random.default_rng(0)
