@@ -191,6 +191,16 @@ h2_status h2_factor(h2_ctx* c, int32_t prec);
 h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target,
                    int32_t max_iters, double* relres_out, int32_t* iters_out);
 
+/* Several right-hand sides (the paper's solve is per vector; the columns
+ * are independent): B and X hold nrhs vectors of N doubles each, one after
+ * another (column-major N x nrhs), host or device.  Each column is solved
+ * as h2_solve solves one vector, with the same target and max_iters;
+ * relres_out and iters_out (host, may be NULL) receive nrhs values.
+ * Errors: H2_ERR_INVALID_ARG (nrhs < 0), else as h2_solve; the first
+ * failing column ends the call (its index is in h2_last_error). */
+h2_status h2_solve_many(h2_ctx* c, const double* B, double* X, int32_t nrhs, double target,
+                        int32_t max_iters, double* relres_out, int32_t* iters_out);
+
 /* One application of the factorization, x = ULV^-1 b, without refinement
  * (the parallel substitution of Eq. 24-31 and its mirror).  N doubles each,
  * host or device.  Errors: H2_ERR_STATE, H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
@@ -200,6 +210,10 @@ h2_status h2_ulv_apply(h2_ctx* c, const double* b, double* x);
  * every level, downward pass and the dense near blocks of the leaves.
  * N doubles each, host or device.  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
 h2_status h2_matvec(h2_ctx* c, const double* x, double* y);
+
+/* Y = A_H2 X for nrhs vectors laid out as in h2_solve_many (host or
+ * device).  Errors: H2_ERR_INVALID_ARG (nrhs < 0), else as h2_matvec. */
+h2_status h2_matvec_many(h2_ctx* c, const double* X, double* Y, int32_t nrhs);
 
 /* Choose the refinement scheme of h2_solve (0..3, see h2_solve; default 3)
  * and the FGMRES restart length (1..1000, default 30).

@@ -1,7 +1,7 @@
 """ctypes binding of the C ABI declared in include/h2ulv.h.
 
 The module-level functions carry the C names (h2_build, h2_import,
-h2_factor, h2_solve, h2_ulv_apply, h2_matvec, h2_set_stream, h2_stats,
+h2_factor, h2_solve, h2_solve_many, h2_ulv_apply, h2_matvec, h2_matvec_many, h2_set_stream, h2_stats,
 h2_export, h2_last_error, h2_destroy) and only marshal arguments: every step
 of the computation runs in the library.  ``H2Solver`` wraps a context.
 
@@ -27,8 +27,8 @@ STATUS = {0: "H2_OK", -1: "H2_ERR_INVALID_ARG", -2: "H2_ERR_OOM", -3: "H2_ERR_SI
           -4: "H2_ERR_NOT_CONVERGED", -5: "H2_ERR_CUDA", -6: "H2_ERR_TIMEOUT", -7: "H2_ERR_STATE"}
 
 # every symbol include/h2ulv.h declares
-EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_ulv_apply", "h2_matvec",
-            "h2_matvec_noalloc",
+EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_solve_many", "h2_ulv_apply",
+            "h2_matvec", "h2_matvec_many", "h2_matvec_noalloc",
             "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
 
 
@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
             "h2_import": (i32, [pp, vp, vp]),
             "h2_factor": (i32, [vp, i32]),
             "h2_solve": (i32, [vp, vp, vp, dbl, i32, vp, vp]),
+            "h2_solve_many": (i32, [vp, vp, vp, i32, dbl, i32, vp, vp]),
+            "h2_matvec_many": (i32, [vp, vp, vp, i32]),
             "h2_ulv_apply": (i32, [vp, vp, vp]),
             "h2_matvec": (i32, [vp, vp, vp]),
             "h2_matvec_noalloc": (i32, [vp, vp, vp]),
@@ -178,6 +180,22 @@ def h2_solve(ctx, b, x, target=1e-10, max_iters=50, check=True):
     return st, rel.value, its.value
 
 
+def h2_solve_many(ctx, B, X, target=1e-10, max_iters=50, check=True):
+    """B, X: nrhs x N (one right-hand side per row, contiguous)."""
+    nrhs = int(B.shape[0])
+    rel = (ctypes.c_double * max(nrhs, 1))()
+    its = (ctypes.c_int32 * max(nrhs, 1))()
+    st = lib().h2_solve_many(ctx, _ptr(B), _ptr(X), nrhs, target, max_iters, ctypes.cast(rel, ctypes.c_void_p),
+                             ctypes.cast(its, ctypes.c_void_p))
+    if check:
+        _check(st, ctx)
+    return st, list(rel)[:nrhs], list(its)[:nrhs]
+
+
+def h2_matvec_many(ctx, X, Y):
+    _check(lib().h2_matvec_many(ctx, _ptr(X), _ptr(Y), int(X.shape[0])), ctx)
+
+
 def h2_ulv_apply(ctx, b, x):
     _check(lib().h2_ulv_apply(ctx, _ptr(b), _ptr(x)), ctx)
 
@@ -255,6 +273,22 @@ class H2Solver:
             x = np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)
         st, rel, its = h2_solve(self.ctx, b, x, target, max_iters)
         return x, rel, its
+
+    def solve_many(self, B, target=1e-10, max_iters=50):
+        """One row of B per right-hand side; returns (X, relres list, iteration list)."""
+        if isinstance(B, np.ndarray):
+            B = np.ascontiguousarray(B, dtype=np.float64)
+        else:
+            B = B.contiguous()
+        X = np.zeros_like(B) if isinstance(B, np.ndarray) else B.new_zeros(B.shape)
+        st, rel, its = h2_solve_many(self.ctx, B, X, target, max_iters)
+        return X, rel, its
+
+    def matvec_many(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64) if isinstance(X, np.ndarray) else X.contiguous()
+        Y = np.zeros_like(X) if isinstance(X, np.ndarray) else X.new_zeros(X.shape)
+        h2_matvec_many(self.ctx, X, Y)
+        return Y
 
     def ulv_apply(self, b):
         x = np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape)

@@ -1550,6 +1550,29 @@ h2_status h2_matvec(h2_ctx* c, const double* x, double* y) {
   return H2_OK;
 }
 
+h2_status h2_solve_many(h2_ctx* c, const double* B, double* X, int32_t nrhs, double target, int32_t max_iters,
+                        double* relres_out, int32_t* iters_out) {
+  if (!c || !B || !X || nrhs < 0) return H2_ERR_INVALID_ARG;
+  for (int32_t k = 0; k < nrhs; ++k) {
+    double rel = 0;
+    int32_t its = 0;
+    const h2_status s = h2_solve(c, B + (int64_t)k * c->N, X + (int64_t)k * c->N, target, max_iters, &rel, &its);
+    if (relres_out) relres_out[k] = rel;
+    if (iters_out) iters_out[k] = its;
+    if (s != H2_OK) {
+      c->err = "right-hand side " + std::to_string(k) + ": " + c->err;
+      return s;
+    }
+  }
+  return H2_OK;
+}
+
+h2_status h2_matvec_many(h2_ctx* c, const double* X, double* Y, int32_t nrhs) {
+  if (!c || !X || !Y || nrhs < 0) return H2_ERR_INVALID_ARG;
+  for (int32_t k = 0; k < nrhs; ++k) CKS(h2_matvec(c, X + (int64_t)k * c->N, Y + (int64_t)k * c->N));
+  return H2_OK;
+}
+
 h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t max_iters, double* relres_out,
                    int32_t* iters_out) {
   if (!c || !b || !x || max_iters < 0) return H2_ERR_INVALID_ARG;

@@ -154,6 +154,30 @@ def test_poly2_equals_dense_solve(B):
     S.close()
 
 
+def test_many_right_hand_sides(B):
+    """h2_solve_many / h2_matvec_many: each column equals the single-vector
+    call on it (the refinement is per vector), host and device buffers."""
+    import torch
+    H, F, flat, b = oracle_case("cube2048_laplace")
+    S = lib_case(B, "cube2048_laplace")
+    S.factor("fp16")
+    n = b.shape[0]
+    Bm = np.stack([b, W.uniform_rhs(n, 77), np.zeros(n)])
+    X, rels, its = S.solve_many(Bm, target=1e-12, max_iters=80)
+    assert len(rels) == 3 and len(its) == 3
+    for k in range(2):
+        x1, r1, i1 = S.solve(Bm[k], target=1e-12, max_iters=80)
+        assert rel(X[k], x1) <= 1e-14 and i1 == its[k], k
+        assert rels[k] <= 1e-12
+    assert np.abs(X[2]).max() == 0.0 and rels[2] == 0.0  # a zero right-hand side
+    Y = S.matvec_many(Bm)
+    for k in range(3):
+        assert rel(Y[k], S.matvec(Bm[k])) <= 1e-15
+    Yd = S.matvec_many(torch.from_numpy(Bm).cuda()).cpu().numpy()
+    assert rel(Yd, Y) <= 1e-15
+    S.close()
+
+
 @pytest.mark.parametrize("method", ["auto", "gmres"])
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("name", ["cube2048_laplace", "sphere1000_ragged", "cube8192_yukawa"])
