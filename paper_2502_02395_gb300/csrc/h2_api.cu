@@ -383,7 +383,7 @@ h2_status setup_device(h2_ctx* c) {
   if (c->cb_ok) {
     CKS(upload(c, &c->cb_i, cbi));
     CKS(upload(c, &c->cb_j, cbj));
-    npart = std::max(npart, (size_t)c->cb_n * 2 * c->cb_K);
+    CKC(dalloc(c, &c->part32c, (size_t)c->cb_n * 2 * c->cb_K));
   }
   if (npart) {
     CKC(dalloc(c, &c->part32, npart));
@@ -1001,29 +1001,48 @@ void matvec_t(h2_ctx* c, const T* A, T* const* X, T* const* S, T* xh, T* yh, con
     return;
   }
   const std::vector<int64_t>& off = c->hat_off;
-  launch_matvec_up<T>(c->lv[L], X[L], x, xh + off[L], st);
-  for (int l = L - 1; l >= 1; --l) launch_matvec_up<T>(c->lv[l], X[l], xh + off[l + 1], xh + off[l], st);
   if constexpr (std::is_same<T, float>::value) {
-    if (c->cb_ok) {
-      // every level's coupling products in one launch, then the downward
-      // pass adds each level's sums as it goes
-      launch_matvec_sym_pairs(c->cb_K, c->cb_n, c->cb_i, c->cb_j, c->S32u_all, xh, c->part32, true, st);
+    if (c->cb_ok && c->sym) {
+      // the leaf near-field products need only x: they run on the leaf
+      // stream beside the upward pass, the couplings (every level in one
+      // launch) and the downward pass, which adds each level's coupling
+      // sums as it goes; the per-box leaf sums follow the join
+      if (!c->leaf_stream) {
+        cudaStreamCreateWithFlags(&c->leaf_stream, cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&c->mv_fork, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->mv_join, cudaEventDisableTiming);
+      }
+      cudaStream_t sl = c->leaf_stream;
+      const DevLevel& lf = c->lv[L];
+      cudaEventRecord(c->mv_fork, st);
+      cudaStreamWaitEvent(sl, c->mv_fork, 0);
+      if (leaf_ev) cudaEventRecord(e0, sl);
+      launch_matvec_sym_pairs(lf.D, c->npu, c->sym_i, c->sym_j, A, x, c->part32, false, sl);
+      if (leaf_ev) cudaEventRecord(e1, sl), leaf_ev->push_back({e0, e1});
+      cudaEventRecord(c->mv_join, sl);
+      launch_matvec_up<T>(c->lv[L], X[L], x, xh + off[L], st);
+      for (int l = L - 1; l >= 1; --l) launch_matvec_up<T>(c->lv[l], X[l], xh + off[l + 1], xh + off[l], st);
+      launch_matvec_sym_pairs(c->cb_K, c->cb_n, c->cb_i, c->cb_j, c->S32u_all, xh, c->part32c, true, st);
       const DevLevel& d1 = c->lv[1];
       if (d1.FP > 0 && d1.K > 0)
         launch_matvec_sym_sum<float>(d1.nb, d1.K, 0, d1.fs_ptr, d1.fs_ent, nullptr, nullptr,
-                                     c->part32 + d1.fs_goff * 2 * d1.K, yh + off[1], st);
+                                     c->part32c + d1.fs_goff * 2 * d1.K, yh + off[1], st);
       else
         cudaMemsetAsync(yh + off[1], 0, sizeof(T) * (size_t)d1.nb * d1.K, st);
       for (int l = 1; l < L; ++l) {
         const DevLevel& dc = c->lv[l + 1];
         const bool has = dc.FP > 0 && dc.K > 0;
         launch_matvec_down_far<float>(c->lv[l], X[l], yh + off[l], yh + off[l + 1], has ? dc.fs_ptr : nullptr,
-                                      has ? dc.fs_ent : nullptr, c->part32 + dc.fs_goff * 2 * dc.K, st);
+                                      has ? dc.fs_ent : nullptr, c->part32c + dc.fs_goff * 2 * dc.K, st);
       }
-      leaf(X[L], yh + off[L]);
+      cudaStreamWaitEvent(st, c->mv_join, 0);
+      launch_matvec_sym_sum<float>(lf.nb, lf.D, lf.K, c->sym_ptr, c->sym_ent, X[L], yh + off[L], c->part32, y, st,
+                                   false);
       return;
     }
   }
+  launch_matvec_up<T>(c->lv[L], X[L], x, xh + off[L], st);
+  for (int l = L - 1; l >= 1; --l) launch_matvec_up<T>(c->lv[l], X[l], xh + off[l + 1], xh + off[l], st);
   for (int l = 1; l <= L; ++l) {
     const DevLevel& d = c->lv[l];
     if constexpr (std::is_same<T, float>::value) {
@@ -1831,7 +1850,9 @@ const char* h2_last_error(const h2_ctx* c) { return c ? c->err.c_str() : g_last_
 
 void h2_destroy(h2_ctx* c) {
   if (!c) return;
-  for (cudaStream_t s : {c->basis_stream, c->coupling_stream, c->product_stream}) {
+  if (c->mv_fork) cudaEventDestroy(c->mv_fork);
+  if (c->mv_join) cudaEventDestroy(c->mv_join);
+  for (cudaStream_t s : {c->basis_stream, c->coupling_stream, c->product_stream, c->leaf_stream}) {
     if (!s) continue;
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);

@@ -266,6 +266,11 @@ struct h2_ctx {
   int32_t *sym_q = nullptr, *sym_i = nullptr, *sym_j = nullptr, *sym_ent = nullptr;
   int64_t* sym_ptr = nullptr;
   float* part32 = nullptr;   // npu * 2 D partial products (FP32 matvec)
+  float* part32c = nullptr;  // cb_n * 2 cb_K coupling partial products (beside the leaf's)
+  // the FP32 matvec's leaf near field runs on leaf_stream beside the passes
+  // through the bases (created on first use), forked and joined by events
+  cudaStream_t leaf_stream = nullptr;
+  cudaEvent_t mv_fork = nullptr, mv_join = nullptr;
   double* part64 = nullptr;  // the same for the FP32-pair matvec
   float *xhat32 = nullptr, *yhat32 = nullptr;
   // the stored coupling pairs of every level as one batch (levels with the

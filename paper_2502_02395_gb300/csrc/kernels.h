@@ -139,7 +139,7 @@ void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int
                                 const float* Al, const double* x, double* part, cudaStream_t st);
 template <typename T>
 void launch_matvec_sym_sum(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const T* X, const T* yh,
-                           const T* part, T* y, cudaStream_t st);
+                           const T* part, T* y, cudaStream_t st, bool pdl = true);
 // out[k] = fl32(in[idx[k]]), lo[k] = fl32(in[idx[k]] - hi[k]) for blocks of n entries
 void launch_gather_blocks(const double* in, const int32_t* idx, int64_t n, int64_t nblk, float* out, cudaStream_t st);
 void launch_gather_split_lo(const double* in, const int32_t* idx, int64_t n, int64_t nblk, const float* hi, float* lo,

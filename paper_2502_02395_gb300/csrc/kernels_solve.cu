@@ -1815,14 +1815,19 @@ void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int
 }
 template <typename T>
 void launch_matvec_sym_sum(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const T* X, const T* yh,
-                           const T* part, T* y, cudaStream_t st) {
+                           const T* part, T* y, cudaStream_t st, bool pdl) {
   const size_t sm = sizeof(T) * ((size_t)((K + 3) & ~3) + D);
-  launch_pdl(mv_sym_sum_kernel<T>, nb, 256, sm, st, D, K, ptr, ent, X, yh, part, y);
+  if (pdl) {
+    launch_pdl(mv_sym_sum_kernel<T>, nb, 256, sm, st, D, K, ptr, ent, X, yh, part, y);
+  } else {
+    ++g_launches;
+    mv_sym_sum_kernel<T><<<nb, 256, sm, st>>>(D, K, ptr, ent, X, yh, part, y);
+  }
 }
 template void launch_matvec_sym_sum<float>(int, int, int, const int64_t*, const int32_t*, const float*, const float*,
-                                           const float*, float*, cudaStream_t);
+                                           const float*, float*, cudaStream_t, bool);
 template void launch_matvec_sym_sum<double>(int, int, int, const int64_t*, const int32_t*, const double*,
-                                            const double*, const double*, double*, cudaStream_t);
+                                            const double*, const double*, double*, cudaStream_t, bool);
 
 // out[k] = (To) in[idx[k]] for blocks of n entries
 template <typename Ti, typename To>
