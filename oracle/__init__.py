@@ -36,6 +36,8 @@ PARITY = {
     "kernels": "pinned: closed forms at fixed points (tests/test_oracle_pins.py)",
     "tree": "pinned: partition invariants and brute-force admissibility",
     "construct.sampling_rule": "parity unpinned (the paper does not fix it)",
+    "construct.prefactor": "pinned: dropped Eq. 21 fill-ins fall with tol only with the close-field term; "
+                           "that term scales with the inverse diagonal (tests/test_oracle_pins.py)",
     "construct.id": "pinned: exact-rank kernel gives an exact ID; interpolation rows",
     "ulv.complement_basis": "pinned: orthogonality <= 1e-13, span of X",
     "ulv.factor": "pinned: exact-rank kernel equals dense LU to ~1e-12; brute force on tiny trees",

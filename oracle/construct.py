@@ -83,7 +83,10 @@ def id_basis(piv: np.ndarray, R: np.ndarray, k: int) -> np.ndarray:
 
 
 def construct(points: np.ndarray, kernel: Kernel, leaf: int, eta: float, tol: float,
-              max_rank: int = 0, far_samples: int = 1024, near_samples: int = 64):
+              max_rank: int = 0, far_samples: int = 1024, near_samples: int = 64, prefactor: bool = True):
+    """Algorithm 1.  prefactor=False leaves the close-field part out of M_i
+    (the plain H^2 basis of Fig. 7, without the fill-in content of Eq. 22-23);
+    the tests use it to show what the pre-factorization term contributes."""
     points = np.ascontiguousarray(points, dtype=np.float64)
     N = len(points)
     perm, ranges = build_tree(points, leaf)
@@ -116,7 +119,7 @@ def construct(points: np.ndarray, kernel: Kernel, leaf: int, eta: float, tol: fl
             SF = stride_sample(perm[mask], far_samples)
             parts = [kernel.matrix(points, Pi, SF)]
             for j in nbrs[i]:
-                if j == i:
+                if j == i or not prefactor:
                     continue
                 SC = stride_sample(box_pts[l][j], near_samples)
                 Acc = kernel.matrix(points, SC, SC)

@@ -363,3 +363,58 @@ def test_hss_needs_higher_rank_than_h2():
     hss = construct(P, kern, 128, 0.0, 1e-6, 128, 0, 0)
     L = h2["L"]
     assert max(hss["ranks"][L]) > max(h2["ranks"][L]) or np.mean(hss["ranks"][L]) > np.mean(h2["ranks"][L])
+
+
+def test_prefactor_basis_bounds_dropped_fill():
+    """Section 3.4, Eq. 21-23: with the close-field term G(B_i, S_C)
+    G(S_C, S_C)^-1 in the composite matrix, the Schur fill-ins the
+    factorization drops (Eq. 10-12, the terms Eq. 21 sets to zero) fall with
+    the truncation tolerance, and one ULV application (no refinement) is the
+    dense solve to within the tolerance.  With the term left out (the plain
+    H^2 basis of Fig. 7) the dropped fill-ins stay at the 1e-2 level whatever
+    the tolerance.  Real kernel (1/(r+1e-3) on a sphere), no rank cap, no
+    sampling."""
+    n = 1024
+    P = W.sphere_points(n, 8)
+    kern = Kernel("laplace_eps")
+    A = dense.dense_matrix(P, kern)
+    b = W.uniform_rhs(n, 9)
+    xd = np.linalg.solve(A, b)
+
+    def run(tol, prefactor):
+        H = construct(P, kern, 64, 1.0, tol, 10 ** 6, 0, 0, prefactor=prefactor)
+        F = ulv.factor(H)
+        drop = max(v[0] for v in ulv.dropped_fill_norms(F).values())
+        x = ulv.solve_parallel(F, H, b)
+        return drop, np.linalg.norm(x - xd) / np.linalg.norm(xd)
+
+    tols = (1e-3, 1e-5, 1e-7)
+    got = [run(t, True) for t in tols]
+    for (drop, err), tol in zip(got, tols):
+        assert drop <= 0.5 * tol, (tol, drop)
+        assert err <= tol, (tol, err)
+    assert got[0][0] > got[1][0] > got[2][0]
+    drop_far, err_far = run(1e-7, False)
+    assert drop_far >= 1e4 * got[2][0] and drop_far >= 1e-3
+    assert err_far >= 1e3 * got[2][1]
+
+
+def test_prefactor_term_scales_with_inverse_diagonal():
+    """The close-field content of Eq. 22-23 is A_ji A_ii^-1.  With a diagonal
+    shift of 1e6 (A_ii^-1 ~ 1e-6 I) that content lies far below the far
+    field's at tol 1e-3 and 1e-5, so the leaf ranks equal those of the
+    far-field-only basis exactly; with the plain diagonal (1e3) the
+    pre-factorization basis needs strictly more rank.  (A close-field term
+    without the inverse would keep the block at full weight and raise the
+    ranks in the shifted case too.)"""
+    P = W.sphere_points(1024, 8)
+    for tol in (1e-3, 1e-5):
+        for shift, same in ((1e6, True), (0.0, False)):
+            kern = Kernel("laplace_eps", diag_shift=shift)
+            Hp = construct(P, kern, 64, 1.0, tol, 10 ** 6, 0, 0, prefactor=True)
+            Hf = construct(P, kern, 64, 1.0, tol, 10 ** 6, 0, 0, prefactor=False)
+            L = Hp["L"]
+            if same:
+                assert list(Hp["ranks"][L]) == list(Hf["ranks"][L]), (tol, shift)
+            else:
+                assert max(Hp["ranks"][L]) > max(Hf["ranks"][L]), (tol, shift)
