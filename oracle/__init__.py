@@ -20,6 +20,9 @@ on GPUs" (arXiv 2502.02395):
                 (Algorithm 3) and the parallel substitution (Eq. 24-31), the
                 H^2 matrix-vector product and iterative refinement
   dense.py      dense assembly and a textbook partial-pivot LU solve
+  mlp.py        the rank predictor's 16-64-64-1 network (forward, loss and
+                chain-rule gradient), the spec extension that learns
+                the ranks Algorithm 1's compression keeps
   instance.py   writes an H^2 instance to a .npz file for the library's
                 h2_import
 
@@ -44,5 +47,6 @@ PARITY = {
     "ulv.solve_parallel": "pinned: equals the naive Algorithm 3 on the exact-rank kernel",
     "ulv.matvec": "pinned: equals the dense assembly of the H^2 matrix",
     "ulv.refine": "pinned: residual reaches the target; matches dense solve within the H^2 error",
+    "mlp": "pinned: central finite differences of the loss; closed form for a constant network",
     "dense": "pinned: numpy.linalg.solve on random systems",
 }
