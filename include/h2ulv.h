@@ -11,7 +11,7 @@
  *              Section 3.6), every level one wide batch on the GPU.
  *   h2_solve   forward/backward substitution in the parallel product form of
  *              Eq. 24-31 (Section 3.7), wrapped in iterative refinement whose
- *              residual uses the FP64 H^2 matrix-vector product.
+ *              residual is the H^2 matrix-vector product to FP64 accuracy.
  *   h2_matvec  y = A_H2 x in FP64.
  *
  * Conventions (all entry points):
@@ -90,13 +90,28 @@ typedef struct {
   int32_t near_samples;/* sample size per close box */
 } h2_params;
 
-/* Arithmetic of the projection and Schur-update contractions (Algorithm 4
- * line 3, line 6 and line 10).  The LU of the redundant diagonal blocks, the
- * refinement residual and update always run in FP64.
- *   H2_PREC_FP64   FP64 everywhere (the plain H^2-ULV).
- *   H2_PREC_FP16   FP16 inputs, FP32 accumulation on the tensor cores;
- *                  FP32 bases, factors and substitution.
- *   H2_PREC_BF16   as FP16 with BF16 inputs. */
+/* Arithmetic of the factorization (Algorithm 4), of the substitution
+ * (Eq. 24-31) and of the refinement around it.
+ *   H2_PREC_FP64   FP64 everywhere (the plain H^2-ULV): complement bases,
+ *                  projection, LU and inverse of Ahat_ii^RR, Schur update,
+ *                  couplings, merge and substitution; the refinement's
+ *                  residual and update in FP64.
+ *   H2_PREC_FP16   the projection U_i^T A_ij U_j and the couplings
+ *                  T_i S_ij T_j^T on the tensor cores with FP16 operands
+ *                  (scaled by powers of two) and FP32 accumulation; the
+ *                  complement bases (Householder QR), the Schur update and
+ *                  the merge in FP32; the inverse of Ahat_ii^RR by FP32
+ *                  Gauss-Jordan elimination with partial pivoting (default)
+ *                  or by FP64 partial-pivot elimination rounded once to FP32
+ *                  (h2_set_option H2_OPT_RR_LU_FP64 = 1).  The substitution
+ *                  reads 16-bit RR/RS/SR quadrants and FP32 bases and
+ *                  inverses.  Refinement (scheme 2 of h2_solve): the
+ *                  residual b - A_H2 x with each FP64 matrix entry held as
+ *                  two FP32 numbers and FP32-pair sums (about 2^-46
+ *                  relative per product sum; default) or with FP64
+ *                  instructions (H2_OPT_RESIDUAL_FP64 = 1); the update
+ *                  x += d in FP64; the inner FGMRES in FP32.
+ *   H2_PREC_BF16   as FP16 with BF16 operands. */
 typedef enum { H2_PREC_FP64 = 0, H2_PREC_FP16 = 1, H2_PREC_BF16 = 2 } h2_prec;
 
 /* An H^2 instance given as plain host arrays (for h2_import).  Layouts:
@@ -171,10 +186,13 @@ h2_status h2_import(h2_ctx** out, const h2_params* p, const h2_instance* inst);
 h2_status h2_factor(h2_ctx* c, int32_t prec);
 
 /* Solve A_H2 x = b by refinement with the factorization as preconditioner.
- * Every refinement residual r = b - A_H2 x is computed in FP64 (the
- * h2_matvec operator) and every update x += d is FP64; each preconditioner
- * application is the parallel substitution of Eq. 24-31 and its mirror, in
- * the factorization's storage precision.  Schemes (h2_set_refinement):
+ * Every refinement residual r = b - A_H2 x is FP64-accurate: FP64
+ * instructions (the h2_matvec operator) in schemes 0 and 1, FP32-pair
+ * arithmetic by default in scheme 2 (H2_OPT_RESIDUAL_FP64 selects FP64
+ * instructions there too).  Every update x += d is FP64; each
+ * preconditioner application is the parallel substitution of Eq. 24-31 and
+ * its mirror, in the factorization's storage precision.  Schemes
+ * (h2_set_refinement):
  *   0 plain iterative refinement: x += M^-1 (b - A_H2 x);
  *   1 FGMRES-based refinement: restarted right-preconditioned flexible
  *     GMRES in FP64, true residual recomputed after every cycle;
@@ -240,6 +258,150 @@ h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart);
  * Errors: H2_ERR_INVALID_ARG (NULL or host pointers, wrong device, too
  * large), H2_ERR_CUDA. */
 h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
+
+/* Options of a context (h2_set_option).  Both apply to the next
+ * h2_factor / h2_solve.
+ *   H2_OPT_RR_LU_FP64     FP16/BF16 factorizations: 0 (default) inverts
+ *                         Ahat_ii^RR (and the root block) by Gauss-Jordan
+ *                         elimination with partial pivoting in FP32; 1 does
+ *                         the partial-pivot elimination in FP64 and rounds
+ *                         the inverse once to FP32 (same pivot rule; LAPACK's
+ *                         pivots).  FP64 factorizations always use FP64.
+ *   H2_OPT_RESIDUAL_FP64  refinement scheme 2: 0 (default) forms
+ *                         b - A_H2 x in FP32-pair arithmetic, 1 with FP64
+ *                         instructions (the h2_matvec operator). */
+typedef enum { H2_OPT_RR_LU_FP64 = 0, H2_OPT_RESIDUAL_FP64 = 1 } h2_option;
+
+/* Set an h2_option to value (0 or 1).  Errors: H2_ERR_INVALID_ARG. */
+h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value);
+
+/* y = A_H2 x in one of the library's three matvec arithmetics (the same
+ * kernels the solver runs), for inspection and tests:
+ *   0  FP64 (h2_matvec; the refinement residual of FP64 factorizations);
+ *   1  FP32: the FP32 copy of A_H2 that the inner solver of refinement
+ *      scheme 2 multiplies by, applied to x rounded to FP32; y is that FP32
+ *      result widened to FP64;
+ *   2  FP32 pairs: every FP64 matrix entry held as hi = fl32(a) plus
+ *      lo = fl32(a - hi) and products summed as FP32 pairs, with the
+ *      passes through the bases in FP64 (the default residual of scheme 2).
+ * N doubles each, host or device.  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
+h2_status h2_matvec_arith(h2_ctx* c, const double* x, double* y, int32_t arith);
+
+/* Self-test of the library's bounded device-side waits (no counterpart in
+ * the paper).  Launches one CTA whose thread 0 waits, with the same
+ * bounded mbarrier wait the TMA-fed kernels use, on a barrier that nothing
+ * ever completes; after timeout_ns (1 .. 10^10) of GPU global time the wait
+ * gives up and the kernel records it in the context's status word, exactly
+ * as a kernel whose copies never landed would.  Returns H2_ERR_TIMEOUT with
+ * the reason in h2_last_error when the wait gave up as designed (the
+ * context stays usable), H2_OK if it did not, H2_ERR_INVALID_ARG or
+ * H2_ERR_CUDA. */
+h2_status h2_wait_selftest(h2_ctx* c, int64_t timeout_ns);
+
+/* Process-wide cap on the device memory one context may allocate (bytes;
+ * 0: no cap beyond the device's free memory).  h2_build and h2_import check
+ * the instance's device bytes, and h2_factor the factorization's, against
+ * the cap and against cudaMemGetInfo's free memory before allocating or
+ * launching anything, and return H2_ERR_OOM with both figures in
+ * h2_last_error when it does not fit.  The check against the cap comes
+ * before any CUDA call.  The byte counts are estimates of the largest
+ * arrays (blocks, bases, couplings), not of every small buffer. */
+h2_status h2_set_memory_limit(uint64_t bytes);
+
+/* ---------------------------------------------------------------------------
+ * Learned rank predictor (an extension of Algorithm 1; the paper has no
+ * counterpart).  A 16 -> 64 -> 64 -> 1 multilayer perceptron with ReLU
+ * activations maps a cluster's geometry features to the fraction k / n of
+ * its dimension n that the rank-revealing compression keeps, so that every
+ * level's rank (the batch layout) is known before any compression runs.
+ * The network is trained and evaluated on the GPU by the library's own
+ * kernels: BF16 weights, inputs and hidden activations with FP32
+ * accumulation, FP32 master weights, full-batch Adam.
+ * Parameters, flat, 5313 floats: W1 (64 x 16 row-major), b1 (64),
+ * W2 (64 x 64 row-major), b2 (64), w3 (64), b3 (1).
+ * Features of box i at level l (16 floats, in this order): log10 of the
+ * three extents of the box's bounding box, largest first; log2 of its point
+ * count; log2 of its dimension n (points at the leaves, twice the
+ * children's rank above); log2 of its near-box count; log2(1 + far-box
+ * count); log10 of the smallest centre distance to a far box over the box
+ * radius (0 without far boxes); eta; l / L; log10(tol); three indicators of
+ * the kernel family (1/r-type, exp(-r)/r-type, Gaussian); log10 of the
+ * kernel's length parameter (eps, or ell; 0 for the paper's kernels);
+ * log10 of the diagonal entry.
+ * ------------------------------------------------------------------------- */
+typedef struct h2_rank_model h2_rank_model;
+
+/* Training data from the plain compression: runs the host part of h2_build
+ * (no GPU) and writes, for every box of levels L .. 1 (leaves first, boxes
+ * in order), its 16 features (feats, nbox x 16 row-major), the fraction
+ * k_i / n_i its tolerance rank keeps (targets; k_i before the level's rank
+ * cap) and its level (levels).  cap is the room of the arrays in boxes;
+ * *nbox receives the box count (with cap too small: H2_ERR_INVALID_ARG and
+ * *nbox the count needed).  feats, targets and levels may be NULL when cap
+ * is 0.  Errors: as h2_plan. */
+h2_status h2_rank_data(const h2_params* p, const double* points, int64_t N, float* feats, float* targets,
+                       int32_t* levels, int64_t cap, int64_t* nbox);
+
+/* Create a model on the current device with He-uniform weights drawn from
+ * splitmix64(seed) and zero biases.  Errors: H2_ERR_OOM, H2_ERR_CUDA. */
+h2_status h2_rank_model_create(h2_rank_model** out, uint64_t seed);
+
+/* Set the 5313 parameters (host floats; rounded to BF16 for the kernels,
+ * kept in FP32 as the master copy) and reset the optimizer state. */
+h2_status h2_rank_model_set_weights(h2_rank_model* m, const float* theta);
+
+/* Copy the FP32 master parameters to theta (host, 5313 floats) and, when
+ * not NULL, the feature normalization (mean and 1 / standard deviation,
+ * 16 floats each) the last training set gave. */
+h2_status h2_rank_model_get_weights(h2_rank_model* m, float* theta, float* mean, float* istd);
+
+/* Loss mean((o - y)^2) and its gradient (host, 5313 floats) at the current
+ * weights for n samples whose network inputs are given directly (inputs:
+ * n x 16, rounded to BF16; no feature normalization), targets y (n).
+ * Inputs and targets host or device.  For checking the training kernels. */
+h2_status h2_rank_model_grad(h2_rank_model* m, const float* inputs, const float* targets, int64_t n, float* loss,
+                             float* grad);
+
+/* Train on n samples (features n x 16 and targets, host or device): the
+ * features are normalized by their mean and standard deviation over this
+ * set (kept with the model), then steps full-batch Adam steps (learning
+ * rate lr, beta 0.9 / 0.999) run on the GPU, 64 steps per CUDA graph.
+ * *loss_out (may be NULL) receives the last step's loss. */
+h2_status h2_rank_model_train(h2_rank_model* m, const float* feats, const float* targets, int64_t n, int32_t steps,
+                              float lr, float* loss_out);
+
+/* Network outputs (predicted k / n) for n feature rows (host or device in
+ * and out), with the model's normalization. */
+h2_status h2_rank_model_predict(h2_rank_model* m, const float* feats, int64_t n, float* out);
+
+/* One-line description of the model's last error ("" if none). */
+const char* h2_rank_model_last_error(const h2_rank_model* m);
+
+/* Free the model.  NULL is ignored. */
+void h2_rank_model_destroy(h2_rank_model* m);
+
+/* The batch layout from the predictor alone: cluster tree, near/far lists,
+ * features and one inference per level (leaves first; each level's
+ * dimension is twice the predicted rank below), no compression.  The JSON
+ * (as h2_plan's) gives per level nb, D, predicted K, NP, FP and the
+ * device bytes.  Needs the model's device.  Errors: as h2_plan. */
+h2_status h2_plan_predicted(const h2_params* p, const double* points, int64_t N, h2_rank_model* model, char* json,
+                            size_t cap);
+
+/* h2_build with the ranks laid out by the predictor: each level's rank is
+ * K_l = min(cap, max_i ceil(prediction_i n_i) + 2), and each box's
+ * interpolative decomposition comes from a randomized sketch M_i Omega of
+ * K_l + 10 columns (Rademacher Omega from splitmix64) followed by a pivoted
+ * QR truncated at K_l, in place of the full rank-revealing pass over M_i.
+ * The plain pivoted-QR compression stays the fallback and the judge: a box
+ * whose sketch shows more than tol of its leading pivot beyond K_l (below
+ * the cap), or whose error on 6 further random probes of M_i exceeds
+ * 10 max(tol, that estimate), is compressed the plain way; if that needs a
+ * larger rank the level is redone the plain way.  h2_stats reports the
+ * predicted and final ranks, the fallback count and the host compression
+ * time.  Errors: as h2_build. */
+h2_status h2_build_predicted(h2_ctx** out, const h2_params* p, const double* points, int64_t N,
+                             h2_rank_model* model);
 
 /* Issue all later work on the given cudaStream_t (NULL: legacy default). */
 h2_status h2_set_stream(h2_ctx* c, void* stream);

@@ -7,7 +7,7 @@ extension to Algorithm 1; the paper has no counterpart).  Parameters, in the
 flat order the library's C ABI uses:
 
     W1 (64 x 16, row-major), b1 (64), W2 (64 x 64, row-major), b2 (64),
-    w3 (64), b3 (1)                                  -> 5249 numbers
+    w3 (64), b3 (1)                                  -> 5313 numbers
 
 Forward:  z1 = W1 x + b1,  h1 = max(z1, 0),  z2 = W2 h1 + b2,
           h2 = max(z2, 0),  o = w3 . h2 + b3.

@@ -1,8 +1,11 @@
 """ctypes binding of the C ABI declared in include/h2ulv.h.
 
-The module-level functions carry the C names (h2_build, h2_import,
-h2_factor, h2_solve, h2_solve_many, h2_ulv_apply, h2_matvec, h2_matvec_many, h2_set_stream, h2_stats,
-h2_export, h2_last_error, h2_destroy) and only marshal arguments: every step
+The module-level functions carry the C names (h2_build, h2_plan, h2_import,
+h2_factor, h2_solve, h2_solve_many, h2_ulv_apply, h2_matvec, h2_matvec_many,
+h2_matvec_noalloc, h2_matvec_arith, h2_set_option, h2_wait_selftest,
+h2_set_memory_limit, the rank predictor's h2_rank_data / h2_rank_model_* /
+h2_plan_predicted / h2_build_predicted, h2_set_refinement, h2_set_stream, h2_stats, h2_export,
+h2_last_error, h2_destroy) and only marshal arguments: every step
 of the computation runs in the library.  ``H2Solver`` wraps a context.
 
 Vectors may be NumPy float64 arrays (host) or CUDA torch float64 tensors
@@ -28,8 +31,14 @@ STATUS = {0: "H2_OK", -1: "H2_ERR_INVALID_ARG", -2: "H2_ERR_OOM", -3: "H2_ERR_SI
 
 # every symbol include/h2ulv.h declares
 EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_solve_many", "h2_ulv_apply",
-            "h2_matvec", "h2_matvec_many", "h2_matvec_noalloc",
+            "h2_matvec", "h2_matvec_many", "h2_matvec_noalloc", "h2_matvec_arith", "h2_set_option",
+            "h2_wait_selftest", "h2_set_memory_limit", "h2_rank_data", "h2_rank_model_create",
+            "h2_rank_model_set_weights", "h2_rank_model_get_weights", "h2_rank_model_grad", "h2_rank_model_train",
+            "h2_rank_model_predict", "h2_rank_model_last_error", "h2_rank_model_destroy", "h2_plan_predicted",
+            "h2_build_predicted",
             "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
+OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1}
+ARITH = {"fp64": 0, "fp32": 1, "fp32_pair": 2}
 
 
 class H2Error(RuntimeError):
@@ -78,6 +87,21 @@ def lib() -> ctypes.CDLL:
             "h2_matvec": (i32, [vp, vp, vp]),
             "h2_matvec_noalloc": (i32, [vp, vp, vp]),
             "h2_set_refinement": (i32, [vp, i32, i32]),
+            "h2_set_option": (i32, [vp, i32, i64]),
+            "h2_matvec_arith": (i32, [vp, vp, vp, i32]),
+            "h2_wait_selftest": (i32, [vp, i64]),
+            "h2_set_memory_limit": (i32, [ctypes.c_uint64]),
+            "h2_rank_data": (i32, [vp, vp, i64, vp, vp, vp, i64, vp]),
+            "h2_rank_model_create": (i32, [pp, ctypes.c_uint64]),
+            "h2_rank_model_set_weights": (i32, [vp, vp]),
+            "h2_rank_model_get_weights": (i32, [vp, vp, vp, vp]),
+            "h2_rank_model_grad": (i32, [vp, vp, vp, i64, vp, vp]),
+            "h2_rank_model_train": (i32, [vp, vp, vp, i64, i32, ctypes.c_float, vp]),
+            "h2_rank_model_predict": (i32, [vp, vp, i64, vp]),
+            "h2_rank_model_last_error": (ctypes.c_char_p, [vp]),
+            "h2_rank_model_destroy": (None, [vp]),
+            "h2_plan_predicted": (i32, [vp, vp, i64, vp, ctypes.c_char_p, ctypes.c_size_t]),
+            "h2_build_predicted": (i32, [pp, vp, vp, i64, vp]),
             "h2_set_stream": (i32, [vp, vp]),
             "h2_stats": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
             "h2_export": (i32, [vp, ctypes.c_char_p, i32, vp, ctypes.c_size_t, vp, vp]),
@@ -217,6 +241,114 @@ def h2_set_refinement(ctx, method: str | int = "auto", restart: int = 30):
     _check(lib().h2_set_refinement(ctx, int(m), int(restart)), ctx)
 
 
+def h2_set_option(ctx, option: str | int, value: int):
+    """option: "rr_lu_fp64" (0) or "residual_fp64" (1); value 0 or 1."""
+    _check(lib().h2_set_option(ctx, OPTIONS.get(option, option), int(value)), ctx)
+
+
+def h2_matvec_arith(ctx, x, y, arith: str | int = "fp64"):
+    """y = A_H2 x in "fp64" (0), "fp32" (1) or "fp32_pair" (2) arithmetic."""
+    _check(lib().h2_matvec_arith(ctx, _ptr(x), _ptr(y), ARITH.get(arith, arith)), ctx)
+
+
+def h2_wait_selftest(ctx, timeout_ns: int):
+    """Returns the raw status (-6, H2_ERR_TIMEOUT, when the wait gave up)."""
+    return lib().h2_wait_selftest(ctx, int(timeout_ns))
+
+
+def h2_set_memory_limit(nbytes: int):
+    _check(lib().h2_set_memory_limit(int(nbytes)), None)
+
+
+# ------------------------------------------------------ rank predictor ---
+RANK_FEATURES = 16
+RANK_PARAMS = 5313
+
+
+def _check_model(st: int, m):
+    if st != 0:
+        msg = lib().h2_rank_model_last_error(m) if m else lib().h2_last_error(None)
+        raise H2Error(st, msg.decode() if msg else "")
+
+
+def h2_rank_data(params: Params, points: np.ndarray):
+    """Features (nbox x 16), targets k_i / n_i and levels of every box from
+    the plain compression (host only)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    nbox = ctypes.c_int64()
+    st = lib().h2_rank_data(ctypes.byref(params), _ptr(pts), len(pts), None, None, None, 0, ctypes.byref(nbox))
+    if st not in (0, -1):
+        _check(st, None)
+    n = nbox.value
+    F = np.zeros((n, RANK_FEATURES), dtype=np.float32)
+    y = np.zeros(n, dtype=np.float32)
+    lv = np.zeros(n, dtype=np.int32)
+    _check(lib().h2_rank_data(ctypes.byref(params), _ptr(pts), len(pts), _ptr(F), _ptr(y), _ptr(lv), n,
+                              ctypes.byref(nbox)), None)
+    return F, y, lv
+
+
+def h2_rank_model_create(seed: int = 0):
+    out = ctypes.c_void_p()
+    _check_model(lib().h2_rank_model_create(ctypes.byref(out), int(seed)), None)
+    return out
+
+
+def h2_rank_model_set_weights(m, theta):
+    t = np.ascontiguousarray(theta, dtype=np.float32)
+    _check_model(lib().h2_rank_model_set_weights(m, _ptr(t)), m)
+
+
+def h2_rank_model_get_weights(m):
+    t = np.zeros(RANK_PARAMS, dtype=np.float32)
+    mean = np.zeros(RANK_FEATURES, dtype=np.float32)
+    istd = np.zeros(RANK_FEATURES, dtype=np.float32)
+    _check_model(lib().h2_rank_model_get_weights(m, _ptr(t), _ptr(mean), _ptr(istd)), m)
+    return t, mean, istd
+
+
+def h2_rank_model_grad(m, inputs, targets):
+    X = np.ascontiguousarray(inputs, dtype=np.float32)
+    y = np.ascontiguousarray(targets, dtype=np.float32)
+    g = np.zeros(RANK_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check_model(lib().h2_rank_model_grad(m, _ptr(X), _ptr(y), len(y), ctypes.byref(loss), _ptr(g)), m)
+    return float(loss.value), g
+
+
+def h2_rank_model_train(m, feats, targets, steps=2000, lr=3e-3):
+    X = np.ascontiguousarray(feats, dtype=np.float32)
+    y = np.ascontiguousarray(targets, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check_model(lib().h2_rank_model_train(m, _ptr(X), _ptr(y), len(y), int(steps), float(lr), ctypes.byref(loss)), m)
+    return float(loss.value)
+
+
+def h2_rank_model_predict(m, feats):
+    X = np.ascontiguousarray(feats, dtype=np.float32)
+    out = np.zeros(len(X), dtype=np.float32)
+    _check_model(lib().h2_rank_model_predict(m, _ptr(X), len(X), _ptr(out)), m)
+    return out
+
+
+def h2_rank_model_destroy(m):
+    lib().h2_rank_model_destroy(m)
+
+
+def h2_plan_predicted(params: Params, points: np.ndarray, m) -> dict:
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    buf = ctypes.create_string_buffer(1 << 20)
+    _check(lib().h2_plan_predicted(ctypes.byref(params), _ptr(pts), len(pts), m, buf, len(buf)), None)
+    return json.loads(buf.value.decode())
+
+
+def h2_build_predicted(params: Params, points: np.ndarray, m):
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(lib().h2_build_predicted(ctypes.byref(out), ctypes.byref(params), _ptr(pts), len(pts), m), None)
+    return out
+
+
 def h2_set_stream(ctx, stream):
     handle = getattr(stream, "cuda_stream", stream)
     _check(lib().h2_set_stream(ctx, ctypes.c_void_p(int(handle) if handle else 0)), ctx)
@@ -262,6 +394,11 @@ class H2Solver:
         return cls(h2_build(make_params(**kw), points), len(points))
 
     @classmethod
+    def build_predicted(cls, points, model, **kw):
+        """h2_build with the ranks laid out by a trained rank model."""
+        return cls(h2_build_predicted(make_params(**kw), points, model), len(points))
+
+    @classmethod
     def from_instance(cls, flat: dict, **kw):
         return cls(h2_import(make_params(**kw), flat), int(flat["N"]))
 
@@ -302,6 +439,14 @@ class H2Solver:
 
     def set_stream(self, stream):
         h2_set_stream(self.ctx, stream)
+
+    def set_option(self, option, value):
+        h2_set_option(self.ctx, option, value)
+
+    def matvec_arith(self, x, arith="fp64"):
+        y = np.zeros_like(x) if isinstance(x, np.ndarray) else x.new_zeros(x.shape)
+        h2_matvec_arith(self.ctx, x, y, arith)
+        return y
 
     def set_refinement(self, method="auto", restart=30):
         h2_set_refinement(self.ctx, method, restart)

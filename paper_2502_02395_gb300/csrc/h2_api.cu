@@ -558,6 +558,14 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   const int bf16 = (prec == H2_PREC_BF16) ? 1 : 0;
   F.bf16 = bf16;
   const bool mixed = !std::is_same<T, double>::value;
+  // FP64 a3 for the FP16/BF16 factorizations: scratch for the largest level
+  const bool lu64_mixed = mixed && c->rr_lu64;
+  if (lu64_mixed && !F.rr_lu) {
+    size_t n = (size_t)c->lv[0].D * c->lv[0].D;
+    for (int l = 1; l <= L; ++l) n = std::max(n, (size_t)c->lv[l].nb * c->lv[l].R * c->lv[l].R);
+    CKC(dalloc(c, &F.rr_lu, n));
+    CKC(dalloc(c, &F.rr_inv, n));
+  }
   bool any_tc = false;
   for (int l = 1; l <= L; ++l) any_tc = any_tc || F.lv[l].tc || F.lv[l].tc_coup;
   if (mixed && any_tc) CKS(make_leaf_lowp(c, bf16));
@@ -755,6 +763,15 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
         launch_transpose16_blocks(D, R, d.n_lw, d.lw_q, d.lw_m, f.Ahat16, sp);
       }
       if (!ok) return fail(H2_ERR_CUDA, "tensor-core GEMM setup failed at level " + std::to_string(l));
+    } else if (!mixed && d.near_sym && d.n_lw > 0) {
+      // FP64, symmetric near list: project the upper pairs i <= j, then
+      // Ahat_ji = Ahat_ij^T for the lower ones (the kernels are symmetric)
+      const T* Ain = (l == L) ? Aleaf : f.Ain;
+      gemm<T>(prec, D, D, D, Ain, DD, d.su_q, D, false, f.U, DD, d.su_j, D, true, F.Wk, DD, nullptr, D, T(1), T(0),
+              d.n_up, st);
+      gemm<T>(prec, D, D, D, f.U, DD, d.su_i, D, false, F.Wk, DD, nullptr, D, false, f.Ahat, DD, d.su_q, D, T(1),
+              T(0), d.n_up, st);
+      launch_transpose_pairs<T>(D, d.n_lw, d.lw_q, d.lw_m, f.Ahat, st);
     } else {
       const T* Ain = (l == L) ? Aleaf : f.Ain;
       gemm<T>(prec, D, D, D, Ain, DD, nullptr, D, false, f.U, DD, d.near_j, D, true, F.Wk, DD, nullptr, D, T(1),
@@ -763,8 +780,13 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
               T(0), d.NP, st);
     }
     mark();
-    // a3: LU of Ahat_ii^RR and its inverse
-    launch_lu_inverse<T>(d.nb, D, R, f.Ahat, d.diag_pair, f.lu, f.luT, f.piv, f.Ainv, c->status, l, st);
+    // a3: LU of Ahat_ii^RR and its inverse (FP16/BF16 factorizations: in
+    // FP64 from the FP32 blocks, or FP32 Gauss-Jordan)
+    if (lu64_mixed)
+      launch_lu_inverse_f64_for_f32(d.nb, D, R, reinterpret_cast<const float*>(f.Ahat), d.diag_pair, F.rr_lu,
+                                    F.rr_inv, f.piv, reinterpret_cast<float*>(f.Ainv), c->status, l, st);
+    else
+      launch_lu_inverse<T>(d.nb, D, R, f.Ahat, d.diag_pair, f.lu, f.luT, f.piv, f.Ainv, c->status, l, st);
     mark();
     // the substitution's first product M1 = Ainv (U^R)^T, beside the chain
     // ((U^R)^T: the first R columns of the column-major U, as rows)
@@ -820,7 +842,11 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   // a7: root
   const int D0 = c->lv[0].D;
   const T* Aroot = (L == 0) ? Aleaf : F.lv[0].Ain;
-  launch_lu_inverse<T>(1, D0, D0, Aroot, nullptr, F.root_lu, F.root_luT, F.root_piv, F.root_inv, c->status, 0, st);
+  if (lu64_mixed)
+    launch_lu_inverse_f64_for_f32(1, D0, D0, reinterpret_cast<const float*>(Aroot), nullptr, F.rr_lu, F.rr_inv,
+                                  F.root_piv, reinterpret_cast<float*>(F.root_inv), c->status, 0, st);
+  else
+    launch_lu_inverse<T>(1, D0, D0, Aroot, nullptr, F.root_lu, F.root_luT, F.root_piv, F.root_inv, c->status, 0, st);
   mark();
   CKC(cudaGetLastError());
   CKC(cudaStreamSynchronize(st));
@@ -1392,10 +1418,68 @@ h2_status nested_refine(h2_ctx* c, SolveTimer& tm, double bnorm, double target, 
     for (int i = 0; i < k; ++i) W.y[i] *= beta;
     CKC(cudaMemcpyAsync(W.yv, W.y.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
     launch_multi_axpy<float, double>(c->gm_Z32, n, k, W.yv, 1.0, c->x64, n, st);
-    CKS(fp64_residual(c, tm, beta, true));
+    CKS(fp64_residual(c, tm, beta, !c->resid64));
     rel = beta / bnorm;
     c->times.history.push_back(rel);
     if (!std::isfinite(rel)) break;
+  }
+  return H2_OK;
+}
+
+// ---------------------------------------------------------------------------
+// device-memory estimates checked before allocating (h2_set_memory_limit)
+// ---------------------------------------------------------------------------
+uint64_t g_mem_limit = 0;  // process-wide cap on one context's device bytes (0: none)
+
+// The instance's largest device arrays: the leaf near blocks (FP64, the FP32
+// pair of the stored halves, the 16-bit copy), bases and couplings.
+double instance_bytes(const HostH2& H) {
+  const int L = H.L;
+  const HostLevel& lf = H.lv[L];
+  const double D = lf.D, NP = lf.near.size() / 2.0;
+  double b = NP * D * D * (8.0 + 2.0) + (NP + lf.nb) / 2.0 * D * D * 8.0;
+  for (int l = 1; l <= L; ++l) {
+    const HostLevel& h = H.lv[l];
+    b += (double)h.nb * h.D * h.K * 16.0 + (h.far.size() / 2.0) * h.K * h.K * 22.0;
+  }
+  return b + (double)lf.nb * D * 8.0 * 8.0;
+}
+
+// One factorization's largest arrays in storage type of size sz (8: FP64,
+// 4: FP16/BF16 factorizations with FP32 storage).
+double factor_bytes(const h2_ctx* c, int sz) {
+  double b = 0, wk = 0;
+  for (int l = 1; l <= c->L; ++l) {
+    const DevLevel& d = c->lv[l];
+    const double D = d.D, K = d.K, R = d.R, nb = d.nb, NP = (double)d.NP;
+    b += NP * D * D * (sz + (sz == 4 ? 2.0 : 0.0));                  // Ahat (+ 16-bit copy)
+    if (l < c->L) b += NP * D * D * (sz == 4 ? 2.0 : sz);            // the level's input blocks
+    b += nb * (3 * D * D + 2 * D * K + 2 * K * K + R * K + 2 * R * R + R * D) * sz;
+    b += (double)d.FP * K * K * sz;
+    wk = std::max(wk, NP * D * D * sz);
+  }
+  return b + wk;
+}
+
+// H2_ERR_OOM when need exceeds the cap or the device's free memory; the cap
+// is checked first, before any CUDA call.
+h2_status check_fits(double need, const char* what, std::string& err) {
+  char buf[256];
+  if (g_mem_limit > 0 && need > (double)g_mem_limit) {
+    std::snprintf(buf, sizeof buf, "%s needs about %.0f device bytes; the memory limit is %llu", what, need,
+                  (unsigned long long)g_mem_limit);
+    err = buf;
+    return H2_ERR_OOM;
+  }
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+    if (need > (double)fr) {
+      std::snprintf(buf, sizeof buf, "%s needs about %.0f device bytes; %zu are free", what, need, fr);
+      err = buf;
+      return H2_ERR_OOM;
+    }
+  } else {
+    cudaGetLastError();
   }
   return H2_OK;
 }
@@ -1424,6 +1508,11 @@ h2_status h2_build(h2_ctx** out, const h2_params* p, const double* points, int64
     g_last_error = e;
     delete c;
     return H2_ERR_SINGULAR;
+  }
+  s = check_fits(instance_bytes(c->host), "the H^2 instance", g_last_error);
+  if (s != H2_OK) {
+    delete c;
+    return s;
   }
   s = setup_device(c);
   if (s != H2_OK) {
@@ -1461,7 +1550,8 @@ h2_status h2_plan(const h2_params* p, const double* points, int64_t N, char* jso
     bytes_build += 8.0 * (nb * D * K + FP * K * K) + (l == H.L ? 8.0 * NP * D * D : 0.0);
     bytes_factor64 += 8.0 * (2 * NP * D * D + nb * (D * D + D * K + 2 * R * R + R * K) + FP * K * K);
   }
-  o << "],\"device_bytes_build\":" << bytes_build << ",\"device_bytes_factor_fp64\":" << bytes_factor64 << "}";
+  o << "],\"device_bytes_build\":" << bytes_build << ",\"device_bytes_factor_fp64\":" << bytes_factor64
+    << ",\"compress_s\":" << H.rec.compress_s << "}";
   std::string str = o.str();
   if (str.size() + 1 > cap) { g_last_error = "cap too small"; return H2_ERR_INVALID_ARG; }
   std::memcpy(json, str.c_str(), str.size() + 1);
@@ -1519,6 +1609,11 @@ h2_status h2_import(h2_ctx** out, const h2_params* p, const h2_instance* in) {
     delete c;
     return H2_ERR_INVALID_ARG;
   }
+  s = check_fits(instance_bytes(c->host), "the H^2 instance", g_last_error);
+  if (s != H2_OK) {
+    delete c;
+    return s;
+  }
   s = setup_device(c);
   if (s != H2_OK) {
     g_last_error = c->err;
@@ -1537,6 +1632,8 @@ h2_status h2_factor(h2_ctx* c, int32_t prec) {
     return H2_ERR_INVALID_ARG;
   }
   c->prec = -1;
+  const bool fresh = (prec == H2_PREC_FP64) ? c->f64.lv.empty() : c->f32.lv.empty();
+  if (fresh) CKS(check_fits(factor_bytes(c, prec == H2_PREC_FP64 ? 8 : 4), "the factorization", c->err));
   h2_status s = (prec == H2_PREC_FP64) ? factor_impl<double>(c, c->f64, prec) : factor_impl<float>(c, c->f32, prec);
   if (s == H2_OK) c->prec = prec;
   return s;
@@ -1681,6 +1778,178 @@ h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart) {
   return H2_OK;
 }
 
+h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value) {
+  if (!c) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  if (value != 0 && value != 1) {
+    c->err = "option value must be 0 or 1";
+    return H2_ERR_INVALID_ARG;
+  }
+  switch (option) {
+    case H2_OPT_RR_LU_FP64: c->rr_lu64 = value != 0; return H2_OK;
+    case H2_OPT_RESIDUAL_FP64: c->resid64 = value != 0; return H2_OK;
+    default: c->err = "unknown option"; return H2_ERR_INVALID_ARG;
+  }
+}
+
+h2_status h2_matvec_arith(h2_ctx* c, const double* x, double* y, int32_t arith) {
+  if (!c || !x || !y) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  if (arith < 0 || arith > 2) {
+    c->err = "arith must be 0 (FP64), 1 (FP32) or 2 (FP32 pairs)";
+    return H2_ERR_INVALID_ARG;
+  }
+  const int64_t n = nslots(c);
+  CKS(vec_in(c, x, c->x64));
+  if (arith == 0) {
+    matvec_impl(c, c->x64, c->y64);
+  } else if (arith == 2) {
+    matvec_df(c, c->x64, c->y64);
+  } else {
+    if (!c->mv32_x) {
+      CKC(dalloc(c, &c->mv32_x, (size_t)n));
+      CKC(dalloc(c, &c->mv32_y, (size_t)n));
+    }
+    launch_convert<double, float>(c->x64, c->mv32_x, n, c->stream);
+    matvec32(c, c->mv32_x, c->mv32_y);
+    launch_convert<float, double>(c->mv32_y, c->y64, n, c->stream);
+  }
+  CKC(cudaGetLastError());
+  CKS(vec_out(c, c->y64, y));
+  CKC(cudaStreamSynchronize(c->stream));
+  return H2_OK;
+}
+
+h2_status h2_wait_selftest(h2_ctx* c, int64_t timeout_ns) {
+  if (!c) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  if (timeout_ns < 1 || timeout_ns > 10000000000ll) {
+    c->err = "timeout_ns outside 1 .. 1e10";
+    return H2_ERR_INVALID_ARG;
+  }
+  // the substitution kernels' status word: cleared, set by the waiting
+  // kernel when it gives up, read back
+  CKS(subst_clear(c));
+  launch_wait_selftest((unsigned long long)timeout_ns, c->status + 3, c->stream);
+  CKC(cudaGetLastError());
+  const h2_status s = subst_check(c);
+  if (s == H2_ERR_TIMEOUT) {
+    c->err = "self-test: the bounded wait gave up after " + std::to_string(timeout_ns) + " ns as designed";
+    CKS(subst_clear(c));
+    CKC(cudaStreamSynchronize(c->stream));
+  }
+  return s;
+}
+
+h2_status h2_set_memory_limit(uint64_t bytes) {
+  g_mem_limit = bytes;
+  return H2_OK;
+}
+
+h2_status h2_rank_data(const h2_params* p, const double* points, int64_t N, float* feats, float* targets,
+                       int32_t* levels, int64_t cap, int64_t* nbox) {
+  g_last_error.clear();
+  h2_status s = check_params(p, g_last_error);
+  if (s != H2_OK) return s;
+  if (N < 1 || !points || !nbox || cap < 0) { g_last_error = "N < 1 or NULL pointer"; return H2_ERR_INVALID_ARG; }
+  for (int64_t t = 0; t < 3 * N; ++t)
+    if (!std::isfinite(points[t])) { g_last_error = "non-finite coordinate"; return H2_ERR_INVALID_ARG; }
+  HostH2 H;
+  std::string e = build_host(*p, points, N, H);
+  if (!e.empty()) { g_last_error = e; return H2_ERR_SINGULAR; }
+  int64_t total = 0;
+  for (int l = H.L; l >= 1; --l) total += H.lv[l].nb;
+  *nbox = total;
+  if (cap < total) { g_last_error = "cap too small"; return H2_ERR_INVALID_ARG; }
+  if (total && (!feats || !targets || !levels)) { g_last_error = "NULL output array"; return H2_ERR_INVALID_ARG; }
+  int64_t k = 0;
+  for (int l = H.L; l >= 1; --l)
+    for (int i = 0; i < H.lv[l].nb; ++i, ++k) {
+      std::memcpy(feats + k * kRankFeatures, &H.rec.feats[l][(size_t)i * kRankFeatures], sizeof(float) * kRankFeatures);
+      const int n = H.rec.dims[l][i];
+      targets[k] = n > 0 ? (float)H.rec.ranks[l][i] / (float)n : 0.f;
+      levels[k] = l;
+    }
+  return H2_OK;
+}
+
+namespace {
+// the rank model as the construction calls it
+struct ModelPredictor : RankPredictor {
+  h2_rank_model* m;
+  explicit ModelPredictor(h2_rank_model* mm) : m(mm) {}
+  bool predict(const std::vector<float>& f, int nb, std::vector<float>& out) override {
+    out.assign(nb, 0.f);
+    return h2_rank_model_predict(m, f.data(), nb, out.data()) == H2_OK;
+  }
+};
+}  // namespace
+
+h2_status h2_plan_predicted(const h2_params* p, const double* points, int64_t N, h2_rank_model* model, char* json,
+                            size_t cap) {
+  g_last_error.clear();
+  h2_status s = check_params(p, g_last_error);
+  if (s != H2_OK) return s;
+  if (N < 1 || !points || !json || !model) { g_last_error = "N < 1 or NULL pointer"; return H2_ERR_INVALID_ARG; }
+  for (int64_t t = 0; t < 3 * N; ++t)
+    if (!std::isfinite(points[t])) { g_last_error = "non-finite coordinate"; return H2_ERR_INVALID_ARG; }
+  HostH2 H;
+  ModelPredictor pred(model);
+  std::string e = build_host(*p, points, N, H, &pred, true);
+  if (!e.empty()) { g_last_error = e; return H2_ERR_CUDA; }
+  std::ostringstream o;
+  double bytes_build = 0;
+  o << "{\"N\":" << N << ",\"L\":" << H.L << ",\"levels\":[";
+  for (int l = 0; l <= H.L; ++l) {
+    const HostLevel& h = H.lv[l];
+    const double D = h.D, K = l ? h.K : 0, NP = h.near.size() / 2, FP = h.far.size() / 2, nb = h.nb;
+    if (l) o << ",";
+    o << "{\"l\":" << l << ",\"nb\":" << h.nb << ",\"D\":" << h.D << ",\"K\":" << (l ? h.K : 0)
+      << ",\"NP\":" << (int64_t)NP << ",\"FP\":" << (int64_t)FP << "}";
+    bytes_build += 8.0 * (nb * D * K + FP * K * K) + (l == H.L ? 8.0 * NP * D * D : 0.0);
+  }
+  o << "],\"device_bytes_build\":" << bytes_build << "}";
+  std::string str = o.str();
+  if (str.size() + 1 > cap) { g_last_error = "cap too small"; return H2_ERR_INVALID_ARG; }
+  std::memcpy(json, str.c_str(), str.size() + 1);
+  return H2_OK;
+}
+
+h2_status h2_build_predicted(h2_ctx** out, const h2_params* p, const double* points, int64_t N,
+                             h2_rank_model* model) {
+  g_last_error.clear();
+  if (!out || !model) { g_last_error = "NULL argument"; return H2_ERR_INVALID_ARG; }
+  *out = nullptr;
+  h2_status s = check_params(p, g_last_error);
+  if (s != H2_OK) return s;
+  if (N < 1 || !points) { g_last_error = "N < 1 or points NULL"; return H2_ERR_INVALID_ARG; }
+  for (int64_t t = 0; t < 3 * N; ++t)
+    if (!std::isfinite(points[t])) { g_last_error = "non-finite coordinate"; return H2_ERR_INVALID_ARG; }
+  h2_ctx* c = new h2_ctx();
+  c->params = *p;
+  c->kfn = KernelFn{p->kernel, p->eps, p->ell, p->diag_shift};
+  ModelPredictor pred(model);
+  std::string e = build_host(*p, points, N, c->host, &pred);
+  if (!e.empty()) {
+    g_last_error = e;
+    delete c;
+    return H2_ERR_SINGULAR;
+  }
+  s = check_fits(instance_bytes(c->host), "the H^2 instance", g_last_error);
+  if (s != H2_OK) {
+    delete c;
+    return s;
+  }
+  s = setup_device(c);
+  if (s != H2_OK) {
+    g_last_error = c->err;
+    h2_destroy(c);
+    return s;
+  }
+  *out = c;
+  return H2_OK;
+}
+
 h2_status h2_set_stream(h2_ctx* c, void* stream) {
   if (!c) return H2_ERR_INVALID_ARG;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -1758,7 +2027,16 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     << ",\"restart\":" << c->restart << ",\"tensor_cores\":" << (c->used_tc ? "true" : "false")
     << ",\"history\":[";
   for (size_t k = 0; k < t.history.size(); ++k) o << (k ? "," : "") << t.history[k];
-  o << "]}";
+  o << "]";
+  // the construction's rank layout: the predictor's ranks (-1: not used),
+  // the final ranks, the boxes and levels that fell back to the plain pass
+  const RankRecord& rec = c->host.rec;
+  o << ",\"construction\":{\"compress_s\":" << rec.compress_s << ",\"fallback_boxes\":" << rec.fallback_boxes
+    << ",\"fallback_levels\":" << rec.fallback_levels << ",\"K_pred\":[";
+  for (int l = 0; l <= c->L; ++l) o << (l ? "," : "") << (l < (int)rec.K_pred.size() ? rec.K_pred[l] : -1);
+  o << "],\"K\":[";
+  for (int l = 0; l <= c->L; ++l) o << (l ? "," : "") << c->lv[l].K;
+  o << "]}}";
   std::string s = o.str();
   if (s.size() + 1 > cap) return H2_ERR_INVALID_ARG;
   std::memcpy(json, s.c_str(), s.size() + 1);

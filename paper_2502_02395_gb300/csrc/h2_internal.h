@@ -79,6 +79,20 @@ struct HostLevel {
   std::vector<int64_t> SK;    // nb * K
 };
 
+// Features of the learned rank predictor per box (the list in h2ulv.h).
+constexpr int kRankFeatures = 16;
+
+// What the construction records about its ranks.
+struct RankRecord {
+  std::vector<std::vector<float>> feats;  // per level: nb * kRankFeatures
+  std::vector<std::vector<int>> ranks;    // per level: tolerance rank of each box (plain boxes; -1 sketched)
+  std::vector<std::vector<int>> dims;     // per level: box dimension n_i
+  std::vector<int> K_pred;                // per level: the predictor's rank (-1: not used)
+  int fallback_boxes = 0;                 // boxes compressed the plain way after a failed sketch check
+  int fallback_levels = 0;                // levels redone the plain way (rank too small)
+  double compress_s = 0;                  // wall time of the per-box compression passes
+};
+
 struct HostH2 {
   int64_t N = 0;
   int L = 0;
@@ -87,10 +101,23 @@ struct HostH2 {
   std::vector<int64_t> leaf_offsets; // 2^L + 1
   std::vector<HostLevel> lv;         // L + 1
   std::vector<int> ranks_leaf;       // tol-rank per leaf box (diagnostic)
+  RankRecord rec;
+};
+
+// The rank predictor as the construction calls it: predictions k / n for
+// nb rows of features (nb * kRankFeatures floats).  False on failure.
+struct RankPredictor {
+  virtual bool predict(const std::vector<float>& feats, int nb, std::vector<float>& out) = 0;
+  virtual ~RankPredictor() = default;
 };
 
 // Host construction (host_build.cpp).  Returns an empty string on success.
-std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& out);
+// With pred, every level's rank comes from the predictor and the boxes are
+// compressed by randomized sketches (plain pivoted QR as the fallback);
+// with layout_only, the levels are laid out from predictions alone (no
+// compression; X and SK stay empty).
+std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& out,
+                       RankPredictor* pred = nullptr, bool layout_only = false);
 
 // ---------------------------------------------------------------------------
 // Device-side state.
@@ -208,6 +235,8 @@ struct Factor {
   T* Wc = nullptr;            // max FP * K * K: SIMT coupling products
   void* W16c = nullptr;       // max FP * K * K: 16-bit coupling products
   T* part = nullptr;          // max NP * max(R, K): partial products of the substitution
+  double* rr_lu = nullptr;    // FP64 LU / inverse scratch of Ahat_ii^RR for the FP16/BF16
+  double* rr_inv = nullptr;   // factorizations' FP64 a3: max(nb R^2, D0^2) doubles each
   float* scales = nullptr;    // 2 (L + 1): per-level operand scale and its inverse
   float* tscale = nullptr;    // 2 (L + 1): scale of T16 and its inverse
   float* cscale = nullptr;    // L + 1: 1 / (scale(S16) scale(T16)^2) for the couplings
@@ -290,6 +319,9 @@ struct h2_ctx {
   bool used_tc = false;          // the last factorization ran contractions on the tensor cores
   int refine_method = 3;         // 0: plain IR, 1: FGMRES-IR in FP64, 2: FP64 outer / FP32 FGMRES inner,
                                  // 3: automatic (1 for FP64 factorizations, 2 otherwise)
+  bool rr_lu64 = false;          // FP16/BF16 factorizations: Ahat_ii^RR inverted in FP64 (else FP32)
+  bool resid64 = false;          // refinement scheme 2: residual with FP64 instructions (else FP32 pairs)
+  float *mv32_x = nullptr, *mv32_y = nullptr;  // h2_matvec_arith's FP32 tree vectors (created on first use)
   double inner_tol = 1e-6;       // relative accuracy of the FP32 inner solves
   int restart = 30;              // FGMRES restart length
   double* gm_V = nullptr;        // (restart + 1) * nslot Krylov basis

@@ -52,13 +52,14 @@ h2_status scratch_address(int dev, double** out, std::string& err) {
   return H2_OK;
 }
 
-bool on_device(const void* p) {
+// p is managed memory, or device memory of the context's device dev.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a{};
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
 }
 
 }  // namespace
@@ -66,8 +67,8 @@ bool on_device(const void* p) {
 extern "C" h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y) {
   if (!c) return H2_ERR_INVALID_ARG;
   c->err.clear();
-  if (!x || !y || !on_device(x) || !on_device(y)) {
-    c->err = "h2_matvec_noalloc needs device pointers for x and y";
+  if (!x || !y || !on_device(x, c->dev) || !on_device(y, c->dev)) {
+    c->err = "h2_matvec_noalloc needs device pointers on the context's device for x and y";
     return H2_ERR_INVALID_ARG;
   }
   int dev = -1;

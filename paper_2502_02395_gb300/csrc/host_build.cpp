@@ -12,8 +12,10 @@
 // pivots and X_i = P [I; (R11^-1 R12)^T].  Boxes of a level are independent
 // and run in parallel (OpenMP).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <numeric>
 
 #include "h2_internal.h"
@@ -202,9 +204,200 @@ bool lu_solve_cols(double* Acc, int s, double* B, int m) {
   return true;
 }
 
+// splitmix64 (Steele, Lea, Flood 2014): the counter-based generator of the
+// sketches' random signs.
+uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// The 16 features of every box of a level (the list in h2ulv.h) into f
+// (nb x kRankFeatures row-major); nbox[i] is box i's dimension.
+void level_features(const h2_params& p, const double* P, const std::vector<int64_t>& perm,
+                    const std::vector<int64_t>& off, const HostLevel& hl, int l, int L, const std::vector<int>& nbox,
+                    std::vector<float>& f) {
+  const int nb = hl.nb;
+  f.assign((size_t)nb * kRankFeatures, 0.f);
+  std::vector<double> lo(3 * (size_t)nb, INFINITY), hi(3 * (size_t)nb, -INFINITY), c(3 * (size_t)nb), R(nb);
+  for (int i = 0; i < nb; ++i) {
+    for (int64_t t = off[i]; t < off[i + 1]; ++t)
+      for (int d = 0; d < 3; ++d) {
+        const double v = P[3 * perm[t] + d];
+        lo[3 * i + d] = std::min(lo[3 * i + d], v);
+        hi[3 * i + d] = std::max(hi[3 * i + d], v);
+      }
+    double s2 = 0;
+    for (int d = 0; d < 3; ++d) {
+      if (off[i + 1] == off[i]) lo[3 * i + d] = hi[3 * i + d] = 0.0;
+      c[3 * i + d] = 0.5 * (lo[3 * i + d] + hi[3 * i + d]);
+      s2 += (hi[3 * i + d] - lo[3 * i + d]) * (hi[3 * i + d] - lo[3 * i + d]);
+    }
+    R[i] = 0.5 * std::sqrt(s2);
+  }
+  std::vector<int> nnear(nb, 0), nfar(nb, 0);
+  std::vector<double> dfar(nb, INFINITY);
+  for (size_t q = 0; q < hl.near.size() / 2; ++q) ++nnear[hl.near[2 * q]];
+  for (size_t q = 0; q < hl.far.size() / 2; ++q) {
+    const int i = hl.far[2 * q], j = hl.far[2 * q + 1];
+    ++nfar[i];
+    double d2 = 0;
+    for (int d = 0; d < 3; ++d) d2 += (c[3 * i + d] - c[3 * j + d]) * (c[3 * i + d] - c[3 * j + d]);
+    dfar[i] = std::min(dfar[i], std::sqrt(d2) / std::max(R[i], 1e-12));
+  }
+  const int k = p.kernel;
+  const float fam_lap = (k == H2_K_LAPLACE_EPS || k == H2_K_LAPLACE_PAPER) ? 1.f : 0.f;
+  const float fam_yuk = (k == H2_K_YUKAWA_EPS || k == H2_K_YUKAWA_PAPER) ? 1.f : 0.f;
+  const float fam_gau = (k == H2_K_GAUSSIAN) ? 1.f : 0.f;
+  const double lenp = (k == H2_K_LAPLACE_EPS || k == H2_K_YUKAWA_EPS) ? p.eps : (k == H2_K_GAUSSIAN ? p.ell : 1.0);
+  KernelFn G{p.kernel, p.eps, p.ell, p.diag_shift};
+  const double origin[3] = {0.0, 0.0, 0.0};
+  const double dg = std::fabs(G.diag(origin));
+  for (int i = 0; i < nb; ++i) {
+    float* fi = &f[(size_t)i * kRankFeatures];
+    double e[3] = {hi[3 * i] - lo[3 * i], hi[3 * i + 1] - lo[3 * i + 1], hi[3 * i + 2] - lo[3 * i + 2]};
+    std::sort(e, e + 3, [](double a, double b) { return a > b; });
+    for (int d = 0; d < 3; ++d) fi[d] = (float)std::log10(std::max(e[d], 1e-12));
+    fi[3] = (float)std::log2(std::max<double>(1.0, (double)(off[i + 1] - off[i])));
+    fi[4] = (float)std::log2(std::max(1, nbox[i]));
+    fi[5] = (float)std::log2(std::max(1, nnear[i]));
+    fi[6] = (float)std::log2(1.0 + nfar[i]);
+    fi[7] = nfar[i] ? (float)std::log10(std::max(dfar[i], 1e-12)) : 0.f;
+    fi[8] = (float)p.eta;
+    fi[9] = L ? (float)l / (float)L : 0.f;
+    fi[10] = (float)std::log10(p.tol);
+    fi[11] = fam_lap;
+    fi[12] = fam_yuk;
+    fi[13] = fam_gau;
+    fi[14] = (float)std::log10(std::max(lenp, 1e-30));
+    fi[15] = (float)std::log10(std::max(dg, 1e-30));
+  }
+}
+
+// A level's rank from the predictions y_i of k_i / n_i: max_i ceil(y_i n_i)
+// + 2, at least 1, at most the level's cap (max_rank, else D / 2).
+int predicted_rank(const h2_params& p, const std::vector<float>& y, const std::vector<int>& n, int D) {
+  int k = 1;
+  for (size_t i = 0; i < y.size(); ++i) {
+    const double v = std::min(1.0, std::max(0.0, (double)y[i]));
+    k = std::max(k, (int)std::ceil(v * n[i]) + 2);
+  }
+  const int cap = p.max_rank > 0 ? p.max_rank : D / 2;
+  return std::max(1, std::min(k, cap));
+}
+
+// Column-pivoted Householder QR of the m x n column-major matrix Z (in
+// place, ld m) for `steps` steps; piv[t] = original column of column t.
+void pivoted_qr_rect(std::vector<double>& Z, int m, int n, int steps, std::vector<int>& piv) {
+  piv.resize(n);
+  std::iota(piv.begin(), piv.end(), 0);
+  for (int k = 0; k < steps; ++k) {
+    int pc = k;
+    double best = -1.0;
+    for (int j = k; j < n; ++j) {
+      const double* zj = &Z[(size_t)j * m];
+      double s = 0.0;
+      for (int r = k; r < m; ++r) s += zj[r] * zj[r];
+      if (s > best) best = s, pc = j;
+    }
+    if (pc != k) {
+      std::swap_ranges(Z.begin() + (size_t)k * m, Z.begin() + (size_t)(k + 1) * m, Z.begin() + (size_t)pc * m);
+      std::swap(piv[k], piv[pc]);
+    }
+    double* zk = &Z[(size_t)k * m];
+    const double alpha = zk[k];
+    double xn2 = 0.0;
+    for (int r = k + 1; r < m; ++r) xn2 += zk[r] * zk[r];
+    if (xn2 == 0.0) continue;
+    const double beta = -std::copysign(std::sqrt(alpha * alpha + xn2), alpha);
+    const double tau = (beta - alpha) / beta, scal = 1.0 / (alpha - beta);
+    for (int r = k + 1; r < m; ++r) zk[r] *= scal;
+    zk[k] = beta;
+    for (int j = k + 1; j < n; ++j) {
+      double* zj = &Z[(size_t)j * m];
+      double w = zj[k];
+      for (int r = k + 1; r < m; ++r) w += zk[r] * zj[r];
+      w *= tau;
+      zj[k] -= w;
+      for (int r = k + 1; r < m; ++r) zj[r] -= w * zk[r];
+    }
+  }
+}
+
+using RowSink = std::function<void(double*, int)>;
+using RowsFn = std::function<bool(int, const RowSink&)>;
+
+// Randomized interpolative decomposition of box i (dimension n) at rank K:
+// Y = M_i Omega with K + 10 sketch columns and 6 probe columns (Rademacher
+// signs from splitmix64(seed, row, column)); a column-pivoted QR of the
+// sketch part of Y^T, K + 1 steps, gives the skeleton (the first K pivots)
+// and R11, R12 (written as the first K rows of Rout, n x n row-major, as the
+// plain pass leaves them).  Accepted when the sketch's (K+1)-th pivot is at
+// most tol of the first (or K is the level's cap) and the interpolation
+// error on the probe columns, ||Yq - X Yq[SK]|| / ||Yq||, is at most
+// 10 max(tol, that pivot ratio).
+bool sketch_box(const RowsFn& rows_of, int i, int n, int K, bool capped, double tol, uint64_t seed,
+                std::vector<double>& Rout, std::vector<int>& piv) {
+  const int ms = std::min(K + 10, n), q = 6, m = ms + q;
+  std::vector<double> Y((size_t)n * m, 0.0), w(m);
+  uint64_t g = 0;
+  const bool rows_ok = rows_of(i, [&](double* C, int c) {
+    for (int r = 0; r < c; ++r, ++g) {
+      for (int t0 = 0; t0 < m; t0 += 64) {
+        const uint64_t bits = splitmix64(seed ^ (g * 0x100000001B3ull + (uint64_t)t0));
+        for (int t = t0; t < std::min(m, t0 + 64); ++t) w[t] = ((bits >> (t - t0)) & 1ull) ? 1.0 : -1.0;
+      }
+      for (int a = 0; a < n; ++a) {
+        const double v = C[(size_t)a * c + r];
+        if (v == 0.0) continue;
+        double* y = &Y[(size_t)a * m];
+#pragma omp simd
+        for (int t = 0; t < m; ++t) y[t] += v * w[t];
+      }
+    }
+  });
+  if (!rows_ok) return false;
+  std::vector<double> Z((size_t)ms * n);
+  for (int j = 0; j < n; ++j)
+    for (int t = 0; t < ms; ++t) Z[(size_t)j * ms + t] = Y[(size_t)j * m + t];
+  const int steps = std::min(K + 1, std::min(ms, n));
+  pivoted_qr_rect(Z, ms, n, steps, piv);
+  const double r0 = std::fabs(Z[0]);
+  if (!(r0 > 0.0)) return false;
+  const double rho = (steps > K) ? std::fabs(Z[(size_t)K * ms + K]) / r0 : 0.0;
+  Rout.assign((size_t)n * n, 0.0);
+  for (int t = 0; t < K; ++t)
+    for (int u = t; u < n; ++u) Rout[(size_t)t * n + u] = Z[(size_t)u * ms + t];
+  // T = R11^-1 R12 and the probe error
+  const int mm = n - K;
+  std::vector<double> T((size_t)K * mm, 0.0);
+  for (int t = K - 1; t >= 0; --t) {
+    const double d = Rout[(size_t)t * n + t];
+    if (!(std::fabs(d) > 1e-15 * r0)) continue;
+    for (int b = 0; b < mm; ++b) {
+      double s = Rout[(size_t)t * n + K + b];
+      for (int u = t + 1; u < K; ++u) s -= Rout[(size_t)t * n + u] * T[(size_t)u * mm + b];
+      T[(size_t)t * mm + b] = s / d;
+    }
+  }
+  double e2 = 0.0, y2 = 0.0;
+  for (int a = 0; a < n; ++a)
+    for (int k = 0; k < q; ++k) y2 += Y[(size_t)a * m + ms + k] * Y[(size_t)a * m + ms + k];
+  for (int b = 0; b < mm; ++b)
+    for (int k = 0; k < q; ++k) {
+      double v = Y[(size_t)piv[K + b] * m + ms + k];
+      for (int u = 0; u < K; ++u) v -= T[(size_t)u * mm + b] * Y[(size_t)piv[u] * m + ms + k];
+      e2 += v * v;
+    }
+  const double e = std::sqrt(e2 / std::max(y2, 1e-300));
+  return (capped || rho <= tol) && e <= 10.0 * std::max(tol, rho);
+}
+
 }  // namespace
 
-std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& H) {
+std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& H, RankPredictor* pred,
+                       bool layout_only) {
   KernelFn G{p.kernel, p.eps, p.ell, p.diag_shift};
   H.N = N;
   H.points.assign(pts, pts + 3 * N);
@@ -256,46 +449,81 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
     Dl = std::max<int>(Dl, (int)bp[L][i].size());
   }
   H.lv[L].D = Dl;
+  RankRecord& rec = H.rec;
+  rec.feats.assign(L + 1, {});
+  rec.ranks.assign(L + 1, {});
+  rec.dims.assign(L + 1, {});
+  rec.K_pred.assign(L + 1, -1);
 
-  const int CH = 256;  // chunk rows of the streamed QR
+  // predicted layout without any compression: each level's dimension is
+  // twice the predicted rank of the level below
+  if (layout_only) {
+    if (!pred) return "layout without a predictor";
+    int nprev = 0;
+    for (int l = L; l >= 1; --l) {
+      HostLevel& hl = H.lv[l];
+      std::vector<int> nbox(hl.nb);
+      for (int i = 0; i < hl.nb; ++i) nbox[i] = (l == L) ? (int)bp[L][i].size() : 2 * nprev;
+      if (l < L) hl.D = 2 * nprev;
+      std::vector<float> f;
+      level_features(p, P, H.perm, off[l], hl, l, L, nbox, f);
+      std::vector<float> yhat;
+      if (!pred->predict(f, hl.nb, yhat)) return "rank predictor failed at level " + std::to_string(l);
+      hl.K = predicted_rank(p, yhat, nbox, hl.D);
+      rec.K_pred[l] = hl.K;
+      rec.feats[l].swap(f);
+      rec.dims[l] = nbox;
+      nprev = hl.K;
+    }
+    H.lv[0].D = L ? 2 * nprev : (int)N;
+    return "";
+  }
+
+  const int CH = 256;  // chunk rows of the streamed QR / sketch
   for (int l = L; l >= 1; --l) {
     HostLevel& hl = H.lv[l];
     int nb = hl.nb, D = hl.D;
     std::vector<std::vector<int>> nbrs(nb);
     for (size_t q = 0; q < hl.near.size() / 2; ++q) nbrs[hl.near[2 * q]].push_back(hl.near[2 * q + 1]);
-    std::vector<std::vector<double>> Rb(nb);
-    std::vector<std::vector<int>> pivs(nb);
-    std::vector<int> ranks(nb, 0);
-    int bad = -1;
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int i = 0; i < nb; ++i) {
+    std::vector<int> nbox(nb);
+    for (int i = 0; i < nb; ++i) nbox[i] = (int)bp[l][i].size();
+    std::vector<float> feats;
+    level_features(p, P, H.perm, off[l], hl, l, L, nbox, feats);
+    int cap = p.max_rank > 0 ? p.max_rank : D / 2;
+    int nmin = D;
+    for (int i = 0; i < nb; ++i) nmin = std::min<int>(nmin, (int)bp[l][i].size());
+    const int capK = std::max(1, std::min(cap, nmin));
+
+    // The rows of M_i^T (Algorithm 1): the stride-sampled far field, then
+    // G(S_C, S_C)^-1 G(S_C, B_i) for each close box j != i, in chunks of at
+    // most CH rows (c x n, column-major), handed to sink(C, c).  False if a
+    // close-field sample block is singular.
+    auto rows_of = [&](int i, const std::function<void(double*, int)>& sink) -> bool {
       const std::vector<int64_t>& Pi = bp[l][i];
-      int n = (int)Pi.size();
-      std::vector<double> R((size_t)n * n, 0.0), C((size_t)CH * n);
-      // far field: tree positions outside the near boxes, stride-sampled
+      const int n = (int)Pi.size();
+      std::vector<double> C((size_t)CH * n);
       int64_t nearcnt = 0;
       for (int j : nbrs[i]) nearcnt += off[l][j + 1] - off[l][j];
-      int64_t F = N - nearcnt;
-      int64_t s = (p.far_samples <= 0 || p.far_samples >= F) ? F : p.far_samples;
+      const int64_t F = N - nearcnt;
+      const int64_t s = (p.far_samples <= 0 || p.far_samples >= F) ? F : p.far_samples;
       for (int64_t t0 = 0; t0 < s; t0 += CH) {
-        int c = (int)std::min<int64_t>(CH, s - t0);
+        const int c = (int)std::min<int64_t>(CH, s - t0);
         for (int r = 0; r < c; ++r) {
           int64_t q = ((t0 + r) * F) / s;
           for (int j : nbrs[i]) {  // sorted intervals
             if (q < off[l][j]) break;
             q += off[l][j + 1] - off[l][j];
           }
-          int64_t pt = H.perm[q];
+          const int64_t pt = H.perm[q];
           for (int cc = 0; cc < n; ++cc) C[(size_t)cc * c + r] = G.entry(P, pt, Pi[cc], false);
         }
-        tsqr_update(R.data(), n, C.data(), c);
+        sink(C.data(), c);
       }
-      // close field: G(S_C, S_C)^-1 G(S_C, B_i) for each close j != i
       for (int j : nbrs[i]) {
         if (j == i) continue;
         const std::vector<int64_t>& Pj = bp[l][j];
-        int nj = (int)Pj.size();
-        int sc = (p.near_samples <= 0 || p.near_samples >= nj) ? nj : p.near_samples;
+        const int nj = (int)Pj.size();
+        const int sc = (p.near_samples <= 0 || p.near_samples >= nj) ? nj : p.near_samples;
         std::vector<int64_t> SC(sc);
         for (int t = 0; t < sc; ++t) SC[t] = Pj[((int64_t)t * nj) / sc];
         std::vector<double> Acc((size_t)sc * sc), B((size_t)sc * n);
@@ -303,33 +531,81 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
           for (int b = 0; b < sc; ++b) Acc[(size_t)a * sc + b] = G.entry(P, SC[a], SC[b], a == b);
         for (int cc = 0; cc < n; ++cc)
           for (int a = 0; a < sc; ++a) B[(size_t)cc * sc + a] = G.entry(P, SC[a], Pi[cc], false);
-        if (!lu_solve_cols(Acc.data(), sc, B.data(), n)) {
+        if (!lu_solve_cols(Acc.data(), sc, B.data(), n)) return false;
+        sink(B.data(), sc);
+      }
+      return true;
+    };
+
+    std::vector<std::vector<double>> Rb(nb);
+    std::vector<std::vector<int>> pivs(nb);
+    std::vector<int> ranks(nb, 0);
+    int bad = -1;
+    // the plain rank-revealing pass of one box: streamed QR of M_i^T, then a
+    // column-pivoted QR of its triangle; ranks[i] = #{|R_tt| > tol |R_11|}
+    auto plain_box = [&](int i) {
+      const int n = (int)bp[l][i].size();
+      std::vector<double> R((size_t)n * n, 0.0);
+      if (!rows_of(i, [&](double* C, int c) { tsqr_update(R.data(), n, C, c); })) {
 #pragma omp critical
-          bad = i;
-          continue;
-        }
-        tsqr_update(R.data(), n, B.data(), sc);
+        bad = i;
+        return;
       }
       std::vector<int> piv;
       pivoted_qr(R.data(), n, piv);
-      double r0 = n ? std::fabs(R[0]) : 0.0;
+      const double r0 = n ? std::fabs(R[0]) : 0.0;
       int k = 0;
       if (r0 > 0)
         for (int t = 0; t < n; ++t) k += std::fabs(R[(size_t)t * n + t]) > p.tol * r0;
       ranks[i] = k;
       Rb[i].swap(R);
       pivs[i].swap(piv);
+    };
+
+    auto t0 = std::chrono::steady_clock::now();
+    int K = 0;
+    bool done = false;
+    if (pred) {
+      std::vector<float> yhat;
+      if (!pred->predict(feats, nb, yhat)) return "rank predictor failed at level " + std::to_string(l);
+      K = std::min(predicted_rank(p, yhat, nbox, D), capK);
+      rec.K_pred[l] = K;
+      std::vector<char> ok(nb, 0);
+      const uint64_t lseed = splitmix64(0x5eedull + (uint64_t)l);
+#pragma omp parallel for schedule(dynamic, 1)
+      for (int i = 0; i < nb; ++i) {
+        ranks[i] = -1;
+        ok[i] = sketch_box(rows_of, i, (int)bp[l][i].size(), K, K >= capK, p.tol, splitmix64(lseed ^ (uint64_t)i),
+                           Rb[i], pivs[i]);
+      }
+      if (bad >= 0)
+        return "singular close-field sample block at level " + std::to_string(l) + " box " + std::to_string(bad);
+      int need = K;
+#pragma omp parallel for schedule(dynamic, 1) reduction(max : need)
+      for (int i = 0; i < nb; ++i) {
+        if (ok[i]) continue;
+        plain_box(i);
+        need = std::max(need, std::min(ranks[i], capK));
+      }
+      for (int i = 0; i < nb; ++i) rec.fallback_boxes += !ok[i];
+      done = need <= K;
+      if (!done) ++rec.fallback_levels;
     }
+    if (!done) {
+#pragma omp parallel for schedule(dynamic, 1)
+      for (int i = 0; i < nb; ++i) plain_box(i);
+      int kmax = *std::max_element(ranks.begin(), ranks.end());
+      K = std::max(1, std::min(kmax, capK));
+    }
+    rec.compress_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (bad >= 0)
       return "singular close-field sample block at level " + std::to_string(l) + " box " + std::to_string(bad);
-    int kmax = *std::max_element(ranks.begin(), ranks.end());
-    int cap = p.max_rank > 0 ? p.max_rank : D / 2;
-    int nmin = D;
-    for (int i = 0; i < nb; ++i) nmin = std::min<int>(nmin, (int)bp[l][i].size());
-    int K = std::max(1, std::min(std::min(kmax, cap), nmin));
     if (nmin == 0) K = 0;
     hl.K = K;
     if (l == L) H.ranks_leaf = ranks;
+    rec.feats[l].swap(feats);
+    rec.ranks[l] = ranks;
+    rec.dims[l] = nbox;
     hl.X.assign((size_t)nb * D * K, 0.0);
     hl.SK.assign((size_t)nb * K, 0);
     bp[l - 1].resize(nb / 2);

@@ -35,6 +35,11 @@ void launch_form_u(int64_t nb, int D, int K, const float* W1, const float* V, fl
 template <typename T>
 void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_idx, double* lu, T* luT,
                        int32_t* piv, T* Ainv, int32_t* status, int level, cudaStream_t st);
+// the FP16/BF16 factorizations' a3 in FP64: FP32 blocks in, FP64 LU and
+// inverse (scratch lu, inv: nb * R * R each), FP32 inverse out
+void launch_lu_inverse_f64_for_f32(int nb, int D, int R, const float* Ablk, const int32_t* diag_idx, double* lu,
+                                   double* inv, int32_t* piv, float* Ainv, int32_t* status, int level,
+                                   cudaStream_t st);
 template <typename T>
 void launch_merge(int D, int K, int64_t NP, const T* Ahat, const int32_t* ni, const int32_t* nj,
                   const int32_t* ndst, int64_t FP, const T* Shat, const int32_t* fi, const int32_t* fj,
@@ -56,6 +61,9 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
 // shared memory).  False if the driver or the shape does not allow it.
 bool make_tile_map(CUtensorMap* tm, const void* base, int bf16, uint64_t rows, uint64_t cols, uint64_t ld,
                    uint32_t box_rows, uint32_t box_cols);
+// One CTA whose thread 0 waits (bounded by timeout_ns) on an mbarrier that
+// nothing completes, then sets *flag = 1: the self-test of the bounded waits.
+void launch_wait_selftest(unsigned long long timeout_ns, int32_t* flag, cudaStream_t st);
 template <typename S>
 void launch_amax_blocks(const S* base, int64_t nblk, int64_t stride, int rows, int cols, int ld, unsigned int* out,
                         cudaStream_t st, const int32_t* idx = nullptr);  // idx: block q is base + idx[q] stride
@@ -104,6 +112,8 @@ void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const 
                  cudaStream_t st);
 template <typename T>
 void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st);
+template <typename T>
+void launch_transpose_pairs(int D, int64_t n, const int32_t* dst, const int32_t* src, T* A, cudaStream_t st);
 template <typename T>
 void launch_transpose_blocks(int64_t nb, int D, const T* in, T* out, cudaStream_t st);  // out_b = in_b^T (D x D)  // y = M x, M n x n row-major
 

@@ -533,11 +533,13 @@ __global__ void __launch_bounds__(512) qr_panel_kernel(int D, int K, const T* __
 // product over c in [r, i) (Tw is upper triangular).
 template <typename T>
 __global__ void __launch_bounds__(256) wy_tfactor_kernel(int K, const T* __restrict__ S, const T* __restrict__ tau,
-                                                         T* __restrict__ Tw) {
+                                                         T* __restrict__ Tw, int use_smem) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* Ts = reinterpret_cast<T*>(smraw);  // K x K row-major
-  T* w = Ts + K * K;                    // K
   const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // K x K row-major working triangle: shared memory when it fits, else the
+  // output block itself; w (K entries) always in shared memory
+  T* Ts = use_smem ? reinterpret_cast<T*>(smraw) : Tw + (size_t)box * K * K;
+  T* w = use_smem ? Ts + K * K : reinterpret_cast<T*>(smraw);
   const T* Sb = S + (size_t)box * K * K;
   const T* tb = tau + (size_t)box * K;
   for (int e = tid; e < K * K; e += blockDim.x) Ts[e] = T(0);
@@ -556,7 +558,8 @@ __global__ void __launch_bounds__(256) wy_tfactor_kernel(int K, const T* __restr
     __syncthreads();
   }
   T* out = Tw + (size_t)box * K * K;
-  for (int e = tid; e < K * K; e += blockDim.x) out[e] = Ts[e];
+  if (use_smem)
+    for (int e = tid; e < K * K; e += blockDim.x) out[e] = Ts[e];
 }
 
 // C[r0.., c0..] = alpha A B for the 4 x 4 tile at (r0, c0) of an h x h
@@ -928,10 +931,12 @@ void launch_wy_tfactor(int nb, int K, const T* S, const T* tau, T* Tw, cudaStrea
     wy_tinv_kernel<T><<<nb, 256, sm, st>>>(K, Kp, S, tau, Tw);
     return;
   }
-  const size_t sm = sizeof(T) * ((size_t)K * K + K);
+  size_t sm = sizeof(T) * ((size_t)K * K + K);
+  const int use = sm <= 200 * 1024;
+  if (!use) sm = sizeof(T) * (size_t)K;
   if (sm > 48 * 1024) cudaFuncSetAttribute(wy_tfactor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ++g_launches;
-  wy_tfactor_kernel<T><<<nb, 256, sm, st>>>(K, S, tau, Tw);
+  wy_tfactor_kernel<T><<<nb, 256, sm, st>>>(K, S, tau, Tw, use);
 }
 template <typename T>
 void launch_perm_identity(int nb, int D, int K, T* U, cudaStream_t st) {
@@ -958,22 +963,23 @@ H2_INST_QR(float)
 // A zero pivot records (level, box) in status[0..1]; the rest of that box's
 // factorization is then undefined.
 // ------------------------------------------------------------------------
-template <typename T>
+// (TI: the type Ablk is stored in; the factorization runs in T)
+template <typename T, typename TI = T>
 __global__ void __launch_bounds__(256)
-lu_factor_kernel(int D, int R, const T* __restrict__ Ablk, const int32_t* __restrict__ diag_idx,
+lu_factor_kernel(int D, int R, const TI* __restrict__ Ablk, const int32_t* __restrict__ diag_idx,
                  T* __restrict__ luT, int32_t* __restrict__ piv, int32_t* __restrict__ status, int level,
                  int use_smem) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ int s_p;
   __shared__ T s_inv;
   const int box = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const T* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
+  const TI* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
   T* G = luT + (size_t)box * R * R;
   T* M = use_smem ? reinterpret_cast<T*>(sm_raw) : G;
   const int ld = use_smem ? R + 1 : R;
   int32_t* pv = piv + (size_t)box * R;
   for (int r = warp; r < R; r += 8)
-    for (int c = lane; c < R; c += 32) M[c * ld + r] = A[(size_t)r * D + c];
+    for (int c = lane; c < R; c += 32) M[c * ld + r] = static_cast<T>(A[(size_t)r * D + c]);
   __syncthreads();
   int bad = 0;
   for (int k = 0; k < R; ++k) {
@@ -1603,6 +1609,187 @@ void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_
   ++g_launches;
   lu_inverse_kernel<T><<<nb, 256, sm, st>>>(R, luT, piv, Ainv, mode);
 }
+// ------------------------------------------------------------------------
+// a3 in FP64 for R <= 128: in-place Gauss-Jordan inversion with partial
+// pivoting, the matrix in registers.  The R x R block (identity-padded to
+// 128 x 128) is spread over 16 x 16 threads; thread (ty, tx) owns rows
+// 8 ty .. 8 ty + 7 and columns 8 tx .. 8 tx + 7.  Step k:
+//   (a) the owners of column k publish it (f_i = a_ik) and the owners of
+//       row k publish that row; barrier;
+//   (b) warp 0 picks the pivot row p >= k of largest |a_pk| (the first on
+//       ties: LAPACK's choice, which Gauss-Jordan shares with LU because the
+//       entries below the diagonal are those of the Schur complement);
+//       barrier;
+//   (c) the owners of row p publish the scaled pivot row
+//       w_j = a_pj / a_pk (j != k), w_k = 1 / a_pk; barrier;
+//   (d) rows k and p trade places and every row i != k becomes
+//       a_ij - f_i w_j (with a_ik read as 0); row k becomes w.
+// After step R-1 the array holds (P A)^-1 = A^-1 P^T; the interchanges
+// applied to the columns in reverse order give A^-1, which is written in
+// FP32 (one rounding).  Work: R^3 FP64 multiply-adds, bound by the FP64
+// pipe; three barriers per step.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 1) gj64_reg_kernel(int D, int R, const float* __restrict__ Ablk,
+                                                          const int32_t* __restrict__ diag_idx,
+                                                          float* __restrict__ Ainv, int32_t* __restrict__ piv,
+                                                          int32_t* __restrict__ status, int level) {
+  __shared__ double colk[2][128], oldk[2][128], rowk[2][128];
+  __shared__ int s_p[2], s_bad;
+  __shared__ int src[128], dst[128], pv[128];
+  const int box = blockIdx.x, tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
+  double a[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = ty * 8 + r;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = tx * 8 + c;
+      a[r][c] = (i < R && j < R) ? (double)__ldg(A + (size_t)i * D + j) : (i == j ? 1.0 : 0.0);
+    }
+  }
+  if (tid == 0) s_bad = 0;
+  for (int k = 0; k < R; ++k) {
+    const int b = k & 1;
+    const int kt = k >> 3, kc = k & 7;
+    // (a) column k and row k
+    if (tx == kt) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        double v = 0.0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v = (c == kc) ? a[r][c] : v;
+        colk[b][ty * 8 + r] = v;
+      }
+    }
+    if (ty == kt) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r == kc) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) oldk[b][tx * 8 + c] = a[r][c];
+        }
+    }
+    __syncthreads();
+    // (b) pivot row
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + tid; i < R; i += 32) {
+        const double v = fabs(colk[b][i]);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) {
+        s_p[b] = bi;
+        pv[k] = bi;
+        if (!(best > 0.0)) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int p = s_p[b];
+    const double dinv = 1.0 / colk[b][p];
+    // (c) scaled pivot row
+    if (ty == (p >> 3)) {
+      const int pr = p & 7;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r == pr) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int j = tx * 8 + c;
+            rowk[b][j] = (j == k) ? dinv : a[r][c] * dinv;
+          }
+        }
+    }
+    __syncthreads();
+    // (d) swap rows k and p, eliminate column k from every other row
+    double w[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) w[c] = rowk[b][tx * 8 + c];
+    const double fk = colk[b][k];  // row k's entry, which moves to row p
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int i = ty * 8 + r;
+      if (i == k) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) a[r][c] = w[c];
+      } else {
+        const bool isp = (i == p);
+        const double f = isp ? fk : colk[b][i];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int j = tx * 8 + c;
+          const double base = isp ? oldk[b][j] : a[r][c];
+          a[r][c] = fma(-f, w[c], (j == k) ? 0.0 : base);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_bad) {
+    if (tid == 0 && atomicCAS(status, 0, level + 1) == 0) status[1] = box;
+    return;
+  }
+  // column unscramble: A^-1[:, j] = X[:, src[j]] after the swaps k = R-1 .. 0
+  if (tid == 0) {
+    for (int j = 0; j < R; ++j) src[j] = j;
+    for (int k = R - 1; k >= 0; --k) {
+      const int t = src[k];
+      src[k] = src[pv[k]];
+      src[pv[k]] = t;
+    }
+    for (int j = 0; j < R; ++j) dst[src[j]] = j;
+  }
+  __syncthreads();
+  for (int k = tid; k < R; k += 256) piv[(size_t)box * R + k] = pv[k];
+  float* Y = Ainv + (size_t)box * R * R;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = ty * 8 + r;
+    if (i >= R) continue;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = tx * 8 + c;
+      if (j < R) Y[(size_t)i * R + dst[j]] = (float)a[r][c];
+    }
+  }
+}
+
+// a3 for the FP16/BF16 factorizations with FP64 arithmetic: the FP32
+// Ahat_ii^RR are widened as they are read and inverted in FP64, and the
+// inverse is rounded once to FP32 (Ainv); the pivots are LAPACK's.  R <= 128:
+// the register Gauss-Jordan kernel above; larger R: the FP64 getf2 kernel
+// (lu, nb * R * R FP64 scratch) and the FP64 inverse (inv, the same size).
+void launch_lu_inverse_f64_for_f32(int nb, int D, int R, const float* Ablk, const int32_t* diag_idx, double* lu,
+                                   double* inv, int32_t* piv, float* Ainv, int32_t* status, int level,
+                                   cudaStream_t st) {
+  if (nb == 0 || R == 0 || R > 1024) return;
+  if (R <= 128) {
+    ++g_launches;
+    gj64_reg_kernel<<<nb, 256, 0, st>>>(D, R, Ablk, diag_idx, Ainv, piv, status, level);
+    return;
+  }
+  const size_t cap = 220 * 1024;
+  const size_t sm1 = sizeof(double) * (size_t)R * (R + 1);
+  const int use = sm1 <= cap;
+  if (use) cudaFuncSetAttribute(lu_factor_kernel<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  ++g_launches;
+  lu_factor_kernel<double, float><<<nb, 256, use ? sm1 : 0, st>>>(D, R, Ablk, diag_idx, lu, piv, status, level, use);
+  const size_t f = sizeof(double) * (size_t)R * (R + 1), y = sizeof(double) * (size_t)R * R;
+  const int mode = (f + y <= cap) ? 2 : (f <= cap ? 1 : 0);
+  const size_t sm = mode == 2 ? f + y : (mode == 1 ? f : 0);
+  if (sm) cudaFuncSetAttribute(lu_inverse_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  ++g_launches;
+  lu_inverse_kernel<double><<<nb, 256, sm, st>>>(R, lu, piv, inv, mode);
+  launch_convert<double, float>(inv, Ainv, (int64_t)nb * R * R, st);
+}
+
 template void launch_lu_inverse<double>(int, int, int, const double*, const int32_t*, double*, double*, int32_t*,
                                         double*, int32_t*, int, cudaStream_t);
 template void launch_lu_inverse<float>(int, int, int, const float*, const int32_t*, double*, float*, int32_t*,

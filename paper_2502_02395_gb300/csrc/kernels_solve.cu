@@ -1030,6 +1030,36 @@ void launch_transpose_blocks(int64_t nb, int D, const T* in, T* out, cudaStream_
   transpose_blocks_kernel<T><<<grid, dim3(32, 8), 0, st>>>(D, in, out);
 }
 
+// A[dst[k]] = A[src[k]]^T for D x D blocks of one array (the lower near
+// pairs of a symmetric level from their mirrors); blocks by z, grid-strided.
+template <typename T>
+__global__ void transpose_pairs_kernel(int D, int64_t n, const int32_t* __restrict__ dsti,
+                                       const int32_t* __restrict__ srci, T* __restrict__ A) {
+  __shared__ T tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int64_t k = blockIdx.z; k < n; k += gridDim.z) {
+    const T* src = A + (int64_t)srci[k] * D * D;
+    T* dst = A + (int64_t)dsti[k] * D * D;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+      const int r = by + y, c = bx + threadIdx.x;
+      if (r < D && c < D) tile[y][threadIdx.x] = src[(int64_t)r * D + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+      const int r = bx + y, c = by + threadIdx.x;
+      if (r < D && c < D) dst[(int64_t)r * D + c] = tile[threadIdx.x][y];
+    }
+    __syncthreads();
+  }
+}
+template <typename T>
+void launch_transpose_pairs(int D, int64_t n, const int32_t* dst, const int32_t* src, T* A, cudaStream_t st) {
+  if (n == 0 || D == 0) return;
+  ++g_launches;
+  dim3 grid((D + 31) / 32, (D + 31) / 32, (unsigned)std::min<int64_t>(n, 65535));
+  transpose_pairs_kernel<T><<<grid, dim3(32, 8), 0, st>>>(D, n, dst, src, A);
+}
+
 static void set_smem(const void* f, size_t sm) {
   if (sm > 48 * 1024) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
@@ -1180,6 +1210,7 @@ void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st) {
 #define H2_INST_SOLVE(T)                                                                     \
   template void launch_fwd1<T>(const DevLevel&, const FacLevel<T>&, const ChildIn<T>&, cudaStream_t); \
   template void launch_transpose_blocks<T>(int64_t, int, const T*, T*, cudaStream_t);         \
+  template void launch_transpose_pairs<T>(int, int64_t, const int32_t*, const int32_t*, T*, cudaStream_t); \
   template void launch_gemv_rows<T>(int, const T*, const T*, T*, cudaStream_t);
 H2_INST_SOLVE(double)
 H2_INST_SOLVE(float)

@@ -376,6 +376,29 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
 }
 
 // ------------------------------------------------------------------------
+// self-test of the bounded waits: an mbarrier that expects one arrival which
+// never comes.  Thread 0 waits with the same helper the TMA kernels use; when
+// the wait gives up it records the failure in *flag (as those kernels record
+// theirs in the context's status word) and the CTA returns.  Nothing else
+// touches global memory.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) wait_selftest_kernel(unsigned long long timeout_ns, int32_t* flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  if (threadIdx.x == 0 && !h2::mbar_wait(&bar, 0, timeout_ns)) atomicExch(flag, 1);
+  __syncwarp();
+}
+
+void launch_wait_selftest(unsigned long long timeout_ns, int32_t* flag, cudaStream_t st) {
+  ++g_launches;
+  wait_selftest_kernel<<<1, 32, 0, st>>>(timeout_ns, flag);
+}
+
+// ------------------------------------------------------------------------
 // operand preparation
 // ------------------------------------------------------------------------
 // amax[0] = max |x| over nblk strided sub-blocks: block q holds rows x cols

@@ -101,3 +101,23 @@ def test_single_box_plan(B):
     P = W.cube_points(40, 2)
     plan = B.h2_plan(B.make_params("laplace_eps", leaf=64), P)
     assert plan["L"] == 0 and plan["levels"][0]["D"] == 40
+
+
+def test_memory_limit_gives_oom_before_any_launch(B):
+    """h2_set_memory_limit: an instance whose device arrays exceed the cap is
+    refused with H2_ERR_OOM after the host construction and before any CUDA
+    call (so this runs on a machine without a GPU); the message names the
+    bytes needed and the cap."""
+    P = W.cube_points(2048, 3)
+    prm = B.make_params("laplace_eps", leaf=64, tol=1e-6, far_samples=256, near_samples=32)
+    plan = B.h2_plan(prm, P)
+    B.h2_set_memory_limit(1 << 20)
+    try:
+        with pytest.raises(B.H2Error) as e:
+            B.h2_build(prm, P)
+        assert e.value.status == -2
+        assert "memory limit is 1048576" in e.value.message
+        need = float(e.value.message.split("about ")[1].split(" ")[0])
+        assert need >= plan["device_bytes_build"]
+    finally:
+        B.h2_set_memory_limit(0)

@@ -52,3 +52,152 @@ def test_oracle_parameter_layout():
     assert mlp.N_PARAMS == 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
     assert p["W1"][1, 0] == 16 and p["b1"][0] == 1024 and p["b3"][0] == mlp.N_PARAMS - 1
     assert np.array_equal(mlp.pack(p), np.arange(mlp.N_PARAMS))
+
+
+# ---------------------------------------------------------------- GPU ---
+def _bf16(a):
+    """Round float32 values to the nearest BF16 (ties to even), as floats."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_02395_gb300 import build as bld
+    bld.build()
+    from paper_2502_02395_gb300 import binding
+    return binding
+
+
+GROUPS = (("W1", 0, 1024), ("b1", 1024, 1088), ("W2", 1088, 5184), ("b2", 5184, 5248), ("w3", 5248, 5312),
+          ("b3", 5312, 5313))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("seed", [11, 12])
+def test_gpu_gradient_matches_oracle(B, seed):
+    """The training kernels' loss and gradient against the oracle's FP64
+    chain rule on the same BF16-valued weights and inputs.  The kernels
+    round the hidden activations to BF16 (unit roundoff 2^-9) and sum in
+    FP32, so each parameter group agrees to a few 2^-9 in relative norm;
+    the bound is 2^-5."""
+    rng = np.random.default_rng(seed)
+    theta = _bf16(rng.normal(0.0, 0.25, mlp.N_PARAMS))
+    X = _bf16(rng.normal(0.0, 1.0, (300, mlp.N_IN)))
+    y = rng.uniform(0.0, 1.0, 300).astype(np.float32)
+    m = B.h2_rank_model_create(1)
+    try:
+        B.h2_rank_model_set_weights(m, theta)
+        loss, g = B.h2_rank_model_grad(m, X, y)
+    finally:
+        B.h2_rank_model_destroy(m)
+    loss_ref, g_ref = mlp.loss_and_grad(theta.astype(np.float64), X.astype(np.float64), y.astype(np.float64))
+    assert abs(loss - loss_ref) <= 2.0 ** -7 * loss_ref
+    for name, a, b in GROUPS:
+        e = np.linalg.norm(g[a:b] - g_ref[a:b]) / np.linalg.norm(g_ref[a:b])
+        print(f"seed {seed} {name}: relative gradient error {e:.2e}")
+        assert e <= 2.0 ** -5, (name, e)
+
+
+def _training_set(B):
+    """Ranks of the plain compression on the shapes of the three solver
+    workloads (cube 2048 / 1/(r+1e-3) / leaf 64; sphere / 1/(r+1e-3) /
+    leaf 256; cube / Yukawa + 1 / leaf 256), at several tolerances."""
+    import workloads as W
+    sets = []
+    for tol in (1e-4, 1e-6, 1e-8, 1e-10):
+        sets.append((W.cube_points(2048, 1), dict(kernel="laplace_eps", leaf=64, tol=tol)))
+    for tol in (1e-6, 1e-8):
+        sets.append((W.sphere_points(16384, 3), dict(kernel="laplace_eps", leaf=256, tol=tol)))
+    for tol in (1e-8, 1e-10):
+        sets.append((W.cube_points(16384, 5), dict(kernel="yukawa_eps", leaf=256, tol=tol, diag_shift=1.0)))
+    F, Y = [], []
+    for pts, kw in sets:
+        f, y, _ = B.h2_rank_data(B.make_params(far_samples=512, near_samples=64, **kw), pts)
+        F.append(f)
+        Y.append(y)
+    return np.concatenate(F), np.concatenate(Y)
+
+
+@pytest.fixture(scope="module")
+def trained(B):
+    F, Y = _training_set(B)
+    m = B.h2_rank_model_create(7)
+    loss0 = float(np.mean((B.h2_rank_model_predict(m, F) - Y) ** 2))
+    loss = B.h2_rank_model_train(m, F, Y, steps=1500, lr=3e-3)
+    yield m, F, Y, loss0, loss
+    B.h2_rank_model_destroy(m)
+
+
+@pytest.mark.gpu
+def test_gpu_training_fits_the_plain_ranks(B, trained):
+    """Full-batch Adam on the GPU drives the loss down and the trained
+    network reproduces the training ranks k / n to a few percent."""
+    m, F, Y, loss0, loss = trained
+    pred = B.h2_rank_model_predict(m, F)
+    mae = float(np.mean(np.abs(pred - Y)))
+    print(f"training loss {loss0:.3e} -> {loss:.3e}, mean |k/n error| {mae:.3f} on {len(Y)} boxes")
+    assert loss <= 0.1 * loss0
+    assert mae <= 0.05
+
+
+@pytest.mark.gpu
+def test_gpu_predicted_layout_and_build_gain(B, trained):
+    """What the trained network gains over the method without it, on a
+    held-out problem shaped like the large workload (cube, 1/(r+1e-3),
+    leaf 256, tol 1e-8): (1) the whole batch layout (every level's rank)
+    comes from features and one inference per level, with no compression
+    pass, and matches the plain build's ranks; (2) h2_build_predicted
+    compresses with sketches sized by those ranks, faster than the plain
+    rank-revealing pass, with few plain fallbacks; (3) the resulting H^2
+    matrix is as accurate: against exactly evaluated rows of A, and the
+    refined solve reaches 1e-10."""
+    import time
+
+    import workloads as W
+    from oracle.kernels import Kernel
+    m = trained[0]
+    n = 65536
+    P = W.cube_points(n, 71)
+    kw = dict(kernel="laplace_eps", leaf=256, tol=1e-8, far_samples=1024, near_samples=64)
+    prm = B.make_params(**kw)
+    t0 = time.perf_counter()
+    plan = B.h2_plan(prm, P)
+    t_plan = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lay = B.h2_plan_predicted(prm, P, m)
+    t_lay = time.perf_counter() - t0
+    K_plain = [lv["K"] for lv in plan["levels"]]
+    K_lay = [lv["K"] for lv in lay["levels"]]
+    print(f"layout: plain pass {t_plan:.2f} s (compression {plan['compress_s']:.2f} s), predicted {t_lay:.3f} s; "
+          f"K plain {K_plain}, predicted {K_lay}")
+    assert all(abs(a - b) <= max(4, 0.05 * a) for a, b in zip(K_plain, K_lay))
+    assert t_lay <= 0.2 * t_plan
+
+    S0 = B.H2Solver.build(P, **kw)
+    Sp = B.H2Solver.build_predicted(P, m, **kw)
+    c0, cp = S0.stats()["construction"], Sp.stats()["construction"]
+    print(f"compression: plain {c0['compress_s']:.2f} s, predicted {cp['compress_s']:.2f} s; "
+          f"fallback boxes {cp['fallback_boxes']}, levels {cp['fallback_levels']}; K {cp['K']}")
+    assert cp["compress_s"] <= 0.8 * c0["compress_s"]
+    assert cp["fallback_levels"] == 0
+    # accuracy of A_H2 against exact rows of A (256 sampled rows)
+    rng = np.random.default_rng(3)
+    rows = rng.choice(n, 256, replace=False)
+    x = W.uniform_rhs(n, 72)
+    exact = Kernel("laplace_eps").matrix(P, rows, np.arange(n)) @ x
+    e0 = np.linalg.norm(S0.matvec(x)[rows] - exact) / np.linalg.norm(exact)
+    ep = np.linalg.norm(Sp.matvec(x)[rows] - exact) / np.linalg.norm(exact)
+    print(f"sampled-row error of A_H2: plain {e0:.2e}, predicted {ep:.2e}")
+    assert ep <= max(2 * e0, 1e-8)
+    for S in (S0, Sp):
+        S.factor("fp16")
+        _, rel, its = S.solve(W.uniform_rhs(n, 73), target=1e-10, max_iters=100)
+        assert rel <= 1e-10
+    S0.close()
+    Sp.close()

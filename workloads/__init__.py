@@ -100,6 +100,10 @@ WORKLOADS = {
     # 65536 points on the unit sphere, 1/(r+1e-3), leaf 256, tol 1e-8, FP64.
     "sphere65536_laplace": Workload("sphere65536_laplace", 65536, "sphere", 3, 4,
                                     "laplace_eps", 256, 1.0, 1e-8),
+    # An eighth-size version of the next one: small-case profiler captures
+    # (a few GB on the device, leaf blocks still larger than L2).
+    "cube32768_yukawa": Workload("cube32768_yukawa", 32768, "cube", 5, 6,
+                                 "yukawa_eps", 256, 1.0, 1e-10, diag_shift=1.0),
     # A quarter-size version of the next one (profiling captures).
     "cube65536_yukawa": Workload("cube65536_yukawa", 65536, "cube", 5, 6,
                                  "yukawa_eps", 256, 1.0, 1e-10, diag_shift=1.0),
