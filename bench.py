@@ -61,6 +61,11 @@ def parse():
                     help="arithmetic of the LU / inverse of Ahat_ii^RR in FP16/BF16 factorizations")
     ap.add_argument("--residual", default="pair", choices=["pair", "fp64"],
                     help="arithmetic of the mixed refinement's residual: FP32 pairs or FP64 instructions")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead of the single-system step: a batch of this many Gaussian-covariance systems of "
+                         "uneven size (workloads.batch_systems), factored and solved concurrently")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay the FP32 substitution as a CUDA graph (1) or launch it kernel by kernel (0)")
     return ap.parse_args()
 
 
@@ -198,10 +203,13 @@ def fp64_peak_tflops() -> float:
 
 
 # DRAM traffic of one launch of the FP32 matvec's leaf kernel (the step's
-# largest kernel: the symmetric-storage pair kernel) from an ncu capture of
-# this bench's workload, valid while the kernel's source is the one captured
-# (digest of its text below).
-LEAF_TRAFFIC = {"digest": "1381b342a0b471df", "bytes_per_launch": 3.38e9 + 27.41e6,
+# largest kernel: the symmetric-storage pair kernel), valid while the
+# kernel's source is the one captured (digest of its text below).  Captured
+# on the small case cube32768_yukawa (1323 stored pairs: 347.00 MB read +
+# 4.45 MB written in one launch) and scaled to the 12875 stored pairs of
+# cube262144_yukawa: the kernel reads each stored 256 x 256 block once, so
+# its traffic grows with the stored pairs.
+LEAF_TRAFFIC = {"digest": "1381b342a0b471df", "bytes_per_launch": (347.004160e6 + 4.454144e6) * 12875 / 1323,
                 "profile": "profiles/mv_sym_pair_kernel_cube262144_yukawa.md"}
 
 
@@ -277,8 +285,54 @@ def roofline_for(phase, stats, t_phase, calls, peaks, prec, tc, fp64_tf):
             "traffic": None, "phase": phase, "peak_source": src}
 
 
+def run_batch(args):
+    """--batch S: S independent Gaussian-covariance systems (N log-uniform
+    in [4096, 65536], l in [0.05, 0.5], leaf 128 / 256, tol 1e-8), FP16
+    factorizations refined to --target, run by the library's worker pool
+    with the worker count its tuner picks; one JSON line."""
+    import torch
+    import workloads as W
+    from paper_2502_02395_gb300 import build as bld
+    bld.build()
+    from paper_2502_02395_gb300 import H2Solver
+    from paper_2502_02395_gb300.binding import H2Batch
+    specs = W.batch_systems(count=args.batch)
+    t0 = time.perf_counter()
+    solvers, rhs = [], []
+    for sp in specs:
+        P = W.cube_points(sp["n"], sp["point_seed"])
+        solvers.append(H2Solver.build(P, kernel="gaussian", ell=sp["ell"], diag_shift=0.01, leaf=sp["leaf"], eta=1.0,
+                                      tol=1e-8, far_samples=1024, near_samples=64))
+        rhs.append(torch.from_numpy(W.uniform_rhs(sp["n"], sp["rhs_seed"])).cuda())
+    build_s = time.perf_counter() - t0
+    batch = H2Batch(solvers)
+    workers = batch.tune(args.prec, rhs, target=args.target, max_iters=200)
+    tune = batch.stats()["tune_seconds"]
+    times, its_all = [], None
+    for k in range(args.warmup + args.steps):
+        _, rel, its, sec = batch.run(args.prec, rhs, target=args.target, max_iters=200)
+        if k >= args.warmup:
+            times.append(sec)
+            its_all = its
+    value = float(np.mean(times))
+    line = {"metric": f"factor+solve s for {args.batch} independent Gaussian-covariance systems to {args.target:g}",
+            "value": value, "unit": "s", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+            "workers": workers, "tune_seconds_by_workers": tune, "sequential_s": tune.get("1"),
+            "speedup_vs_one_worker": (tune.get("1") / value) if tune.get("1") else None,
+            "total_N": int(sum(s["n"] for s in specs)), "N": [s["n"] for s in specs],
+            "iters": its_all, "build_s": build_s, "dtype": {"fp16": "f16/f32/f64", "bf16": "bf16/f32/f64"}.get(
+                args.prec, "f64"), "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for S in solvers:
+        S.close()
+
+
 def main():
     args = parse()
+    if args.batch > 0:
+        run_batch(args)
+        return
     import workloads as W
     wl = W.workload(args.workload)
     rank = int(os.environ.get("RANK", "0"))
@@ -318,6 +372,7 @@ def main():
     S.set_stream(stream)
     S.set_option("rr_lu_fp64", 1 if args.rr_lu == "fp64" else 0)
     S.set_option("residual_fp64", 1 if args.residual == "fp64" else 0)
+    S.set_option("graphs", args.graphs)
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.zeros_like(b_dev)
     torch.cuda.synchronize()
@@ -439,7 +494,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "no flush: inputs (13 GB leaf blocks, factors) exceed L2"},
         "relres": float(np.max(rels)), "relres_fp64_matvec": r_check, "iters": int(np.max(its_all)),
-        "rr_lu": args.rr_lu, "residual": args.residual,
+        "rr_lu": args.rr_lu, "residual": args.residual, "graphs": args.graphs,
         "phases_s": ph, "build_s": build_s, "fp64": fp64,
         "speedup_vs_fp64": (fp64["s_per_step"] / value) if fp64 else None,
         "roofline": roof, "rooflines": roofs, "fp64_peak_tflops": fp64_tf, "calls": calls,

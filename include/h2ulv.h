@@ -259,7 +259,7 @@ h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart);
  * large), H2_ERR_CUDA. */
 h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
 
-/* Options of a context (h2_set_option).  Both apply to the next
+/* Options of a context (h2_set_option).  They apply to the next
  * h2_factor / h2_solve.
  *   H2_OPT_RR_LU_FP64     FP16/BF16 factorizations: 0 (default) inverts
  *                         Ahat_ii^RR (and the root block) by Gauss-Jordan
@@ -269,8 +269,14 @@ h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
  *                         pivots).  FP64 factorizations always use FP64.
  *   H2_OPT_RESIDUAL_FP64  refinement scheme 2: 0 (default) forms
  *                         b - A_H2 x in FP32-pair arithmetic, 1 with FP64
- *                         instructions (the h2_matvec operator). */
-typedef enum { H2_OPT_RR_LU_FP64 = 0, H2_OPT_RESIDUAL_FP64 = 1 } h2_option;
+ *                         instructions (the h2_matvec operator).
+ *   H2_OPT_GRAPHS         1 (default): the FP32 substitution of FP16/BF16
+ *                         factorizations is captured once per factorization
+ *                         as a CUDA graph (on a private stream) and replayed
+ *                         for every preconditioner application; 0: plain
+ *                         launches.  A capture that fails falls back to
+ *                         plain launches. */
+typedef enum { H2_OPT_RR_LU_FP64 = 0, H2_OPT_RESIDUAL_FP64 = 1, H2_OPT_GRAPHS = 2 } h2_option;
 
 /* Set an h2_option to value (0 or 1).  Errors: H2_ERR_INVALID_ARG. */
 h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value);
@@ -389,9 +395,10 @@ h2_status h2_plan_predicted(const h2_params* p, const double* points, int64_t N,
                             size_t cap);
 
 /* h2_build with the ranks laid out by the predictor: each level's rank is
- * K_l = min(cap, max_i ceil(prediction_i n_i) + 2), and each box's
+ * K_l = max_i ceil(1.05 prediction_i n_i) + 2, raised to the level's cap
+ * once it is within 10 % of it and never above it, and each box's
  * interpolative decomposition comes from a randomized sketch M_i Omega of
- * K_l + 10 columns (Rademacher Omega from splitmix64) followed by a pivoted
+ * K_l + 26 columns (Rademacher Omega from splitmix64) followed by a pivoted
  * QR truncated at K_l, in place of the full rank-revealing pass over M_i.
  * The plain pivoted-QR compression stays the fallback and the judge: a box
  * whose sketch shows more than tol of its leading pivot beyond K_l (below
@@ -402,6 +409,67 @@ h2_status h2_plan_predicted(const h2_params* p, const double* points, int64_t N,
  * time.  Errors: as h2_build. */
 h2_status h2_build_predicted(h2_ctx** out, const h2_params* p, const double* points, int64_t N,
                              h2_rank_model* model);
+
+/* h2_build with Algorithm 1's compression on the GPU, each level at a rank
+ * laid out beforehand: the predictor's (model; as in h2_build_predicted) or,
+ * with model NULL, the level's cap (fixed-rank truncation).  For every box
+ * of a level at once, in FP64: W_j = G(S_C(j), S_C(j))^-1 Omega(S_C(j)) per
+ * close-sample set (Gauss-Jordan with partial pivoting, or gs_sweeps
+ * Gauss-Seidel sweeps from 0 when gs_sweeps > 0: the shortcut of Section
+ * 3.5), the sketch Y_i = G(B_i, S_F) Omega(S_F) + sum_j G(B_i, S_C(j)) W_j
+ * with K + 32 columns, 6 of them probes (Omega(p, t) = +-1 from splitmix64 of the sample point
+ * p and column t), and a column-pivoted QR of the sketch truncated at K + 1
+ * steps giving the skeleton and X_i.  The acceptance test and the plain
+ * host fallback are those of h2_build_predicted.  Levels the kernels do not
+ * cover (box dimension above 256, K above 128, near_samples outside 1..64)
+ * run on the host.  h2_stats "construction" reports the GPU levels and the
+ * flops of the close-field (pre-factorization) and far-field parts.
+ * Errors: as h2_build; H2_ERR_INVALID_ARG also for gs_sweeps outside 0..16. */
+h2_status h2_build_gpu(h2_ctx** out, const h2_params* p, const double* points, int64_t N, h2_rank_model* model,
+                       int32_t gs_sweeps);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent systems (uneven N and per-cluster ranks; no
+ * counterpart in the paper).  Every system keeps its own context; a pool
+ * of host workers, each with its own CUDA stream, factors and solves them
+ * concurrently, largest system first, so that systems too small to fill
+ * the GPU alone share it.  Each context's FP32 substitution replays as a
+ * CUDA graph (H2_OPT_GRAPHS).  The worker count is picked by measurement
+ * (h2_batch_tune).  A context in a batch must not be used elsewhere while
+ * a batch call runs; the batch sets each context's stream.
+ * ------------------------------------------------------------------------- */
+typedef struct h2_batch h2_batch;
+
+/* A batch over count contexts (not owned) with their sizes n[i].
+ * Errors: H2_ERR_INVALID_ARG. */
+h2_status h2_batch_create(h2_batch** out, h2_ctx* const* ctxs, const int64_t* n, int32_t count);
+
+/* Factor every system in precision prec (prec = -1: keep the current
+ * factorizations) and, with B non-NULL, solve system i for B[i] into X[i]
+ * as h2_solve does (target, max_iters).  relres and iters (host, may be
+ * NULL) receive count values; *seconds (may be NULL) the wall time.
+ * Errors: those of h2_factor / h2_solve, with the system in the message
+ * (h2_batch_last_error). */
+h2_status h2_batch_run(h2_batch* b, int32_t prec, const double* const* B, double* const* X, double target,
+                       int32_t max_iters, double* relres, int32_t* iters, double* seconds);
+
+/* Autotune the worker count: run the whole batch (factor and solve) with
+ * 1, 2, 4, 8 and 16 workers (up to twice the system count) and keep the
+ * fastest; *workers_out (may be NULL) receives it.  Errors: as
+ * h2_batch_run. */
+h2_status h2_batch_tune(h2_batch* b, int32_t prec, const double* const* B, double* const* X, double target,
+                        int32_t max_iters, int32_t* workers_out);
+
+/* JSON: system count, worker count, the last run's seconds and the tuning
+ * times by worker count.  Errors: H2_ERR_INVALID_ARG (cap too small). */
+h2_status h2_batch_stats(const h2_batch* b, char* json, size_t cap);
+
+/* One-line description of the batch's last error ("" if none). */
+const char* h2_batch_last_error(const h2_batch* b);
+
+/* Free the batch (not its contexts; they go back to the legacy default
+ * stream).  NULL is ignored. */
+void h2_batch_destroy(h2_batch* b);
 
 /* Issue all later work on the given cudaStream_t (NULL: legacy default). */
 h2_status h2_set_stream(h2_ctx* c, void* stream);

@@ -4,7 +4,7 @@ The module-level functions carry the C names (h2_build, h2_plan, h2_import,
 h2_factor, h2_solve, h2_solve_many, h2_ulv_apply, h2_matvec, h2_matvec_many,
 h2_matvec_noalloc, h2_matvec_arith, h2_set_option, h2_wait_selftest,
 h2_set_memory_limit, the rank predictor's h2_rank_data / h2_rank_model_* /
-h2_plan_predicted / h2_build_predicted, h2_set_refinement, h2_set_stream, h2_stats, h2_export,
+h2_plan_predicted / h2_build_predicted / h2_build_gpu, h2_set_refinement, h2_set_stream, h2_stats, h2_export,
 h2_last_error, h2_destroy) and only marshal arguments: every step
 of the computation runs in the library.  ``H2Solver`` wraps a context.
 
@@ -35,9 +35,10 @@ EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_sol
             "h2_wait_selftest", "h2_set_memory_limit", "h2_rank_data", "h2_rank_model_create",
             "h2_rank_model_set_weights", "h2_rank_model_get_weights", "h2_rank_model_grad", "h2_rank_model_train",
             "h2_rank_model_predict", "h2_rank_model_last_error", "h2_rank_model_destroy", "h2_plan_predicted",
-            "h2_build_predicted",
+            "h2_build_predicted", "h2_build_gpu", "h2_batch_create", "h2_batch_run", "h2_batch_tune",
+            "h2_batch_stats", "h2_batch_last_error", "h2_batch_destroy",
             "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
-OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1}
+OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1, "graphs": 2}
 ARITH = {"fp64": 0, "fp32": 1, "fp32_pair": 2}
 
 
@@ -102,6 +103,13 @@ def lib() -> ctypes.CDLL:
             "h2_rank_model_destroy": (None, [vp]),
             "h2_plan_predicted": (i32, [vp, vp, i64, vp, ctypes.c_char_p, ctypes.c_size_t]),
             "h2_build_predicted": (i32, [pp, vp, vp, i64, vp]),
+            "h2_build_gpu": (i32, [pp, vp, vp, i64, vp, i32]),
+            "h2_batch_create": (i32, [pp, vp, vp, i32]),
+            "h2_batch_run": (i32, [vp, i32, vp, vp, dbl, i32, vp, vp, vp]),
+            "h2_batch_tune": (i32, [vp, i32, vp, vp, dbl, i32, vp]),
+            "h2_batch_stats": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+            "h2_batch_last_error": (ctypes.c_char_p, [vp]),
+            "h2_batch_destroy": (None, [vp]),
             "h2_set_stream": (i32, [vp, vp]),
             "h2_stats": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
             "h2_export": (i32, [vp, ctypes.c_char_p, i32, vp, ctypes.c_size_t, vp, vp]),
@@ -242,7 +250,7 @@ def h2_set_refinement(ctx, method: str | int = "auto", restart: int = 30):
 
 
 def h2_set_option(ctx, option: str | int, value: int):
-    """option: "rr_lu_fp64" (0) or "residual_fp64" (1); value 0 or 1."""
+    """option: "rr_lu_fp64" (0), "residual_fp64" (1) or "graphs" (2); value 0 or 1."""
     _check(lib().h2_set_option(ctx, OPTIONS.get(option, option), int(value)), ctx)
 
 
@@ -349,6 +357,76 @@ def h2_build_predicted(params: Params, points: np.ndarray, m):
     return out
 
 
+def h2_build_gpu(params: Params, points: np.ndarray, m=None, gs_sweeps: int = 0):
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(lib().h2_build_gpu(ctypes.byref(out), ctypes.byref(params), _ptr(pts), len(pts), m, int(gs_sweeps)), None)
+    return out
+
+
+# ------------------------------------------------------------- batches ---
+class H2Batch:
+    """Independent systems (H2Solver objects) factored and solved
+    concurrently by the library's worker pool."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        n = len(self.solvers)
+        self._ctx = (ctypes.c_void_p * n)(*[s.ctx.value if hasattr(s.ctx, "value") else s.ctx for s in self.solvers])
+        self._n = (ctypes.c_int64 * n)(*[s.n for s in self.solvers])
+        out = ctypes.c_void_p()
+        _check(lib().h2_batch_create(ctypes.byref(out), ctypes.cast(self._ctx, ctypes.c_void_p),
+                                     ctypes.cast(self._n, ctypes.c_void_p), n), None)
+        self.b = out
+
+    def _ptrs(self, arrs):
+        a = (ctypes.c_void_p * len(arrs))(*[_ptr(x).value for x in arrs])
+        return a
+
+    def _err(self, st):
+        if st != 0:
+            m = lib().h2_batch_last_error(self.b)
+            raise H2Error(st, m.decode() if m else "")
+
+    def run(self, prec="fp16", B=None, target=1e-10, max_iters=100):
+        """Factor all systems (prec None: keep) and solve each for B[i];
+        returns (X list, relres, iters, seconds)."""
+        n = len(self.solvers)
+        p = -1 if prec is None else PRECS[prec]
+        rel = (ctypes.c_double * n)()
+        its = (ctypes.c_int32 * n)()
+        sec = ctypes.c_double()
+        X = None
+        if B is not None:
+            X = [np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape) for b in B]
+            pb, px = self._ptrs(B), self._ptrs(X)
+            st = lib().h2_batch_run(self.b, p, ctypes.cast(pb, ctypes.c_void_p), ctypes.cast(px, ctypes.c_void_p),
+                                    target, max_iters, ctypes.cast(rel, ctypes.c_void_p),
+                                    ctypes.cast(its, ctypes.c_void_p), ctypes.byref(sec))
+        else:
+            st = lib().h2_batch_run(self.b, p, None, None, target, max_iters, None, None, ctypes.byref(sec))
+        self._err(st)
+        return X, list(rel), list(its), sec.value
+
+    def tune(self, prec="fp16", B=None, target=1e-10, max_iters=100):
+        X = [np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape) for b in B]
+        pb, px = self._ptrs(B), self._ptrs(X)
+        w = ctypes.c_int32()
+        self._err(lib().h2_batch_tune(self.b, PRECS[prec], ctypes.cast(pb, ctypes.c_void_p),
+                                      ctypes.cast(px, ctypes.c_void_p), target, max_iters, ctypes.byref(w)))
+        return w.value
+
+    def stats(self) -> dict:
+        buf = ctypes.create_string_buffer(1 << 14)
+        self._err(lib().h2_batch_stats(self.b, buf, len(buf)))
+        return json.loads(buf.value.decode())
+
+    def close(self):
+        if self.b:
+            lib().h2_batch_destroy(self.b)
+            self.b = None
+
+
 def h2_set_stream(ctx, stream):
     handle = getattr(stream, "cuda_stream", stream)
     _check(lib().h2_set_stream(ctx, ctypes.c_void_p(int(handle) if handle else 0)), ctx)
@@ -397,6 +475,12 @@ class H2Solver:
     def build_predicted(cls, points, model, **kw):
         """h2_build with the ranks laid out by a trained rank model."""
         return cls(h2_build_predicted(make_params(**kw), points, model), len(points))
+
+    @classmethod
+    def build_gpu(cls, points, model=None, gs_sweeps=0, **kw):
+        """h2_build with the compression on the GPU (ranks from the model, or
+        each level's cap when model is None)."""
+        return cls(h2_build_gpu(make_params(**kw), points, model, gs_sweeps), len(points))
 
     @classmethod
     def from_instance(cls, flat: dict, **kw):

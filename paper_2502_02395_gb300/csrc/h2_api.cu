@@ -480,6 +480,8 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   CKC(dalloc(c, &F.tscale, 2 * (size_t)(L + 1)));
   CKC(dalloc(c, &F.cscale, (size_t)(L + 1)));
   CKC(dalloc(c, &F.amax, 3 * (size_t)(L + 1)));
+  CKC(dalloc(c, &F.sch, 8));
+  CKC(dalloc(c, &F.sch_amax, 2));
   if (std::is_same<T, double>::value) {
     CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
     F.root_luT = reinterpret_cast<T*>(F.root_lu);
@@ -557,6 +559,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   mark();
   const int bf16 = (prec == H2_PREC_BF16) ? 1 : 0;
   F.bf16 = bf16;
+  F.schur_tc = false;
   const bool mixed = !std::is_same<T, double>::value;
   // FP64 a3 for the FP16/BF16 factorizations: scratch for the largest level
   const bool lu64_mixed = mixed && c->rr_lu64;
@@ -795,8 +798,42 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       gemm<T>(prec, R, D, R, f.Ainv, (int64_t)R * R, nullptr, R, false, f.U, DD, nullptr, D, false, f.M1,
               (int64_t)R * D, nullptr, D, T(1), T(0), d.nb, sp);
     }
-    // a4 + a5: Z = Ainv Ahat_ii^RS; Ahat_ii^SS -= Ahat_ii^SR Z
-    if (R > 0 && K > 0) {
+    // a4 + a5: Z = Ainv Ahat_ii^RS; Ahat_ii^SS -= Ahat_ii^SR Z.  On the
+    // tensor cores (16-bit operands, FP32 accumulation) where the level's
+    // 16-bit copy s Ahat holds the diagonal blocks' SR quadrant: with the
+    // symmetric Ahat_ii (Ahat_ii^RS = (Ahat_ii^SR)^T),
+    //   Z^T = Ahat_ii^SR Ainv^T        (GEMM 1: A = s SR, B = s_i Ainv)
+    //   SS -= Ahat_ii^SR (Z^T)^T       (GEMM 2: A = s SR, B = s_z Z^T)
+    // with power-of-two scales s_i, s_z from max |Ainv|, max |Z^T|.
+    const float* sc_l = (l == L) ? c->A16_scale[bf16] : F.scales + 2 * l;
+    const bool schur_tc = mixed && f.tc && f.ahat_isc && d.near_sym && R > 0 && K > 0 && R % 64 == 0 &&
+                          gemm_tc_supported(K, R, R, D, R, R) && gemm_tc_supported(K, K, R, D, R, D);
+    if (schur_tc) {
+      const int64_t nb = d.nb, RR = (int64_t)R * R, KR = (int64_t)K * R;
+      float* Zt = reinterpret_cast<float*>(F.Wk);
+      uint16_t* Ai16 = reinterpret_cast<uint16_t*>(F.W16);
+      uint16_t* Z16 = Ai16 + nb * RR;
+      CKC(cudaMemsetAsync(F.sch_amax, 0, 2 * sizeof(unsigned int), st));
+      launch_amax_blocks<float>(reinterpret_cast<const float*>(f.Ainv), nb, RR, R, R, R, F.sch_amax, st);
+      launch_pow2_scale(F.sch_amax, 16384.0f, F.sch, st);
+      launch_to_lowp<float>(bf16, reinterpret_cast<const float*>(f.Ainv), Ai16, nb * RR, F.sch, st);
+      launch_inv_scale_pair(sc_l, F.sch, F.sch + 4, st);
+      const void* SR16 = static_cast<const uint16_t*>(f.Ahat16) + (int64_t)R * D;
+      bool ok = gemm_tc(bf16, K, R, R, SR16, d.NP, D, D, d.diag_pair, Ai16, nb, R, R, nullptr, Zt, KR, nullptr, R, 0,
+                        0, 1.0f, F.sch + 4, nb, c->status + 2, st, nullptr, -1, nullptr, nullptr, nullptr,
+                        d.NP * (int64_t)D - R);
+      if (ok) {
+        launch_amax_blocks<float>(Zt, nb, KR, K, R, R, F.sch_amax + 1, st);
+        launch_pow2_scale(F.sch_amax + 1, 16384.0f, F.sch + 2, st);
+        launch_to_lowp<float>(bf16, Zt, Z16, nb * KR, F.sch + 2, st);
+        launch_inv_scale_pair(sc_l, F.sch + 2, F.sch + 5, st);
+        ok = gemm_tc(bf16, K, K, R, SR16, d.NP, D, D, d.diag_pair, Z16, nb, K, R, nullptr,
+                     reinterpret_cast<float*>(f.Ahat) + (int64_t)R * D + R, DD, d.diag_pair, D, 3, 0, -1.0f,
+                     F.sch + 5, nb, c->status + 2, st, nullptr, -1, nullptr, nullptr, nullptr, d.NP * (int64_t)D - R);
+      }
+      if (!ok) return fail(H2_ERR_CUDA, "tensor-core Schur update setup failed at level " + std::to_string(l));
+      F.schur_tc = true;
+    } else if (R > 0 && K > 0) {
       gemm<T>(prec, R, K, R, f.Ainv, (int64_t)R * R, nullptr, R, false, f.Ahat + R, DD, d.diag_pair, D, false, f.Z,
               (int64_t)R * K, nullptr, K, T(1), T(0), d.nb, st);
       gemm<T>(prec, K, K, R, f.Ahat + (int64_t)R * D, DD, d.diag_pair, D, false, f.Z, (int64_t)R * K, nullptr, K,
@@ -978,12 +1015,52 @@ void ulv_apply_impl(h2_ctx* c, Factor<T>& F, const double* r, double* x) {
   launch_axpy_from<T>(ulv_out(c, F), c->red, x, n, c->stream);
 }
 
-// z = ULV^-1 v for FP32 tree vectors (mixed-precision factorization).
+// Capture fn's work on the context's stream into a CUDA graph (on a private
+// capture stream); nullptr if the capture or instantiation fails, in which
+// case the caller runs fn directly.
+template <class Fn>
+cudaGraphExec_t capture_graph(h2_ctx* c, long long& kernels, Fn fn) {
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  cudaStream_t keep = c->stream;
+  c->stream = c->cap_stream;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  const long long n0 = g_launches.load();
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    fn();
+    if (cudaStreamEndCapture(c->cap_stream, &g) == cudaSuccess && g) {
+      if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+    }
+  }
+  kernels = g_launches.load() - n0;
+  g_launches -= kernels;  // counted again per replay
+  if (g) cudaGraphDestroy(g);
+  c->stream = keep;
+  cudaGetLastError();
+  return ex;
+}
+
+void drop_graphs(h2_ctx* c) {
+  if (c->g_ulv) cudaGraphExecDestroy(c->g_ulv);
+  c->g_ulv = nullptr;
+}
+
+// z = ULV^-1 v for FP32 tree vectors (mixed-precision factorization); the
+// sweep (about a hundred dependent launches) replays as one CUDA graph.
 void ulv_apply_f32(h2_ctx* c, const float* v, float* z) {
   const int64_t n = nslots(c);
   Factor<float>& F = c->f32;
   cudaMemcpyAsync(ulv_in(c, F), v, n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
-  ulv_sweep<float>(c, F);
+  if (c->use_graphs && !c->g_ulv) c->g_ulv = capture_graph(c, c->g_ulv_kernels, [&] { ulv_sweep<float>(c, F); });
+  if (c->use_graphs && c->g_ulv) {
+    cudaGraphLaunch(c->g_ulv, c->stream);
+    g_launches += c->g_ulv_kernels;
+  } else {
+    ulv_sweep<float>(c, F);
+  }
   cudaMemcpyAsync(z, ulv_out(c, F), n * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
 }
 
@@ -1632,6 +1709,7 @@ h2_status h2_factor(h2_ctx* c, int32_t prec) {
     return H2_ERR_INVALID_ARG;
   }
   c->prec = -1;
+  drop_graphs(c);
   const bool fresh = (prec == H2_PREC_FP64) ? c->f64.lv.empty() : c->f32.lv.empty();
   if (fresh) CKS(check_fits(factor_bytes(c, prec == H2_PREC_FP64 ? 8 : 4), "the factorization", c->err));
   h2_status s = (prec == H2_PREC_FP64) ? factor_impl<double>(c, c->f64, prec) : factor_impl<float>(c, c->f32, prec);
@@ -1788,6 +1866,10 @@ h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value) {
   switch (option) {
     case H2_OPT_RR_LU_FP64: c->rr_lu64 = value != 0; return H2_OK;
     case H2_OPT_RESIDUAL_FP64: c->resid64 = value != 0; return H2_OK;
+    case H2_OPT_GRAPHS:
+      c->use_graphs = value != 0;
+      drop_graphs(c);
+      return H2_OK;
     default: c->err = "unknown option"; return H2_ERR_INVALID_ARG;
   }
 }
@@ -1950,6 +2032,51 @@ h2_status h2_build_predicted(h2_ctx** out, const h2_params* p, const double* poi
   return H2_OK;
 }
 
+h2_status h2_build_gpu(h2_ctx** out, const h2_params* p, const double* points, int64_t N, h2_rank_model* model,
+                       int32_t gs_sweeps) {
+  g_last_error.clear();
+  if (!out) { g_last_error = "out is NULL"; return H2_ERR_INVALID_ARG; }
+  *out = nullptr;
+  h2_status s = check_params(p, g_last_error);
+  if (s != H2_OK) return s;
+  if (N < 1 || !points || gs_sweeps < 0 || gs_sweeps > 16) {
+    g_last_error = "N < 1, points NULL or gs_sweeps outside 0..16";
+    return H2_ERR_INVALID_ARG;
+  }
+  for (int64_t t = 0; t < 3 * N; ++t)
+    if (!std::isfinite(points[t])) { g_last_error = "non-finite coordinate"; return H2_ERR_INVALID_ARG; }
+  h2_ctx* c = new h2_ctx();
+  c->params = *p;
+  c->kfn = KernelFn{p->kernel, p->eps, p->ell, p->diag_shift};
+  GpuCompressor* gpu = make_gpu_compressor(c->kfn, points, N, gs_sweeps);
+  if (!gpu) {
+    g_last_error = "GPU construction: device upload of the points failed";
+    delete c;
+    return H2_ERR_CUDA;
+  }
+  ModelPredictor pred(model);
+  std::string e = build_host(*p, points, N, c->host, model ? &pred : nullptr, false, gpu);
+  delete gpu;
+  if (!e.empty()) {
+    g_last_error = e;
+    delete c;
+    return e.rfind("GPU construction", 0) == 0 ? H2_ERR_CUDA : H2_ERR_SINGULAR;
+  }
+  s = check_fits(instance_bytes(c->host), "the H^2 instance", g_last_error);
+  if (s != H2_OK) {
+    delete c;
+    return s;
+  }
+  s = setup_device(c);
+  if (s != H2_OK) {
+    g_last_error = c->err;
+    h2_destroy(c);
+    return s;
+  }
+  *out = c;
+  return H2_OK;
+}
+
 h2_status h2_set_stream(h2_ctx* c, void* stream) {
   if (!c) return H2_ERR_INVALID_ARG;
   c->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -2025,6 +2152,8 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     << ",\"iters\":" << t.iters << ",\"relres\":" << t.relres
     << ",\"kernel_launches\":" << g_launches.load() << ",\"refine_method\":" << c->refine_method
     << ",\"restart\":" << c->restart << ",\"tensor_cores\":" << (c->used_tc ? "true" : "false")
+    << ",\"schur_tensor_cores\":" << ((c->prec > 0 && c->f32.schur_tc) ? "true" : "false")
+    << ",\"rr_lu_fp64\":" << (c->rr_lu64 ? "true" : "false")
     << ",\"history\":[";
   for (size_t k = 0; k < t.history.size(); ++k) o << (k ? "," : "") << t.history[k];
   o << "]";
@@ -2032,7 +2161,8 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
   // the final ranks, the boxes and levels that fell back to the plain pass
   const RankRecord& rec = c->host.rec;
   o << ",\"construction\":{\"compress_s\":" << rec.compress_s << ",\"fallback_boxes\":" << rec.fallback_boxes
-    << ",\"fallback_levels\":" << rec.fallback_levels << ",\"K_pred\":[";
+    << ",\"fallback_levels\":" << rec.fallback_levels << ",\"gpu_levels\":" << rec.gpu_levels
+    << ",\"flops_prefactor\":" << rec.flops_prefactor << ",\"flops_far\":" << rec.flops_far << ",\"K_pred\":[";
   for (int l = 0; l <= c->L; ++l) o << (l ? "," : "") << (l < (int)rec.K_pred.size() ? rec.K_pred[l] : -1);
   o << "],\"K\":[";
   for (int l = 0; l <= c->L; ++l) o << (l ? "," : "") << c->lv[l].K;
@@ -2130,7 +2260,8 @@ void h2_destroy(h2_ctx* c) {
   if (!c) return;
   if (c->mv_fork) cudaEventDestroy(c->mv_fork);
   if (c->mv_join) cudaEventDestroy(c->mv_join);
-  for (cudaStream_t s : {c->basis_stream, c->coupling_stream, c->product_stream, c->leaf_stream}) {
+  drop_graphs(c);
+  for (cudaStream_t s : {c->basis_stream, c->coupling_stream, c->product_stream, c->leaf_stream, c->cap_stream}) {
     if (!s) continue;
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);

@@ -91,6 +91,33 @@ struct RankRecord {
   int fallback_boxes = 0;                 // boxes compressed the plain way after a failed sketch check
   int fallback_levels = 0;                // levels redone the plain way (rank too small)
   double compress_s = 0;                  // wall time of the per-box compression passes
+  int gpu_levels = 0;                     // levels whose sketches ran on the GPU
+  double flops_prefactor = 0;             // GPU construction: the close-field (pre-factorization) part
+  double flops_far = 0;                   //                   the far-field part
+};
+
+// One level of the GPU construction (construct_gpu.cu): nb boxes of at most
+// D points (nbox[i]; bpts: nb * D original indices, -1 pad), far samples
+// (fptr / fidx), close boxes (nptr / nidx: the near list, j == i skipped),
+// close samples of each box (cptr / cidx), rank K, m sketch + probe columns
+// (ms of them sketch), q = m - ms probes, Gauss-Seidel sweeps gs (0: exact
+// solve).  Outputs: X (nb * D * K row-major), SK (nb * K), piv (nb * D),
+// the pivot ratio rho and probe error err per box.
+struct GpuLevelJob {
+  int nb = 0, D = 0, K = 0, m = 0, ms = 0, q = 0, gs = 0;
+  uint64_t seed = 0;
+  std::vector<int> nbox;
+  std::vector<int64_t> bpts, fptr, fidx, nptr, cptr, cidx;
+  std::vector<int32_t> nidx;
+  std::vector<double> X, rho, err;
+  std::vector<int64_t> SK;
+  std::vector<int32_t> piv;
+  double flops_prefactor = 0, flops_far = 0;
+};
+struct GpuCompressor {
+  virtual bool supported(int D, int K) const = 0;
+  virtual std::string run(GpuLevelJob& job) = 0;  // "" on success
+  virtual ~GpuCompressor() = default;
 };
 
 struct HostH2 {
@@ -117,7 +144,10 @@ struct RankPredictor {
 // with layout_only, the levels are laid out from predictions alone (no
 // compression; X and SK stay empty).
 std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& out,
-                       RankPredictor* pred = nullptr, bool layout_only = false);
+                       RankPredictor* pred = nullptr, bool layout_only = false, GpuCompressor* gpu = nullptr);
+// The GPU compressor of construct_gpu.cu over the N points (kernel G);
+// nullptr if the device upload fails.
+GpuCompressor* make_gpu_compressor(const KernelFn& G, const double* pts, int64_t N, int gs_sweeps);
 
 // ---------------------------------------------------------------------------
 // Device-side state.
@@ -241,6 +271,12 @@ struct Factor {
   float* tscale = nullptr;    // 2 (L + 1): scale of T16 and its inverse
   float* cscale = nullptr;    // L + 1: 1 / (scale(S16) scale(T16)^2) for the couplings
   unsigned int* amax = nullptr;  // 2 (L + 1) max-abs accumulators: [l] merge, [L + 1 + l] couplings
+  // tensor-core Schur update (FP16/BF16 factorizations): scales of the 16-bit
+  // (Ahat_ii^RR)^-1 [0, 1] and Z^T [2, 3], the two GEMMs' output scales
+  // [4, 5]; max-abs accumulators [0, 1]
+  float* sch = nullptr;
+  unsigned int* sch_amax = nullptr;
+  bool schur_tc = false;  // the last factorization ran a4/a5 on the tensor cores at some level
   int bf16 = -1;              // operand type the 16-bit buffers hold
 };
 
@@ -322,6 +358,12 @@ struct h2_ctx {
   bool rr_lu64 = false;          // FP16/BF16 factorizations: Ahat_ii^RR inverted in FP64 (else FP32)
   bool resid64 = false;          // refinement scheme 2: residual with FP64 instructions (else FP32 pairs)
   float *mv32_x = nullptr, *mv32_y = nullptr;  // h2_matvec_arith's FP32 tree vectors (created on first use)
+  // the FP32 substitution sweep of the current FP16/BF16 factorization as a
+  // CUDA graph (captured on first use after each h2_factor; H2_OPT_GRAPHS)
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t g_ulv = nullptr;
+  long long g_ulv_kernels = 0;  // kernels in that graph (added to the launch count per replay)
   double inner_tol = 1e-6;       // relative accuracy of the FP32 inner solves
   int restart = 30;              // FGMRES restart length
   double* gm_V = nullptr;        // (restart + 1) * nslot Krylov basis

@@ -275,15 +275,17 @@ void level_features(const h2_params& p, const double* P, const std::vector<int64
   }
 }
 
-// A level's rank from the predictions y_i of k_i / n_i: max_i ceil(y_i n_i)
-// + 2, at least 1, at most the level's cap (max_rank, else D / 2).
+// A level's rank from the predictions y_i of k_i / n_i: max_i ceil(1.05 y_i
+// n_i) + 2 (a 5 % margin), raised to the level's cap (max_rank, else D / 2)
+// once it is within 10 % of it, at least 1.
 int predicted_rank(const h2_params& p, const std::vector<float>& y, const std::vector<int>& n, int D) {
   int k = 1;
   for (size_t i = 0; i < y.size(); ++i) {
     const double v = std::min(1.0, std::max(0.0, (double)y[i]));
-    k = std::max(k, (int)std::ceil(v * n[i]) + 2);
+    k = std::max(k, (int)std::ceil(1.05 * v * n[i]) + 2);
   }
   const int cap = p.max_rank > 0 ? p.max_rank : D / 2;
+  if (k >= 0.9 * cap) k = cap;
   return std::max(1, std::min(k, cap));
 }
 
@@ -329,7 +331,7 @@ using RowSink = std::function<void(double*, int)>;
 using RowsFn = std::function<bool(int, const RowSink&)>;
 
 // Randomized interpolative decomposition of box i (dimension n) at rank K:
-// Y = M_i Omega with K + 10 sketch columns and 6 probe columns (Rademacher
+// Y = M_i Omega with K + 26 sketch columns and 6 probe columns (Rademacher
 // signs from splitmix64(seed, row, column)); a column-pivoted QR of the
 // sketch part of Y^T, K + 1 steps, gives the skeleton (the first K pivots)
 // and R11, R12 (written as the first K rows of Rout, n x n row-major, as the
@@ -339,7 +341,7 @@ using RowsFn = std::function<bool(int, const RowSink&)>;
 // 10 max(tol, that pivot ratio).
 bool sketch_box(const RowsFn& rows_of, int i, int n, int K, bool capped, double tol, uint64_t seed,
                 std::vector<double>& Rout, std::vector<int>& piv) {
-  const int ms = std::min(K + 10, n), q = 6, m = ms + q;
+  const int ms = std::min(K + 26, n), q = 6, m = ms + q;
   std::vector<double> Y((size_t)n * m, 0.0), w(m);
   uint64_t g = 0;
   const bool rows_ok = rows_of(i, [&](double* C, int c) {
@@ -397,7 +399,7 @@ bool sketch_box(const RowsFn& rows_of, int i, int n, int K, bool capped, double 
 }  // namespace
 
 std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& H, RankPredictor* pred,
-                       bool layout_only) {
+                       bool layout_only, GpuCompressor* gpu) {
   KernelFn G{p.kernel, p.eps, p.ell, p.diag_shift};
   H.N = N;
   H.points.assign(pts, pts + 3 * N);
@@ -565,31 +567,92 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
     auto t0 = std::chrono::steady_clock::now();
     int K = 0;
     bool done = false;
-    if (pred) {
-      std::vector<float> yhat;
-      if (!pred->predict(feats, nb, yhat)) return "rank predictor failed at level " + std::to_string(l);
-      K = std::min(predicted_rank(p, yhat, nbox, D), capK);
-      rec.K_pred[l] = K;
+    // boxes whose X and skeleton come straight from the GPU construction
+    std::vector<char> direct(nb, 0);
+    GpuLevelJob job;
+    if (pred || gpu) {
+      if (pred) {
+        std::vector<float> yhat;
+        if (!pred->predict(feats, nb, yhat)) return "rank predictor failed at level " + std::to_string(l);
+        K = std::min(predicted_rank(p, yhat, nbox, D), capK);
+        rec.K_pred[l] = K;
+      } else {
+        K = capK;  // fixed rank: the level's cap
+      }
       std::vector<char> ok(nb, 0);
-      const uint64_t lseed = splitmix64(0x5eedull + (uint64_t)l);
+      bool sketched = false;
+      if (gpu && gpu->supported(D, K) && p.near_samples > 0 && p.near_samples <= 64) {
+        // the level's sample lists for the GPU sketches
+        job.nb = nb, job.D = D, job.K = K;
+        job.m = std::min(160, ((K + 32 + 1) / 2) * 2);  // K + 26 sketch columns, 6 probes
+        job.q = 6, job.ms = job.m - 6;
+        job.seed = splitmix64(0xC0FFEEull + (uint64_t)l);
+        job.nbox = nbox;
+        job.bpts.assign((size_t)nb * D, -1);
+        job.fptr.assign(nb + 1, 0);
+        job.nptr.assign(nb + 1, 0);
+        job.cptr.assign(nb + 1, 0);
+        for (int i = 0; i < nb; ++i) {
+          for (size_t a = 0; a < bp[l][i].size(); ++a) job.bpts[(size_t)i * D + a] = bp[l][i][a];
+          int64_t nearcnt = 0;
+          for (int j : nbrs[i]) nearcnt += off[l][j + 1] - off[l][j];
+          const int64_t F = N - nearcnt;
+          const int64_t sF = (p.far_samples <= 0 || p.far_samples >= F) ? F : p.far_samples;
+          for (int64_t t = 0; t < sF; ++t) {
+            int64_t q = (t * F) / sF;
+            for (int j : nbrs[i]) {
+              if (q < off[l][j]) break;
+              q += off[l][j + 1] - off[l][j];
+            }
+            job.fidx.push_back(H.perm[q]);
+          }
+          job.fptr[i + 1] = (int64_t)job.fidx.size();
+          for (int j : nbrs[i]) job.nidx.push_back(j);
+          job.nptr[i + 1] = (int64_t)job.nidx.size();
+          const std::vector<int64_t>& Pi = bp[l][i];
+          const int ni = (int)Pi.size();
+          const int sc = std::min(ni, p.near_samples);
+          for (int t = 0; t < sc; ++t) job.cidx.push_back(Pi[((int64_t)t * ni) / sc]);
+          job.cptr[i + 1] = (int64_t)job.cidx.size();
+        }
+        const std::string e = gpu->run(job);
+        if (!e.empty()) return "GPU construction at level " + std::to_string(l) + ": " + e;
+        for (int i = 0; i < nb; ++i) {
+          ranks[i] = -1;
+          ok[i] = (K >= capK || job.rho[i] <= p.tol) && job.err[i] <= 10.0 * std::max(p.tol, job.rho[i]);
+          direct[i] = ok[i];
+        }
+        ++rec.gpu_levels;
+        rec.flops_prefactor += job.flops_prefactor;
+        rec.flops_far += job.flops_far;
+        sketched = true;
+      } else if (pred) {
+        const uint64_t lseed = splitmix64(0x5eedull + (uint64_t)l);
 #pragma omp parallel for schedule(dynamic, 1)
-      for (int i = 0; i < nb; ++i) {
-        ranks[i] = -1;
-        ok[i] = sketch_box(rows_of, i, (int)bp[l][i].size(), K, K >= capK, p.tol, splitmix64(lseed ^ (uint64_t)i),
-                           Rb[i], pivs[i]);
+        for (int i = 0; i < nb; ++i) {
+          ranks[i] = -1;
+          ok[i] = sketch_box(rows_of, i, (int)bp[l][i].size(), K, K >= capK, p.tol, splitmix64(lseed ^ (uint64_t)i),
+                             Rb[i], pivs[i]);
+        }
+        sketched = true;
       }
-      if (bad >= 0)
-        return "singular close-field sample block at level " + std::to_string(l) + " box " + std::to_string(bad);
-      int need = K;
+      if (sketched) {
+        int need = K;
 #pragma omp parallel for schedule(dynamic, 1) reduction(max : need)
-      for (int i = 0; i < nb; ++i) {
-        if (ok[i]) continue;
-        plain_box(i);
-        need = std::max(need, std::min(ranks[i], capK));
+        for (int i = 0; i < nb; ++i) {
+          if (ok[i]) continue;
+          plain_box(i);
+          need = std::max(need, std::min(ranks[i], capK));
+        }
+        if (bad >= 0)
+          return "singular close-field sample block at level " + std::to_string(l) + " box " + std::to_string(bad);
+        for (int i = 0; i < nb; ++i) rec.fallback_boxes += !ok[i];
+        done = need <= K;
+        if (!done) {
+          ++rec.fallback_levels;
+          std::fill(direct.begin(), direct.end(), 0);
+        }
       }
-      for (int i = 0; i < nb; ++i) rec.fallback_boxes += !ok[i];
-      done = need <= K;
-      if (!done) ++rec.fallback_levels;
     }
     if (!done) {
 #pragma omp parallel for schedule(dynamic, 1)
@@ -611,6 +674,12 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
     bp[l - 1].resize(nb / 2);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int i = 0; i < nb; ++i) {
+      double* X = &hl.X[(size_t)i * D * K];
+      if (direct[i]) {
+        std::memcpy(X, &job.X[(size_t)i * D * K], sizeof(double) * (size_t)D * K);
+        for (int a = 0; a < K; ++a) hl.SK[(size_t)i * K + a] = job.SK[(size_t)i * K + a];
+        continue;
+      }
       const std::vector<double>& R = Rb[i];
       const std::vector<int>& piv = pivs[i];
       int n = (int)bp[l][i].size();
@@ -627,7 +696,6 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
           T[(size_t)t * m + b] = s / d;
         }
       }
-      double* X = &hl.X[(size_t)i * D * K];
       for (int a = 0; a < K; ++a) X[(size_t)piv[a] * K + a] = 1.0;
       for (int b = 0; b < m; ++b)
         for (int a = 0; a < K; ++a) X[(size_t)piv[K + b] * K + a] = T[(size_t)a * m + b];

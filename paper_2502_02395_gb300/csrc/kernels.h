@@ -48,14 +48,17 @@ void launch_merge(int D, int K, int64_t NP, const T* Ahat, const int32_t* ni, co
 // kernels_tc.cu: tensor-core (tcgen05 + TMA) batched GEMM
 //   C_b = alpha * (*alpha_dev) * A_b B_b^T, A_b = matrix ia[b] (rowsA x K,
 //   K-major, 16-bit) of the nA-matrix array A, B_b likewise, FP32
-//   accumulation; out_mode 0: FP32 row-major C, 1: 16-bit C^T.
+//   accumulation; out_mode 0: FP32 row-major C, 1: 16-bit C^T, 3: FP32
+//   C += result (read-modify-write).
 // gemm_tc returns false (and launches nothing) for unsupported shapes.
 bool gemm_tc_supported(int M, int N, int K, int lda, int ldb, int ldc);
 bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int rowsA, int lda, const int32_t* ia,
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
              int64_t batch, int32_t* err, cudaStream_t st, void* C2 = nullptr, int qsplit = -1,
-             const int32_t* qi = nullptr, const int32_t* qj = nullptr, unsigned int* amax_ss = nullptr);
+             const int32_t* qi = nullptr, const int32_t* qj = nullptr, unsigned int* amax_ss = nullptr,
+             int64_t rowsA_total = 0);  // rowsA_total > 0: the rows A's tensor map spans (else nA * rowsA)
+void launch_inv_scale_pair(const float* a, const float* b, float* out, cudaStream_t st);  // out = 1 / (a b)
 // 2-D tensor map over a rows x cols 16-bit array (row stride ld elements)
 // with box_rows x box_cols tiles, no swizzle (dense row-major tiles in
 // shared memory).  False if the driver or the shape does not allow it.

@@ -70,7 +70,7 @@ struct TcArgs {
   int64_t sC;
   const int32_t* ic;
   int ldc;
-  int out_mode;  // 0: FP32 row-major; 1: 16-bit transposed (C^T row-major, ld = ldc)
+  int out_mode;  // 0: FP32 row-major; 1: 16-bit transposed (C^T row-major, ld = ldc); 3: FP32 C += result
   int out_bf16;  // 16-bit output type for out_mode 1
   float alpha;
   const float* alpha_dev;
@@ -231,6 +231,17 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
           o2[0] = make_uint4(h[0], h[1], h[2], h[3]);
           o2[1] = make_uint4(h[4], h[5], h[6], h[7]);
         }
+      } else if (p.out_mode == 3) {
+        float* out = reinterpret_cast<float*>(Cb) + cbase + (int64_t)m * p.ldc + n0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          float4 v = *reinterpret_cast<float4*>(out + j);
+          v.x = fmaf(__uint_as_float(r[j]), alpha, v.x);
+          v.y = fmaf(__uint_as_float(r[j + 1]), alpha, v.y);
+          v.z = fmaf(__uint_as_float(r[j + 2]), alpha, v.z);
+          v.w = fmaf(__uint_as_float(r[j + 3]), alpha, v.w);
+          *reinterpret_cast<float4*>(out + j) = v;
+        }
       } else if (p.out_bf16) {
         __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Cb) + cbase;
 #pragma unroll
@@ -325,12 +336,14 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
              int64_t batch, int32_t* err, cudaStream_t st, void* C2, int qsplit, const int32_t* qi,
-             const int32_t* qj, unsigned int* amax_ss) {
+             const int32_t* qj, unsigned int* amax_ss, int64_t rowsA_total) {
   if (batch == 0) return true;
   if (!gemm_tc_supported(M, N, K, lda, ldb, ldc)) return false;
-  if ((uint64_t)nA * rowsA >= (1ull << 31) || (uint64_t)nB * rowsB >= (1ull << 31)) return false;
+  const uint64_t ra = rowsA_total > 0 ? (uint64_t)rowsA_total : (uint64_t)nA * rowsA;
+  if (ra >= (1ull << 31) || (uint64_t)nB * rowsB >= (1ull << 31)) return false;
+  if (out_mode == 3 && (ldc % 4 || (reinterpret_cast<uintptr_t>(C) & 15))) return false;
   CUtensorMap ta, tb;
-  if (!make_map(&ta, A, ab_bf16, (uint64_t)nA * rowsA, (uint64_t)K, (uint64_t)lda, TC_BM)) return false;
+  if (!make_map(&ta, A, ab_bf16, ra, (uint64_t)K, (uint64_t)lda, TC_BM)) return false;
   if (!make_map(&tb, B, ab_bf16, (uint64_t)nB * rowsB, (uint64_t)K, (uint64_t)ldb, (uint32_t)N)) return false;
   TcArgs p{};
   p.M = M;
@@ -462,6 +475,16 @@ __global__ void inv_scale_product_kernel(const float* __restrict__ a, const floa
 void launch_inv_scale_product(const float* a, const float* b, float* out, cudaStream_t st) {
   ++g_launches;
   inv_scale_product_kernel<<<1, 1, 0, st>>>(a, b, out);
+}
+
+// out[0] = 1 / (a[0] * b[0])  (the inverse scale of a product of two scaled operands)
+__global__ void inv_scale_pair_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                      float* __restrict__ out) {
+  out[0] = 1.0f / (a[0] * b[0]);
+}
+void launch_inv_scale_pair(const float* a, const float* b, float* out, cudaStream_t st) {
+  ++g_launches;
+  inv_scale_pair_kernel<<<1, 1, 0, st>>>(a, b, out);
 }
 
 // out16[e] = (16-bit) (in[e] * scale[0])

@@ -41,9 +41,10 @@ YUKAWA = ("yukawa_eps", dict(diag_shift=1.0))
 CASES = {
     "cube8192_yukawa": (8192, 256, 1024, 64, 5) + YUKAWA,
     "cube32768_yukawa": (32768, 256, 1024, 64, 5) + YUKAWA,
-    # a Gaussian kernel exp(-r^2 / 0.04) + 0.01 on the diagonal: the RR blocks
-    # are far from diagonal, so the self Schur update of Eq. 21 is large
-    "cube2048_gauss": (2048, 128, 512, 64, 7, "gaussian", dict(ell=0.2, diag_shift=0.01)),
+    # a Gaussian kernel exp(-r^2 / 0.0225) + 0.01 on the diagonal, leaf 256,
+    # rank 128: the RR blocks are far from diagonal, so the self Schur update
+    # of Eq. 21 is 9 - 51 % of the result
+    "cube4096_gauss": (4096, 256, 512, 64, 7, "gaussian", dict(ell=0.15, diag_shift=0.01)),
 }
 MAIN = ["cube8192_yukawa", "cube32768_yukawa"]
 
@@ -160,14 +161,16 @@ def test_mixed_schur_update_leaf(B):
     factorization: the stored SS quadrant of Ahat_ii equals
     (U_i^T A_ii U_i)^SS - SR (RR)^-1 RS, evaluated in FP64 from the library's
     FP32 bases and its own RR, RS, SR quadrants, to the 16-bit rounding of
-    the projection (4e-3 relative, the leaf projection test's bound).  On the
-    Gaussian case the update is 2 - 20 % of the result, so leaving it out or
-    applying it with a wrong sign fails the bound."""
-    name = "cube2048_gauss"
+    the projection (4e-3 relative, the leaf projection test's bound).  The
+    update runs on the tensor cores (16-bit (Ahat_ii^RR)^-1 and Z^T, FP32
+    accumulation); on this Gaussian case it is 9 - 51 % of the result, so
+    leaving it out or applying it with a wrong sign fails the bound."""
+    name = "cube4096_gauss"
     H, F, flat, b = oracle_case(name)
     S = solver(B, name)
     S.factor("fp16")
-    assert S.stats()["tensor_cores"] is True
+    st = S.stats()
+    assert st["tensor_cores"] is True and st["schur_tensor_cores"] is True
     L = H["L"]
     D, K = H["D"][L], H["K"][L]
     R, nb = D - K, 1 << L
