@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the single-system step: a batch of this many Gaussian-covariance systems of "
                          "uneven size (workloads.batch_systems), factored and solved concurrently")
+    ap.add_argument("--tc-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor-core GEMM form: 0 one CTA per entry, 1 persistent grid, 2 warp-specialized")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay the FP32 substitution as a CUDA graph (1) or launch it kernel by kernel (0)")
     return ap.parse_args()
@@ -287,7 +289,8 @@ def roofline_for(phase, stats, t_phase, calls, peaks, prec, tc, fp64_tf):
 
 def run_batch(args):
     """--batch S: S independent Gaussian-covariance systems (N log-uniform
-    in [4096, 65536], l in [0.05, 0.5], leaf 128 / 256, tol 1e-8), FP16
+    in [4096, 65536], l in [0.05, 0.5], + I on the diagonal, leaf 128 / 256,
+    tol 1e-8), FP16
     factorizations refined to --target, run by the library's worker pool
     with the worker count its tuner picks; one JSON line."""
     import torch
@@ -301,7 +304,7 @@ def run_batch(args):
     solvers, rhs = [], []
     for sp in specs:
         P = W.cube_points(sp["n"], sp["point_seed"])
-        solvers.append(H2Solver.build(P, kernel="gaussian", ell=sp["ell"], diag_shift=0.01, leaf=sp["leaf"], eta=1.0,
+        solvers.append(H2Solver.build(P, kernel="gaussian", ell=sp["ell"], diag_shift=sp["shift"], leaf=sp["leaf"], eta=1.0,
                                       tol=1e-8, far_samples=1024, near_samples=64))
         rhs.append(torch.from_numpy(W.uniform_rhs(sp["n"], sp["rhs_seed"])).cuda())
     build_s = time.perf_counter() - t0
@@ -373,6 +376,7 @@ def main():
     S.set_option("rr_lu_fp64", 1 if args.rr_lu == "fp64" else 0)
     S.set_option("residual_fp64", 1 if args.residual == "fp64" else 0)
     S.set_option("graphs", args.graphs)
+    S.set_option("tc_kernel", args.tc_kernel)
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.zeros_like(b_dev)
     torch.cuda.synchronize()
@@ -494,7 +498,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "no flush: inputs (13 GB leaf blocks, factors) exceed L2"},
         "relres": float(np.max(rels)), "relres_fp64_matvec": r_check, "iters": int(np.max(its_all)),
-        "rr_lu": args.rr_lu, "residual": args.residual, "graphs": args.graphs,
+        "rr_lu": args.rr_lu, "residual": args.residual, "graphs": args.graphs, "tc_kernel": args.tc_kernel,
         "phases_s": ph, "build_s": build_s, "fp64": fp64,
         "speedup_vs_fp64": (fp64["s_per_step"] / value) if fp64 else None,
         "roofline": roof, "rooflines": roofs, "fp64_peak_tflops": fp64_tf, "calls": calls,

@@ -275,10 +275,23 @@ h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
  *                         as a CUDA graph (on a private stream) and replayed
  *                         for every preconditioner application; 0: plain
  *                         launches.  A capture that fails falls back to
- *                         plain launches. */
-typedef enum { H2_OPT_RR_LU_FP64 = 0, H2_OPT_RESIDUAL_FP64 = 1, H2_OPT_GRAPHS = 2 } h2_option;
+ *                         plain launches.
+ *   H2_OPT_TC_KERNEL      the tensor-core GEMMs' kernel form (process-wide,
+ *                         all contexts): 0 (default) one CTA per batch
+ *                         entry; 1 a persistent grid of two CTAs per SM
+ *                         looping over the entries; 2 a persistent
+ *                         warp-specialized kernel, one CTA per SM, whose
+ *                         epilogue of one tile overlaps the MMAs of the next
+ *                         (two TMEM accumulators). */
+typedef enum {
+  H2_OPT_RR_LU_FP64 = 0,
+  H2_OPT_RESIDUAL_FP64 = 1,
+  H2_OPT_GRAPHS = 2,
+  H2_OPT_TC_KERNEL = 3
+} h2_option;
 
-/* Set an h2_option to value (0 or 1).  Errors: H2_ERR_INVALID_ARG. */
+/* Set an h2_option to value (0 or 1; 0 .. 2 for H2_OPT_TC_KERNEL).
+ * Errors: H2_ERR_INVALID_ARG. */
 h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value);
 
 /* y = A_H2 x in one of the library's three matvec arithmetics (the same

@@ -1859,13 +1859,20 @@ h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart) {
 h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value) {
   if (!c) return H2_ERR_INVALID_ARG;
   c->err.clear();
-  if (value != 0 && value != 1) {
+  if ((value != 0 && value != 1) && option != H2_OPT_TC_KERNEL) {
     c->err = "option value must be 0 or 1";
     return H2_ERR_INVALID_ARG;
   }
   switch (option) {
     case H2_OPT_RR_LU_FP64: c->rr_lu64 = value != 0; return H2_OK;
     case H2_OPT_RESIDUAL_FP64: c->resid64 = value != 0; return H2_OK;
+    case H2_OPT_TC_KERNEL:
+      if (value < 0 || value > 2) {
+        c->err = "tensor-core kernel form outside 0..2";
+        return H2_ERR_INVALID_ARG;
+      }
+      g_tc_kernel = (int)value;
+      return H2_OK;
     case H2_OPT_GRAPHS:
       c->use_graphs = value != 0;
       drop_graphs(c);

@@ -9,6 +9,10 @@ namespace h2 {
 
 // Number of kernels this library has launched (reported by h2_stats).
 extern std::atomic<long long> g_launches;
+// Tensor-core GEMM kernel form, process-wide (H2_OPT_TC_KERNEL): 0 one CTA
+// per batch entry, 1 a persistent grid of two CTAs per SM, 2 the persistent
+// warp-specialized kernel with two TMEM accumulators.
+extern std::atomic<int> g_tc_kernel;
 
 // kernels_factor.cu
 void launch_eval_blocks(const KernelFn& G, const double* pts, int64_t npairs, const int32_t* pi,

@@ -28,6 +28,8 @@
 
 namespace h2 {
 
+std::atomic<int> g_tc_kernel{0};
+
 namespace {
 
 constexpr int TC_BM = 128;
@@ -90,6 +92,82 @@ struct TcArgs {
   // entries, accumulated by atomicMax on the float bits (the merge's scale)
   unsigned int* amax_ss;
 };
+
+// Epilogue of one output row m of batch entry b: reads the row's N
+// accumulator columns from TMEM (lane_addr: this warp's lane quarter) in
+// 16-column chunks and stores them in the output mode of p.  Every lane of
+// the warp must call it (tcgen05.ld is warp-collective); rows m >= M and
+// failed tiles (ok false) store nothing.  Returns max |FP32 output| over the
+// SS quadrant of an off-diagonal split entry (0 otherwise).
+__device__ __forceinline__ float tc_epilogue_row(const TcArgs& p, int64_t b, int m, uint32_t lane_addr, bool ok) {
+  const float alpha = p.alpha * (p.alpha_dev ? *p.alpha_dev : 1.0f);
+  char* Cb = reinterpret_cast<char*>(p.C);
+  const int64_t cbase = (int64_t)(p.ic ? p.ic[b] : (int)b) * p.sC;
+  const bool split = p.qsplit >= 0 && p.qi[b] != p.qj[b];
+  float ss_max = 0.0f;
+  for (int n0 = 0; n0 < p.N; n0 += 16) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(lane_addr + (uint32_t)n0));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (!ok || m >= p.M) continue;
+    if (p.out_mode == 0) {
+      const bool ss = (m >= p.qsplit) && (n0 >= p.qsplit);
+      if (!split || ss) {
+        float* out = reinterpret_cast<float*>(Cb) + cbase + (int64_t)m * p.ldc + n0;
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          float4 v = make_float4(__uint_as_float(r[j]) * alpha, __uint_as_float(r[j + 1]) * alpha,
+                                 __uint_as_float(r[j + 2]) * alpha, __uint_as_float(r[j + 3]) * alpha);
+          *reinterpret_cast<float4*>(out + j) = v;
+          if (split)
+            ss_max = fmaxf(ss_max, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+      }
+      if (p.C2 && !(p.qsplit >= 0 && ss)) {
+        uint32_t h[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const float a0 = __uint_as_float(r[j]), a1 = __uint_as_float(r[j + 1]);
+          if (p.c2_bf16) {
+            __nv_bfloat162 t = __floats2bfloat162_rn(a0, a1);
+            h[j / 2] = *reinterpret_cast<uint32_t*>(&t);
+          } else {
+            __half2 t = __floats2half2_rn(a0, a1);
+            h[j / 2] = *reinterpret_cast<uint32_t*>(&t);
+          }
+        }
+        uint4* o2 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(p.C2) + cbase + (int64_t)m * p.ldc + n0);
+        o2[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        o2[1] = make_uint4(h[4], h[5], h[6], h[7]);
+      }
+    } else if (p.out_mode == 3) {
+      float* out = reinterpret_cast<float*>(Cb) + cbase + (int64_t)m * p.ldc + n0;
+#pragma unroll
+      for (int j = 0; j < 16; j += 4) {
+        float4 v = *reinterpret_cast<float4*>(out + j);
+        v.x = fmaf(__uint_as_float(r[j]), alpha, v.x);
+        v.y = fmaf(__uint_as_float(r[j + 1]), alpha, v.y);
+        v.z = fmaf(__uint_as_float(r[j + 2]), alpha, v.z);
+        v.w = fmaf(__uint_as_float(r[j + 3]), alpha, v.w);
+        *reinterpret_cast<float4*>(out + j) = v;
+      }
+    } else if (p.out_bf16) {
+      __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Cb) + cbase;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        out[(int64_t)(n0 + j) * p.ldc + m] = __float2bfloat16_rn(__uint_as_float(r[j]) * alpha);
+    } else {
+      __half* out = reinterpret_cast<__half*>(Cb) + cbase;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) out[(int64_t)(n0 + j) * p.ldc + m] = __float2half_rn(__uint_as_float(r[j]) * alpha);
+    }
+  }
+  return ss_max;
+}
 
 __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                                                       const __grid_constant__ CUtensorMap tmB, TcArgs p,
@@ -185,74 +263,10 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
     bool ok = mbar_wait(&done_bar, it_count & 1);
     if (!ok) fail_sh = 1;
     tc_fence_after();
-    const float alpha = p.alpha * (p.alpha_dev ? *p.alpha_dev : 1.0f);
     const int m = m0 + tid;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    char* Cb = reinterpret_cast<char*>(p.C);
-    const int64_t cbase = (int64_t)(p.ic ? p.ic[b] : (int)b) * p.sC;
     const bool split = p.qsplit >= 0 && p.qi[b] != p.qj[b];
-    float ss_max = 0.0f;
-    for (int n0 = 0; n0 < p.N; n0 += 16) {
-      uint32_t r[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(lane_addr + (uint32_t)n0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (!ok || m >= p.M) continue;
-      if (p.out_mode == 0) {
-        const bool ss = (m >= p.qsplit) && (n0 >= p.qsplit);
-        if (!split || ss) {
-          float* out = reinterpret_cast<float*>(Cb) + cbase + (int64_t)m * p.ldc + n0;
-#pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            float4 v = make_float4(__uint_as_float(r[j]) * alpha, __uint_as_float(r[j + 1]) * alpha,
-                                   __uint_as_float(r[j + 2]) * alpha, __uint_as_float(r[j + 3]) * alpha);
-            *reinterpret_cast<float4*>(out + j) = v;
-            if (split)
-              ss_max = fmaxf(ss_max, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-          }
-        }
-        if (p.C2 && !(p.qsplit >= 0 && ss)) {
-          uint32_t h[8];
-#pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            const float a0 = __uint_as_float(r[j]), a1 = __uint_as_float(r[j + 1]);
-            if (p.c2_bf16) {
-              __nv_bfloat162 t = __floats2bfloat162_rn(a0, a1);
-              h[j / 2] = *reinterpret_cast<uint32_t*>(&t);
-            } else {
-              __half2 t = __floats2half2_rn(a0, a1);
-              h[j / 2] = *reinterpret_cast<uint32_t*>(&t);
-            }
-          }
-          uint4* o2 = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(p.C2) + cbase + (int64_t)m * p.ldc + n0);
-          o2[0] = make_uint4(h[0], h[1], h[2], h[3]);
-          o2[1] = make_uint4(h[4], h[5], h[6], h[7]);
-        }
-      } else if (p.out_mode == 3) {
-        float* out = reinterpret_cast<float*>(Cb) + cbase + (int64_t)m * p.ldc + n0;
-#pragma unroll
-        for (int j = 0; j < 16; j += 4) {
-          float4 v = *reinterpret_cast<float4*>(out + j);
-          v.x = fmaf(__uint_as_float(r[j]), alpha, v.x);
-          v.y = fmaf(__uint_as_float(r[j + 1]), alpha, v.y);
-          v.z = fmaf(__uint_as_float(r[j + 2]), alpha, v.z);
-          v.w = fmaf(__uint_as_float(r[j + 3]), alpha, v.w);
-          *reinterpret_cast<float4*>(out + j) = v;
-        }
-      } else if (p.out_bf16) {
-        __nv_bfloat16* out = reinterpret_cast<__nv_bfloat16*>(Cb) + cbase;
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-          out[(int64_t)(n0 + j) * p.ldc + m] = __float2bfloat16_rn(__uint_as_float(r[j]) * alpha);
-      } else {
-        __half* out = reinterpret_cast<__half*>(Cb) + cbase;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) out[(int64_t)(n0 + j) * p.ldc + m] = __float2half_rn(__uint_as_float(r[j]) * alpha);
-      }
-    }
+    float ss_max = tc_epilogue_row(p, b, m, lane_addr, ok);
     if (p.amax_ss && split) {
       for (int o = 16; o; o >>= 1) ss_max = fmaxf(ss_max, __shfl_xor_sync(0xffffffffu, ss_max, o));
       if (lane == 0 && ss_max > 0.0f) atomicMax(p.amax_ss, __float_as_uint(ss_max));
@@ -270,6 +284,187 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------------
+// The same GEMM as a persistent, warp-specialized kernel: one CTA per SM
+// loops over (M tile, batch entry) tiles.  Warp 0 (one thread) streams the
+// K slices with TMA through a WS_STAGES ring; warp 1 allocates two FP32
+// accumulators in TMEM (2 x N columns) and one thread issues the MMAs,
+// alternating accumulators tile by tile; warps 2-5 run the epilogue of
+// tile t (warp w reads TMEM lane quarter w % 4) while the MMAs of tile t + 1
+// fill the other accumulator, and release it with 128 arrivals on acc_empty.
+// Every wait is bounded as in tc_gemm_kernel; on expiry the role records
+// the failure and stops, the MMAs are drained through a final commit, the
+// producer's copies in flight are waited for, and TMEM is freed.
+// ------------------------------------------------------------------------
+constexpr int WS_STAGES = 4;
+
+__global__ void __launch_bounds__(192, 1) tc_gemm_ws_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                            const __grid_constant__ CUtensorMap tmB, TcArgs p,
+                                                            int64_t batch) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[WS_STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[WS_STAGES];
+  __shared__ __align__(8) uint64_t accf[2];
+  __shared__ __align__(8) uint64_t acce[2];
+  __shared__ __align__(8) uint64_t fin_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int fail_sh;
+  __shared__ uint32_t issued_sh;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  uint8_t* base = smem_raw + pad;
+  const uint32_t a_bytes = TC_BM * TC_BK * 2;
+  const uint32_t b_bytes = (uint32_t)p.N * TC_BK * 2;
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  const int kblocks = p.K / TC_BK;
+  const int mtiles = p.M / TC_BM;
+  const int64_t ntiles = batch * mtiles;
+  const uint32_t cols = p.tmem_cols;  // one accumulator; two are allocated
+
+  if (tid == 0) {
+    for (int s = 0; s < WS_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&accf[k], 1);
+      mbar_init(&acce[k], 128);
+    }
+    mbar_init(&fin_bar, 1);
+    fail_sh = 0;
+    issued_sh = 0;
+    mbar_init_fence();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(2 * cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t idesc = idesc_f16(p.ab_bf16, TC_BM, p.N);
+  volatile int* fail = &fail_sh;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t u = 0;
+      for (int64_t t = blockIdx.x; t < ntiles && !*fail; t += gridDim.x) {
+        const int64_t b = t / mtiles;
+        const int m0 = (int)(t % mtiles) * TC_BM;
+        const int rowA = (p.ia ? p.ia[b] : (int)b) * p.rowsA + m0;
+        const int rowB = (p.ib ? p.ib[b] : (int)b) * p.rowsB;
+        for (int kb = 0; kb < kblocks; ++kb, ++u) {
+          const int s = u % WS_STAGES;
+          if (u >= WS_STAGES && !mbar_wait(&empty_bar[s], ((u / WS_STAGES) - 1) & 1)) {
+            *fail = 1;
+            break;
+          }
+          uint8_t* sa = base + s * stage_bytes;
+          mbar_expect_tx(&full_bar[s], stage_bytes);
+          tma_load_2d(sa, &tmA, &full_bar[s], kb * TC_BK, rowA);
+          tma_load_2d(sa + a_bytes, &tmB, &full_bar[s], kb * TC_BK, rowB);
+        }
+      }
+      issued_sh = u;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      uint32_t u = 0, lt = 0;
+      for (int64_t t = blockIdx.x; t < ntiles && !*fail; t += gridDim.x, ++lt) {
+        const uint32_t buf = lt & 1;
+        if (lt >= 2 && !mbar_wait(&acce[buf], ((lt / 2) - 1) & 1)) {
+          *fail = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t acc_addr = tmem + buf * cols;
+        bool ok = true;
+        for (int kb = 0; kb < kblocks; ++kb, ++u) {
+          const int s = u % WS_STAGES;
+          if (!mbar_wait(&full_bar[s], (u / WS_STAGES) & 1)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(base + s * stage_bytes);
+          const uint64_t da = smem_desc_sw128(sa);
+          const uint64_t db = smem_desc_sw128(sa + a_bytes);
+#pragma unroll
+          for (int k = 0; k < TC_BK / 16; ++k) {
+            const uint64_t off = (uint64_t)((k * 32) >> 4);
+            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(acc_addr),
+                "l"(da + off), "l"(db + off), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty_bar[s]))
+                       : "memory");
+        }
+        if (!ok) {
+          *fail = 1;
+          break;
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&accf[buf]))
+                     : "memory");
+      }
+      // every MMA issued so far completes before fin_bar's first phase
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&fin_bar))
+                   : "memory");
+      if (!mbar_wait(&fin_bar, 0)) *fail = 1;
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    uint32_t lt = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const uint32_t buf = lt & 1;
+      const bool ok = mbar_wait(&accf[buf], (lt / 2) & 1);
+      tc_fence_after();
+      const int64_t b = t / mtiles;
+      const int m = (int)(t % mtiles) * TC_BM + row;
+      float ss_max = tc_epilogue_row(p, b, m, tmem + buf * cols + lane_off, ok);
+      if (p.amax_ss && p.qsplit >= 0 && p.qi[b] != p.qj[b]) {
+        for (int o = 16; o; o >>= 1) ss_max = fmaxf(ss_max, __shfl_xor_sync(0xffffffffu, ss_max, o));
+        if (lane == 0 && ss_max > 0.0f) atomicMax(p.amax_ss, __float_as_uint(ss_max));
+      }
+      tc_fence_before();
+      mbar_arrive(&acce[buf]);
+      if (!ok) {
+        *fail = 1;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (fail_sh && tid == 0) {
+    atomicExch(p.err, 1);
+    // wait for the producer's copies in flight: stage s was armed
+    // ceil((issued - s) / WS_STAGES) times; its last phase must complete
+    const uint32_t issued = issued_sh;
+    for (int s = 0; s < WS_STAGES; ++s)
+      if (issued > (uint32_t)s) {
+        const uint32_t uses = (issued - s + WS_STAGES - 1) / WS_STAGES;
+        mbar_wait(&full_bar[s], (uses - 1) & 1);
+      }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * cols) : "memory");
   }
 }
 
@@ -382,7 +577,25 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
   const size_t max_ctas = 512 / cols;
   smem = std::max(smem, per_sm / (max_ctas + 1) + 1024);
   cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid(M / TC_BM, (unsigned)std::min<int64_t>(batch, 65535));
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int mode = g_tc_kernel.load();
+  if (mode == 2 && 2 * cols <= 512) {
+    // persistent warp-specialized kernel: one CTA per SM (TMEM holds two
+    // accumulators), WS_STAGES-deep ring
+    const size_t sm_ws = (size_t)WS_STAGES * (TC_BM * TC_BK * 2 + (size_t)N * TC_BK * 2) + 1024;
+    cudaFuncSetAttribute(tc_gemm_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ws);
+    const int64_t ntiles = batch * (M / TC_BM);
+    ++g_launches;
+    tc_gemm_ws_kernel<<<(unsigned)std::min<int64_t>(ntiles, nsm), 192, sm_ws, st>>>(ta, tb, p, batch);
+    return true;
+  }
+  // one CTA per batch entry (mode 0), or a persistent grid of two CTAs per
+  // SM looping over the entries (mode 1)
+  int64_t gy = std::min<int64_t>(batch, 65535);
+  if (mode == 1) gy = std::min<int64_t>(gy, std::max<int64_t>(1, (int64_t)nsm * 2 / (M / TC_BM)));
+  dim3 grid(M / TC_BM, (unsigned)gy);
   ++g_launches;
   tc_gemm_kernel<<<grid, 128, smem, st>>>(ta, tb, p, batch);
   return true;

@@ -228,16 +228,23 @@ def test_mixed_complement_bases(B, name):
     S.close()
 
 
+@pytest.mark.parametrize("tc_kernel", [0, 1, 2])
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
-def test_tensor_core_projection_leaf(B, prec):
+def test_tensor_core_projection_leaf(B, prec, tc_kernel):
     """Leaf-level projected blocks of the mixed path (tcgen05 GEMMs with
     16-bit inputs, FP32 accumulation) against U^T A U in FP64 with the
     library's own FP32 bases: the error is the 16-bit rounding of the
     operands, 2^-11 (FP16) or 2^-8 (BF16) relative, grown by at most a few
-    times over a 256-term sum."""
+    times over a 256-term sum.  Run with each form of the GEMM kernel: one
+    CTA per batch entry, a persistent grid, and the persistent
+    warp-specialized kernel with two TMEM accumulators."""
     H, F, flat, b = oracle_case("cube8192_yukawa")
     S = lib_case(B, "cube8192_yukawa")
-    S.factor(prec)
+    S.set_option("tc_kernel", tc_kernel)  # one CTA per entry / persistent / warp-specialized
+    try:
+        S.factor(prec)
+    finally:
+        S.set_option("tc_kernel", 0)
     st = S.stats()
     assert st["tensor_cores"] is True
     L = H["L"]

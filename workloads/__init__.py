@@ -125,10 +125,11 @@ def batch_systems(count: int = 64, seed: int = 100, n_min: int = 4096, n_max: in
     l_s ~ U[0.05, 0.5] (both drawn from `seed`), points uniform in the unit
     cube with seed 1000 + s, right-hand side seed 2000 + s, leaf 256 when
     N_s >= 16384 else 128.  Returns a list of dicts (n, ell, leaf,
-    point_seed, rhs_seed); kernel exp(-r^2 / l^2) with 1e-2 added to the
-    diagonal, tolerance 1e-8."""
+    point_seed, rhs_seed, shift); kernel exp(-r^2 / l^2) with `shift` added
+    to the diagonal (1.0: with 1e-2 the H^2-ULV preconditioner of the
+    FP64 oracle itself stalls for l around 0.1 - 0.4), tolerance 1e-8."""
     rng = np.random.default_rng(seed)
     ns = np.rint(np.exp(rng.uniform(np.log(n_min), np.log(n_max), count))).astype(int)
     ells = rng.uniform(0.05, 0.5, count)
-    return [dict(n=int(n), ell=float(e), leaf=256 if n >= 16384 else 128, point_seed=1000 + s, rhs_seed=2000 + s)
-            for s, (n, e) in enumerate(zip(ns, ells))]
+    return [dict(n=int(n), ell=float(e), leaf=256 if n >= 16384 else 128, point_seed=1000 + s, rhs_seed=2000 + s,
+                 shift=1.0) for s, (n, e) in enumerate(zip(ns, ells))]
