@@ -468,8 +468,9 @@ h2_status h2_batch_run(h2_batch* b, int32_t prec, const double* const* B, double
 
 /* Autotune the worker count: run the whole batch (factor and solve) with
  * 1, 2, 4, 8 and 16 workers (up to twice the system count) and keep the
- * fastest; *workers_out (may be NULL) receives it.  Errors: as
- * h2_batch_run. */
+ * fastest; *workers_out (may be NULL) receives it.  A system that stops
+ * above the target does not end the tuning (H2_ERR_NOT_CONVERGED is
+ * returned at the end).  Errors: as h2_batch_run. */
 h2_status h2_batch_tune(h2_batch* b, int32_t prec, const double* const* B, double* const* X, double target,
                         int32_t max_iters, int32_t* workers_out);
 

@@ -388,9 +388,10 @@ class H2Batch:
             m = lib().h2_batch_last_error(self.b)
             raise H2Error(st, m.decode() if m else "")
 
-    def run(self, prec="fp16", B=None, target=1e-10, max_iters=100):
+    def run(self, prec="fp16", B=None, target=1e-10, max_iters=100, check=True):
         """Factor all systems (prec None: keep) and solve each for B[i];
-        returns (X list, relres, iters, seconds)."""
+        returns (X list, relres, iters, seconds).  check=False: a system
+        that stops above the target does not raise (see relres)."""
         n = len(self.solvers)
         p = -1 if prec is None else PRECS[prec]
         rel = (ctypes.c_double * n)()
@@ -405,15 +406,18 @@ class H2Batch:
                                     ctypes.cast(its, ctypes.c_void_p), ctypes.byref(sec))
         else:
             st = lib().h2_batch_run(self.b, p, None, None, target, max_iters, None, None, ctypes.byref(sec))
-        self._err(st)
+        if check or st != -4:
+            self._err(st)
         return X, list(rel), list(its), sec.value
 
-    def tune(self, prec="fp16", B=None, target=1e-10, max_iters=100):
+    def tune(self, prec="fp16", B=None, target=1e-10, max_iters=100, check=True):
         X = [np.zeros_like(b) if isinstance(b, np.ndarray) else b.new_zeros(b.shape) for b in B]
         pb, px = self._ptrs(B), self._ptrs(X)
         w = ctypes.c_int32()
-        self._err(lib().h2_batch_tune(self.b, PRECS[prec], ctypes.cast(pb, ctypes.c_void_p),
-                                      ctypes.cast(px, ctypes.c_void_p), target, max_iters, ctypes.byref(w)))
+        st = lib().h2_batch_tune(self.b, PRECS[prec], ctypes.cast(pb, ctypes.c_void_p), ctypes.cast(px, ctypes.c_void_p),
+                                 target, max_iters, ctypes.byref(w))
+        if check or st != -4:
+            self._err(st)
         return w.value
 
     def stats(self) -> dict:

@@ -123,16 +123,19 @@ h2_status h2_batch_tune(h2_batch* b, int32_t prec, const double* const* B, doubl
   const int cand[5] = {1, 2, 4, 8, 16};
   double best = INFINITY;
   int bw = b->workers;
+  h2_status last = H2_OK;
   for (int k = 0; k < 5; ++k) {
     if (cand[k] > 2 * (int)b->ctx.size()) break;
+    // a system that stops above the target still gives a timing
     h2_status s = run(b, cand[k], prec, B, X, target, max_iters, nullptr, nullptr);
-    if (s != H2_OK) return s;
+    if (s != H2_OK && s != H2_ERR_NOT_CONVERGED) return s;
+    last = s;
     b->tune_seconds[k] = b->last_seconds;
     if (b->last_seconds < best) best = b->last_seconds, bw = cand[k];
   }
   b->workers = bw;
   if (workers_out) *workers_out = bw;
-  return H2_OK;
+  return last;
 }
 
 h2_status h2_batch_stats(const h2_batch* b, char* json, size_t cap) {

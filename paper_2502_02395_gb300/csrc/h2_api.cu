@@ -670,9 +670,11 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
       launch_to_lowp<T>(bf16, f.Tm, f.T16, d.nb * KK, F.tscale + 2 * l, sc);
       launch_inv_scale_product(d.S16_scale[bf16], F.tscale + 2 * l, F.cscale + l, sc);
       bool ok = gemm_tc(bf16, K, K, K, d.S16[bf16], d.FP, K, K, nullptr, f.T16, d.nb, K, K, d.far_j, F.W16c, KK,
-                        nullptr, K, 1, bf16, 1.0f, nullptr, d.FP, c->status + 2, sc) &&
+                        nullptr, K, 1, bf16, 1.0f, nullptr, d.FP, c->status + 2, sc, nullptr, -1, nullptr, nullptr,
+                        nullptr, 0, 0) &&
                 gemm_tc(bf16, K, K, K, f.T16, d.nb, K, K, d.far_i, F.W16c, d.FP, K, K, nullptr, f.Shat, KK, nullptr, K,
-                        0, 0, 1.0f, F.cscale + l, d.FP, c->status + 2, sc);
+                        0, 0, 1.0f, F.cscale + l, d.FP, c->status + 2, sc, nullptr, -1, nullptr, nullptr, nullptr, 0,
+                        0);
       if (!ok) {
         coup_err = "tensor-core coupling GEMM setup failed at level " + std::to_string(l);
         break;

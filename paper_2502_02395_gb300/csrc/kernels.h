@@ -9,9 +9,12 @@ namespace h2 {
 
 // Number of kernels this library has launched (reported by h2_stats).
 extern std::atomic<long long> g_launches;
-// Tensor-core GEMM kernel form, process-wide (H2_OPT_TC_KERNEL): 0 one CTA
-// per batch entry, 1 a persistent grid of two CTAs per SM, 2 the persistent
-// warp-specialized kernel with two TMEM accumulators.
+// Tensor-core GEMM kernel form of the factorization's main chain
+// (projection, Schur update), process-wide (H2_OPT_TC_KERNEL): 0 one CTA per
+// batch entry, 1 a persistent grid of two CTAs per SM, 2 the persistent
+// warp-specialized kernel with two TMEM accumulators.  The coupling
+// products on their own stream always use form 0, so that they keep sharing
+// the SMs with the main chain.
 extern std::atomic<int> g_tc_kernel;
 
 // kernels_factor.cu
@@ -61,7 +64,8 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
              int64_t batch, int32_t* err, cudaStream_t st, void* C2 = nullptr, int qsplit = -1,
              const int32_t* qi = nullptr, const int32_t* qj = nullptr, unsigned int* amax_ss = nullptr,
-             int64_t rowsA_total = 0);  // rowsA_total > 0: the rows A's tensor map spans (else nA * rowsA)
+             int64_t rowsA_total = 0,  // rowsA_total > 0: the rows A's tensor map spans (else nA * rowsA)
+             int form = -1);           // kernel form 0 / 1 / 2 (g_tc_kernel's meaning); -1: g_tc_kernel
 void launch_inv_scale_pair(const float* a, const float* b, float* out, cudaStream_t st);  // out = 1 / (a b)
 // 2-D tensor map over a rows x cols 16-bit array (row stride ld elements)
 // with box_rows x box_cols tiles, no swizzle (dense row-major tiles in

@@ -531,7 +531,7 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
              const void* B, int64_t nB, int rowsB, int ldb, const int32_t* ib, void* C, int64_t sC,
              const int32_t* ic, int ldc, int out_mode, int out_bf16, float alpha, const float* alpha_dev,
              int64_t batch, int32_t* err, cudaStream_t st, void* C2, int qsplit, const int32_t* qi,
-             const int32_t* qj, unsigned int* amax_ss, int64_t rowsA_total) {
+             const int32_t* qj, unsigned int* amax_ss, int64_t rowsA_total, int form) {
   if (batch == 0) return true;
   if (!gemm_tc_supported(M, N, K, lda, ldb, ldc)) return false;
   const uint64_t ra = rowsA_total > 0 ? (uint64_t)rowsA_total : (uint64_t)nA * rowsA;
@@ -580,7 +580,7 @@ bool gemm_tc(int ab_bf16, int M, int N, int K, const void* A, int64_t nA, int ro
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int mode = g_tc_kernel.load();
+  const int mode = form >= 0 ? form : g_tc_kernel.load();
   if (mode == 2 && 2 * cols <= 512) {
     // persistent warp-specialized kernel: one CTA per SM (TMEM holds two
     // accumulators), WS_STAGES-deep ring
@@ -762,6 +762,72 @@ __global__ void __launch_bounds__(256) merge_lowp_kernel(int D, int K, int64_t N
   }
 }
 
+// The same merge with vector accesses, for K a multiple of 32 and 16-byte
+// aligned rows (R, D multiples of 4): a child quadrant is read as float4
+// pairs and written as 8 packed 16-bit entries per thread; a lower pair's
+// quadrant (its mirror's SS transposed) goes through 32 x 32 shared-memory
+// tiles so that both its reads and its writes stay coalesced.
+__device__ __forceinline__ uint32_t pack2_lowp(float a, float b, int bf16) {
+  if (bf16) {
+    __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&t);
+  }
+  __half2 t = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&t);
+}
+
+__global__ void __launch_bounds__(256) merge_lowp_vec_kernel(int D, int K, int64_t NP, const float* __restrict__ Ahat,
+                                                             const int32_t* __restrict__ ni,
+                                                             const int32_t* __restrict__ nj,
+                                                             const int32_t* __restrict__ ndst, int64_t FP,
+                                                             const float* __restrict__ Shat,
+                                                             const int32_t* __restrict__ fi,
+                                                             const int32_t* __restrict__ fj,
+                                                             const int32_t* __restrict__ fdst, void* __restrict__ Apar,
+                                                             const float* __restrict__ scale, int bf16,
+                                                             const int32_t* __restrict__ mirror, int skip_lower) {
+  __shared__ float t[32][33];
+  const int R = D - K, Dp = 2 * K;
+  const float s = scale[0];
+  uint16_t* out16 = reinterpret_cast<uint16_t*>(Apar);
+  for (int64_t q = blockIdx.x; q < NP + FP; q += gridDim.x) {
+    const bool nr = q < NP;
+    const int64_t qq = nr ? q : q - NP;
+    const int i = nr ? ni[qq] : fi[qq], j = nr ? nj[qq] : fj[qq];
+    if (skip_lower && (i >> 1) > (j >> 1)) continue;
+    const bool tr = nr && mirror && i > j;
+    const int64_t dst = nr ? ndst[qq] : fdst[qq];
+    const int64_t sq = tr ? (int64_t)mirror[qq] : qq;
+    const float* src = nr ? Ahat + sq * D * D + (int64_t)R * D + R : Shat + qq * K * K;
+    const int lds = nr ? D : K;
+    const int64_t obase = dst * Dp * Dp + (int64_t)(i & 1) * K * Dp + (j & 1) * K;
+    if (!tr) {
+      const int groups = K / 8;
+      for (int e = threadIdx.x; e < K * groups; e += blockDim.x) {
+        const int a = e / groups, g = e - a * groups;
+        const float4 v0 = __ldg(reinterpret_cast<const float4*>(src + (int64_t)a * lds + g * 8));
+        const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + (int64_t)a * lds + g * 8 + 4));
+        const uint4 w = make_uint4(pack2_lowp(v0.x * s, v0.y * s, bf16), pack2_lowp(v0.z * s, v0.w * s, bf16),
+                                   pack2_lowp(v1.x * s, v1.y * s, bf16), pack2_lowp(v1.z * s, v1.w * s, bf16));
+        *reinterpret_cast<uint4*>(out16 + obase + (int64_t)a * Dp + g * 8) = w;
+      }
+    } else {
+      const int nt = K / 32, x = threadIdx.x & 31, y0 = threadIdx.x >> 5;
+      for (int tile = 0; tile < nt * nt; ++tile) {
+        const int ta = tile / nt, tb = tile - ta * nt;  // output rows ta*32.., columns tb*32..
+        __syncthreads();
+        for (int y = y0; y < 32; y += 8) t[y][x] = __ldg(src + (int64_t)(tb * 32 + y) * lds + ta * 32 + x);
+        __syncthreads();
+        for (int y = y0; y < 32; y += 8) {
+          const float v = t[x][y] * s;
+          const uint16_t h = bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+          out16[obase + (int64_t)(ta * 32 + y) * Dp + tb * 32 + x] = h;
+        }
+      }
+    }
+  }
+}
+
 // 16-bit blocks of the lower pairs as their mirrors transposed:
 // A[dst[k]] = A[src[k]]^T (D x D), outside the trailing R.. x R.. (SS)
 // quadrant.  32 x 32 tiles through shared memory; blockIdx.x is the tile,
@@ -830,6 +896,9 @@ void launch_transpose16_blocks(int D, int R, int64_t n, const int32_t* dst, cons
   ++g_launches;
   transpose16_blocks_kernel<<<grid, 256, 0, st>>>(D, R, n, dst, src, reinterpret_cast<uint16_t*>(A));
 }
+// rows of Ahat's SS quadrant start on 16 bytes: D and R = D - K multiples of 4
+static bool R_aligned(int D, int K) { return D % 4 == 0 && (D - K) % 4 == 0; }
+
 void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_t* ni, const int32_t* nj,
                        const int32_t* ndst, int64_t FP, const float* Shat, const int32_t* fi, const int32_t* fj,
                        const int32_t* fdst, void* Apar, const float* scale, int bf16, cudaStream_t st,
@@ -838,6 +907,12 @@ void launch_merge_lowp(int D, int K, int64_t NP, const float* Ahat, const int32_
   if (n == 0 || K == 0) return;
   const int blocks = (int)std::min<int64_t>(n, 152 * 16);
   ++g_launches;
+  if (K % 32 == 0 && R_aligned(D, K) && (reinterpret_cast<uintptr_t>(Apar) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(Ahat) & 15) == 0 && (reinterpret_cast<uintptr_t>(Shat) & 15) == 0) {
+    merge_lowp_vec_kernel<<<blocks, 256, 0, st>>>(D, K, NP, Ahat, ni, nj, ndst, FP, Shat, fi, fj, fdst, Apar, scale,
+                                                  bf16, mirror, skip_lower);
+    return;
+  }
   merge_lowp_kernel<<<blocks, 256, 0, st>>>(D, K, NP, Ahat, ni, nj, ndst, FP, Shat, fi, fj, fdst, Apar, scale, bf16,
                                             mirror, skip_lower);
 }
