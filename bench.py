@@ -65,10 +65,12 @@ def parse():
                     help="instead of the single-system step: a batch of this many Gaussian-covariance systems of "
                          "uneven size (workloads.batch_systems), factored and solved concurrently")
     ap.add_argument("--batch-max-iters", type=int, default=600)
+    ap.add_argument("--dense-rows", type=int, default=4096,
+                    help="rows sampled for the check against the dense matrix after the timed region (0: none)")
     ap.add_argument("--build", default="plain", choices=["plain", "gpu"],
                     help="construction of the instance (untimed): the host rank-revealing pass, or the GPU "
                          "sketches at the level caps (h2_build_gpu)")
-    ap.add_argument("--tc-kernel", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--tc-kernel", type=int, default=2, choices=[0, 1, 2],
                     help="tensor-core GEMM form: 0 one CTA per entry, 1 persistent grid, 2 warp-specialized")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay the FP32 substitution as a CUDA graph (1) or launch it kernel by kernel (0)")
@@ -336,6 +338,48 @@ def run_batch(args):
         S.close()
 
 
+def kernel_rows_torch(wl, P, rows, cols):
+    """Exact entries G(P[rows], P[cols]) of the workload's kernel (FP64, on
+    the GPU), the diagonal where a row meets its own point."""
+    import torch
+    X = torch.from_numpy(P[rows]).cuda()
+    Y = torch.from_numpy(P[cols]).cuda()
+    r = torch.cdist(X, Y).double()
+    same = torch.from_numpy(rows).cuda()[:, None] == torch.from_numpy(cols).cuda()[None, :]
+    if wl.kernel == "laplace_eps":
+        G, d = 1.0 / (r + wl.eps), 1.0 / wl.eps + wl.diag_shift
+    elif wl.kernel == "yukawa_eps":
+        G, d = torch.exp(-r) / (r + wl.eps), 1.0 / wl.eps + wl.diag_shift
+    else:
+        return None
+    return torch.where(same, torch.full_like(G, d), G)
+
+
+def dense_rows_check(wl, P, b, x, S, rows=4096, chunk=16384):
+    """Accuracy against the dense matrix on sampled rows: the residual
+    ||(A x - b)[rows]|| / ||b[rows]|| of the refined solution and the H^2
+    approximation error ||(A_H2 x - A x)[rows]|| / ||(A x)[rows]||, with the
+    kernel entries of those rows evaluated exactly (all rows when N <= rows)."""
+    import torch
+    if rows <= 0:
+        return None
+    n = len(P)
+    rng = np.random.default_rng(11)
+    sel = np.arange(n) if n <= rows else np.sort(rng.choice(n, rows, replace=False))
+    Ax = torch.zeros(len(sel), dtype=torch.float64, device="cuda")
+    xd = torch.from_numpy(x).cuda()
+    for c0 in range(0, n, chunk):
+        cols = np.arange(c0, min(n, c0 + chunk))
+        G = kernel_rows_torch(wl, P, sel, cols)
+        if G is None:
+            return None
+        Ax += G @ xd[c0:c0 + len(cols)]
+    Ax = Ax.cpu().numpy()
+    h2x = S.matvec(x)[sel]
+    return {"rows": int(len(sel)), "relres_dense": float(np.linalg.norm(Ax - b[sel]) / np.linalg.norm(b[sel])),
+            "h2_vs_dense": float(np.linalg.norm(h2x - Ax) / np.linalg.norm(Ax))}
+
+
 def main():
     args = parse()
     if args.batch > 0:
@@ -440,6 +484,7 @@ def main():
     # the last step's solution checked with the FP64 H^2 matvec (h2_matvec),
     # outside the timed region
     r_check = float(np.linalg.norm(b - S.matvec(x_host)) / np.linalg.norm(b))
+    dense = dense_rows_check(wl, P, b, x_host, S, rows=args.dense_rows)
 
     # end to end through the C ABI with host buffers (H2D of b, D2H of x inside)
     xh = np.zeros_like(b)
@@ -467,7 +512,7 @@ def main():
         s64 = S.stats()
         fp64 = {"s_per_step": f0.elapsed_time(f1) / args.fp64_steps / 1e3, "relres": r64[-1][1],
                 "iters": r64[-1][2], "factor_s": s64["times"]["factor"], "solve_s": s64["times"]["solve"],
-                "phases": {p: s64["times"][p] for p in PHASES}}
+                "phases": {p: s64["times"][p] for p in PHASES}, "stats": s64}
 
     # dominant phase of the step and its roofline
     tc = stats.get("tensor_cores", False)
@@ -481,6 +526,12 @@ def main():
         roof = roofline_for(top, stats, ph[top], calls, peaks, args.prec, tc, fp64_tf)
     roofs = {p: roofline_for(p, stats, ph[p], calls, peaks, args.prec, tc, fp64_tf)
              for p in ("a1_qr", "a2_proj", "a3_lu", "solve_subst", "solve_matvec", "solve_matvec32")}
+    if fp64:
+        # the FP64 comparator's phases against the FP64 peak measured now
+        s64 = fp64.pop("stats")
+        fp64["rooflines"] = {p: roofline_for(p, s64, s64["times"][p], s64["calls"], peaks, "fp64", False, fp64_tf)
+                             for p in ("a1_qr", "a2_proj", "a3_lu", "a45_schur", "solve_subst", "solve_matvec")
+                             if s64["times"].get(p, 0) > 0}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -503,7 +554,8 @@ def main():
                    "eta": wl.eta, "tol": wl.tol, "prec": args.prec, "target_relres": args.target,
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "no flush: inputs (13 GB leaf blocks, factors) exceed L2"},
-        "relres": float(np.max(rels)), "relres_fp64_matvec": r_check, "iters": int(np.max(its_all)),
+        "relres": float(np.max(rels)), "relres_fp64_matvec": r_check, "dense_rows_check": dense,
+        "iters": int(np.max(its_all)),
         "rr_lu": args.rr_lu, "residual": args.residual, "graphs": args.graphs, "tc_kernel": args.tc_kernel,
         "phases_s": ph, "build_s": build_s, "build": args.build, "fp64": fp64,
         "speedup_vs_fp64": (fp64["s_per_step"] / value) if fp64 else None,

@@ -276,13 +276,15 @@ h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
  *                         for every preconditioner application; 0: plain
  *                         launches.  A capture that fails falls back to
  *                         plain launches.
- *   H2_OPT_TC_KERNEL      the tensor-core GEMMs' kernel form (process-wide,
- *                         all contexts): 0 (default) one CTA per batch
+ *   H2_OPT_TC_KERNEL      the kernel form of the factorization's main-chain
+ *                         tensor-core GEMMs (projection, Schur update;
+ *                         process-wide, all contexts): 0 one CTA per batch
  *                         entry; 1 a persistent grid of two CTAs per SM
- *                         looping over the entries; 2 a persistent
- *                         warp-specialized kernel, one CTA per SM, whose
- *                         epilogue of one tile overlaps the MMAs of the next
- *                         (two TMEM accumulators). */
+ *                         looping over the entries; 2 (default) a
+ *                         persistent warp-specialized kernel, one CTA per
+ *                         SM, whose epilogue of one tile overlaps the MMAs
+ *                         of the next (two TMEM accumulators).  The coupling
+ *                         products, on their own stream, always use form 0. */
 typedef enum {
   H2_OPT_RR_LU_FP64 = 0,
   H2_OPT_RESIDUAL_FP64 = 1,

@@ -11,8 +11,8 @@ namespace h2 {
 extern std::atomic<long long> g_launches;
 // Tensor-core GEMM kernel form of the factorization's main chain
 // (projection, Schur update), process-wide (H2_OPT_TC_KERNEL): 0 one CTA per
-// batch entry, 1 a persistent grid of two CTAs per SM, 2 the persistent
-// warp-specialized kernel with two TMEM accumulators.  The coupling
+// batch entry, 1 a persistent grid of two CTAs per SM, 2 (default) the
+// persistent warp-specialized kernel with two TMEM accumulators.  The coupling
 // products on their own stream always use form 0, so that they keep sharing
 // the SMs with the main chain.
 extern std::atomic<int> g_tc_kernel;

@@ -28,7 +28,7 @@
 
 namespace h2 {
 
-std::atomic<int> g_tc_kernel{0};
+std::atomic<int> g_tc_kernel{2};
 
 namespace {
 

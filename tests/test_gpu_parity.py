@@ -244,7 +244,7 @@ def test_tensor_core_projection_leaf(B, prec, tc_kernel):
     try:
         S.factor(prec)
     finally:
-        S.set_option("tc_kernel", 0)
+        S.set_option("tc_kernel", 2)  # the library's default
     st = S.stats()
     assert st["tensor_cores"] is True
     L = H["L"]
@@ -320,4 +320,31 @@ def test_device_pointers_and_stream(B):
     torch.cuda.synchronize()
     xh, r2, its2 = S.solve(b, target=1e-10)
     assert np.abs(xd.cpu().numpy() - xh).max() == 0.0 and its == its2
+    S.close()
+
+
+def test_fp64_sphere65536_against_dense_rows(B):
+    """The plain FP64 H^2-ULV at scale (65536 points on the sphere,
+    1/(r+1e-3), leaf 256, tol 1e-8, FP64 throughout): the refined solution's
+    residual against the dense matrix on 1024 sampled rows, whose kernel
+    entries are evaluated exactly, stays at the H^2 approximation level
+    (1e-6), while the residual against A_H2 reaches 1e-10."""
+    from oracle.kernels import Kernel
+    wl = W.workload("sphere65536_laplace")
+    P = wl.points()
+    b = wl.rhs()
+    S = B.H2Solver.build(P, kernel=wl.kernel, leaf=wl.leaf, eta=wl.eta, tol=wl.tol, far_samples=wl.far_samples,
+                         near_samples=wl.near_samples)
+    S.factor("fp64")
+    x, rel, its = S.solve(b, target=1e-10, max_iters=100)
+    assert rel <= 1e-10
+    rng = np.random.default_rng(12)
+    rows = np.sort(rng.choice(wl.n, 1024, replace=False))
+    kern = Kernel(wl.kernel)
+    Ax = np.concatenate([kern.matrix(P, rows[k:k + 128], np.arange(wl.n)) @ x for k in range(0, len(rows), 128)])
+    r_dense = np.linalg.norm(Ax - b[rows]) / np.linalg.norm(b[rows])
+    h2_err = np.linalg.norm(S.matvec(x)[rows] - Ax) / np.linalg.norm(Ax)
+    print(f"\nsphere65536 FP64: {its} FGMRES steps, relres vs A_H2 {rel:.2e}, vs dense rows {r_dense:.2e}, "
+          f"|A_H2 x - A x| / |A x| on the rows {h2_err:.2e}")
+    assert r_dense <= 1e-6 and h2_err <= 1e-6
     S.close()
