@@ -283,6 +283,14 @@ def roofline_for(phase, stats, t_phase, calls, peaks, prec, tc, fp64_tf):
     if phase == "a2_proj" and tc:
         bound, peak, src = "tensor", peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops"), \
             "measured bf16 sustained (FP16 runs at the same dense rate)"
+        # at K = 256 the projection GEMMs are memory-bound: also against HBM,
+        # from the phase's algorithmic bytes (16-bit inputs and bases read
+        # once, outputs written once)
+        if stats.get("bytes_proj"):
+            gbs = stats["bytes_proj"] / t_phase / 1e9
+            return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None, "phase": phase, "peak_source": src, "hbm_gbs": gbs,
+                    "hbm_frac": gbs / peaks.get("hbm_gbs", 6800.0)}
     elif prec == "fp64":
         bound, peak, src = "alu", fp64_tf, "FP64 peak measured live"
     else:

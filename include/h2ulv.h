@@ -179,7 +179,7 @@ h2_status h2_import(h2_ctx** out, const h2_params* p, const h2_instance* inst);
  *   LU of Ahat_ii^RR; the self Schur update Ahat_ii^SS -= Ahat_ii^SR
  *   (Ahat_ii^RR)^-1 Ahat_ii^RS (the only trailing update, Eq. 21); couplings
  *   T_i S_ij T_j^T; merge of the children's skeleton blocks into the parent
- *   level (Algorithm 2 line 18-20); LU of the root.
+ *   level (Algorithm 2); LU of the root.
  * prec is an h2_prec.  A later call replaces the previous factorization.
  * Errors: H2_ERR_INVALID_ARG (prec), H2_ERR_SINGULAR (zero pivot),
  * H2_ERR_OOM, H2_ERR_CUDA. */

@@ -14,10 +14,9 @@ Algorithm 1 (Section 3.5), level by level from the leaves to level 1:
   * The ID is a column-pivoted QR of M_i^T: M_i^T P = Q R.  The first k pivots
     are the skeleton SK_i and X_i = P [I; (R_11^-1 R_12)^T] is the basis, so
     that M_i ~= X_i M_i[SK_i, :].
-  * Dense near blocks G(B_i, B_j) at the leaf level (lines 10-12) and
-    couplings S_ij = G(SK_i, SK_j) for far pairs (lines 13-15).
-  * The points of box i at level l-1 are the skeletons (SK_2i, SK_2i+1)
-    (lines 16-18).
+  * Dense near blocks G(B_i, B_j) at the leaf level and couplings
+    S_ij = G(SK_i, SK_j) for far pairs.
+  * The points of box i at level l-1 are the skeletons (SK_2i, SK_2i+1).
 
 Readings of what the paper leaves open:
   * Rank: k_i = #{t : |R_tt| > tol * |R_11|}.  Following the constant-rank

@@ -1,6 +1,6 @@
 """Binary cluster tree, admissibility and near/far interaction lists (oracle).
 
-Section 3.5 / Algorithm 1 (line 17): the boxes of level l-1 are formed from
+Section 3.5 / Algorithm 1: the boxes of level l-1 are formed from
 their two children 2i and 2i+1 at level l, so the tree is a complete binary
 tree whose box i at level l has children 2i and 2i+1 at level l+1.  The root
 is level 0; the leaves are level L.

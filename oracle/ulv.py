@@ -15,14 +15,14 @@ Cholesky; for symmetric positive definite blocks both give the same solution):
                     X_p^orth = blockdiag(T_2p, T_2p+1) X_p  (from
                     A ~= X_c S X_d^T = U_c^S (T_c S T_d^T) U_d^S^T).
   factor            for l = L..1:
-                      Ahat_ij = U_i^T A_ij U_j for every near pair        (Alg. 2 l.3)
-                      P_i L_i U_i' = Ahat_ii^RR                          (Alg. 2 l.9)
-                      Z_i = (Ahat_ii^RR)^-1 Ahat_ii^RS                   (Alg. 2 l.13-15)
-                      Ahat_ii^SS -= Ahat_ii^SR Z_i                       (Alg. 2 l.16, Eq. 21)
-                      Shat_ij = T_i S_ij T_j^T for every far pair        (Alg. 2 l.5-7)
+                      Ahat_ij = U_i^T A_ij U_j for every near pair        (Alg. 2: projection)
+                      P_i L_i U_i' = Ahat_ii^RR                          (Alg. 2: RR LU)
+                      Z_i = (Ahat_ii^RR)^-1 Ahat_ii^RS                   (Alg. 2: RS solve)
+                      Ahat_ii^SS -= Ahat_ii^SR Z_i                       (Alg. 2: Schur, Eq. 21)
+                      Shat_ij = T_i S_ij T_j^T for every far pair        (Alg. 2: couplings)
                       merge the children's SS / Shat blocks into the
-                      parent's near blocks                               (Alg. 2 l.18-20)
-                    then LU of the root block                            (Alg. 2 l.22)
+                      parent's near blocks                               (Alg. 2: merge)
+                    then LU of the root block                            (Alg. 2: root)
                     Every fill-in other than the self Schur update is
                     dropped, as Eq. 10-12 / Eq. 21 state.
   solve_naive       Algorithm 3 (block triangular solve with the factors,
@@ -182,10 +182,10 @@ def solve_naive(F, H, b):
         R = D - K
         U, Ah, lus = F["U"][l], F["Ahat"][l], F["lu"][l]
         nbr = _nbrs(F["near"][l], nb)
-        c = [U[i].T @ vec[i * D:(i + 1) * D] for i in range(nb)]     # Alg. 3 l.2-4
+        c = [U[i].T @ vec[i * D:(i + 1) * D] for i in range(nb)]     # Alg. 3: c_i = U_i^T b_i
         bR = [ci[:R].copy() for ci in c]
         bS = [ci[R:].copy() for ci in c]
-        for i in range(nb):                                           # Alg. 3 l.5-13
+        for i in range(nb):                                           # Alg. 3: redundant parts
             bR[i] = _solve_PL(lus[i], bR[i])
             ui = _solve_U(lus[i], bR[i])                              # U'_ii^-1 y_i
             for j in nbr[i]:
@@ -194,7 +194,7 @@ def solve_naive(F, H, b):
             for j in nbr[i]:
                 bS[j] = bS[j] - Ah[(j, i)][R:, :R] @ ui               # L(s)_ji y_i
         ys[l] = bR
-        vec = np.concatenate(bS) if K else np.zeros(0)                # Alg. 3 l.14-16
+        vec = np.concatenate(bS) if K else np.zeros(0)                # Alg. 3: skeletons to the parent
     xs = _root_solve(F, vec)
     for l in range(1, L + 1):
         nb, D, K = 1 << l, F["D"][l], F["K"][l]

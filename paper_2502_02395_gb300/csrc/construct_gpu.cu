@@ -11,8 +11,8 @@
 // once per box j and shared by every box that has j close:
 //   cc_weights_kernel  per box j: W_j by Gauss-Jordan on [G(S_C, S_C) | Omega]
 //                      (partial pivoting), or by `gs` Gauss-Seidel sweeps from
-//                      W = 0 (the shortcut of Section 3.5 for the inverse in
-//                      line 7 of Algorithm 1)
+//                      W = 0 (the shortcut of Section 3.5 for the inverse of
+//                      the close part in Algorithm 1)
 //   sketch_kernel      per box and half of its rows: Y_i = G(B_i, S_F)
 //                      Omega(S_F) + sum_j G(B_i, S_C(j)) W_j, kernel entries
 //                      evaluated in 32-sample chunks into shared memory

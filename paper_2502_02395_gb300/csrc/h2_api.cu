@@ -2097,7 +2097,7 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
   std::ostringstream o;
   o.precision(9);
   const PhaseTimes& t = c->times;
-  double fl_proj = 0, fl_lu = 0, fl_schur = 0, fl_coup = 0, fl_qr = 0;
+  double fl_proj = 0, fl_lu = 0, fl_schur = 0, fl_coup = 0, fl_qr = 0, by_proj = 0;
   o << "{\"N\":" << c->N << ",\"L\":" << c->L << ",\"prec\":" << c->prec << ",\"levels\":[";
   // (per-level sizes; flop counts below use the actual ranks, not padded tiles)
   for (int l = 0; l <= c->L; ++l) {
@@ -2110,7 +2110,20 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
       fl_lu += 2.0 * D * D * D;
       continue;
     }
-    fl_proj += d.NP * 4.0 * D * D * D;
+    // the projection's flops: the pairs actually projected (symmetric near
+    // lists: the upper pairs i <= j; the lower ones are their transposes)
+    const bool up_only = (c->prec == H2_PREC_FP64) ? (d.near_sym && d.n_lw > 0)
+                                                   : ((int)c->f32.lv.size() > l && c->f32.lv[l].proj_sym);
+    const double npj = (double)(up_only ? d.n_up : d.NP);
+    fl_proj += npj * 4.0 * D * D * D;
+    // algorithmic bytes of the tensor-core projection: the 16-bit input
+    // blocks and bases read once, the outputs written once (FP32 SS of the
+    // off-diagonal pairs or whole FP32 blocks, and the 16-bit copy)
+    if (c->prec != H2_PREC_FP64 && (int)c->f32.lv.size() > l && c->f32.lv[l].tc) {
+      const FacLevel<float>& f = c->f32.lv[l];
+      const double out32 = f.ahat_ss_only ? (npj - d.nb) * K * K + (double)d.nb * D * D : npj * D * D;
+      by_proj += 2.0 * npj * D * D + 2.0 * d.nb * D * D + 4.0 * out32 + (f.ahat_isc ? 2.0 * npj * D * D : 0.0);
+    }
     fl_lu += d.nb * 2.0 * R * R * R;
     fl_schur += d.nb * (2.0 * R * R * K + 2.0 * K * K * R);
     fl_coup += d.FP * 4.0 * K * K * K;
@@ -2146,7 +2159,7 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     by_leaf32 = symm ? 4.0 * ((double)c->npu * lf.D * lf.D + (double)lf.nb * lf.D + 2.0 * c->npu * lf.D)
                      : 4.0 * ((double)lf.NP * lf.D * lf.D + (double)lf.nb * lf.D * K + 2.0 * lf.nb * lf.D + lf.nb * K);
   }
-  o << "],\"bytes_subst\":" << by_sub << ",\"bytes_matvec\":" << by_mv << ",\"flops_matvec\":" << fl_mv
+  o << "],\"bytes_proj\":" << by_proj << ",\"bytes_subst\":" << by_sub << ",\"bytes_matvec\":" << by_mv << ",\"flops_matvec\":" << fl_mv
     << ",\"bytes_matvec32\":" << by_mv / 2 << ",\"bytes_matvec32_leaf\":" << by_leaf32 << ",\"leaf_kernel\":\""
     << ((c->sym && c->prec != H2_PREC_FP64) ? "mv_sym_pair_kernel<float>" : "mv_leaf_kernel<float>") << "\"";
   o << ",\"flops\":{\"a1_qr\":" << fl_qr << ",\"a2_proj\":" << fl_proj << ",\"a3_lu\":" << fl_lu

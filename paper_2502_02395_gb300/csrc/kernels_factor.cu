@@ -1,23 +1,24 @@
 // Factorization kernels of the H^2-ULV library (sm_103a).
 //
 //   eval_blocks_kernel     dense kernel blocks G(B_i, B_j) of the leaf near
-//                          pairs and couplings G(SK_i, SK_j) (Algorithm 1
-//                          line 10-15), evaluated from the points
+//                          pairs and couplings G(SK_i, SK_j) (Algorithm 1),
+//                          evaluated from the points
 //   gemm_batched_kernel    SIMT batched GEMM C = alpha op(A) op(B) + beta C
-//                          (FP64 path: projection Algorithm 4 line 3 / 10,
-//                          Schur update line 6, couplings)
+//                          (FP64 path: the projection and Schur update
+//                          of Algorithm 4, couplings)
 //   qr_panel_kernel,       Householder QR of X^orth, its compact WY factor
 //   wy_tfactor_kernel      and the explicit U = [U^R U^S] (Eq. 6-7)
 //   lu_inverse_kernel      partial-pivot LU of Ahat_ii^RR in FP64 (Algorithm
-//                          2 line 9 with LU in place of Cholesky) and the
+//                          2, with LU in place of Cholesky) and the
 //                          explicit inverse (Ahat_ii^RR)^-1 used by the
 //                          Schur update and by the substitution of Eq. 31
 //   merge_kernel           children's SS blocks / couplings into the parent
-//                          near blocks (Algorithm 2 line 18-20)
+//                          near blocks (the merge of Algorithm 2)
 #include <type_traits>
 
 #include "h2_internal.h"
 #include "kernels.h"
+#include "ptx_util.h"
 
 namespace h2 {
 
@@ -1353,6 +1354,212 @@ __global__ void __launch_bounds__(NT) gj_inverse_kernel(int D, int R, const floa
   }
 }
 
+// ------------------------------------------------------------------------
+// The same in-place elimination for blocks too large for the registers of
+// one CTA (FP32 192 < R <= 512, FP64 128 < R <= 256): the columns are split
+// over a cluster of CL CTAs (thread-block cluster, distributed shared
+// memory).  CTA q of a box holds the columns [q W, (q + 1) W), W = Rp / CL,
+// as TR x TC register tiles, thread t at tile (t % G, q W / TC + t / G)
+// (16 x 4 tiles of FP32 or 16 x 2 of FP64: 64 registers of data).
+// Step k: the CTA owning column k picks the pivot row among the unused rows
+// and publishes (p, a_pk) and column k in its shared memory, in the buffer
+// of the step's parity; one cluster barrier; every CTA reads them from the
+// owner, scales its part of row p and eliminates column k from its other
+// rows.  The owner rewrites a buffer two steps later, after every CTA has
+// passed the next barrier, so one cluster barrier per step suffices.  A
+// failed pivot is seen by every CTA at the same step; all of them leave
+// after one more cluster barrier, so that no CTA exits while another may
+// still read its shared memory.
+// ------------------------------------------------------------------------
+template <typename T>
+struct __align__(16) GjcShared {
+  T fcol[2][512];  // the owner's column k, by step parity
+  T fl[512];       // this CTA's copy of it
+  T P[512];        // the scaled pivot row (this CTA's columns)
+  T pvs[2];        // a_pk, by step parity
+  int ps[2];       // p, by step parity
+  int prow[512], pinv[512], rowat[512];
+};
+
+__device__ __forceinline__ float rcp_pivot(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp_pivot(double v) { return 1.0 / v; }
+
+template <typename T, int TR, int TC, int J>
+__device__ __forceinline__ bool gjc_step(GjcShared<T>& sh, T (&a)[TR][TC], unsigned& used, int kc, int oq, int kcl,
+                                         int q, int G, int Rp, bool has, int tr, int tc, int tcl, int r0, int c0) {
+  const int t = threadIdx.x, k = kc * TC + J, b = k & 1;
+  if (q == oq) {
+    // (a) the owner warp of column k: the first largest |a_rk| over unused rows
+    if ((t >> 5) == ((kcl * G) >> 5)) {
+      T best = T(-1), sv = T(0);
+      int bi = -1;
+      if (has && tcl == kcl) {
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+          const T v = fabs(a[i][J]);
+          if (!((used >> i) & 1u) && v > best) best = v, sv = a[i][J], bi = r0 + i;
+        }
+      }
+      for (int o = G >> 1; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o), os = __shfl_xor_sync(0xffffffffu, sv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) best = ob, sv = os, bi = oi;
+      }
+      if (tcl == kcl && tr == 0) sh.ps[b] = bi, sh.pvs[b] = sv;
+    }
+    if (has && tcl == kcl) {
+#pragma unroll
+      for (int i = 0; i < TR; ++i) sh.fcol[b][r0 + i] = a[i][J];
+    }
+  }
+  cluster_sync();
+  const int p = ld_cluster(cluster_map(&sh.ps[b], (uint32_t)oq), int());
+  const T pv = ld_cluster(cluster_map(&sh.pvs[b], (uint32_t)oq), T());
+  if (p < 0 || pv == T(0) || !isfinite(pv)) return false;
+  const T inv = rcp_pivot(pv);
+  if (t == 0) sh.prow[k] = p;
+  // (b) column k from the owner; this CTA's part of the scaled pivot row
+  {
+    constexpr int PER = 16 / (int)sizeof(T);
+    const uint32_t src = cluster_map(&sh.fcol[b][0], (uint32_t)oq);
+    for (int e = t; e < Rp / PER; e += blockDim.x)
+      *reinterpret_cast<uint4*>(&sh.fl[e * PER]) = ld_cluster_v4(src + 16u * (uint32_t)e);
+  }
+  if (has && tr == p / TR) {
+#pragma unroll
+    for (int i = 0; i < TR; ++i)
+      if (r0 + i == p) {
+#pragma unroll
+        for (int jj = 0; jj < TC; ++jj) {
+          const T v = ((jj == J && c0 + jj == k) ? T(1) : a[i][jj]) * inv;
+          a[i][jj] = v;
+          sh.P[c0 + jj] = v;
+        }
+        used |= 1u << i;
+      }
+  }
+  __syncthreads();
+  // (c) eliminate column k from every other row
+  if (has) {
+    T pr[TC];
+#pragma unroll
+    for (int jj = 0; jj < TC; ++jj) pr[jj] = sh.P[c0 + jj];
+    const bool own = (tc == kc);
+#pragma unroll
+    for (int i = 0; i < TR; ++i) {
+      const T f = (r0 + i == p) ? T(0) : sh.fl[r0 + i];
+      if (own && r0 + i != p) a[i][J] = T(0);
+#pragma unroll
+      for (int jj = 0; jj < TC; ++jj) a[i][jj] = fma(-f, pr[jj], a[i][jj]);
+    }
+  }
+  return true;
+}
+
+template <typename T, int TR, int TC, int J>
+__device__ __forceinline__ void gjc_steps(bool& ok, GjcShared<T>& sh, T (&a)[TR][TC], unsigned& used, int kc, int oq,
+                                          int kcl, int q, int G, int Rp, int left, bool has, int tr, int tc, int tcl,
+                                          int r0, int c0) {
+  if constexpr (J < TC) {
+    if (ok && left > J) ok = gjc_step<T, TR, TC, J>(sh, a, used, kc, oq, kcl, q, G, Rp, has, tr, tc, tcl, r0, c0);
+    gjc_steps<T, TR, TC, J + 1>(ok, sh, a, used, kc, oq, kcl, q, G, Rp, left, has, tr, tc, tcl, r0, c0);
+  }
+}
+
+template <typename T, int TR, int TC, int CL, int NT>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT, 1)
+    gj_cluster_kernel(int D, int R, int Rp, const float* __restrict__ Ablk, const int32_t* __restrict__ diag_idx,
+                      float* __restrict__ Ainv, int32_t* __restrict__ piv, int32_t* __restrict__ status, int level) {
+  __shared__ GjcShared<T> sh;
+  const int q = (int)cluster_rank();
+  const int box = blockIdx.x / CL, t = threadIdx.x;
+  const int W = Rp / CL, ntr = Rp / TR, ntcl = W / TC, G = gj_group(ntr);
+  const int tr = t % G, tcl = t / G;
+  const bool has = tr < ntr && tcl < ntcl;
+  const int tc = q * ntcl + tcl;
+  const int r0 = tr * TR, c0 = tc * TC;
+  const float* A = Ablk + (size_t)(diag_idx ? diag_idx[box] : box) * D * D;
+  T a[TR][TC];
+  unsigned used = 0;
+#pragma unroll
+  for (int i = 0; i < TR; ++i) {
+    const int r = r0 + i;
+    if (!has || r >= R) used |= 1u << i;
+#pragma unroll
+    for (int j = 0; j < TC; ++j) {
+      const int c = c0 + j;
+      a[i][j] = (has && r < R && c < R) ? static_cast<T>(A[(size_t)r * D + c]) : T(0);
+    }
+  }
+  bool ok = true;
+  const int nkc = (R + TC - 1) / TC;
+  for (int kc = 0; kc < nkc && ok; ++kc) {
+    const int oq = kc / ntcl;
+    gjc_steps<T, TR, TC, 0>(ok, sh, a, used, kc, oq, kc - oq * ntcl, q, G, Rp, R - kc * TC, has, tr, tc, tcl, r0,
+                            c0);
+  }
+  cluster_sync();
+  if (!ok) {
+    if (q == 0 && t == 0 && atomicCAS(status, 0, level + 1) == 0) status[1] = box;
+    return;
+  }
+  // unscramble this CTA's columns: Ainv[k][prow[j]] = a[prow[k]][j]
+  for (int k = t; k < R; k += blockDim.x) sh.pinv[sh.prow[k]] = k;
+  __syncthreads();
+  if (has) {
+    float* out = Ainv + (size_t)box * R * R;
+#pragma unroll
+    for (int i = 0; i < TR; ++i) {
+      const int r = r0 + i;
+      if (r >= R) continue;
+      const size_t row = (size_t)sh.pinv[r] * R;
+#pragma unroll
+      for (int jj = 0; jj < TC; ++jj)
+        if (c0 + jj < R) out[row + sh.prow[c0 + jj]] = static_cast<float>(a[i][jj]);
+    }
+  }
+  if (q == 0) {
+    // LAPACK-style interchange sequence of the same pivots
+    __syncthreads();
+    if (t == 0) {
+      int* pos = sh.pinv;
+      for (int r = 0; r < R; ++r) pos[r] = r, sh.rowat[r] = r;
+      int32_t* pv_out = piv + (size_t)box * R;
+      for (int k = 0; k < R; ++k) {
+        const int r = sh.prow[k], qq = pos[r], rk = sh.rowat[k];
+        pv_out[k] = qq;
+        sh.rowat[k] = r, sh.rowat[qq] = rk;
+        pos[r] = k, pos[rk] = qq;
+      }
+    }
+  }
+}
+
+// Inverses of nb blocks by the cluster kernel: FP32 elimination (fp64 = 0)
+// for 192 < R <= 512, FP64 for 128 < R <= 256.  False: R not covered.
+static bool launch_gj_cluster(bool fp64, int nb, int D, int R, const float* Ablk, const int32_t* diag_idx,
+                              float* Ainv, int32_t* piv, int32_t* status, int level, cudaStream_t st) {
+  if (!fp64 && R > 192 && R <= 256) {
+    ++g_launches;
+    gj_cluster_kernel<float, 16, 4, 4, 256><<<nb * 4, 256, 0, st>>>(D, R, (R + 15) / 16 * 16, Ablk, diag_idx, Ainv,
+                                                                     piv, status, level);
+    return true;
+  }
+  if (!fp64 && R > 256 && R <= 512) {
+    ++g_launches;
+    gj_cluster_kernel<float, 16, 4, 8, 512><<<nb * 8, 512, 0, st>>>(D, R, (R + 31) / 32 * 32, Ablk, diag_idx, Ainv,
+                                                                     piv, status, level);
+    return true;
+  }
+  if (fp64 && R > 128 && R <= 256) {
+    ++g_launches;
+    gj_cluster_kernel<double, 16, 2, 8, 256><<<nb * 8, 256, 0, st>>>(D, R, (R + 15) / 16 * 16, Ablk, diag_idx,
+                                                                      Ainv, piv, status, level);
+    return true;
+  }
+  return false;
+}
+
 // The same elimination for R <= 128 in 16-column panels.  Thread t of warp
 // w holds the 8 x 8 tile at rows 8 (lane % 16), columns 16 w + 8 (lane / 16),
 // so warp w holds panel w (columns 16 w .. 16 w + 15) for every row.  Per
@@ -1584,6 +1791,10 @@ void launch_lu_inverse(int nb, int D, int R, const T* Ablk, const int32_t* diag_
     }
     return;
   }
+  if (std::is_same<T, float>::value &&
+      launch_gj_cluster(false, nb, D, R, reinterpret_cast<const float*>(Ablk), diag_idx, reinterpret_cast<float*>(Ainv),
+                        piv, status, level, st))
+    return;
   const size_t cap = 220 * 1024;
   size_t sm1 = sizeof(T) * (size_t)R * (R + 1);
   int use = sm1 <= cap;
@@ -1775,6 +1986,7 @@ void launch_lu_inverse_f64_for_f32(int nb, int D, int R, const float* Ablk, cons
     gj64_reg_kernel<<<nb, 256, 0, st>>>(D, R, Ablk, diag_idx, Ainv, piv, status, level);
     return;
   }
+  if (launch_gj_cluster(true, nb, D, R, Ablk, diag_idx, Ainv, piv, status, level, st)) return;
   const size_t cap = 220 * 1024;
   const size_t sm1 = sizeof(double) * (size_t)R * (R + 1);
   const int use = sm1 <= cap;

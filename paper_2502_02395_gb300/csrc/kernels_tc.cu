@@ -721,7 +721,7 @@ void launch_to_lowp(int bf16, const S* in, void* out, int64_t n, const float* sc
 template void launch_to_lowp<float>(int, const float*, void*, int64_t, const float*, cudaStream_t);
 template void launch_to_lowp<double>(int, const double*, void*, int64_t, const float*, cudaStream_t);
 
-// 16-bit merge (Algorithm 2 line 18-20 in the scaled low-precision layout):
+// 16-bit merge (the merge of Algorithm 2 in the scaled low-precision layout):
 // child SS blocks (FP32 Ahat, rows/cols R..D) and couplings (FP32 Shat) go
 // to the parent's 16-bit near blocks, multiplied by scale[0].  One CTA per
 // child pair; warps over rows, lanes over columns.  mirror (non-NULL when

@@ -293,3 +293,37 @@ def test_bounded_wait_gives_timeout_and_context_survives(B):
     x, r, its = S.solve(b, target=1e-10, max_iters=100)
     assert r <= 1e-10
     S.close()
+
+
+@pytest.mark.parametrize("rr", [0, 1])
+def test_cluster_inverse_root256(B, rr):
+    """A root block of dimension 256 (every level at rank 128 from the
+    fixed-rank GPU construction, so D_0 = 2 K_1 = 256): its inverse comes
+    from the Gauss-Jordan elimination split over a thread-block cluster
+    (FP32: 4 CTAs; FP64 with H2_OPT_RR_LU_FP64: 8 CTAs).  Against numpy's
+    inverse of the same FP32 root block: FP64 elimination, relative error
+    <= 8 u32 and LAPACK getrf's pivots; FP32, <= 2 R u32 cond.  The refined
+    solve then reaches 1e-10."""
+    n = 8192
+    P = W.cube_points(n, 81)
+    S = B.H2Solver.build_gpu(P, None, 0, kernel="laplace_eps", leaf=256, tol=1e-8, far_samples=1024,
+                             near_samples=64)
+    D0 = S.stats()["levels"][0]["D"]
+    assert D0 == 256
+    S.set_option("rr_lu_fp64", rr)
+    S.factor("fp16")
+    A0 = S.export("A", 0).reshape(D0, D0).astype(np.float64)
+    inv = S.export("root_inv", 0).reshape(D0, D0).astype(np.float64)
+    piv = S.export("root_piv", 0)
+    ref = np.linalg.inv(A0)
+    e = np.linalg.norm(inv - ref) / np.linalg.norm(ref)
+    cond = np.linalg.cond(A0)
+    print(f"\nroot 256, rr_lu_fp64={rr}: relative inverse error {e:.3e} ({e / U32:.1f} u32), cond {cond:.2e}")
+    if rr:
+        assert (piv == sla.lu_factor(A0)[1]).all()
+        assert e <= 8 * U32
+    else:
+        assert e <= 2 * D0 * U32 * cond
+    _, rel, its = S.solve(W.uniform_rhs(n, 83), target=1e-10, max_iters=100)
+    assert rel <= 1e-10
+    S.close()

@@ -213,7 +213,7 @@ def test_exact_rank_pipeline_equals_dense_solve(n, leaf, eta):
         assert np.linalg.norm(x - xd) <= 1e-11 * np.linalg.norm(xd)
     for l, (drop, rr) in ulv.dropped_fill_norms(F).items():
         assert drop <= 1e-12 and rr <= 1e-12
-    # the self Schur update (Alg. 2 l.16) is not trivial on this kernel
+    # the self Schur update (Algorithm 2, Eq. 21) is not trivial on this kernel
     lv = H["L"]
     R = H["D"][lv] - H["K"][lv]
     Aii = F["Ahat"][lv][(0, 0)]
