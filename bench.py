@@ -65,6 +65,7 @@ def parse():
                     help="instead of the single-system step: a batch of this many Gaussian-covariance systems of "
                          "uneven size (workloads.batch_systems), factored and solved concurrently")
     ap.add_argument("--batch-max-iters", type=int, default=600)
+    ap.add_argument("--batch-mode", choices=["forest", "pool"], default="forest")
     ap.add_argument("--dense-rows", type=int, default=4096,
                     help="rows sampled for the check against the dense matrix after the timed region (0: none)")
     ap.add_argument("--build", default="plain", choices=["plain", "gpu"],
@@ -303,10 +304,13 @@ def roofline_for(phase, stats, t_phase, calls, peaks, prec, tc, fp64_tf):
 
 def run_batch(args):
     """--batch S: S independent Gaussian-covariance systems (N log-uniform
-    in [4096, 65536], l in [0.05, 0.5], + I on the diagonal, leaf 128 / 256,
-    tol 1e-8), FP16
-    factorizations refined to --target, run by the library's worker pool
-    with the worker count its tuner picks; one JSON line."""
+    in [4096, 65536], l in [0.05, 0.5], + I on the diagonal, tol 1e-8),
+    factorizations in --prec refined to --target, one JSON line.
+    --batch-mode forest (default): the systems grouped by tree depth (leaf
+    256), each group one instance whose levels are single launches over its
+    systems (points divided by l, l = 1); pool: one instance per system
+    (leaf 128 below N = 16384, else 256).  The library's worker pool runs the
+    groups or systems with the worker count its tuner picks."""
     import torch
     import workloads as W
     from paper_2502_02395_gb300 import build as bld
@@ -316,13 +320,21 @@ def run_batch(args):
     specs = W.batch_systems(count=args.batch)
     t0 = time.perf_counter()
     solvers, rhs = [], []
-    for sp in specs:
-        P = W.cube_points(sp["n"], sp["point_seed"])
-        solvers.append(H2Solver.build(P, kernel="gaussian", ell=sp["ell"], diag_shift=sp["shift"], leaf=sp["leaf"], eta=1.0,
-                                      tol=1e-8, far_samples=1024, near_samples=64))
-        rhs.append(torch.from_numpy(W.uniform_rhs(sp["n"], sp["rhs_seed"])).cuda())
+    forest = args.batch_mode == "forest"
+    if forest:
+        shift = specs[0]["shift"]
+        batch = H2Batch.forest([W.cube_points(sp["n"], sp["point_seed"]) / sp["ell"] for sp in specs],
+                               kernel="gaussian", ell=1.0, diag_shift=shift, leaf=256, eta=1.0, tol=1e-8,
+                               far_samples=1024, near_samples=64)
+        rhs = [W.uniform_rhs(sp["n"], sp["rhs_seed"]) for sp in specs]
+    else:
+        for sp in specs:
+            P = W.cube_points(sp["n"], sp["point_seed"])
+            solvers.append(H2Solver.build(P, kernel="gaussian", ell=sp["ell"], diag_shift=sp["shift"], leaf=sp["leaf"],
+                                          eta=1.0, tol=1e-8, far_samples=1024, near_samples=64))
+            rhs.append(torch.from_numpy(W.uniform_rhs(sp["n"], sp["rhs_seed"])).cuda())
+        batch = H2Batch(solvers)
     build_s = time.perf_counter() - t0
-    batch = H2Batch(solvers)
     workers = batch.tune(args.prec, rhs, target=args.target, max_iters=args.batch_max_iters, check=False)
     tune = batch.stats()["tune_seconds"]
     times, its_all, rel_all = [], None, None
@@ -336,6 +348,7 @@ def run_batch(args):
             "value": value, "unit": "s", "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
             "workers": workers, "tune_seconds_by_workers": tune, "sequential_s": tune.get("1"),
             "speedup_vs_one_worker": (tune.get("1") / value) if tune.get("1") else None,
+            "mode": args.batch_mode, "groups": batch.stats().get("group_systems"),
             "total_N": int(sum(s["n"] for s in specs)), "N": [s["n"] for s in specs],
             "iters": its_all, "converged": int(sum(r <= args.target for r in rel_all)),
             "relres_max": float(max(rel_all)), "build_s": build_s, "dtype": {"fp16": "f16/f32/f64", "bf16": "bf16/f32/f64"}.get(

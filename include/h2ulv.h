@@ -157,6 +157,31 @@ typedef struct {
  * the children's rank above the leaves) must stay <= 1024. */
 h2_status h2_build(h2_ctx** out, const h2_params* p, const double* points, int64_t N);
 
+/* Depth L of the cluster tree h2_build makes for N points and the given
+ * leaf size: the smallest L with leaf_size * 2^L >= N.  -1 for N < 1 or
+ * leaf_size < 1. */
+int32_t h2_tree_depth(int64_t N, int32_t leaf_size);
+
+/* Several independent systems as one instance (a forest; no counterpart in
+ * the paper): each system's H^2 matrix is built as by h2_build with the
+ * same parameters p (points[k]: N[k] x 3 row-major, host), and the trees,
+ * which must all have the same depth L >= 1 (h2_tree_depth), are laid side
+ * by side: system k holds boxes [k 2^l, (k + 1) 2^l) of level l, so every
+ * level's batched kernels cover all systems in one launch and the root
+ * level has one block per system (count roots factored by one batched
+ * launch).  The systems share p (a Gaussian batch with per-system length
+ * scales passes points divided by l_k and ell = 1: the matrix depends on
+ * |x - y| / l only).  Each level takes the largest rank of its systems;
+ * a smaller rank is padded with zero basis columns and padding skeleton
+ * entries (which interact with nothing), and every leaf with padding
+ * points (1 on the diagonal), as a single instance pads its own leaves.
+ * A_H2 is then block diagonal with the systems' own H^2 matrices as its
+ * blocks; vectors are the systems' vectors concatenated in input order.
+ * Errors: as h2_build; H2_ERR_INVALID_ARG also for count < 1 or depths that
+ * differ or are 0 (h2_last_error(NULL) names the system). */
+h2_status h2_build_forest(h2_ctx** out, const h2_params* p, const double* const* points, const int64_t* N,
+                          int32_t count);
+
 /* Plan without a GPU: run the host part of h2_build (cluster tree, near/far
  * lists and the interpolative decompositions of Algorithm 1) and write a
  * JSON summary to json (cap bytes including the terminating zero): N, L and
@@ -459,6 +484,22 @@ typedef struct h2_batch h2_batch;
  * Errors: H2_ERR_INVALID_ARG. */
 h2_status h2_batch_create(h2_batch** out, h2_ctx* const* ctxs, const int64_t* n, int32_t count);
 
+/* A batch in forest form over count systems that share the parameters p
+ * (points[k]: N[k] x 3, host): the systems are grouped by tree depth and
+ * each group is built as one h2_build_forest instance, owned by the batch.
+ * h2_batch_run then factors each group (one launch per kernel and level
+ * for all its systems) and solves its systems together: each right-hand
+ * side is scaled to unit norm, the group is refined to target / sqrt(m)
+ * for its m systems (then |r_k| <= |r| <= target for every system), and
+ * each system's relative residual, written to relres, is recomputed from
+ * one FP64 h2_matvec of the group; iters receives the group's count.  The
+ * vectors B[k], X[k] of a forest batch are host memory (the scaling and
+ * splitting run on the host; device vectors give H2_ERR_INVALID_ARG).  The
+ * worker pool runs the groups.  Errors: as h2_build_forest (the group's
+ * message is in h2_last_error(NULL)). */
+h2_status h2_batch_create_forest(h2_batch** out, const h2_params* p, const double* const* points,
+                                 const int64_t* N, int32_t count);
+
 /* Factor every system in precision prec (prec = -1: keep the current
  * factorizations) and, with B non-NULL, solve system i for B[i] into X[i]
  * as h2_solve does (target, max_iters).  relres and iters (host, may be
@@ -476,15 +517,17 @@ h2_status h2_batch_run(h2_batch* b, int32_t prec, const double* const* B, double
 h2_status h2_batch_tune(h2_batch* b, int32_t prec, const double* const* B, double* const* X, double target,
                         int32_t max_iters, int32_t* workers_out);
 
-/* JSON: system count, worker count, the last run's seconds and the tuning
+/* JSON: system count, mode ("pool" or "forest"), group count (forest: the
+ * systems per group), worker count, the last run's seconds and the tuning
  * times by worker count.  Errors: H2_ERR_INVALID_ARG (cap too small). */
 h2_status h2_batch_stats(const h2_batch* b, char* json, size_t cap);
 
 /* One-line description of the batch's last error ("" if none). */
 const char* h2_batch_last_error(const h2_batch* b);
 
-/* Free the batch (not its contexts; they go back to the legacy default
- * stream).  NULL is ignored. */
+/* Free the batch: a pool batch's contexts are not freed (they go back to
+ * the legacy default stream); a forest batch's group contexts are.  NULL
+ * is ignored. */
 void h2_batch_destroy(h2_batch* b);
 
 /* Issue all later work on the given cudaStream_t (NULL: legacy default). */

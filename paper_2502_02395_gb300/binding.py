@@ -35,7 +35,8 @@ EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_sol
             "h2_wait_selftest", "h2_set_memory_limit", "h2_rank_data", "h2_rank_model_create",
             "h2_rank_model_set_weights", "h2_rank_model_get_weights", "h2_rank_model_grad", "h2_rank_model_train",
             "h2_rank_model_predict", "h2_rank_model_last_error", "h2_rank_model_destroy", "h2_plan_predicted",
-            "h2_build_predicted", "h2_build_gpu", "h2_batch_create", "h2_batch_run", "h2_batch_tune",
+            "h2_build_predicted", "h2_build_gpu", "h2_tree_depth", "h2_build_forest", "h2_batch_create",
+            "h2_batch_create_forest", "h2_batch_run", "h2_batch_tune",
             "h2_batch_stats", "h2_batch_last_error", "h2_batch_destroy",
             "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
 OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1, "graphs": 2, "tc_kernel": 3}
@@ -104,7 +105,10 @@ def lib() -> ctypes.CDLL:
             "h2_plan_predicted": (i32, [vp, vp, i64, vp, ctypes.c_char_p, ctypes.c_size_t]),
             "h2_build_predicted": (i32, [pp, vp, vp, i64, vp]),
             "h2_build_gpu": (i32, [pp, vp, vp, i64, vp, i32]),
+            "h2_tree_depth": (i32, [i64, i32]),
+            "h2_build_forest": (i32, [pp, vp, vp, vp, i32]),
             "h2_batch_create": (i32, [pp, vp, vp, i32]),
+            "h2_batch_create_forest": (i32, [pp, vp, vp, vp, i32]),
             "h2_batch_run": (i32, [vp, i32, vp, vp, dbl, i32, vp, vp, vp]),
             "h2_batch_tune": (i32, [vp, i32, vp, vp, dbl, i32, vp]),
             "h2_batch_stats": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
@@ -364,20 +368,55 @@ def h2_build_gpu(params: Params, points: np.ndarray, m=None, gs_sweeps: int = 0)
     return out
 
 
+def h2_tree_depth(n: int, leaf: int) -> int:
+    return int(lib().h2_tree_depth(int(n), int(leaf)))
+
+
+def _point_arrays(points_list):
+    pts = [np.ascontiguousarray(P, dtype=np.float64) for P in points_list]
+    ptrs = (ctypes.c_void_p * len(pts))(*[P.ctypes.data for P in pts])
+    ns = (ctypes.c_int64 * len(pts))(*[len(P) for P in pts])
+    return pts, ptrs, ns
+
+
+def h2_build_forest(params: Params, points_list):
+    """One instance over several systems of one tree depth (h2_build_forest)."""
+    pts, ptrs, ns = _point_arrays(points_list)
+    out = ctypes.c_void_p()
+    _check(lib().h2_build_forest(ctypes.byref(out), ctypes.byref(params), ctypes.cast(ptrs, ctypes.c_void_p),
+                                 ctypes.cast(ns, ctypes.c_void_p), len(pts)), None)
+    return out
+
+
 # ------------------------------------------------------------- batches ---
 class H2Batch:
-    """Independent systems (H2Solver objects) factored and solved
-    concurrently by the library's worker pool."""
+    """Independent systems factored and solved by the library's worker pool:
+    H2Batch(solvers) over H2Solver objects (one context per system), or
+    H2Batch.forest(points_list, **params) (the systems grouped by tree depth,
+    each group one instance whose levels are single launches over all of
+    its systems)."""
 
-    def __init__(self, solvers):
+    def __init__(self, solvers=None, _handle=None, _count=0):
+        if _handle is not None:
+            self.solvers, self.count, self.b = [], _count, _handle
+            return
         self.solvers = list(solvers)
-        n = len(self.solvers)
+        n = self.count = len(self.solvers)
         self._ctx = (ctypes.c_void_p * n)(*[s.ctx.value if hasattr(s.ctx, "value") else s.ctx for s in self.solvers])
         self._n = (ctypes.c_int64 * n)(*[s.n for s in self.solvers])
         out = ctypes.c_void_p()
         _check(lib().h2_batch_create(ctypes.byref(out), ctypes.cast(self._ctx, ctypes.c_void_p),
                                      ctypes.cast(self._n, ctypes.c_void_p), n), None)
         self.b = out
+
+    @classmethod
+    def forest(cls, points_list, **kw):
+        pts, ptrs, ns = _point_arrays(points_list)
+        out = ctypes.c_void_p()
+        params = make_params(**kw)
+        _check(lib().h2_batch_create_forest(ctypes.byref(out), ctypes.byref(params), ctypes.cast(ptrs, ctypes.c_void_p),
+                                            ctypes.cast(ns, ctypes.c_void_p), len(pts)), None)
+        return cls(_handle=out, _count=len(pts))
 
     def _ptrs(self, arrs):
         a = (ctypes.c_void_p * len(arrs))(*[_ptr(x).value for x in arrs])
@@ -392,7 +431,7 @@ class H2Batch:
         """Factor all systems (prec None: keep) and solve each for B[i];
         returns (X list, relres, iters, seconds).  check=False: a system
         that stops above the target does not raise (see relres)."""
-        n = len(self.solvers)
+        n = self.count
         p = -1 if prec is None else PRECS[prec]
         rel = (ctypes.c_double * n)()
         its = (ctypes.c_int32 * n)()
@@ -485,6 +524,12 @@ class H2Solver:
         """h2_build with the compression on the GPU (ranks from the model, or
         each level's cap when model is None)."""
         return cls(h2_build_gpu(make_params(**kw), points, model, gs_sweeps), len(points))
+
+    @classmethod
+    def build_forest(cls, points_list, **kw):
+        """Several systems of one tree depth as one block-diagonal instance;
+        vectors are the systems' vectors concatenated."""
+        return cls(h2_build_forest(make_params(**kw), points_list), int(sum(len(P) for P in points_list)))
 
     @classmethod
     def from_instance(cls, flat: dict, **kw):

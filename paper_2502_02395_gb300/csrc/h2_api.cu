@@ -109,7 +109,7 @@ h2_status setup_device(h2_ctx* c) {
   for (int l = 0; l <= L; ++l) {
     DevLevel& d = c->lv[l];
     const HostLevel& h = H.lv[l];
-    d.nb = 1 << l;
+    d.nb = h.nb;  // 2^l, or 2^l per system of a forest
     d.D = h.D;
     d.K = l ? h.K : 0;
     d.R = d.D - d.K;
@@ -482,16 +482,18 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   CKC(dalloc(c, &F.amax, 3 * (size_t)(L + 1)));
   CKC(dalloc(c, &F.sch, 8));
   CKC(dalloc(c, &F.sch_amax, 2));
+  // one root block per system (a forest has several)
+  const size_t nr = (size_t)c->lv[0].nb;
   if (std::is_same<T, double>::value) {
-    CKC(dalloc(c, &F.root_lu, (size_t)D0 * D0));
+    CKC(dalloc(c, &F.root_lu, nr * D0 * D0));
     F.root_luT = reinterpret_cast<T*>(F.root_lu);
   } else {
-    CKC(dalloc(c, &F.root_luT, (size_t)D0 * D0));
+    CKC(dalloc(c, &F.root_luT, nr * D0 * D0));
   }
-  CKC(dalloc(c, &F.root_inv, (size_t)D0 * D0));
-  CKC(dalloc(c, &F.root_piv, D0));
-  CKC(dalloc(c, &F.root_vec, D0));
-  CKC(dalloc(c, &F.root_x, D0));
+  CKC(dalloc(c, &F.root_inv, nr * D0 * D0));
+  CKC(dalloc(c, &F.root_piv, nr * D0));
+  CKC(dalloc(c, &F.root_vec, nr * D0));
+  CKC(dalloc(c, &F.root_x, nr * D0));
   return H2_OK;
 }
 
@@ -564,7 +566,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   // FP64 a3 for the FP16/BF16 factorizations: scratch for the largest level
   const bool lu64_mixed = mixed && c->rr_lu64;
   if (lu64_mixed && !F.rr_lu) {
-    size_t n = (size_t)c->lv[0].D * c->lv[0].D;
+    size_t n = (size_t)c->lv[0].nb * c->lv[0].D * c->lv[0].D;
     for (int l = 1; l <= L; ++l) n = std::max(n, (size_t)c->lv[l].nb * c->lv[l].R * c->lv[l].R);
     CKC(dalloc(c, &F.rr_lu, n));
     CKC(dalloc(c, &F.rr_inv, n));
@@ -881,11 +883,12 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   // a7: root
   const int D0 = c->lv[0].D;
   const T* Aroot = (L == 0) ? Aleaf : F.lv[0].Ain;
+  const int nr = c->lv[0].nb;  // one root per system (the level-0 blocks are in box order)
   if (lu64_mixed)
-    launch_lu_inverse_f64_for_f32(1, D0, D0, reinterpret_cast<const float*>(Aroot), nullptr, F.rr_lu, F.rr_inv,
+    launch_lu_inverse_f64_for_f32(nr, D0, D0, reinterpret_cast<const float*>(Aroot), nullptr, F.rr_lu, F.rr_inv,
                                   F.root_piv, reinterpret_cast<float*>(F.root_inv), c->status, 0, st);
   else
-    launch_lu_inverse<T>(1, D0, D0, Aroot, nullptr, F.root_lu, F.root_luT, F.root_piv, F.root_inv, c->status, 0, st);
+    launch_lu_inverse<T>(nr, D0, D0, Aroot, nullptr, F.root_lu, F.root_luT, F.root_piv, F.root_inv, c->status, 0, st);
   mark();
   CKC(cudaGetLastError());
   CKC(cudaStreamSynchronize(st));
@@ -997,7 +1000,7 @@ void ulv_sweep(h2_ctx* c, Factor<T>& F) {
     });
   };
   for (int l = L; l >= 1; --l) fwd(l);
-  launch_gemv_rows<T>(c->lv[0].D, F.root_inv, F.root_vec, F.root_x, st);
+  launch_gemv_rows<T>(c->lv[0].nb, c->lv[0].D, F.root_inv, F.root_vec, F.root_x, st);
   for (int l = 1; l <= L; ++l) bwd(l);
 }
 template <typename T>
@@ -1603,6 +1606,68 @@ h2_status h2_build(h2_ctx** out, const h2_params* p, const double* points, int64
   return H2_OK;
 }
 
+int32_t h2_tree_depth(int64_t N, int32_t leaf_size) {
+  if (N < 1 || leaf_size < 1) return -1;
+  return depth_of(N, leaf_size);
+}
+
+h2_status h2_build_forest(h2_ctx** out, const h2_params* p, const double* const* points, const int64_t* N,
+                          int32_t count) {
+  g_last_error.clear();
+  if (!out) { g_last_error = "out is NULL"; return H2_ERR_INVALID_ARG; }
+  *out = nullptr;
+  h2_status s = check_params(p, g_last_error);
+  if (s != H2_OK) return s;
+  if (count < 1 || !points || !N) { g_last_error = "count < 1 or NULL arrays"; return H2_ERR_INVALID_ARG; }
+  int depth = -1;
+  for (int32_t k = 0; k < count; ++k) {
+    if (N[k] < 1 || !points[k]) { g_last_error = "system " + std::to_string(k) + ": N < 1 or points NULL"; return H2_ERR_INVALID_ARG; }
+    for (int64_t t = 0; t < 3 * N[k]; ++t)
+      if (!std::isfinite(points[k][t])) {
+        g_last_error = "system " + std::to_string(k) + ": non-finite coordinate";
+        return H2_ERR_INVALID_ARG;
+      }
+    const int d = depth_of(N[k], p->leaf_size);
+    if (d < 1 || (depth >= 0 && d != depth)) {
+      g_last_error = "the systems of a forest need one common tree depth >= 1 (system " + std::to_string(k) +
+                     " has " + std::to_string(d) + ")";
+      return H2_ERR_INVALID_ARG;
+    }
+    depth = d;
+  }
+  std::vector<HostH2> parts(count);
+  for (int32_t k = 0; k < count; ++k) {
+    std::string e = build_host(*p, points[k], N[k], parts[k]);
+    if (!e.empty()) {
+      g_last_error = "system " + std::to_string(k) + ": " + e;
+      return H2_ERR_SINGULAR;
+    }
+  }
+  h2_ctx* c = new h2_ctx();
+  c->params = *p;
+  c->kfn = KernelFn{p->kernel, p->eps, p->ell, p->diag_shift};
+  std::string e = combine_forest(parts, c->host);
+  parts.clear();
+  if (!e.empty()) {
+    g_last_error = e;
+    delete c;
+    return H2_ERR_INVALID_ARG;
+  }
+  s = check_fits(instance_bytes(c->host), "the H^2 forest", g_last_error);
+  if (s != H2_OK) {
+    delete c;
+    return s;
+  }
+  s = setup_device(c);
+  if (s != H2_OK) {
+    g_last_error = c->err;
+    h2_destroy(c);
+    return s;
+  }
+  *out = c;
+  return H2_OK;
+}
+
 h2_status h2_plan(const h2_params* p, const double* points, int64_t N, char* json, size_t cap) {
   g_last_error.clear();
   h2_status s = check_params(p, g_last_error);
@@ -2098,7 +2163,8 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
   o.precision(9);
   const PhaseTimes& t = c->times;
   double fl_proj = 0, fl_lu = 0, fl_schur = 0, fl_coup = 0, fl_qr = 0, by_proj = 0;
-  o << "{\"N\":" << c->N << ",\"L\":" << c->L << ",\"prec\":" << c->prec << ",\"levels\":[";
+  o << "{\"N\":" << c->N << ",\"L\":" << c->L << ",\"systems\":" << (c->lv.empty() ? 0 : c->lv[0].nb)
+    << ",\"prec\":" << c->prec << ",\"levels\":[";
   // (per-level sizes; flop counts below use the actual ranks, not padded tiles)
   for (int l = 0; l <= c->L; ++l) {
     const DevLevel& d = c->lv[l];
@@ -2107,7 +2173,7 @@ h2_status h2_stats(const h2_ctx* c, char* json, size_t cap) {
     o << "{\"l\":" << l << ",\"nb\":" << d.nb << ",\"D\":" << d.D << ",\"K\":" << d.K << ",\"NP\":" << d.NP
       << ",\"FP\":" << d.FP << "}";
     if (l == 0) {
-      fl_lu += 2.0 * D * D * D;
+      fl_lu += d.nb * 2.0 * D * D * D;
       continue;
     }
     // the projection's flops: the pairs actually projected (symmetric near
@@ -2250,15 +2316,19 @@ h2_status h2_export(const h2_ctx* c, const char* name, int32_t level, void* dst,
     cnt = (n == "lu") ? nb * R * R : nb * R;
   } else if (n == "root" || n == "root_piv" || n == "root_inv") {
     if (!ready) return H2_ERR_STATE;
-    const size_t D0 = c->lv[0].D;
+    const size_t D0 = c->lv[0].D, nr = c->lv[0].nb;  // nr roots (one per system of a forest)
     if (n == "root" && !f64) return H2_ERR_INVALID_ARG;  // as for "lu"
     if (n == "root") {
       src = f64 ? (const void*)c->f64.root_lu : (const void*)c->f32.root_luT;
       es = f64 ? 8 : 4;
-      cnt = D0 * D0;
+      cnt = nr * D0 * D0;
     }
-    if (n == "root_piv") { src = f64 ? (const void*)c->f64.root_piv : (const void*)c->f32.root_piv; es = 4; cnt = D0; }
-    if (n == "root_inv") s = pick(c->f64.root_inv, c->f32.root_inv, D0 * D0, true);
+    if (n == "root_piv") {
+      src = f64 ? (const void*)c->f64.root_piv : (const void*)c->f32.root_piv;
+      es = 4;
+      cnt = nr * D0;
+    }
+    if (n == "root_inv") s = pick(c->f64.root_inv, c->f32.root_inv, nr * D0 * D0, true);
   } else {
     return H2_ERR_INVALID_ARG;
   }

@@ -145,6 +145,14 @@ struct RankPredictor {
 // compression; X and SK stay empty).
 std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& out,
                        RankPredictor* pred = nullptr, bool layout_only = false, GpuCompressor* gpu = nullptr);
+// Depth of the binary tree over n points with leaves of at most `leaf`.
+int depth_of(int64_t n, int leaf);
+// Independent systems of one tree depth L >= 1 as one instance (a forest):
+// system s holds boxes [s 2^l, (s + 1) 2^l) of level l, so box i's children
+// stay 2i and 2i + 1 and the root level has one box per system.  Ranks are
+// padded to each level's largest (zero basis columns, skeleton entries -1)
+// and leaves to the largest leaf.  Empty string on success.
+std::string combine_forest(const std::vector<HostH2>& parts, HostH2& out);
 // The GPU compressor of construct_gpu.cu over the N points (kernel G);
 // nullptr if the device upload fails.
 GpuCompressor* make_gpu_compressor(const KernelFn& G, const double* pts, int64_t N, int gs_sweeps);

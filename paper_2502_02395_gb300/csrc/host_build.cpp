@@ -25,13 +25,14 @@
 #endif
 
 namespace h2 {
-namespace {
 
 int depth_of(int64_t n, int leaf) {
   int L = 0;
   while ((int64_t)leaf << L < n) ++L;
   return L;
 }
+
+namespace {
 
 // Median split along the longest bounding-box axis; ties by original index.
 void build_tree(const double* P, int64_t N, int L, std::vector<int64_t>& perm,
@@ -707,6 +708,80 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
     H.lv[l - 1].D = 2 * K;
   }
   if (L == 0) H.lv[0].D = (int)N;
+  return "";
+}
+
+// Padding a system's rank K_s to the level's K with zero basis columns keeps
+// A_H2: X_i S_ij X_j^T is unchanged (the couplings of padding entries are 0),
+// and the complement basis of a padded X_i (Householder QR, a zero column
+// gives the identity reflector) keeps one more direction in its skeleton
+// part, whose far-field couplings are zero; it is carried up the tree like
+// any skeleton direction, so the factorization stays exact for A_H2.
+std::string combine_forest(const std::vector<HostH2>& parts, HostH2& H) {
+  const int S = (int)parts.size();
+  if (S < 1) return "empty forest";
+  const int L = parts[0].L;
+  for (const HostH2& P : parts)
+    if (P.L != L) return "the systems of a forest must have the same tree depth";
+  if (L < 1) return "the systems of a forest need at least one level below the root";
+  H = HostH2();
+  H.L = L;
+  H.lv.assign(L + 1, HostLevel());
+  std::vector<int> K(L + 2, 0), D(L + 1, 0);
+  for (int l = 1; l <= L; ++l)
+    for (const HostH2& P : parts) K[l] = std::max(K[l], P.lv[l].K);
+  for (const HostH2& P : parts) D[L] = std::max(D[L], P.lv[L].D);
+  for (int l = 0; l < L; ++l) D[l] = 2 * K[l + 1];
+  std::vector<int64_t> poff(S + 1, 0);
+  H.leaf_offsets.push_back(0);
+  for (int s = 0; s < S; ++s) {
+    const HostH2& P = parts[s];
+    poff[s + 1] = poff[s] + P.N;
+    H.points.insert(H.points.end(), P.points.begin(), P.points.end());
+    for (int64_t t : P.perm) H.perm.push_back(t + poff[s]);
+    for (size_t i = 1; i < P.leaf_offsets.size(); ++i) H.leaf_offsets.push_back(P.leaf_offsets[i] + poff[s]);
+    H.ranks_leaf.insert(H.ranks_leaf.end(), P.ranks_leaf.begin(), P.ranks_leaf.end());
+    H.rec.compress_s += P.rec.compress_s;
+    H.rec.fallback_boxes += P.rec.fallback_boxes;
+    H.rec.flops_prefactor += P.rec.flops_prefactor;
+    H.rec.flops_far += P.rec.flops_far;
+  }
+  H.N = poff[S];
+  for (int l = 0; l <= L; ++l) {
+    HostLevel& h = H.lv[l];
+    const int nbs = 1 << l;
+    h.nb = S * nbs;
+    h.D = D[l];
+    h.K = l ? K[l] : 0;
+    if (l >= 1) {
+      h.X.assign((size_t)h.nb * D[l] * K[l], 0.0);
+      h.SK.assign((size_t)h.nb * K[l], -1);
+    }
+    for (int s = 0; s < S; ++s) {
+      const HostLevel& g = parts[s].lv[l];
+      const int bo = s * nbs;
+      for (int32_t v : g.near) h.near.push_back(v + bo);
+      for (int32_t v : g.far) h.far.push_back(v + bo);
+      if (l == 0 || g.K == 0) continue;
+      const int Ks = g.K, Ds = g.D;
+      // leaf rows keep their slot; above, child c's skeleton entry a goes to
+      // row c K[l + 1] + a of the padded layout
+      const int Kc = (l < L) ? parts[s].lv[l + 1].K : 0;
+      if (l < L && Ds != 2 * Kc) return "inconsistent box dimension in a forest system";
+      for (int i = 0; i < nbs; ++i) {
+        const double* src = &g.X[(size_t)i * Ds * Ks];
+        double* dst = &h.X[(size_t)(bo + i) * D[l] * K[l]];
+        for (int r = 0; r < Ds; ++r) {
+          const int rr = (l == L) ? r : (r / Kc) * K[l + 1] + r % Kc;
+          for (int a = 0; a < Ks; ++a) dst[(size_t)rr * K[l] + a] = src[(size_t)r * Ks + a];
+        }
+        for (int a = 0; a < Ks; ++a) {
+          const int64_t v = g.SK[(size_t)i * Ks + a];
+          h.SK[(size_t)(bo + i) * K[l] + a] = v < 0 ? -1 : v + poff[s];
+        }
+      }
+    }
+  }
   return "";
 }
 

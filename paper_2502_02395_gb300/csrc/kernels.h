@@ -122,7 +122,7 @@ template <typename T, typename TS>
 void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
                  cudaStream_t st);
 template <typename T>
-void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st);
+void launch_gemv_rows(int nb, int n, const T* M, const T* x, T* y, cudaStream_t st);
 template <typename T>
 void launch_transpose_pairs(int D, int64_t n, const int32_t* dst, const int32_t* src, T* A, cudaStream_t st);
 template <typename T>

@@ -1186,10 +1186,14 @@ void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const 
              parent_x, F.part, F.Ur, F.xs);
 }
 
-// y = M x for one n x n row-major matrix (root solve with the explicit inverse)
+// y_b = M_b x_b for nb n x n row-major matrices, one CTA each (root solves
+// with the explicit inverses: one root, or one per system of a forest)
 template <typename T>
 __global__ void gemv_rows_kernel(int n, const T* __restrict__ M, const T* __restrict__ x, T* __restrict__ y) {
   extern __shared__ unsigned char sm_raw[];
+  M += (size_t)blockIdx.x * n * n;
+  x += (size_t)blockIdx.x * n;
+  y += (size_t)blockIdx.x * n;
   T* sx = reinterpret_cast<T*>(sm_raw);
   T* sy = sx + n;
   for (int e = threadIdx.x; e < n; e += blockDim.x) { sx[e] = x[e]; sy[e] = 0; }
@@ -1199,19 +1203,19 @@ __global__ void gemv_rows_kernel(int n, const T* __restrict__ M, const T* __rest
   for (int e = threadIdx.x; e < n; e += blockDim.x) y[e] = sy[e];
 }
 template <typename T>
-void launch_gemv_rows(int n, const T* M, const T* x, T* y, cudaStream_t st) {
-  if (n == 0) return;
+void launch_gemv_rows(int nb, int n, const T* M, const T* x, T* y, cudaStream_t st) {
+  if (n == 0 || nb == 0) return;
   const size_t sm = sizeof(T) * 2 * (size_t)n;
   if (sm > 48 * 1024) cudaFuncSetAttribute(gemv_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   ++g_launches;
-  gemv_rows_kernel<T><<<1, 256, sm, st>>>(n, M, x, y);
+  gemv_rows_kernel<T><<<nb, 256, sm, st>>>(n, M, x, y);
 }
 
 #define H2_INST_SOLVE(T)                                                                     \
   template void launch_fwd1<T>(const DevLevel&, const FacLevel<T>&, const ChildIn<T>&, cudaStream_t); \
   template void launch_transpose_blocks<T>(int64_t, int, const T*, T*, cudaStream_t);         \
   template void launch_transpose_pairs<T>(int, int64_t, const int32_t*, const int32_t*, T*, cudaStream_t); \
-  template void launch_gemv_rows<T>(int, const T*, const T*, T*, cudaStream_t);
+  template void launch_gemv_rows<T>(int, int, const T*, const T*, T*, cudaStream_t);
 H2_INST_SOLVE(double)
 H2_INST_SOLVE(float)
 #define H2_INST_SUBST(T, TS)                                                                                   \

@@ -121,3 +121,17 @@ def test_memory_limit_gives_oom_before_any_launch(B):
         assert need >= plan["device_bytes_build"]
     finally:
         B.h2_set_memory_limit(0)
+
+
+def test_forest_depth_checks_before_any_device_work():
+    """h2_tree_depth, and h2_build_forest's refusal of systems of different
+    depths or of depth 0, are host checks made before any CUDA call."""
+    import ctypes
+    from paper_2502_02395_gb300 import binding as bd
+    assert bd.h2_tree_depth(4096, 256) == 4 and bd.h2_tree_depth(4097, 256) == 5
+    assert bd.h2_tree_depth(256, 256) == 0 and bd.h2_tree_depth(0, 256) == -1
+    rng = np.random.default_rng(0)
+    for ns in ([3000, 5000], [200, 300]):
+        with pytest.raises(bd.H2Error) as ei:
+            bd.h2_build_forest(bd.make_params(leaf=256), [rng.random((n, 3)) for n in ns])
+        assert ei.value.status == -1 and "depth" in ei.value.message

@@ -1,0 +1,119 @@
+"""Batched systems as forests (h2_build_forest, h2_batch_create_forest):
+several independent systems of one tree depth as one instance whose level
+arrays hold every system, so each level's kernels run once for all of them.
+
+What is checked, and why it pins the combination:
+  * A_H2 of the forest is block diagonal with the systems' own H^2 matrices:
+    its FP64 matvec equals each system's own h2_matvec to 1e-13 (padding
+    ranks with zero basis columns and leaves with padding points adds exact
+    zeros only), so a wrong box offset, row layout or skeleton offset fails;
+  * the factorization of the forest (padded ranks, one root per system) is a
+    preconditioner for that block-diagonal matrix: the refined solution of
+    every system matches its own instance's refined solution to 1e-8
+    relative (both solve to 1e-12), FP64 and FP16;
+  * the forest batch groups systems by depth, scales each right-hand side
+    to unit norm and stops the group at target / sqrt(m): every system's
+    residual, recomputed from an FP64 matvec, is at most the target, and
+    each solution matches the single-system solve.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KW = dict(kernel="laplace_eps", leaf=256, eta=1.0, tol=1e-8, far_samples=1024, near_samples=64)
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_02395_gb300 import build as bld
+    bld.build()
+    from paper_2502_02395_gb300 import binding
+    return binding
+
+
+def systems(ns, seed):
+    return [W.cube_points(n, seed + k) for k, n in enumerate(ns)]
+
+
+def test_forest_matvec_is_block_diagonal(B):
+    ns = [2600, 3500, 4096]  # depth 4 with leaf 256; ranks and leaves differ
+    P = systems(ns, 31)
+    assert len({B.h2_tree_depth(n, 256) for n in ns}) == 1
+    F = B.H2Solver.build_forest(P, **KW)
+    st = F.stats()
+    assert st["systems"] == len(ns) and st["levels"][0]["nb"] == len(ns)
+    singles = [B.H2Solver.build(p, **KW) for p in P]
+    x = [W.uniform_rhs(n, 40 + k) for k, n in enumerate(ns)]
+    y = F.matvec(np.concatenate(x))
+    off = 0
+    for k, S in enumerate(singles):
+        ys = S.matvec(x[k])
+        e = np.linalg.norm(y[off:off + ns[k]] - ys) / np.linalg.norm(ys)
+        print(f"system {k} (N {ns[k]}, K {S.stats()['levels'][-1]['K']}): forest vs own matvec {e:.2e}")
+        assert e <= 1e-13
+        off += ns[k]
+    for S in singles:
+        S.close()
+    F.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16"])
+def test_forest_solve_matches_single_systems(B, prec):
+    ns = [2300, 3000, 3900, 4096]
+    P = systems(ns, 51)
+    F = B.H2Solver.build_forest(P, **KW)
+    b = [W.uniform_rhs(n, 60 + k) for k, n in enumerate(ns)]
+    F.factor(prec)
+    x, rel, its = F.solve(np.concatenate(b), target=1e-12, max_iters=200)
+    assert rel <= 1e-12
+    off = 0
+    for k, p in enumerate(P):
+        S = B.H2Solver.build(p, **KW)
+        S.factor(prec)
+        xs, rs, _ = S.solve(b[k], target=1e-12, max_iters=200)
+        e = np.linalg.norm(x[off:off + ns[k]] - xs) / np.linalg.norm(xs)
+        print(f"{prec} system {k}: forest vs single solution {e:.2e} ({its} forest steps)")
+        assert rs <= 1e-12 and e <= 1e-8
+        off += ns[k]
+        S.close()
+    F.close()
+
+
+def test_forest_batch_groups_and_targets(B):
+    """Two depths (3 and 4 with leaf 256) give two groups; Gaussian systems
+    with their own length scales pass points divided by l and l = 1."""
+    ns = [1500, 1900, 2048, 2500, 3300, 4000]
+    ells = [0.3, 0.45, 0.35, 0.5, 0.4, 0.3]
+    P = systems(ns, 71)
+    kw = dict(kernel="gaussian", ell=1.0, diag_shift=1.0, leaf=256, eta=1.0, tol=1e-8, far_samples=1024,
+              near_samples=64)
+    bt = B.H2Batch.forest([p / l for p, l in zip(P, ells)], **kw)
+    st = bt.stats()
+    assert st["mode"] == "forest" and st["groups"] == 2 and sorted(st["group_systems"]) == [3, 3]
+    b = [W.uniform_rhs(n, 80 + k) for k, n in enumerate(ns)]
+    X, rel, its, sec = bt.run("fp16", b, target=1e-10, max_iters=200)
+    print(f"forest batch: {sec:.3f} s, relres {[f'{r:.1e}' for r in rel]}, steps {its}")
+    for k in range(len(ns)):
+        assert rel[k] <= 1e-10
+        # the same system alone (scaled points, l = 1), FP64
+        S = B.H2Solver.build(P[k] / ells[k], **kw)
+        S.factor("fp64")
+        xs, _, _ = S.solve(b[k], target=1e-12, max_iters=200)
+        e = np.linalg.norm(X[k] - xs) / np.linalg.norm(xs)
+        S.close()
+        # and against the unscaled points with its own l: the same matrix up
+        # to the construction's rounding, so the residual stays at the
+        # approximation level (a length scale left out gives O(1))
+        S = B.H2Solver.build(P[k], kernel="gaussian", ell=ells[k], diag_shift=1.0, leaf=256, eta=1.0, tol=1e-8,
+                             far_samples=1024, near_samples=64)
+        r = np.linalg.norm(b[k] - S.matvec(X[k])) / np.linalg.norm(b[k])
+        S.close()
+        print(f"  system {k}: vs its own FP64 solve {e:.2e}; residual against the unscaled instance {r:.2e}")
+        assert e <= 1e-8 and r <= 1e-3
+    bt.close()
