@@ -66,6 +66,12 @@ def parse():
                          "uneven size (workloads.batch_systems), factored and solved concurrently")
     ap.add_argument("--batch-max-iters", type=int, default=600)
     ap.add_argument("--batch-mode", choices=["forest", "pool"], default="forest")
+    ap.add_argument("--batch-leaf", type=int, default=128)
+    ap.add_argument("--batch-near-samples", type=int, default=0)
+    ap.add_argument("--batch-shift", type=float, default=None,
+                    help="diagonal shift of the batch systems (default: the workload's)")
+    ap.add_argument("--rank-study", action="store_true",
+                    help="instead of the step: the learned rank predictor against the plain build at N = 2^20")
     ap.add_argument("--dense-rows", type=int, default=4096,
                     help="rows sampled for the check against the dense matrix after the timed region (0: none)")
     ap.add_argument("--build", default="plain", choices=["plain", "gpu"],
@@ -307,10 +313,14 @@ def run_batch(args):
     in [4096, 65536], l in [0.05, 0.5], + I on the diagonal, tol 1e-8),
     factorizations in --prec refined to --target, one JSON line.
     --batch-mode forest (default): the systems grouped by tree depth (leaf
-    256), each group one instance whose levels are single launches over its
-    systems (points divided by l, l = 1); pool: one instance per system
-    (leaf 128 below N = 16384, else 256).  The library's worker pool runs the
-    groups or systems with the worker count its tuner picks."""
+    --batch-leaf, 128 by default: the padded forests of 64 systems at leaf
+    256 would need about 330 GB), each group one instance whose levels are
+    single launches over its systems (points divided by l, l = 1); pool: one
+    instance per system (leaf 128 below N = 16384, else 256).  Close-field
+    samples --batch-near-samples (0: every point of each close box; with 64
+    the pre-factorization basis misses the Gaussian's fill-ins and the
+    refinement stalls).  The library's worker pool runs the groups or
+    systems with the worker count its tuner picks."""
     import torch
     import workloads as W
     from paper_2502_02395_gb300 import build as bld
@@ -318,20 +328,23 @@ def run_batch(args):
     from paper_2502_02395_gb300 import H2Solver
     from paper_2502_02395_gb300.binding import H2Batch
     specs = W.batch_systems(count=args.batch)
+    if args.batch_shift is not None:
+        for sp in specs:
+            sp["shift"] = args.batch_shift
     t0 = time.perf_counter()
     solvers, rhs = [], []
     forest = args.batch_mode == "forest"
     if forest:
         shift = specs[0]["shift"]
         batch = H2Batch.forest([W.cube_points(sp["n"], sp["point_seed"]) / sp["ell"] for sp in specs],
-                               kernel="gaussian", ell=1.0, diag_shift=shift, leaf=256, eta=1.0, tol=1e-8,
-                               far_samples=1024, near_samples=64)
+                               kernel="gaussian", ell=1.0, diag_shift=shift, leaf=args.batch_leaf, eta=1.0,
+                               tol=1e-8, far_samples=1024, near_samples=args.batch_near_samples)
         rhs = [W.uniform_rhs(sp["n"], sp["rhs_seed"]) for sp in specs]
     else:
         for sp in specs:
             P = W.cube_points(sp["n"], sp["point_seed"])
             solvers.append(H2Solver.build(P, kernel="gaussian", ell=sp["ell"], diag_shift=sp["shift"], leaf=sp["leaf"],
-                                          eta=1.0, tol=1e-8, far_samples=1024, near_samples=64))
+                                          eta=1.0, tol=1e-8, far_samples=1024, near_samples=args.batch_near_samples))
             rhs.append(torch.from_numpy(W.uniform_rhs(sp["n"], sp["rhs_seed"])).cuda())
         batch = H2Batch(solvers)
     build_s = time.perf_counter() - t0
@@ -349,6 +362,8 @@ def run_batch(args):
             "workers": workers, "tune_seconds_by_workers": tune, "sequential_s": tune.get("1"),
             "speedup_vs_one_worker": (tune.get("1") / value) if tune.get("1") else None,
             "mode": args.batch_mode, "groups": batch.stats().get("group_systems"),
+            "leaf": args.batch_leaf if forest else "128 / 256", "near_samples": args.batch_near_samples,
+            "diag_shift": specs[0]["shift"],
             "total_N": int(sum(s["n"] for s in specs)), "N": [s["n"] for s in specs],
             "iters": its_all, "converged": int(sum(r <= args.target for r in rel_all)),
             "relres_max": float(max(rel_all)), "build_s": build_s, "dtype": {"fp16": "f16/f32/f64", "bf16": "bf16/f32/f64"}.get(
@@ -401,10 +416,80 @@ def dense_rows_check(wl, P, b, x, S, rows=4096, chunk=16384):
             "h2_vs_dense": float(np.linalg.norm(h2x - Ax) / np.linalg.norm(Ax))}
 
 
+def run_rank_study(args):
+    """--rank-study: the learned rank predictor at N = 2^20
+    (cube1048576_laplace: 1/(r+1e-3), leaf 256, eta 1, tol 1e-8).  The model
+    is trained on the GPU on the plain compression's ranks of the solver
+    workloads (workloads.rank_training_sets); then the same problem is built
+    twice, by the plain rank-revealing host construction and by the
+    predicted layout with GPU sketches (h2_build_gpu with the model), and
+    each instance is factored (--prec) and solved to 1e-10.  Reported per
+    build: construction seconds, per-level ranks, fallbacks, the refined
+    solve's time and steps, and the H^2 approximation error on 1024 exactly
+    evaluated rows.  One JSON line."""
+    import torch
+    import workloads as W
+    from paper_2502_02395_gb300 import build as bld
+    bld.build()
+    from paper_2502_02395_gb300 import binding as B
+    wl = W.workload("cube1048576_laplace")
+    P, b = wl.points(), wl.rhs()
+    kw = dict(kernel=wl.kernel, leaf=wl.leaf, eta=wl.eta, tol=wl.tol, far_samples=wl.far_samples,
+              near_samples=wl.near_samples)
+    t0 = time.perf_counter()
+    F, Y = [], []
+    for pts, k2 in W.rank_training_sets():
+        f, y, _ = B.h2_rank_data(B.make_params(**k2), pts)
+        F.append(f)
+        Y.append(y)
+    F, Y = np.concatenate(F), np.concatenate(Y)
+    data_s = time.perf_counter() - t0
+    m = B.h2_rank_model_create(7)
+    loss0 = float(np.mean((B.h2_rank_model_predict(m, F) - Y) ** 2))
+    t0 = time.perf_counter()
+    loss = B.h2_rank_model_train(m, F, Y, steps=1500, lr=3e-3)
+    train_s = time.perf_counter() - t0
+
+    def measure(S, build_s):
+        st = S.stats()
+        c = st.get("construction", {})
+        S.factor(args.prec)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        x, rel, its = S.solve(b, target=1e-10, max_iters=200)
+        torch.cuda.synchronize()
+        step = time.perf_counter() - t
+        chk = dense_rows_check(wl, P, b, x, S, rows=1024)
+        return {"build_s": build_s, "compress_s": c.get("compress_s"), "K": [lv["K"] for lv in st["levels"]],
+                "fallback_boxes": c.get("fallback_boxes"), "fallback_levels": c.get("fallback_levels"),
+                "gpu_levels": c.get("gpu_levels"), "solve_s": step, "relres": rel, "iters": its,
+                "h2_vs_dense_rows": chk["h2_vs_dense"] if chk else None}
+
+    t0 = time.perf_counter()
+    S = B.H2Solver.build(P, **kw)
+    plain = measure(S, time.perf_counter() - t0)
+    S.close()
+    t0 = time.perf_counter()
+    S = B.H2Solver.build_gpu(P, m, 0, **kw)
+    pred = measure(S, time.perf_counter() - t0)
+    S.close()
+    B.h2_rank_model_destroy(m)
+    line = {"metric": "H2 construction at N=2^20: learned-rank GPU build vs plain rank-revealing build",
+            "workload": wl.name, "N": wl.n, "prec": args.prec, "data": "synthetic",
+            "training": {"samples": int(len(Y)), "data_s": data_s, "train_s": train_s, "loss0": loss0, "loss": loss,
+                         "steps": 1500},
+            "plain": plain, "predicted_gpu": pred,
+            "build_speedup": plain["build_s"] / pred["build_s"] if pred["build_s"] else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.batch > 0:
         run_batch(args)
+        return
+    if args.rank_study:
+        run_rank_study(args)
         return
     import workloads as W
     wl = W.workload(args.workload)

@@ -105,21 +105,12 @@ def test_gpu_gradient_matches_oracle(B, seed):
 
 
 def _training_set(B):
-    """Ranks of the plain compression on the three solver workloads: cube
-    2048 / 1/(r+1e-3) / leaf 64 (tolerances 1e-4 .. 1e-10), sphere 65536 /
-    1/(r+1e-3) / leaf 256 (1e-6, 1e-8) and cube 262144 / Yukawa + 1 / leaf
-    256 (1e-8, 1e-10)."""
+    """Ranks of the plain compression on the three solver workloads
+    (workloads.rank_training_sets)."""
     import workloads as W
-    sets = []
-    for tol in (1e-4, 1e-6, 1e-8, 1e-10):
-        sets.append((W.cube_points(2048, 1), dict(kernel="laplace_eps", leaf=64, tol=tol)))
-    for tol in (1e-6, 1e-8):
-        sets.append((W.sphere_points(65536, 3), dict(kernel="laplace_eps", leaf=256, tol=tol)))
-    for tol in (1e-8, 1e-10):
-        sets.append((W.cube_points(262144, 5), dict(kernel="yukawa_eps", leaf=256, tol=tol, diag_shift=1.0)))
     F, Y = [], []
-    for pts, kw in sets:
-        f, y, _ = B.h2_rank_data(B.make_params(far_samples=1024, near_samples=64, **kw), pts)
+    for pts, kw in W.rank_training_sets():
+        f, y, _ = B.h2_rank_data(B.make_params(**kw), pts)
         F.append(f)
         Y.append(y)
     return np.concatenate(F), np.concatenate(Y)

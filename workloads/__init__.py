@@ -112,7 +112,27 @@ WORKLOADS = {
     # diagonal, leaf 256, eta 1, tol 1e-10 with the default rank cap.
     "cube262144_yukawa": Workload("cube262144_yukawa", 262144, "cube", 5, 6,
                                   "yukawa_eps", 256, 1.0, 1e-10, diag_shift=1.0),
+    # 2^20 points in the unit cube, 1/(r+1e-3), leaf 256, eta 1, tol 1e-8:
+    # the learned rank predictor against the plain rank-revealing build.
+    "cube1048576_laplace": Workload("cube1048576_laplace", 1048576, "cube", 9, 10,
+                                    "laplace_eps", 256, 1.0, 1e-8),
 }
+
+
+def rank_training_sets():
+    """The problems whose plain-compression ranks train the rank predictor:
+    (points, parameters) for cube 2048 / 1/(r+1e-3) / leaf 64 at tolerances
+    1e-4 .. 1e-10, sphere 65536 / 1/(r+1e-3) / leaf 256 at 1e-6 and 1e-8, and
+    cube 262144 / Yukawa + 1 / leaf 256 at 1e-8 and 1e-10 (far / near
+    samples 1024 / 64 throughout)."""
+    sets = []
+    for tol in (1e-4, 1e-6, 1e-8, 1e-10):
+        sets.append((cube_points(2048, 1), dict(kernel="laplace_eps", leaf=64, tol=tol)))
+    for tol in (1e-6, 1e-8):
+        sets.append((sphere_points(65536, 3), dict(kernel="laplace_eps", leaf=256, tol=tol)))
+    for tol in (1e-8, 1e-10):
+        sets.append((cube_points(262144, 5), dict(kernel="yukawa_eps", leaf=256, tol=tol, diag_shift=1.0)))
+    return [(P, dict(far_samples=1024, near_samples=64, **kw)) for P, kw in sets]
 
 
 def workload(name: str) -> Workload:
