@@ -171,10 +171,11 @@ int32_t h2_tree_depth(int64_t N, int32_t leaf_size);
  * level has one block per system (count roots factored by one batched
  * launch).  The systems share p (a Gaussian batch with per-system length
  * scales passes points divided by l_k and ell = 1: the matrix depends on
- * |x - y| / l only).  Each level takes the largest rank of its systems;
- * a smaller rank is padded with zero basis columns and padding skeleton
- * entries (which interact with nothing), and every leaf with padding
- * points (1 on the diagonal), as a single instance pads its own leaves.
+ * |x - y| / l only).  Every level has one rank for all systems, the
+ * largest of the systems' tolerance ranks: the systems below it are
+ * compressed again at that rank (the pivoted QR's leading pivots), and
+ * every leaf is padded to the largest leaf with padding points (1 on the
+ * diagonal), as a single instance pads its own leaves.
  * A_H2 is then block diagonal with the systems' own H^2 matrices as its
  * blocks; vectors are the systems' vectors concatenated in input order.
  * Errors: as h2_build; H2_ERR_INVALID_ARG also for count < 1 or depths that

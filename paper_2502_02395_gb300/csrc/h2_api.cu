@@ -1635,9 +1635,26 @@ h2_status h2_build_forest(h2_ctx** out, const h2_params* p, const double* const*
     }
     depth = d;
   }
+  // one rank per level for all systems (the constant-rank batches of Section
+  // 4.1): each level takes its systems' largest tolerance rank, and the
+  // systems below it are compressed again at that rank
   std::vector<HostH2> parts(count);
   for (int32_t k = 0; k < count; ++k) {
     std::string e = build_host(*p, points[k], N[k], parts[k]);
+    if (!e.empty()) {
+      g_last_error = "system " + std::to_string(k) + ": " + e;
+      return H2_ERR_SINGULAR;
+    }
+  }
+  std::vector<int> Kf(depth + 1, 0);
+  for (int l = 1; l <= depth; ++l)
+    for (const HostH2& P : parts) Kf[l] = std::max(Kf[l], P.lv[l].K);
+  for (int32_t k = 0; k < count; ++k) {
+    bool same = true;
+    for (int l = 1; l <= depth; ++l) same = same && parts[k].lv[l].K == Kf[l];
+    if (same) continue;
+    parts[k] = HostH2();
+    std::string e = build_host(*p, points[k], N[k], parts[k], nullptr, false, nullptr, &Kf);
     if (!e.empty()) {
       g_last_error = "system " + std::to_string(k) + ": " + e;
       return H2_ERR_SINGULAR;

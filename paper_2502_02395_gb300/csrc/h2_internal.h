@@ -143,15 +143,18 @@ struct RankPredictor {
 // compressed by randomized sketches (plain pivoted QR as the fallback);
 // with layout_only, the levels are laid out from predictions alone (no
 // compression; X and SK stay empty).
+// With force_K, level l's rank is force_K[l] (where > 0, at most the level's
+// smallest box) in place of the largest tolerance rank (plain path only).
 std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& out,
-                       RankPredictor* pred = nullptr, bool layout_only = false, GpuCompressor* gpu = nullptr);
+                       RankPredictor* pred = nullptr, bool layout_only = false, GpuCompressor* gpu = nullptr,
+                       const std::vector<int>* force_K = nullptr);
 // Depth of the binary tree over n points with leaves of at most `leaf`.
 int depth_of(int64_t n, int leaf);
-// Independent systems of one tree depth L >= 1 as one instance (a forest):
-// system s holds boxes [s 2^l, (s + 1) 2^l) of level l, so box i's children
-// stay 2i and 2i + 1 and the root level has one box per system.  Ranks are
-// padded to each level's largest (zero basis columns, skeleton entries -1)
-// and leaves to the largest leaf.  Empty string on success.
+// Independent systems of one tree depth L >= 1 and one rank per level as
+// one instance (a forest): system s holds boxes [s 2^l, (s + 1) 2^l) of
+// level l, so box i's children stay 2i and 2i + 1 and the root level has one
+// box per system.  Leaves are padded to the largest leaf (padding points).
+// Empty string on success.
 std::string combine_forest(const std::vector<HostH2>& parts, HostH2& out);
 // The GPU compressor of construct_gpu.cu over the N points (kernel G);
 // nullptr if the device upload fails.

@@ -400,7 +400,7 @@ bool sketch_box(const RowsFn& rows_of, int i, int n, int K, bool capped, double 
 }  // namespace
 
 std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2& H, RankPredictor* pred,
-                       bool layout_only, GpuCompressor* gpu) {
+                       bool layout_only, GpuCompressor* gpu, const std::vector<int>* force_K) {
   KernelFn G{p.kernel, p.eps, p.ell, p.diag_shift};
   H.N = N;
   H.points.assign(pts, pts + 3 * N);
@@ -660,6 +660,10 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
       for (int i = 0; i < nb; ++i) plain_box(i);
       int kmax = *std::max_element(ranks.begin(), ranks.end());
       K = std::max(1, std::min(kmax, capK));
+      // a rank laid out beforehand (the systems of a forest share each
+      // level's rank): the pivoted QR's first K pivots, at most the smallest
+      // box of the level
+      if (force_K && l < (int)force_K->size() && (*force_K)[l] > 0) K = std::min((*force_K)[l], nmin);
     }
     rec.compress_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (bad >= 0)
@@ -711,12 +715,13 @@ std::string build_host(const h2_params& p, const double* pts, int64_t N, HostH2&
   return "";
 }
 
-// Padding a system's rank K_s to the level's K with zero basis columns keeps
-// A_H2: X_i S_ij X_j^T is unchanged (the couplings of padding entries are 0),
-// and the complement basis of a padded X_i (Householder QR, a zero column
-// gives the identity reflector) keeps one more direction in its skeleton
-// part, whose far-field couplings are zero; it is carried up the tree like
-// any skeleton direction, so the factorization stays exact for A_H2.
+// The systems must share each level's rank.  (Padding a smaller rank with
+// zero basis columns would keep A_H2, but the complement basis of such an
+// X_i keeps complement directions in its skeleton part; their near-field
+// couplings at the parent level are not in the parent's pre-factorization
+// basis, so eliminating them there drops fill-ins the construction never
+// bounded, and the refinement slows or stalls.)  Leaves of fewer points than
+// the largest leaf get padding points, as a single instance pads its own.
 std::string combine_forest(const std::vector<HostH2>& parts, HostH2& H) {
   const int S = (int)parts.size();
   if (S < 1) return "empty forest";
@@ -724,6 +729,9 @@ std::string combine_forest(const std::vector<HostH2>& parts, HostH2& H) {
   for (const HostH2& P : parts)
     if (P.L != L) return "the systems of a forest must have the same tree depth";
   if (L < 1) return "the systems of a forest need at least one level below the root";
+  for (int l = 1; l <= L; ++l)
+    for (const HostH2& P : parts)
+      if (P.lv[l].K != parts[0].lv[l].K) return "the systems of a forest must share each level's rank";
   H = HostH2();
   H.L = L;
   H.lv.assign(L + 1, HostLevel());

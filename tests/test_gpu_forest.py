@@ -4,17 +4,22 @@ arrays hold every system, so each level's kernels run once for all of them.
 
 What is checked, and why it pins the combination:
   * A_H2 of the forest is block diagonal with the systems' own H^2 matrices:
-    its FP64 matvec equals each system's own h2_matvec to 1e-13 (padding
-    ranks with zero basis columns and leaves with padding points adds exact
-    zeros only), so a wrong box offset, row layout or skeleton offset fails;
-  * the factorization of the forest (padded ranks, one root per system) is a
+    with one rank for every system (a rank cap all of them reach), its FP64
+    matvec equals each system's own h2_matvec to 1e-13 (leaves padded with
+    padding points add exact zeros only), so a wrong box offset, row layout
+    or skeleton offset fails;
+  * the factorization of the forest (one root per system) is a
     preconditioner for that block-diagonal matrix: the refined solution of
     every system matches its own instance's refined solution to 1e-8
     relative (both solve to 1e-12), FP64 and FP16;
+  * systems whose tolerance ranks differ are compressed again at each
+    level's largest rank; the forest then converges within a few steps of
+    its slowest system alone (zero-padded ranks stalled here: the padding
+    directions' near-field couplings are missing from the parent's
+    pre-factorization basis);
   * the forest batch groups systems by depth, scales each right-hand side
     to unit norm and stops the group at target / sqrt(m): every system's
-    residual, recomputed from an FP64 matvec, is at most the target, and
-    each solution matches the single-system solve.
+    residual, recomputed from an FP64 matvec, is at most the target.
 """
 import numpy as np
 import pytest
@@ -23,7 +28,8 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-KW = dict(kernel="laplace_eps", leaf=256, eta=1.0, tol=1e-8, far_samples=1024, near_samples=64)
+# tol 1e-10 with a rank cap of 64 that every system reaches: equal ranks
+KW = dict(kernel="laplace_eps", leaf=256, eta=1.0, tol=1e-10, max_rank=64, far_samples=1024, near_samples=64)
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +61,8 @@ def test_forest_matvec_is_block_diagonal(B):
     for k, S in enumerate(singles):
         ys = S.matvec(x[k])
         e = np.linalg.norm(y[off:off + ns[k]] - ys) / np.linalg.norm(ys)
-        print(f"system {k} (N {ns[k]}, K {S.stats()['levels'][-1]['K']}): forest vs own matvec {e:.2e}")
+        assert [lv["K"] for lv in S.stats()["levels"]] == [lv["K"] for lv in st["levels"]]
+        print(f"system {k} (N {ns[k]}): forest vs own matvec {e:.2e}")
         assert e <= 1e-13
         off += ns[k]
     for S in singles:
@@ -85,6 +92,38 @@ def test_forest_solve_matches_single_systems(B, prec):
     F.close()
 
 
+def test_forest_mixed_ranks_converge(B):
+    """Gaussian systems of one depth whose tolerance ranks differ (length
+    scales 0.15 .. 0.45, points divided by l, every close-field point
+    sampled): the forest takes each level's largest rank, and its FP16
+    refinement needs at most 3 steps more than the slowest system alone."""
+    ns = [1300, 1600, 1800, 2048]
+    ells = [0.15, 0.25, 0.35, 0.45]
+    kw = dict(kernel="gaussian", ell=1.0, diag_shift=1.0, leaf=128, eta=1.0, tol=1e-8, far_samples=1024,
+              near_samples=0)
+    P = [p / l for p, l in zip(systems(ns, 91), ells)]
+    b = [W.uniform_rhs(n, 95 + k) for k, n in enumerate(ns)]
+    ks, its_single = [], []
+    for k, p in enumerate(P):
+        S = B.H2Solver.build(p, **kw)
+        ks.append([lv["K"] for lv in S.stats()["levels"]])
+        S.factor("fp16")
+        _, rs, it = S.solve(b[k], target=1e-10, max_iters=200)
+        assert rs <= 1e-10
+        its_single.append(it)
+        S.close()
+    F = B.H2Solver.build_forest(P, **kw)
+    kf = [lv["K"] for lv in F.stats()["levels"]]
+    assert kf == [max(c) for c in zip(*ks)]
+    assert len({tuple(k) for k in ks}) > 1
+    F.factor("fp16")
+    bn = np.concatenate([v / np.linalg.norm(v) for v in b])
+    _, rel, its = F.solve(bn, target=1e-10 / 2, max_iters=200)
+    print(f"ranks {ks} -> forest {kf}; steps alone {its_single}, forest {its}")
+    assert rel <= 0.5e-10 and its <= max(its_single) + 3
+    F.close()
+
+
 def test_forest_batch_groups_and_targets(B):
     """Two depths (3 and 4 with leaf 256) give two groups; Gaussian systems
     with their own length scales pass points divided by l and l = 1."""
@@ -101,7 +140,8 @@ def test_forest_batch_groups_and_targets(B):
     print(f"forest batch: {sec:.3f} s, relres {[f'{r:.1e}' for r in rel]}, steps {its}")
     for k in range(len(ns)):
         assert rel[k] <= 1e-10
-        # the same system alone (scaled points, l = 1), FP64
+        # the same system alone (scaled points, l = 1; its own ranks, so
+        # the two H^2 matrices differ at the compression's level), FP64
         S = B.H2Solver.build(P[k] / ells[k], **kw)
         S.factor("fp64")
         xs, _, _ = S.solve(b[k], target=1e-12, max_iters=200)
@@ -115,5 +155,5 @@ def test_forest_batch_groups_and_targets(B):
         r = np.linalg.norm(b[k] - S.matvec(X[k])) / np.linalg.norm(b[k])
         S.close()
         print(f"  system {k}: vs its own FP64 solve {e:.2e}; residual against the unscaled instance {r:.2e}")
-        assert e <= 1e-8 and r <= 1e-3
+        assert e <= 1e-5 and r <= 1e-3
     bt.close()
