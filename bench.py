@@ -66,7 +66,8 @@ def parse():
                          "uneven size (workloads.batch_systems), factored and solved concurrently")
     ap.add_argument("--batch-max-iters", type=int, default=600)
     ap.add_argument("--batch-mode", choices=["forest", "pool"], default="forest")
-    ap.add_argument("--batch-leaf", type=int, default=128)
+    ap.add_argument("--batch-leaf", type=int, default=0,
+                    help="leaf size of every batch system (0: 128 below N = 16384, else 256)")
     ap.add_argument("--batch-near-samples", type=int, default=0)
     ap.add_argument("--batch-shift", type=float, default=None,
                     help="diagonal shift of the batch systems (default: the workload's)")
@@ -312,11 +313,12 @@ def run_batch(args):
     """--batch S: S independent Gaussian-covariance systems (N log-uniform
     in [4096, 65536], l in [0.05, 0.5], + I on the diagonal, tol 1e-8),
     factorizations in --prec refined to --target, one JSON line.
-    --batch-mode forest (default): the systems grouped by tree depth (leaf
-    --batch-leaf, 128 by default: the padded forests of 64 systems at leaf
-    256 would need about 330 GB), each group one instance whose levels are
-    single launches over its systems (points divided by l, l = 1); pool: one
-    instance per system (leaf 128 below N = 16384, else 256).  Close-field
+    Leaf size --batch-leaf (default 128 below N = 16384, else 256).
+    --batch-mode forest (default): the systems grouped by (leaf, tree
+    depth), each group one instance whose levels are single launches over
+    its systems (points divided by l, l = 1; the FP64 leaf blocks released
+    after each group is built, so that the padded forests fit); pool: one
+    instance per system.  Close-field
     samples --batch-near-samples (0: every point of each close box; with 64
     the pre-factorization basis misses the Gaussian's fill-ins and the
     refinement stalls).  The library's worker pool runs the groups or
@@ -336,14 +338,15 @@ def run_batch(args):
     forest = args.batch_mode == "forest"
     if forest:
         shift = specs[0]["shift"]
-        batch = H2Batch.forest([W.cube_points(sp["n"], sp["point_seed"]) / sp["ell"] for sp in specs],
-                               kernel="gaussian", ell=1.0, diag_shift=shift, leaf=args.batch_leaf, eta=1.0,
+        leaves = [args.batch_leaf or sp["leaf"] for sp in specs]
+        batch = H2Batch.forest([W.cube_points(sp["n"], sp["point_seed"]) / sp["ell"] for sp in specs], leaves,
+                               kernel="gaussian", ell=1.0, diag_shift=shift, leaf=256, eta=1.0,
                                tol=1e-8, far_samples=1024, near_samples=args.batch_near_samples)
         rhs = [W.uniform_rhs(sp["n"], sp["rhs_seed"]) for sp in specs]
     else:
         for sp in specs:
             P = W.cube_points(sp["n"], sp["point_seed"])
-            solvers.append(H2Solver.build(P, kernel="gaussian", ell=sp["ell"], diag_shift=sp["shift"], leaf=sp["leaf"],
+            solvers.append(H2Solver.build(P, kernel="gaussian", ell=sp["ell"], diag_shift=sp["shift"], leaf=args.batch_leaf or sp["leaf"],
                                           eta=1.0, tol=1e-8, far_samples=1024, near_samples=args.batch_near_samples))
             rhs.append(torch.from_numpy(W.uniform_rhs(sp["n"], sp["rhs_seed"])).cuda())
         batch = H2Batch(solvers)
@@ -362,7 +365,7 @@ def run_batch(args):
             "workers": workers, "tune_seconds_by_workers": tune, "sequential_s": tune.get("1"),
             "speedup_vs_one_worker": (tune.get("1") / value) if tune.get("1") else None,
             "mode": args.batch_mode, "groups": batch.stats().get("group_systems"),
-            "leaf": args.batch_leaf if forest else "128 / 256", "near_samples": args.batch_near_samples,
+            "leaf": args.batch_leaf or "128 below N = 16384, else 256", "near_samples": args.batch_near_samples,
             "diag_shift": specs[0]["shift"],
             "total_N": int(sum(s["n"] for s in specs)), "N": [s["n"] for s in specs],
             "iters": its_all, "converged": int(sum(r <= args.target for r in rel_all)),

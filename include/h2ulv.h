@@ -310,12 +310,23 @@ h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
  *                         persistent warp-specialized kernel, one CTA per
  *                         SM, whose epilogue of one tile overlaps the MMAs
  *                         of the next (two TMEM accumulators).  The coupling
- *                         products, on their own stream, always use form 0. */
+ *                         products, on their own stream, always use form 0.
+ *   H2_OPT_FP64_LEAF      1 (default): keep the FP64 leaf near blocks; 0
+ *                         releases them (the largest array of an instance,
+ *                         8 bytes per entry), keeping the FP32 pair and FP16
+ *                         copies the FP16 path reads.  Afterwards FP64 and
+ *                         BF16 factorizations, the FP64 matvec (h2_matvec,
+ *                         arith 0, h2_matvec_noalloc), the FP64 residual
+ *                         option and the leaf "A" export return
+ *                         H2_ERR_STATE; 1 cannot undo a release (H2_ERR_STATE).
+ *                         0 also returns H2_ERR_STATE when the instance has
+ *                         no FP16 copy of its leaf blocks. */
 typedef enum {
   H2_OPT_RR_LU_FP64 = 0,
   H2_OPT_RESIDUAL_FP64 = 1,
   H2_OPT_GRAPHS = 2,
-  H2_OPT_TC_KERNEL = 3
+  H2_OPT_TC_KERNEL = 3,
+  H2_OPT_FP64_LEAF = 4
 } h2_option;
 
 /* Set an h2_option to value (0 or 1; 0 .. 2 for H2_OPT_TC_KERNEL).
@@ -486,20 +497,24 @@ typedef struct h2_batch h2_batch;
 h2_status h2_batch_create(h2_batch** out, h2_ctx* const* ctxs, const int64_t* n, int32_t count);
 
 /* A batch in forest form over count systems that share the parameters p
- * (points[k]: N[k] x 3, host): the systems are grouped by tree depth and
- * each group is built as one h2_build_forest instance, owned by the batch.
- * h2_batch_run then factors each group (one launch per kernel and level
- * for all its systems) and solves its systems together: each right-hand
- * side is scaled to unit norm, the group is refined to target / sqrt(m)
- * for its m systems (then |r_k| <= |r| <= target for every system), and
- * each system's relative residual, written to relres, is recomputed from
- * one FP64 h2_matvec of the group; iters receives the group's count.  The
- * vectors B[k], X[k] of a forest batch are host memory (the scaling and
- * splitting run on the host; device vectors give H2_ERR_INVALID_ARG).  The
- * worker pool runs the groups.  Errors: as h2_build_forest (the group's
- * message is in h2_last_error(NULL)). */
+ * but the leaf size (points[k]: N[k] x 3, host; leaf[k] the leaf size of
+ * system k, or NULL for p->leaf_size): the systems are grouped by (leaf
+ * size, tree depth) and each group is built as one h2_build_forest
+ * instance, owned by the batch, whose FP64 leaf blocks are then released
+ * (H2_OPT_FP64_LEAF; the batch factors in FP16 or BF16 from the FP16 copy,
+ * so prec must be H2_PREC_FP16).  h2_batch_run then factors each group
+ * (one launch per kernel and level for all its systems) and solves its
+ * systems together: each right-hand side is scaled to unit norm, the group
+ * is refined to target / sqrt(m) for its m systems (then |r_k| <= |r| <=
+ * target for every system), and each system's relative residual, written
+ * to relres, is recomputed from one FP32-pair matvec of the group
+ * (h2_matvec_arith arith 2); iters receives the group's count.  The vectors
+ * B[k], X[k] of a forest batch are host memory (the scaling and splitting
+ * run on the host; device vectors give H2_ERR_INVALID_ARG).  The worker pool
+ * runs the groups.  Errors: as h2_build_forest (the group's message is in
+ * h2_last_error(NULL)). */
 h2_status h2_batch_create_forest(h2_batch** out, const h2_params* p, const double* const* points,
-                                 const int64_t* N, int32_t count);
+                                 const int64_t* N, const int32_t* leaf, int32_t count);
 
 /* Factor every system in precision prec (prec = -1: keep the current
  * factorizations) and, with B non-NULL, solve system i for B[i] into X[i]

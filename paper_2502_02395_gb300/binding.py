@@ -39,7 +39,7 @@ EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_sol
             "h2_batch_create_forest", "h2_batch_run", "h2_batch_tune",
             "h2_batch_stats", "h2_batch_last_error", "h2_batch_destroy",
             "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
-OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1, "graphs": 2, "tc_kernel": 3}
+OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1, "graphs": 2, "tc_kernel": 3, "fp64_leaf": 4}
 ARITH = {"fp64": 0, "fp32": 1, "fp32_pair": 2}
 
 
@@ -108,7 +108,7 @@ def lib() -> ctypes.CDLL:
             "h2_tree_depth": (i32, [i64, i32]),
             "h2_build_forest": (i32, [pp, vp, vp, vp, i32]),
             "h2_batch_create": (i32, [pp, vp, vp, i32]),
-            "h2_batch_create_forest": (i32, [pp, vp, vp, vp, i32]),
+            "h2_batch_create_forest": (i32, [pp, vp, vp, vp, vp, i32]),
             "h2_batch_run": (i32, [vp, i32, vp, vp, dbl, i32, vp, vp, vp]),
             "h2_batch_tune": (i32, [vp, i32, vp, vp, dbl, i32, vp]),
             "h2_batch_stats": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
@@ -410,12 +410,16 @@ class H2Batch:
         self.b = out
 
     @classmethod
-    def forest(cls, points_list, **kw):
+    def forest(cls, points_list, leaves=None, **kw):
+        """Systems grouped by (leaf size, tree depth); leaves: one leaf size
+        per system (None: the `leaf` parameter for all)."""
         pts, ptrs, ns = _point_arrays(points_list)
+        lv = None if leaves is None else (ctypes.c_int32 * len(pts))(*[int(v) for v in leaves])
         out = ctypes.c_void_p()
         params = make_params(**kw)
         _check(lib().h2_batch_create_forest(ctypes.byref(out), ctypes.byref(params), ctypes.cast(ptrs, ctypes.c_void_p),
-                                            ctypes.cast(ns, ctypes.c_void_p), len(pts)), None)
+                                            ctypes.cast(ns, ctypes.c_void_p),
+                                            None if lv is None else ctypes.cast(lv, ctypes.c_void_p), len(pts)), None)
         return cls(_handle=out, _count=len(pts))
 
     def _ptrs(self, arrs):

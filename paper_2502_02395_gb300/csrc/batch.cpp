@@ -26,6 +26,7 @@
 #include <numeric>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/h2ulv.h"
@@ -71,7 +72,9 @@ h2_status solve_group(h2_batch* b, int g, const double* const* B, double* const*
   const double tg = target > 0 ? target / std::sqrt((double)sys.size()) : target;
   h2_status r = h2_solve(c, bg.data(), xg.data(), tg, max_iters, &rel, &its);
   if (r != H2_OK && r != H2_ERR_NOT_CONVERGED) return r;
-  h2_status rm = h2_matvec(c, xg.data(), yg.data());
+  // A_H2 x in FP32-pair arithmetic (about 2^-46 of the row sums; the FP64
+  // leaf blocks are released)
+  h2_status rm = h2_matvec_arith(c, xg.data(), yg.data(), 2);
   if (rm != H2_OK) return rm;
   int worst = -1;
   double wrel = 0;
@@ -199,15 +202,16 @@ h2_status h2_batch_create(h2_batch** out, h2_ctx* const* ctxs, const int64_t* n,
 }
 
 h2_status h2_batch_create_forest(h2_batch** out, const h2_params* p, const double* const* points, const int64_t* N,
-                                 int32_t count) {
+                                 const int32_t* leaf, int32_t count) {
   if (!out || !p || !points || !N || count < 1) return H2_ERR_INVALID_ARG;
   *out = nullptr;
-  // group the systems by tree depth (ascending)
-  std::vector<std::pair<int, int>> key(count);
+  // group the systems by (leaf size, tree depth), ascending
+  std::vector<std::tuple<int, int, int>> key(count);
   for (int32_t s = 0; s < count; ++s) {
-    const int d = h2_tree_depth(N[s], p->leaf_size);
-    if (d < 1 || !points[s]) return H2_ERR_INVALID_ARG;
-    key[s] = {d, s};
+    const int lf = leaf ? leaf[s] : p->leaf_size;
+    const int d = h2_tree_depth(N[s], lf);
+    if (lf < 1 || d < 1 || !points[s]) return H2_ERR_INVALID_ARG;
+    key[s] = {lf, d, s};
   }
   std::sort(key.begin(), key.end());
   h2_batch* b = new h2_batch();
@@ -217,14 +221,14 @@ h2_status h2_batch_create_forest(h2_batch** out, const h2_params* p, const doubl
   b->sys_n.assign(N, N + count);
   for (int32_t k = 0; k < count;) {
     int32_t e = k;
-    while (e < count && key[e].first == key[k].first) ++e;
+    while (e < count && std::get<0>(key[e]) == std::get<0>(key[k]) && std::get<1>(key[e]) == std::get<1>(key[k])) ++e;
     const int g = (int)b->group_sys.size();
     std::vector<int> sys;
     std::vector<const double*> pts;
     std::vector<int64_t> ns;
     int64_t off = 0;
     for (int32_t t = k; t < e; ++t) {
-      const int s = key[t].second;
+      const int s = std::get<2>(key[t]);
       sys.push_back(s);
       pts.push_back(points[s]);
       ns.push_back(N[s]);
@@ -232,10 +236,15 @@ h2_status h2_batch_create_forest(h2_batch** out, const h2_params* p, const doubl
       b->sys_off[s] = off;
       off += N[s];
     }
+    h2_params pg = *p;
+    pg.leaf_size = std::get<0>(key[k]);
     h2_ctx* c = nullptr;
-    h2_status st = h2_build_forest(&c, p, pts.data(), ns.data(), (int32_t)sys.size());
+    h2_status st = h2_build_forest(&c, &pg, pts.data(), ns.data(), (int32_t)sys.size());
+    // the batch factors in FP16 / BF16 only: the FP64 leaf blocks (8 bytes of
+    // the instance's 14 per leaf entry) go before the next group is built
+    if (st == H2_OK) st = h2_set_option(c, H2_OPT_FP64_LEAF, 0);
     if (st != H2_OK) {
-      b->err = std::string("group of depth ") + std::to_string(key[k].first) + ": " + h2_last_error(nullptr);
+      if (c) h2_destroy(c);
       h2_batch_destroy(b);
       return st;
     }

@@ -584,6 +584,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   if (!mixed) {
     Aleaf = reinterpret_cast<const T*>(c->A64);
   } else if (L == 0 || !F.lv[L].tc) {
+    if (!c->A64) return fail(H2_ERR_STATE, "the leaf level needs the FP64 leaf blocks, which were released");
     launch_convert<double, T>(c->A64, F.lv[L].Ain, (int64_t)c->lv[L].NP * c->lv[L].D * c->lv[L].D, st);
     Aleaf = F.lv[L].Ain;
   }
@@ -1646,9 +1647,19 @@ h2_status h2_build_forest(h2_ctx** out, const h2_params* p, const double* const*
       return H2_ERR_SINGULAR;
     }
   }
+  // the shared rank: the largest, rounded up to a multiple of 64 (upper
+  // boxes of dimension 2K then fit the tensor-core tiles), at most the
+  // smallest box of the level (leaves: the fewest points of any leaf)
   std::vector<int> Kf(depth + 1, 0);
-  for (int l = 1; l <= depth; ++l)
+  int64_t leaf_min = INT64_MAX;
+  for (const HostH2& P : parts)
+    for (size_t i = 0; i + 1 < P.leaf_offsets.size(); ++i)
+      leaf_min = std::min<int64_t>(leaf_min, P.leaf_offsets[i + 1] - P.leaf_offsets[i]);
+  for (int l = depth; l >= 1; --l) {
     for (const HostH2& P : parts) Kf[l] = std::max(Kf[l], P.lv[l].K);
+    const int64_t nmin = (l == depth) ? leaf_min : 2 * (int64_t)Kf[l + 1];
+    Kf[l] = (int)std::min<int64_t>((Kf[l] + 63) / 64 * 64, nmin);
+  }
   for (int32_t k = 0; k < count; ++k) {
     bool same = true;
     for (int l = 1; l <= depth; ++l) same = same && parts[k].lv[l].K == Kf[l];
@@ -1792,6 +1803,10 @@ h2_status h2_factor(h2_ctx* c, int32_t prec) {
     c->err = "unknown precision";
     return H2_ERR_INVALID_ARG;
   }
+  if (!c->A64 && (prec == H2_PREC_FP64 || (prec == H2_PREC_BF16 && !c->A16[1]))) {
+    c->err = "this factorization needs the FP64 leaf blocks, which were released (H2_OPT_FP64_LEAF)";
+    return H2_ERR_STATE;
+  }
   c->prec = -1;
   drop_graphs(c);
   const bool fresh = (prec == H2_PREC_FP64) ? c->f64.lv.empty() : c->f32.lv.empty();
@@ -1820,6 +1835,7 @@ h2_status h2_ulv_apply(h2_ctx* c, const double* b, double* x) {
 h2_status h2_matvec(h2_ctx* c, const double* x, double* y) {
   if (!c || !x || !y) return H2_ERR_INVALID_ARG;
   c->err.clear();
+  if (!c->A64) { c->err = "the FP64 leaf blocks were released (H2_OPT_FP64_LEAF)"; return H2_ERR_STATE; }
   CKS(vec_in(c, x, c->x64));
   matvec_impl(c, c->x64, c->y64);
   CKC(cudaGetLastError());
@@ -1856,6 +1872,10 @@ h2_status h2_solve(h2_ctx* c, const double* b, double* x, double target, int32_t
   if (!c || !b || !x || max_iters < 0) return H2_ERR_INVALID_ARG;
   c->err.clear();
   if (!factor_ready(c)) { c->err = "no factorization"; return H2_ERR_STATE; }
+  if (!c->A64 && c->resid64) {
+    c->err = "the FP64 residual needs the FP64 leaf blocks, which were released (H2_OPT_FP64_LEAF)";
+    return H2_ERR_STATE;
+  }
   cudaStream_t st = c->stream;
   const DevLevel& lf = c->lv[c->L];
   const int64_t nslot = (int64_t)lf.nb * lf.D;
@@ -1961,6 +1981,28 @@ h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value) {
       c->use_graphs = value != 0;
       drop_graphs(c);
       return H2_OK;
+    case H2_OPT_FP64_LEAF:
+      if (value == 1) {
+        if (c->A64) return H2_OK;
+        c->err = "the FP64 leaf blocks were released and cannot be restored";
+        return H2_ERR_STATE;
+      }
+      if (!c->A64) return H2_OK;
+      // the mixed-precision path keeps what it needs: the FP32 pair of the
+      // leaf blocks (residual, inner matvec) and their FP16 copy (projection)
+      if (!c->A32 || !c->Alo || !c->A16[0] || c->L < 1) {
+        c->err = "the FP64 leaf blocks are still needed (no FP16 copy of the leaf blocks)";
+        return H2_ERR_STATE;
+      }
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return H2_ERR_CUDA;
+      for (auto it = c->allocs.begin(); it != c->allocs.end(); ++it)
+        if (*it == (void*)c->A64) {
+          c->allocs.erase(it);
+          break;
+        }
+      cudaFree(c->A64);
+      c->A64 = nullptr;
+      return H2_OK;
     default: c->err = "unknown option"; return H2_ERR_INVALID_ARG;
   }
 }
@@ -1974,6 +2016,10 @@ h2_status h2_matvec_arith(h2_ctx* c, const double* x, double* y, int32_t arith) 
   }
   const int64_t n = nslots(c);
   CKS(vec_in(c, x, c->x64));
+  if (arith == 0 && !c->A64) {
+    c->err = "the FP64 leaf blocks were released (H2_OPT_FP64_LEAF)";
+    return H2_ERR_STATE;
+  }
   if (arith == 0) {
     matvec_impl(c, c->x64, c->y64);
   } else if (arith == 2) {
@@ -2311,7 +2357,10 @@ h2_status h2_export(const h2_ctx* c, const char* name, int32_t level, void* dst,
     if (level == 0) return H2_ERR_INVALID_ARG;
     src = d.X; cnt = nb * D * K; es = 8;
   } else if (n == "A") {
-    if (level == c->L) { src = c->A64; cnt = (size_t)d.NP * D * D; es = 8; }
+    if (level == c->L) {
+      if (!c->A64) return H2_ERR_STATE;
+      src = c->A64; cnt = (size_t)d.NP * D * D; es = 8;
+    }
     else s = pick(c->f64.lv.empty() ? nullptr : c->f64.lv[level].Ain,
                   c->f32.lv.empty() ? nullptr : c->f32.lv[level].Ain, (size_t)d.NP * D * D, true);
   } else if (level >= 1 && (n == "U" || n == "T" || n == "Ahat" || n == "Ainv" || n == "Shat")) {

@@ -67,6 +67,10 @@ bool on_device(const void* p, int dev) {
 extern "C" h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y) {
   if (!c) return H2_ERR_INVALID_ARG;
   c->err.clear();
+  if (!c->A64) {
+    c->err = "the FP64 leaf blocks were released (H2_OPT_FP64_LEAF)";
+    return H2_ERR_STATE;
+  }
   if (!x || !y || !on_device(x, c->dev) || !on_device(y, c->dev)) {
     c->err = "h2_matvec_noalloc needs device pointers on the context's device for x and y";
     return H2_ERR_INVALID_ARG;

@@ -739,6 +739,9 @@ std::string combine_forest(const std::vector<HostH2>& parts, HostH2& H) {
   for (int l = 1; l <= L; ++l)
     for (const HostH2& P : parts) K[l] = std::max(K[l], P.lv[l].K);
   for (const HostH2& P : parts) D[L] = std::max(D[L], P.lv[L].D);
+  // leaves padded to a multiple of 128 (the tensor-core tile and the
+  // symmetric-storage matvec's block widths) while that stays <= 1024
+  if ((D[L] + 127) / 128 * 128 <= 1024) D[L] = (D[L] + 127) / 128 * 128;
   for (int l = 0; l < L; ++l) D[l] = 2 * K[l + 1];
   std::vector<int64_t> poff(S + 1, 0);
   H.leaf_offsets.push_back(0);

@@ -105,6 +105,16 @@ __device__ __forceinline__ uint4 ld_cluster_v4(uint32_t a) {
   return v;
 }
 
+// One-dimensional bulk copy global -> shared of `bytes` bytes (both
+// addresses 16-byte aligned, bytes a multiple of 16), completing on an
+// mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 // 2-D tiled tensor copy global -> shared, completing on an mbarrier.  c0 is
 // the inner (column) coordinate, c1 the row.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, uint64_t* bar, int c0, int c1) {
