@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--build", default="plain", choices=["plain", "gpu"],
                     help="construction of the instance (untimed): the host rank-revealing pass, or the GPU "
                          "sketches at the level caps (h2_build_gpu)")
+    ap.add_argument("--box-stream", type=int, default=1, choices=[0, 1],
+                    help="substitution per-box steps on large levels: 1 streamed persistent kernels, 0 row-split")
     ap.add_argument("--tc-kernel", type=int, default=2, choices=[0, 1, 2],
                     help="tensor-core GEMM form: 0 one CTA per entry, 1 persistent grid, 2 warp-specialized")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
@@ -536,6 +538,7 @@ def main():
     S.set_option("residual_fp64", 1 if args.residual == "fp64" else 0)
     S.set_option("graphs", args.graphs)
     S.set_option("tc_kernel", args.tc_kernel)
+    S.set_option("box_stream", args.box_stream)
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.zeros_like(b_dev)
     torch.cuda.synchronize()
@@ -665,7 +668,7 @@ def main():
                    "l2": "no flush: inputs (13 GB leaf blocks, factors) exceed L2"},
         "relres": float(np.max(rels)), "relres_fp64_matvec": r_check, "dense_rows_check": dense,
         "iters": int(np.max(its_all)),
-        "rr_lu": args.rr_lu, "residual": args.residual, "graphs": args.graphs, "tc_kernel": args.tc_kernel,
+        "rr_lu": args.rr_lu, "residual": args.residual, "graphs": args.graphs, "tc_kernel": args.tc_kernel, "box_stream": args.box_stream,
         "phases_s": ph, "build_s": build_s, "build": args.build, "fp64": fp64,
         "speedup_vs_fp64": (fp64["s_per_step"] / value) if fp64 else None,
         "roofline": roof, "rooflines": roofs, "fp64_peak_tflops": fp64_tf, "calls": calls,

@@ -320,16 +320,25 @@ h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
  *                         option and the leaf "A" export return
  *                         H2_ERR_STATE; 1 cannot undo a release (H2_ERR_STATE).
  *                         0 also returns H2_ERR_STATE when the instance has
- *                         no FP16 copy of its leaf blocks. */
+ *                         no FP16 copy of its leaf blocks.
+ *   H2_OPT_BOX_STREAM     the per-box steps of the FP32 substitution on
+ *                         levels with at least one box per SM (D = 256,
+ *                         R = 128 or D = 128, R = 64; process-wide):
+ *                         1 (default) a persistent kernel per step whose
+ *                         factor rows stream through a shared-memory ring
+ *                         of bulk copies; 2 the same on every level of
+ *                         those shapes, whatever its box count; 0 row-split
+ *                         kernels. */
 typedef enum {
   H2_OPT_RR_LU_FP64 = 0,
   H2_OPT_RESIDUAL_FP64 = 1,
   H2_OPT_GRAPHS = 2,
   H2_OPT_TC_KERNEL = 3,
-  H2_OPT_FP64_LEAF = 4
+  H2_OPT_FP64_LEAF = 4,
+  H2_OPT_BOX_STREAM = 5
 } h2_option;
 
-/* Set an h2_option to value (0 or 1; 0 .. 2 for H2_OPT_TC_KERNEL).
+/* Set an h2_option to value (0 or 1; 0 .. 2 for H2_OPT_TC_KERNEL and H2_OPT_BOX_STREAM).
  * Errors: H2_ERR_INVALID_ARG. */
 h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value);
 

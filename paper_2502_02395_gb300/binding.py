@@ -39,7 +39,7 @@ EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_sol
             "h2_batch_create_forest", "h2_batch_run", "h2_batch_tune",
             "h2_batch_stats", "h2_batch_last_error", "h2_batch_destroy",
             "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
-OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1, "graphs": 2, "tc_kernel": 3, "fp64_leaf": 4}
+OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1, "graphs": 2, "tc_kernel": 3, "fp64_leaf": 4, "box_stream": 5}
 ARITH = {"fp64": 0, "fp32": 1, "fp32_pair": 2}
 
 

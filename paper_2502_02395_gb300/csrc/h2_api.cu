@@ -1963,7 +1963,7 @@ h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart) {
 h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value) {
   if (!c) return H2_ERR_INVALID_ARG;
   c->err.clear();
-  if ((value != 0 && value != 1) && option != H2_OPT_TC_KERNEL) {
+  if ((value != 0 && value != 1) && option != H2_OPT_TC_KERNEL && !(option == H2_OPT_BOX_STREAM && value == 2)) {
     c->err = "option value must be 0 or 1";
     return H2_ERR_INVALID_ARG;
   }
@@ -1979,6 +1979,10 @@ h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value) {
       return H2_OK;
     case H2_OPT_GRAPHS:
       c->use_graphs = value != 0;
+      drop_graphs(c);
+      return H2_OK;
+    case H2_OPT_BOX_STREAM:
+      g_box_stream = (int)value;
       drop_graphs(c);
       return H2_OK;
     case H2_OPT_FP64_LEAF:

@@ -18,6 +18,8 @@
 // H^2 matvec (FP64): upward pass x^_i = X_i^T x_i, couplings y^_i +=
 // S_ij x^_j on every level, downward pass, leaf y_i = X_i y^_i +
 // sum_near A_ij x_j.
+#include <atomic>
+
 #include "h2_internal.h"
 #include "kernels.h"
 #include "ptx_util.h"
@@ -1146,8 +1148,266 @@ static void launch_pairs(const DevLevel& L, const FacLevel<T>& F, const int32_t*
   launch_pdl(pair_kernel<T, TS, PH>, (unsigned)n, 256, sm, st, L.D, L.R, L.K, list, L.near_j, Ahat, xv, part);
 }
 
+// ------------------------------------------------------------------------
+// Streamed per-box steps for levels with many boxes (D = 256, R = 128 or
+// D = 128, R = 64; FP32 factors).  A persistent CTA (one per SM) walks its
+// boxes i = blockIdx.x, + gridDim.x, ..., and each box's factor rows flow
+// through a shared-memory ring of kBoxStages 16 KB stages, filled by
+// one-dimensional bulk copies that thread 0 issues kBoxStages stages ahead,
+// across box boundaries, so that the copies of the next box overlap the
+// reductions of this one.  A stage holds whole rows (16 KB / row bytes of
+// them); warp w takes rows w, w + 8, ..., each lane RW / 32 consecutive
+// entries of a row, with its part of the box's input vector in registers,
+// and the rows of a warp meet in one transposed butterfly.
+//   BX_FWD1: [u_i; c_i^S] = [M1_i; (U_i^S)^T] b_i, b_i as fwd1 forms it;
+//   BX_FWD2: v_i = u_i - Ainv_i (s^-1 sum_{j<i near} part);
+//   BX_BWD1: om_i = v_i - Ainv_i (s^-1 sum_{j near} part);
+//   BX_BWD2: x_i^R = om_i - Ainv_i (s^-1 sum_{j>i near} part), then
+//            x_i = U_i [x_i^R; x_i^S] from the row-major copy Ur.
+// The same products as fwd1..bwd2 with the sums grouped differently.
+// Waits are bounded (2 s); on expiry every thread leaves together, thread 0
+// having waited (bounded) for the copies still in flight and set *err.
+// ------------------------------------------------------------------------
+enum { BX_FWD1 = 0, BX_FWD2 = 1, BX_BWD1 = 2, BX_BWD2 = 3 };
+constexpr int kBoxStages = 8;
+constexpr uint32_t kBoxStageBytes = 16384;
+
+struct BoxArgs {
+  int64_t nb;
+  const int64_t* ptr;    // near-pair CSR of the level
+  const int32_t* cnt;    // pairs j < i (FWD2) or j > i (BWD2) of each box
+  const float* iscale;   // 1 / s of the 16-bit Ahat, or NULL
+  const float* Ainv;     // nb x R x R
+  const float* M1;       // nb x R x D
+  const float* U;        // nb x D x D, column-major (rows R.. of U^T: (U^S)^T)
+  const float* Ur;       // nb x D x D, row-major
+  const float* vin;      // leaf input (FWD1 without children)
+  ChildIn<float> ch;     // children's SR sums (FWD1 above the leaf)
+  float* u;
+  float* c;
+  float* v;
+  float* om;
+  const float* px;       // parent's solution slots (BWD2)
+  float* xs;
+  const float* part;
+  int32_t* err;
+};
+
+template <int MODE, int D, int R>
+struct BoxShape {
+  static constexpr int K = D - R;
+  static constexpr int RWA = (MODE == BX_FWD1) ? D : R;              // row width of the first matrix
+  static constexpr int RPA = (int)kBoxStageBytes / (4 * RWA);          // its rows per stage
+  static constexpr int NA = ((MODE == BX_FWD1) ? D : R) / RPA;         // its stages
+  static constexpr int RPB = (int)kBoxStageBytes / (4 * D);            // BWD2's Ur rows per stage
+  static constexpr int NB = (MODE == BX_BWD2) ? D / RPB : 0;
+  static constexpr int NS = NA + NB;
+  static_assert(R % RPA == 0 && D % RPB == 0 && RPA % 8 == 0 && RPB % 8 == 0, "stage rows");
+};
+
+template <int MODE, int D, int R>
+__device__ __forceinline__ const float* box_stage_src(const BoxArgs& a, int64_t i, int j) {
+  using S = BoxShape<MODE, D, R>;
+  if constexpr (MODE == BX_FWD1) {
+    const int r0 = j * S::RPA;
+    return r0 < R ? a.M1 + ((size_t)i * R + r0) * D : a.U + ((size_t)i * D + r0) * D;
+  } else {
+    if (j < S::NA) return a.Ainv + ((size_t)i * R + (size_t)j * S::RPA) * R;
+    return a.Ur + ((size_t)i * D + (size_t)(j - S::NA) * S::RPB) * D;
+  }
+}
+
+// One stage: RPS rows of width RW at tile (rows j * RPS .. of the box's
+// current matrix); out(row, value) stores a finished row.
+template <int RW, int RPS, typename Out>
+__device__ __forceinline__ void box_stage_rows(const float* tile, const float (&xr)[RW / 32], int row0, Out out) {
+  constexpr int VL = RW / 32, NR = RPS / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[NR];
+#pragma unroll
+  for (int t = 0; t < NR; ++t) {
+    const float* rowp = tile + (size_t)(warp + 8 * t) * RW + lane * VL;
+    float s = 0.0f;
+    if constexpr (VL % 4 == 0) {
+#pragma unroll
+      for (int e = 0; e < VL; e += 4) {
+        const float4 m = *reinterpret_cast<const float4*>(rowp + e);
+        s = fmaf(m.x, xr[e], s);
+        s = fmaf(m.y, xr[e + 1], s);
+        s = fmaf(m.z, xr[e + 2], s);
+        s = fmaf(m.w, xr[e + 3], s);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < VL; e += 2) {
+        const float2 m = *reinterpret_cast<const float2*>(rowp + e);
+        s = fmaf(m.x, xr[e], s);
+        s = fmaf(m.y, xr[e + 1], s);
+      }
+    }
+    acc[t] = s;
+  }
+  const float v = tsum<NR, 32, float>(acc);
+  if (tsum_leader<NR, 32>(lane)) out(row0 + warp + 8 * tsum_index<NR, 32>(lane), v);
+}
+
+template <int MODE, int D, int R>
+__global__ void __launch_bounds__(256, 1) box_stream_kernel(BoxArgs a) {
+  using S = BoxShape<MODE, D, R>;
+  constexpr int K = S::K;
+  extern __shared__ __align__(128) unsigned char sm_dyn[];
+  __shared__ __align__(8) uint64_t full[kBoxStages];
+  unsigned char* ring = sm_dyn + ((128u - (smem_u32(sm_dyn) & 127u)) & 127u);
+  float* xv = reinterpret_cast<float*>(ring + (size_t)kBoxStages * kBoxStageBytes);  // D
+  float* zs = xv + D;                                                                  // D
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t G = gridDim.x;
+  const int64_t nmine = (blockIdx.x < a.nb) ? (a.nb - blockIdx.x + G - 1) / G : 0;
+  const int64_t total = nmine * S::NS;  // this CTA's stages
+  if (tid == 0) {
+    for (int s = 0; s < kBoxStages; ++s) mbar_init(&full[s], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t g) {
+    const int s = (int)(g % kBoxStages);
+    const int64_t i = blockIdx.x + (g / S::NS) * G;
+    mbar_expect_tx(&full[s], kBoxStageBytes);
+    bulk_load(ring + (size_t)s * kBoxStageBytes, box_stage_src<MODE, D, R>(a, i, (int)(g % S::NS)), kBoxStageBytes,
+              &full[s]);
+  };
+  // factor rows are fixed during a solve: their copies start before the
+  // wait for the previous kernel
+  if (tid == 0)
+    for (int64_t g = 0; g < kBoxStages && g < total; ++g) issue(g);
+  griddep_wait();
+  griddep_launch_next();
+  const float isc = a.iscale ? a.iscale[0] : 1.0f;
+  int64_t g = 0;
+  for (int64_t k = 0; k < nmine; ++k) {
+    const int64_t i = blockIdx.x + k * G;
+    // the box's input vector
+    if constexpr (MODE == BX_FWD1) {
+      if (a.ch.c) {
+        const float cs = a.ch.iscale ? a.ch.iscale[0] : 1.0f;
+        for (int e = tid; e < D; e += blockDim.x) {
+          const int64_t cc = 2 * i + e / a.ch.K;
+          const int r = e % a.ch.K;
+          xv[e] = a.ch.c[cc * a.ch.D + a.ch.R + r] - cs * sum_pairs(a.ch.part, a.ch.K, a.ch.ptr[cc], a.ch.ptr[cc + 1], r);
+        }
+      } else {
+        for (int e = tid; e < D; e += blockDim.x) xv[e] = a.vin[i * D + e];
+      }
+    } else {
+      int64_t q0 = a.ptr[i], q1 = a.ptr[i + 1];
+      if (MODE == BX_FWD2) q1 = q0 + a.cnt[i];
+      if (MODE == BX_BWD2) q0 = q1 - a.cnt[i];
+      for (int r = tid; r < R; r += blockDim.x) xv[r] = isc * sum_pairs(a.part, R, q0, q1, r);
+      if (MODE == BX_BWD2) {
+        const float* xp = a.px + (i >> 1) * 2 * K + (i & 1) * K;
+        for (int e = tid; e < K; e += blockDim.x) zs[R + e] = xp[e];
+      }
+    }
+    __syncthreads();
+    float xa[S::RWA / 32];
+#pragma unroll
+    for (int e = 0; e < S::RWA / 32; ++e) xa[e] = xv[lane * (S::RWA / 32) + e];
+    float xb[D / 32];
+    for (int j = 0; j < S::NS; ++j, ++g) {
+      if (MODE == BX_BWD2 && j == S::NA) {
+        // x_i^R is complete (the stage loop ends in a barrier)
+#pragma unroll
+        for (int e = 0; e < D / 32; ++e) xb[e] = zs[lane * (D / 32) + e];
+      }
+      const int s = (int)(g % kBoxStages);
+      const uint32_t par = (uint32_t)(g / kBoxStages) & 1u;
+      bool ok = true;
+      if (tid == 0) ok = mbar_wait(&full[s], par, kPairTimeoutNs);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicExch(a.err, 1);
+          for (int64_t h = g; h < g + kBoxStages && h < total; ++h)
+            mbar_wait(&full[h % kBoxStages], (uint32_t)(h / kBoxStages) & 1u, kPairTimeoutNs);
+        }
+        __syncthreads();
+        return;
+      }
+      if (!mbar_test(&full[s], par)) mbar_wait(&full[s], par, kPairTimeoutNs);
+      const float* tile = reinterpret_cast<const float*>(ring + (size_t)s * kBoxStageBytes);
+      if (j < S::NA) {
+        box_stage_rows<S::RWA, S::RPA>(tile, xa, j * S::RPA, [&](int r, float val) {
+          if constexpr (MODE == BX_FWD1) {
+            if (r < R) a.u[i * R + r] = val;
+            else a.c[i * D + r] = val;
+          } else if constexpr (MODE == BX_FWD2) {
+            a.v[i * R + r] = a.u[i * R + r] - val;
+          } else if constexpr (MODE == BX_BWD1) {
+            a.om[i * R + r] = a.v[i * R + r] - val;
+          } else {
+            zs[r] = a.om[i * R + r] - val;
+          }
+        });
+      } else if constexpr (MODE == BX_BWD2) {
+        box_stage_rows<D, S::RPB>(tile, xb, (j - S::NA) * S::RPB, [&](int r, float val) { a.xs[i * D + r] = val; });
+      }
+      __syncthreads();  // every thread is done with stage s (and zs / xv of this box)
+      if (tid == 0 && g + kBoxStages < total) issue(g + kBoxStages);
+    }
+  }
+}
+
+// The streamed form for a level: D = 256 with R = 128, or D = 128 with
+// R = 64, FP32 factors with 16-byte aligned rows, and enough boxes to give
+// every SM some (false: use the row-split kernels).
+std::atomic<int> g_box_stream{1};  // H2_OPT_BOX_STREAM (process-wide)
+
+template <int MODE>
+static bool launch_box_stream(const DevLevel& L, const BoxArgs& a, cudaStream_t st) {
+  const int nsm = num_sms();
+  const int mode = g_box_stream.load();
+  if (mode == 0 || (mode == 1 && L.nb < nsm) || a.err == nullptr) return false;
+  if (!((L.D == 256 && L.R == 128) || (L.D == 128 && L.R == 64))) return false;
+  const size_t sm = (size_t)kBoxStages * kBoxStageBytes + 2 * sizeof(float) * L.D + 128;
+  const unsigned grid = (unsigned)std::min<int64_t>(L.nb, nsm);
+  if (L.D == 256) {
+    set_smem((const void*)box_stream_kernel<MODE, 256, 128>, sm);
+    launch_pdl(box_stream_kernel<MODE, 256, 128>, grid, 256, sm, st, a);
+  } else {
+    set_smem((const void*)box_stream_kernel<MODE, 128, 64>, sm);
+    launch_pdl(box_stream_kernel<MODE, 128, 64>, grid, 256, sm, st, a);
+  }
+  return true;
+}
+
+// the streamed per-box form's arguments for a level
+template <typename T>
+static BoxArgs box_args(const DevLevel& L, const FacLevel<T>& F, const float* iscale) {
+  BoxArgs a{};
+  a.nb = L.nb;
+  a.ptr = L.near_ptr;
+  a.iscale = iscale;
+  a.Ainv = reinterpret_cast<const float*>(F.Ainv);
+  a.M1 = reinterpret_cast<const float*>(F.M1);
+  a.U = reinterpret_cast<const float*>(F.U);
+  a.Ur = reinterpret_cast<const float*>(F.Ur);
+  a.vin = reinterpret_cast<const float*>(F.vin);
+  a.u = reinterpret_cast<float*>(F.u);
+  a.c = reinterpret_cast<float*>(F.c);
+  a.v = reinterpret_cast<float*>(F.v);
+  a.om = reinterpret_cast<float*>(F.om);
+  a.xs = reinterpret_cast<float*>(F.xs);
+  a.part = reinterpret_cast<const float*>(F.part);
+  a.err = F.err;
+  return a;
+}
+
 template <typename T>
 void launch_fwd1(const DevLevel& L, const FacLevel<T>& F, const ChildIn<T>& ch, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    BoxArgs a = box_args(L, F, nullptr);
+    a.ch = ch;
+    if (launch_box_stream<BX_FWD1>(L, a, st)) return;
+  }
   const int ns = row_splits(L.nb, L.D);
   launch_pdl(fwd1_kernel<T>, L.nb * ns, 256, sizeof(T) * L.D, st, L.D, L.R, ns, F.M1, F.U, F.vin, ch, F.u, F.c);
 }
@@ -1155,6 +1415,11 @@ template <typename T, typename TS>
 void launch_fwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, cudaStream_t st) {
   if (L.R == 0) return;
   launch_pairs<T, TS, PH_RR>(L, F, L.lo_pairs, L.n_lo, Ahat, F.u, F.part, st);
+  if constexpr (std::is_same<T, float>::value) {
+    BoxArgs a = box_args(L, F, iscale);
+    a.cnt = L.lo_cnt;
+    if (launch_box_stream<BX_FWD2>(L, a, st)) return;
+  }
   const int ns = row_splits(L.nb, L.R);
   launch_pdl(fwd2_kernel<T>, L.nb * ns, 256, sizeof(T) * L.R, st, L.R, ns, L.near_ptr, L.lo_cnt, iscale, F.Ainv, F.u,
              F.part, F.v);
@@ -1172,6 +1437,9 @@ void launch_bwd1(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const 
                  cudaStream_t st) {
   if (L.R == 0) return;
   launch_pairs<T, TS, PH_RS>(L, F, nullptr, L.NP, Ahat, parent_x, F.part, st);
+  if constexpr (std::is_same<T, float>::value) {
+    if (launch_box_stream<BX_BWD1>(L, box_args(L, F, iscale), st)) return;
+  }
   const int ns = row_splits(L.nb, L.R);
   launch_pdl(bwd1_kernel<T>, L.nb * ns, 256, sizeof(T) * L.R, st, L.R, ns, L.near_ptr, iscale, F.Ainv, F.v, F.part,
              F.om);
@@ -1180,6 +1448,12 @@ template <typename T, typename TS>
 void launch_bwd2(const DevLevel& L, const FacLevel<T>& F, const TS* Ahat, const float* iscale, const T* parent_x,
                  cudaStream_t st) {
   if (L.R > 0) launch_pairs<T, TS, PH_RR>(L, F, L.hi_pairs, L.n_hi, Ahat, F.om, F.part, st);
+  if constexpr (std::is_same<T, float>::value) {
+    BoxArgs a = box_args(L, F, iscale);
+    a.cnt = L.hi_cnt;
+    a.px = reinterpret_cast<const float*>(parent_x);
+    if (launch_box_stream<BX_BWD2>(L, a, st)) return;
+  }
   const int ns = row_splits(L.nb, L.D);
   const size_t sm = sizeof(T) * ((size_t)((L.D + 3) & ~3) + std::max(L.R, 1));
   launch_pdl(bwd2_kernel<T>, L.nb * ns, 256, sm, st, L.D, L.R, L.K, ns, L.near_ptr, L.hi_cnt, iscale, F.Ainv, F.om,

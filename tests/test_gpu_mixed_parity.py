@@ -115,6 +115,35 @@ def test_mixed_ulv_apply_elementwise(B, name, prec, rr):
     S.close()
 
 
+@pytest.mark.parametrize("name", MAIN)
+def test_streamed_box_steps_elementwise(B, name):
+    """The streamed per-box substitution kernels (bulk-copy ring, persistent
+    CTAs; H2_OPT_BOX_STREAM = 2 puts them on every level of these shapes,
+    the default only on levels with a box per SM) against the oracle's FP64
+    Eq. 24-31, with the bound of the row-split kernels (8 u16), and against
+    the row-split kernels on the same factorization (FP32 sums grouped
+    differently: 1e-5 of max|x|)."""
+    from oracle import ulv
+    H, F, flat, b = oracle_case(name)
+    S = solver(B, name)
+    S.factor("fp16")
+    try:
+        S.set_option("box_stream", 0)
+        x0 = S.ulv_apply(b)
+        S.set_option("box_stream", 2)
+        x2 = S.ulv_apply(b)
+        _, rel, its = S.solve(b, target=1e-10, max_iters=100)
+    finally:
+        S.set_option("box_stream", 1)  # the library's default
+    x_ref = ulv.solve_parallel(F, H, b)
+    e_ref = np.abs(x2 - x_ref).max() / np.abs(x_ref).max()
+    e_rs = np.abs(x2 - x0).max() / np.abs(x0).max()
+    print(f"\n{name}: streamed vs oracle {e_ref:.3e} ({e_ref / U16['fp16']:.2f} u16), vs row-split {e_rs:.2e}; "
+          f"refined {rel:.2e} in {its}")
+    assert e_ref <= 8 * U16["fp16"] and e_rs <= 1e-5 and rel <= 1e-10
+    S.close()
+
+
 @pytest.mark.parametrize("rr", [1, 0])
 @pytest.mark.parametrize("name", MAIN)
 def test_mixed_inverses_and_pivots(B, name, rr):
