@@ -211,6 +211,11 @@ h2_status h2_import(h2_ctx** out, const h2_params* p, const h2_instance* inst);
  * H2_ERR_OOM, H2_ERR_CUDA. */
 h2_status h2_factor(h2_ctx* c, int32_t prec);
 
+/* Free the device arrays of the context's factorizations (FP64 and
+ * FP16/BF16) and their CUDA graphs; the instance stays.  Solves need a new
+ * h2_factor, which allocates them again.  Errors: H2_ERR_INVALID_ARG. */
+h2_status h2_release_factorization(h2_ctx* c);
+
 /* Solve A_H2 x = b by refinement with the factorization as preconditioner.
  * Every refinement residual r = b - A_H2 x is FP64-accurate: FP64
  * instructions (the h2_matvec operator) in schemes 0 and 1, FP32-pair
@@ -520,7 +525,11 @@ h2_status h2_batch_create(h2_batch** out, h2_ctx* const* ctxs, const int64_t* n,
  * (h2_matvec_arith arith 2); iters receives the group's count.  The vectors
  * B[k], X[k] of a forest batch are host memory (the scaling and splitting
  * run on the host; device vectors give H2_ERR_INVALID_ARG).  The worker pool
- * runs the groups.  Errors: as h2_build_forest (the group's message is in
+ * runs the groups; a group's factorization is released after its solve
+ * (h2_release_factorization), so prec = -1 is not available, and a worker
+ * whose factorization does not fit (H2_ERR_OOM) waits for another group to
+ * release its arrays and tries again (the error stands when no other group
+ * holds any).  Errors: as h2_build_forest (the group's message is in
  * h2_last_error(NULL)). */
 h2_status h2_batch_create_forest(h2_batch** out, const h2_params* p, const double* const* points,
                                  const int64_t* N, const int32_t* leaf, int32_t count);

@@ -30,7 +30,7 @@ STATUS = {0: "H2_OK", -1: "H2_ERR_INVALID_ARG", -2: "H2_ERR_OOM", -3: "H2_ERR_SI
           -4: "H2_ERR_NOT_CONVERGED", -5: "H2_ERR_CUDA", -6: "H2_ERR_TIMEOUT", -7: "H2_ERR_STATE"}
 
 # every symbol include/h2ulv.h declares
-EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_solve", "h2_solve_many", "h2_ulv_apply",
+EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_release_factorization", "h2_solve", "h2_solve_many", "h2_ulv_apply",
             "h2_matvec", "h2_matvec_many", "h2_matvec_noalloc", "h2_matvec_arith", "h2_set_option",
             "h2_wait_selftest", "h2_set_memory_limit", "h2_rank_data", "h2_rank_model_create",
             "h2_rank_model_set_weights", "h2_rank_model_get_weights", "h2_rank_model_grad", "h2_rank_model_train",
@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
             "h2_plan": (i32, [vp, vp, i64, ctypes.c_char_p, ctypes.c_size_t]),
             "h2_import": (i32, [pp, vp, vp]),
             "h2_factor": (i32, [vp, i32]),
+            "h2_release_factorization": (i32, [vp]),
             "h2_solve": (i32, [vp, vp, vp, dbl, i32, vp, vp]),
             "h2_solve_many": (i32, [vp, vp, vp, i32, dbl, i32, vp, vp]),
             "h2_matvec_many": (i32, [vp, vp, vp, i32]),
@@ -541,6 +542,9 @@ class H2Solver:
 
     def factor(self, prec="fp64"):
         h2_factor(self.ctx, prec)
+
+    def release_factorization(self):
+        _check(lib().h2_release_factorization(self.ctx), self.ctx)
 
     def solve(self, b, target=1e-10, max_iters=50, x=None):
         if x is None:

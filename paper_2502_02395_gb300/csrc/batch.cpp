@@ -26,6 +26,8 @@
 #include <numeric>
 #include <string>
 #include <thread>
+#include <condition_variable>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -146,6 +148,10 @@ h2_status run(h2_batch* b, int w, int32_t prec, const double* const* B, double* 
   std::atomic<int> next{0};
   std::vector<h2_status> st(ns, H2_OK);
   std::vector<std::string> msg(ns);
+  // forest groups holding a factorization, and releases so far
+  std::mutex mu;
+  std::condition_variable cv;
+  int holding = 0, released = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   auto worker = [&](int k) {
@@ -156,7 +162,25 @@ h2_status run(h2_batch* b, int w, int32_t prec, const double* const* B, double* 
       const int i = order[t];
       h2_ctx* c = b->ctx[i];
       h2_status r = h2_set_stream(c, b->streams[k]);
-      if (r == H2_OK && prec >= 0) r = h2_factor(c, prec);
+      bool holds = false;
+      if (r == H2_OK && prec >= 0) {
+        r = h2_factor(c, prec);
+        // a forest group whose factorization does not fit waits for another
+        // group to release its arrays, while some group holds any
+        while (b->forest && r == H2_ERR_OOM) {
+          std::unique_lock<std::mutex> lk(mu);
+          if (holding == 0) break;
+          const int seen = released;
+          cv.wait(lk, [&] { return released != seen || holding == 0; });
+          lk.unlock();
+          r = h2_factor(c, prec);
+        }
+        if (r == H2_OK && b->forest) {
+          std::lock_guard<std::mutex> lk(mu);
+          ++holding;
+          holds = true;
+        }
+      }
       if (r == H2_OK && B && !b->forest) {
         double rel = 0;
         int32_t its = 0;
@@ -167,6 +191,16 @@ h2_status run(h2_batch* b, int w, int32_t prec, const double* const* B, double* 
         r = solve_group(b, i, B, X, target, max_iters, relres, iters, msg[i]);
       }
       if (r == H2_OK) r = cudaStreamSynchronize(b->streams[k]) == cudaSuccess ? H2_OK : H2_ERR_CUDA;
+      if (holds) {
+        const h2_status rr = h2_release_factorization(c);
+        if (r == H2_OK) r = rr;
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          --holding;
+          ++released;
+        }
+        cv.notify_all();
+      }
       st[i] = r;
     }
   };

@@ -408,8 +408,11 @@ struct Ev {
 };
 
 template <typename T>
-h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
-  if (!F.lv.empty()) return H2_OK;
+void release_factor(h2_ctx* c, Factor<T>& F);
+
+template <typename T>
+h2_status alloc_factor_arrays(h2_ctx* c, Factor<T>& F) {
+  AllocSink sink(c, &F.allocs);
   const int L = c->L;
   F.lv.assign(L + 1, FacLevel<T>());
   size_t wk = 0, wk16 = 0, wq = 0, wc = 0, wc16 = 0;
@@ -497,6 +500,19 @@ h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
   return H2_OK;
 }
 
+// A factorization's arrays, all or none: a failed allocation frees the
+// ones made before it, so that the next h2_factor starts afresh.
+template <typename T>
+h2_status alloc_factor(h2_ctx* c, Factor<T>& F) {
+  if (!F.lv.empty()) return H2_OK;
+  const h2_status s = alloc_factor_arrays(c, F);
+  if (s != H2_OK) {
+    cudaGetLastError();
+    release_factor(c, F);
+  }
+  return s;
+}
+
 template <typename T>
 void gemm(int prec, int M, int N, int K, const T* A, int64_t sA, const int32_t* ia, int lda, bool tA, const T* B,
           int64_t sB, const int32_t* ib, int ldb, bool tB, T* C, int64_t sC, const int32_t* ic, int ldc, T alpha,
@@ -566,6 +582,7 @@ h2_status factor_impl(h2_ctx* c, Factor<T>& F, int prec) {
   // FP64 a3 for the FP16/BF16 factorizations: scratch for the largest level
   const bool lu64_mixed = mixed && c->rr_lu64;
   if (lu64_mixed && !F.rr_lu) {
+    AllocSink sink(c, &F.allocs);
     size_t n = (size_t)c->lv[0].nb * c->lv[0].D * c->lv[0].D;
     for (int l = 1; l <= L; ++l) n = std::max(n, (size_t)c->lv[l].nb * c->lv[l].R * c->lv[l].R);
     CKC(dalloc(c, &F.rr_lu, n));
@@ -1567,6 +1584,19 @@ h2_status check_fits(double need, const char* what, std::string& err) {
   return H2_OK;
 }
 
+// Free a factorization's arrays (its CUDA graphs first); the next
+// h2_factor allocates them again.
+template <typename T>
+void release_factor(h2_ctx* c, Factor<T>& F) {
+  if (F.allocs.empty() && F.lv.empty()) return;
+  for (cudaStream_t s : {c->stream, c->basis_stream, c->coupling_stream, c->product_stream, c->leaf_stream,
+                         c->cap_stream})
+    if (s || s == c->stream) cudaStreamSynchronize(s);
+  drop_graphs(c);
+  for (void* q : F.allocs) cudaFree(q);
+  F = Factor<T>();
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1814,6 +1844,16 @@ h2_status h2_factor(h2_ctx* c, int32_t prec) {
   h2_status s = (prec == H2_PREC_FP64) ? factor_impl<double>(c, c->f64, prec) : factor_impl<float>(c, c->f32, prec);
   if (s == H2_OK) c->prec = prec;
   return s;
+}
+
+h2_status h2_release_factorization(h2_ctx* c) {
+  if (!c) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  release_factor(c, c->f64);
+  release_factor(c, c->f32);
+  c->prec = -1;
+  CKC(cudaGetLastError());
+  return H2_OK;
 }
 
 h2_status h2_ulv_apply(h2_ctx* c, const double* b, double* x) {
@@ -2429,6 +2469,8 @@ void h2_destroy(h2_ctx* c) {
     cudaStreamDestroy(s);
   }
   for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->f64.allocs) cudaFree(p);
+  for (void* p : c->f32.allocs) cudaFree(p);
   if (c->gm_host) cudaFreeHost(c->gm_host);
   delete c;
 }

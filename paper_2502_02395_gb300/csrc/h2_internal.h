@@ -289,6 +289,7 @@ struct Factor {
   unsigned int* sch_amax = nullptr;
   bool schur_tc = false;  // the last factorization ran a4/a5 on the tensor cores at some level
   int bf16 = -1;              // operand type the 16-bit buffers hold
+  std::vector<void*> allocs;  // this factorization's device arrays (h2_release_factorization)
 };
 
 struct PhaseTimes {
@@ -390,19 +391,30 @@ struct h2_ctx {
   h2::Factor<float> f32;
   h2::PhaseTimes times;
   std::vector<void*> allocs;
+  std::vector<void*>* alloc_sink = nullptr;  // where dalloc records (NULL: allocs)
   std::string err;
 };
 
 namespace h2 {
 
-// device allocation helper: records the pointer in ctx->allocs
+// records allocations made while it lives in the given list (a
+// factorization's own arrays)
+struct AllocSink {
+  h2_ctx* c;
+  std::vector<void*>* prev;
+  AllocSink(h2_ctx* ctx, std::vector<void*>* to) : c(ctx), prev(ctx->alloc_sink) { c->alloc_sink = to; }
+  ~AllocSink() { c->alloc_sink = prev; }
+};
+
+// device allocation helper: records the pointer in ctx->allocs (or the
+// active AllocSink's list)
 template <typename T>
 inline cudaError_t dalloc(h2_ctx* c, T** p, size_t n) {
   if (n == 0) n = 1;
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, n * sizeof(T));
   if (e == cudaSuccess) {
-    c->allocs.push_back(q);
+    (c->alloc_sink ? *c->alloc_sink : c->allocs).push_back(q);
     *p = static_cast<T*>(q);
   }
   return e;

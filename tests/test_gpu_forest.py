@@ -183,3 +183,22 @@ def test_fp64_leaf_release(B):
             call()
         assert ei.value.status == -7
     S.close()
+
+
+def test_release_factorization(B):
+    """h2_release_factorization frees the factorization's arrays (a forest
+    batch does so after each group's solve): a solve then reports
+    H2_ERR_STATE, and a new factorization gives the same solution."""
+    P = W.cube_points(4096, 130)
+    b = W.uniform_rhs(4096, 131)
+    S = B.H2Solver.build(P, **KW)
+    S.factor("fp16")
+    x0, _, i0 = S.solve(b, target=1e-10, max_iters=100)
+    S.release_factorization()
+    with pytest.raises(B.H2Error) as ei:
+        S.solve(b, target=1e-10, max_iters=100)
+    assert ei.value.status == -7
+    S.factor("fp16")
+    x1, _, i1 = S.solve(b, target=1e-10, max_iters=100)
+    assert i1 == i0 and np.abs(x0 - x1).max() <= 1e-12 * np.abs(x0).max()
+    S.close()
