@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--build", default="plain", choices=["plain", "gpu"],
                     help="construction of the instance (untimed): the host rank-revealing pass, or the GPU "
                          "sketches at the level caps (h2_build_gpu)")
-    ap.add_argument("--box-stream", type=int, default=1, choices=[0, 1],
+    ap.add_argument("--box-stream", type=int, default=0, choices=[0, 1],
                     help="substitution per-box steps on large levels: 1 streamed persistent kernels, 0 row-split")
     ap.add_argument("--tc-kernel", type=int, default=2, choices=[0, 1, 2],
                     help="tensor-core GEMM form: 0 one CTA per entry, 1 persistent grid, 2 warp-specialized")

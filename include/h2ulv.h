@@ -329,11 +329,12 @@ h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
  *   H2_OPT_BOX_STREAM     the per-box steps of the FP32 substitution on
  *                         levels with at least one box per SM (D = 256,
  *                         R = 128 or D = 128, R = 64; process-wide):
- *                         1 (default) a persistent kernel per step whose
- *                         factor rows stream through a shared-memory ring
- *                         of bulk copies; 2 the same on every level of
- *                         those shapes, whatever its box count; 0 row-split
- *                         kernels. */
+ *                         1 a persistent kernel per step whose factor rows
+ *                         stream through a shared-memory ring of bulk
+ *                         copies; 2 the same on every level of those
+ *                         shapes, whatever its box count; 0 (default)
+ *                         row-split kernels (measured faster at N = 2^18:
+ *                         22.6 against 24.9 ms of substitution per step). */
 typedef enum {
   H2_OPT_RR_LU_FP64 = 0,
   H2_OPT_RESIDUAL_FP64 = 1,

@@ -164,21 +164,34 @@ h2_status run(h2_batch* b, int w, int32_t prec, const double* const* B, double* 
       h2_status r = h2_set_stream(c, b->streams[k]);
       bool holds = false;
       if (r == H2_OK && prec >= 0) {
+        if (b->forest) {
+          std::lock_guard<std::mutex> lk(mu);
+          ++holding;  // factoring or holding a factorization
+          holds = true;
+        }
         r = h2_factor(c, prec);
-        // a forest group whose factorization does not fit waits for another
-        // group to release its arrays, while some group holds any
+        // a forest group whose factorization does not fit waits until
+        // another group releases its arrays (none left: the error stands)
         while (b->forest && r == H2_ERR_OOM) {
           std::unique_lock<std::mutex> lk(mu);
+          --holding;
+          holds = false;
           if (holding == 0) break;
           const int seen = released;
           cv.wait(lk, [&] { return released != seen || holding == 0; });
+          ++holding;
+          holds = true;
           lk.unlock();
           r = h2_factor(c, prec);
         }
-        if (r == H2_OK && b->forest) {
-          std::lock_guard<std::mutex> lk(mu);
-          ++holding;
-          holds = true;
+        if (r != H2_OK && holds) {
+          {
+            std::lock_guard<std::mutex> lk(mu);
+            --holding;
+            ++released;
+          }
+          holds = false;
+          cv.notify_all();
         }
       }
       if (r == H2_OK && B && !b->forest) {

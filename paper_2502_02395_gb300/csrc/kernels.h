@@ -16,9 +16,9 @@ extern std::atomic<long long> g_launches;
 // products on their own stream always use form 0, so that they keep sharing
 // the SMs with the main chain.
 extern std::atomic<int> g_tc_kernel;
-// The substitution's per-box steps: 1 (default) the streamed persistent
-// form (bulk-copy ring) on levels with at least one box per SM, 2 on every
-// level of a supported shape, 0 never (row-split kernels); process-wide
+// The substitution's per-box steps: 1 the streamed persistent form
+// (bulk-copy ring) on levels with at least one box per SM, 2 on every level
+// of a supported shape, 0 (default) never (row-split kernels); process-wide
 // (H2_OPT_BOX_STREAM).
 extern std::atomic<int> g_box_stream;
 

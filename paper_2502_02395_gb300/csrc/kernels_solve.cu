@@ -1359,7 +1359,7 @@ __global__ void __launch_bounds__(256, 1) box_stream_kernel(BoxArgs a) {
 // The streamed form for a level: D = 256 with R = 128, or D = 128 with
 // R = 64, FP32 factors with 16-byte aligned rows, and enough boxes to give
 // every SM some (false: use the row-split kernels).
-std::atomic<int> g_box_stream{1};  // H2_OPT_BOX_STREAM (process-wide)
+std::atomic<int> g_box_stream{0};  // H2_OPT_BOX_STREAM (process-wide)
 
 template <int MODE>
 static bool launch_box_stream(const DevLevel& L, const BoxArgs& a, cudaStream_t st) {
