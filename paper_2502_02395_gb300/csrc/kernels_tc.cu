@@ -93,13 +93,58 @@ struct TcArgs {
   unsigned int* amax_ss;
 };
 
+// Row-major stores of a warp's 32 consecutive rows through shared memory:
+// every lane holds 16 values (FP32) or 8 packed pairs (16 bits) of its row
+// m0 + lane at columns n0 .. n0 + 15; they are transposed in stg (32 x 17
+// words, this warp's) and written as whole row segments, 4 lanes per FP32
+// row (8 rows per store) or 2 lanes per 16-bit row (16 rows per store),
+// instead of one 16-byte piece of 32 different rows per store.  add: C +=
+// (read-modify-write).  Warp-collective.
+__device__ __forceinline__ void tc_rows_store_f32(float* stg, const float (&v)[16], float* C, int64_t ldc, bool add) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) stg[lane * 17 + j] = v[j];
+  __syncwarp();
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int r = it * 8 + (lane >> 2), c4 = (lane & 3) * 4;
+    const float* q = stg + r * 17 + c4;
+    float4 w = make_float4(q[0], q[1], q[2], q[3]);
+    float4* o = reinterpret_cast<float4*>(C + (int64_t)r * ldc + c4);
+    if (add) {
+      const float4 old = *o;
+      w.x += old.x, w.y += old.y, w.z += old.z, w.w += old.w;
+    }
+    *o = w;
+  }
+  __syncwarp();
+}
+__device__ __forceinline__ void tc_rows_store_u16(float* stg, const uint32_t (&h)[8], uint16_t* C, int64_t ldc) {
+  const int lane = threadIdx.x & 31;
+  uint32_t* su = reinterpret_cast<uint32_t*>(stg);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) su[lane * 9 + j] = h[j];
+  __syncwarp();
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int r = it * 16 + (lane >> 1), c = (lane & 1) * 4;
+    const uint32_t* q = su + r * 9 + c;
+    *reinterpret_cast<uint4*>(C + (int64_t)r * ldc + 2 * c) = make_uint4(q[0], q[1], q[2], q[3]);
+  }
+  __syncwarp();
+}
+
 // Epilogue of one output row m of batch entry b: reads the row's N
 // accumulator columns from TMEM (lane_addr: this warp's lane quarter) in
 // 16-column chunks and stores them in the output mode of p.  Every lane of
 // the warp must call it (tcgen05.ld is warp-collective); rows m >= M and
 // failed tiles (ok false) store nothing.  Returns max |FP32 output| over the
-// SS quadrant of an off-diagonal split entry (0 otherwise).
-__device__ __forceinline__ float tc_epilogue_row(const TcArgs& p, int64_t b, int m, uint32_t lane_addr, bool ok) {
+// SS quadrant of an off-diagonal split entry (0 otherwise).  With stg (this
+// warp's 32 x 17 words of shared memory), the warp's rows are m - lane ..
+// m - lane + 31, and the row-major outputs (modes 0 and 3) go through
+// tc_rows_store_*.
+__device__ __forceinline__ float tc_epilogue_row(const TcArgs& p, int64_t b, int m, uint32_t lane_addr, bool ok,
+                                                 float* stg = nullptr) {
   const float alpha = p.alpha * (p.alpha_dev ? *p.alpha_dev : 1.0f);
   char* Cb = reinterpret_cast<char*>(p.C);
   const int64_t cbase = (int64_t)(p.ic ? p.ic[b] : (int)b) * p.sC;
@@ -114,6 +159,45 @@ __device__ __forceinline__ float tc_epilogue_row(const TcArgs& p, int64_t b, int
         : "r"(lane_addr + (uint32_t)n0));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (!ok || m >= p.M) continue;
+    // the staged stores need warp-uniform quadrant tests: rows of a warp on
+    // one side of qsplit (true for a multiple of 32)
+    const int lane = threadIdx.x & 31;
+    if (stg && (p.out_mode == 0 || p.out_mode == 3) && (p.qsplit < 0 || p.qsplit % 32 == 0)) {
+      const int64_t row0 = (int64_t)(m - lane) * p.ldc + n0;
+      if (p.out_mode == 3) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) * alpha;
+        tc_rows_store_f32(stg, v, reinterpret_cast<float*>(Cb) + cbase + row0, p.ldc, true);
+        continue;
+      }
+      const bool ss = (m >= p.qsplit) && (n0 >= p.qsplit);
+      if (!split || ss) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          v[j] = __uint_as_float(r[j]) * alpha;
+          if (split) ss_max = fmaxf(ss_max, fabsf(v[j]));
+        }
+        tc_rows_store_f32(stg, v, reinterpret_cast<float*>(Cb) + cbase + row0, p.ldc, false);
+      }
+      if (p.C2 && !(p.qsplit >= 0 && ss)) {
+        uint32_t h[8];
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const float a0 = __uint_as_float(r[j]), a1 = __uint_as_float(r[j + 1]);
+          if (p.c2_bf16) {
+            __nv_bfloat162 t = __floats2bfloat162_rn(a0, a1);
+            h[j / 2] = *reinterpret_cast<uint32_t*>(&t);
+          } else {
+            __half2 t = __floats2half2_rn(a0, a1);
+            h[j / 2] = *reinterpret_cast<uint32_t*>(&t);
+          }
+        }
+        tc_rows_store_u16(stg, h, reinterpret_cast<uint16_t*>(p.C2) + cbase + row0, p.ldc);
+      }
+      continue;
+    }
     if (p.out_mode == 0) {
       const bool ss = (m >= p.qsplit) && (n0 >= p.qsplit);
       if (!split || ss) {
@@ -178,6 +262,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int fail_sh;
+  __shared__ float stg_sh[4][32 * 17];  // the epilogue's row transposes, one per warp
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // 1024-byte aligned stage buffers
@@ -266,7 +351,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ CU
     const int m = m0 + tid;
     const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
     const bool split = p.qsplit >= 0 && p.qi[b] != p.qj[b];
-    float ss_max = tc_epilogue_row(p, b, m, lane_addr, ok);
+    float ss_max = tc_epilogue_row(p, b, m, lane_addr, ok, stg_sh[warp]);
     if (p.amax_ss && split) {
       for (int o = 16; o; o >>= 1) ss_max = fmaxf(ss_max, __shfl_xor_sync(0xffffffffu, ss_max, o));
       if (lane == 0 && ss_max > 0.0f) atomicMax(p.amax_ss, __float_as_uint(ss_max));
@@ -313,6 +398,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_ws_kernel(const __grid_constan
   __shared__ uint32_t tmem_base_sh;
   __shared__ int fail_sh;
   __shared__ uint32_t issued_sh;
+  __shared__ float stg_sh[4][32 * 17];  // the epilogue warps' row transposes
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t raw = smem_u32(smem_raw);
@@ -436,7 +522,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_ws_kernel(const __grid_constan
       tc_fence_after();
       const int64_t b = t / mtiles;
       const int m = (int)(t % mtiles) * TC_BM + row;
-      float ss_max = tc_epilogue_row(p, b, m, tmem + buf * cols + lane_off, ok);
+      float ss_max = tc_epilogue_row(p, b, m, tmem + buf * cols + lane_off, ok, stg_sh[q]);
       if (p.amax_ss && p.qsplit >= 0 && p.qi[b] != p.qj[b]) {
         for (int o = 16; o; o >>= 1) ss_max = fmaxf(ss_max, __shfl_xor_sync(0xffffffffu, ss_max, o));
         if (lane == 0 && ss_max > 0.0f) atomicMax(p.amax_ss, __float_as_uint(ss_max));
