@@ -300,7 +300,6 @@ h2_status setup_device(h2_ctx* c) {
   c->X32p.assign(L + 1, nullptr);
   c->S32p.assign(L + 1, nullptr);
   c->Slo.assign(L + 1, nullptr);
-  c->Xlo_lv.assign(L + 1, nullptr);
   size_t npart = c->sym ? (size_t)c->npu * 2 * lf.D : 0;
   // one batch of all levels' stored coupling pairs when every level with
   // couplings qualifies for the symmetric form with one common rank
@@ -372,10 +371,10 @@ h2_status setup_device(h2_ctx* c) {
     // the residual's FP32-pair matvec reads the couplings in full
     CKC(dalloc(c, &c->Slo[l], ns));
     launch_split_lo(d.S, d.S32, c->Slo[l], (int64_t)d.FP * d.K * d.K, 0);
-    // and the bases of every level (its passes through them)
-    CKC(dalloc(c, &c->Xlo_lv[l], nx));
-    launch_split_lo(d.X, d.X32, c->Xlo_lv[l], (int64_t)nx, 0);
-    if (l == L) c->Xlo = c->Xlo_lv[l];
+    if (l == L) {
+      CKC(dalloc(c, &c->Xlo, nx));
+      launch_split_lo(d.X, d.X32, c->Xlo, (int64_t)nx, 0);
+    }
     c->X64p[l] = d.X;
     c->S64p[l] = d.S;
     c->X32p[l] = d.X32;
@@ -1194,20 +1193,12 @@ void matvec_impl(h2_ctx* c, const double* x, double* y) {
 void matvec_df(h2_ctx* c, const double* x, double* y) {
   const int L = c->L;
   cudaStream_t st = c->stream;
-  // the passes through the bases in FP32 pairs too, for ranks the
-  // column kernel covers (K <= 256)
-  bool pair_bases = true;
-  for (int l = 1; l <= L; ++l) pair_bases = pair_bases && c->lv[l].K <= 256 && c->lv[l].K % 4 == 0;
   auto leaf = [&](const double* yhL) {
     const DevLevel& lf = c->lv[L];
     if (c->sym) {
       launch_matvec_sym_pairs_df(lf.D, c->npu, c->sym_i, c->sym_j, c->A32, c->Alo, x, c->part64, st);
-      if (L && pair_bases)
-        launch_matvec_sym_sum_df(lf.nb, lf.D, lf.K, c->sym_ptr, c->sym_ent, c->X32p[L], c->Xlo_lv[L], yhL, c->part64,
-                                 y, st);
-      else
-        launch_matvec_sym_sum<double>(lf.nb, lf.D, L ? lf.K : 0, c->sym_ptr, c->sym_ent, L ? c->X64p[L] : nullptr,
-                                      yhL, c->part64, y, st);
+      launch_matvec_sym_sum<double>(lf.nb, lf.D, L ? lf.K : 0, c->sym_ptr, c->sym_ent, L ? c->X64p[L] : nullptr, yhL,
+                                    c->part64, y, st);
     } else {
       launch_matvec_leaf_df(lf, c->A32, c->Alo, L ? c->X32p[L] : nullptr, L ? c->Xlo : nullptr, x, yhL, y, st);
     }
@@ -1217,19 +1208,13 @@ void matvec_df(h2_ctx* c, const double* x, double* y) {
     return;
   }
   const std::vector<int64_t>& off = c->hat_off;
-  for (int l = L; l >= 1; --l) {
-    const double* xin = (l == L) ? x : c->xhat + off[l + 1];
-    if (pair_bases) launch_matvec_up_df(c->lv[l], c->X32p[l], c->Xlo_lv[l], xin, c->xhat + off[l], st);
-    else launch_matvec_up<double>(c->lv[l], c->X64p[l], xin, c->xhat + off[l], st);
-  }
+  launch_matvec_up<double>(c->lv[L], c->X64p[L], x, c->xhat + off[L], st);
+  for (int l = L - 1; l >= 1; --l) launch_matvec_up<double>(c->lv[l], c->X64p[l], c->xhat + off[l + 1], c->xhat + off[l], st);
   // (the couplings in full: the symmetric pair form is slower in FP32-pair
   // arithmetic at these sizes)
   for (int l = 1; l <= L; ++l)
     launch_matvec_far_df(c->lv[l], c->S32p[l], c->Slo[l], c->xhat + off[l], c->yhat + off[l], st);
-  for (int l = 1; l < L; ++l) {
-    if (pair_bases) launch_matvec_down_df(c->lv[l], c->X32p[l], c->Xlo_lv[l], c->yhat + off[l], c->yhat + off[l + 1], st);
-    else launch_matvec_down<double>(c->lv[l], c->X64p[l], c->yhat + off[l], c->yhat + off[l + 1], st);
-  }
+  for (int l = 1; l < L; ++l) launch_matvec_down<double>(c->lv[l], c->X64p[l], c->yhat + off[l], c->yhat + off[l + 1], st);
   leaf(c->yhat + off[L]);
 }
 void matvec32(h2_ctx* c, const float* x, float* y, EventPairs* leaf_ev = nullptr) {

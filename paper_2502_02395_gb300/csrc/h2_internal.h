@@ -333,7 +333,6 @@ struct h2_ctx {
   // residual)
   float* Alo = nullptr;
   float* Xlo = nullptr;      // leaf level
-  std::vector<float*> Xlo_lv;  // every level's (index l; [0] unused)
   std::vector<float*> Slo;   // per level (index l; [0] unused)
   // Symmetric leaf storage of A32 / Alo: only the near pairs i <= j
   // ("stored pairs", sym_q: their index among the near pairs), and per box

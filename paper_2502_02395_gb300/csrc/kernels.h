@@ -143,12 +143,6 @@ template <typename T>
 void launch_matvec_leaf(const DevLevel& L, const T* A, const T* X, const T* x, const T* yh, T* y, cudaStream_t st);
 // The FP64 matvec's far and leaf steps with each FP64 matrix held as an FP32
 // pair (hi = fl32, lo = fl32 of the rest) and FP32 pair arithmetic.
-void launch_matvec_up_df(const DevLevel& L, const float* Xh, const float* Xl, const double* x, double* xh,
-                         cudaStream_t st);
-void launch_matvec_down_df(const DevLevel& L, const float* Xh, const float* Xl, const double* yh, double* yhc,
-                           cudaStream_t st);
-void launch_matvec_sym_sum_df(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const float* Xh,
-                              const float* Xl, const double* yh, const double* part, double* y, cudaStream_t st);
 void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const double* xh, double* yh,
                           cudaStream_t st);
 void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, const float* Xh, const float* Xl,

@@ -1842,125 +1842,6 @@ void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, 
   mv_leaf_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, Ah, Al, Xh, Xl, x, yh, y);
 }
 
-// The passes through the bases in FP32-pair arithmetic (the residual's
-// matvec; FP64 in, FP64 out, about 2^-46 of the absolute row sums, as the
-// couplings and the leaf blocks).
-// upward: xh_i[a] = sum_d X_i[d*K + a] x_i[d]: thread t takes column
-// a = t % K and every G-th d from t / K (G = 256 / K groups), the groups'
-// pairs meet in FP64 in shared memory.
-__global__ void __launch_bounds__(256) mv_up_df_kernel(int D, int K, const float* __restrict__ Xh,
-                                                       const float* __restrict__ Xl, const double* __restrict__ x,
-                                                       double* __restrict__ xh) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float* sxh = reinterpret_cast<float*>(smraw);    // D
-  float* sxl = sxh + ((D + 3) & ~3);               // D
-  double* sp = reinterpret_cast<double*>(sxl + ((D + 3) & ~3));  // 256
-  const int i = blockIdx.x, tid = threadIdx.x;
-  const int G = max(1, (int)blockDim.x / K);
-  for (int e = tid; e < D; e += blockDim.x) df_split(x[(int64_t)i * D + e], sxh[e], sxl[e]);
-  __syncthreads();
-  const int a = tid % K, g = tid / K;
-  double v = 0.0;
-  if (g < G && a < K) {
-    const float* Mh = Xh + (int64_t)i * D * K + a;
-    const float* Ml = Xl + (int64_t)i * D * K + a;
-    float H = 0.0f, L = 0.0f;
-    int d = g;
-    for (; d + 3 * G < D; d += 4 * G) {
-      float mh[4], ml[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) mh[u] = __ldg(Mh + (int64_t)(d + u * G) * K), ml[u] = __ldg(Ml + (int64_t)(d + u * G) * K);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) df_fma(H, L, mh[u], ml[u], sxh[d + u * G], sxl[d + u * G]);
-    }
-    for (; d < D; d += G) df_fma(H, L, __ldg(Mh + (int64_t)d * K), __ldg(Ml + (int64_t)d * K), sxh[d], sxl[d]);
-    v = (double)H + (double)L;
-  }
-  sp[tid] = v;
-  __syncthreads();
-  for (int e = tid; e < K; e += blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < G; ++q) s += sp[q * K + e];
-    xh[(int64_t)i * K + e] = s;
-  }
-}
-void launch_matvec_up_df(const DevLevel& L, const float* Xh, const float* Xl, const double* x, double* xh,
-                         cudaStream_t st) {
-  const size_t sm = 2 * sizeof(float) * (size_t)((L.D + 3) & ~3) + sizeof(double) * 256;
-  set_smem((const void*)mv_up_df_kernel, sm);
-  ++g_launches;
-  mv_up_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, Xh, Xl, x, xh);
-}
-
-// downward: [yh_2p; yh_2p+1] += X_p yh_p (rows of X_p)
-__global__ void __launch_bounds__(256, 2) mv_down_df_kernel(int D, int K, const float* __restrict__ Xh,
-                                                            const float* __restrict__ Xl, const double* __restrict__ yh,
-                                                            double* __restrict__ yhc) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int Kp = (K + 3) & ~3;
-  float* hh = reinterpret_cast<float*>(smraw);  // Kp
-  float* hl = hh + Kp;                          // Kp
-  const int p = blockIdx.x;
-  for (int e = threadIdx.x; e < K; e += blockDim.x) df_split(yh[(int64_t)p * K + e], hh[e], hl[e]);
-  __syncthreads();
-  float H[kRPWdf], L[kRPWdf];
-  double* out = yhc + (int64_t)p * D;
-  for (int r0 = 0; r0 < D; r0 += 8 * kRPWdf) {
-    zero(H);
-    zero(L);
-    rows_acc_df<kRPWdf>(r0, Xh + (int64_t)p * D * K, Xl + (int64_t)p * D * K, K, D, K, hh, hl, H, L);
-    rows_finish_df<kRPWdf>(r0, D, H, L, out, out);
-  }
-}
-void launch_matvec_down_df(const DevLevel& L, const float* Xh, const float* Xl, const double* yh, double* yhc,
-                           cudaStream_t st) {
-  const size_t sm = 2 * sizeof(float) * (size_t)((L.K + 3) & ~3);
-  ++g_launches;
-  mv_down_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, Xh, Xl, yh, yhc);
-}
-
-// leaf, symmetric storage: y_i = X_i yh_i + the box's partial products
-// (FP64, in list order)
-__global__ void __launch_bounds__(256, 2) mv_sym_sum_df_kernel(int D, int K, const int64_t* __restrict__ ptr,
-                                                               const int32_t* __restrict__ ent,
-                                                               const float* __restrict__ Xh,
-                                                               const float* __restrict__ Xl,
-                                                               const double* __restrict__ yh,
-                                                               const double* __restrict__ part,
-                                                               double* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int Kp = (K + 3) & ~3;
-  float* hh = reinterpret_cast<float*>(smraw);  // Kp
-  float* hl = hh + Kp;                          // Kp
-  double* sb = reinterpret_cast<double*>(hl + Kp + (Kp & 1));  // D (8-byte aligned: 2 Kp floats, Kp even)
-  const int i = blockIdx.x;
-  const int64_t e0 = ptr[i], e1 = ptr[i + 1];
-  for (int e = threadIdx.x; e < K; e += blockDim.x) df_split(yh[(int64_t)i * K + e], hh[e], hl[e]);
-  for (int r = threadIdx.x; r < D; r += blockDim.x) {
-    double s = 0.0;
-    for (int64_t q = e0; q < e1; ++q) {
-      const int en = ent[q];
-      s += part[(int64_t)(en >> 1) * 2 * D + (en & 1) * D + r];
-    }
-    sb[r] = s;
-  }
-  __syncthreads();
-  float H[kRPWdf], L[kRPWdf];
-  for (int r0 = 0; r0 < D; r0 += 8 * kRPWdf) {
-    zero(H);
-    zero(L);
-    rows_acc_df<kRPWdf>(r0, Xh + (int64_t)i * D * K, Xl + (int64_t)i * D * K, K, D, K, hh, hl, H, L);
-    rows_finish_df<kRPWdf>(r0, D, H, L, sb, y + (int64_t)i * D);
-  }
-}
-void launch_matvec_sym_sum_df(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const float* Xh,
-                              const float* Xl, const double* yh, const double* part, double* y, cudaStream_t st) {
-  const size_t Kp = (size_t)((K + 3) & ~3);
-  const size_t sm = 2 * sizeof(float) * Kp + sizeof(double) * ((size_t)D + 1);
-  ++g_launches;
-  mv_sym_sum_df_kernel<<<nb, 256, sm, st>>>(D, K, ptr, ent, Xh, Xl, yh, part, y);
-}
-
 // lo[e] = fl32(a[e] - hi[e]) (hi = fl32(a))
 __global__ void split_lo_kernel(const double* __restrict__ a, const float* __restrict__ hi, float* __restrict__ lo,
                                 int64_t n) {
