@@ -467,7 +467,7 @@ h2_status h2_plan_predicted(const h2_params* p, const double* points, int64_t N,
  * interpolative decomposition comes from a randomized sketch M_i Omega of
  * K_l + 26 columns (Rademacher Omega from splitmix64) followed by a pivoted
  * QR truncated at K_l, in place of the full rank-revealing pass over M_i.
- * The plain pivoted-QR compression stays the fallback and the judge: a box
+ * The plain pivoted-QR compression stays the fallback and the error check: a box
  * whose sketch shows more than tol of its leading pivot beyond K_l (below
  * the cap), or whose error on 6 further random probes of M_i exceeds
  * 10 max(tol, that estimate), is compressed the plain way; if that needs a
