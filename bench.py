@@ -78,6 +78,9 @@ def parse():
     ap.add_argument("--build", default="plain", choices=["plain", "gpu"],
                     help="construction of the instance (untimed): the host rank-revealing pass, or the GPU "
                          "sketches at the level caps (h2_build_gpu)")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="before the timed steps, h2_autotune picks the GEMM form and the substitution's launch "
+                         "shapes on this instance (overrides --tc-kernel, --graphs, --box-stream)")
     ap.add_argument("--box-stream", type=int, default=0, choices=[0, 1],
                     help="substitution per-box steps on large levels: 1 streamed persistent kernels, 0 row-split")
     ap.add_argument("--tc-kernel", type=int, default=2, choices=[0, 1, 2],
@@ -539,6 +542,11 @@ def main():
     S.set_option("graphs", args.graphs)
     S.set_option("tc_kernel", args.tc_kernel)
     S.set_option("box_stream", args.box_stream)
+    tuned = None
+    if args.autotune and args.prec != "fp64":
+        # kernel forms and launch shapes measured on this instance (untimed)
+        tuned = S.autotune(args.prec)
+        args.tc_kernel, args.graphs, args.box_stream = tuned["tc_kernel"], tuned["graphs"], tuned["box_stream"]
     b_dev = torch.from_numpy(b).cuda()
     x_dev = torch.zeros_like(b_dev)
     torch.cuda.synchronize()
@@ -669,6 +677,7 @@ def main():
         "relres": float(np.max(rels)), "relres_fp64_matvec": r_check, "dense_rows_check": dense,
         "iters": int(np.max(its_all)),
         "rr_lu": args.rr_lu, "residual": args.residual, "graphs": args.graphs, "tc_kernel": args.tc_kernel, "box_stream": args.box_stream,
+        "autotune": tuned and {k: v for k, v in tuned.items() if k != "tried"},
         "phases_s": ph, "build_s": build_s, "build": args.build, "fp64": fp64,
         "speedup_vs_fp64": (fp64["s_per_step"] / value) if fp64 else None,
         "roofline": roof, "rooflines": roofs, "fp64_peak_tflops": fp64_tf, "calls": calls,

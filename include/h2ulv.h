@@ -334,15 +334,39 @@ h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
  *                         copies; 2 the same on every level of those
  *                         shapes, whatever its box count; 0 (default)
  *                         row-split kernels (measured faster at N = 2^18:
- *                         22.6 against 24.9 ms of substitution per step). */
+ *                         22.6 against 24.9 ms of substitution per step).
+ *   H2_OPT_PAIR_CTAS      CTAs per SM of the TMA-fed pair kernels of the
+ *                         FP16/BF16 substitution, 1..3 (default 3;
+ *                         process-wide).
+ *   H2_OPT_BOX_CTAS       CTAs per SM the substitution's per-box row splits
+ *                         aim at, 1..8 (default 2; process-wide). */
 typedef enum {
   H2_OPT_RR_LU_FP64 = 0,
   H2_OPT_RESIDUAL_FP64 = 1,
   H2_OPT_GRAPHS = 2,
   H2_OPT_TC_KERNEL = 3,
   H2_OPT_FP64_LEAF = 4,
-  H2_OPT_BOX_STREAM = 5
+  H2_OPT_BOX_STREAM = 5,
+  H2_OPT_PAIR_CTAS = 6,
+  H2_OPT_BOX_CTAS = 7
 } h2_option;
+
+/* Autotuner of the kernel forms and launch shapes (no counterpart in the
+ * paper), process-wide settings measured on this context's instance:
+ * (1) the form of the factorization's main-chain tensor-core GEMMs
+ * (H2_OPT_TC_KERNEL 0, 1, 2: each factors twice, the second timed);
+ * (2) the substitution's launch shapes: TMA pair-kernel CTAs per SM (2 or
+ * 3), per-box row-split CTAs per SM (1, 2 or 4), the streamed per-box form
+ * (H2_OPT_BOX_STREAM 0 or 1) and CUDA-graph replay (H2_OPT_GRAPHS 0 or 1),
+ * each of the 24 combinations timed over six ULV applications after two.
+ * The fastest of each is kept (set for every context) and the context is
+ * left factored in prec (H2_PREC_FP16 or H2_PREC_BF16).  json (may be NULL)
+ * receives the choices and the times: {"tc_kernel", "factor_s": [3],
+ * "pair_ctas_per_sm", "box_ctas_per_sm", "box_stream", "graphs",
+ * "subst_ms", "tried": [[pair, box, stream, graphs, ms], ...]}.
+ * Errors: H2_ERR_INVALID_ARG (prec, cap too small), those of h2_factor,
+ * H2_ERR_OOM, H2_ERR_TIMEOUT. */
+h2_status h2_autotune(h2_ctx* c, int32_t prec, char* json, size_t cap);
 
 /* Set an h2_option to value (0 or 1; 0 .. 2 for H2_OPT_TC_KERNEL and H2_OPT_BOX_STREAM).
  * Errors: H2_ERR_INVALID_ARG. */
@@ -544,7 +568,9 @@ h2_status h2_batch_create_forest(h2_batch** out, const h2_params* p, const doubl
 h2_status h2_batch_run(h2_batch* b, int32_t prec, const double* const* B, double* const* X, double target,
                        int32_t max_iters, double* relres, int32_t* iters, double* seconds);
 
-/* Autotune the worker count: run the whole batch (factor and solve) with
+/* Autotune the batch: first h2_autotune on the largest context (kernel
+ * forms and launch shapes, process-wide), then the worker count: run the
+ * whole batch (factor and solve) with
  * 1, 2, 4, 8 and 16 workers (up to twice the system count) and keep the
  * fastest; *workers_out (may be NULL) receives it.  A system that stops
  * above the target does not end the tuning (H2_ERR_NOT_CONVERGED is
@@ -553,8 +579,9 @@ h2_status h2_batch_tune(h2_batch* b, int32_t prec, const double* const* B, doubl
                         int32_t max_iters, int32_t* workers_out);
 
 /* JSON: system count, mode ("pool" or "forest"), group count (forest: the
- * systems per group), worker count, the last run's seconds and the tuning
- * times by worker count.  Errors: H2_ERR_INVALID_ARG (cap too small). */
+ * systems per group), worker count, the last run's seconds, the tuning
+ * times by worker count and h2_autotune's choices ("kernels").  Errors:
+ * H2_ERR_INVALID_ARG (cap too small). */
 h2_status h2_batch_stats(const h2_batch* b, char* json, size_t cap);
 
 /* One-line description of the batch's last error ("" if none). */

@@ -32,14 +32,15 @@ STATUS = {0: "H2_OK", -1: "H2_ERR_INVALID_ARG", -2: "H2_ERR_OOM", -3: "H2_ERR_SI
 # every symbol include/h2ulv.h declares
 EXPORTED = ("h2_build", "h2_plan", "h2_import", "h2_factor", "h2_release_factorization", "h2_solve", "h2_solve_many", "h2_ulv_apply",
             "h2_matvec", "h2_matvec_many", "h2_matvec_noalloc", "h2_matvec_arith", "h2_set_option",
-            "h2_wait_selftest", "h2_set_memory_limit", "h2_rank_data", "h2_rank_model_create",
+            "h2_wait_selftest", "h2_autotune", "h2_set_memory_limit", "h2_rank_data", "h2_rank_model_create",
             "h2_rank_model_set_weights", "h2_rank_model_get_weights", "h2_rank_model_grad", "h2_rank_model_train",
             "h2_rank_model_predict", "h2_rank_model_last_error", "h2_rank_model_destroy", "h2_plan_predicted",
             "h2_build_predicted", "h2_build_gpu", "h2_tree_depth", "h2_build_forest", "h2_batch_create",
             "h2_batch_create_forest", "h2_batch_run", "h2_batch_tune",
             "h2_batch_stats", "h2_batch_last_error", "h2_batch_destroy",
             "h2_set_refinement", "h2_set_stream", "h2_stats", "h2_export", "h2_last_error", "h2_destroy")
-OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1, "graphs": 2, "tc_kernel": 3, "fp64_leaf": 4, "box_stream": 5}
+OPTIONS = {"rr_lu_fp64": 0, "residual_fp64": 1, "graphs": 2, "tc_kernel": 3, "fp64_leaf": 4, "box_stream": 5,
+           "pair_ctas": 6, "box_ctas": 7}
 ARITH = {"fp64": 0, "fp32": 1, "fp32_pair": 2}
 
 
@@ -93,6 +94,7 @@ def lib() -> ctypes.CDLL:
             "h2_set_option": (i32, [vp, i32, i64]),
             "h2_matvec_arith": (i32, [vp, vp, vp, i32]),
             "h2_wait_selftest": (i32, [vp, i64]),
+            "h2_autotune": (i32, [vp, i32, ctypes.c_char_p, ctypes.c_size_t]),
             "h2_set_memory_limit": (i32, [ctypes.c_uint64]),
             "h2_rank_data": (i32, [vp, vp, i64, vp, vp, vp, i64, vp]),
             "h2_rank_model_create": (i32, [pp, ctypes.c_uint64]),
@@ -583,6 +585,13 @@ class H2Solver:
 
     def set_option(self, option, value):
         h2_set_option(self.ctx, option, value)
+
+    def autotune(self, prec="fp16") -> dict:
+        """h2_autotune: measure and keep the fastest kernel forms and launch
+        shapes on this instance; the context is left factored in prec."""
+        buf = ctypes.create_string_buffer(1 << 14)
+        _check(lib().h2_autotune(self.ctx, PRECS[prec], buf, len(buf)), self.ctx)
+        return json.loads(buf.value.decode())
 
     def matvec_arith(self, x, arith="fp64"):
         y = np.zeros_like(x) if isinstance(x, np.ndarray) else x.new_zeros(x.shape)

@@ -43,6 +43,7 @@ struct h2_batch {
   std::vector<int> sys_group;
   std::vector<int64_t> sys_off, sys_n;
   int workers = 4;
+  std::string kernels;  // h2_autotune's choices on the largest context (JSON; "" before h2_batch_tune)
   std::vector<cudaStream_t> streams;
   std::string err;
   double last_seconds = 0;
@@ -320,6 +321,20 @@ h2_status h2_batch_tune(h2_batch* b, int32_t prec, const double* const* B, doubl
   if (!b || prec < 0 || prec > H2_PREC_BF16 || !B || !X) return H2_ERR_INVALID_ARG;
   b->err.clear();
   if (!host_vectors(b, B, X)) return H2_ERR_INVALID_ARG;
+  // kernel forms and launch shapes first, on the largest context
+  {
+    size_t big = 0;
+    for (size_t k = 1; k < b->ctx.size(); ++k)
+      if (b->n[k] > b->n[big]) big = k;
+    std::vector<char> js(1 << 14);
+    h2_status s = h2_autotune(b->ctx[big], prec, js.data(), js.size());
+    if (b->forest) h2_release_factorization(b->ctx[big]);
+    if (s != H2_OK) {
+      b->err = std::string("autotune: ") + h2_last_error(b->ctx[big]);
+      return s;
+    }
+    b->kernels = js.data();
+  }
   const int cand[5] = {1, 2, 4, 8, 16};
   double best = INFINITY;
   int bw = b->workers;
@@ -352,6 +367,7 @@ h2_status h2_batch_stats(const h2_batch* b, char* json, size_t cap) {
     first = false;
   }
   o += "}";
+  if (!b->kernels.empty()) o += ",\"kernels\":" + b->kernels;
   if (b->forest) {
     o += ",\"group_systems\":[";
     for (size_t g = 0; g < b->group_sys.size(); ++g) o += (g ? "," : "") + std::to_string(b->group_sys[g].size());

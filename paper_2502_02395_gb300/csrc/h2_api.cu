@@ -2003,7 +2003,8 @@ h2_status h2_set_refinement(h2_ctx* c, int32_t method, int32_t restart) {
 h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value) {
   if (!c) return H2_ERR_INVALID_ARG;
   c->err.clear();
-  if ((value != 0 && value != 1) && option != H2_OPT_TC_KERNEL && !(option == H2_OPT_BOX_STREAM && value == 2)) {
+  if ((value != 0 && value != 1) && option != H2_OPT_TC_KERNEL && !(option == H2_OPT_BOX_STREAM && value == 2) &&
+      option != H2_OPT_PAIR_CTAS && option != H2_OPT_BOX_CTAS) {
     c->err = "option value must be 0 or 1";
     return H2_ERR_INVALID_ARG;
   }
@@ -2019,6 +2020,22 @@ h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value) {
       return H2_OK;
     case H2_OPT_GRAPHS:
       c->use_graphs = value != 0;
+      drop_graphs(c);
+      return H2_OK;
+    case H2_OPT_PAIR_CTAS:
+      if (value < 1 || value > 3) {
+        c->err = "pair-kernel CTAs per SM outside 1..3";
+        return H2_ERR_INVALID_ARG;
+      }
+      g_pair_ctas_per_sm = (int)value;
+      drop_graphs(c);
+      return H2_OK;
+    case H2_OPT_BOX_CTAS:
+      if (value < 1 || value > 8) {
+        c->err = "per-box CTAs per SM outside 1..8";
+        return H2_ERR_INVALID_ARG;
+      }
+      g_box_ctas_per_sm = (int)value;
       drop_graphs(c);
       return H2_OK;
     case H2_OPT_BOX_STREAM:
@@ -2080,6 +2097,98 @@ h2_status h2_matvec_arith(h2_ctx* c, const double* x, double* y, int32_t arith) 
   CKC(cudaGetLastError());
   CKS(vec_out(c, c->y64, y));
   CKC(cudaStreamSynchronize(c->stream));
+  return H2_OK;
+}
+
+h2_status h2_autotune(h2_ctx* c, int32_t prec, char* json, size_t cap) {
+  if (!c || (prec != H2_PREC_FP16 && prec != H2_PREC_BF16)) return H2_ERR_INVALID_ARG;
+  c->err.clear();
+  std::ostringstream o;
+  o.precision(6);
+  // (1) the kernel form of the factorization's main-chain GEMMs: each form
+  // factors twice (the first also allocates), the second is timed
+  double tf[3] = {0, 0, 0};
+  int best_form = 2;
+  for (int form = 0; form < 3; ++form) {
+    g_tc_kernel = form;
+    for (int rep = 0; rep < 2; ++rep) CKS(h2_factor(c, prec));
+    tf[form] = c->times.total_factor;
+  }
+  best_form = 0;
+  for (int form = 1; form < 3; ++form)
+    if (tf[form] < tf[best_form]) best_form = form;
+  g_tc_kernel = best_form;
+  CKS(h2_factor(c, prec));
+  o << "{\"tc_kernel\":" << best_form << ",\"factor_s\":[" << tf[0] << "," << tf[1] << "," << tf[2] << "]";
+  // (2) the substitution's launch shapes, timed on ULV applications
+  const int64_t n = nslots(c);
+  float *v = nullptr, *z = nullptr;
+  if (cudaMalloc(&v, n * sizeof(float)) != cudaSuccess || cudaMalloc(&z, n * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    if (v) cudaFree(v);
+    c->err = "autotune: no room for two vectors";
+    return H2_ERR_OOM;
+  }
+  cudaMemsetAsync(v, 0, n * sizeof(float), c->stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  struct Shape {
+    int pair, box, stream, graphs;
+    float ms;
+  };
+  std::vector<Shape> tried;
+  Shape best{g_pair_ctas_per_sm.load(), g_box_ctas_per_sm.load(), g_box_stream.load(), c->use_graphs ? 1 : 0, 1e30f};
+  h2_status st = subst_clear(c);
+  for (int pair : {2, 3})
+    for (int box : {1, 2, 4})
+      for (int stream : {0, 1})
+        for (int graphs : {0, 1}) {
+          if (st != H2_OK) break;
+          g_pair_ctas_per_sm = pair;
+          g_box_ctas_per_sm = box;
+          g_box_stream = stream;
+          c->use_graphs = graphs != 0;
+          drop_graphs(c);
+          for (int w = 0; w < 2; ++w) ulv_apply_f32(c, v, z);
+          cudaEventRecord(e0, c->stream);
+          for (int k = 0; k < 6; ++k) ulv_apply_f32(c, v, z);
+          cudaEventRecord(e1, c->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = H2_ERR_CUDA;
+            break;
+          }
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= 6;
+          tried.push_back({pair, box, stream, graphs, ms});
+          if (ms < best.ms) best = tried.back();
+        }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(v);
+  cudaFree(z);
+  if (st == H2_OK) st = subst_check(c);
+  g_pair_ctas_per_sm = best.pair;
+  g_box_ctas_per_sm = best.box;
+  g_box_stream = best.stream;
+  c->use_graphs = best.graphs != 0;
+  drop_graphs(c);
+  if (st != H2_OK) {
+    if (c->err.empty()) c->err = "autotune: a substitution run failed";
+    return st;
+  }
+  o << ",\"pair_ctas_per_sm\":" << best.pair << ",\"box_ctas_per_sm\":" << best.box << ",\"box_stream\":" << best.stream
+    << ",\"graphs\":" << best.graphs << ",\"subst_ms\":" << best.ms << ",\"tried\":[";
+  for (size_t k = 0; k < tried.size(); ++k)
+    o << (k ? "," : "") << "[" << tried[k].pair << "," << tried[k].box << "," << tried[k].stream << ","
+      << tried[k].graphs << "," << tried[k].ms << "]";
+  o << "]}";
+  const std::string s = o.str();
+  if (json) {
+    if (s.size() + 1 > cap) return H2_ERR_INVALID_ARG;
+    std::memcpy(json, s.c_str(), s.size() + 1);
+  }
   return H2_OK;
 }
 

@@ -21,6 +21,11 @@ extern std::atomic<int> g_tc_kernel;
 // of a supported shape, 0 (default) never (row-split kernels); process-wide
 // (H2_OPT_BOX_STREAM).
 extern std::atomic<int> g_box_stream;
+// Launch shapes of the substitution (h2_autotune): CTAs per SM targeted by
+// the per-box row splits (default 2) and of the TMA-fed pair kernels
+// (default 3; at most 3 fit their shared-memory rings).
+extern std::atomic<int> g_box_ctas_per_sm;
+extern std::atomic<int> g_pair_ctas_per_sm;
 
 // kernels_factor.cu
 void launch_eval_blocks(const KernelFn& G, const double* pts, int64_t npairs, const int32_t* pi,

@@ -1099,10 +1099,15 @@ static int num_sms() {
 // so they ask L2 for them before waiting on the previous kernel
 static bool small_level(int64_t nblocks) { return nblocks <= num_sms(); }
 
+// launch shapes the autotuner (h2_autotune) sets: per-box CTAs per SM and
+// TMA pair-kernel CTAs per SM (process-wide)
+std::atomic<int> g_box_ctas_per_sm{2};
+std::atomic<int> g_pair_ctas_per_sm{3};
+
 static int row_splits(int nb, int nrows) {
   const int nsm = num_sms();
   if (nb <= 0) return 1;
-  int ns = (2 * nsm + nb - 1) / nb;
+  int ns = (g_box_ctas_per_sm.load() * nsm + nb - 1) / nb;
   ns = std::min(ns, std::max(1, nrows / 32));
   return std::max(ns, 1);
 }
@@ -1118,7 +1123,7 @@ static void launch_pairs(const DevLevel& L, const FacLevel<T>& F, const int32_t*
       const CUtensorMap& tm = (PH == PH_RR) ? F.tm_rr : (PH == PH_SR ? F.tm_sr : F.tm_rs);
       const size_t stage = ((size_t)nr * nc * 2 + 127) & ~(size_t)127;
       const size_t sm = kPairStages * stage + 128;  // + room to align the ring
-      const int64_t grid = std::min<int64_t>(n, 3 * (int64_t)num_sms());
+      const int64_t grid = std::min<int64_t>(n, (int64_t)g_pair_ctas_per_sm.load() * num_sms());
       set_smem((const void*)pair_tma_kernel<TS, PH>, sm);
       launch_pdl(pair_tma_kernel<TS, PH>, (unsigned)grid, 256, sm, st, tm, L.D, L.R, L.K, n, list, L.near_j,
                  reinterpret_cast<const float*>(xv), reinterpret_cast<float*>(part), F.err);

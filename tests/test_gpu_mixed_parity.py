@@ -356,3 +356,31 @@ def test_cluster_inverse_root256(B, rr):
     _, rel, its = S.solve(W.uniform_rhs(n, 83), target=1e-10, max_iters=100)
     assert rel <= 1e-10
     S.close()
+
+
+def test_autotune_choices_and_parity(B):
+    """h2_autotune times the three GEMM forms and the 24 launch-shape
+    combinations of the substitution on this instance and keeps the fastest
+    of each; the context is left factored, its ULV application still meets
+    the oracle bound (8 u16) and the refined solve reaches 1e-10.  The
+    process-wide settings go back to the library's defaults afterwards."""
+    from oracle import ulv
+    name = "cube32768_yukawa"
+    H, F, flat, b = oracle_case(name)
+    S = solver(B, name)
+    try:
+        t = S.autotune("fp16")
+        print(f"\nautotune: form {t['tc_kernel']} (factor s {t['factor_s']}), pair {t['pair_ctas_per_sm']}, "
+              f"box {t['box_ctas_per_sm']}, streamed {t['box_stream']}, graphs {t['graphs']}: {t['subst_ms']:.3f} ms")
+        assert t["tc_kernel"] in (0, 1, 2) and t["factor_s"][t["tc_kernel"]] == min(t["factor_s"])
+        assert len(t["tried"]) == 24 and all(r[4] > 0 for r in t["tried"])
+        assert abs(t["subst_ms"] - min(r[4] for r in t["tried"])) <= 1e-6 * t["subst_ms"] + 1e-9
+        x = S.ulv_apply(b)
+        x_ref = ulv.solve_parallel(F, H, b)
+        assert np.abs(x - x_ref).max() <= 8 * U16["fp16"] * np.abs(x_ref).max()
+        _, rel, _ = S.solve(b, target=1e-10, max_iters=100)
+        assert rel <= 1e-10
+    finally:
+        for opt, val in (("tc_kernel", 2), ("pair_ctas", 3), ("box_ctas", 2), ("box_stream", 0), ("graphs", 1)):
+            S.set_option(opt, val)
+    S.close()
