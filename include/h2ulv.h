@@ -339,7 +339,8 @@ h2_status h2_matvec_noalloc(h2_ctx* c, const double* x, double* y);
  *                         FP16/BF16 substitution, 1..3 (default 3;
  *                         process-wide).
  *   H2_OPT_BOX_CTAS       CTAs per SM the substitution's per-box row splits
- *                         aim at, 1..8 (default 2; process-wide). */
+ *                         aim at, 1..8 (default 1, the autotuner's choice at
+ *                         N = 2^15 and 2^18; process-wide). */
 typedef enum {
   H2_OPT_RR_LU_FP64 = 0,
   H2_OPT_RESIDUAL_FP64 = 1,

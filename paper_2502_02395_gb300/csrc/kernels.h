@@ -22,7 +22,7 @@ extern std::atomic<int> g_tc_kernel;
 // (H2_OPT_BOX_STREAM).
 extern std::atomic<int> g_box_stream;
 // Launch shapes of the substitution (h2_autotune): CTAs per SM targeted by
-// the per-box row splits (default 2) and of the TMA-fed pair kernels
+// the per-box row splits (default 1) and of the TMA-fed pair kernels
 // (default 3; at most 3 fit their shared-memory rings).
 extern std::atomic<int> g_box_ctas_per_sm;
 extern std::atomic<int> g_pair_ctas_per_sm;

@@ -1101,7 +1101,7 @@ static bool small_level(int64_t nblocks) { return nblocks <= num_sms(); }
 
 // launch shapes the autotuner (h2_autotune) sets: per-box CTAs per SM and
 // TMA pair-kernel CTAs per SM (process-wide)
-std::atomic<int> g_box_ctas_per_sm{2};
+std::atomic<int> g_box_ctas_per_sm{1};
 std::atomic<int> g_pair_ctas_per_sm{3};
 
 static int row_splits(int nb, int nrows) {

@@ -381,6 +381,6 @@ def test_autotune_choices_and_parity(B):
         _, rel, _ = S.solve(b, target=1e-10, max_iters=100)
         assert rel <= 1e-10
     finally:
-        for opt, val in (("tc_kernel", 2), ("pair_ctas", 3), ("box_ctas", 2), ("box_stream", 0), ("graphs", 1)):
+        for opt, val in (("tc_kernel", 2), ("pair_ctas", 3), ("box_ctas", 1), ("box_stream", 0), ("graphs", 1)):
             S.set_option(opt, val)
     S.close()
