@@ -632,7 +632,8 @@ def main():
         s64 = S.stats()
         fp64 = {"s_per_step": f0.elapsed_time(f1) / args.fp64_steps / 1e3, "relres": r64[-1][1],
                 "iters": r64[-1][2], "factor_s": s64["times"]["factor"], "solve_s": s64["times"]["solve"],
-                "phases": {p: s64["times"][p] for p in PHASES}, "stats": s64}
+                "phases": {p: s64["times"][p] for p in PHASES}, "stats": s64,
+                "factor_gflops": sum(s64["flops"].values()) / s64["times"]["factor"] / 1e9}
 
     # dominant phase of the step and its roofline
     tc = stats.get("tensor_cores", False)
@@ -681,6 +682,9 @@ def main():
         "phases_s": ph, "build_s": build_s, "build": args.build, "fp64": fp64,
         "speedup_vs_fp64": (fp64["s_per_step"] / value) if fp64 else None,
         "roofline": roof, "rooflines": roofs, "fp64_peak_tflops": fp64_tf, "calls": calls,
+        # algorithmic flops of the factorization (QR, projection of the
+        # projected pairs, inverses, Schur updates, couplings) over its time
+        "factor_gflops": (sum(stats["flops"].values()) / ph["factor"] / 1e9) if ph.get("factor") else None,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(b.nbytes), "d2h_bytes_per_step": int(b.nbytes)},
         "gpu_launches": int(launches), "clocks": clocks,
