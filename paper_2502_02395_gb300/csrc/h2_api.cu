@@ -227,6 +227,8 @@ h2_status setup_device(h2_ctx* c) {
   // mixed-precision refinement (part of the instance)
   CKC(dalloc(c, &c->xhat32, c->hat_off[L + 1]));
   CKC(dalloc(c, &c->yhat32, c->hat_off[L + 1]));
+  for (float** p : {&c->xdf_h, &c->xdf_l}) CKC(dalloc(c, p, nslot));
+  for (float** p : {&c->hdf_h, &c->hdf_l}) CKC(dalloc(c, p, c->hat_off[L + 1]));
   c->sym = sym_leaf_supported(lf.D);
   if (c->sym) {
     // the kernels' near blocks are symmetric (A_ji = A_ij^T): keep i <= j
@@ -1193,14 +1195,16 @@ void matvec_impl(h2_ctx* c, const double* x, double* y) {
 void matvec_df(h2_ctx* c, const double* x, double* y) {
   const int L = c->L;
   cudaStream_t st = c->stream;
+  launch_split_df(x, c->xdf_h, c->xdf_l, nslots(c), st);
   auto leaf = [&](const double* yhL) {
     const DevLevel& lf = c->lv[L];
     if (c->sym) {
-      launch_matvec_sym_pairs_df(lf.D, c->npu, c->sym_i, c->sym_j, c->A32, c->Alo, x, c->part64, st);
+      launch_matvec_sym_pairs_df(lf.D, c->npu, c->sym_i, c->sym_j, c->A32, c->Alo, c->xdf_h, c->xdf_l, c->part64, st);
       launch_matvec_sym_sum<double>(lf.nb, lf.D, L ? lf.K : 0, c->sym_ptr, c->sym_ent, L ? c->X64p[L] : nullptr, yhL,
                                     c->part64, y, st);
     } else {
-      launch_matvec_leaf_df(lf, c->A32, c->Alo, L ? c->X32p[L] : nullptr, L ? c->Xlo : nullptr, x, yhL, y, st);
+      launch_matvec_leaf_df(lf, c->A32, c->Alo, L ? c->X32p[L] : nullptr, L ? c->Xlo : nullptr, c->xdf_h, c->xdf_l,
+                            yhL, y, st);
     }
   };
   if (L == 0) {
@@ -1210,10 +1214,11 @@ void matvec_df(h2_ctx* c, const double* x, double* y) {
   const std::vector<int64_t>& off = c->hat_off;
   launch_matvec_up<double>(c->lv[L], c->X64p[L], x, c->xhat + off[L], st);
   for (int l = L - 1; l >= 1; --l) launch_matvec_up<double>(c->lv[l], c->X64p[l], c->xhat + off[l + 1], c->xhat + off[l], st);
+  launch_split_df(c->xhat + off[1], c->hdf_h + off[1], c->hdf_l + off[1], off[L + 1] - off[1], st);
   // (the couplings in full: the symmetric pair form is slower in FP32-pair
   // arithmetic at these sizes)
   for (int l = 1; l <= L; ++l)
-    launch_matvec_far_df(c->lv[l], c->S32p[l], c->Slo[l], c->xhat + off[l], c->yhat + off[l], st);
+    launch_matvec_far_df(c->lv[l], c->S32p[l], c->Slo[l], c->hdf_h + off[l], c->hdf_l + off[l], c->yhat + off[l], st);
   for (int l = 1; l < L; ++l) launch_matvec_down<double>(c->lv[l], c->X64p[l], c->yhat + off[l], c->yhat + off[l + 1], st);
   leaf(c->yhat + off[L]);
 }

@@ -349,6 +349,9 @@ struct h2_ctx {
   cudaStream_t leaf_stream = nullptr;
   cudaEvent_t mv_fork = nullptr, mv_join = nullptr;
   double* part64 = nullptr;  // the same for the FP32-pair matvec
+  // the FP32-pair matvec's input vector and its basis coefficients (all
+  // levels) split into FP32 pairs once per matvec
+  float *xdf_h = nullptr, *xdf_l = nullptr, *hdf_h = nullptr, *hdf_l = nullptr;
   float *xhat32 = nullptr, *yhat32 = nullptr;
   // the stored coupling pairs of every level as one batch (levels with the
   // same rank cb_K): the FP32 matvec forms all levels' coupling products in

@@ -147,12 +147,14 @@ void launch_matvec_down(const DevLevel& L, const T* X, const T* yh, T* yh_child,
 template <typename T>
 void launch_matvec_leaf(const DevLevel& L, const T* A, const T* X, const T* x, const T* yh, T* y, cudaStream_t st);
 // The FP64 matvec's far and leaf steps with each FP64 matrix held as an FP32
-// pair (hi = fl32, lo = fl32 of the rest) and FP32 pair arithmetic.
-void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const double* xh, double* yh,
-                          cudaStream_t st);
+// pair (hi = fl32, lo = fl32 of the rest) and FP32 pair arithmetic; their
+// input vectors come as FP32 pairs too (launch_split_df).
+void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const float* xhh, const float* xhl,
+                          double* yh, cudaStream_t st);
 void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, const float* Xh, const float* Xl,
-                           const double* x, const double* yh, double* y, cudaStream_t st);
+                           const float* xh, const float* xl, const double* yh, double* y, cudaStream_t st);
 void launch_split_lo(const double* a, const float* hi, float* lo, int64_t n, cudaStream_t st);  // lo = fl32(a - hi)
+void launch_split_df(const double* v, float* h, float* l, int64_t n, cudaStream_t st);  // h = fl32(v), l = fl32(v - h)
 // Leaf matvec on the stored (i <= j) halves of symmetric leaf near blocks:
 // per stored pair k = (ui[k], uj[k]) the partial products [A x_j; A^T x_i]
 // into part (2 D per pair), then per box y = X yh + its partial products.
@@ -167,7 +169,7 @@ void launch_matvec_down_far(const DevLevel& L, const T* X, const T* yh, T* yh_ch
 void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A, const float* x,
                              float* part, bool pdl, cudaStream_t st);
 void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
-                                const float* Al, const double* x, double* part, cudaStream_t st);
+                                const float* Al, const float* xh, const float* xl, double* part, cudaStream_t st);
 template <typename T>
 void launch_matvec_sym_sum(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const T* X, const T* yh,
                            const T* part, T* y, cudaStream_t st, bool pdl = true);

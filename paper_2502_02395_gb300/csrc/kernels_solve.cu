@@ -1707,6 +1707,43 @@ __device__ __forceinline__ void df_fma(float& H, float& L, float mh, float ml, f
   L = __fadd_rn(L, __fadd_rn(small, err));
 }
 
+// (H, L) += (h, l) for FP32 pairs: an error-free two-sum of the high parts
+// (exact in either operand order) with its error joining the low parts
+__device__ __forceinline__ void df_add(float& H, float& L, float h, float l) {
+  const float s = __fadd_rn(H, h);
+  const float bb = __fsub_rn(s, H);
+  const float err = __fadd_rn(__fsub_rn(H, __fsub_rn(s, bb)), __fsub_rn(h, bb));
+  H = s;
+  L = __fadd_rn(L, __fadd_rn(l, err));
+}
+// The transposed warp sum (tsum) of N FP32 pairs per lane, in FP32-pair
+// arithmetic: lane l ends with the pair sum of value tsum_index<N, G>(l).
+// GB300 runs FP64 instructions at a small fraction of the FP32 rate, so the
+// FP32-pair kernels reduce in pairs and convert to FP64 once per result.
+template <int N, int G>
+__device__ __forceinline__ void df_tsum(const float (&h)[N], const float (&l)[N], float& H, float& L) {
+  if constexpr (N == 1) {
+    H = h[0], L = l[0];
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, H, o), ol = __shfl_xor_sync(0xffffffffu, L, o);
+      df_add(H, L, oh, ol);
+    }
+  } else {
+    const bool up = threadIdx.x & (G / 2);
+    float wh[N / 2], wl[N / 2];
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) {
+      wh[q] = up ? h[q + N / 2] : h[q];
+      wl[q] = up ? l[q + N / 2] : l[q];
+      const float xh = up ? h[q] : h[q + N / 2], xl = up ? l[q] : l[q + N / 2];
+      const float oh = __shfl_xor_sync(0xffffffffu, xh, G / 2), ol = __shfl_xor_sync(0xffffffffu, xl, G / 2);
+      df_add(wh[q], wl[q], oh, ol);
+    }
+    df_tsum<N / 2, G / 2>(wh, wl, H, L);
+  }
+}
+
 constexpr int kRPWdf = 8;  // rows per warp per pass: 64-row chunks
 
 // H[t] + L[t] += sum_c (Mh + Ml)[r_t * ld + c] (xh + xl)[c], rows r_t = r0 + warp + 8 t < nr
@@ -1753,17 +1790,16 @@ __device__ __forceinline__ void rows_acc_df(int r0, const float* __restrict__ Mh
   }
 }
 
-// out[r] = base[r] + sum over lanes of (H + L), added in FP64
+// out[r] = base[r] + sum over lanes of (H + L): the lanes' pairs added in
+// FP32-pair arithmetic, the result converted to FP64 once
 template <int RPW>
 __device__ __forceinline__ void rows_finish_df(int r0, int nr, const float (&H)[RPW], const float (&L)[RPW],
                                                const double* base, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double d[RPW];
-#pragma unroll
-  for (int t = 0; t < RPW; ++t) d[t] = (double)H[t] + (double)L[t];
-  const double v = tsum<RPW, 32, double>(d);
+  float sh, sl;
+  df_tsum<RPW, 32>(H, L, sh, sl);
   const int r = r0 + warp + 8 * tsum_index<RPW, 32>(lane);
-  if (tsum_leader<RPW, 32>(lane) && r < nr) out[r] = (base ? base[r] : 0.0) + v;
+  if (tsum_leader<RPW, 32>(lane) && r < nr) out[r] = (base ? base[r] : 0.0) + ((double)sh + (double)sl);
 }
 
 __device__ __forceinline__ void df_split(double v, float& h, float& l) {
@@ -1771,11 +1807,11 @@ __device__ __forceinline__ void df_split(double v, float& h, float& l) {
   l = (float)(v - (double)h);
 }
 
-// couplings: yh_i = sum_{far j} S_f xh_j
+// couplings: yh_i = sum_{far j} S_f xh_j (xh as FP32 pairs xhh + xhl)
 __global__ void __launch_bounds__(256, 2) mv_far_df_kernel(int K, const int64_t* __restrict__ ptr,
                                                            const int32_t* __restrict__ fj, const float* __restrict__ Sh,
-                                                           const float* __restrict__ Sl, const double* __restrict__ xh,
-                                                           double* __restrict__ yh) {
+                                                           const float* __restrict__ Sl, const float* __restrict__ xhh,
+                                                           const float* __restrict__ xhl, double* __restrict__ yh) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int i = blockIdx.x, tid = threadIdx.x;
   const int64_t p0 = ptr[i];
@@ -1785,7 +1821,9 @@ __global__ void __launch_bounds__(256, 2) mv_far_df_kernel(int K, const int64_t*
   float* sl = sh + (size_t)nf * Kp;             // nf * Kp
   for (int e = tid; e < nf * K; e += blockDim.x) {
     const int q = e / K, a = e - q * K;
-    df_split(xh[(int64_t)fj[p0 + q] * K + a], sh[q * Kp + a], sl[q * Kp + a]);
+    const int64_t g = (int64_t)fj[p0 + q] * K + a;
+    sh[q * Kp + a] = xhh[g];
+    sl[q * Kp + a] = xhl[g];
   }
   __syncthreads();
   float H[kRPWdf], L[kRPWdf];
@@ -1797,20 +1835,21 @@ __global__ void __launch_bounds__(256, 2) mv_far_df_kernel(int K, const int64_t*
     rows_finish_df<kRPWdf>(r0, K, H, L, nullptr, yh + (int64_t)i * K);
   }
 }
-void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const double* xh, double* yh,
-                          cudaStream_t st) {
+void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const float* xhh, const float* xhl,
+                          double* yh, cudaStream_t st) {
   const size_t sm = 2 * sizeof(float) * (size_t)((L.K + 3) & ~3) * std::max(L.max_far, 1);
   set_smem((const void*)mv_far_df_kernel, sm);
   ++g_launches;
-  mv_far_df_kernel<<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, Sh, Sl, xh, yh);
+  mv_far_df_kernel<<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, Sh, Sl, xhh, xhl, yh);
 }
 
 // leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j
 __global__ void __launch_bounds__(256, 2) mv_leaf_df_kernel(int D, int K, const int64_t* __restrict__ ptr,
                                                             const int32_t* __restrict__ nj, const float* __restrict__ Ah,
                                                             const float* __restrict__ Al, const float* __restrict__ Xh,
-                                                            const float* __restrict__ Xl, const double* __restrict__ x,
-                                                            const double* __restrict__ yh, double* __restrict__ y) {
+                                                            const float* __restrict__ Xl, const float* __restrict__ xh,
+                                                            const float* __restrict__ xl, const double* __restrict__ yh,
+                                                            double* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int i = blockIdx.x, tid = threadIdx.x;
   const int64_t p0 = ptr[i];
@@ -1824,7 +1863,9 @@ __global__ void __launch_bounds__(256, 2) mv_leaf_df_kernel(int D, int K, const 
     for (int e = tid; e < K; e += blockDim.x) df_split(yh[(int64_t)i * K + e], hh[e], hl[e]);
   for (int e = tid; e < nn * D; e += blockDim.x) {
     const int q = e / D, d = e - q * D;
-    df_split(x[(int64_t)nj[p0 + q] * D + d], xsh[q * Dp + d], xsl[q * Dp + d]);
+    const int64_t g = (int64_t)nj[p0 + q] * D + d;
+    xsh[q * Dp + d] = xh[g];
+    xsl[q * Dp + d] = xl[g];
   }
   __syncthreads();
   float H[kRPWdf], L[kRPWdf];
@@ -1839,12 +1880,25 @@ __global__ void __launch_bounds__(256, 2) mv_leaf_df_kernel(int D, int K, const 
   }
 }
 void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, const float* Xh, const float* Xl,
-                           const double* x, const double* yh, double* y, cudaStream_t st) {
+                           const float* xh, const float* xl, const double* yh, double* y, cudaStream_t st) {
   const size_t Kp = (L.K + 3) & ~3, Dp = (L.D + 3) & ~3;
   const size_t sm = 2 * sizeof(float) * (Kp + Dp * (size_t)L.max_near);
   set_smem((const void*)mv_leaf_df_kernel, sm);
   ++g_launches;
-  mv_leaf_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, Ah, Al, Xh, Xl, x, yh, y);
+  mv_leaf_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, Ah, Al, Xh, Xl, xh, xl, yh, y);
+}
+
+// h = fl32(v), l = fl32(v - h): an FP64 vector as FP32 pairs, once per use
+// of the vector rather than once per block that reads it
+__global__ void split_df_kernel(const double* __restrict__ v, float* __restrict__ h, float* __restrict__ l,
+                                int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    df_split(v[e], h[e], l[e]);
+}
+void launch_split_df(const double* v, float* h, float* l, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ++g_launches;
+  split_df_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(v, h, l, n);
 }
 
 // lo[e] = fl32(a[e] - hi[e]) (hi = fl32(a))
@@ -1993,31 +2047,40 @@ __global__ void __launch_bounds__(256) mv_sym_sum_kernel(int D, int K, const int
   }
 }
 
-// FP32-pair form for the residual (see df_fma): A as hi + lo, x FP64,
-// partial products FP64.
+// FP32-pair form for the residual (see df_fma): A as hi + lo, x as FP32
+// pairs xh + xl, partial products FP64.  Every sum stays in FP32 pairs until
+// it is final: a row's lanes are added by df_tsum, the lane that keeps the
+// row (lane k keeps the row of pass k mod 16 and half k / 16) converts it to
+// FP64 after the last pass, and the column sums of A^T x_i are added over
+// the warps in pairs and converted once per column.
 template <int CH>
 __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t npu, const int32_t* __restrict__ ui,
                                                                 const int32_t* __restrict__ uj,
                                                                 const float* __restrict__ Ah,
                                                                 const float* __restrict__ Al,
-                                                                const double* __restrict__ x,
+                                                                const float* __restrict__ xh,
+                                                                const float* __restrict__ xl,
                                                                 double* __restrict__ part) {
   constexpr int RPW = 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* xah = reinterpret_cast<float*>(smraw);  // D
   float* xal = xah + D;                          // D
-  double* wp = reinterpret_cast<double*>(xal + D);  // 8 * D (D a multiple of 128: 8-byte aligned)
+  float* wph = xal + D;                          // 8 * D column partials (high parts)
+  float* wpl = wph + 8 * D;                      // 8 * D (low parts)
   const int64_t k = blockIdx.x;
   const int a = ui[k], b = uj[k], tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool both = a != b;
   const float* Mh = Ah + k * D * D;
   const float* Ml = Al + k * D * D;
-  for (int e = tid; e < D; e += blockDim.x) df_split(x[(int64_t)a * D + e], xah[e], xal[e]);
+  for (int e = tid; e < D; e += blockDim.x) xah[e] = xh[(int64_t)a * D + e], xal[e] = xl[(int64_t)a * D + e];
   float xbh[CH][4], xbl[CH][4];
 #pragma unroll
-  for (int h = 0; h < CH; ++h)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) df_split(x[(int64_t)b * D + lane * 4 + 128 * h + e], xbh[h][e], xbl[h][e]);
+  for (int h = 0; h < CH; ++h) {
+    const float4 vh = *reinterpret_cast<const float4*>(xh + (int64_t)b * D + lane * 4 + 128 * h);
+    const float4 vl = *reinterpret_cast<const float4*>(xl + (int64_t)b * D + lane * 4 + 128 * h);
+    xbh[h][0] = vh.x, xbh[h][1] = vh.y, xbh[h][2] = vh.z, xbh[h][3] = vh.w;
+    xbl[h][0] = vl.x, xbl[h][1] = vl.y, xbl[h][2] = vl.z, xbl[h][3] = vl.w;
+  }
   float wH[CH][4], wL[CH][4];
 #pragma unroll
   for (int h = 0; h < CH; ++h)
@@ -2041,14 +2104,15 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
   };
   float4 nh[RPW][CH], nl[RPW][CH];
   load_rows(warp, nh, nl);
-  for (int r0 = warp; r0 < D; r0 += 8 * RPW) {
+  float keep_h = 0.0f, keep_l = 0.0f;  // the row this lane converts at the end
+  for (int r0 = warp, it = 0; r0 < D; r0 += 8 * RPW, ++it) {
     float4 vh[RPW][CH], vl[RPW][CH];
 #pragma unroll
     for (int t = 0; t < RPW; ++t)
 #pragma unroll
       for (int h = 0; h < CH; ++h) vh[t][h] = nh[t][h], vl[t][h] = nl[t][h];
     if (r0 + 8 * RPW < D) load_rows(r0 + 8 * RPW, nh, nl);
-    double su[RPW];
+    float rh[RPW], rl[RPW];
 #pragma unroll
     for (int t = 0; t < RPW; ++t) {
       const int r = r0 + 8 * t;
@@ -2064,25 +2128,30 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
           if (both) df_fma(wH[h][e], wL[h][e], mh[e], ml[e], xrh, xrl);
         }
       }
-      su[t] = (double)H + (double)L;
+      rh[t] = H, rl[t] = L;
     }
-    {
-      const double sv = tsum<RPW, 32, double>(su);
-      const int r = r0 + 8 * tsum_index<RPW, 32>(lane);
-      if (tsum_leader<RPW, 32>(lane) && r < D) u[r] = sv;
-    }
+    float sh, sl;
+    df_tsum<RPW, 32>(rh, rl, sh, sl);  // lanes 0-15: row r0, lanes 16-31: row r0 + 8
+    if ((lane & 15) == it) keep_h = sh, keep_l = sl;
+  }
+  {
+    const int r = warp + 8 * RPW * (lane & 15) + 8 * (lane >> 4);
+    if (r < D) u[r] = (double)keep_h + (double)keep_l;
   }
   if (!both) return;
 #pragma unroll
   for (int h = 0; h < CH; ++h)
 #pragma unroll
-    for (int e = 0; e < 4; ++e) wp[warp * D + lane * 4 + 128 * h + e] = (double)wH[h][e] + (double)wL[h][e];
+    for (int e = 0; e < 4; ++e) {
+      wph[warp * D + lane * 4 + 128 * h + e] = wH[h][e];
+      wpl[warp * D + lane * 4 + 128 * h + e] = wL[h][e];
+    }
   __syncthreads();
   for (int c = tid; c < D; c += blockDim.x) {
-    double s = 0.0;
+    float H = wph[c], L = wpl[c];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) s += wp[w * D + c];
-    u[D + c] = s;
+    for (int w = 1; w < 8; ++w) df_add(H, L, wph[w * D + c], wpl[w * D + c]);
+    u[D + c] = (double)H + (double)L;
   }
 }
 
@@ -2112,19 +2181,19 @@ void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_
 }
 template <int CH>
 static void launch_sym_pairs_df_ch(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
-                                   const float* Al, const double* x, double* part, cudaStream_t st) {
-  const size_t sm = sizeof(float) * 2 * (size_t)D + sizeof(double) * 8 * (size_t)D;
+                                   const float* Al, const float* xh, const float* xl, double* part, cudaStream_t st) {
+  const size_t sm = sizeof(float) * 18 * (size_t)D;
   set_smem((const void*)mv_sym_pair_df_kernel<CH>, sm);
   ++g_launches;
-  mv_sym_pair_df_kernel<CH><<<(unsigned)npu, 256, sm, st>>>(D, npu, ui, uj, Ah, Al, x, part);
+  mv_sym_pair_df_kernel<CH><<<(unsigned)npu, 256, sm, st>>>(D, npu, ui, uj, Ah, Al, xh, xl, part);
 }
 void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
-                                const float* Al, const double* x, double* part, cudaStream_t st) {
+                                const float* Al, const float* xh, const float* xl, double* part, cudaStream_t st) {
   if (npu <= 0) return;
   switch (D / 128) {
-    case 1: launch_sym_pairs_df_ch<1>(D, npu, ui, uj, Ah, Al, x, part, st); break;
-    case 2: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, x, part, st); break;
-    default: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, x, part, st); break;
+    case 1: launch_sym_pairs_df_ch<1>(D, npu, ui, uj, Ah, Al, xh, xl, part, st); break;
+    case 2: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, xh, xl, part, st); break;
+    default: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, xh, xl, part, st); break;
   }
 }
 template <typename T>
