@@ -2280,8 +2280,39 @@ void launch_residual(const double* b, const double* y, double* r, int64_t n, cud
 }
 // deterministic two-pass sum of squares (accumulated in FP64): 256 partials,
 // then one block
+// (a product a b added to the FP32 pair (H, L): a fused multiply-add splits
+// it exactly into p + e)
+__device__ __forceinline__ void df_acc(float& H, float& L, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  df_add(H, L, p, fmaf(a, b, -p));
+}
+// The block's FP32-pair partial (H, L) as one FP64 value, by thread 0: lanes
+// and warps are added in FP32 pairs (FP64 instructions are slow on GB300).
+__device__ __forceinline__ double block_df_total(float H, float L) {
+  __shared__ float bh[8], bl[8];
+  float rh[1] = {H}, rl[1] = {L}, sh, sl;
+  df_tsum<1, 32>(rh, rl, sh, sl);
+  if ((threadIdx.x & 31) == 0) bh[threadIdx.x >> 5] = sh, bl[threadIdx.x >> 5] = sl;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    float th = bh[0], tl = bl[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) df_add(th, tl, bh[w], bl[w]);
+    t = (double)th + (double)tl;
+  }
+  return t;
+}
+
 template <typename T>
 __global__ void norm2_part_kernel(const T* __restrict__ v, int64_t n, double* __restrict__ part) {
+  if constexpr (std::is_same<T, float>::value) {
+    float H = 0.0f, L = 0.0f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+      df_acc(H, L, v[e], v[e]);
+    const double t = block_df_total(H, L);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+    return;
+  }
   __shared__ double sb[8];
   double s = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -2322,16 +2353,30 @@ template void launch_norm2<float>(const float*, int64_t, double*, cudaStream_t);
 
 // out[e] = (To)(in[e] * scale), scale = 1/sqrt(nrm2[0]) (or sqrt(nrm2[0]) when
 // inverse == 0); nrm2 == NULL: plain conversion
+// (the scale is formed once per block: an FP64 square root and division per
+// thread would cost more than the copy on GB300; FP32 data are scaled in FP32)
 template <typename Ti, typename To>
 __global__ void scaled_copy_kernel(const Ti* __restrict__ in, const double* __restrict__ nrm2, int inverse,
                                    To* __restrict__ out, int64_t n) {
-  double s = 1.0;
-  if (nrm2) {
-    const double r = sqrt(nrm2[0]);
-    s = inverse ? (r > 0 ? 1.0 / r : 0.0) : r;
+  __shared__ double ss;
+  if (threadIdx.x == 0) {
+    double s = 1.0;
+    if (nrm2) {
+      const double r = sqrt(nrm2[0]);
+      s = inverse ? (r > 0 ? 1.0 / r : 0.0) : r;
+    }
+    ss = s;
   }
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    out[e] = (To)((double)in[e] * s);
+  __syncthreads();
+  const double s = ss;
+  if constexpr (std::is_same<Ti, float>::value && std::is_same<To, float>::value) {
+    const float sf = (float)s;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+      out[e] = in[e] * sf;
+  } else {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+      out[e] = (To)((double)in[e] * s);
+  }
 }
 template <typename Ti, typename To>
 void launch_scaled_copy(const Ti* in, const double* nrm2, bool inverse, To* out, int64_t n, cudaStream_t st) {
@@ -2346,14 +2391,20 @@ template void launch_scaled_copy<double, double>(const double*, const double*, b
 template <typename T>
 __global__ void scale_to_kernel(const double* __restrict__ in, const double* __restrict__ nrm2, T* __restrict__ out,
                                 int64_t n) {
-  const double s = nrm2[0] > 0 ? 1.0 / sqrt(nrm2[0]) : 1.0;
+  __shared__ double ss;
+  if (threadIdx.x == 0) ss = nrm2[0] > 0 ? 1.0 / sqrt(nrm2[0]) : 1.0;
+  __syncthreads();
+  const double s = ss;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (T)(in[e] * s);
 }
 template <typename T>
 __global__ void axpy_from_kernel(const T* __restrict__ d, const double* __restrict__ nrm2, double* __restrict__ x,
                                  int64_t n) {
-  const double s = nrm2[0] > 0 ? sqrt(nrm2[0]) : 1.0;
+  __shared__ double ss;
+  if (threadIdx.x == 0) ss = nrm2[0] > 0 ? sqrt(nrm2[0]) : 1.0;
+  __syncthreads();
+  const double s = ss;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     x[e] += s * (double)d[e];
 }
@@ -2372,9 +2423,17 @@ void launch_axpy_from(const T* d, const double* norm2, double* x, int64_t n, cud
 template <typename T>
 __global__ void multi_dot_part_kernel(const T* __restrict__ V, int64_t ldv, const T* __restrict__ w, int64_t n,
                                       double* __restrict__ part) {
-  __shared__ double sb[8];
   const int v = blockIdx.y;
   const T* Vv = V + (int64_t)v * ldv;
+  if constexpr (std::is_same<T, float>::value) {
+    float H = 0.0f, L = 0.0f;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+      df_acc(H, L, Vv[e], w[e]);
+    const double t = block_df_total(H, L);
+    if (threadIdx.x == 0) part[(int64_t)v * gridDim.x + blockIdx.x] = t;
+    return;
+  }
+  __shared__ double sb[8];
   double s = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
     s = fma((double)Vv[e], (double)w[e], s);
@@ -2422,11 +2481,38 @@ __global__ void multi_axpy_kernel(const T* __restrict__ V, int64_t ldv, int nv, 
     w[e] = (TW)((double)w[e] + sign * s);
   }
 }
+// The FP32 form (nv <= kAxpyPairs): the coefficients as FP32 pairs in shared
+// memory (split once per block), the combination in FP32-pair arithmetic,
+// w rounded to FP32 once.
+constexpr int kAxpyPairs = 128;
+__global__ void multi_axpy_f32_kernel(const float* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ coef,
+                                      float sign, float* __restrict__ w, int64_t n) {
+  __shared__ float ch[kAxpyPairs], cl[kAxpyPairs];
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) df_split(coef[v], ch[v], cl[v]);
+  __syncthreads();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    float H = 0.0f, L = 0.0f;
+    for (int v = 0; v < nv; ++v) {
+      const float x = V[(int64_t)v * ldv + e];
+      df_acc(H, L, ch[v], x);
+      L = fmaf(cl[v], x, L);
+    }
+    float wh = w[e], wl = 0.0f;
+    df_add(wh, wl, sign * H, sign * L);
+    w[e] = wh + wl;
+  }
+}
 template <typename T, typename TW>
 void launch_multi_axpy(const T* V, int64_t ldv, int nv, const double* coef, double sign, TW* w, int64_t n,
                        cudaStream_t st) {
   if (nv == 0) return;
   ++g_launches;
+  if constexpr (std::is_same<T, float>::value && std::is_same<TW, float>::value) {
+    if (nv <= kAxpyPairs) {
+      multi_axpy_f32_kernel<<<grid_for(n), 256, 0, st>>>(V, ldv, nv, coef, (float)sign, w, n);
+      return;
+    }
+  }
   multi_axpy_kernel<T, TW><<<grid_for(n), 256, 0, st>>>(V, ldv, nv, coef, sign, w, n);
 }
 template void launch_multi_dot<double>(const double*, int64_t, int, const double*, int64_t, double*, double*, bool,
