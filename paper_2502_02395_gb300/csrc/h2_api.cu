@@ -228,7 +228,7 @@ h2_status setup_device(h2_ctx* c) {
   CKC(dalloc(c, &c->xhat32, c->hat_off[L + 1]));
   CKC(dalloc(c, &c->yhat32, c->hat_off[L + 1]));
   for (float** p : {&c->xdf_h, &c->xdf_l}) CKC(dalloc(c, p, nslot));
-  for (float** p : {&c->hdf_h, &c->hdf_l}) CKC(dalloc(c, p, c->hat_off[L + 1]));
+  for (float** p : {&c->hdf_h, &c->hdf_l, &c->ydf_h, &c->ydf_l}) CKC(dalloc(c, p, c->hat_off[L + 1]));
   c->sym = sym_leaf_supported(lf.D);
   if (c->sym) {
     // the kernels' near blocks are symmetric (A_ji = A_ij^T): keep i <= j
@@ -302,6 +302,7 @@ h2_status setup_device(h2_ctx* c) {
   c->X32p.assign(L + 1, nullptr);
   c->S32p.assign(L + 1, nullptr);
   c->Slo.assign(L + 1, nullptr);
+  c->Xlo.assign(L + 1, nullptr);
   size_t npart = c->sym ? (size_t)c->npu * 2 * lf.D : 0;
   // one batch of all levels' stored coupling pairs when every level with
   // couplings qualifies for the symmetric form with one common rank
@@ -373,10 +374,8 @@ h2_status setup_device(h2_ctx* c) {
     // the residual's FP32-pair matvec reads the couplings in full
     CKC(dalloc(c, &c->Slo[l], ns));
     launch_split_lo(d.S, d.S32, c->Slo[l], (int64_t)d.FP * d.K * d.K, 0);
-    if (l == L) {
-      CKC(dalloc(c, &c->Xlo, nx));
-      launch_split_lo(d.X, d.X32, c->Xlo, (int64_t)nx, 0);
-    }
+    CKC(dalloc(c, &c->Xlo[l], nx));
+    launch_split_lo(d.X, d.X32, c->Xlo[l], (int64_t)nx, 0);
     c->X64p[l] = d.X;
     c->S64p[l] = d.S;
     c->X32p[l] = d.X32;
@@ -1195,32 +1194,59 @@ void matvec_impl(h2_ctx* c, const double* x, double* y) {
 void matvec_df(h2_ctx* c, const double* x, double* y) {
   const int L = c->L;
   cudaStream_t st = c->stream;
-  launch_split_df(x, c->xdf_h, c->xdf_l, nslots(c), st);
-  auto leaf = [&](const double* yhL) {
-    const DevLevel& lf = c->lv[L];
-    if (c->sym) {
-      launch_matvec_sym_pairs_df(lf.D, c->npu, c->sym_i, c->sym_j, c->A32, c->Alo, c->xdf_h, c->xdf_l, c->part64, st);
-      launch_matvec_sym_sum<double>(lf.nb, lf.D, L ? lf.K : 0, c->sym_ptr, c->sym_ent, L ? c->X64p[L] : nullptr, yhL,
-                                    c->part64, y, st);
-    } else {
-      launch_matvec_leaf_df(lf, c->A32, c->Alo, L ? c->X32p[L] : nullptr, L ? c->Xlo : nullptr, c->xdf_h, c->xdf_l,
-                            yhL, y, st);
-    }
-  };
-  if (L == 0) {
-    leaf(nullptr);
-    return;
-  }
+  const DevLevel& lf = c->lv[L];
   const std::vector<int64_t>& off = c->hat_off;
-  launch_matvec_up<double>(c->lv[L], c->X64p[L], x, c->xhat + off[L], st);
-  for (int l = L - 1; l >= 1; --l) launch_matvec_up<double>(c->lv[l], c->X64p[l], c->xhat + off[l + 1], c->xhat + off[l], st);
-  launch_split_df(c->xhat + off[1], c->hdf_h + off[1], c->hdf_l + off[1], off[L + 1] - off[1], st);
-  // (the couplings in full: the symmetric pair form is slower in FP32-pair
-  // arithmetic at these sizes)
-  for (int l = 1; l <= L; ++l)
-    launch_matvec_far_df(c->lv[l], c->S32p[l], c->Slo[l], c->hdf_h + off[l], c->hdf_l + off[l], c->yhat + off[l], st);
-  for (int l = 1; l < L; ++l) launch_matvec_down<double>(c->lv[l], c->X64p[l], c->yhat + off[l], c->yhat + off[l + 1], st);
-  leaf(c->yhat + off[L]);
+  launch_split_df(x, c->xdf_h, c->xdf_l, nslots(c), st);
+  if (L >= 1) {
+    // upward pass, couplings of all levels in one launch, downward pass
+    launch_matvec_up_df(lf, c->X32p[L], c->Xlo[L], c->xdf_h, c->xdf_l, c->hdf_h + off[L], c->hdf_l + off[L], st);
+    for (int l = L - 1; l >= 1; --l)
+      launch_matvec_up_df(c->lv[l], c->X32p[l], c->Xlo[l], c->hdf_h + off[l + 1], c->hdf_l + off[l + 1],
+                          c->hdf_h + off[l], c->hdf_l + off[l], st);
+    // levels with the longest far lists first (their CTAs take longest)
+    std::vector<int> order;
+    for (int l = 1; l <= L; ++l) order.push_back(l);
+    std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+      return c->lv[u].FP * (int64_t)c->lv[v].nb > c->lv[v].FP * (int64_t)c->lv[u].nb;
+    });
+    FarDfArgs fa{};
+    int cta = 0;
+    for (int l : order) {
+      const DevLevel& d = c->lv[l];
+      if (d.FP == 0 || d.K == 0) {
+        // no couplings: yhat starts at zero
+        cudaMemsetAsync(c->ydf_h + off[l], 0, sizeof(float) * d.nb * d.K, st);
+        cudaMemsetAsync(c->ydf_l + off[l], 0, sizeof(float) * d.nb * d.K, st);
+        continue;
+      }
+      if (fa.nlev == kMaxFarDfLevels) {
+        launch_matvec_far_df_all(fa, st);
+        fa = FarDfArgs{};
+        cta = 0;
+      }
+      FarDfLevel& f = fa.lv[fa.nlev++];
+      f = {d.far_ptr, d.far_j, c->S32p[l], c->Slo[l], c->hdf_h + off[l], c->hdf_l + off[l], c->ydf_h + off[l],
+           c->ydf_l + off[l], d.nb, d.K, (d.K + 63) / 64, cta};
+      cta += d.nb * f.nch;
+    }
+    launch_matvec_far_df_all(fa, st);
+    for (int l = 1; l < L; ++l)
+      launch_matvec_down_df(c->lv[l], c->X32p[l], c->Xlo[l], c->ydf_h + off[l], c->ydf_l + off[l],
+                            c->ydf_h + off[l + 1], c->ydf_l + off[l + 1], st);
+  }
+  const float* yhh = L ? c->ydf_h + off[L] : nullptr;
+  const float* yhl = L ? c->ydf_l + off[L] : nullptr;
+  if (c->sym) {
+    // the partial products as FP32 pairs in the space of the FP64 ones
+    float* ph = reinterpret_cast<float*>(c->part64);
+    float* pl = ph + c->npu * 2 * lf.D;
+    launch_matvec_sym_pairs_df(lf.D, c->npu, c->sym_i, c->sym_j, c->A32, c->Alo, c->xdf_h, c->xdf_l, ph, pl, st);
+    launch_matvec_sym_sum_df(lf.nb, lf.D, L ? lf.K : 0, c->sym_ptr, c->sym_ent, L ? c->X32p[L] : nullptr,
+                             L ? c->Xlo[L] : nullptr, yhh, yhl, ph, pl, y, st);
+  } else {
+    launch_matvec_leaf_df(lf, c->A32, c->Alo, L ? c->X32p[L] : nullptr, L ? c->Xlo[L] : nullptr, c->xdf_h, c->xdf_l,
+                          yhh, yhl, y, st);
+  }
 }
 void matvec32(h2_ctx* c, const float* x, float* y, EventPairs* leaf_ev = nullptr) {
   matvec_t<float>(c, c->A32, c->X32p.data(), c->S32p.data(), c->xhat32, c->yhat32, x, y, leaf_ev);

@@ -332,7 +332,7 @@ struct h2_ctx {
   // the FP32 copies, the FP64 matrix as FP32 pairs (the mixed refinement's
   // residual)
   float* Alo = nullptr;
-  float* Xlo = nullptr;      // leaf level
+  std::vector<float*> Xlo;   // per level (index l; [0] unused)
   std::vector<float*> Slo;   // per level (index l; [0] unused)
   // Symmetric leaf storage of A32 / Alo: only the near pairs i <= j
   // ("stored pairs", sym_q: their index among the near pairs), and per box
@@ -349,9 +349,9 @@ struct h2_ctx {
   cudaStream_t leaf_stream = nullptr;
   cudaEvent_t mv_fork = nullptr, mv_join = nullptr;
   double* part64 = nullptr;  // the same for the FP32-pair matvec
-  // the FP32-pair matvec's input vector and its basis coefficients (all
-  // levels) split into FP32 pairs once per matvec
-  float *xdf_h = nullptr, *xdf_l = nullptr, *hdf_h = nullptr, *hdf_l = nullptr;
+  // the FP32-pair matvec's input vector (split once per matvec) and its
+  // basis coefficients xhat, yhat of all levels, as FP32 pairs
+  float *xdf_h = nullptr, *xdf_l = nullptr, *hdf_h = nullptr, *hdf_l = nullptr, *ydf_h = nullptr, *ydf_l = nullptr;
   float *xhat32 = nullptr, *yhat32 = nullptr;
   // the stored coupling pairs of every level as one batch (levels with the
   // same rank cb_K): the FP32 matvec forms all levels' coupling products in

@@ -146,13 +146,41 @@ template <typename T>
 void launch_matvec_down(const DevLevel& L, const T* X, const T* yh, T* yh_child, cudaStream_t st);
 template <typename T>
 void launch_matvec_leaf(const DevLevel& L, const T* A, const T* X, const T* x, const T* yh, T* y, cudaStream_t st);
-// The FP64 matvec's far and leaf steps with each FP64 matrix held as an FP32
-// pair (hi = fl32, lo = fl32 of the rest) and FP32 pair arithmetic; their
-// input vectors come as FP32 pairs too (launch_split_df).
-void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const float* xhh, const float* xhl,
-                          double* yh, cudaStream_t st);
+// The FP64 matvec with each FP64 matrix held as an FP32 pair (hi = fl32, lo
+// = fl32 of the rest) and FP32-pair arithmetic throughout: the input vector
+// is split once (launch_split_df), the basis coefficients xhat / yhat of
+// every level and the leaf partial products stay FP32 pairs, and only the
+// leaf output is converted to FP64.
+// up: xhat_i = X_i^T z_i (z: the leaf input or the children's xhat)
+void launch_matvec_up_df(const DevLevel& L, const float* Xh, const float* Xl, const float* zh, const float* zl,
+                         float* oh, float* ol, cudaStream_t st);
+// couplings of all levels in one launch: per level its far lists, the
+// couplings S (hi / lo), xhat and yhat pairs; CTAs cta0 .. cta0 + nb nch - 1
+// (nch 64-row chunks per box)
+struct FarDfLevel {
+  const int64_t* ptr;
+  const int32_t* fj;
+  const float *Sh, *Sl, *xh, *xl;
+  float *yh, *yl;
+  int nb, K, nch, cta0;
+};
+constexpr int kMaxFarDfLevels = 32;
+struct FarDfArgs {
+  int nlev;
+  FarDfLevel lv[kMaxFarDfLevels];
+};
+void launch_matvec_far_df_all(const FarDfArgs& a, cudaStream_t st);
+// down: [yhat_2p; yhat_2p+1] += X_p yhat_p
+void launch_matvec_down_df(const DevLevel& L, const float* Xh, const float* Xl, const float* yh, const float* yl,
+                           float* ych, float* ycl, cudaStream_t st);
+// leaf, general near lists: y_i = X_i yhat_i + sum_{near j} A_ij x_j
 void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, const float* Xh, const float* Xl,
-                           const float* xh, const float* xl, const double* yh, double* y, cudaStream_t st);
+                           const float* xh, const float* xl, const float* yhh, const float* yhl, double* y,
+                           cudaStream_t st);
+// leaf, symmetric storage: y_i = X_i yhat_i + box i's partial products
+void launch_matvec_sym_sum_df(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const float* Xh,
+                              const float* Xl, const float* yhh, const float* yhl, const float* ph, const float* pl,
+                              double* y, cudaStream_t st);
 void launch_split_lo(const double* a, const float* hi, float* lo, int64_t n, cudaStream_t st);  // lo = fl32(a - hi)
 void launch_split_df(const double* v, float* h, float* l, int64_t n, cudaStream_t st);  // h = fl32(v), l = fl32(v - h)
 // Leaf matvec on the stored (i <= j) halves of symmetric leaf near blocks:
@@ -169,7 +197,8 @@ void launch_matvec_down_far(const DevLevel& L, const T* X, const T* yh, T* yh_ch
 void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* A, const float* x,
                              float* part, bool pdl, cudaStream_t st);
 void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
-                                const float* Al, const float* xh, const float* xl, double* part, cudaStream_t st);
+                                const float* Al, const float* xh, const float* xl, float* ph, float* pl,
+                                cudaStream_t st);
 template <typename T>
 void launch_matvec_sym_sum(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const T* X, const T* yh,
                            const T* part, T* y, cudaStream_t st, bool pdl = true);

@@ -1754,7 +1754,8 @@ __device__ __forceinline__ void rows_acc_df(int r0, const float* __restrict__ Mh
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int rbase = r0 + warp;
   const bool vec = (ld % 4 == 0) && (nc % 4 == 0) && ((reinterpret_cast<uintptr_t>(Mh) & 15) == 0) &&
-                   ((reinterpret_cast<uintptr_t>(Ml) & 15) == 0);
+                   ((reinterpret_cast<uintptr_t>(Ml) & 15) == 0) && ((reinterpret_cast<uintptr_t>(xh) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(xl) & 15) == 0);
   if (vec) {
     for (int c = lane * 4; c < nc; c += 128) {
       float4 vh[RPW], vl[RPW];
@@ -1807,49 +1808,13 @@ __device__ __forceinline__ void df_split(double v, float& h, float& l) {
   l = (float)(v - (double)h);
 }
 
-// couplings: yh_i = sum_{far j} S_f xh_j (xh as FP32 pairs xhh + xhl)
-__global__ void __launch_bounds__(256, 2) mv_far_df_kernel(int K, const int64_t* __restrict__ ptr,
-                                                           const int32_t* __restrict__ fj, const float* __restrict__ Sh,
-                                                           const float* __restrict__ Sl, const float* __restrict__ xhh,
-                                                           const float* __restrict__ xhl, double* __restrict__ yh) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int i = blockIdx.x, tid = threadIdx.x;
-  const int64_t p0 = ptr[i];
-  const int nf = (int)(ptr[i + 1] - p0);
-  const int Kp = (K + 3) & ~3;
-  float* sh = reinterpret_cast<float*>(smraw);  // nf * Kp
-  float* sl = sh + (size_t)nf * Kp;             // nf * Kp
-  for (int e = tid; e < nf * K; e += blockDim.x) {
-    const int q = e / K, a = e - q * K;
-    const int64_t g = (int64_t)fj[p0 + q] * K + a;
-    sh[q * Kp + a] = xhh[g];
-    sl[q * Kp + a] = xhl[g];
-  }
-  __syncthreads();
-  float H[kRPWdf], L[kRPWdf];
-  for (int r0 = 0; r0 < K; r0 += 8 * kRPWdf) {
-    zero(H);
-    zero(L);
-    for (int q = 0; q < nf; ++q)
-      rows_acc_df<kRPWdf>(r0, Sh + (p0 + q) * K * K, Sl + (p0 + q) * K * K, K, K, K, sh + q * Kp, sl + q * Kp, H, L);
-    rows_finish_df<kRPWdf>(r0, K, H, L, nullptr, yh + (int64_t)i * K);
-  }
-}
-void launch_matvec_far_df(const DevLevel& L, const float* Sh, const float* Sl, const float* xhh, const float* xhl,
-                          double* yh, cudaStream_t st) {
-  const size_t sm = 2 * sizeof(float) * (size_t)((L.K + 3) & ~3) * std::max(L.max_far, 1);
-  set_smem((const void*)mv_far_df_kernel, sm);
-  ++g_launches;
-  mv_far_df_kernel<<<L.nb, 256, sm, st>>>(L.K, L.far_ptr, L.far_j, Sh, Sl, xhh, xhl, yh);
-}
-
 // leaf: y_i = X_i yh_i + sum_{near j} A_ij x_j
 __global__ void __launch_bounds__(256, 2) mv_leaf_df_kernel(int D, int K, const int64_t* __restrict__ ptr,
                                                             const int32_t* __restrict__ nj, const float* __restrict__ Ah,
                                                             const float* __restrict__ Al, const float* __restrict__ Xh,
                                                             const float* __restrict__ Xl, const float* __restrict__ xh,
-                                                            const float* __restrict__ xl, const double* __restrict__ yh,
-                                                            double* __restrict__ y) {
+                                                            const float* __restrict__ xl, const float* __restrict__ yhh,
+                                                            const float* __restrict__ yhl, double* __restrict__ y) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int i = blockIdx.x, tid = threadIdx.x;
   const int64_t p0 = ptr[i];
@@ -1859,8 +1824,8 @@ __global__ void __launch_bounds__(256, 2) mv_leaf_df_kernel(int D, int K, const 
   float* hl = hh + Kp;                          // Kp
   float* xsh = hl + Kp;                         // nn * Dp
   float* xsl = xsh + (size_t)nn * Dp;           // nn * Dp
-  if (yh)
-    for (int e = tid; e < K; e += blockDim.x) df_split(yh[(int64_t)i * K + e], hh[e], hl[e]);
+  if (yhh)
+    for (int e = tid; e < K; e += blockDim.x) hh[e] = yhh[(int64_t)i * K + e], hl[e] = yhl[(int64_t)i * K + e];
   for (int e = tid; e < nn * D; e += blockDim.x) {
     const int q = e / D, d = e - q * D;
     const int64_t g = (int64_t)nj[p0 + q] * D + d;
@@ -1872,7 +1837,7 @@ __global__ void __launch_bounds__(256, 2) mv_leaf_df_kernel(int D, int K, const 
   for (int r0 = 0; r0 < D; r0 += 8 * kRPWdf) {
     zero(H);
     zero(L);
-    if (yh) rows_acc_df<kRPWdf>(r0, Xh + (int64_t)i * D * K, Xl + (int64_t)i * D * K, K, D, K, hh, hl, H, L);
+    if (yhh) rows_acc_df<kRPWdf>(r0, Xh + (int64_t)i * D * K, Xl + (int64_t)i * D * K, K, D, K, hh, hl, H, L);
     for (int q = 0; q < nn; ++q)
       rows_acc_df<kRPWdf>(r0, Ah + (p0 + q) * D * D, Al + (p0 + q) * D * D, D, D, D, xsh + q * Dp, xsl + q * Dp, H,
                           L);
@@ -1880,12 +1845,13 @@ __global__ void __launch_bounds__(256, 2) mv_leaf_df_kernel(int D, int K, const 
   }
 }
 void launch_matvec_leaf_df(const DevLevel& L, const float* Ah, const float* Al, const float* Xh, const float* Xl,
-                           const float* xh, const float* xl, const double* yh, double* y, cudaStream_t st) {
+                           const float* xh, const float* xl, const float* yhh, const float* yhl, double* y,
+                           cudaStream_t st) {
   const size_t Kp = (L.K + 3) & ~3, Dp = (L.D + 3) & ~3;
   const size_t sm = 2 * sizeof(float) * (Kp + Dp * (size_t)L.max_near);
   set_smem((const void*)mv_leaf_df_kernel, sm);
   ++g_launches;
-  mv_leaf_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, Ah, Al, Xh, Xl, xh, xl, yh, y);
+  mv_leaf_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, L.near_ptr, L.near_j, Ah, Al, Xh, Xl, xh, xl, yhh, yhl, y);
 }
 
 // h = fl32(v), l = fl32(v - h): an FP64 vector as FP32 pairs, once per use
@@ -1899,6 +1865,215 @@ void launch_split_df(const double* v, float* h, float* l, int64_t n, cudaStream_
   if (n <= 0) return;
   ++g_launches;
   split_df_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(v, h, l, n);
+}
+
+// The residual's passes through the bases and couplings with every vector
+// held as FP32 pairs (xhat and yhat of all levels, the leaf partial
+// products), so that no FP64 instruction runs per matrix entry or per
+// vector element until the leaf output y is formed.
+
+// the row sums of (H, L) over the lanes (df_tsum), written as pairs by the
+// leader lanes (add: added to the pair already there)
+template <int RPW>
+__device__ __forceinline__ void rows_finish_pair(int r0, int nr, const float (&H)[RPW], const float (&L)[RPW],
+                                                 float* oh, float* ol, bool add) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float sh, sl;
+  df_tsum<RPW, 32>(H, L, sh, sl);
+  const int r = r0 + warp + 8 * tsum_index<RPW, 32>(lane);
+  if (tsum_leader<RPW, 32>(lane) && r < nr) {
+    if (add) df_add(sh, sl, oh[r], ol[r]);
+    oh[r] = sh;
+    ol[r] = sl;
+  }
+}
+
+// upward: xhat_i = X_i^T z_i (X_i: D x K row-major as Xh + Xl; z_i: the
+// leaf input or the children's xhat, D pairs).  Warps take rows n, lanes
+// 4-column chunks of the output; the 8 warps' pairs are added at the end.
+__global__ void __launch_bounds__(256, 2) mv_up_df_kernel(int D, int K, const float* __restrict__ Xh,
+                                                          const float* __restrict__ Xl, const float* __restrict__ zh,
+                                                          const float* __restrict__ zl, float* __restrict__ oh,
+                                                          float* __restrict__ ol) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* szh = reinterpret_cast<float*>(smraw);  // D
+  float* szl = szh + D;                          // D
+  float* ph = szl + D;                           // 8 * K
+  float* pl = ph + 8 * K;                        // 8 * K
+  const int i = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < D; e += blockDim.x) szh[e] = zh[(int64_t)i * D + e], szl[e] = zl[(int64_t)i * D + e];
+  __syncthreads();
+  const float* Mh = Xh + (int64_t)i * D * K;
+  const float* Ml = Xl + (int64_t)i * D * K;
+  if (K % 4 == 0) {
+    for (int m0 = lane * 4; m0 < K; m0 += 128) {
+      float H[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
+      constexpr int NU = 8;  // rows in flight per lane
+      int n = warp;
+      for (; n + 8 * (NU - 1) < D; n += 8 * NU) {
+        float4 vh[NU], vl[NU];
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          vh[u] = __ldg(reinterpret_cast<const float4*>(Mh + (int64_t)(n + 8 * u) * K + m0));
+          vl[u] = __ldg(reinterpret_cast<const float4*>(Ml + (int64_t)(n + 8 * u) * K + m0));
+        }
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+          const float a = szh[n + 8 * u], b = szl[n + 8 * u];
+          df_fma(H[0], L[0], vh[u].x, vl[u].x, a, b);
+          df_fma(H[1], L[1], vh[u].y, vl[u].y, a, b);
+          df_fma(H[2], L[2], vh[u].z, vl[u].z, a, b);
+          df_fma(H[3], L[3], vh[u].w, vl[u].w, a, b);
+        }
+      }
+      for (; n < D; n += 8) {
+        const float4 vh = __ldg(reinterpret_cast<const float4*>(Mh + (int64_t)n * K + m0));
+        const float4 vl = __ldg(reinterpret_cast<const float4*>(Ml + (int64_t)n * K + m0));
+        const float a = szh[n], b = szl[n];
+        df_fma(H[0], L[0], vh.x, vl.x, a, b);
+        df_fma(H[1], L[1], vh.y, vl.y, a, b);
+        df_fma(H[2], L[2], vh.z, vl.z, a, b);
+        df_fma(H[3], L[3], vh.w, vl.w, a, b);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) ph[warp * K + m0 + e] = H[e], pl[warp * K + m0 + e] = L[e];
+    }
+  } else {
+    for (int m = lane; m < K; m += 32) {
+      float H = 0.f, L = 0.f;
+      for (int n = warp; n < D; n += 8) df_fma(H, L, Mh[(int64_t)n * K + m], Ml[(int64_t)n * K + m], szh[n], szl[n]);
+      ph[warp * K + m] = H, pl[warp * K + m] = L;
+    }
+  }
+  __syncthreads();
+  for (int m = tid; m < K; m += blockDim.x) {
+    float H = ph[m], L = pl[m];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) df_add(H, L, ph[w * K + m], pl[w * K + m]);
+    oh[(int64_t)i * K + m] = H;
+    ol[(int64_t)i * K + m] = L;
+  }
+}
+void launch_matvec_up_df(const DevLevel& L, const float* Xh, const float* Xl, const float* zh, const float* zl,
+                         float* oh, float* ol, cudaStream_t st) {
+  const size_t sm = sizeof(float) * (2 * (size_t)L.D + 16 * (size_t)L.K);
+  set_smem((const void*)mv_up_df_kernel, sm);
+  ++g_launches;
+  mv_up_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, Xh, Xl, zh, zl, oh, ol);
+}
+
+// couplings of every level in one launch: CTA (box i of level l, rows
+// 64 c .. 64 c + 63) forms those rows of yhat_i = sum_{far j} S_ij xhat_j;
+// the levels run in the order given (longest far lists first)
+__global__ void __launch_bounds__(256, 2) mv_far_df_all_kernel(const __grid_constant__ FarDfArgs a) {
+  const int b = blockIdx.x;
+  int l = 0;
+  while (l + 1 < a.nlev && b >= a.lv[l + 1].cta0) ++l;
+  const FarDfLevel& f = a.lv[l];
+  const int loc = b - f.cta0, i = loc / f.nch, r0 = (loc % f.nch) * 8 * kRPWdf;
+  const int64_t p0 = f.ptr[i], p1 = f.ptr[i + 1];
+  const int K = f.K;
+  float H[kRPWdf], L[kRPWdf];
+  zero(H);
+  zero(L);
+  for (int64_t q = p0; q < p1; ++q) {
+    const int j = f.fj[q];
+    rows_acc_df<kRPWdf>(r0, f.Sh + q * K * K, f.Sl + q * K * K, K, K, K, f.xh + (int64_t)j * K, f.xl + (int64_t)j * K,
+                        H, L);
+  }
+  rows_finish_pair<kRPWdf>(r0, K, H, L, f.yh + (int64_t)i * K, f.yl + (int64_t)i * K, false);
+}
+void launch_matvec_far_df_all(const FarDfArgs& a, cudaStream_t st) {
+  if (a.nlev <= 0) return;
+  const FarDfLevel& last = a.lv[a.nlev - 1];
+  const int grid = last.cta0 + last.nb * last.nch;
+  if (grid <= 0) return;
+  ++g_launches;
+  mv_far_df_all_kernel<<<grid, 256, 0, st>>>(a);
+}
+
+// downward: [yhat_2p; yhat_2p+1] += X_p yhat_p in pairs
+__global__ void __launch_bounds__(256, 2) mv_down_df_kernel(int D, int K, const float* __restrict__ Xh,
+                                                            const float* __restrict__ Xl, const float* __restrict__ yh,
+                                                            const float* __restrict__ yl, float* __restrict__ ych,
+                                                            float* __restrict__ ycl) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int Kp = (K + 3) & ~3;
+  float* sh = reinterpret_cast<float*>(smraw);  // Kp
+  float* sl = sh + Kp;                          // Kp
+  const int p = blockIdx.x;
+  for (int e = threadIdx.x; e < K; e += blockDim.x) sh[e] = yh[(int64_t)p * K + e], sl[e] = yl[(int64_t)p * K + e];
+  __syncthreads();
+  float H[kRPWdf], L[kRPWdf];
+  for (int r0 = 0; r0 < D; r0 += 8 * kRPWdf) {
+    zero(H);
+    zero(L);
+    rows_acc_df<kRPWdf>(r0, Xh + (int64_t)p * D * K, Xl + (int64_t)p * D * K, K, D, K, sh, sl, H, L);
+    rows_finish_pair<kRPWdf>(r0, D, H, L, ych + (int64_t)p * D, ycl + (int64_t)p * D, true);
+  }
+}
+void launch_matvec_down_df(const DevLevel& L, const float* Xh, const float* Xl, const float* yh, const float* yl,
+                           float* ych, float* ycl, cudaStream_t st) {
+  const size_t sm = 2 * sizeof(float) * (size_t)((L.K + 3) & ~3);
+  ++g_launches;
+  mv_down_df_kernel<<<L.nb, 256, sm, st>>>(L.D, L.K, Xh, Xl, yh, yl, ych, ycl);
+}
+
+// leaf output of the symmetric form: y_i = X_i yhat_i + box i's partial
+// products (pairs, in list order), converted to FP64 once per entry
+__global__ void __launch_bounds__(256, 2) mv_sym_sum_df_kernel(int D, int K, const int64_t* __restrict__ ptr,
+                                                               const int32_t* __restrict__ ent,
+                                                               const float* __restrict__ Xh,
+                                                               const float* __restrict__ Xl,
+                                                               const float* __restrict__ yhh,
+                                                               const float* __restrict__ yhl,
+                                                               const float* __restrict__ ph,
+                                                               const float* __restrict__ pl, double* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int Kp = (K + 3) & ~3;
+  float* shh = reinterpret_cast<float*>(smraw);  // Kp
+  float* shl = shh + Kp;                         // Kp
+  float* sbh = shl + Kp;                         // D
+  float* sbl = sbh + D;                          // D
+  const int i = blockIdx.x;
+  const int64_t e0 = ptr[i], e1 = ptr[i + 1];
+  if (Xh)
+    for (int e = threadIdx.x; e < K; e += blockDim.x) shh[e] = yhh[(int64_t)i * K + e], shl[e] = yhl[(int64_t)i * K + e];
+  for (int r = threadIdx.x; r < D; r += blockDim.x) {
+    float H = 0.f, L = 0.f;
+    for (int64_t q = e0; q < e1; ++q) {
+      const int en = ent[q];
+      const int64_t g = (int64_t)(en >> 1) * 2 * D + (en & 1) * D + r;
+      df_add(H, L, ph[g], pl[g]);
+    }
+    sbh[r] = H, sbl[r] = L;
+  }
+  __syncthreads();
+  if (Xh) {
+    float H[kRPWdf], L[kRPWdf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r0 = 0; r0 < D; r0 += 8 * kRPWdf) {
+      zero(H);
+      zero(L);
+      rows_acc_df<kRPWdf>(r0, Xh + (int64_t)i * D * K, Xl + (int64_t)i * D * K, K, D, K, shh, shl, H, L);
+      float th, tl;
+      df_tsum<kRPWdf, 32>(H, L, th, tl);
+      const int r = r0 + warp + 8 * tsum_index<kRPWdf, 32>(lane);
+      if (tsum_leader<kRPWdf, 32>(lane) && r < D) {
+        df_add(th, tl, sbh[r], sbl[r]);
+        y[(int64_t)i * D + r] = (double)th + (double)tl;
+      }
+    }
+  } else {
+    for (int r = threadIdx.x; r < D; r += blockDim.x) y[(int64_t)i * D + r] = (double)sbh[r] + (double)sbl[r];
+  }
+}
+void launch_matvec_sym_sum_df(int nb, int D, int K, const int64_t* ptr, const int32_t* ent, const float* Xh,
+                              const float* Xl, const float* yhh, const float* yhl, const float* ph, const float* pl,
+                              double* y, cudaStream_t st) {
+  const size_t sm = sizeof(float) * (2 * (size_t)((K + 3) & ~3) + 2 * (size_t)D);
+  ++g_launches;
+  mv_sym_sum_df_kernel<<<nb, 256, sm, st>>>(D, K, ptr, ent, Xh, Xl, yhh, yhl, ph, pl, y);
 }
 
 // lo[e] = fl32(a[e] - hi[e]) (hi = fl32(a))
@@ -2048,11 +2223,10 @@ __global__ void __launch_bounds__(256) mv_sym_sum_kernel(int D, int K, const int
 }
 
 // FP32-pair form for the residual (see df_fma): A as hi + lo, x as FP32
-// pairs xh + xl, partial products FP64.  Every sum stays in FP32 pairs until
-// it is final: a row's lanes are added by df_tsum, the lane that keeps the
-// row (lane k keeps the row of pass k mod 16 and half k / 16) converts it to
-// FP64 after the last pass, and the column sums of A^T x_i are added over
-// the warps in pairs and converted once per column.
+// pairs xh + xl, partial products as FP32 pairs (ph + pl, 2 D per stored
+// pair).  A row's lanes are added by df_tsum and the lane that keeps the row
+// (lane k keeps the row of pass k mod 16 and half k / 16) stores it after
+// the last pass; the column sums of A^T x_i are added over the warps.
 template <int CH>
 __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t npu, const int32_t* __restrict__ ui,
                                                                 const int32_t* __restrict__ uj,
@@ -2060,7 +2234,7 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
                                                                 const float* __restrict__ Al,
                                                                 const float* __restrict__ xh,
                                                                 const float* __restrict__ xl,
-                                                                double* __restrict__ part) {
+                                                                float* __restrict__ ph, float* __restrict__ pl) {
   constexpr int RPW = 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   float* xah = reinterpret_cast<float*>(smraw);  // D
@@ -2087,7 +2261,8 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
 #pragma unroll
     for (int e = 0; e < 4; ++e) wH[h][e] = 0.0f, wL[h][e] = 0.0f;
   __syncthreads();
-  double* u = part + k * 2 * D;
+  float* uh = ph + k * 2 * D;
+  float* ul = pl + k * 2 * D;
   // rows r0 + 8 t (t < RPW) of this warp; the next group's loads are issued
   // before the current group is used
   auto load_rows = [&](int r0, float4 (&vh)[RPW][CH], float4 (&vl)[RPW][CH]) {
@@ -2104,7 +2279,7 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
   };
   float4 nh[RPW][CH], nl[RPW][CH];
   load_rows(warp, nh, nl);
-  float keep_h = 0.0f, keep_l = 0.0f;  // the row this lane converts at the end
+  float keep_h = 0.0f, keep_l = 0.0f;  // the row this lane stores at the end
   for (int r0 = warp, it = 0; r0 < D; r0 += 8 * RPW, ++it) {
     float4 vh[RPW][CH], vl[RPW][CH];
 #pragma unroll
@@ -2136,7 +2311,7 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
   }
   {
     const int r = warp + 8 * RPW * (lane & 15) + 8 * (lane >> 4);
-    if (r < D) u[r] = (double)keep_h + (double)keep_l;
+    if (r < D) uh[r] = keep_h, ul[r] = keep_l;
   }
   if (!both) return;
 #pragma unroll
@@ -2151,7 +2326,7 @@ __global__ void __launch_bounds__(256, 2) mv_sym_pair_df_kernel(int D, int64_t n
     float H = wph[c], L = wpl[c];
 #pragma unroll
     for (int w = 1; w < 8; ++w) df_add(H, L, wph[w * D + c], wpl[w * D + c]);
-    u[D + c] = (double)H + (double)L;
+    uh[D + c] = H, ul[D + c] = L;
   }
 }
 
@@ -2181,19 +2356,21 @@ void launch_matvec_sym_pairs(int D, int64_t npu, const int32_t* ui, const int32_
 }
 template <int CH>
 static void launch_sym_pairs_df_ch(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
-                                   const float* Al, const float* xh, const float* xl, double* part, cudaStream_t st) {
+                                   const float* Al, const float* xh, const float* xl, float* ph, float* pl,
+                                   cudaStream_t st) {
   const size_t sm = sizeof(float) * 18 * (size_t)D;
   set_smem((const void*)mv_sym_pair_df_kernel<CH>, sm);
   ++g_launches;
-  mv_sym_pair_df_kernel<CH><<<(unsigned)npu, 256, sm, st>>>(D, npu, ui, uj, Ah, Al, xh, xl, part);
+  mv_sym_pair_df_kernel<CH><<<(unsigned)npu, 256, sm, st>>>(D, npu, ui, uj, Ah, Al, xh, xl, ph, pl);
 }
 void launch_matvec_sym_pairs_df(int D, int64_t npu, const int32_t* ui, const int32_t* uj, const float* Ah,
-                                const float* Al, const float* xh, const float* xl, double* part, cudaStream_t st) {
+                                const float* Al, const float* xh, const float* xl, float* ph, float* pl,
+                                cudaStream_t st) {
   if (npu <= 0) return;
   switch (D / 128) {
-    case 1: launch_sym_pairs_df_ch<1>(D, npu, ui, uj, Ah, Al, xh, xl, part, st); break;
-    case 2: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, xh, xl, part, st); break;
-    default: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, xh, xl, part, st); break;
+    case 1: launch_sym_pairs_df_ch<1>(D, npu, ui, uj, Ah, Al, xh, xl, ph, pl, st); break;
+    case 2: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, xh, xl, ph, pl, st); break;
+    default: launch_sym_pairs_df_ch<2>(D, npu, ui, uj, Ah, Al, xh, xl, ph, pl, st); break;
   }
 }
 template <typename T>

@@ -245,9 +245,11 @@ def test_fp32_matvec_elementwise(B, name):
 def test_fp32_pair_residual_elementwise(B, name):
     """The mixed refinement's residual matvec (FP32-pair arithmetic) against
     the oracle's FP64 matvec: |y - y_ref|_i <= 2^-46 s_i (the pair
-    arithmetic's error per product sum; measured at most 0.09 2^-46, which
+    arithmetic's error per product sum; measured at most 0.16 2^-46, which
     includes the FP64 evaluation's own rounding); on a refined solution the
-    residuals b - A_H2 x agree to 1e-14 ||b|| in norm (measured 4e-15)."""
+    residuals b - A_H2 x agree to 5e-14 ||b|| in norm, 2000 times below the
+    1e-10 stopping threshold the residual decides (measured 1.2e-14, with
+    the bases, couplings and leaf sums in FP32 pairs as well)."""
     from oracle import ulv
     H, F, flat, b = oracle_case(name)
     S = solver(B, name)
@@ -267,7 +269,7 @@ def test_fp32_pair_residual_elementwise(B, name):
     r_ref = b - ulv.matvec(H, xs)
     d = np.linalg.norm(r_df - r_ref) / np.linalg.norm(b)
     print(f"{name}: ||r_pair - r_ref|| / ||b|| = {d:.3e}, relres {rel:.2e}")
-    assert d <= 1e-14, d
+    assert d <= 5e-14, d
     S.close()
 
 
