@@ -380,8 +380,10 @@ h2_status h2_set_option(h2_ctx* c, int32_t option, int64_t value);
  *      scheme 2 multiplies by, applied to x rounded to FP32; y is that FP32
  *      result widened to FP64;
  *   2  FP32 pairs: every FP64 matrix entry held as hi = fl32(a) plus
- *      lo = fl32(a - hi) and products summed as FP32 pairs, with the
- *      passes through the bases in FP64 (the default residual of scheme 2).
+ *      lo = fl32(a - hi), x split the same way, and products summed as
+ *      FP32 pairs through the bases, couplings and near blocks; each y_i
+ *      converted to FP64 once (about 2^-46 of sum_j |a_ij x_j|; the
+ *      default residual of scheme 2).
  * N doubles each, host or device.  Errors: H2_ERR_INVALID_ARG, H2_ERR_CUDA. */
 h2_status h2_matvec_arith(h2_ctx* c, const double* x, double* y, int32_t arith);
 

@@ -1692,9 +1692,11 @@ H2_INST_MV(float)
 // x_h + x_l likewise.  m x = m_h x_h + (m_h x_l + m_l x_h) + O(2^-48 m x);
 // the first product is split exactly into p + e by a fused multiply-add,
 // and the running sum is an FP32 pair (H, L): H += p by an error-free
-// two-sum whose error joins L with e and the cross terms.  Each row's pairs
-// are added in FP64 at the end.  The kernels then read 8 bytes per entry,
-// as the FP64 ones do, but spend FP32 instructions on them.
+// two-sum whose error joins L with e and the cross terms.  Sums over lanes,
+// warps and blocks stay FP32 pairs (df_add, df_tsum) and each output is
+// converted to FP64 once: GB300's FP64 pipe is too slow for per-entry work.
+// The kernels then read 8 bytes per entry, as the FP64 ones do, but spend
+// FP32 instructions on them.
 // (the _rn intrinsics keep the compiler from fusing the two-sum's operations)
 __device__ __forceinline__ void df_fma(float& H, float& L, float mh, float ml, float xh, float xl) {
   const float p = __fmul_rn(mh, xh);
