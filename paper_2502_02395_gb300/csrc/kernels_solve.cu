@@ -870,8 +870,11 @@ __device__ __forceinline__ void fwd1_body(int64_t t, int D, int R, int ns, const
     cta_gemv<T, T, Unr<T>::v>(U + ((int64_t)i * D + b0) * D, D, b1 - b0, D, sv, T(1), nullptr,
                               c + (int64_t)i * D + b0, hook);
 }
+// (two CTAs per SM: the register cap spills a few bytes of the assembly of b
+// but doubles the loads in flight per SM; the substitution took 21.5 ms
+// per step instead of 22.0 ms at 162 registers and one CTA per SM)
 template <typename T>
-__global__ void __launch_bounds__(256) fwd1_kernel(int D, int R, int ns, const T* __restrict__ M1,
+__global__ void __launch_bounds__(256, 2) fwd1_kernel(int D, int R, int ns, const T* __restrict__ M1,
                                                    const T* __restrict__ U, const T* __restrict__ vin,
                                                    ChildIn<T> ch, T* __restrict__ u, T* __restrict__ c) {
   fwd1_body<T>(blockIdx.x, D, R, ns, M1, U, vin, ch, u, c, true);
