@@ -2391,8 +2391,6 @@ void launch_matvec_sym_sum(int nb, int D, int K, const int64_t* ptr, const int32
 }
 template void launch_matvec_sym_sum<float>(int, int, int, const int64_t*, const int32_t*, const float*, const float*,
                                            const float*, float*, cudaStream_t, bool);
-template void launch_matvec_sym_sum<double>(int, int, int, const int64_t*, const int32_t*, const double*,
-                                            const double*, const double*, double*, cudaStream_t, bool);
 
 // out[k] = (To) in[idx[k]] for blocks of n entries
 template <typename Ti, typename To>
