@@ -37,6 +37,13 @@ def test_exports_every_declared_symbol(B):
     assert sorted(B.EXPORTED) == names
 
 
+def test_library_binds_every_symbol_at_load(B):
+    """With immediate binding every symbol the library references resolves
+    at load time (a template launcher used but never instantiated would only
+    fail at its first call otherwise)."""
+    ctypes.CDLL(B.LIB_PATH, mode=os.RTLD_NOW)
+
+
 @pytest.mark.parametrize("n,leaf,eta,geom", [(2048, 64, 1.0, "cube"), (1000, 64, 1.0, "cube"),
                                              (3000, 100, 0.0, "sphere"), (777, 50, 2.0, "cube")])
 def test_plan_lists_match_oracle(B, n, leaf, eta, geom):
